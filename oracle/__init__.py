@@ -1,0 +1,241 @@
+"""FP64 CPU oracle of the online 3DGS optimisation step (TEST INFRASTRUCTURE).
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  It shares no code with the CUDA path:
+the arithmetic lives in ``gs_oracle.c`` (plain C, double precision), and this
+wrapper only converts array layouts and calls it.
+
+Every stage takes its inputs explicitly so that a test can feed it either the
+oracle's own upstream results (end to end) or the GPU's float32 upstream
+results (stage-wise comparison).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from gs_inputs import planes_to_rows, rows_to_planes
+from . import build as _build
+
+_lib = None
+
+_D = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
+_F = np.ctypeslib.ndpointer(dtype=np.float32, flags="C_CONTIGUOUS")
+_I32 = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
+_U32 = np.ctypeslib.ndpointer(dtype=np.uint32, flags="C_CONTIGUOUS")
+_U64 = np.ctypeslib.ndpointer(dtype=np.uint64, flags="C_CONTIGUOUS")
+_U8 = np.ctypeslib.ndpointer(dtype=np.uint8, flags="C_CONTIGUOUS")
+
+TILE = 16
+PROJ_FIELDS = ("u", "v", "depth", "opacity", "A", "B", "C", "radius", "r", "g", "b",
+               "clamp", "x0", "y0", "x1", "y1")
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = C.CDLL(path)
+        L.or_sh_basis.argtypes = [_D, _D]
+        L.or_sh_basis_grad.argtypes = [_D, _D]
+        L.or_rect.argtypes = [C.c_double, C.c_double, C.c_double, C.c_int, C.c_int, C.c_int, _I32]
+        L.or_project.argtypes = [C.c_int64, C.c_int, _D, C.c_int, _D, C.c_int, _D]
+        L.or_bin_count.argtypes = [C.c_int, C.c_int64, _I32]
+        L.or_bin_count.restype = C.c_int64
+        L.or_bin_sort.argtypes = [C.c_int, C.c_int64, _D, C.c_int, _I32, _F, _U64, _U32, _U32]
+        L.or_bin_sort.restype = C.c_int64
+        L.or_render.argtypes = [C.c_int, C.c_int64, _D, C.c_int, _D, _U32, _U32, _D, _D, _D, _I32]
+        L.or_render_bwd.argtypes = [C.c_int, C.c_int64, _D, C.c_int, _D, _U32, _U32, _D, _D, _D]
+        L.or_project_bwd.argtypes = [C.c_int64, C.c_int, _D, C.c_int, _D, C.c_int, _D, _D]
+        L.or_ssim_map.argtypes = [C.c_int, C.c_int, _D, _D, _D, C.c_void_p]
+        L.or_loss.argtypes = [C.c_int, C.c_int, C.c_int, _D, _D, C.c_double, C.c_double, _D]
+        L.or_loss.restype = C.c_double
+        L.or_adam.argtypes = [C.c_int64, _D, _D, _D, _D, _D, C.c_double, C.c_double, C.c_double, C.c_int]
+        L.or_f32_to_f16.argtypes = [C.c_float]
+        L.or_f32_to_f16.restype = C.c_uint16
+        L.or_delta.argtypes = [C.c_int64, _F, _F, C.c_float, _U32, _U8]
+        L.or_delta.restype = C.c_int64
+        _lib = L
+    return _lib
+
+
+def _d(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+# ------------------------------------------------------------------ layout
+def cams_array(cams: dict) -> np.ndarray:
+    """Camera dict (see gs_inputs) -> oracle records [V][20] float64."""
+    V = len(cams["fx"])
+    out = np.zeros((V, 20))
+    out[:, 0:9] = np.asarray(cams["R"]).reshape(V, 9)
+    out[:, 9:12] = cams["t"]
+    out[:, 12] = cams["fx"]; out[:, 13] = cams["fy"]
+    out[:, 14] = cams["cx"]; out[:, 15] = cams["cy"]
+    out[:, 16] = cams["width"]; out[:, 17] = cams["height"]
+    out[:, 18] = cams["near"]
+    return out
+
+
+def view_shapes(cams: dict):
+    return [(int(h), int(w)) for w, h in zip(cams["width"], cams["height"])]
+
+
+def n_tiles(cams: dict, tile: int = TILE) -> int:
+    return int(sum(((int(w) + tile - 1) // tile) * ((int(h) + tile - 1) // tile)
+                   for w, h in zip(cams["width"], cams["height"])))
+
+
+def n_pixels(cams: dict) -> int:
+    return int(sum(int(w) * int(h) for w, h in zip(cams["width"], cams["height"])))
+
+
+# ------------------------------------------------------------------ stages
+def sh_basis(d) -> np.ndarray:
+    Y = np.zeros(16)
+    lib().or_sh_basis(_d(d), Y)
+    return Y
+
+
+def sh_basis_grad(d) -> np.ndarray:
+    dY = np.zeros(48)
+    lib().or_sh_basis_grad(_d(d), dY)
+    return dY.reshape(16, 3)
+
+
+def rect(u, v, r, width, height, tile=TILE):
+    out = np.zeros(4, dtype=np.int32)
+    lib().or_rect(float(u), float(v), float(r), int(width), int(height), int(tile), out)
+    return out
+
+
+def project(planes, sh_degree: int, cams: dict, tile: int = TILE) -> np.ndarray:
+    """-> proj [V][n][16] float64 (fields PROJ_FIELDS; zero when culled)."""
+    rows = _d(planes_to_rows(planes))
+    n = rows.shape[0]
+    V = len(cams["fx"])
+    out = np.zeros((V, n, 16))
+    lib().or_project(n, sh_degree, rows, V, cams_array(cams), tile, out)
+    return out
+
+
+def rects_of(proj) -> np.ndarray:
+    return np.ascontiguousarray(proj[..., 12:16].astype(np.int32))
+
+
+def bin_sort(cams: dict, rects, depth32, tile: int = TILE):
+    """rects [V][n][4] int32, depth32 [V][n] float32 -> (keys u64, vals u32, ranges [T][2])."""
+    rects = np.ascontiguousarray(rects, dtype=np.int32)
+    depth32 = np.ascontiguousarray(depth32, dtype=np.float32)
+    V, n = depth32.shape
+    K = int(lib().or_bin_count(V, n, rects))
+    keys = np.zeros(max(K, 1), dtype=np.uint64)
+    vals = np.zeros(max(K, 1), dtype=np.uint32)
+    ranges = np.zeros((n_tiles(cams, tile), 2), dtype=np.uint32)
+    lib().or_bin_sort(V, n, cams_array(cams), tile, rects, depth32, keys, vals, ranges)
+    return keys[:K], vals[:K], ranges
+
+
+def render(cams: dict, proj, vals, ranges, bg=(0.0, 0.0, 0.0), tile: int = TILE):
+    """-> (image [sum 3HW], T_final [sum HW], n_contrib [sum HW]) flat per view."""
+    proj = _d(proj)
+    V, n = proj.shape[:2]
+    P = n_pixels(cams)
+    img = np.zeros(3 * P); T = np.zeros(P); nc = np.zeros(P, dtype=np.int32)
+    lib().or_render(V, n, cams_array(cams), tile, proj,
+                    np.ascontiguousarray(vals, dtype=np.uint32),
+                    np.ascontiguousarray(ranges, dtype=np.uint32), _d(bg), img, T, nc)
+    return img, T, nc
+
+
+def render_bwd(cams: dict, proj, vals, ranges, dimage, bg=(0.0, 0.0, 0.0), tile: int = TILE):
+    """-> grad2d [V][n][9]."""
+    proj = _d(proj)
+    V, n = proj.shape[:2]
+    g = np.zeros((V, n, 9))
+    lib().or_render_bwd(V, n, cams_array(cams), tile, proj,
+                        np.ascontiguousarray(vals, dtype=np.uint32),
+                        np.ascontiguousarray(ranges, dtype=np.uint32), _d(bg), _d(dimage), g)
+    return g
+
+
+def project_bwd(planes, sh_degree: int, cams: dict, grad2d, tile: int = TILE) -> np.ndarray:
+    """-> parameter gradient as planes [15][n][4] float64."""
+    rows = _d(planes_to_rows(planes))
+    n = rows.shape[0]
+    V = len(cams["fx"])
+    d = np.zeros((n, 60))
+    lib().or_project_bwd(n, sh_degree, rows, V, cams_array(cams), tile, _d(grad2d), d)
+    return rows_to_planes(d)
+
+
+def ssim_map(x, y, with_partials: bool = False):
+    x = _d(x); y = _d(y)
+    H, W = x.shape
+    s = np.zeros((H, W))
+    if with_partials:
+        d = np.zeros((H, W, 3))
+        lib().or_ssim_map(H, W, x, y, s, d.ctypes.data_as(C.c_void_p))
+        return s, d
+    lib().or_ssim_map(H, W, x, y, s, None)
+    return s
+
+
+def loss(image, target, V: int, H: int, W: int, w_l1: float = 0.8, w_ssim: float = 0.2):
+    """-> (L, dL/dimage) for V equal-size views, planar [V][3][H][W]."""
+    dimg = np.zeros(V * 3 * H * W)
+    L = lib().or_loss(V, H, W, _d(image).ravel(), _d(target).ravel(), w_l1, w_ssim, dimg)
+    return float(L), dimg
+
+
+def adam(theta, grad, m, v, lr, step: int, b1=0.9, b2=0.999, eps=1e-8):
+    """In place on float64 arrays; lr broadcast to theta's shape."""
+    lr = np.ascontiguousarray(np.broadcast_to(lr, theta.shape), dtype=np.float64)
+    lib().or_adam(theta.size, theta, _d(grad), m, v, lr, b1, b2, eps, step)
+
+
+def f32_to_f16_bits(x) -> np.ndarray:
+    x = np.asarray(x, dtype=np.float32).ravel()
+    return np.array([lib().or_f32_to_f16(float(v)) for v in x], dtype=np.uint16)
+
+
+def delta(theta_planes, base_planes, thr: float = 1e-3):
+    """Float32 planes in; returns (idx u32[M], records u8[M][128], new baseline planes)."""
+    th = np.ascontiguousarray(planes_to_rows(theta_planes), dtype=np.float32)
+    base = np.ascontiguousarray(planes_to_rows(base_planes), dtype=np.float32)
+    n = th.shape[0]
+    idx = np.zeros(max(n, 1), dtype=np.uint32)
+    rec = np.zeros((max(n, 1), 128), dtype=np.uint8)
+    M = int(lib().or_delta(n, th, base, np.float32(thr), idx, rec))
+    return idx[:M], rec[:M], rows_to_planes(base)
+
+
+# ------------------------------------------------------------------ composed
+def forward(planes, sh_degree, cams, bg=(0.0, 0.0, 0.0), tile=TILE):
+    proj = project(planes, sh_degree, cams, tile)
+    keys, vals, ranges = bin_sort(cams, rects_of(proj), proj[..., 2].astype(np.float32), tile)
+    img, T, nc = render(cams, proj, vals, ranges, bg, tile)
+    return {"proj": proj, "keys": keys, "vals": vals, "ranges": ranges,
+            "image": img, "T_final": T, "n_contrib": nc}
+
+
+def loss_and_grad(planes, sh_degree, cams, target, w_l1=0.8, w_ssim=0.2,
+                  bg=(0.0, 0.0, 0.0), tile=TILE):
+    """Full FP64 chain: render, loss, image gradient, 2D and parameter gradients."""
+    f = forward(planes, sh_degree, cams, bg, tile)
+    V = len(cams["fx"])
+    H, W = int(cams["height"][0]), int(cams["width"][0])
+    L, dimg = loss(f["image"], target, V, H, W, w_l1, w_ssim)
+    g2 = render_bwd(cams, f["proj"], f["vals"], f["ranges"], dimg, bg, tile)
+    dp = project_bwd(planes, sh_degree, cams, g2, tile)
+    f.update({"loss": L, "dimage": dimg, "grad2d": g2, "dparams": dp})
+    return f
+
+
+def render_loss(planes, sh_degree, cams, target, w_l1=0.8, w_ssim=0.2, bg=(0.0, 0.0, 0.0), tile=TILE):
+    f = forward(planes, sh_degree, cams, bg, tile)
+    V = len(cams["fx"])
+    H, W = int(cams["height"][0]), int(cams["width"][0])
+    return loss(f["image"], target, V, H, W, w_l1, w_ssim)[0]

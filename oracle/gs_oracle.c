@@ -1,0 +1,748 @@
+/*
+ * FP64 CPU oracle of the online 3DGS optimisation step -- TEST INFRASTRUCTURE.
+ *
+ * Only the test suite, the smoke check and the benchmark's CPU-baseline leg
+ * may load this library.  It shares no code with the CUDA path.  It is the
+ * plain, slow definition of what the step computes, written out in the order
+ * the method states it; every function names the passage it follows.
+ *
+ * The paper (Sec. 3.2.3) refines "the same parameters as in prior 3DGS work"
+ * by differentiable rendering, and states no formula itself.  The maths here
+ * is the standard EWA-splatting definition of the cited 3DGS method with the
+ * constants fixed for this build (alpha clamp 0.99, 1/255 cut-off, T < 1e-4
+ * termination, L1 + D-SSIM with an 11x11 sigma=1.5 window, Adam).  Readings
+ * where the paper is silent are marked READING.
+ *
+ * Layouts (oracle side; the Python wrapper converts, it does no arithmetic):
+ *   rows   [n][60]  : mean xyz, opacity logit, log-scale xyz, pad,
+ *                     quaternion wxyz, 48 SH coefficients (3*k + channel)
+ *   cams   [V][20]  : R (row-major world->camera), t, fx, fy, cx, cy,
+ *                     width, height, near, unused
+ *   proj   [V][n][16]: u, v, depth, opacity, A, B, C, radius, r, g, b,
+ *                     clamp mask, x0, y0, x1, y1   (all zero when culled)
+ *   grad2d [V][n][9] : dL/du, dL/dv, dL/dA, dL/dB, dL/dC, dL/dopacity,
+ *                     dL/dr, dL/dg, dL/db
+ *   images : views concatenated, each planar [3][H][W]
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define CAM_STRIDE 20
+#define PROJ_STRIDE 16
+#define G2D_STRIDE 9
+#define ROW 60
+
+/* READING: constants fixed for this build from the cited method. */
+static const double ALPHA_MAX = 0.99;
+static const double ALPHA_MIN = 1.0 / 255.0;
+static const double T_MIN = 1e-4;
+static const double DILATION = 0.3;
+static const double GUARD = 1.3;
+
+static double clampd(double x, double lo, double hi) { return x < lo ? lo : (x > hi ? hi : x); }
+
+/* ------------------------------------------------------------------------
+ * Real spherical harmonics, degree <= 3, order l = 0..3, m = -l..l.
+ * Sec. 3.2.2 / 3.4.1: appearance is stored as SH coefficients.
+ * Convention: the real form of the complex harmonics with the
+ * Condon-Shortley phase kept (sqrt(2) Re Y_l^m for m > 0, sqrt(2) Im Y_l^|m|
+ * for m < 0), which is the sign pattern of the cited 3DGS method.  Written as
+ * polynomials of the unit direction (x, y, z); normalisations are the closed
+ * forms sqrt((2l+1)/(4 pi) (l-|m|)!/(l+|m|)!) times the polynomial factor.
+ * ---------------------------------------------------------------------- */
+void or_sh_basis(const double* d, double* Y) {
+    const double PI = 3.14159265358979323846;
+    double x = d[0], y = d[1], z = d[2];
+    double xx = x * x, yy = y * y, zz = z * z;
+    double k0 = sqrt(1.0 / (4.0 * PI));
+    double k1 = sqrt(3.0 / (4.0 * PI));
+    double k2a = sqrt(15.0 / (4.0 * PI)), k2b = sqrt(5.0 / (16.0 * PI)), k2c = sqrt(15.0 / (16.0 * PI));
+    double k3a = sqrt(35.0 / (32.0 * PI)), k3b = sqrt(105.0 / (4.0 * PI)), k3c = sqrt(21.0 / (32.0 * PI));
+    double k3d = sqrt(7.0 / (16.0 * PI)), k3e = sqrt(105.0 / (16.0 * PI));
+    Y[0] = k0;
+    Y[1] = -k1 * y;
+    Y[2] = k1 * z;
+    Y[3] = -k1 * x;
+    Y[4] = k2a * x * y;
+    Y[5] = -k2a * y * z;
+    Y[6] = k2b * (2.0 * zz - xx - yy);
+    Y[7] = -k2a * x * z;
+    Y[8] = k2c * (xx - yy);
+    Y[9] = -k3a * y * (3.0 * xx - yy);
+    Y[10] = k3b * x * y * z;
+    Y[11] = -k3c * y * (4.0 * zz - xx - yy);
+    Y[12] = k3d * z * (2.0 * zz - 3.0 * xx - 3.0 * yy);
+    Y[13] = -k3c * x * (4.0 * zz - xx - yy);
+    Y[14] = k3e * z * (xx - yy);
+    Y[15] = -k3a * x * (xx - 3.0 * yy);
+}
+
+/* Partial derivatives of the polynomials above w.r.t. (x, y, z): dY[k*3+i]. */
+void or_sh_basis_grad(const double* d, double* dY) {
+    const double PI = 3.14159265358979323846;
+    double x = d[0], y = d[1], z = d[2];
+    double xx = x * x, yy = y * y, zz = z * z;
+    double k1 = sqrt(3.0 / (4.0 * PI));
+    double k2a = sqrt(15.0 / (4.0 * PI)), k2b = sqrt(5.0 / (16.0 * PI)), k2c = sqrt(15.0 / (16.0 * PI));
+    double k3a = sqrt(35.0 / (32.0 * PI)), k3b = sqrt(105.0 / (4.0 * PI)), k3c = sqrt(21.0 / (32.0 * PI));
+    double k3d = sqrt(7.0 / (16.0 * PI)), k3e = sqrt(105.0 / (16.0 * PI));
+    memset(dY, 0, sizeof(double) * 48);
+#define SETG(k, gx, gy, gz) do { dY[(k)*3+0] = (gx); dY[(k)*3+1] = (gy); dY[(k)*3+2] = (gz); } while (0)
+    SETG(1, 0.0, -k1, 0.0);
+    SETG(2, 0.0, 0.0, k1);
+    SETG(3, -k1, 0.0, 0.0);
+    SETG(4, k2a * y, k2a * x, 0.0);
+    SETG(5, 0.0, -k2a * z, -k2a * y);
+    SETG(6, -2.0 * k2b * x, -2.0 * k2b * y, 4.0 * k2b * z);
+    SETG(7, -k2a * z, 0.0, -k2a * x);
+    SETG(8, 2.0 * k2c * x, -2.0 * k2c * y, 0.0);
+    SETG(9, -k3a * 6.0 * x * y, -k3a * (3.0 * xx - 3.0 * yy), 0.0);
+    SETG(10, k3b * y * z, k3b * x * z, k3b * x * y);
+    SETG(11, -k3c * y * (-2.0 * x), -k3c * (4.0 * zz - xx - 3.0 * yy), -k3c * y * 8.0 * z);
+    SETG(12, k3d * z * (-6.0 * x), k3d * z * (-6.0 * y), k3d * (6.0 * zz - 3.0 * xx - 3.0 * yy));
+    SETG(13, -k3c * (4.0 * zz - 3.0 * xx - yy), -k3c * x * (-2.0 * y), -k3c * x * 8.0 * z);
+    SETG(14, k3e * z * 2.0 * x, k3e * z * (-2.0 * y), k3e * (xx - yy));
+    SETG(15, -k3a * (3.0 * xx - 3.0 * yy), -k3a * x * (-6.0 * y), 0.0);
+#undef SETG
+}
+
+/* Unit quaternion (w, x, y, z) -> rotation matrix, row-major. */
+static void quat_to_rot(const double* q, double* R) {
+    double w = q[0], x = q[1], y = q[2], z = q[3];
+    R[0] = 1.0 - 2.0 * (y * y + z * z); R[1] = 2.0 * (x * y - w * z);       R[2] = 2.0 * (x * z + w * y);
+    R[3] = 2.0 * (x * y + w * z);       R[4] = 1.0 - 2.0 * (x * x + z * z); R[5] = 2.0 * (y * z - w * x);
+    R[6] = 2.0 * (x * z - w * y);       R[7] = 2.0 * (y * z + w * x);       R[8] = 1.0 - 2.0 * (x * x + y * y);
+}
+
+static int tiles_along(int extent, int tile) { return (extent + tile - 1) / tile; }
+
+/* Tile rectangle [x0, x1) x [y0, y1) of the screen-space square of half-side r
+ * around (u, v), clamped to the tile grid.  READING of the cited method's
+ * binning: the Gaussian is evaluated at every pixel of every tile it touches. */
+void or_rect(double u, double v, double r, int W, int H, int tile, int32_t* rect) {
+    int TX = tiles_along(W, tile), TY = tiles_along(H, tile);
+    rect[0] = (int32_t)clampd(floor((u - r) / tile), 0.0, (double)TX);
+    rect[1] = (int32_t)clampd(floor((v - r) / tile), 0.0, (double)TY);
+    rect[2] = (int32_t)clampd(floor((u + r + tile - 1) / tile), 0.0, (double)TX);
+    rect[3] = (int32_t)clampd(floor((v + r + tile - 1) / tile), 0.0, (double)TY);
+}
+
+/* ------------------------------------------------------------------------
+ * Projection + SH colour (Sec. 3.2.3: the 3DGS parameters rendered by
+ * differentiable splatting; Sec. 3.2.2: SH appearance).
+ * ---------------------------------------------------------------------- */
+typedef struct {
+    double t[3];      /* camera-space mean */
+    double xt, yt;    /* guard-band clamped t_x, t_y used in J */
+    int clx, cly;     /* -1 / 0 / +1: which side the guard band clamped */
+    double limx, limy;
+    double J[6];      /* 2x3 */
+    double M[6];      /* J W, 2x3 */
+    double a, b, c, det;
+    double dir[3], len;
+    double Y[16];
+} view_geom;
+
+static void gauss_common(const double* p, double* mu, double* s, double* qhat, double* qnorm,
+                         double* R, double* Sig, double* opac) {
+    mu[0] = p[0]; mu[1] = p[1]; mu[2] = p[2];
+    *opac = 1.0 / (1.0 + exp(-p[3]));
+    for (int i = 0; i < 3; ++i) s[i] = exp(p[4 + i]);
+    double qn = sqrt(p[8] * p[8] + p[9] * p[9] + p[10] * p[10] + p[11] * p[11]);
+    *qnorm = qn;
+    for (int i = 0; i < 4; ++i) qhat[i] = p[8 + i] / qn;
+    quat_to_rot(qhat, R);
+    /* Sigma = R diag(s^2) R^T */
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double acc = 0.0;
+            for (int k = 0; k < 3; ++k) acc += R[i * 3 + k] * s[k] * s[k] * R[j * 3 + k];
+            Sig[i * 3 + j] = acc;
+        }
+}
+
+/* Returns 1 if the Gaussian survives the near-plane and determinant tests. */
+static int view_geometry(const double* mu, const double* Sig, const double* cam, view_geom* G) {
+    const double* W = cam;
+    const double* tc = cam + 9;
+    double fx = cam[12], fy = cam[13];
+    double Wimg = cam[16], Himg = cam[17], near = cam[18];
+    for (int i = 0; i < 3; ++i) G->t[i] = W[i * 3] * mu[0] + W[i * 3 + 1] * mu[1] + W[i * 3 + 2] * mu[2] + tc[i];
+    double tz = G->t[2];
+    if (tz <= near) return 0;
+    G->limx = GUARD * (Wimg / (2.0 * fx));
+    G->limy = GUARD * (Himg / (2.0 * fy));
+    double rx = G->t[0] / tz, ry = G->t[1] / tz;
+    G->clx = rx < -G->limx ? -1 : (rx > G->limx ? 1 : 0);
+    G->cly = ry < -G->limy ? -1 : (ry > G->limy ? 1 : 0);
+    G->xt = clampd(rx, -G->limx, G->limx) * tz;
+    G->yt = clampd(ry, -G->limy, G->limy) * tz;
+    G->J[0] = fx / tz; G->J[1] = 0.0; G->J[2] = -fx * G->xt / (tz * tz);
+    G->J[3] = 0.0; G->J[4] = fy / tz; G->J[5] = -fy * G->yt / (tz * tz);
+    for (int k = 0; k < 2; ++k)
+        for (int i = 0; i < 3; ++i) {
+            double acc = 0.0;
+            for (int l = 0; l < 3; ++l) acc += G->J[k * 3 + l] * W[l * 3 + i];
+            G->M[k * 3 + i] = acc;
+        }
+    double a = 0.0, b = 0.0, c = 0.0;
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            a += G->M[i] * Sig[i * 3 + j] * G->M[j];
+            b += G->M[i] * Sig[i * 3 + j] * G->M[3 + j];
+            c += G->M[3 + i] * Sig[i * 3 + j] * G->M[3 + j];
+        }
+    G->a = a + DILATION;
+    G->b = b;
+    G->c = c + DILATION;
+    G->det = G->a * G->c - G->b * G->b;
+    if (G->det <= 0.0) return 0;
+    /* view direction from the camera centre -W^T t */
+    double cp[3];
+    for (int i = 0; i < 3; ++i) cp[i] = -(W[i] * tc[0] + W[3 + i] * tc[1] + W[6 + i] * tc[2]);
+    double dv[3] = {mu[0] - cp[0], mu[1] - cp[1], mu[2] - cp[2]};
+    G->len = sqrt(dv[0] * dv[0] + dv[1] * dv[1] + dv[2] * dv[2]);
+    for (int i = 0; i < 3; ++i) G->dir[i] = dv[i] / G->len;
+    or_sh_basis(G->dir, G->Y);
+    return 1;
+}
+
+void or_project(int64_t n, int sh_degree, const double* rows, int V, const double* cams,
+                int tile, double* out) {
+    int nb = (sh_degree + 1) * (sh_degree + 1);
+#pragma omp parallel for schedule(dynamic, 1024)
+    for (int64_t g = 0; g < n; ++g) {
+        const double* p = rows + g * ROW;
+        double mu[3], s[3], q[4], qn, R[9], Sig[9], opac;
+        gauss_common(p, mu, s, q, &qn, R, Sig, &opac);
+        for (int v = 0; v < V; ++v) {
+            const double* cam = cams + (int64_t)v * CAM_STRIDE;
+            double* o = out + ((int64_t)v * n + g) * PROJ_STRIDE;
+            memset(o, 0, sizeof(double) * PROJ_STRIDE);
+            view_geom G;
+            if (!view_geometry(mu, Sig, cam, &G)) continue;
+            double mid = 0.5 * (G.a + G.c);
+            double lam = mid + sqrt(fmax(0.1, mid * mid - G.det));
+            double r = ceil(3.0 * sqrt(lam));
+            double u = cam[12] * G.t[0] / G.t[2] + cam[14];
+            double vv = cam[13] * G.t[1] / G.t[2] + cam[15];
+            int32_t rect[4];
+            or_rect(u, vv, r, (int)cam[16], (int)cam[17], tile, rect);
+            if ((rect[2] - rect[0]) * (rect[3] - rect[1]) == 0) continue;
+            double rgb[3];
+            int mask = 0;
+            for (int ch = 0; ch < 3; ++ch) {
+                double acc = 0.0;
+                for (int k = 0; k < nb; ++k) acc += p[12 + 3 * k + ch] * G.Y[k];
+                acc += 0.5;
+                if (acc < 0.0) { acc = 0.0; mask |= 1 << ch; }
+                rgb[ch] = acc;
+            }
+            o[0] = u; o[1] = vv; o[2] = G.t[2]; o[3] = opac;
+            o[4] = G.c / G.det; o[5] = -G.b / G.det; o[6] = G.a / G.det; o[7] = r;
+            o[8] = rgb[0]; o[9] = rgb[1]; o[10] = rgb[2]; o[11] = (double)mask;
+            o[12] = rect[0]; o[13] = rect[1]; o[14] = rect[2]; o[15] = rect[3];
+        }
+    }
+}
+
+/* ------------------------------------------------------------------------
+ * Binning and sort.  Every (view, Gaussian, touched tile) becomes one entry;
+ * entries are ordered lexicographically by (view, tile, depth as float32 bits,
+ * Gaussian index).  READING: depth = camera-space z; the sort key uses the
+ * float32 value of the depth so that float32 and float64 producers agree.
+ * Tile index: per-view offset + ty * TX + tx (views in order).
+ * ---------------------------------------------------------------------- */
+typedef struct { uint64_t key; uint32_t g; } entry;
+
+static int cmp_entry(const void* A, const void* B) {
+    const entry* a = (const entry*)A;
+    const entry* b = (const entry*)B;
+    if (a->key != b->key) return a->key < b->key ? -1 : 1;
+    return a->g < b->g ? -1 : (a->g > b->g ? 1 : 0);
+}
+
+int64_t or_bin_count(int V, int64_t n, const int32_t* rects) {
+    int64_t K = 0;
+    for (int64_t i = 0; i < (int64_t)V * n; ++i) {
+        const int32_t* r = rects + i * 4;
+        K += (int64_t)(r[2] - r[0]) * (r[3] - r[1]);
+    }
+    return K;
+}
+
+/* rects [V][n][4], depth [V][n] float32; writes keys (u64), vals (u32),
+ * ranges [total_tiles][2]; returns the entry count. */
+int64_t or_bin_sort(int V, int64_t n, const double* cams, int tile, const int32_t* rects,
+                    const float* depth, uint64_t* keys, uint32_t* vals, uint32_t* ranges) {
+    int64_t K = or_bin_count(V, n, rects);
+    entry* E = (entry*)malloc(sizeof(entry) * (size_t)(K > 0 ? K : 1));
+    int64_t toff = 0, k = 0;
+    for (int v = 0; v < V; ++v) {
+        const double* cam = cams + (int64_t)v * CAM_STRIDE;
+        int TX = tiles_along((int)cam[16], tile), TY = tiles_along((int)cam[17], tile);
+        for (int64_t g = 0; g < n; ++g) {
+            const int32_t* r = rects + ((int64_t)v * n + g) * 4;
+            uint32_t dbits;
+            memcpy(&dbits, &depth[(int64_t)v * n + g], 4);
+            for (int ty = r[1]; ty < r[3]; ++ty)
+                for (int tx = r[0]; tx < r[2]; ++tx) {
+                    E[k].key = ((uint64_t)(toff + (int64_t)ty * TX + tx) << 32) | dbits;
+                    E[k].g = (uint32_t)g;
+                    ++k;
+                }
+        }
+        for (int64_t t = 0; t < (int64_t)TX * TY; ++t) { ranges[(toff + t) * 2] = 0; ranges[(toff + t) * 2 + 1] = 0; }
+        toff += (int64_t)TX * TY;
+    }
+    qsort(E, (size_t)K, sizeof(entry), cmp_entry);
+    for (int64_t i = 0; i < K; ++i) {
+        keys[i] = E[i].key;
+        vals[i] = E[i].g;
+        uint32_t t = (uint32_t)(E[i].key >> 32);
+        if (i == 0 || (uint32_t)(E[i - 1].key >> 32) != t) ranges[(int64_t)t * 2] = (uint32_t)i;
+        if (i == K - 1 || (uint32_t)(E[i + 1].key >> 32) != t) ranges[(int64_t)t * 2 + 1] = (uint32_t)(i + 1);
+    }
+    free(E);
+    return K;
+}
+
+/* ------------------------------------------------------------------------
+ * Front-to-back alpha compositing (Sec. 3.2.3 differentiable rendering, as in
+ * the cited method).  Per pixel, in sorted order, from T = 1:
+ *   d = (u, v) - pixel centre, P = -(A dx^2 + C dy^2)/2 - B dx dy,
+ *   skip if P > 0; alpha = min(0.99, o e^P); skip if alpha < 1/255;
+ *   T' = T (1 - alpha); READING: if T' < 1e-4 stop without adding it;
+ *   else C += rgb alpha T, T = T'.  Output C + T bg.  n_contrib = position
+ *   (1-based, within the tile's list) of the last fragment added.
+ * Pixel (x, y) is sampled at (x + 0.5, y + 0.5).
+ * ---------------------------------------------------------------------- */
+static int64_t view_tile_offset(const double* cams, int v, int tile) {
+    int64_t off = 0;
+    for (int w = 0; w < v; ++w) {
+        const double* c = cams + (int64_t)w * CAM_STRIDE;
+        off += (int64_t)tiles_along((int)c[16], tile) * tiles_along((int)c[17], tile);
+    }
+    return off;
+}
+
+static int64_t view_pixel_offset(const double* cams, int v) {
+    int64_t off = 0;
+    for (int w = 0; w < v; ++w) off += (int64_t)cams[w * CAM_STRIDE + 16] * (int64_t)cams[w * CAM_STRIDE + 17];
+    return off;
+}
+
+void or_render(int V, int64_t n, const double* cams, int tile, const double* proj,
+               const uint32_t* vals, const uint32_t* ranges, const double* bg,
+               double* image, double* T_final, int32_t* n_contrib) {
+    for (int v = 0; v < V; ++v) {
+        const double* cam = cams + (int64_t)v * CAM_STRIDE;
+        int W = (int)cam[16], H = (int)cam[17], TX = tiles_along(W, tile);
+        int64_t toff = view_tile_offset(cams, v, tile), poff = view_pixel_offset(cams, v);
+        double* img = image + 3 * poff;
+#pragma omp parallel for schedule(dynamic, 4)
+        for (int y = 0; y < H; ++y)
+            for (int x = 0; x < W; ++x) {
+                int64_t t = toff + (int64_t)(y / tile) * TX + x / tile;
+                uint32_t s = ranges[2 * t], e = ranges[2 * t + 1];
+                double px = x + 0.5, py = y + 0.5, T = 1.0, C[3] = {0, 0, 0};
+                int32_t nc = 0;
+                for (uint32_t j = s; j < e; ++j) {
+                    const double* o = proj + ((int64_t)v * n + vals[j]) * PROJ_STRIDE;
+                    double dx = o[0] - px, dy = o[1] - py;
+                    double P = -0.5 * (o[4] * dx * dx + o[6] * dy * dy) - o[5] * dx * dy;
+                    if (P > 0.0) continue;
+                    double al = fmin(ALPHA_MAX, o[3] * exp(P));
+                    if (al < ALPHA_MIN) continue;
+                    double Tn = T * (1.0 - al);
+                    if (Tn < T_MIN) break;
+                    for (int ch = 0; ch < 3; ++ch) C[ch] += o[8 + ch] * al * T;
+                    T = Tn;
+                    nc = (int32_t)(j - s + 1);
+                }
+                int64_t pix = (int64_t)y * W + x;
+                for (int ch = 0; ch < 3; ++ch) img[(int64_t)ch * W * H + pix] = C[ch] + T * bg[ch];
+                T_final[poff + pix] = T;
+                n_contrib[poff + pix] = nc;
+            }
+    }
+}
+
+/* Adjoint of or_render: per pixel, re-walk the list, keep each added
+ * fragment's (alpha, T_j), then with S_j = sum_{k>j} c_k a_k T_k + T_N bg:
+ *   dC/dc_j = a_j T_j,  dC/da_j = c_j T_j - S_j / (1 - a_j),
+ * then a = o e^P (no gradient where clamped at 0.99) down to (u, v, A, B, C, o).
+ * Discrete events (skips, termination, clamps) have zero derivative. */
+void or_render_bwd(int V, int64_t n, const double* cams, int tile, const double* proj,
+                   const uint32_t* vals, const uint32_t* ranges, const double* bg,
+                   const double* dimage, double* grad2d) {
+    memset(grad2d, 0, sizeof(double) * (size_t)V * (size_t)n * G2D_STRIDE);
+    for (int v = 0; v < V; ++v) {
+        const double* cam = cams + (int64_t)v * CAM_STRIDE;
+        int W = (int)cam[16], H = (int)cam[17], TX = tiles_along(W, tile);
+        int64_t toff = view_tile_offset(cams, v, tile), poff = view_pixel_offset(cams, v);
+        const double* dimg = dimage + 3 * poff;
+#pragma omp parallel
+        {
+            int cap = 1024;
+            uint32_t* lj = (uint32_t*)malloc(sizeof(uint32_t) * cap);
+            double* la = (double*)malloc(sizeof(double) * cap);
+            double* lT = (double*)malloc(sizeof(double) * cap);
+            double* lG = (double*)malloc(sizeof(double) * cap);
+            int* lcl = (int*)malloc(sizeof(int) * cap);
+#pragma omp for schedule(dynamic, 4)
+            for (int y = 0; y < H; ++y)
+                for (int x = 0; x < W; ++x) {
+                    int64_t t = toff + (int64_t)(y / tile) * TX + x / tile;
+                    uint32_t s = ranges[2 * t], e = ranges[2 * t + 1];
+                    double px = x + 0.5, py = y + 0.5, T = 1.0;
+                    int m = 0;
+                    for (uint32_t j = s; j < e; ++j) {
+                        const double* o = proj + ((int64_t)v * n + vals[j]) * PROJ_STRIDE;
+                        double dx = o[0] - px, dy = o[1] - py;
+                        double P = -0.5 * (o[4] * dx * dx + o[6] * dy * dy) - o[5] * dx * dy;
+                        if (P > 0.0) continue;
+                        double Gv = exp(P);
+                        double raw = o[3] * Gv;
+                        double al = fmin(ALPHA_MAX, raw);
+                        if (al < ALPHA_MIN) continue;
+                        double Tn = T * (1.0 - al);
+                        if (Tn < T_MIN) break;
+                        if (m == cap) {
+                            cap *= 2;
+                            lj = (uint32_t*)realloc(lj, sizeof(uint32_t) * cap);
+                            la = (double*)realloc(la, sizeof(double) * cap);
+                            lT = (double*)realloc(lT, sizeof(double) * cap);
+                            lG = (double*)realloc(lG, sizeof(double) * cap);
+                            lcl = (int*)realloc(lcl, sizeof(int) * cap);
+                        }
+                        lj[m] = j; la[m] = al; lT[m] = T; lG[m] = Gv; lcl[m] = raw > ALPHA_MAX;
+                        ++m;
+                        T = Tn;
+                    }
+                    int64_t pix = (int64_t)y * W + x;
+                    double dC[3];
+                    for (int ch = 0; ch < 3; ++ch) dC[ch] = dimg[(int64_t)ch * W * H + pix];
+                    double S[3] = {T * bg[0], T * bg[1], T * bg[2]};
+                    for (int i = m - 1; i >= 0; --i) {
+                        uint32_t g = vals[lj[i]];
+                        const double* o = proj + ((int64_t)v * n + g) * PROJ_STRIDE;
+                        double al = la[i], Tj = lT[i];
+                        double dal = 0.0;
+                        double* gg = grad2d + ((int64_t)v * n + g) * G2D_STRIDE;
+                        for (int ch = 0; ch < 3; ++ch) {
+                            double c = o[8 + ch];
+                            dal += dC[ch] * (c * Tj - S[ch] / (1.0 - al));
+#pragma omp atomic
+                            gg[6 + ch] += dC[ch] * al * Tj;
+                            S[ch] += c * al * Tj;
+                        }
+                        if (lcl[i]) continue;
+                        double dx = o[0] - px, dy = o[1] - py;
+                        double dP = dal * o[3] * lG[i];
+                        double dO = dal * lG[i];
+                        double du = dP * (-o[4] * dx - o[5] * dy);
+                        double dv = dP * (-o[6] * dy - o[5] * dx);
+#pragma omp atomic
+                        gg[0] += du;
+#pragma omp atomic
+                        gg[1] += dv;
+#pragma omp atomic
+                        gg[2] += dP * (-0.5 * dx * dx);
+#pragma omp atomic
+                        gg[3] += dP * (-dx * dy);
+#pragma omp atomic
+                        gg[4] += dP * (-0.5 * dy * dy);
+#pragma omp atomic
+                        gg[5] += dO;
+                    }
+                }
+            free(lj); free(la); free(lT); free(lG); free(lcl);
+        }
+    }
+}
+
+/* ------------------------------------------------------------------------
+ * Adjoint of or_project: 2D gradients of every view -> parameter gradients
+ * (mean, opacity logit, log-scale, quaternion, SH), summed over views.
+ * ---------------------------------------------------------------------- */
+void or_project_bwd(int64_t n, int sh_degree, const double* rows, int V, const double* cams,
+                    int tile, const double* grad2d, double* drows) {
+    int nb = (sh_degree + 1) * (sh_degree + 1);
+#pragma omp parallel for schedule(dynamic, 1024)
+    for (int64_t g = 0; g < n; ++g) {
+        const double* p = rows + g * ROW;
+        double* dp = drows + g * ROW;
+        memset(dp, 0, sizeof(double) * ROW);
+        double mu[3], s[3], q[4], qn, R[9], Sig[9], opac;
+        gauss_common(p, mu, s, q, &qn, R, Sig, &opac);
+        double dmu[3] = {0, 0, 0}, dSig[9] = {0}, dlogit = 0.0;
+        for (int v = 0; v < V; ++v) {
+            const double* cam = cams + (int64_t)v * CAM_STRIDE;
+            const double* W = cam;
+            double fx = cam[12], fy = cam[13];
+            view_geom G;
+            if (!view_geometry(mu, Sig, cam, &G)) continue;
+            /* the same culling as the forward pass */
+            double mid = 0.5 * (G.a + G.c);
+            double r = ceil(3.0 * sqrt(mid + sqrt(fmax(0.1, mid * mid - G.det))));
+            double u = fx * G.t[0] / G.t[2] + cam[14], vv = fy * G.t[1] / G.t[2] + cam[15];
+            int32_t rect[4];
+            or_rect(u, vv, r, (int)cam[16], (int)cam[17], tile, rect);
+            if ((rect[2] - rect[0]) * (rect[3] - rect[1]) == 0) continue;
+            const double* gr = grad2d + ((int64_t)v * n + g) * G2D_STRIDE;
+            double gu = gr[0], gv = gr[1], gA = gr[2], gB = gr[3], gC = gr[4], go = gr[5];
+            /* opacity = sigmoid(logit) */
+            dlogit += go * opac * (1.0 - opac);
+            /* colour: rgb_c = sum_k sh[k][c] Y_k(dir) + 0.5, clamped at 0 */
+            double ddir[3] = {0, 0, 0}, dY[48];
+            or_sh_basis_grad(G.dir, dY);
+            for (int ch = 0; ch < 3; ++ch) {
+                double raw = 0.5;
+                for (int k = 0; k < nb; ++k) raw += p[12 + 3 * k + ch] * G.Y[k];
+                if (raw < 0.0) continue;
+                double gc = gr[6 + ch];
+                for (int k = 0; k < nb; ++k) {
+                    dp[12 + 3 * k + ch] += gc * G.Y[k];
+                    for (int i = 0; i < 3; ++i) ddir[i] += gc * p[12 + 3 * k + ch] * dY[k * 3 + i];
+                }
+            }
+            double dd = G.dir[0] * ddir[0] + G.dir[1] * ddir[1] + G.dir[2] * ddir[2];
+            for (int i = 0; i < 3; ++i) dmu[i] += (ddir[i] - G.dir[i] * dd) / G.len;
+            /* conic (A, B, C) = (c, -b, a) / det */
+            double a = G.a, b = G.b, c = G.c, det = G.det, d2 = det * det;
+            double da = gA * (-c * c / d2) + gB * (b * c / d2) + gC * (1.0 / det - a * c / d2);
+            double db = gA * (2.0 * b * c / d2) + gB * (-1.0 / det - 2.0 * b * b / d2) + gC * (2.0 * a * b / d2);
+            double dc = gA * (1.0 / det - a * c / d2) + gB * (a * b / d2) + gC * (-a * a / d2);
+            /* a = M0 Sig M0^T + 0.3, b = M0 Sig M1^T, c = M1 Sig M1^T + 0.3 */
+            double SM0[3], SM1[3], dM[6];
+            for (int i = 0; i < 3; ++i) {
+                SM0[i] = Sig[i * 3] * G.M[0] + Sig[i * 3 + 1] * G.M[1] + Sig[i * 3 + 2] * G.M[2];
+                SM1[i] = Sig[i * 3] * G.M[3] + Sig[i * 3 + 1] * G.M[4] + Sig[i * 3 + 2] * G.M[5];
+            }
+            for (int i = 0; i < 3; ++i) {
+                dM[i] = 2.0 * da * SM0[i] + db * SM1[i];
+                dM[3 + i] = 2.0 * dc * SM1[i] + db * SM0[i];
+            }
+            for (int i = 0; i < 3; ++i)
+                for (int j = 0; j < 3; ++j)
+                    dSig[i * 3 + j] += da * G.M[i] * G.M[j] + db * G.M[i] * G.M[3 + j] + dc * G.M[3 + i] * G.M[3 + j];
+            /* M = J W */
+            double dJ[6];
+            for (int k = 0; k < 2; ++k)
+                for (int l = 0; l < 3; ++l) {
+                    double acc = 0.0;
+                    for (int i = 0; i < 3; ++i) acc += dM[k * 3 + i] * W[l * 3 + i];
+                    dJ[k * 3 + l] = acc;
+                }
+            double tx = G.t[0], ty = G.t[1], tz = G.t[2];
+            double dt[3] = {0, 0, 0};
+            dt[2] += dJ[0] * (-fx / (tz * tz)) + dJ[4] * (-fy / (tz * tz));
+            dt[2] += dJ[2] * (2.0 * fx * G.xt / (tz * tz * tz)) + dJ[5] * (2.0 * fy * G.yt / (tz * tz * tz));
+            double dxt = dJ[2] * (-fx / (tz * tz)), dyt = dJ[5] * (-fy / (tz * tz));
+            if (G.clx == 0) dt[0] += dxt; else dt[2] += dxt * (G.clx * G.limx);
+            if (G.cly == 0) dt[1] += dyt; else dt[2] += dyt * (G.cly * G.limy);
+            /* u = fx tx / tz + cx, v = fy ty / tz + cy */
+            dt[0] += gu * fx / tz;
+            dt[1] += gv * fy / tz;
+            dt[2] += -gu * fx * tx / (tz * tz) - gv * fy * ty / (tz * tz);
+            /* t = W mu + t_cam */
+            for (int i = 0; i < 3; ++i) dmu[i] += W[i] * dt[0] + W[3 + i] * dt[1] + W[6 + i] * dt[2];
+        }
+        /* Sigma = R diag(s^2) R^T */
+        double dR[9], ds[3];
+        for (int aa = 0; aa < 3; ++aa)
+            for (int bb = 0; bb < 3; ++bb) {
+                double acc = 0.0;
+                for (int j = 0; j < 3; ++j) acc += dSig[aa * 3 + j] * s[bb] * s[bb] * R[j * 3 + bb];
+                for (int i = 0; i < 3; ++i) acc += dSig[i * 3 + aa] * R[i * 3 + bb] * s[bb] * s[bb];
+                dR[aa * 3 + bb] = acc;
+            }
+        for (int k = 0; k < 3; ++k) {
+            double acc = 0.0;
+            for (int i = 0; i < 3; ++i)
+                for (int j = 0; j < 3; ++j) acc += dSig[i * 3 + j] * R[i * 3 + k] * R[j * 3 + k];
+            ds[k] = acc * 2.0 * s[k];
+        }
+        /* R(q) partials */
+        double w = q[0], x = q[1], y = q[2], z = q[3];
+        double dq[4];
+        dq[0] = dR[1] * (-2 * z) + dR[2] * (2 * y) + dR[3] * (2 * z) + dR[5] * (-2 * x) + dR[6] * (-2 * y) + dR[7] * (2 * x);
+        dq[1] = dR[1] * (2 * y) + dR[2] * (2 * z) + dR[3] * (2 * y) + dR[4] * (-4 * x) + dR[5] * (-2 * w) + dR[6] * (2 * z) + dR[7] * (2 * w) + dR[8] * (-4 * x);
+        dq[2] = dR[0] * (-4 * y) + dR[1] * (2 * x) + dR[2] * (2 * w) + dR[3] * (2 * x) + dR[5] * (2 * z) + dR[6] * (-2 * w) + dR[7] * (2 * z) + dR[8] * (-4 * y);
+        dq[3] = dR[0] * (-4 * z) + dR[1] * (-2 * w) + dR[2] * (2 * x) + dR[3] * (2 * w) + dR[4] * (-4 * z) + dR[5] * (2 * y) + dR[6] * (2 * x) + dR[7] * (2 * y);
+        double qd = q[0] * dq[0] + q[1] * dq[1] + q[2] * dq[2] + q[3] * dq[3];
+        for (int i = 0; i < 3; ++i) dp[i] = dmu[i];
+        dp[3] = dlogit;
+        for (int i = 0; i < 3; ++i) dp[4 + i] = ds[i] * s[i];
+        for (int i = 0; i < 4; ++i) dp[8 + i] = (dq[i] - q[i] * qd) / qn;
+    }
+}
+
+/* ------------------------------------------------------------------------
+ * Loss (Sec. 3.1: "compares the result to the captured ground-truth images"
+ * with the configured loss).  L = w_l1 mean|x - y| + w_ssim (1 - mean SSIM).
+ * SSIM: 11x11 Gaussian window (sigma 1.5, normalised), C1 = 0.01^2,
+ * C2 = 0.03^2, "same"-size window sums with zero padding (READING), mean over
+ * all pixels, channels and views.  Writes dL/dx.
+ * ---------------------------------------------------------------------- */
+static void ssim_window(double* g) {
+    double s = 0.0;
+    for (int i = 0; i < 11; ++i) { g[i] = exp(-(double)((i - 5) * (i - 5)) / (2.0 * 1.5 * 1.5)); s += g[i]; }
+    for (int i = 0; i < 11; ++i) g[i] /= s;
+}
+
+static const double SSIM_C1 = 0.0001, SSIM_C2 = 0.0009;
+
+/* SSIM map of one plane (and, if dmap != NULL, the three per-pixel partials
+ * dS/dmu_x, dS/dE[x^2], dS/dE[xy] used by the gradient). */
+void or_ssim_map(int H, int W, const double* x, const double* y, double* smap, double* dmap) {
+    double g[11];
+    ssim_window(g);
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int i = 0; i < H; ++i)
+        for (int j = 0; j < W; ++j) {
+            double mx = 0, my = 0, exx = 0, eyy = 0, exy = 0;
+            for (int a = -5; a <= 5; ++a)
+                for (int b = -5; b <= 5; ++b) {
+                    int ii = i + a, jj = j + b;
+                    if (ii < 0 || ii >= H || jj < 0 || jj >= W) continue;
+                    double w = g[a + 5] * g[b + 5];
+                    double xv = x[(int64_t)ii * W + jj], yv = y[(int64_t)ii * W + jj];
+                    mx += w * xv; my += w * yv; exx += w * xv * xv; eyy += w * yv * yv; exy += w * xv * yv;
+                }
+            double sxx = exx - mx * mx, syy = eyy - my * my, sxy = exy - mx * my;
+            double n1 = 2 * mx * my + SSIM_C1, n2 = 2 * sxy + SSIM_C2;
+            double d1 = mx * mx + my * my + SSIM_C1, d2 = sxx + syy + SSIM_C2;
+            double S = n1 * n2 / (d1 * d2);
+            int64_t p = (int64_t)i * W + j;
+            smap[p] = S;
+            if (dmap) {
+                dmap[3 * p + 0] = S * (2 * my / n1 - 2 * my / n2 - 2 * mx / d1 + 2 * mx / d2);
+                dmap[3 * p + 1] = -S / d2;
+                dmap[3 * p + 2] = 2 * S / n2;
+            }
+        }
+}
+
+double or_loss(int V, int H, int W, const double* img, const double* tgt, double w_l1,
+               double w_ssim, double* dimg) {
+    double g[11];
+    ssim_window(g);
+    int64_t P = (int64_t)H * W, M = (int64_t)V * 3 * P;
+    double l1 = 0.0, ssum = 0.0;
+    double* smap = (double*)malloc(sizeof(double) * P);
+    double* dmap = (double*)malloc(sizeof(double) * P * 3);
+    for (int64_t pl = 0; pl < (int64_t)V * 3; ++pl) {
+        const double* x = img + pl * P;
+        const double* y = tgt + pl * P;
+        double* dx = dimg + pl * P;
+        or_ssim_map(H, W, x, y, smap, dmap);
+        for (int64_t p = 0; p < P; ++p) {
+            double d = x[p] - y[p];
+            l1 += fabs(d);
+            ssum += smap[p];
+            dx[p] = w_l1 * (d > 0 ? 1.0 : (d < 0 ? -1.0 : 0.0)) / (double)M;
+        }
+        /* dL/dx_q -= w_ssim/M * sum_p dS_p/dx_q, with
+         * dS_p/dx_q = w(p-q) (dS/dmu_x + 2 x_q dS/dE[x^2] + y_q dS/dE[xy]) */
+#pragma omp parallel for schedule(dynamic, 4)
+        for (int i = 0; i < H; ++i)
+            for (int j = 0; j < W; ++j) {
+                double acc = 0.0;
+                int64_t q = (int64_t)i * W + j;
+                for (int a = -5; a <= 5; ++a)
+                    for (int b = -5; b <= 5; ++b) {
+                        int ii = i + a, jj = j + b;
+                        if (ii < 0 || ii >= H || jj < 0 || jj >= W) continue;
+                        int64_t pp = (int64_t)ii * W + jj;
+                        double w = g[a + 5] * g[b + 5];
+                        acc += w * (dmap[3 * pp] + 2.0 * x[q] * dmap[3 * pp + 1] + y[q] * dmap[3 * pp + 2]);
+                    }
+                dx[q] -= w_ssim * acc / (double)M;
+            }
+    }
+    free(smap);
+    free(dmap);
+    return w_l1 * l1 / (double)M + w_ssim * (1.0 - ssum / (double)M);
+}
+
+/* ------------------------------------------------------------------------
+ * Adam (Sec. 3.1: "updates the trainable Gaussian parameters using the
+ * configured loss and learning rates"; Sec. 3.3: optimizer state is extended
+ * with the model).  READING: the torch defaults beta1 0.9, beta2 0.999,
+ * eps 1e-8, bias-corrected, dense.  lr is given per element.
+ * ---------------------------------------------------------------------- */
+void or_adam(int64_t count, double* theta, const double* grad, double* m, double* v,
+             const double* lr, double b1, double b2, double eps, int step) {
+    double bc1 = 1.0 - pow(b1, step), bc2 = 1.0 - pow(b2, step);
+    for (int64_t i = 0; i < count; ++i) {
+        m[i] = b1 * m[i] + (1.0 - b1) * grad[i];
+        v[i] = b2 * v[i] + (1.0 - b2) * grad[i] * grad[i];
+        double mh = m[i] / bc1, vh = v[i] / bc2;
+        theta[i] -= lr[i] * mh / (sqrt(vh) + eps);
+    }
+}
+
+/* ------------------------------------------------------------------------
+ * Changed-set extraction for the incremental stream (Sec. 3.5: tensor-delta
+ * packets between snapshots; residuals relative to the previously transmitted
+ * state; fresh baselines after a snapshot).
+ * READING: Gaussian i is sent when max over its 59 stored attributes of
+ * |theta - baseline| > thr (decided in float32, as the GPU decides it); the
+ * baseline is the last transmitted float32 value; indices ascend; record =
+ * u32 index, float32 mean xyz, then 56 float16 (round to nearest even):
+ * log-scale xyz, quaternion wxyz, opacity logit, 48 SH.  Sent baselines are
+ * replaced by theta.
+ * ---------------------------------------------------------------------- */
+uint16_t or_f32_to_f16(float f) {
+    double a = fabs((double)f);
+    uint16_t sign = signbit(f) ? 0x8000 : 0;
+    if (isnan(f)) return sign | 0x7E00;
+    if (a >= 65520.0) return sign | 0x7C00;          /* rounds to infinity */
+    if (a < ldexp(1.0, -14)) {                       /* subnormal range */
+        double m = rint(a / ldexp(1.0, -24));        /* nearest, ties to even */
+        return sign | (uint16_t)m;                   /* m == 1024 encodes 2^-14 */
+    }
+    int e;
+    frexp(a, &e);                                    /* a = f * 2^e, f in [0.5, 1) */
+    e -= 1;                                          /* a in [2^e, 2^(e+1)) */
+    double m = rint(a / ldexp(1.0, e - 10));         /* in [1024, 2048] */
+    if (m == 2048.0) { m = 1024.0; e += 1; }
+    if (e + 15 >= 31) return sign | 0x7C00;
+    return sign | (uint16_t)(((e + 15) << 10) | ((int)m - 1024));
+}
+
+int64_t or_delta(int64_t n, const float* theta, float* base, float thr, uint32_t* idx, uint8_t* rec) {
+    int64_t cnt = 0;
+    for (int64_t g = 0; g < n; ++g) {
+        const float* t = theta + g * ROW;
+        float* b = base + g * ROW;
+        int changed = 0;
+        for (int k = 0; k < ROW; ++k) {
+            float d = fabsf(t[k] - b[k]);
+            if (d > thr) changed = 1;
+        }
+        if (!changed) continue;
+        idx[cnt] = (uint32_t)g;
+        uint8_t* r = rec + cnt * 128;
+        uint32_t gi = (uint32_t)g;
+        memcpy(r, &gi, 4);
+        memcpy(r + 4, t, 12);
+        /* order: log-scale (4..6), quaternion (8..11), opacity logit (3), SH (12..59) */
+        int order[56], o = 0;
+        for (int k = 4; k < 7; ++k) order[o++] = k;
+        for (int k = 8; k < 12; ++k) order[o++] = k;
+        order[o++] = 3;
+        for (int k = 12; k < 60; ++k) order[o++] = k;
+        for (int k = 0; k < 56; ++k) {
+            uint16_t h = or_f32_to_f16(t[order[k]]);
+            memcpy(r + 16 + 2 * k, &h, 2);
+        }
+        memcpy(b, t, sizeof(float) * ROW);
+        ++cnt;
+    }
+    return cnt;
+}

@@ -1,0 +1,510 @@
+"""Pins of the FP64 oracle against facts fixed outside it (CPU only).
+
+Each test checks the oracle against something other than itself: a library
+routine of independent provenance (scipy spherical harmonics and rotations,
+torch.optim.Adam, numpy float16), a closed form, a brute-force evaluation, an
+invariant, or central finite differences.  A plausible slip in the oracle (a
+dropped term, a wrong sign or index, a transposed operand) fails one of them.
+"""
+import math
+
+import numpy as np
+import pytest
+import scipy.special as sp
+from scipy.spatial.transform import Rotation
+
+import gs_inputs as gi
+import oracle as O
+
+RNG = np.random.default_rng(1234)
+
+
+def _real_sh_scipy(d):
+    th = math.acos(max(-1.0, min(1.0, d[2])))
+    ph = math.atan2(d[1], d[0])
+    out = []
+    for l in range(4):
+        for m in range(-l, l + 1):
+            if m == 0:
+                out.append(sp.sph_harm_y(l, 0, th, ph).real)
+            elif m > 0:
+                out.append(math.sqrt(2) * sp.sph_harm_y(l, m, th, ph).real)
+            else:
+                out.append(math.sqrt(2) * sp.sph_harm_y(l, -m, th, ph).imag)
+    return np.array(out)
+
+
+# --------------------------------------------------------------- SH basis
+def test_sh_basis_matches_scipy():
+    for _ in range(50):
+        d = RNG.normal(size=3); d /= np.linalg.norm(d)
+        np.testing.assert_allclose(O.sh_basis(d), _real_sh_scipy(d), atol=1e-13, rtol=0)
+
+
+def test_sh_basis_orthonormal_by_quadrature():
+    # Gauss-Legendre in cos(theta) x uniform phi integrates degree <= 6 exactly
+    x, w = np.polynomial.legendre.leggauss(12)
+    nphi = 16
+    G = np.zeros((16, 16))
+    for xi, wi in zip(x, w):
+        s = math.sqrt(1 - xi * xi)
+        for k in range(nphi):
+            ph = 2 * math.pi * k / nphi
+            Y = O.sh_basis(np.array([s * math.cos(ph), s * math.sin(ph), xi]))
+            G += wi * (2 * math.pi / nphi) * np.outer(Y, Y)
+    np.testing.assert_allclose(G, np.eye(16), atol=1e-12)
+
+
+def test_sh_basis_gradient_fd():
+    for _ in range(10):
+        d = RNG.normal(size=3)
+        g = O.sh_basis_grad(d)
+        h = 1e-6
+        for i in range(3):
+            e = np.zeros(3); e[i] = h
+            fd = (O.sh_basis(d + e) - O.sh_basis(d - e)) / (2 * h)
+            np.testing.assert_allclose(g[:, i], fd, atol=1e-8)
+
+
+# --------------------------------------------------------------- projection
+def _one_gaussian(mean, log_s, quat, logit, sh=None, sh_degree=0):
+    planes = np.zeros((15, 1, 4), dtype=np.float64)
+    planes[0, 0, :3] = mean; planes[0, 0, 3] = logit
+    planes[1, 0, :3] = log_s
+    planes[2, 0, :] = quat
+    if sh is not None:
+        flat = np.zeros(48); flat[:sh.size] = sh.ravel()
+        planes[3:15, 0, :] = flat.reshape(12, 4)
+    return planes
+
+
+def _project_fn(cam, mean):
+    R = np.asarray(cam["R"])[0]; t = np.asarray(cam["t"])[0]
+    p = R @ mean + t
+    return np.array([cam["fx"][0] * p[0] / p[2] + cam["cx"][0], cam["fy"][0] * p[1] / p[2] + cam["cy"][0]])
+
+
+def test_projection_conic_from_fd_jacobian_and_scipy_rotation():
+    cams = gi.cameras_from_eyes([(0.7, -0.4, 3.1)], [96], [80])
+    for _ in range(20):
+        mean = RNG.uniform(-0.4, 0.4, 3)
+        log_s = RNG.normal(-2.5, 0.4, 3)
+        q = RNG.normal(size=4)
+        pl = _one_gaussian(mean, log_s, q, 0.3)
+        pr = O.project(pl, 0, cams)[0, 0]
+        assert pr[14] > pr[12]  # visible
+        # Jacobian of the pinhole map by central differences (no J formula)
+        M = np.zeros((2, 3))
+        for i in range(3):
+            e = np.zeros(3); e[i] = 1e-6
+            M[:, i] = (_project_fn(cams, mean + e) - _project_fn(cams, mean - e)) / 2e-6
+        Rq = Rotation.from_quat([q[1], q[2], q[3], q[0]]).as_matrix()  # scipy is (x, y, z, w)
+        Sig = Rq @ np.diag(np.exp(2 * log_s)) @ Rq.T
+        S2 = M @ Sig @ M.T + 0.3 * np.eye(2)
+        inv = np.linalg.inv(S2)
+        np.testing.assert_allclose([pr[4], pr[5], pr[6]], [inv[0, 0], inv[0, 1], inv[1, 1]], rtol=2e-6)
+        np.testing.assert_allclose(pr[:2], _project_fn(cams, mean), rtol=1e-12)
+        tz = (np.asarray(cams["R"])[0] @ mean + np.asarray(cams["t"])[0])[2]
+        assert pr[2] == pytest.approx(tz, rel=1e-14)
+        lam = np.linalg.eigvalsh(S2)
+        mid = 0.5 * (S2[0, 0] + S2[1, 1])
+        if mid * mid - np.linalg.det(S2) > 0.1:
+            assert pr[7] == math.ceil(3 * math.sqrt(lam.max()))
+        assert pr[3] == pytest.approx(1 / (1 + math.exp(-0.3)), rel=1e-14)
+
+
+def test_projection_sh_colour_matches_scipy_basis():
+    cams = gi.ring_cameras(3, 64, 64)
+    sh = RNG.normal(0, 0.3, size=(16, 3))
+    mean = np.array([0.1, -0.2, 0.15])
+    pl = _one_gaussian(mean, [-2.0] * 3, [1, 0, 0, 0], 0.0, sh)
+    pr = O.project(pl, 3, cams)
+    for v in range(3):
+        R = cams["R"][v]; t = cams["t"][v]
+        centre = -R.T @ t
+        d = mean - centre; d /= np.linalg.norm(d)
+        rgb = _real_sh_scipy(d) @ sh + 0.5
+        expect = np.maximum(rgb, 0.0)
+        np.testing.assert_allclose(pr[v, 0, 8:11], expect, atol=1e-12)
+        mask = sum(1 << c for c in range(3) if rgb[c] < 0)
+        assert pr[v, 0, 11] == mask
+
+
+def test_sh_degree0_colour_is_view_independent():
+    cams = gi.ring_cameras(6, 64, 64)
+    dc = np.array([[0.3, -0.7, 1.1]])
+    pl = _one_gaussian([0.05, 0.0, -0.1], [-2.0] * 3, [1, 0, 0, 0], 0.0, dc)
+    pr = O.project(pl, 0, cams)
+    y00 = 0.5 / math.sqrt(math.pi)
+    for v in range(6):
+        np.testing.assert_allclose(pr[v, 0, 8:11], dc[0] * y00 + 0.5, atol=1e-14)
+
+
+def test_projection_culls_behind_near_plane():
+    cams = gi.cameras_from_eyes([(0, 0, 3.0)], [32], [32])
+    # camera at z = 3 looking at -z: a point at z = 2.85 is 0.15 in front (< near 0.2)
+    pl = _one_gaussian([0, 0, 2.85], [-2.0] * 3, [1, 0, 0, 0], 0.0)
+    assert np.all(O.project(pl, 0, cams) == 0)
+    pl = _one_gaussian([0, 0, 3.5], [-2.0] * 3, [1, 0, 0, 0], 0.0)  # behind the camera
+    assert np.all(O.project(pl, 0, cams) == 0)
+
+
+# --------------------------------------------------------------- compositing
+def _iso_sigma2(cams, s, z):
+    f = cams["fx"][0]
+    return (f * s / z) ** 2 + 0.3
+
+
+def test_single_gaussian_closed_form():
+    """An isotropic Gaussian on the optical axis at depth z renders as
+    rgb * min(0.99, o exp(-rho^2 / (2 sigma^2))) with sigma^2 = (f s / z)^2 + 0.3,
+    or 0 where that alpha is below 1/255."""
+    W = H = 32
+    cams = gi.cameras_from_eyes([(0, 0, 3.0)], [W], [H])
+    for log_s, logit in [(-3.0, 0.5), (-2.2, 2.0), (-3.5, -1.0), (-2.6, 5.0)]:
+        s = math.exp(log_s)
+        dc = np.array([[0.4, 0.1, -0.2]])
+        pl = _one_gaussian([0, 0, 0], [log_s] * 3, [1, 0, 0, 0], logit, dc)
+        f = O.forward(pl, 0, cams)
+        sig2 = _iso_sigma2(cams, s, 3.0)
+        o = 1 / (1 + math.exp(-logit))
+        rgb = dc[0] * (0.5 / math.sqrt(math.pi)) + 0.5
+        ys, xs = np.mgrid[0:H, 0:W]
+        rho2 = (xs + 0.5 - W / 2) ** 2 + (ys + 0.5 - H / 2) ** 2
+        a = np.minimum(0.99, o * np.exp(-rho2 / (2 * sig2)))
+        a[a < 1 / 255] = 0.0
+        # the square support of half-side ceil(3 sqrt(lambda)) is wider than the image here
+        assert f["proj"][0, 0, 7] >= 3 * math.sqrt(sig2)
+        assert (f["proj"][0, 0, 12:16] == [0, 0, 2, 2]).all()
+        img = f["image"].reshape(3, H, W)
+        for c in range(3):
+            np.testing.assert_allclose(img[c], rgb[c] * a, atol=1e-14)
+        np.testing.assert_allclose(f["T_final"].reshape(H, W), 1 - a, atol=1e-14)
+
+
+def test_two_gaussians_closed_form_and_order():
+    W = H = 32
+    cams = gi.cameras_from_eyes([(0, 0, 3.0)], [W], [H])
+    y00 = 0.5 / math.sqrt(math.pi)
+    c1 = np.array([0.9, 0.2, 0.1]); c2 = np.array([0.1, 0.3, 0.8])
+    for z1, z2 in [(0.3, -0.3), (-0.3, 0.3)]:
+        pl = np.concatenate([
+            _one_gaussian([0, 0, z1], [-2.8] * 3, [1, 0, 0, 0], 0.4, ((c1 - 0.5) / y00)[None]),
+            _one_gaussian([0, 0, z2], [-2.6] * 3, [1, 0, 0, 0], 1.0, ((c2 - 0.5) / y00)[None])], axis=1)
+        f = O.forward(pl, 0, cams)
+        ys, xs = np.mgrid[0:H, 0:W]
+        rho2 = (xs + 0.5 - W / 2) ** 2 + (ys + 0.5 - H / 2) ** 2
+        alphas = []
+        for z, ls, lg in [(z1, -2.8, 0.4), (z2, -2.6, 1.0)]:
+            sig2 = _iso_sigma2(cams, math.exp(ls), 3.0 - z)
+            a = np.minimum(0.99, np.exp(-rho2 / (2 * sig2)) / (1 + math.exp(-lg)))
+            a[a < 1 / 255] = 0
+            alphas.append(a)
+        a1, a2 = alphas
+        front_first = z1 > z2  # the camera sits at +z: larger z is nearer
+        if front_first:
+            expect = c1[:, None, None] * a1 + c2[:, None, None] * a2 * (1 - a1)
+        else:
+            expect = c2[:, None, None] * a2 + c1[:, None, None] * a1 * (1 - a2)
+        np.testing.assert_allclose(f["image"].reshape(3, H, W), expect, atol=1e-14)
+
+
+def _brute_force_render(cams, proj, tile=16, bg=(0, 0, 0)):
+    """Per pixel: every Gaussian whose tile rectangle holds the pixel's tile,
+    fully sorted by (float32 depth, index), composited front to back."""
+    V, n = proj.shape[:2]
+    outs = []
+    for v in range(V):
+        W, H = int(cams["width"][v]), int(cams["height"][v])
+        img = np.zeros((3, H, W)); Tm = np.zeros((H, W))
+        for y in range(H):
+            for x in range(W):
+                tx, ty = x // tile, y // tile
+                cand = [g for g in range(n)
+                        if proj[v, g, 12] <= tx < proj[v, g, 14] and proj[v, g, 13] <= ty < proj[v, g, 15]]
+                cand.sort(key=lambda g: (np.float32(proj[v, g, 2]), g))
+                T = 1.0; C = np.zeros(3)
+                for g in cand:
+                    o = proj[v, g]
+                    dx, dy = o[0] - (x + 0.5), o[1] - (y + 0.5)
+                    P = -0.5 * (o[4] * dx * dx + o[6] * dy * dy) - o[5] * dx * dy
+                    if P > 0:
+                        continue
+                    a = min(0.99, o[3] * math.exp(P))
+                    if a < 1 / 255:
+                        continue
+                    Tn = T * (1 - a)
+                    if Tn < 1e-4:
+                        break
+                    C += o[8:11] * a * T
+                    T = Tn
+                img[:, y, x] = C + T * np.asarray(bg)
+                Tm[y, x] = T
+        outs.append((img, Tm))
+    return outs
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_tiled_render_equals_brute_force_full_sort(seed):
+    n = 48
+    sc = gi.make_scene(n, 1, seed)
+    sc[1, :, :3] += 1.5  # larger Gaussians so that lists overlap heavily
+    cams = gi.ring_cameras(2, 32, 24)
+    f = O.forward(sc, 1, cams, bg=(0.1, 0.2, 0.3))
+    bf = _brute_force_render(cams, f["proj"], bg=(0.1, 0.2, 0.3))
+    off = 0
+    for v, (img, Tm) in enumerate(bf):
+        P = img.shape[1] * img.shape[2]
+        np.testing.assert_allclose(f["image"][3 * off:3 * (off + P)].reshape(img.shape), img, atol=1e-13)
+        np.testing.assert_allclose(f["T_final"][off:off + P].reshape(Tm.shape), Tm, atol=1e-13)
+        off += P
+
+
+def test_bin_sort_matches_lexsort():
+    V, n = 3, 400
+    cams = gi.ring_cameras(V, 70, 50)
+    rects = np.zeros((V, n, 4), dtype=np.int32)
+    TX, TY = 5, 4
+    x0 = RNG.integers(0, TX, (V, n)); y0 = RNG.integers(0, TY, (V, n))
+    rects[..., 0] = x0; rects[..., 1] = y0
+    rects[..., 2] = np.minimum(TX, x0 + RNG.integers(0, 3, (V, n)))
+    rects[..., 3] = np.minimum(TY, y0 + RNG.integers(0, 3, (V, n)))
+    depth = RNG.uniform(0.5, 5, (V, n)).astype(np.float32)
+    depth[0, :50] = depth[0, 50:100]  # equal depths: ties broken by index
+    keys, vals, ranges = O.bin_sort(cams, rects, depth)
+    tl, dl, gl = [], [], []
+    for v in range(V):
+        for g in range(n):
+            r = rects[v, g]
+            for ty in range(r[1], r[3]):
+                for tx in range(r[0], r[2]):
+                    tl.append(v * TX * TY + ty * TX + tx)
+                    dl.append(depth[v, g].view(np.uint32)); gl.append(g)
+    tl, dl, gl = map(np.array, (tl, dl, gl))
+    order = np.lexsort((gl, dl, tl))
+    np.testing.assert_array_equal(vals, gl[order])
+    np.testing.assert_array_equal(keys >> np.uint64(32), tl[order])
+    for t in range(V * TX * TY):
+        sel = np.nonzero(tl[order] == t)[0]
+        if sel.size:
+            assert tuple(ranges[t]) == (sel[0], sel[-1] + 1)
+        else:
+            assert ranges[t, 0] == ranges[t, 1]
+
+
+def test_render_invariants():
+    sc = gi.make_scene(3000, 2, 5)
+    cams = gi.ring_cameras(2, 48, 40)
+    f = O.forward(sc, 2, cams)
+    T = f["T_final"]
+    assert T.min() >= 1e-4 and T.max() <= 1.0
+    rgbmax = f["proj"][..., 8:11].max()
+    assert f["image"].min() >= 0 and f["image"].max() <= rgbmax + 1e-12
+    # transmittance is non-increasing along each pixel's list: re-walk one tile
+    vals, ranges, proj = f["vals"], f["ranges"], f["proj"]
+    s, e = ranges[1]
+    for x in range(16, 20):
+        Tp = 1.0
+        for j in range(s, e):
+            o = proj[0, vals[j]]
+            dx, dy = o[0] - (x + 0.5), o[1] - 0.5
+            P = -0.5 * (o[4] * dx * dx + o[6] * dy * dy) - o[5] * dx * dy
+            a = min(0.99, o[3] * math.exp(P)) if P <= 0 else 0.0
+            if a >= 1 / 255:
+                if Tp * (1 - a) < 1e-4:
+                    break
+                assert Tp * (1 - a) <= Tp
+                Tp *= 1 - a
+        assert Tp == pytest.approx(T[x], rel=1e-12)
+
+
+# --------------------------------------------------------------- loss
+def test_ssim_identity_and_zero_gradient():
+    x = RNG.uniform(0, 1, size=(2, 3, 20, 24))
+    L, g = O.loss(x.ravel(), x.ravel(), 2, 20, 24)
+    assert L == pytest.approx(0.0, abs=1e-14)
+    assert np.abs(g).max() < 1e-15
+    s = O.ssim_map(x[0, 0], x[0, 0])
+    np.testing.assert_allclose(s, 1.0, atol=1e-14)
+
+
+def test_ssim_constant_images_closed_form():
+    H, W = 30, 30
+    for a, b in [(0.2, 0.7), (0.5, 0.5), (0.9, 0.05)]:
+        s = O.ssim_map(np.full((H, W), a), np.full((H, W), b))
+        c1 = 0.01 ** 2
+        # interior pixels see the whole window: sigma terms vanish
+        np.testing.assert_allclose(s[5:-5, 5:-5], (2 * a * b + c1) / (a * a + b * b + c1), rtol=1e-10)
+
+
+def test_ssim_map_against_scipy_filtering():
+    from scipy.ndimage import correlate
+    x = RNG.uniform(0, 1, (25, 31)); y = np.clip(x + RNG.normal(0, 0.1, x.shape), 0, 1)
+    g = np.exp(-((np.arange(11) - 5) ** 2) / (2 * 1.5 ** 2)); g /= g.sum()
+    w = np.outer(g, g)
+    f = lambda z: correlate(z, w, mode="constant", cval=0.0)
+    mx, my = f(x), f(y)
+    sxx, syy, sxy = f(x * x) - mx ** 2, f(y * y) - my ** 2, f(x * y) - mx * my
+    c1, c2 = 0.01 ** 2, 0.03 ** 2
+    ref = (2 * mx * my + c1) * (2 * sxy + c2) / ((mx ** 2 + my ** 2 + c1) * (sxx + syy + c2))
+    np.testing.assert_allclose(O.ssim_map(x, y), ref, atol=1e-13)
+
+
+def test_loss_gradient_fd():
+    V, H, W = 2, 14, 17
+    x = RNG.uniform(0, 1, V * 3 * H * W); y = RNG.uniform(0, 1, x.size)
+    L, g = O.loss(x, y, V, H, W, 0.8, 0.2)
+    l1 = np.abs(x - y).mean(); assert L > 0.8 * l1
+    for i in RNG.choice(x.size, 40, replace=False):
+        h = 1e-7
+        xp = x.copy(); xp[i] += h
+        xm = x.copy(); xm[i] -= h
+        fd = (O.loss(xp, y, V, H, W, 0.8, 0.2)[0] - O.loss(xm, y, V, H, W, 0.8, 0.2)[0]) / (2 * h)
+        assert fd == pytest.approx(g[i], rel=1e-5, abs=1e-11)
+
+
+# --------------------------------------------------------------- gradients
+def _discrete_state(planes, sh, cams):
+    f = O.forward(planes, sh, cams)
+    p = f["proj"]
+    return (p[..., 12:16].copy(), p[..., 11].copy(), f["n_contrib"].copy())
+
+
+def _same_state(a, b):
+    return all(np.array_equal(x, y) for x, y in zip(a, b))
+
+
+@pytest.mark.parametrize("sh_degree,seed", [(0, 0), (3, 1)])
+def test_full_gradient_matches_central_differences(sh_degree, seed):
+    """Analytic adjoint of render + loss vs central differences on 64 seeded
+    parameters; a parameter whose +-h step changes any discrete state
+    (tile rectangles, clamp flags, contributor counts) or shows a kink is
+    resampled."""
+    n = 60
+    sc = gi.make_scene(n, sh_degree, seed).astype(np.float64)
+    sc[1, :, :3] += 1.2
+    sc[0, :, :3] *= 0.6
+    cams = gi.ring_cameras(2, 40, 32)
+    tgt_sc = gi.make_scene(n, sh_degree, seed + 10).astype(np.float64)
+    tgt_sc[1, :, :3] += 1.2
+    tgt_sc[0, :, :3] *= 0.6
+    target = O.forward(tgt_sc, sh_degree, cams)["image"]
+    r = O.loss_and_grad(sc, sh_degree, cams, target)
+    g = r["dparams"]
+    base_state = _discrete_state(sc, sh_degree, cams)
+    nb = (sh_degree + 1) ** 2
+    valid = [(p, i, c) for p in range(15) for i in range(n) for c in range(4)
+             if not (p == 1 and c == 3) and not (p >= 3 and (4 * (p - 3) + c) >= 3 * nb)]
+    rng = np.random.default_rng(seed + 99)
+    checked, tries = 0, 0
+    rel_errs = []
+    while checked < 64 and tries < 400:
+        tries += 1
+        p, i, c = valid[rng.integers(len(valid))]
+        if np.all(r["proj"][:, i, 14] == 0):
+            continue  # never on screen: gradient is zero, nothing to check
+        th = sc[p, i, c]
+        h = 1e-6 * max(1.0, abs(th))
+        sp_ = sc.copy(); sp_[p, i, c] = th + h
+        sm_ = sc.copy(); sm_[p, i, c] = th - h
+        if not (_same_state(_discrete_state(sp_, sh_degree, cams), base_state)
+                and _same_state(_discrete_state(sm_, sh_degree, cams), base_state)):
+            continue
+        Lp = O.render_loss(sp_, sh_degree, cams, target)
+        Lm = O.render_loss(sm_, sh_degree, cams, target)
+        L0 = r["loss"]
+        fwd, bwd = (Lp - L0) / h, (L0 - Lm) / h
+        if abs(fwd - bwd) > 1e-3 * max(abs(fwd), abs(bwd), 1e-8):
+            continue  # a skip threshold was crossed inside the step
+        fd = (Lp - Lm) / (2 * h)
+        an = g[p, i, c]
+        # central differences carry a rounding error of about eps * |L| / h
+        fd_noise = 100 * np.finfo(float).eps * abs(L0) / h
+        rel_errs.append(max(abs(fd - an) - fd_noise, 0.0) / max(abs(fd), abs(an), 1e-12))
+        checked += 1
+    assert checked >= 48
+    assert max(rel_errs) <= 1e-5, sorted(rel_errs)[-5:]
+
+
+def test_render_bwd_matches_fd_in_screen_space():
+    """Adjoint of compositing alone, w.r.t. the 2D quantities (u, v, A, B, C,
+    opacity, rgb), against central differences through the oracle render."""
+    sc = gi.make_scene(40, 0, 3)
+    sc[1, :, :3] += 1.3
+    cams = gi.ring_cameras(1, 32, 32)
+    f = O.forward(sc, 0, cams)
+    proj = f["proj"].copy()
+    wimg = RNG.normal(size=f["image"].size)
+    L = lambda pr: float(wimg @ O.render(cams, pr, f["vals"], f["ranges"])[0])
+    g2 = O.render_bwd(cams, proj, f["vals"], f["ranges"], wimg)
+    fields = [0, 1, 4, 5, 6, 3, 8, 9, 10]
+    checked = 0
+    for g in RNG.permutation(40):
+        if proj[0, g, 14] == 0:
+            continue
+        for k, fld in enumerate(fields):
+            h = 1e-7 * max(1.0, abs(proj[0, g, fld]))
+            pp = proj.copy(); pp[0, g, fld] += h
+            pm = proj.copy(); pm[0, g, fld] -= h
+            if not np.array_equal(O.render(cams, pp, f["vals"], f["ranges"])[2], f["n_contrib"]) or \
+               not np.array_equal(O.render(cams, pm, f["vals"], f["ranges"])[2], f["n_contrib"]):
+                continue
+            fd = (L(pp) - L(pm)) / (2 * h)
+            assert fd == pytest.approx(g2[0, g, k], rel=2e-5, abs=1e-7), (g, fld)
+            checked += 1
+    assert checked > 100
+
+
+# --------------------------------------------------------------- Adam, FP16, delta
+def test_adam_equals_torch_adam_float64():
+    import torch
+    n = 257
+    theta0 = RNG.normal(size=n)
+    lr = 10 ** RNG.uniform(-4, -2, size=n)
+    th = theta0.copy(); m = np.zeros(n); v = np.zeros(n)
+    params = [torch.nn.Parameter(torch.tensor(theta0[i:i + 1], dtype=torch.float64)) for i in range(n)]
+    opt = torch.optim.Adam([{"params": [p], "lr": float(lr[i])} for i, p in enumerate(params)],
+                           betas=(0.9, 0.999), eps=1e-8)
+    for step in range(1, 6):
+        g = RNG.normal(size=n) * 10 ** RNG.uniform(-6, 0, size=n)
+        O.adam(th, g, m, v, lr, step)
+        for i, p in enumerate(params):
+            p.grad = torch.tensor(g[i:i + 1], dtype=torch.float64)
+        opt.step()
+        ref = np.array([p.item() for p in params])
+        np.testing.assert_allclose(th, ref, rtol=1e-12, atol=1e-15)
+
+
+def test_f16_matches_numpy():
+    vals = np.concatenate([
+        RNG.normal(0, 1, 2000), RNG.normal(0, 1e-5, 500), RNG.normal(0, 3e4, 500),
+        [0.0, -0.0, 65504.0, 65519.99, 65520.0, -70000.0, 2.0 ** -24, 2.0 ** -25, 3 * 2.0 ** -26,
+         2.0 ** -14, (1 + 2 ** -11) * 1.0, (1 + 3 * 2 ** -11), 6.1e-5, 1e-8]]).astype(np.float32)
+    np.testing.assert_array_equal(O.f32_to_f16_bits(vals), vals.astype(np.float16).view(np.uint16))
+
+
+def test_delta_against_numpy_definition():
+    n = 500
+    th = gi.make_scene(n, 3, 7)
+    base = th.copy()
+    rng = np.random.default_rng(3)
+    pick = rng.random(n) < 0.3
+    plane = rng.integers(0, 15, n); lane = rng.integers(0, 4, n)
+    lane[(plane == 1) & (lane == 3)] = 0
+    for i in np.nonzero(pick)[0]:
+        th[plane[i], i, lane[i]] += np.float32(rng.choice([2e-3, -5e-3, 9e-4]))
+    idx, rec, nb = O.delta(th, base, 1e-3)
+    rows_t = gi.planes_to_rows(th).astype(np.float32)
+    rows_b = gi.planes_to_rows(base).astype(np.float32)
+    expect = np.nonzero((np.abs(rows_t - rows_b) > np.float32(1e-3)).any(axis=1))[0]
+    np.testing.assert_array_equal(idx, expect)
+    order = [4, 5, 6, 8, 9, 10, 11, 3] + list(range(12, 60))
+    for k, g in enumerate(expect):
+        r = rec[k]
+        assert r[:4].view(np.uint32)[0] == g
+        np.testing.assert_array_equal(r[4:16].view(np.float32), rows_t[g, :3])
+        np.testing.assert_array_equal(r[16:128].view(np.float16), rows_t[g, order].astype(np.float16))
+    nbr = gi.planes_to_rows(nb)
+    np.testing.assert_array_equal(nbr[expect], rows_t[expect])
+    keep = np.setdiff1d(np.arange(n), expect)
+    np.testing.assert_array_equal(nbr[keep], rows_b[keep])
