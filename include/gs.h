@@ -1,0 +1,281 @@
+/*
+ * gs.h -- C ABI of the B300 (sm_103a) online 3D Gaussian Splatting step.
+ *
+ * The paper (Streaming Real-Time Rendered Scenes as 3D Gaussians) keeps a
+ * 3DGS scene model that an optimiser thread continuously refits to rendered
+ * reference views: it "renders the present Gaussian model from those
+ * viewpoints, compares the result to the captured ground-truth images, and
+ * updates the trainable Gaussian parameters" (Sec. 3.1), with "the same
+ * parameters as in prior 3DGS work" (Sec. 3.2.3), and streams the changed
+ * Gaussians as tensor-delta packets between snapshots (Sec. 3.5).  The calls
+ * below are the data-parallel steps of that loop.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Every call returns gs_status_t and, unless stated, only ENQUEUES work on
+ *    `stream` (a cudaStream_t passed as void*; NULL = legacy default stream).
+ *    Argument errors are detected on the host before anything is enqueued and
+ *    returned synchronously (GS_ERR_ARG).  Errors found by kernels (a key
+ *    buffer too small, a bounded wait that ran out) are recorded in the
+ *    context's device status word; read it with gs_get_status().
+ *  - All array pointers are DEVICE pointers unless marked "host".  The caller
+ *    owns every buffer it passes; the library only borrows them for the
+ *    duration of the enqueued work.  The context owns its scratch workspace.
+ *  - No call allocates device memory except gs_ctx_create / gs_ctx_reserve.
+ *  - A context is used by one host thread and one stream at a time.
+ *  - Float data are IEEE float32.  Integer keys/indices are uint32.
+ *
+ * Layouts
+ * -------
+ *  params  float [15][n][4]  "planes"; plane 0 = mean x,y,z + opacity logit,
+ *          plane 1 = log-scale x,y,z + 0, plane 2 = quaternion (w,x,y,z),
+ *          planes 3..14 = 48 SH coefficients, coefficient k (l=0..3,
+ *          m=-l..l) of channel c at flat index 3k+c (plane 3 + idx/4).
+ *  proj    float [V][n][16]  per (view, Gaussian): u, v, depth, opacity,
+ *          A, B, C (conic), radius, r, g, b, clamp mask (uint32 bits),
+ *          rect lo (uint32 x0 | y0<<16), rect hi (x1 | y1<<16),
+ *          tiles touched (uint32), 0.  All zero when culled.
+ *  images  float, views concatenated, each planar [3][H][W]; T_final and
+ *          n_contrib are [H][W] per view, concatenated the same way.
+ *  tiles   views in order; tile (tx, ty) of view v has global index
+ *          tile_offset(v) + ty * ceil(W/B) + tx with B = the context's tile
+ *          size (16 by default).  ranges uint32 [total_tiles][2] = [start, end).
+ *  grad2d  float [V][n][12] per (view, Gaussian): dL/du, dL/dv, dL/dA, dL/dB,
+ *          dL/dC, dL/dopacity, dL/dr, dL/dg, dL/db, 0, 0, 0.
+ */
+#ifndef GS_H_
+#define GS_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    GS_OK = 0,
+    GS_ERR_ARG = 1,       /* bad argument (null pointer, bad size or range)        */
+    GS_ERR_CAPACITY = 2,  /* a caller buffer or the workspace is too small         */
+    GS_ERR_CUDA = 3,      /* a CUDA runtime call failed                            */
+    GS_ERR_OOM = 4,       /* workspace allocation failed                           */
+    GS_ERR_TIMEOUT = 5    /* a bounded inter-block wait in a kernel ran out        */
+} gs_status_t;
+
+typedef struct gs_ctx gs_ctx;
+
+/* Pinhole camera, world -> camera: x_cam = R x_world + t; x right, y down,
+ * z forward; pixel (i, j) is sampled at (i + 0.5, j + 0.5).  80 bytes. */
+typedef struct gs_camera {
+    float R[9];          /* row-major */
+    float t[3];
+    float fx, fy, cx, cy;
+    int32_t width, height;
+    float near_plane;    /* Gaussians with camera z <= near_plane are culled */
+    float _pad;
+} gs_camera;
+
+typedef struct gs_scene {
+    int64_t n;           /* number of Gaussians, >= 0 */
+    int32_t sh_degree;   /* 0..3 */
+    int32_t _pad;
+    const float* params; /* device, [15][n][4] */
+} gs_scene;
+
+/* ---------------------------------------------------------------- context */
+
+/* Creates a context bound to CUDA device `device` with `workspace_bytes` of
+ * scratch (may be 0; grow it later with gs_ctx_reserve).  Synchronous. */
+gs_status_t gs_ctx_create(gs_ctx** out, int device, size_t workspace_bytes);
+/* Destroys the context and frees its workspace.  Synchronous. */
+gs_status_t gs_ctx_destroy(gs_ctx* ctx);
+/* Ensures the workspace holds at least `bytes`; reallocates (after a device
+ * synchronise) if it does not.  Synchronous; never call during capture. */
+gs_status_t gs_ctx_reserve(gs_ctx* ctx, size_t bytes);
+/* Tile size B in pixels (8, 16 or 32; default 16).  Changes the tile grid
+ * seen by every later call. */
+gs_status_t gs_ctx_set_tile(gs_ctx* ctx, int32_t tile);
+/* Radix digit width of the tile-key sort (4..8 bits; default 8). */
+gs_status_t gs_ctx_set_sort_bits(gs_ctx* ctx, int32_t bits);
+/* Reads and clears the device status word (synchronises `stream`).
+ * *status receives the first error a kernel recorded since the last read
+ * (GS_OK if none); *detail receives the required size for GS_ERR_CAPACITY. */
+gs_status_t gs_get_status(gs_ctx* ctx, void* stream, int32_t* status, int64_t* detail);
+/* Workspace bytes the steps below need for V views (camera array on the
+ * host), n Gaussians and a key capacity of keys_cap. */
+size_t gs_workspace_size(const gs_ctx* ctx, const gs_camera* host_cams, int32_t n_views,
+                         int64_t n, int64_t keys_cap);
+/* Total tiles and pixels of a camera set (host array), for sizing buffers. */
+int64_t gs_total_tiles(const gs_ctx* ctx, const gs_camera* host_cams, int32_t n_views);
+
+/* ---------------------------------------------------------------- forward */
+
+/* EWA projection with SH colour, for every (view, Gaussian).  Sec. 3.2.3
+ * (3DGS parameters rendered by differentiable splatting), Sec. 3.2.2 / 3.4.1
+ * (SH appearance).  Per view: t = R mu + t_cam; Sigma = R_q S S^T R_q^T;
+ * Jacobian J of the pinhole map at t (x/z, y/z clamped to 1.3 tan(fov/2));
+ * Sigma2D = J R Sigma R^T J^T + 0.3 I; conic = Sigma2D^-1; radius =
+ * ceil(3 sqrt(lambda_max)), lambda_max = mid + sqrt(max(0.1, mid^2 - det));
+ * tile rectangle of that square; rgb = SH(dir) + 0.5 clamped at 0;
+ * opacity = sigmoid(logit).  Culled: z <= near, det <= 0, or empty rect.
+ * d_cams: device gs_camera[V].  Writes proj [V][n][16]. */
+gs_status_t gs_project(gs_ctx* ctx, const gs_scene* scene, const gs_camera* d_cams,
+                       int32_t n_views, float* proj, void* stream);
+
+/* Tile binning + radix sort: every (view, Gaussian, touched tile) becomes one
+ * (tile key, Gaussian index) entry, ordered by (view, tile, float32 depth,
+ * Gaussian index); then per-tile [start, end) ranges.  Implemented as a
+ * stable depth sort of the V*n projected Gaussians followed by a stable
+ * LSD radix sort of the tile keys (both in-house onesweep sorts).
+ * total_tiles: gs_total_tiles() of the camera set (host-known; a mismatch
+ * with the device cameras records GS_ERR_ARG).
+ * sorted_keys (may be NULL) / sorted_vals: uint32 [keys_cap];
+ * ranges: uint32 [total_tiles][2]; d_num_keys: uint32 on the device.
+ * If the entry count K exceeds keys_cap, nothing beyond keys_cap is written,
+ * *d_num_keys = K, and the status word records GS_ERR_CAPACITY with K. */
+gs_status_t gs_bin_sort(gs_ctx* ctx, const float* proj, const gs_camera* d_cams,
+                        int32_t n_views, int64_t n, int64_t total_tiles, int64_t keys_cap,
+                        uint32_t* sorted_keys, uint32_t* sorted_vals, uint32_t* ranges,
+                        uint32_t* d_num_keys, void* stream);
+
+/* Front-to-back alpha compositing per pixel over its tile's sorted list:
+ * alpha = min(0.99, o exp(P)), P = -(A dx^2 + C dy^2)/2 - B dx dy, skipped
+ * when P > 0 or alpha < 1/255; stops before the fragment that would take
+ * T below 1e-4.  image = sum c alpha T + T_final * bg.  n_contrib = 1-based
+ * list position of the last fragment added (0 if none).
+ * bg: host float[3].  T_final / n_contrib may be NULL (forward only). */
+gs_status_t gs_render_fwd(gs_ctx* ctx, const float* proj, const gs_camera* d_cams,
+                          int32_t n_views, int64_t n, int64_t total_tiles,
+                          const uint32_t* sorted_vals,
+                          const uint32_t* ranges, const float* bg, float* image,
+                          float* T_final, uint32_t* n_contrib, void* stream);
+
+/* --------------------------------------------------------------- loss */
+
+/* L = w_l1 * mean|x - y| + w_ssim * (1 - mean SSIM) over V views of H x W x 3
+ * (11x11 Gaussian window, sigma 1.5, C1 = 1e-4, C2 = 9e-4, zero padding),
+ * and dL/dx.  Sec. 3.1 ("compares the result to the captured ground-truth
+ * images ... using the configured loss").  d_loss: one float on the device.
+ * dimage may alias nothing else.  All views must share H and W. */
+gs_status_t gs_loss(gs_ctx* ctx, const float* image, const float* target, int32_t n_views,
+                    int32_t height, int32_t width, float w_l1, float w_ssim,
+                    float* d_loss, float* dimage, void* stream);
+
+/* --------------------------------------------------------------- backward */
+
+/* Reverse-order adjoint of gs_render_fwd: per pixel, walks its list back from
+ * n_contrib, recovering each T_j from T_final (no per-fragment state is
+ * stored), and accumulates dL/d(u, v, A, B, C, opacity, rgb) per (view,
+ * Gaussian) into grad2d (which it first zeroes). */
+gs_status_t gs_raster_bwd(gs_ctx* ctx, const float* proj, const gs_camera* d_cams,
+                          int32_t n_views, int64_t n, int64_t total_tiles,
+                          const uint32_t* sorted_vals,
+                          const uint32_t* ranges, const float* bg, const float* T_final,
+                          const uint32_t* n_contrib, const float* dimage, float* grad2d,
+                          void* stream);
+
+/* Adjoint of gs_project: grad2d of every view -> parameter gradients
+ * dparams [15][n][4], summed over views (accumulate != 0 adds to dparams,
+ * else overwrites).  Zero through clamps, culls and rounding steps. */
+gs_status_t gs_project_bwd(gs_ctx* ctx, const gs_scene* scene, const gs_camera* d_cams,
+                           int32_t n_views, const float* proj, const float* grad2d,
+                           float* dparams, int32_t accumulate, void* stream);
+
+/* gs_raster_bwd followed by gs_project_bwd (overwriting dparams). */
+gs_status_t gs_render_bwd(gs_ctx* ctx, const gs_scene* scene, const gs_camera* d_cams,
+                          int32_t n_views, int64_t total_tiles, const float* proj,
+                          const uint32_t* sorted_vals,
+                          const uint32_t* ranges, const float* bg, const float* T_final,
+                          const uint32_t* n_contrib, const float* dimage, float* grad2d,
+                          float* dparams, void* stream);
+
+/* --------------------------------------------------------------- update */
+
+typedef struct gs_adam_cfg {
+    float lr[60];        /* per element of a Gaussian's 60 floats (plane*4 + lane) */
+    float beta1, beta2, eps;
+    int32_t step;        /* 1-based step, used when d_step is NULL */
+    const int32_t* d_step; /* optional device step counter: read (and, if
+                              increment != 0, incremented by 1 after use) */
+    int32_t increment;
+    int32_t _pad;
+} gs_adam_cfg;
+
+/* Adam with bias correction over theta/grad/m/v [15][n][4] (Sec. 3.1
+ * "configured ... learning rates"; Sec. 3.3 optimiser state).  Pad lanes get
+ * zero gradient and stay put. */
+gs_status_t gs_adam_step(gs_ctx* ctx, float* theta, const float* grad, float* m, float* v,
+                         int64_t n, const gs_adam_cfg* cfg, void* stream);
+
+/* Changed-set extraction for the incremental stream (Sec. 3.5: tensor-delta
+ * packets between snapshots, residuals against the last transmitted state).
+ * Gaussian i is changed when max_k |theta_k - baseline_k| > thr over its 60
+ * floats (float32 arithmetic).  Writes changed indices ascending to d_idx
+ * (uint32 [n]), one 128-byte record each to d_records (uint32 index, float32
+ * mean xyz, then 56 float16 RNE: log-scale xyz, quaternion wxyz, opacity
+ * logit, 48 SH), the count to *d_count, and copies theta into baseline for
+ * every changed Gaussian. */
+gs_status_t gs_extract_delta(gs_ctx* ctx, const float* theta, float* baseline, int64_t n,
+                             float thr, uint32_t* d_idx, uint8_t* d_records,
+                             uint32_t* d_count, void* stream);
+
+/* --------------------------------------------------------------- serving */
+
+/* Forward-only render of R client viewpoints (any mix of resolutions) of a
+ * device-resident model (Sec. 3.1 / 3.5: the client "continuously render[s]
+ * that model ... from the viewpoint of the camera that tracks the user").
+ * image: views concatenated as for gs_render_fwd.  Scratch from the context
+ * workspace (size with gs_workspace_size(ctx, cams, R, n, keys_cap)). */
+gs_status_t gs_render_batch(gs_ctx* ctx, const gs_scene* scene, const gs_camera* d_cams,
+                            int32_t n_requests, int64_t total_tiles, int64_t keys_cap,
+                            const float* bg,
+                            float* image, void* stream);
+
+/* ------------------------------------------------------------ fused step */
+
+typedef struct gs_train_io {
+    float* params;        /* [15][n][4], updated in place */
+    float* grads;         /* [15][n][4], scratch (holds this step's gradient) */
+    float* adam_m;        /* [15][n][4] */
+    float* adam_v;        /* [15][n][4] */
+    float* baseline;      /* [15][n][4], last transmitted values */
+    const float* targets; /* V views, planar [3][H][W] each */
+    float* image;         /* V views, this step's render */
+    float* d_loss;        /* 1 float */
+    uint32_t* d_delta_idx;   /* uint32 [n] */
+    uint8_t* d_delta_records;/* [n][128] */
+    uint32_t* d_delta_count; /* 1 uint32 */
+    int32_t* d_step;      /* Adam step counter, incremented each step */
+} gs_train_io;
+
+typedef struct gs_train_cfg {
+    int64_t n;
+    int32_t sh_degree;
+    int32_t n_views;
+    int32_t width, height; /* shared by all views */
+    int64_t keys_cap;
+    float w_l1, w_ssim;
+    float bg[3];
+    float delta_thr;
+    gs_adam_cfg adam;     /* d_step / step fields are ignored: io.d_step is used */
+} gs_train_cfg;
+
+/* One whole optimisation step over all V reference views (Sec. 3.1: "iterates
+ * over ready reference cameras, optionally grouping them as mini batches"):
+ * project, bin/sort, composite, loss, backward, Adam, delta extraction.
+ * Enqueue-only, no host synchronisation and no allocation: safe to capture
+ * into a CUDA graph.  Workspace: gs_workspace_size(ctx, cams, V, n, keys_cap). */
+gs_status_t gs_train_step(gs_ctx* ctx, const gs_camera* d_cams, const gs_train_io* io,
+                          const gs_train_cfg* cfg, void* stream);
+
+/* Captures gs_train_step into a CUDA graph held by the context (replacing any
+ * earlier one) and replays it with gs_graph_launch.  Synchronous capture. */
+gs_status_t gs_train_graph_capture(gs_ctx* ctx, const gs_camera* d_cams,
+                                   const gs_train_io* io, const gs_train_cfg* cfg,
+                                   void* stream);
+gs_status_t gs_graph_launch(gs_ctx* ctx, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GS_H_ */

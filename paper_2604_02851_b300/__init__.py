@@ -1,0 +1,307 @@
+"""B300 (sm_103a) online 3D Gaussian Splatting step behind a C ABI.
+
+Python names mirror the C entry points of include/gs.h; each function only
+marshals torch tensors (device memory and streams) into the C call.  All
+arithmetic runs in the CUDA kernels of libgs.so.  The library is required:
+without it every call raises (there is no CPU path).
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import _lib
+from ._lib import GsError, check
+
+CAMERA_DTYPE = np.dtype([("R", "<f4", (9,)), ("t", "<f4", (3,)), ("fx", "<f4"), ("fy", "<f4"),
+                         ("cx", "<f4"), ("cy", "<f4"), ("width", "<i4"), ("height", "<i4"),
+                         ("near_plane", "<f4"), ("_pad", "<f4")])
+assert CAMERA_DTYPE.itemsize == 80
+PROJ_STRIDE = 16
+GRAD2D_STRIDE = 12
+RECORD_BYTES = 128
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+# ------------------------------------------------------------------ cameras
+def pack_cameras(cams: dict) -> np.ndarray:
+    """Camera dict (R [V,3,3], t [V,3], fx, fy, cx, cy, width, height, near)
+    -> structured array in the gs_camera layout (80 bytes per view)."""
+    V = len(cams["fx"])
+    a = np.zeros(V, dtype=CAMERA_DTYPE)
+    a["R"] = np.asarray(cams["R"], dtype=np.float64).reshape(V, 9)
+    a["t"] = np.asarray(cams["t"], dtype=np.float64).reshape(V, 3)
+    for k in ("fx", "fy", "cx", "cy"):
+        a[k] = cams[k]
+    a["width"] = cams["width"]
+    a["height"] = cams["height"]
+    a["near_plane"] = cams["near"]
+    return a
+
+
+def cameras_to_device(cams, device="cuda"):
+    """-> uint8 tensor on the device holding gs_camera[V]."""
+    torch = _torch()
+    packed = cams if isinstance(cams, np.ndarray) else pack_cameras(cams)
+    return torch.from_numpy(packed.view(np.uint8).copy()).to(device)
+
+
+def _host_cams(cams):
+    packed = cams if isinstance(cams, np.ndarray) else pack_cameras(cams)
+    packed = np.ascontiguousarray(packed)
+    return packed, packed.ctypes.data_as(C.POINTER(_lib.gs_camera))
+
+
+def view_sizes(cams):
+    packed = cams if isinstance(cams, np.ndarray) else pack_cameras(cams)
+    return [(int(h), int(w)) for w, h in zip(packed["width"], packed["height"])]
+
+
+def total_pixels(cams) -> int:
+    return int(sum(h * w for h, w in view_sizes(cams)))
+
+
+# ------------------------------------------------------------------ context
+class Context:
+    """Owns a gs_ctx (device workspace, status word, graph)."""
+
+    def __init__(self, device: int = 0, workspace_bytes: int = 0, tile: int = 16, sort_bits: int = 8):
+        L = _lib.lib()
+        p = C.c_void_p()
+        check("gs_ctx_create", L.gs_ctx_create(C.byref(p), device, workspace_bytes))
+        self.ptr = p
+        self.device = device
+        self.tile = tile
+        check("gs_ctx_set_tile", L.gs_ctx_set_tile(p, tile))
+        check("gs_ctx_set_sort_bits", L.gs_ctx_set_sort_bits(p, sort_bits))
+
+    def reserve(self, nbytes: int) -> None:
+        check("gs_ctx_reserve", _lib.lib().gs_ctx_reserve(self.ptr, int(nbytes)))
+
+    def status(self, stream=None):
+        code, detail = C.c_int32(), C.c_int64()
+        check("gs_get_status", _lib.lib().gs_get_status(self.ptr, _stream(stream), C.byref(code), C.byref(detail)))
+        return code.value, detail.value
+
+    def raise_status(self, stream=None) -> None:
+        code, detail = self.status(stream)
+        if code != _lib.GS_OK:
+            err = GsError("device status", code)
+            err.detail = detail
+            raise err
+
+    def total_tiles(self, cams) -> int:
+        packed, p = _host_cams(cams)
+        return int(_lib.lib().gs_total_tiles(self.ptr, p, len(packed)))
+
+    def workspace_size(self, cams, n: int, keys_cap: int) -> int:
+        packed, p = _host_cams(cams)
+        return int(_lib.lib().gs_workspace_size(self.ptr, p, len(packed), int(n), int(keys_cap)))
+
+    def close(self) -> None:
+        if self.ptr:
+            _lib.lib().gs_ctx_destroy(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _scene(params, sh_degree):
+    n = params.shape[1] if params is not None else 0
+    return _lib.gs_scene(n=n, sh_degree=sh_degree, params=params.data_ptr() if n else None)
+
+
+# ------------------------------------------------------------------ entry points
+def gs_project(ctx, params, sh_degree, d_cams, n_views, proj=None, stream=None):
+    torch = _torch()
+    n = params.shape[1]
+    if proj is None:
+        proj = torch.empty((n_views, n, PROJ_STRIDE), dtype=torch.float32, device=params.device)
+    sc = _scene(params, sh_degree)
+    check("gs_project", _lib.lib().gs_project(ctx.ptr, C.byref(sc), _ptr(d_cams), n_views, _ptr(proj),
+                                              _stream(stream)))
+    return proj
+
+
+def gs_bin_sort(ctx, proj, d_cams, n_views, n, total_tiles, keys_cap, sorted_keys=None, sorted_vals=None,
+                ranges=None, d_num_keys=None, want_keys=True, stream=None):
+    torch = _torch()
+    dev = proj.device
+    if sorted_vals is None:
+        sorted_vals = torch.empty(max(keys_cap, 1), dtype=torch.int32, device=dev)
+    if want_keys and sorted_keys is None:
+        sorted_keys = torch.empty(max(keys_cap, 1), dtype=torch.int32, device=dev)
+    if ranges is None:
+        ranges = torch.empty((total_tiles, 2), dtype=torch.int32, device=dev)
+    if d_num_keys is None:
+        d_num_keys = torch.zeros(1, dtype=torch.int32, device=dev)
+    check("gs_bin_sort", _lib.lib().gs_bin_sort(ctx.ptr, _ptr(proj), _ptr(d_cams), n_views, n, total_tiles,
+                                                keys_cap, _ptr(sorted_keys), _ptr(sorted_vals), _ptr(ranges),
+                                                _ptr(d_num_keys), _stream(stream)))
+    return sorted_keys, sorted_vals, ranges, d_num_keys
+
+
+def _bg(bg):
+    a = (C.c_float * 3)(*(bg if bg is not None else (0.0, 0.0, 0.0)))
+    return a
+
+
+def gs_render_fwd(ctx, proj, d_cams, n_views, n, total_tiles, sorted_vals, ranges, npix, bg=None,
+                  image=None, T_final=None, n_contrib=None, want_state=True, stream=None):
+    torch = _torch()
+    dev = proj.device
+    if image is None:
+        image = torch.empty(3 * npix, dtype=torch.float32, device=dev)
+    if want_state and T_final is None:
+        T_final = torch.empty(npix, dtype=torch.float32, device=dev)
+    if want_state and n_contrib is None:
+        n_contrib = torch.empty(npix, dtype=torch.int32, device=dev)
+    check("gs_render_fwd", _lib.lib().gs_render_fwd(ctx.ptr, _ptr(proj), _ptr(d_cams), n_views, n, total_tiles,
+                                                    _ptr(sorted_vals), _ptr(ranges), _bg(bg), _ptr(image),
+                                                    _ptr(T_final), _ptr(n_contrib), _stream(stream)))
+    return image, T_final, n_contrib
+
+
+def gs_loss(ctx, image, target, n_views, height, width, w_l1=0.8, w_ssim=0.2, d_loss=None, dimage=None,
+            stream=None):
+    torch = _torch()
+    if d_loss is None:
+        d_loss = torch.zeros(1, dtype=torch.float32, device=image.device)
+    if dimage is None:
+        dimage = torch.empty_like(image)
+    check("gs_loss", _lib.lib().gs_loss(ctx.ptr, _ptr(image), _ptr(target), n_views, height, width, w_l1, w_ssim,
+                                        _ptr(d_loss), _ptr(dimage), _stream(stream)))
+    return d_loss, dimage
+
+
+def gs_raster_bwd(ctx, proj, d_cams, n_views, n, total_tiles, sorted_vals, ranges, T_final, n_contrib, dimage,
+                  bg=None, grad2d=None, stream=None):
+    torch = _torch()
+    if grad2d is None:
+        grad2d = torch.empty((n_views, n, GRAD2D_STRIDE), dtype=torch.float32, device=proj.device)
+    check("gs_raster_bwd", _lib.lib().gs_raster_bwd(ctx.ptr, _ptr(proj), _ptr(d_cams), n_views, n, total_tiles,
+                                                    _ptr(sorted_vals), _ptr(ranges), _bg(bg), _ptr(T_final),
+                                                    _ptr(n_contrib), _ptr(dimage), _ptr(grad2d), _stream(stream)))
+    return grad2d
+
+
+def gs_project_bwd(ctx, params, sh_degree, d_cams, n_views, proj, grad2d, dparams=None, accumulate=False,
+                   stream=None):
+    torch = _torch()
+    if dparams is None:
+        dparams = torch.empty_like(params)
+        accumulate = False
+    sc = _scene(params, sh_degree)
+    check("gs_project_bwd", _lib.lib().gs_project_bwd(ctx.ptr, C.byref(sc), _ptr(d_cams), n_views, _ptr(proj),
+                                                      _ptr(grad2d), _ptr(dparams), int(bool(accumulate)),
+                                                      _stream(stream)))
+    return dparams
+
+
+def gs_render_bwd(ctx, params, sh_degree, d_cams, n_views, total_tiles, proj, sorted_vals, ranges, T_final,
+                  n_contrib, dimage, bg=None, grad2d=None, dparams=None, stream=None):
+    torch = _torch()
+    n = params.shape[1]
+    if grad2d is None:
+        grad2d = torch.empty((n_views, n, GRAD2D_STRIDE), dtype=torch.float32, device=params.device)
+    if dparams is None:
+        dparams = torch.empty_like(params)
+    sc = _scene(params, sh_degree)
+    check("gs_render_bwd", _lib.lib().gs_render_bwd(ctx.ptr, C.byref(sc), _ptr(d_cams), n_views, total_tiles,
+                                                    _ptr(proj), _ptr(sorted_vals), _ptr(ranges), _bg(bg),
+                                                    _ptr(T_final), _ptr(n_contrib), _ptr(dimage), _ptr(grad2d),
+                                                    _ptr(dparams), _stream(stream)))
+    return grad2d, dparams
+
+
+def adam_cfg(lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, step=1, d_step=None, increment=False):
+    cfg = _lib.gs_adam_cfg()
+    lrs = np.broadcast_to(np.asarray(lr, dtype=np.float32), (60,))
+    for i in range(60):
+        cfg.lr[i] = float(lrs[i])
+    cfg.beta1, cfg.beta2, cfg.eps, cfg.step = beta1, beta2, eps, step
+    cfg.d_step = d_step.data_ptr() if d_step is not None else None
+    cfg.increment = int(bool(increment))
+    return cfg
+
+
+def gs_adam_step(ctx, theta, grad, m, v, cfg, stream=None):
+    check("gs_adam_step", _lib.lib().gs_adam_step(ctx.ptr, _ptr(theta), _ptr(grad), _ptr(m), _ptr(v),
+                                                  theta.shape[1], C.byref(cfg), _stream(stream)))
+
+
+def gs_extract_delta(ctx, theta, baseline, thr=1e-3, d_idx=None, d_records=None, d_count=None, stream=None):
+    torch = _torch()
+    n = theta.shape[1]
+    dev = theta.device
+    if d_idx is None:
+        d_idx = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
+    if d_records is None:
+        d_records = torch.empty((max(n, 1), RECORD_BYTES), dtype=torch.uint8, device=dev)
+    if d_count is None:
+        d_count = torch.zeros(1, dtype=torch.int32, device=dev)
+    check("gs_extract_delta", _lib.lib().gs_extract_delta(ctx.ptr, _ptr(theta), _ptr(baseline), n, float(thr),
+                                                          _ptr(d_idx), _ptr(d_records), _ptr(d_count),
+                                                          _stream(stream)))
+    return d_idx, d_records, d_count
+
+
+def gs_render_batch(ctx, params, sh_degree, d_cams, n_requests, total_tiles, keys_cap, npix, bg=None,
+                    image=None, stream=None):
+    torch = _torch()
+    if image is None:
+        image = torch.empty(3 * npix, dtype=torch.float32, device=params.device)
+    sc = _scene(params, sh_degree)
+    check("gs_render_batch", _lib.lib().gs_render_batch(ctx.ptr, C.byref(sc), _ptr(d_cams), n_requests,
+                                                        total_tiles, keys_cap, _bg(bg), _ptr(image),
+                                                        _stream(stream)))
+    return image
+
+
+def train_io(params, grads, m, v, baseline, targets, image, d_loss, d_idx, d_records, d_count, d_step):
+    return _lib.gs_train_io(*(t.data_ptr() for t in (params, grads, m, v, baseline, targets, image, d_loss,
+                                                     d_idx, d_records, d_count, d_step)))
+
+
+def train_cfg(n, sh_degree, n_views, width, height, keys_cap, w_l1=0.8, w_ssim=0.2, bg=(0.0, 0.0, 0.0),
+              delta_thr=1e-3, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
+    cfg = _lib.gs_train_cfg()
+    cfg.n, cfg.sh_degree, cfg.n_views, cfg.width, cfg.height = n, sh_degree, n_views, width, height
+    cfg.keys_cap, cfg.w_l1, cfg.w_ssim, cfg.delta_thr = keys_cap, w_l1, w_ssim, delta_thr
+    for i in range(3):
+        cfg.bg[i] = bg[i]
+    cfg.adam = adam_cfg(lr, beta1, beta2, eps)
+    return cfg
+
+
+def gs_train_step(ctx, d_cams, io, cfg, stream=None):
+    check("gs_train_step", _lib.lib().gs_train_step(ctx.ptr, _ptr(d_cams), C.byref(io), C.byref(cfg),
+                                                    _stream(stream)))
+
+
+def gs_train_graph_capture(ctx, d_cams, io, cfg, stream=None):
+    check("gs_train_graph_capture", _lib.lib().gs_train_graph_capture(ctx.ptr, _ptr(d_cams), C.byref(io),
+                                                                      C.byref(cfg), _stream(stream)))
+
+
+def gs_graph_launch(ctx, stream=None):
+    check("gs_graph_launch", _lib.lib().gs_graph_launch(ctx.ptr, _stream(stream)))

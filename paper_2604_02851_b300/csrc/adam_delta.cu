@@ -1,0 +1,213 @@
+// Adam update and changed-set extraction for the incremental stream.
+//
+// Adam: Sec. 3.1 ("updates the trainable Gaussian parameters using the
+// configured loss and learning rates"), Sec. 3.3 (optimiser state is rebuilt
+// or extended with the model).  Bias-corrected Adam, one float4 per thread,
+// learning rate per element of a Gaussian's 60 floats.
+//
+// Delta: Sec. 3.5 -- between snapshots the server sends tensor-delta packets,
+// with residuals against the previously transmitted state and fresh baselines
+// after a snapshot.  A Gaussian is sent when any of its 60 floats moved by
+// more than thr from its last transmitted value; the sent set is compacted in
+// index order (block sums, one-block scan, ordered emit) and packed as
+// 128-byte records: uint32 index, float32 mean, 56 float16 (RNE) attributes.
+#include <cuda_fp16.h>
+#include <math.h>
+
+#include "gs_internal.cuh"
+
+namespace gs {
+namespace {
+
+struct LrTable { float lr[60]; };
+
+__global__ void __launch_bounds__(256)
+k_adam(float4* __restrict__ theta, const float4* __restrict__ grad, float4* __restrict__ m,
+       float4* __restrict__ v, int64_t n, LrTable lr, float b1, float b2, float eps, int host_step,
+       const int32_t* __restrict__ d_step) {
+    const int step = d_step ? *d_step : host_step;
+    const float bc1 = 1.f - powf(b1, (float)step);
+    const float bc2 = 1.f - powf(b2, (float)step);
+    const float sbc2 = sqrtf(bc2);
+    const int64_t total = 15 * n;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int plane = (int)(i / n);
+        const float4 g = grad[i];
+        float4 mm = m[i], vv = v[i], th = theta[i];
+        const float* l = lr.lr + 4 * plane;
+#define ADAM_LANE(c, k)                                                   \
+        mm.c = b1 * mm.c + (1.f - b1) * g.c;                              \
+        vv.c = b2 * vv.c + (1.f - b2) * g.c * g.c;                        \
+        th.c -= (l[k] / bc1) * mm.c / (sqrtf(vv.c) / sbc2 + eps);
+        ADAM_LANE(x, 0)
+        ADAM_LANE(y, 1)
+        ADAM_LANE(z, 2)
+        ADAM_LANE(w, 3)
+#undef ADAM_LANE
+        m[i] = mm;
+        v[i] = vv;
+        theta[i] = th;
+    }
+}
+
+__global__ void k_inc_step(int32_t* d_step) { *d_step += 1; }
+
+// ---------------------------------------------------------------- delta
+constexpr int kDeltaThreads = 256;
+
+__global__ void __launch_bounds__(kDeltaThreads)
+k_delta_flags(const float4* __restrict__ theta, const float4* __restrict__ base, int64_t n, float thr,
+              uint8_t* __restrict__ flags, uint32_t* __restrict__ block_sums) {
+    const int64_t g = (int64_t)blockIdx.x * kDeltaThreads + threadIdx.x;
+    uint32_t changed = 0;
+    if (g < n) {
+#pragma unroll
+        for (int p = 0; p < 15; ++p) {
+            const float4 a = theta[p * n + g], b = base[p * n + g];
+            const float m = fmaxf(fmaxf(fabsf(a.x - b.x), fabsf(a.y - b.y)), fmaxf(fabsf(a.z - b.z), fabsf(a.w - b.w)));
+            changed |= (m > thr) ? 1u : 0u;
+        }
+        flags[g] = (uint8_t)changed;
+    }
+    const uint32_t cnt = __syncthreads_count(changed);
+    if (threadIdx.x == 0) block_sums[blockIdx.x] = cnt;
+}
+
+__global__ void __launch_bounds__(kDeltaThreads)
+k_delta_emit(const float4* __restrict__ theta, float4* __restrict__ base, int64_t n,
+             const uint8_t* __restrict__ flags, const uint32_t* __restrict__ block_off,
+             uint32_t* __restrict__ d_idx, uint8_t* __restrict__ d_records) {
+    const int64_t g = (int64_t)blockIdx.x * kDeltaThreads + threadIdx.x;
+    const bool ch = g < n && flags[g];
+    const uint32_t ballot = __ballot_sync(0xFFFFFFFFu, ch);
+    __shared__ uint32_t s_w[kDeltaThreads / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) s_w[warp] = __popc(ballot);
+    __syncthreads();
+    uint32_t off = block_off[blockIdx.x];
+    for (int w = 0; w < warp; ++w) off += s_w[w];
+    off += __popc(ballot & ((1u << lane) - 1u));
+    if (!ch) return;
+    d_idx[off] = (uint32_t)g;
+    float t[60];
+#pragma unroll
+    for (int p = 0; p < 15; ++p) {
+        const float4 a = theta[p * n + g];
+        t[4 * p] = a.x; t[4 * p + 1] = a.y; t[4 * p + 2] = a.z; t[4 * p + 3] = a.w;
+        base[p * n + g] = a;
+    }
+    // record: [0] index, [1..3] mean, then float16: log-scale (4..6),
+    // quaternion (8..11), opacity logit (3), SH (12..59)
+    uint32_t w[32];
+    w[0] = (uint32_t)g;
+    w[1] = __float_as_uint(t[0]);
+    w[2] = __float_as_uint(t[1]);
+    w[3] = __float_as_uint(t[2]);
+    uint16_t h[56];
+    int k = 0;
+#pragma unroll
+    for (int i = 4; i < 7; ++i) h[k++] = __half_as_ushort(__float2half_rn(t[i]));
+#pragma unroll
+    for (int i = 8; i < 12; ++i) h[k++] = __half_as_ushort(__float2half_rn(t[i]));
+    h[k++] = __half_as_ushort(__float2half_rn(t[3]));
+#pragma unroll
+    for (int i = 12; i < 60; ++i) h[k++] = __half_as_ushort(__float2half_rn(t[i]));
+#pragma unroll
+    for (int i = 0; i < 28; ++i) w[4 + i] = (uint32_t)h[2 * i] | ((uint32_t)h[2 * i + 1] << 16);
+    uint4* rec = reinterpret_cast<uint4*>(d_records + (size_t)off * 128);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) rec[i] = make_uint4(w[4 * i], w[4 * i + 1], w[4 * i + 2], w[4 * i + 3]);
+}
+
+// ---------------------------------------------------------------- scan
+__global__ void __launch_bounds__(1024)
+k_scan_sums(uint32_t* sums, int64_t count, uint32_t* d_total, long long cap, DevStatus* status) {
+    __shared__ uint32_t s_w[32];
+    __shared__ unsigned long long s_carry;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) s_carry = 0;
+    __syncthreads();
+    for (int64_t base = 0; base < count; base += 1024) {
+        const int64_t i = base + threadIdx.x;
+        const uint32_t x = i < count ? sums[i] : 0u;
+        uint32_t incl = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (lane == 31) s_w[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+            uint32_t w = s_w[lane];
+            uint32_t wi = w;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, wi, o);
+                if (lane >= o) wi += y;
+            }
+            s_w[lane] = wi - w;
+        }
+        __syncthreads();
+        const unsigned long long carry = s_carry;
+        if (i < count) sums[i] = (uint32_t)(carry + s_w[warp] + incl - x);
+        __syncthreads();
+        if (threadIdx.x == 1023) s_carry = carry + s_w[warp] + incl;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const unsigned long long total = s_carry;
+        *d_total = (uint32_t)(total > 0xFFFFFFFFull ? 0xFFFFFFFFull : total);
+        if (cap >= 0 && (long long)total > cap) record_status(status, GS_ERR_CAPACITY, (long long)total);
+    }
+}
+
+}  // namespace
+
+void launch_scan_sums(uint32_t* sums, int64_t count, uint32_t* d_total, long long cap, DevStatus* status,
+                      cudaStream_t st) {
+    k_scan_sums<<<1, 1024, 0, st>>>(sums, count, d_total, cap, status);
+}
+
+void launch_adam(float* theta, const float* grad, float* m, float* v, int64_t n, const gs_adam_cfg& cfg,
+                 cudaStream_t st) {
+    if (n > 0) {
+        LrTable lr;
+        for (int i = 0; i < 60; ++i) lr.lr[i] = cfg.lr[i];
+        const int64_t total = 15 * n;
+        int64_t blocks = (total + 255) / 256;
+        if (blocks > 148 * 16) blocks = 148 * 16;
+        k_adam<<<(unsigned)blocks, 256, 0, st>>>(
+            reinterpret_cast<float4*>(theta), reinterpret_cast<const float4*>(grad),
+            reinterpret_cast<float4*>(m), reinterpret_cast<float4*>(v), n, lr, cfg.beta1, cfg.beta2,
+            cfg.eps, cfg.step, cfg.d_step);
+    }
+    if (cfg.d_step && cfg.increment) k_inc_step<<<1, 1, 0, st>>>(const_cast<int32_t*>(cfg.d_step));
+}
+
+size_t delta_scratch_bytes(int64_t n) {
+    Carver c(nullptr);
+    c.take<uint8_t>(n > 0 ? n : 1);
+    c.take<uint32_t>((n + kDeltaThreads - 1) / kDeltaThreads + 1);
+    return c.off;
+}
+
+void launch_delta(const float* theta, float* baseline, int64_t n, float thr, uint32_t* d_idx,
+                  uint8_t* d_records, uint32_t* d_count, char* scratch, cudaStream_t st) {
+    Carver c(scratch);
+    uint8_t* flags = c.take<uint8_t>(n > 0 ? n : 1);
+    const int64_t nblk = (n + kDeltaThreads - 1) / kDeltaThreads;
+    uint32_t* sums = c.take<uint32_t>(nblk + 1);
+    if (n <= 0) {
+        cudaMemsetAsync(d_count, 0, sizeof(uint32_t), st);
+        return;
+    }
+    const float4* th = reinterpret_cast<const float4*>(theta);
+    float4* b = reinterpret_cast<float4*>(baseline);
+    k_delta_flags<<<(unsigned)nblk, kDeltaThreads, 0, st>>>(th, b, n, thr, flags, sums);
+    k_scan_sums<<<1, 1024, 0, st>>>(sums, nblk, d_count, -1, nullptr);
+    k_delta_emit<<<(unsigned)nblk, kDeltaThreads, 0, st>>>(th, b, n, flags, sums, d_idx, d_records);
+}
+
+}  // namespace gs

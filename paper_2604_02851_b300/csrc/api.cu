@@ -1,0 +1,421 @@
+// extern "C" entry points declared in include/gs.h.
+//
+// Host-side argument checks happen before anything is enqueued; kernels
+// report their own errors through the context's device status word.  Scratch
+// comes from the context workspace, carved per call from its start (calls on
+// one context are stream-ordered, so a later call may reuse the region).
+#include <algorithm>
+#include <cstring>
+#include <new>
+
+#include "gs_internal.cuh"
+
+using namespace gs;
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+inline cudaStream_t S(void* s) { return static_cast<cudaStream_t>(s); }
+
+gs_status_t launch_check() {
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? GS_OK : GS_ERR_CUDA;
+}
+
+int64_t tiles_of(const gs_camera* cams, int V, int tile) {
+    int64_t t = 0;
+    for (int v = 0; v < V; ++v)
+        t += (int64_t)((cams[v].width + tile - 1) / tile) * ((cams[v].height + tile - 1) / tile);
+    return t;
+}
+
+bool bad_views(int V) { return V < 1 || V > kMaxViews; }
+
+// Workspace plan of the fused calls (render_batch, train_step).
+struct FusedPlan {
+    ViewInfo* vt;
+    float* proj;
+    char* sort;
+    uint32_t* vals;
+    uint32_t* ranges;
+    uint32_t* n_keys;
+    float* T_final;
+    uint32_t* n_contrib;
+    float* dimage;
+    char* loss;
+    float* grad2d;
+    char* delta;
+    size_t bytes;
+};
+
+FusedPlan plan_fused(void* base, int V, int64_t n, int64_t keys_cap, int64_t total_tiles,
+                     int64_t total_pixels, int H, int W, bool train) {
+    Carver c(base);
+    FusedPlan p{};
+    p.vt = c.take<ViewInfo>(V + 1);
+    p.proj = c.take<float>((size_t)V * n * kProjStride);
+    p.sort = c.take<char>(sort_scratch_bytes(V, n, keys_cap));
+    p.vals = c.take<uint32_t>(keys_cap);
+    p.ranges = c.take<uint32_t>(total_tiles * 2);
+    p.n_keys = c.take<uint32_t>(1);
+    if (train) {
+        p.T_final = c.take<float>(total_pixels);
+        p.n_contrib = c.take<uint32_t>(total_pixels);
+        p.dimage = c.take<float>(3 * total_pixels);
+        p.loss = c.take<char>(loss_scratch_bytes(V, H, W));
+        p.grad2d = c.take<float>((size_t)V * n * kGradStride);
+        p.delta = c.take<char>(delta_scratch_bytes(n));
+    }
+    p.bytes = c.off;
+    return p;
+}
+
+gs_status_t check_ws(const gs_ctx* ctx, size_t need) {
+    return need <= ctx->ws_bytes ? GS_OK : GS_ERR_CAPACITY;
+}
+
+}  // namespace
+
+extern "C" {
+
+gs_status_t gs_ctx_create(gs_ctx** out, int device, size_t workspace_bytes) {
+    if (!out) return GS_ERR_ARG;
+    *out = nullptr;
+    gs_ctx* c = new (std::nothrow) gs_ctx();
+    if (!c) return GS_ERR_OOM;
+    c->device = device;
+    DeviceGuard g(device);
+    if (cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+        delete c;
+        return GS_ERR_CUDA;
+    }
+    if (cudaMalloc(&c->d_status, sizeof(DevStatus)) != cudaSuccess) {
+        delete c;
+        return GS_ERR_OOM;
+    }
+    cudaMemset(c->d_status, 0, sizeof(DevStatus));
+    if (cudaStreamCreateWithFlags(&c->capture_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaFree(c->d_status);
+        delete c;
+        return GS_ERR_CUDA;
+    }
+    *out = c;
+    if (workspace_bytes) {
+        const gs_status_t s = gs_ctx_reserve(c, workspace_bytes);
+        if (s != GS_OK) {
+            gs_ctx_destroy(c);
+            *out = nullptr;
+            return s;
+        }
+    }
+    return GS_OK;
+}
+
+gs_status_t gs_ctx_destroy(gs_ctx* ctx) {
+    if (!ctx) return GS_ERR_ARG;
+    DeviceGuard g(ctx->device);
+    cudaDeviceSynchronize();
+    if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
+    if (ctx->graph) cudaGraphDestroy(ctx->graph);
+    if (ctx->ws) cudaFree(ctx->ws);
+    if (ctx->d_status) cudaFree(ctx->d_status);
+    if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
+    delete ctx;
+    return GS_OK;
+}
+
+gs_status_t gs_ctx_reserve(gs_ctx* ctx, size_t bytes) {
+    if (!ctx) return GS_ERR_ARG;
+    if (bytes <= ctx->ws_bytes) return GS_OK;
+    DeviceGuard g(ctx->device);
+    cudaDeviceSynchronize();
+    if (ctx->ws) cudaFree(ctx->ws);
+    ctx->ws = nullptr;
+    ctx->ws_bytes = 0;
+    if (cudaMalloc(&ctx->ws, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return GS_ERR_OOM;
+    }
+    ctx->ws_bytes = bytes;
+    return GS_OK;
+}
+
+gs_status_t gs_ctx_set_tile(gs_ctx* ctx, int32_t tile) {
+    if (!ctx || (tile != 8 && tile != 16)) return GS_ERR_ARG;
+    ctx->tile = tile;
+    return GS_OK;
+}
+
+gs_status_t gs_ctx_set_sort_bits(gs_ctx* ctx, int32_t bits) {
+    if (!ctx || bits < 4 || bits > 8) return GS_ERR_ARG;
+    ctx->sort_bits = bits;
+    return GS_OK;
+}
+
+gs_status_t gs_get_status(gs_ctx* ctx, void* stream, int32_t* status, int64_t* detail) {
+    if (!ctx || !status) return GS_ERR_ARG;
+    DeviceGuard g(ctx->device);
+    DevStatus h{};
+    if (cudaMemcpyAsync(&h, ctx->d_status, sizeof(h), cudaMemcpyDeviceToHost, S(stream)) != cudaSuccess)
+        return GS_ERR_CUDA;
+    if (cudaStreamSynchronize(S(stream)) != cudaSuccess) return GS_ERR_CUDA;
+    cudaMemsetAsync(ctx->d_status, 0, sizeof(DevStatus), S(stream));
+    if (cudaStreamSynchronize(S(stream)) != cudaSuccess) return GS_ERR_CUDA;
+    *status = h.code;
+    if (detail) *detail = h.detail;
+    return GS_OK;
+}
+
+int64_t gs_total_tiles(const gs_ctx* ctx, const gs_camera* host_cams, int32_t n_views) {
+    if (!ctx || !host_cams || bad_views(n_views)) return -1;
+    return tiles_of(host_cams, n_views, ctx->tile);
+}
+
+size_t gs_workspace_size(const gs_ctx* ctx, const gs_camera* host_cams, int32_t n_views, int64_t n,
+                         int64_t keys_cap) {
+    if (!ctx || !host_cams || bad_views(n_views) || n < 0 || keys_cap < 0) return 0;
+    const int64_t tt = tiles_of(host_cams, n_views, ctx->tile);
+    int64_t px = 0;
+    for (int v = 0; v < n_views; ++v) px += (int64_t)host_cams[v].width * host_cams[v].height;
+    const FusedPlan p = plan_fused(nullptr, n_views, n, keys_cap, tt, px, host_cams[0].height,
+                                   host_cams[0].width, true);
+    return p.bytes + 4096;
+}
+
+gs_status_t gs_project(gs_ctx* ctx, const gs_scene* scene, const gs_camera* d_cams, int32_t n_views,
+                       float* proj, void* stream) {
+    if (!ctx || !scene || !d_cams || !proj || bad_views(n_views) || scene->n < 0 ||
+        scene->sh_degree < 0 || scene->sh_degree > 3 || (scene->n > 0 && !scene->params))
+        return GS_ERR_ARG;
+    if ((int64_t)n_views * scene->n >= (1LL << 32)) return GS_ERR_ARG;
+    Carver c(ctx->ws);
+    ViewInfo* vt = c.take<ViewInfo>(n_views + 1);
+    if (check_ws(ctx, c.off)) return GS_ERR_CAPACITY;
+    DeviceGuard g(ctx->device);
+    launch_view_table(d_cams, n_views, ctx->tile, vt, -1, ctx->d_status, S(stream));
+    launch_project(scene->params, scene->n, scene->sh_degree, d_cams, vt, n_views, ctx->tile, proj,
+                   nullptr, nullptr, S(stream));
+    return launch_check();
+}
+
+gs_status_t gs_bin_sort(gs_ctx* ctx, const float* proj, const gs_camera* d_cams, int32_t n_views, int64_t n,
+                        int64_t total_tiles, int64_t keys_cap, uint32_t* sorted_keys, uint32_t* sorted_vals,
+                        uint32_t* ranges, uint32_t* d_num_keys, void* stream) {
+    if (!ctx || !proj || !d_cams || !sorted_vals || !ranges || !d_num_keys || bad_views(n_views) || n < 0 ||
+        total_tiles < 1 || keys_cap < 0 || keys_cap >= (1LL << 32) || (int64_t)n_views * n >= (1LL << 32))
+        return GS_ERR_ARG;
+    Carver c(ctx->ws);
+    ViewInfo* vt = c.take<ViewInfo>(n_views + 1);
+    char* ss = c.take<char>(sort_scratch_bytes(n_views, n, keys_cap));
+    if (check_ws(ctx, c.off)) return GS_ERR_CAPACITY;
+    DeviceGuard g(ctx->device);
+    SortScratch s;
+    carve_sort_scratch(ss, n_views, n, keys_cap, &s);
+    launch_view_table(d_cams, n_views, ctx->tile, vt, total_tiles, ctx->d_status, S(stream));
+    launch_bin_sort(proj, vt, n_views, n, keys_cap, total_tiles, ctx->sort_bits, s, false, sorted_keys,
+                    sorted_vals, ranges, d_num_keys, ctx->d_status, ctx->sm_count, S(stream));
+    return launch_check();
+}
+
+gs_status_t gs_render_fwd(gs_ctx* ctx, const float* proj, const gs_camera* d_cams, int32_t n_views, int64_t n,
+                          int64_t total_tiles, const uint32_t* sorted_vals, const uint32_t* ranges,
+                          const float* bg, float* image, float* T_final, uint32_t* n_contrib, void* stream) {
+    if (!ctx || !proj || !d_cams || !sorted_vals || !ranges || !image || bad_views(n_views) || n < 0 ||
+        total_tiles < 1)
+        return GS_ERR_ARG;
+    Carver c(ctx->ws);
+    ViewInfo* vt = c.take<ViewInfo>(n_views + 1);
+    if (check_ws(ctx, c.off)) return GS_ERR_CAPACITY;
+    DeviceGuard g(ctx->device);
+    const float3 b = bg ? make_float3(bg[0], bg[1], bg[2]) : make_float3(0.f, 0.f, 0.f);
+    launch_view_table(d_cams, n_views, ctx->tile, vt, total_tiles, ctx->d_status, S(stream));
+    launch_render_fwd(proj, vt, n_views, n, ctx->tile, sorted_vals, ranges, b, image, T_final, n_contrib,
+                      total_tiles, S(stream));
+    return launch_check();
+}
+
+gs_status_t gs_loss(gs_ctx* ctx, const float* image, const float* target, int32_t n_views, int32_t height,
+                    int32_t width, float w_l1, float w_ssim, float* d_loss, float* dimage, void* stream) {
+    if (!ctx || !image || !target || !d_loss || !dimage || bad_views(n_views) || height < 1 || width < 1)
+        return GS_ERR_ARG;
+    Carver c(ctx->ws);
+    char* ls = c.take<char>(loss_scratch_bytes(n_views, height, width));
+    if (check_ws(ctx, c.off)) return GS_ERR_CAPACITY;
+    DeviceGuard g(ctx->device);
+    launch_loss(image, target, n_views, height, width, w_l1, w_ssim, d_loss, dimage, ls, S(stream));
+    return launch_check();
+}
+
+gs_status_t gs_raster_bwd(gs_ctx* ctx, const float* proj, const gs_camera* d_cams, int32_t n_views, int64_t n,
+                          int64_t total_tiles, const uint32_t* sorted_vals, const uint32_t* ranges,
+                          const float* bg, const float* T_final, const uint32_t* n_contrib,
+                          const float* dimage, float* grad2d, void* stream) {
+    if (!ctx || !proj || !d_cams || !sorted_vals || !ranges || !T_final || !n_contrib || !dimage || !grad2d ||
+        bad_views(n_views) || n < 0 || total_tiles < 1)
+        return GS_ERR_ARG;
+    Carver c(ctx->ws);
+    ViewInfo* vt = c.take<ViewInfo>(n_views + 1);
+    if (check_ws(ctx, c.off)) return GS_ERR_CAPACITY;
+    DeviceGuard g(ctx->device);
+    const float3 b = bg ? make_float3(bg[0], bg[1], bg[2]) : make_float3(0.f, 0.f, 0.f);
+    launch_view_table(d_cams, n_views, ctx->tile, vt, total_tiles, ctx->d_status, S(stream));
+    launch_raster_bwd(proj, vt, n_views, n, ctx->tile, sorted_vals, ranges, b, T_final, n_contrib, dimage,
+                      grad2d, total_tiles, S(stream));
+    return launch_check();
+}
+
+gs_status_t gs_project_bwd(gs_ctx* ctx, const gs_scene* scene, const gs_camera* d_cams, int32_t n_views,
+                           const float* proj, const float* grad2d, float* dparams, int32_t accumulate,
+                           void* stream) {
+    if (!ctx || !scene || !d_cams || !proj || !grad2d || !dparams || bad_views(n_views) || scene->n < 0 ||
+        scene->sh_degree < 0 || scene->sh_degree > 3 || (scene->n > 0 && !scene->params))
+        return GS_ERR_ARG;
+    DeviceGuard g(ctx->device);
+    launch_project_bwd(scene->params, scene->n, scene->sh_degree, d_cams, n_views, proj, grad2d, dparams,
+                       accumulate, S(stream));
+    return launch_check();
+}
+
+gs_status_t gs_render_bwd(gs_ctx* ctx, const gs_scene* scene, const gs_camera* d_cams, int32_t n_views,
+                          int64_t total_tiles, const float* proj, const uint32_t* sorted_vals,
+                          const uint32_t* ranges, const float* bg, const float* T_final,
+                          const uint32_t* n_contrib, const float* dimage, float* grad2d, float* dparams,
+                          void* stream) {
+    if (!scene) return GS_ERR_ARG;
+    gs_status_t s = gs_raster_bwd(ctx, proj, d_cams, n_views, scene->n, total_tiles, sorted_vals, ranges, bg,
+                                  T_final, n_contrib, dimage, grad2d, stream);
+    if (s != GS_OK) return s;
+    return gs_project_bwd(ctx, scene, d_cams, n_views, proj, grad2d, dparams, 0, stream);
+}
+
+gs_status_t gs_adam_step(gs_ctx* ctx, float* theta, const float* grad, float* m, float* v, int64_t n,
+                         const gs_adam_cfg* cfg, void* stream) {
+    if (!ctx || !cfg || n < 0 || (n > 0 && (!theta || !grad || !m || !v)) || (!cfg->d_step && cfg->step < 1))
+        return GS_ERR_ARG;
+    DeviceGuard g(ctx->device);
+    launch_adam(theta, grad, m, v, n, *cfg, S(stream));
+    return launch_check();
+}
+
+gs_status_t gs_extract_delta(gs_ctx* ctx, const float* theta, float* baseline, int64_t n, float thr,
+                             uint32_t* d_idx, uint8_t* d_records, uint32_t* d_count, void* stream) {
+    if (!ctx || n < 0 || !d_count || (n > 0 && (!theta || !baseline || !d_idx || !d_records)) ||
+        n >= (1LL << 32) || !(thr >= 0.f))
+        return GS_ERR_ARG;
+    Carver c(ctx->ws);
+    char* ds = c.take<char>(delta_scratch_bytes(n));
+    if (check_ws(ctx, c.off)) return GS_ERR_CAPACITY;
+    DeviceGuard g(ctx->device);
+    launch_delta(theta, baseline, n, thr, d_idx, d_records, d_count, ds, S(stream));
+    return launch_check();
+}
+
+gs_status_t gs_render_batch(gs_ctx* ctx, const gs_scene* scene, const gs_camera* d_cams, int32_t n_requests,
+                            int64_t total_tiles, int64_t keys_cap, const float* bg, float* image,
+                            void* stream) {
+    if (!ctx || !scene || !d_cams || !image || bad_views(n_requests) || scene->n < 0 || total_tiles < 1 ||
+        keys_cap < 0 || keys_cap >= (1LL << 32) || scene->sh_degree < 0 || scene->sh_degree > 3 ||
+        (scene->n > 0 && !scene->params) || (int64_t)n_requests * scene->n >= (1LL << 32))
+        return GS_ERR_ARG;
+    const FusedPlan p0 = plan_fused(nullptr, n_requests, scene->n, keys_cap, total_tiles, 0, 0, 0, false);
+    if (check_ws(ctx, p0.bytes)) return GS_ERR_CAPACITY;
+    const FusedPlan p = plan_fused(ctx->ws, n_requests, scene->n, keys_cap, total_tiles, 0, 0, 0, false);
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = S(stream);
+    SortScratch s;
+    carve_sort_scratch(p.sort, n_requests, scene->n, keys_cap, &s);
+    const float3 b = bg ? make_float3(bg[0], bg[1], bg[2]) : make_float3(0.f, 0.f, 0.f);
+    launch_view_table(d_cams, n_requests, ctx->tile, p.vt, total_tiles, ctx->d_status, st);
+    launch_project(scene->params, scene->n, scene->sh_degree, d_cams, p.vt, n_requests, ctx->tile, p.proj,
+                   s.dkeys[0], s.dvals[0], st);
+    launch_bin_sort(p.proj, p.vt, n_requests, scene->n, keys_cap, total_tiles, ctx->sort_bits, s, true, nullptr,
+                    p.vals, p.ranges, p.n_keys, ctx->d_status, ctx->sm_count, st);
+    launch_render_fwd(p.proj, p.vt, n_requests, scene->n, ctx->tile, p.vals, p.ranges, b, image, nullptr,
+                      nullptr, total_tiles, st);
+    return launch_check();
+}
+
+gs_status_t gs_train_step(gs_ctx* ctx, const gs_camera* d_cams, const gs_train_io* io, const gs_train_cfg* cfg,
+                          void* stream) {
+    if (!ctx || !d_cams || !io || !cfg || bad_views(cfg->n_views) || cfg->n < 0 || cfg->sh_degree < 0 ||
+        cfg->sh_degree > 3 || cfg->width < 1 || cfg->height < 1 || cfg->keys_cap < 0 ||
+        cfg->keys_cap >= (1LL << 32) || (int64_t)cfg->n_views * cfg->n >= (1LL << 32) || !io->params ||
+        !io->grads || !io->adam_m || !io->adam_v || !io->baseline || !io->targets || !io->image ||
+        !io->d_loss || !io->d_delta_idx || !io->d_delta_records || !io->d_delta_count || !io->d_step)
+        return GS_ERR_ARG;
+    const int V = cfg->n_views;
+    const int64_t n = cfg->n;
+    const int B = ctx->tile;
+    const int64_t tt = (int64_t)V * ((cfg->width + B - 1) / B) * ((cfg->height + B - 1) / B);
+    const int64_t px = (int64_t)V * cfg->width * cfg->height;
+    const FusedPlan p0 = plan_fused(nullptr, V, n, cfg->keys_cap, tt, px, cfg->height, cfg->width, true);
+    if (check_ws(ctx, p0.bytes)) return GS_ERR_CAPACITY;
+    const FusedPlan p = plan_fused(ctx->ws, V, n, cfg->keys_cap, tt, px, cfg->height, cfg->width, true);
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = S(stream);
+    SortScratch s;
+    carve_sort_scratch(p.sort, V, n, cfg->keys_cap, &s);
+    const float3 b = make_float3(cfg->bg[0], cfg->bg[1], cfg->bg[2]);
+    launch_view_table(d_cams, V, B, p.vt, tt, ctx->d_status, st);
+    launch_project(io->params, n, cfg->sh_degree, d_cams, p.vt, V, B, p.proj, s.dkeys[0], s.dvals[0], st);
+    launch_bin_sort(p.proj, p.vt, V, n, cfg->keys_cap, tt, ctx->sort_bits, s, true, nullptr, p.vals, p.ranges,
+                    p.n_keys, ctx->d_status, ctx->sm_count, st);
+    launch_render_fwd(p.proj, p.vt, V, n, B, p.vals, p.ranges, b, io->image, p.T_final, p.n_contrib, tt, st);
+    launch_loss(io->image, io->targets, V, cfg->height, cfg->width, cfg->w_l1, cfg->w_ssim, io->d_loss, p.dimage,
+                p.loss, st);
+    launch_raster_bwd(p.proj, p.vt, V, n, B, p.vals, p.ranges, b, p.T_final, p.n_contrib, p.dimage, p.grad2d, tt,
+                      st);
+    launch_project_bwd(io->params, n, cfg->sh_degree, d_cams, V, p.proj, p.grad2d, io->grads, 0, st);
+    gs_adam_cfg ac = cfg->adam;
+    ac.d_step = io->d_step;
+    ac.increment = 1;
+    launch_adam(io->params, io->grads, io->adam_m, io->adam_v, n, ac, st);
+    launch_delta(io->params, io->baseline, n, cfg->delta_thr, io->d_delta_idx, io->d_delta_records,
+                 io->d_delta_count, p.delta, st);
+    return launch_check();
+}
+
+gs_status_t gs_train_graph_capture(gs_ctx* ctx, const gs_camera* d_cams, const gs_train_io* io,
+                                   const gs_train_cfg* cfg, void* stream) {
+    if (!ctx) return GS_ERR_ARG;
+    DeviceGuard g(ctx->device);
+    if (cudaStreamSynchronize(S(stream)) != cudaSuccess) return GS_ERR_CUDA;
+    if (ctx->graph_exec) { cudaGraphExecDestroy(ctx->graph_exec); ctx->graph_exec = nullptr; }
+    if (ctx->graph) { cudaGraphDestroy(ctx->graph); ctx->graph = nullptr; }
+    if (cudaStreamBeginCapture(ctx->capture_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+        return GS_ERR_CUDA;
+    const gs_status_t s = gs_train_step(ctx, d_cams, io, cfg, ctx->capture_stream);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(ctx->capture_stream, &graph);
+    if (s != GS_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return s;
+    }
+    if (e != cudaSuccess || !graph) return GS_ERR_CUDA;
+    if (cudaGraphInstantiate(&ctx->graph_exec, graph, 0) != cudaSuccess) {
+        cudaGraphDestroy(graph);
+        return GS_ERR_CUDA;
+    }
+    ctx->graph = graph;
+    return GS_OK;
+}
+
+gs_status_t gs_graph_launch(gs_ctx* ctx, void* stream) {
+    if (!ctx || !ctx->graph_exec) return GS_ERR_ARG;
+    DeviceGuard g(ctx->device);
+    return cudaGraphLaunch(ctx->graph_exec, S(stream)) == cudaSuccess ? GS_OK : GS_ERR_CUDA;
+}
+
+}  // extern "C"

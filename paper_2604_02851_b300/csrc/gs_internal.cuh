@@ -1,0 +1,147 @@
+// Internal declarations of the sm_103a implementation behind include/gs.h.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "gs.h"
+
+namespace gs {
+
+constexpr int kProjStride = 16;  // floats per (view, Gaussian) projection record
+constexpr int kGradStride = 12;  // floats per (view, Gaussian) 2D-gradient record
+constexpr int kParamPlanes = 15;
+constexpr int kMaxViews = 4096;
+
+// Compositing constants of the cited 3DGS method (Sec. 3.2.3 of the paper
+// refits "the same parameters as in prior 3DGS work").
+constexpr float kAlphaMax = 0.99f;
+constexpr float kAlphaMin = 1.0f / 255.0f;
+constexpr float kTMin = 1e-4f;
+constexpr float kDilation = 0.3f;
+constexpr float kGuard = 1.3f;
+
+// Per-view derived geometry, computed on the device from the camera array.
+// Entry V holds the totals (tile_off = total tiles, pix_off = total pixels).
+struct ViewInfo {
+    int32_t tx, ty;       // tiles along x / y
+    int32_t width, height;
+    int64_t tile_off;     // first global tile index of this view
+    int64_t pix_off;      // first pixel (per channel) of this view
+};
+
+struct DevStatus {
+    int32_t code;
+    int32_t pad;
+    long long detail;
+};
+
+__device__ __forceinline__ void record_status(DevStatus* s, int code, long long detail) {
+    if (atomicCAS(&s->code, 0, code) == 0) s->detail = detail;
+}
+
+// Spin bound for inter-block waits: about one second at 2 GHz.
+constexpr long long kSpinCycles = 2000000000LL;
+
+// ------------------------------------------------------------ launchers
+// Every launcher enqueues on `st`; none synchronises or allocates.
+
+void launch_view_table(const gs_camera* d_cams, int V, int tile, ViewInfo* vt,
+                       long long expect_tiles, DevStatus* status, cudaStream_t st);
+
+void launch_project(const float* params, int64_t n, int sh_degree, const gs_camera* d_cams,
+                    const ViewInfo* vt, int V, int tile, float* proj, uint32_t* depth_keys,
+                    uint32_t* depth_vals, cudaStream_t st);
+
+void launch_project_bwd(const float* params, int64_t n, int sh_degree, const gs_camera* d_cams,
+                        int V, const float* proj, const float* grad2d, float* dparams,
+                        int accumulate, cudaStream_t st);
+
+// Scratch of the bin/sort stage (all device pointers inside the workspace).
+struct SortScratch {
+    uint32_t* dkeys[2];        // depth sort ping-pong, V*n each
+    uint32_t* dvals[2];
+    uint32_t* block_sums;      // emission block sums (+1)
+    uint32_t* tkeys[3];        // tile-key input / temporary / default output, keys_cap each
+    uint32_t* tvals[2];
+    uint32_t* hist;            // [4][256]
+    uint32_t* counters;        // [8] onesweep tile counters (+ misc)
+    unsigned long long* lookback;  // [4][max_tiles][256]
+    int64_t max_sort_tiles;    // per pass
+    uint32_t* d_count_depth;   // V*n as a device scalar
+};
+
+size_t sort_scratch_bytes(int V, int64_t n, int64_t keys_cap);
+void carve_sort_scratch(char* base, int V, int64_t n, int64_t keys_cap, SortScratch* s);
+
+// Full bin + sort: depth sort, key emission, tile-key sort, ranges.
+void launch_bin_sort(const float* proj, const ViewInfo* vt, int V, int64_t n, int64_t keys_cap,
+                     int64_t total_tiles, int sort_bits, const SortScratch& s, bool depth_ready,
+                     uint32_t* sorted_keys, uint32_t* sorted_vals, uint32_t* ranges,
+                     uint32_t* d_num_keys, DevStatus* status, int sm_count, cudaStream_t st);
+
+void launch_render_fwd(const float* proj, const ViewInfo* vt, int V, int64_t n, int tile,
+                       const uint32_t* vals, const uint32_t* ranges, float3 bg, float* image,
+                       float* T_final, uint32_t* n_contrib, int64_t total_tiles,
+                       cudaStream_t st);
+
+void launch_raster_bwd(const float* proj, const ViewInfo* vt, int V, int64_t n, int tile,
+                       const uint32_t* vals, const uint32_t* ranges, float3 bg,
+                       const float* T_final, const uint32_t* n_contrib, const float* dimage,
+                       float* grad2d, int64_t total_tiles, cudaStream_t st);
+
+size_t loss_scratch_bytes(int V, int H, int W);
+void launch_loss(const float* image, const float* target, int V, int H, int W, float w_l1,
+                 float w_ssim, float* d_loss, float* dimage, char* scratch, cudaStream_t st);
+
+void launch_adam(float* theta, const float* grad, float* m, float* v, int64_t n,
+                 const gs_adam_cfg& cfg, cudaStream_t st);
+
+size_t delta_scratch_bytes(int64_t n);
+void launch_delta(const float* theta, float* baseline, int64_t n, float thr, uint32_t* d_idx,
+                  uint8_t* d_records, uint32_t* d_count, char* scratch, cudaStream_t st);
+
+// Stable sort of (key, value) pairs by the low key_bits bits of the key.
+// Pass p writes (kout, vout) when (passes - 1 - p) is even, else the
+// temporaries; the temporaries must differ from input and output, and the
+// output may alias the input only when the pass count is even.
+void sort_pairs(const uint32_t* kin, const uint32_t* vin, uint32_t* ktmp, uint32_t* vtmp,
+                uint32_t* kout, uint32_t* vout, const uint32_t* d_count, int64_t cap, int key_bits,
+                int digit_bits, const SortScratch& s, DevStatus* status, int sm_count,
+                cudaStream_t st);
+
+// Exclusive scan of `count` uint32 block sums in place (one block); the total
+// goes to *d_total; if cap >= 0 and the total exceeds it, GS_ERR_CAPACITY.
+void launch_scan_sums(uint32_t* sums, int64_t count, uint32_t* d_total, long long cap,
+                      DevStatus* status, cudaStream_t st);
+
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Bump allocator over the workspace; with base == nullptr it only measures.
+struct Carver {
+    char* base;
+    size_t off = 0;
+    explicit Carver(void* b) : base(static_cast<char*>(b)) {}
+    template <class T>
+    T* take(size_t count) {
+        off = align_up(off, 256);
+        T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+        off += count * sizeof(T);
+        return p;
+    }
+};
+
+}  // namespace gs
+
+struct gs_ctx {
+    int device = 0;
+    int sm_count = 148;
+    int tile = 16;
+    int sort_bits = 8;
+    void* ws = nullptr;
+    size_t ws_bytes = 0;
+    gs::DevStatus* d_status = nullptr;
+    cudaStream_t capture_stream = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
+};

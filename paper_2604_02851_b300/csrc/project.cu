@@ -1,0 +1,511 @@
+// EWA projection with spherical-harmonics colour, and its adjoint.
+//
+// Sec. 3.2.3: the model is refined by differentiable rendering of "the same
+// parameters as in prior 3DGS work" (means, scales, rotations, opacities, SH
+// coefficients -- Sec. 3.1); Sec. 3.2.2 / 3.4.1: appearance is a diffuse SH
+// representation of degree <= 3.
+//
+// One thread owns one Gaussian: its 60 parameters are read once (coalesced
+// float4 planes) and every view is projected from registers, so the model is
+// read from HBM once per step however many reference views there are.
+#include "gs_internal.cuh"
+
+namespace gs {
+namespace {
+
+// Real SH normalisation constants: sqrt((2l+1)/(4 pi) (l-|m|)!/(l+|m|)!)
+// times the polynomial factor, for the Condon-Shortley-phase real basis.
+constexpr float kY0 = 0.28209479177387814f;   // sqrt(1/(4 pi))
+constexpr float kY1 = 0.48860251190291992f;   // sqrt(3/(4 pi))
+constexpr float kY2a = 1.0925484305920792f;   // sqrt(15/(4 pi))
+constexpr float kY2b = 0.31539156525252005f;  // sqrt(5/(16 pi))
+constexpr float kY2c = 0.54627421529603959f;  // sqrt(15/(16 pi))
+constexpr float kY3a = 0.59004358992664352f;  // sqrt(35/(32 pi))
+constexpr float kY3b = 2.8906114426405538f;   // sqrt(105/(4 pi))
+constexpr float kY3c = 0.45704579946446572f;  // sqrt(21/(32 pi))
+constexpr float kY3d = 0.3731763325901154f;   // sqrt(7/(16 pi))
+constexpr float kY3e = 1.4453057213202769f;   // sqrt(105/(16 pi))
+
+template <int D>
+__device__ __forceinline__ void sh_basis(float x, float y, float z, float* Y) {
+    Y[0] = kY0;
+    if (D >= 1) {
+        Y[1] = -kY1 * y;
+        Y[2] = kY1 * z;
+        Y[3] = -kY1 * x;
+    }
+    if (D >= 2) {
+        const float xx = x * x, yy = y * y, zz = z * z;
+        Y[4] = kY2a * x * y;
+        Y[5] = -kY2a * y * z;
+        Y[6] = kY2b * (2.f * zz - xx - yy);
+        Y[7] = -kY2a * x * z;
+        Y[8] = kY2c * (xx - yy);
+        if (D >= 3) {
+            Y[9] = -kY3a * y * (3.f * xx - yy);
+            Y[10] = kY3b * x * y * z;
+            Y[11] = -kY3c * y * (4.f * zz - xx - yy);
+            Y[12] = kY3d * z * (2.f * zz - 3.f * xx - 3.f * yy);
+            Y[13] = -kY3c * x * (4.f * zz - xx - yy);
+            Y[14] = kY3e * z * (xx - yy);
+            Y[15] = -kY3a * x * (xx - 3.f * yy);
+        }
+    }
+}
+
+// sum_k w_k * grad Y_k at (x, y, z) (gradient of the polynomial forms above).
+template <int D>
+__device__ __forceinline__ float3 sh_basis_vjp(float x, float y, float z, const float* w) {
+    float gx = 0.f, gy = 0.f, gz = 0.f;
+    if (D >= 1) {
+        gy += -kY1 * w[1];
+        gz += kY1 * w[2];
+        gx += -kY1 * w[3];
+    }
+    if (D >= 2) {
+        const float xx = x * x, yy = y * y, zz = z * z;
+        gx += kY2a * y * w[4];                 gy += kY2a * x * w[4];
+        gy += -kY2a * z * w[5];                gz += -kY2a * y * w[5];
+        gx += -2.f * kY2b * x * w[6];          gy += -2.f * kY2b * y * w[6];     gz += 4.f * kY2b * z * w[6];
+        gx += -kY2a * z * w[7];                gz += -kY2a * x * w[7];
+        gx += 2.f * kY2c * x * w[8];           gy += -2.f * kY2c * y * w[8];
+        if (D >= 3) {
+            gx += -kY3a * 6.f * x * y * w[9];
+            gy += -kY3a * 3.f * (xx - yy) * w[9];
+            gx += kY3b * y * z * w[10];  gy += kY3b * x * z * w[10];  gz += kY3b * x * y * w[10];
+            gx += kY3c * 2.f * x * y * w[11];
+            gy += -kY3c * (4.f * zz - xx - 3.f * yy) * w[11];
+            gz += -kY3c * 8.f * y * z * w[11];
+            gx += -kY3d * 6.f * x * z * w[12];
+            gy += -kY3d * 6.f * y * z * w[12];
+            gz += kY3d * (6.f * zz - 3.f * xx - 3.f * yy) * w[12];
+            gx += -kY3c * (4.f * zz - 3.f * xx - yy) * w[13];
+            gy += kY3c * 2.f * x * y * w[13];
+            gz += -kY3c * 8.f * x * z * w[13];
+            gx += 2.f * kY3e * x * z * w[14];  gy += -2.f * kY3e * y * z * w[14];  gz += kY3e * (xx - yy) * w[14];
+            gx += -kY3a * 3.f * (xx - yy) * w[15];
+            gy += kY3a * 6.f * x * y * w[15];
+        }
+    }
+    return make_float3(gx, gy, gz);
+}
+
+struct Cam {
+    float R[9], t[3], fx, fy, cx, cy, near;
+    int W, H;
+};
+
+__device__ __forceinline__ Cam load_cam(const gs_camera* __restrict__ c) {
+    Cam k;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) k.R[i] = __ldg(&c->R[i]);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) k.t[i] = __ldg(&c->t[i]);
+    k.fx = __ldg(&c->fx); k.fy = __ldg(&c->fy); k.cx = __ldg(&c->cx); k.cy = __ldg(&c->cy);
+    k.near = __ldg(&c->near_plane);
+    k.W = __ldg(&c->width); k.H = __ldg(&c->height);
+    return k;
+}
+
+struct Gauss {
+    float3 mu;
+    float logit, opac;
+    float3 s;        // exp(log-scale)
+    float q[4];      // normalised quaternion
+    float qn;        // |q|
+    float Rq[9];
+    float S[6];      // Sigma: 00 01 02 11 12 22
+};
+
+__device__ __forceinline__ void load_gauss(const float4* __restrict__ P, int64_t n, int64_t g, Gauss& G) {
+    const float4 p0 = P[g], p1 = P[n + g], p2 = P[2 * n + g];
+    G.mu = make_float3(p0.x, p0.y, p0.z);
+    G.logit = p0.w;
+    G.opac = 1.f / (1.f + expf(-p0.w));
+    G.s = make_float3(expf(p1.x), expf(p1.y), expf(p1.z));
+    G.qn = sqrtf(p2.x * p2.x + p2.y * p2.y + p2.z * p2.z + p2.w * p2.w);
+    const float w = p2.x / G.qn, x = p2.y / G.qn, y = p2.z / G.qn, z = p2.w / G.qn;
+    G.q[0] = w; G.q[1] = x; G.q[2] = y; G.q[3] = z;
+    float* R = G.Rq;
+    R[0] = 1.f - 2.f * (y * y + z * z); R[1] = 2.f * (x * y - w * z);       R[2] = 2.f * (x * z + w * y);
+    R[3] = 2.f * (x * y + w * z);       R[4] = 1.f - 2.f * (x * x + z * z); R[5] = 2.f * (y * z - w * x);
+    R[6] = 2.f * (x * z - w * y);       R[7] = 2.f * (y * z + w * x);       R[8] = 1.f - 2.f * (x * x + y * y);
+    const float s0 = G.s.x * G.s.x, s1 = G.s.y * G.s.y, s2 = G.s.z * G.s.z;
+    // Sigma = R diag(s^2) R^T
+    G.S[0] = R[0] * R[0] * s0 + R[1] * R[1] * s1 + R[2] * R[2] * s2;
+    G.S[1] = R[0] * R[3] * s0 + R[1] * R[4] * s1 + R[2] * R[5] * s2;
+    G.S[2] = R[0] * R[6] * s0 + R[1] * R[7] * s1 + R[2] * R[8] * s2;
+    G.S[3] = R[3] * R[3] * s0 + R[4] * R[4] * s1 + R[5] * R[5] * s2;
+    G.S[4] = R[3] * R[6] * s0 + R[4] * R[7] * s1 + R[5] * R[8] * s2;
+    G.S[5] = R[6] * R[6] * s0 + R[7] * R[7] * s1 + R[8] * R[8] * s2;
+}
+
+// Geometry of one Gaussian in one view; returns false when culled by the
+// near plane or a non-positive 2D determinant.
+struct ViewGeom {
+    float tx, ty, tz;
+    float xt, yt;        // guard-band clamped t_x, t_y used in J
+    int clx, cly;
+    float limx, limy;
+    float J00, J02, J11, J12;
+    float M0[3], M1[3];  // rows of J W
+    float a, b, c, det;
+    float3 dir;
+    float len;
+};
+
+__device__ __forceinline__ bool view_geom(const Gauss& G, const Cam& C, ViewGeom& V) {
+    const float* W = C.R;
+    V.tx = W[0] * G.mu.x + W[1] * G.mu.y + W[2] * G.mu.z + C.t[0];
+    V.ty = W[3] * G.mu.x + W[4] * G.mu.y + W[5] * G.mu.z + C.t[1];
+    V.tz = W[6] * G.mu.x + W[7] * G.mu.y + W[8] * G.mu.z + C.t[2];
+    if (!(V.tz > C.near)) return false;
+    V.limx = kGuard * ((float)C.W / (2.f * C.fx));
+    V.limy = kGuard * ((float)C.H / (2.f * C.fy));
+    const float rx = V.tx / V.tz, ry = V.ty / V.tz;
+    V.clx = rx < -V.limx ? -1 : (rx > V.limx ? 1 : 0);
+    V.cly = ry < -V.limy ? -1 : (ry > V.limy ? 1 : 0);
+    V.xt = fminf(fmaxf(rx, -V.limx), V.limx) * V.tz;
+    V.yt = fminf(fmaxf(ry, -V.limy), V.limy) * V.tz;
+    const float iz = 1.f / V.tz, iz2 = iz * iz;
+    V.J00 = C.fx * iz;
+    V.J02 = -C.fx * V.xt * iz2;
+    V.J11 = C.fy * iz;
+    V.J12 = -C.fy * V.yt * iz2;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        V.M0[i] = V.J00 * W[i] + V.J02 * W[6 + i];
+        V.M1[i] = V.J11 * W[3 + i] + V.J12 * W[6 + i];
+    }
+    const float* S = G.S;
+    const float SM0x = S[0] * V.M0[0] + S[1] * V.M0[1] + S[2] * V.M0[2];
+    const float SM0y = S[1] * V.M0[0] + S[3] * V.M0[1] + S[4] * V.M0[2];
+    const float SM0z = S[2] * V.M0[0] + S[4] * V.M0[1] + S[5] * V.M0[2];
+    const float SM1x = S[0] * V.M1[0] + S[1] * V.M1[1] + S[2] * V.M1[2];
+    const float SM1y = S[1] * V.M1[0] + S[3] * V.M1[1] + S[4] * V.M1[2];
+    const float SM1z = S[2] * V.M1[0] + S[4] * V.M1[1] + S[5] * V.M1[2];
+    V.a = V.M0[0] * SM0x + V.M0[1] * SM0y + V.M0[2] * SM0z + kDilation;
+    V.b = V.M0[0] * SM1x + V.M0[1] * SM1y + V.M0[2] * SM1z;
+    V.c = V.M1[0] * SM1x + V.M1[1] * SM1y + V.M1[2] * SM1z + kDilation;
+    V.det = V.a * V.c - V.b * V.b;
+    if (!(V.det > 0.f)) return false;
+    // camera centre = -W^T t
+    const float cx = -(W[0] * C.t[0] + W[3] * C.t[1] + W[6] * C.t[2]);
+    const float cy = -(W[1] * C.t[0] + W[4] * C.t[1] + W[7] * C.t[2]);
+    const float cz = -(W[2] * C.t[0] + W[5] * C.t[1] + W[8] * C.t[2]);
+    const float dx = G.mu.x - cx, dy = G.mu.y - cy, dz = G.mu.z - cz;
+    V.len = sqrtf(dx * dx + dy * dy + dz * dz);
+    V.dir = make_float3(dx / V.len, dy / V.len, dz / V.len);
+    return true;
+}
+
+// Tile rectangle of the square of half-side r around (u, v).  The clamp is
+// applied in float before the conversion so that huge coordinates stay safe.
+__device__ __forceinline__ void tile_rect(float u, float v, float r, int TX, int TY, int tile,
+                                          int& x0, int& y0, int& x1, int& y1) {
+    const float ft = (float)tile;
+    x0 = (int)fminf(fmaxf(floorf((u - r) / ft), 0.f), (float)TX);
+    y0 = (int)fminf(fmaxf(floorf((v - r) / ft), 0.f), (float)TY);
+    x1 = (int)fminf(fmaxf(floorf((u + r + ft - 1.f) / ft), 0.f), (float)TX);
+    y1 = (int)fminf(fmaxf(floorf((v + r + ft - 1.f) / ft), 0.f), (float)TY);
+}
+
+template <int D>
+__global__ void __launch_bounds__(256)
+k_project(const float4* __restrict__ P, int64_t n, const gs_camera* __restrict__ cams,
+          const ViewInfo* __restrict__ vt, int V, int tile, float4* __restrict__ proj,
+          uint32_t* __restrict__ dkeys, uint32_t* __restrict__ dvals) {
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= n) return;
+    constexpr int NB = (D + 1) * (D + 1);
+    constexpr int NPL = (3 * NB + 3) / 4;
+    Gauss G;
+    load_gauss(P, n, g, G);
+    float sh[NPL * 4];
+#pragma unroll
+    for (int pl = 0; pl < NPL; ++pl) {
+        const float4 c = P[(3 + pl) * n + g];
+        sh[4 * pl] = c.x; sh[4 * pl + 1] = c.y; sh[4 * pl + 2] = c.z; sh[4 * pl + 3] = c.w;
+    }
+    for (int v = 0; v < V; ++v) {
+        const Cam C = load_cam(cams + v);
+        const int64_t rec = (int64_t)v * n + g;
+        float4* out = proj + rec * 4;
+        ViewGeom Vg;
+        bool ok = view_geom(G, C, Vg);
+        float u = 0.f, vv = 0.f, r = 0.f;
+        int x0 = 0, y0 = 0, x1 = 0, y1 = 0;
+        if (ok) {
+            const float mid = 0.5f * (Vg.a + Vg.c);
+            const float lam = mid + sqrtf(fmaxf(0.1f, mid * mid - Vg.det));
+            r = ceilf(3.f * sqrtf(lam));
+            u = C.fx * Vg.tx / Vg.tz + C.cx;
+            vv = C.fy * Vg.ty / Vg.tz + C.cy;
+            const ViewInfo vi = vt[v];
+            tile_rect(u, vv, r, vi.tx, vi.ty, tile, x0, y0, x1, y1);
+            ok = (x1 - x0) * (y1 - y0) > 0;
+        }
+        if (!ok) {
+            const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+            out[0] = z; out[1] = z; out[2] = z; out[3] = z;
+            if (dkeys) {
+                dkeys[rec] = 0xFFFFFFFFu;
+                dvals[rec] = (uint32_t)rec;
+            }
+            continue;
+        }
+        float Y[16];
+        sh_basis<D>(Vg.dir.x, Vg.dir.y, Vg.dir.z, Y);
+        float rgb[3];
+        uint32_t mask = 0;
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) {
+            float acc = 0.f;
+#pragma unroll
+            for (int k = 0; k < NB; ++k) acc += sh[3 * k + ch] * Y[k];
+            acc += 0.5f;
+            if (acc < 0.f) { acc = 0.f; mask |= 1u << ch; }
+            rgb[ch] = acc;
+        }
+        const float idet = 1.f / Vg.det;
+        out[0] = make_float4(u, vv, Vg.tz, G.opac);
+        out[1] = make_float4(Vg.c * idet, -Vg.b * idet, Vg.a * idet, r);
+        out[2] = make_float4(rgb[0], rgb[1], rgb[2], __uint_as_float(mask));
+        const uint32_t lo = (uint32_t)x0 | ((uint32_t)y0 << 16), hi = (uint32_t)x1 | ((uint32_t)y1 << 16);
+        out[3] = make_float4(__uint_as_float(lo), __uint_as_float(hi),
+                             __uint_as_float((uint32_t)((x1 - x0) * (y1 - y0))), 0.f);
+        if (dkeys) {
+            dkeys[rec] = __float_as_uint(Vg.tz);
+            dvals[rec] = (uint32_t)rec;
+        }
+    }
+}
+
+// ------------------------------------------------------------------ adjoint
+template <int D>
+__global__ void __launch_bounds__(128)
+k_project_bwd(const float4* __restrict__ P, int64_t n, const gs_camera* __restrict__ cams, int V,
+              const float4* __restrict__ proj, const float4* __restrict__ g2d,
+              float4* __restrict__ dP, int accumulate) {
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= n) return;
+    constexpr int NB = (D + 1) * (D + 1);
+    constexpr int NPL = (3 * NB + 3) / 4;
+    Gauss G;
+    load_gauss(P, n, g, G);
+    float sh[NPL * 4], dsh[NPL * 4];
+#pragma unroll
+    for (int pl = 0; pl < NPL; ++pl) {
+        const float4 c = P[(3 + pl) * n + g];
+        sh[4 * pl] = c.x; sh[4 * pl + 1] = c.y; sh[4 * pl + 2] = c.z; sh[4 * pl + 3] = c.w;
+        dsh[4 * pl] = dsh[4 * pl + 1] = dsh[4 * pl + 2] = dsh[4 * pl + 3] = 0.f;
+    }
+    float dmx = 0.f, dmy = 0.f, dmz = 0.f, dlogit = 0.f;
+    float D00 = 0.f, D01 = 0.f, D02 = 0.f, D11 = 0.f, D12 = 0.f, D22 = 0.f;  // dSigma + dSigma^T
+    for (int v = 0; v < V; ++v) {
+        const int64_t rec = (int64_t)v * n + g;
+        const float4 pr3 = proj[rec * 4 + 3];
+        if (__float_as_uint(pr3.z) == 0u) continue;  // culled in this view
+        const float4 ga = g2d[rec * 3], gb = g2d[rec * 3 + 1], gc = g2d[rec * 3 + 2];
+        const uint32_t mask = __float_as_uint(proj[rec * 4 + 2].w);
+        const Cam C = load_cam(cams + v);
+        ViewGeom Vg;
+        if (!view_geom(G, C, Vg)) continue;
+        const float gu = ga.x, gv = ga.y, gA = ga.z, gB = ga.w, gC = gb.x, go = gb.y;
+        const float grgb[3] = {gb.z, gb.w, gc.x};
+        // opacity = sigmoid(logit)
+        dlogit += go * G.opac * (1.f - G.opac);
+        // colour -> SH coefficients and view direction
+        float Y[16];
+        sh_basis<D>(Vg.dir.x, Vg.dir.y, Vg.dir.z, Y);
+        float wsum[16];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) wsum[k] = 0.f;
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) {
+            if (mask & (1u << ch)) continue;
+#pragma unroll
+            for (int k = 0; k < NB; ++k) {
+                dsh[3 * k + ch] += grgb[ch] * Y[k];
+                wsum[k] += grgb[ch] * sh[3 * k + ch];
+            }
+        }
+        const float3 ddir = sh_basis_vjp<D>(Vg.dir.x, Vg.dir.y, Vg.dir.z, wsum);
+        const float dd = Vg.dir.x * ddir.x + Vg.dir.y * ddir.y + Vg.dir.z * ddir.z;
+        const float il = 1.f / Vg.len;
+        dmx += (ddir.x - Vg.dir.x * dd) * il;
+        dmy += (ddir.y - Vg.dir.y * dd) * il;
+        dmz += (ddir.z - Vg.dir.z * dd) * il;
+        // conic (A, B, C) = (c, -b, a) / det
+        const float a = Vg.a, b = Vg.b, c = Vg.c, id = 1.f / Vg.det, id2 = id * id;
+        const float da = gA * (-c * c * id2) + gB * (b * c * id2) + gC * (id - a * c * id2);
+        const float db = gA * (2.f * b * c * id2) + gB * (-id - 2.f * b * b * id2) + gC * (2.f * a * b * id2);
+        const float dc = gA * (id - a * c * id2) + gB * (a * b * id2) + gC * (-a * a * id2);
+        const float* S = G.S;
+        const float* M0 = Vg.M0;
+        const float* M1 = Vg.M1;
+        const float SM0[3] = {S[0] * M0[0] + S[1] * M0[1] + S[2] * M0[2],
+                              S[1] * M0[0] + S[3] * M0[1] + S[4] * M0[2],
+                              S[2] * M0[0] + S[4] * M0[1] + S[5] * M0[2]};
+        const float SM1[3] = {S[0] * M1[0] + S[1] * M1[1] + S[2] * M1[2],
+                              S[1] * M1[0] + S[3] * M1[1] + S[4] * M1[2],
+                              S[2] * M1[0] + S[4] * M1[1] + S[5] * M1[2]};
+        float dM0[3], dM1[3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            dM0[i] = 2.f * da * SM0[i] + db * SM1[i];
+            dM1[i] = 2.f * dc * SM1[i] + db * SM0[i];
+        }
+        D00 += 2.f * (da * M0[0] * M0[0] + db * M0[0] * M1[0] + dc * M1[0] * M1[0]);
+        D11 += 2.f * (da * M0[1] * M0[1] + db * M0[1] * M1[1] + dc * M1[1] * M1[1]);
+        D22 += 2.f * (da * M0[2] * M0[2] + db * M0[2] * M1[2] + dc * M1[2] * M1[2]);
+        D01 += 2.f * da * M0[0] * M0[1] + db * (M0[0] * M1[1] + M1[0] * M0[1]) + 2.f * dc * M1[0] * M1[1];
+        D02 += 2.f * da * M0[0] * M0[2] + db * (M0[0] * M1[2] + M1[0] * M0[2]) + 2.f * dc * M1[0] * M1[2];
+        D12 += 2.f * da * M0[1] * M0[2] + db * (M0[1] * M1[2] + M1[1] * M0[2]) + 2.f * dc * M1[1] * M1[2];
+        // M0 = J00 W0 + J02 W2, M1 = J11 W1 + J12 W2
+        const float* W = C.R;
+        const float dJ00 = dM0[0] * W[0] + dM0[1] * W[1] + dM0[2] * W[2];
+        const float dJ02 = dM0[0] * W[6] + dM0[1] * W[7] + dM0[2] * W[8];
+        const float dJ11 = dM1[0] * W[3] + dM1[1] * W[4] + dM1[2] * W[5];
+        const float dJ12 = dM1[0] * W[6] + dM1[1] * W[7] + dM1[2] * W[8];
+        const float tz = Vg.tz, iz = 1.f / tz, iz2 = iz * iz, iz3 = iz2 * iz;
+        float dtx = 0.f, dty = 0.f, dtz = 0.f;
+        dtz += -dJ00 * C.fx * iz2 - dJ11 * C.fy * iz2;
+        dtz += dJ02 * 2.f * C.fx * Vg.xt * iz3 + dJ12 * 2.f * C.fy * Vg.yt * iz3;
+        const float dxt = -dJ02 * C.fx * iz2, dyt = -dJ12 * C.fy * iz2;
+        if (Vg.clx == 0) dtx += dxt; else dtz += dxt * (Vg.clx * Vg.limx);
+        if (Vg.cly == 0) dty += dyt; else dtz += dyt * (Vg.cly * Vg.limy);
+        // u = fx tx / tz + cx, v = fy ty / tz + cy
+        dtx += gu * C.fx * iz;
+        dty += gv * C.fy * iz;
+        dtz += -(gu * C.fx * Vg.tx + gv * C.fy * Vg.ty) * iz2;
+        // t = W mu + t_cam
+        dmx += W[0] * dtx + W[3] * dty + W[6] * dtz;
+        dmy += W[1] * dtx + W[4] * dty + W[7] * dtz;
+        dmz += W[2] * dtx + W[5] * dty + W[8] * dtz;
+    }
+    // Sigma = R diag(s^2) R^T:  dR = (dS + dS^T) R diag(s^2),  ds_k = s_k (R^T (dS + dS^T) R)_kk
+    const float* R = G.Rq;
+    const float s2[3] = {G.s.x * G.s.x, G.s.y * G.s.y, G.s.z * G.s.z};
+    const float Dm[9] = {D00, D01, D02, D01, D11, D12, D02, D12, D22};
+    float DR[9];  // Dm R
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+            DR[i * 3 + j] = Dm[i * 3] * R[j] + Dm[i * 3 + 1] * R[3 + j] + Dm[i * 3 + 2] * R[6 + j];
+    float dR[9];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) dR[i * 3 + j] = DR[i * 3 + j] * s2[j];
+    float ds[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) ds[k] = R[k] * DR[k] + R[3 + k] * DR[3 + k] + R[6 + k] * DR[6 + k];
+    // ds above is (R^T Dm R)_kk; d(log s_k) = s_k^2 (R^T Dm R)_kk
+    const float w = G.q[0], x = G.q[1], y = G.q[2], z = G.q[3];
+    float dq[4];
+    dq[0] = dR[1] * (-2.f * z) + dR[2] * (2.f * y) + dR[3] * (2.f * z) + dR[5] * (-2.f * x) + dR[6] * (-2.f * y) + dR[7] * (2.f * x);
+    dq[1] = dR[1] * (2.f * y) + dR[2] * (2.f * z) + dR[3] * (2.f * y) + dR[4] * (-4.f * x) + dR[5] * (-2.f * w) + dR[6] * (2.f * z) + dR[7] * (2.f * w) + dR[8] * (-4.f * x);
+    dq[2] = dR[0] * (-4.f * y) + dR[1] * (2.f * x) + dR[2] * (2.f * w) + dR[3] * (2.f * x) + dR[5] * (2.f * z) + dR[6] * (-2.f * w) + dR[7] * (2.f * z) + dR[8] * (-4.f * y);
+    dq[3] = dR[0] * (-4.f * z) + dR[1] * (-2.f * w) + dR[2] * (2.f * x) + dR[3] * (2.f * w) + dR[4] * (-4.f * z) + dR[5] * (2.f * y) + dR[6] * (2.f * x) + dR[7] * (2.f * y);
+    const float qd = w * dq[0] + x * dq[1] + y * dq[2] + z * dq[3];
+    const float iqn = 1.f / G.qn;
+    float4 o0 = make_float4(dmx, dmy, dmz, dlogit);
+    float4 o1 = make_float4(ds[0] * s2[0], ds[1] * s2[1], ds[2] * s2[2], 0.f);
+    float4 o2 = make_float4((dq[0] - w * qd) * iqn, (dq[1] - x * qd) * iqn, (dq[2] - y * qd) * iqn,
+                            (dq[3] - z * qd) * iqn);
+    if (accumulate) {
+        float4 p;
+        p = dP[g]; o0.x += p.x; o0.y += p.y; o0.z += p.z; o0.w += p.w;
+        p = dP[n + g]; o1.x += p.x; o1.y += p.y; o1.z += p.z; o1.w += p.w;
+        p = dP[2 * n + g]; o2.x += p.x; o2.y += p.y; o2.z += p.z; o2.w += p.w;
+    }
+    dP[g] = o0;
+    dP[n + g] = o1;
+    dP[2 * n + g] = o2;
+#pragma unroll
+    for (int pl = 0; pl < 12; ++pl) {
+        float4 o = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (pl < NPL) {
+            o = make_float4(dsh[4 * pl], dsh[4 * pl + 1], dsh[4 * pl + 2], dsh[4 * pl + 3]);
+            // lanes beyond the 3*NB used coefficients carry no gradient
+            if (4 * pl + 0 >= 3 * NB) o.x = 0.f;
+            if (4 * pl + 1 >= 3 * NB) o.y = 0.f;
+            if (4 * pl + 2 >= 3 * NB) o.z = 0.f;
+            if (4 * pl + 3 >= 3 * NB) o.w = 0.f;
+        }
+        if (accumulate) {
+            const float4 p = dP[(3 + pl) * n + g];
+            o.x += p.x; o.y += p.y; o.z += p.z; o.w += p.w;
+        }
+        dP[(3 + pl) * n + g] = o;
+    }
+}
+
+__global__ void k_view_table(const gs_camera* __restrict__ cams, int V, int tile, ViewInfo* vt,
+                             long long expect_tiles, DevStatus* status) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    int64_t toff = 0, poff = 0;
+    for (int v = 0; v < V; ++v) {
+        ViewInfo vi;
+        vi.width = cams[v].width;
+        vi.height = cams[v].height;
+        vi.tx = (vi.width + tile - 1) / tile;
+        vi.ty = (vi.height + tile - 1) / tile;
+        vi.tile_off = toff;
+        vi.pix_off = poff;
+        vt[v] = vi;
+        toff += (int64_t)vi.tx * vi.ty;
+        poff += (int64_t)vi.width * vi.height;
+    }
+    ViewInfo tot;
+    tot.tx = tot.ty = tot.width = tot.height = 0;
+    tot.tile_off = toff;
+    tot.pix_off = poff;
+    vt[V] = tot;
+    if (expect_tiles >= 0 && toff != expect_tiles) record_status(status, GS_ERR_ARG, toff);
+}
+
+}  // namespace
+
+void launch_view_table(const gs_camera* d_cams, int V, int tile, ViewInfo* vt, long long expect_tiles,
+                       DevStatus* status, cudaStream_t st) {
+    k_view_table<<<1, 32, 0, st>>>(d_cams, V, tile, vt, expect_tiles, status);
+}
+
+void launch_project(const float* params, int64_t n, int sh_degree, const gs_camera* d_cams,
+                    const ViewInfo* vt, int V, int tile, float* proj, uint32_t* depth_keys,
+                    uint32_t* depth_vals, cudaStream_t st) {
+    if (n <= 0) return;
+    const int threads = 256;
+    const unsigned blocks = (unsigned)((n + threads - 1) / threads);
+    const float4* P = reinterpret_cast<const float4*>(params);
+    float4* out = reinterpret_cast<float4*>(proj);
+    switch (sh_degree) {
+        case 0: k_project<0><<<blocks, threads, 0, st>>>(P, n, d_cams, vt, V, tile, out, depth_keys, depth_vals); break;
+        case 1: k_project<1><<<blocks, threads, 0, st>>>(P, n, d_cams, vt, V, tile, out, depth_keys, depth_vals); break;
+        case 2: k_project<2><<<blocks, threads, 0, st>>>(P, n, d_cams, vt, V, tile, out, depth_keys, depth_vals); break;
+        default: k_project<3><<<blocks, threads, 0, st>>>(P, n, d_cams, vt, V, tile, out, depth_keys, depth_vals); break;
+    }
+}
+
+void launch_project_bwd(const float* params, int64_t n, int sh_degree, const gs_camera* d_cams, int V,
+                        const float* proj, const float* grad2d, float* dparams, int accumulate,
+                        cudaStream_t st) {
+    if (n <= 0) return;
+    const int threads = 128;
+    const unsigned blocks = (unsigned)((n + threads - 1) / threads);
+    const float4* P = reinterpret_cast<const float4*>(params);
+    const float4* pr = reinterpret_cast<const float4*>(proj);
+    const float4* g2 = reinterpret_cast<const float4*>(grad2d);
+    float4* dP = reinterpret_cast<float4*>(dparams);
+    switch (sh_degree) {
+        case 0: k_project_bwd<0><<<blocks, threads, 0, st>>>(P, n, d_cams, V, pr, g2, dP, accumulate); break;
+        case 1: k_project_bwd<1><<<blocks, threads, 0, st>>>(P, n, d_cams, V, pr, g2, dP, accumulate); break;
+        case 2: k_project_bwd<2><<<blocks, threads, 0, st>>>(P, n, d_cams, V, pr, g2, dP, accumulate); break;
+        default: k_project_bwd<3><<<blocks, threads, 0, st>>>(P, n, d_cams, V, pr, g2, dP, accumulate); break;
+    }
+}
+
+}  // namespace gs
