@@ -1,0 +1,443 @@
+"""Benchmark of the online 3DGS optimisation step (and the oracle reference arm).
+
+Workload (default): 1M Gaussians, SH degree 3, a batch of 8 reference views
+of 1280x720 on a ring of radius 3, L1 + 0.2 D-SSIM, Adam (lr 1e-3), delta
+extraction (threshold 1e-3) every step, targets drifting by 1e-3 per
+parameter per step.  One step = one graph launch of the whole batched step.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  Multi-GPU runs are independent replicas
+(one model per GPU, no collective on the data path); the timing is the max
+over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import gs_inputs as gi  # noqa: E402
+
+METRIC = "train steps/s (1M Gaussians, 8×720p views, fwd+bwd+Adam); client render p99 ms"
+WORKLOADS = {
+    # name: (n, sh, views, width, height)
+    "c3_1M_8x720p": (1_000_000, 3, 8, 1280, 720),
+    "c2_100k_4x512": (100_000, 3, 4, 512, 512),
+    "c1_10k_128": (10_000, 0, 1, 128, 128),
+}
+DEFAULT_WORKLOAD = "c3_1M_8x720p"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+# FP32 operations per unit of work, counted from the kernels' source (FMA = 2).
+RASTER_FWD_FLOP_PER_FRAGMENT = 20     # one (pixel, fragment) evaluation up to the last kept fragment
+RASTER_BWD_FLOP_PER_FRAGMENT = 60     # one (pixel, fragment) adjoint evaluation
+FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12  # SMs x FP32 lanes x FMA x max SM clock
+
+
+def phase_model(n, V, K, total_tiles, npix, sum_nc, n_changed, tile_passes):
+    """Algorithmic bytes (HBM) or FLOPs per launch of each phase."""
+    vn = V * n
+    return {
+        "project": ("hbm", n * 240 + vn * (64 + 8)),
+        "bin_sort": ("hbm", vn * (4 * 16 + 4) + vn * (4 + 16 + 16) + K * 8 + K * (tile_passes * 16 + 4)
+                     + K * 4 + total_tiles * 8),
+        "render_fwd": ("alu", sum_nc * RASTER_FWD_FLOP_PER_FRAGMENT),
+        "loss": ("hbm", 3 * npix * 44),
+        "raster_bwd": ("alu", sum_nc * RASTER_BWD_FLOP_PER_FRAGMENT),
+        "project_bwd": ("hbm", n * 480 + vn * (48 + 32)),
+        "adam": ("hbm", 60 * n * 4 * 7),
+        "delta": ("hbm", n * (480 + 2) + n_changed * (240 + 240 + 128 + 4)),
+    }
+
+
+def gpu_launches_per_step(tile_passes):
+    # view table 1, projection 1, bin/sort (ranges clear, depth count, depth sort 7,
+    # emission 3, tile sort 3 + passes, ranges) 14 + passes, render 1, loss 2,
+    # raster adjoint 1, projection adjoint 1, Adam 2, delta 3
+    return 1 + 1 + (14 + tile_passes) + 1 + 2 + 1 + 1 + 2 + 3
+
+
+_CUDART = None
+
+
+def event_ms(a, b) -> float:
+    """cudaEventElapsedTime on two torch events' handles (graph-recorded
+    events are not known to torch's own bookkeeping)."""
+    import ctypes
+    global _CUDART
+    if _CUDART is None:
+        for name in ("libcudart.so.13", "libcudart.so", "/usr/local/cuda/lib64/libcudart.so"):
+            try:
+                _CUDART = ctypes.CDLL(name)
+                break
+            except OSError:
+                continue
+        _CUDART.cudaEventElapsedTime.argtypes = [ctypes.POINTER(ctypes.c_float), ctypes.c_void_p, ctypes.c_void_p]
+    ms = ctypes.c_float()
+    rc = _CUDART.cudaEventElapsedTime(ctypes.byref(ms), ctypes.c_void_p(a.cuda_event), ctypes.c_void_p(b.cuda_event))
+    if rc != 0:
+        raise RuntimeError(f"cudaEventElapsedTime failed ({rc})")
+    return float(ms.value)
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    def __init__(self, index: int):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        rows = [r.strip().split(",") for r in open(self.f.name) if r.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1])); mx = float(r[2])
+            except (ValueError, IndexError):
+                continue
+            for nm, val in zip(names, r[5:9]):
+                if val.strip().lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- oracle leg
+class OracleSampler:
+    """Times the FP64 oracle on bounded samples of one optimisation step.
+
+    A sample takes one view and one 16-row band of it: projection of every
+    Gaussian for that band's camera, binning, compositing, loss, both
+    adjoints.  The mean band time is scaled by the bands per view and the
+    views per step; Adam is timed on a slice of the parameters and scaled to
+    all of them."""
+
+    def __init__(self, n, sh, V, W, H, seed_offset=0):
+        import oracle as O
+        self.O = O
+        self.n, self.sh, self.V, self.W, self.H = n, sh, V, W, H
+        self.planes = gi.planes_to_rows(gi.make_scene(n, sh, gi.SEED_MODEL + seed_offset)).astype(np.float64)
+        self.target_planes = gi.planes_to_rows(gi.make_scene(n, sh, gi.SEED_TARGET + seed_offset)).astype(np.float64)
+        self.cams = gi.ring_cameras(V, W, H)
+        self.bands = math.ceil(H / 16)
+        self.k = 0
+        self.t_adam = None
+
+    def _band_cam(self, k):
+        v, b = k % self.V, (k * 7) % self.bands
+        cam = gi.subset_cameras(self.cams, [v])
+        cam["height"] = np.array([min(16, self.H - 16 * b)])
+        cam["cy"] = cam["cy"] - 16 * b
+        return cam
+
+    def sample(self) -> float:
+        cam = self._band_cam(self.k)
+        self.k += 1
+        tgt = self.O.forward(self.target_planes, self.sh, cam)["image"]  # the reference view (not timed)
+        t0 = time.perf_counter()
+        self.O.loss_and_grad(self.planes, self.sh, cam, tgt)
+        return time.perf_counter() - t0
+
+    def adam_seconds(self) -> float:
+        if self.t_adam is None:
+            m = min(self.n * 60, 2_000_000)
+            th = np.zeros(m); g = np.random.default_rng(0).normal(size=m)
+            mm = np.zeros(m); vv = np.zeros(m)
+            t0 = time.perf_counter()
+            self.O.adam(th, g, mm, vv, 1e-3, 1)
+            self.t_adam = (time.perf_counter() - t0) * (self.n * 60 / m)
+            self.adam_floats = m
+        return self.t_adam
+
+    def step_seconds(self, band_times) -> float:
+        return float(np.mean(band_times)) * self.bands * self.V + self.adam_seconds()
+
+    def describe(self, samples) -> str:
+        self.adam_seconds()
+        return (f"{samples} samples of one 16-row band of one view (all {self.n} Gaussians projected, binned, "
+                f"composited, loss + both adjoints, FP64), scaled x{self.bands} bands x{self.V} views; "
+                f"Adam on {self.adam_floats} floats scaled to {self.n * 60}")
+
+
+def omp_cores():
+    try:
+        return int(os.environ.get("OMP_NUM_THREADS", "")) or os.cpu_count()
+    except ValueError:
+        return os.cpu_count()
+
+
+def run_reference(args, rank, world):
+    """The oracle as it stands, on the host cores, same metric and workload.
+    Each step is a bounded sample sized so that warmup + steps end within a
+    few minutes; under torchrun only rank 0 runs."""
+    if rank != 0:
+        return
+    n, sh, V, W, H = WORKLOADS[args.workload]
+    smp = OracleSampler(n, sh, V, W, H)
+    one = smp.sample()
+    budget_s = 150.0
+    # one band sample is the smallest unit; when the requested steps do not
+    # all fit in the budget, the steps share the samples that do
+    total = max(1, min(args.steps + args.warmup, int(budget_s / max(one, 1e-3))))
+    warm = min(args.warmup, max(0, total - 1)) if total > args.steps else min(args.warmup, total // 4)
+    for _ in range(warm):
+        smp.sample()
+    times = []
+    t0 = time.perf_counter()
+    for _ in range(max(1, total - warm)):
+        times.append(smp.sample())
+    wall = time.perf_counter() - t0
+    step_s = smp.step_seconds(times)
+    value = 1.0 / step_s
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_s * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "gaussians": n, "sh_degree": sh, "views": V,
+                       "resolution": [W, H]},
+            "cpu_baseline": {"value": value, "unit": "steps/s", "cores": omp_cores(), "kind": "oracle",
+                             "sample": smp.describe(len(times)), "wall_s": wall},
+            "e2e": {"value": value, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- GPU leg
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import paper_2604_02851_b300 as gs
+    from paper_2604_02851_b300.train import OnlineTrainer, estimate_keys
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    n, sh, V, W, H = WORKLOADS[args.workload]
+    # replicas: rank r trains its own seeded model (independent problems)
+    planes = gi.make_scene(n, sh, gi.SEED_MODEL + 1000 * rank)
+    target_planes = gi.make_scene(n, sh, gi.SEED_TARGET + 1000 * rank)
+    signs = gi.drift_signs(n)
+    cams = gi.ring_cameras(V, W, H)
+    params = torch.from_numpy(planes).to(dev)
+    tparams = torch.from_numpy(target_planes).to(dev)
+    drift = torch.from_numpy(signs).to(dev) * 1e-3
+
+    ctx = gs.Context(local_rank, 0, tile=args.tile, sort_bits=args.sort_bits)
+    keys_cap = estimate_keys(ctx, params, sh, cams, slack=1.3)
+    tr = OnlineTrainer(params, sh, cams, keys_cap, ctx=ctx)
+    packed = tr.packed
+    tctx = gs.Context(local_rank, 0, tile=args.tile, sort_bits=args.sort_bits)
+    tkeys = estimate_keys(tctx, tparams, sh, cams, slack=1.3)
+    tctx.reserve(tctx.workspace_size(packed, n, tkeys))
+
+    def next_targets():
+        # the engine side: drift the target model and render its reference views
+        tparams.add_(drift)
+        gs.gs_render_batch(tctx, tparams, sh, tr.d_cams, V, tr.total_tiles, tkeys, tr.npix, image=tr.targets)
+
+    phase_ev = [torch.cuda.Event(enable_timing=True) for _ in range(gs._lib.TRAIN_PHASE_EVENTS)]
+    next_targets()
+    tr.capture(phase_events=phase_ev)
+    for _ in range(args.warmup):
+        next_targets()
+        tr.step()
+    torch.cuda.synchronize()
+    tr.raise_status()
+    tctx.raise_status()
+
+    # ---- timed region: K steps, device time of each step by CUDA events
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    phase_ms = np.zeros(len(phase_ev) - 1)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local_rank)
+    wall0 = time.perf_counter()
+    for k in range(args.steps):
+        next_targets()
+        ev0[k].record()
+        tr.step()
+        ev1[k].record()
+        ev1[k].synchronize()
+        for i in range(len(phase_ev) - 1):
+            phase_ms[i] += event_ms(phase_ev[i], phase_ev[i + 1])
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    clk = clocks.stop()
+    if world > 1:
+        torch.distributed.barrier()
+    step_ms = np.array([a.elapsed_time(b) for a, b in zip(ev0, ev1)])
+    total_ms = float(step_ms.sum())
+    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    total_ms = float(t.item())
+    code, detail = tr.ctx.status()
+    if code != 0:
+        raise RuntimeError(f"device status {code} ({detail}) during the timed region")
+    ms_per_step = total_ms / args.steps
+    value = world * args.steps / (total_ms / 1e3)
+    loss_last = tr.loss()
+    changed = tr.delta_count()
+    phase_avg = {name: float(ms / args.steps) for name, ms in zip(gs._lib.TRAIN_PHASES, phase_ms)}
+
+    # ---- work counts of the current model, for the roofline (outside the timed region)
+    proj = gs.gs_project(ctx, params, sh, tr.d_cams, V)
+    _, vals, ranges, nk = gs.gs_bin_sort(ctx, proj, tr.d_cams, V, n, tr.total_tiles, keys_cap, want_keys=False)
+    _, T, nc = gs.gs_render_fwd(ctx, proj, tr.d_cams, V, n, tr.total_tiles, vals, ranges, tr.npix)
+    torch.cuda.synchronize()
+    K = int(nk.item())
+    sum_nc = int(nc.to(torch.int64).sum().item())
+    del proj, vals, ranges, T, nc
+    tile_passes = math.ceil(math.ceil(math.log2(max(tr.total_tiles, 2))) / args.sort_bits)
+    model = phase_model(n, V, K, tr.total_tiles, tr.npix, sum_nc, changed, tile_passes)
+    hbm_peak, peak_src = _peaks()
+    kernels = {}
+    for name, ms in phase_avg.items():
+        bound, work = model[name]
+        if bound == "hbm":
+            ach = work / (ms / 1e3) / 1e9
+            kernels[name] = {"ms": ms, "bound": "hbm", "achieved": ach, "unit": "GB/s", "peak": hbm_peak,
+                             "frac": ach / hbm_peak, "algorithmic_bytes": work}
+        else:
+            ach = work / (ms / 1e3) / 1e12
+            kernels[name] = {"ms": ms, "bound": "alu", "achieved": ach, "unit": "TFLOP/s",
+                             "peak": FP32_PEAK_TFLOPS, "frac": ach / FP32_PEAK_TFLOPS, "algorithmic_flop": work}
+    dom = max(phase_avg, key=phase_avg.get)
+    dk = kernels[dom]
+    roofline = {"kernel": dom, "bound": dk["bound"], "achieved": dk["achieved"], "peak": dk["peak"],
+                "unit": dk["unit"], "frac": dk["frac"], "traffic": None,
+                "peak_source": peak_src if dk["bound"] == "hbm" else "derived: 148 SMs x 128 FP32 lanes x 2 x 2032 MHz"}
+
+    # ---- end to end through the public API: host targets in, loss + delta out
+    e2e = None
+    if args.e2e_steps > 0:
+        e2e = run_e2e(args, tr, next_targets, world)
+
+    out = None
+    if rank == 0:
+        cpu = None
+        if world == 1 and not args.no_cpu_baseline:
+            smp = OracleSampler(n, sh, V, W, H)
+            times = [smp.sample() for _ in range(args.cpu_samples)]
+            cpu = {"value": 1.0 / smp.step_seconds(times), "unit": "steps/s", "cores": omp_cores(),
+                   "kind": "oracle", "sample": smp.describe(args.cpu_samples)}
+        out = {"metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+               "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+               "config": {"workload": args.workload, "gaussians": n, "sh_degree": sh, "views": V,
+                          "resolution": [W, H], "keys_per_step": K, "keys_cap": keys_cap, "tile": args.tile,
+                          "sort_digit_bits": args.sort_bits, "graph": True,
+                          "l2": "inputs larger than L2 (params 240 MB, keys > 1 GB per step)",
+                          "targets": "re-rendered each step by gs_render_batch outside the step's events",
+                          "parallelism": "replicas" if world > 1 else "single"},
+               "roofline": roofline, "cpu_baseline": cpu, "clocks": clk, "e2e": e2e,
+               "gpu_launches": gpu_launches_per_step(tile_passes) * args.steps,
+               "phases_ms": phase_avg, "kernels": kernels, "loss_last": loss_last, "delta_changed_last": changed,
+               "wall_s_timed_loop": wall}
+        print(json.dumps(out), flush=True)
+    return out
+
+
+def run_e2e(args, tr, next_targets, world):
+    """The same metric through the C ABI with host buffers: each step copies
+    its targets from pinned host memory, runs the step, and reads back the
+    loss, the delta count and the delta records."""
+    import torch
+    host_targets = [torch.empty(tr.targets.numel(), dtype=torch.float32).pin_memory() for _ in range(2)]
+    for h in host_targets:
+        next_targets()
+        h.copy_(tr.targets)
+    host_loss = torch.empty(1, dtype=torch.float32).pin_memory()
+    host_cnt = torch.empty(1, dtype=torch.int32).pin_memory()
+    host_rec = torch.empty(tr.d_records.shape, dtype=torch.uint8).pin_memory()
+    torch.cuda.synchronize()
+    h2d = d2h = 0
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for k in range(args.e2e_steps):
+        tr.targets.copy_(host_targets[k % 2], non_blocking=True)
+        h2d += tr.targets.numel() * 4
+        tr.step()
+        host_loss.copy_(tr.d_loss, non_blocking=True)
+        host_cnt.copy_(tr.d_count, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+        m = int(host_cnt.item())
+        if m:
+            host_rec[:m].copy_(tr.d_records[:m], non_blocking=True)
+        d2h += 8 + m * 128
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    return {"value": world * args.e2e_steps / (ms / 1e3), "unit": "steps/s",
+            "h2d_bytes_per_step": h2d // args.e2e_steps, "d2h_bytes_per_step": d2h // args.e2e_steps,
+            "steps": args.e2e_steps}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=list(WORKLOADS), default=DEFAULT_WORKLOAD)
+    ap.add_argument("--tile", type=int, default=16)
+    ap.add_argument("--sort-bits", type=int, default=8)
+    ap.add_argument("--e2e-steps", type=int, default=30)
+    ap.add_argument("--cpu-samples", type=int, default=12)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        torch.distributed.init_process_group("nccl")
+    run_ours(args, rank, world, local_rank)
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

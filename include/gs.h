@@ -268,11 +268,29 @@ typedef struct gs_train_cfg {
 gs_status_t gs_train_step(gs_ctx* ctx, const gs_camera* d_cams, const gs_train_io* io,
                           const gs_train_cfg* cfg, void* stream);
 
+/* Number of phase boundaries gs_train_step can mark with events: before
+ * projection, after projection, after bin/sort, after compositing, after the
+ * loss, after the raster adjoint, after the projection adjoint, after Adam,
+ * after delta extraction. */
+#define GS_TRAIN_PHASE_EVENTS 9
+
+/* gs_train_step that also records `events` (GS_TRAIN_PHASE_EVENTS cudaEvent_t
+ * handles passed as void*, created by the caller with timing enabled) at the
+ * phase boundaries, so that a caller can time each kernel phase with CUDA
+ * events on the stream the kernels run on.  Under stream capture the records
+ * become external event-record nodes of the graph. */
+gs_status_t gs_train_step_events(gs_ctx* ctx, const gs_camera* d_cams, const gs_train_io* io,
+                                 const gs_train_cfg* cfg, void* const* events, void* stream);
+
 /* Captures gs_train_step into a CUDA graph held by the context (replacing any
  * earlier one) and replays it with gs_graph_launch.  Synchronous capture. */
 gs_status_t gs_train_graph_capture(gs_ctx* ctx, const gs_camera* d_cams,
                                    const gs_train_io* io, const gs_train_cfg* cfg,
                                    void* stream);
+/* As gs_train_graph_capture, with phase events recorded by every replay. */
+gs_status_t gs_train_graph_capture_events(gs_ctx* ctx, const gs_camera* d_cams,
+                                          const gs_train_io* io, const gs_train_cfg* cfg,
+                                          void* const* events, void* stream);
 gs_status_t gs_graph_launch(gs_ctx* ctx, void* stream);
 
 #ifdef __cplusplus

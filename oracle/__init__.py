@@ -67,6 +67,14 @@ def _d(a):
     return np.ascontiguousarray(a, dtype=np.float64)
 
 
+def _rows(x):
+    """Parameters as float64 rows [n][60]; accepts planes [15][n][4] or rows."""
+    x = np.asarray(x)
+    if x.ndim == 2 and x.shape[1] == 60:
+        return _d(x)
+    return _d(planes_to_rows(x))
+
+
 # ------------------------------------------------------------------ layout
 def cams_array(cams: dict) -> np.ndarray:
     """Camera dict (see gs_inputs) -> oracle records [V][20] float64."""
@@ -115,7 +123,7 @@ def rect(u, v, r, width, height, tile=TILE):
 
 def project(planes, sh_degree: int, cams: dict, tile: int = TILE) -> np.ndarray:
     """-> proj [V][n][16] float64 (fields PROJ_FIELDS; zero when culled)."""
-    rows = _d(planes_to_rows(planes))
+    rows = _rows(planes)
     n = rows.shape[0]
     V = len(cams["fx"])
     out = np.zeros((V, n, 16))
@@ -165,7 +173,7 @@ def render_bwd(cams: dict, proj, vals, ranges, dimage, bg=(0.0, 0.0, 0.0), tile:
 
 def project_bwd(planes, sh_degree: int, cams: dict, grad2d, tile: int = TILE) -> np.ndarray:
     """-> parameter gradient as planes [15][n][4] float64."""
-    rows = _d(planes_to_rows(planes))
+    rows = _rows(planes)
     n = rows.shape[0]
     V = len(cams["fx"])
     d = np.zeros((n, 60))

@@ -21,7 +21,8 @@ EXPORTS = (
     "gs_get_status", "gs_workspace_size", "gs_total_tiles", "gs_project", "gs_bin_sort",
     "gs_render_fwd", "gs_loss", "gs_raster_bwd", "gs_project_bwd", "gs_render_bwd",
     "gs_adam_step", "gs_extract_delta", "gs_render_batch", "gs_train_step",
-    "gs_train_graph_capture", "gs_graph_launch",
+    "gs_train_graph_capture", "gs_graph_launch", "gs_train_step_events",
+    "gs_train_graph_capture_events",
 )
 
 
@@ -88,7 +89,11 @@ _SIGS = {
     "gs_train_step": [_P, _P, C.POINTER(gs_train_io), C.POINTER(gs_train_cfg), _P],
     "gs_train_graph_capture": [_P, _P, C.POINTER(gs_train_io), C.POINTER(gs_train_cfg), _P],
     "gs_graph_launch": [_P, _P],
+    "gs_train_step_events": [_P, _P, C.POINTER(gs_train_io), C.POINTER(gs_train_cfg), C.POINTER(_P), _P],
+    "gs_train_graph_capture_events": [_P, _P, C.POINTER(gs_train_io), C.POINTER(gs_train_cfg), C.POINTER(_P), _P],
 }
+TRAIN_PHASE_EVENTS = 9
+TRAIN_PHASES = ("project", "bin_sort", "render_fwd", "loss", "raster_bwd", "project_bwd", "adam", "delta")
 _RESTYPES = {"gs_workspace_size": C.c_size_t, "gs_total_tiles": C.c_int64}
 _SIGS["gs_workspace_size"] = [_P, C.POINTER(gs_camera), _I32, _I64, _I64]
 _SIGS["gs_total_tiles"] = [_P, C.POINTER(gs_camera), _I32]

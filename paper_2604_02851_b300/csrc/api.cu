@@ -347,8 +347,23 @@ gs_status_t gs_render_batch(gs_ctx* ctx, const gs_scene* scene, const gs_camera*
     return launch_check();
 }
 
+static void mark(void* const* events, int i, cudaStream_t st) {
+    if (!events || !events[i]) return;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(st, &cs);
+    if (cs == cudaStreamCaptureStatusActive)
+        cudaEventRecordWithFlags(static_cast<cudaEvent_t>(events[i]), st, cudaEventRecordExternal);
+    else
+        cudaEventRecord(static_cast<cudaEvent_t>(events[i]), st);
+}
+
 gs_status_t gs_train_step(gs_ctx* ctx, const gs_camera* d_cams, const gs_train_io* io, const gs_train_cfg* cfg,
                           void* stream) {
+    return gs_train_step_events(ctx, d_cams, io, cfg, nullptr, stream);
+}
+
+gs_status_t gs_train_step_events(gs_ctx* ctx, const gs_camera* d_cams, const gs_train_io* io,
+                                 const gs_train_cfg* cfg, void* const* ev, void* stream) {
     if (!ctx || !d_cams || !io || !cfg || bad_views(cfg->n_views) || cfg->n < 0 || cfg->sh_degree < 0 ||
         cfg->sh_degree > 3 || cfg->width < 1 || cfg->height < 1 || cfg->keys_cap < 0 ||
         cfg->keys_cap >= (1LL << 32) || (int64_t)cfg->n_views * cfg->n >= (1LL << 32) || !io->params ||
@@ -368,27 +383,41 @@ gs_status_t gs_train_step(gs_ctx* ctx, const gs_camera* d_cams, const gs_train_i
     SortScratch s;
     carve_sort_scratch(p.sort, V, n, cfg->keys_cap, &s);
     const float3 b = make_float3(cfg->bg[0], cfg->bg[1], cfg->bg[2]);
+    mark(ev, 0, st);
     launch_view_table(d_cams, V, B, p.vt, tt, ctx->d_status, st);
     launch_project(io->params, n, cfg->sh_degree, d_cams, p.vt, V, B, p.proj, s.dkeys[0], s.dvals[0], st);
+    mark(ev, 1, st);
     launch_bin_sort(p.proj, p.vt, V, n, cfg->keys_cap, tt, ctx->sort_bits, s, true, nullptr, p.vals, p.ranges,
                     p.n_keys, ctx->d_status, ctx->sm_count, st);
+    mark(ev, 2, st);
     launch_render_fwd(p.proj, p.vt, V, n, B, p.vals, p.ranges, b, io->image, p.T_final, p.n_contrib, tt, st);
+    mark(ev, 3, st);
     launch_loss(io->image, io->targets, V, cfg->height, cfg->width, cfg->w_l1, cfg->w_ssim, io->d_loss, p.dimage,
                 p.loss, st);
+    mark(ev, 4, st);
     launch_raster_bwd(p.proj, p.vt, V, n, B, p.vals, p.ranges, b, p.T_final, p.n_contrib, p.dimage, p.grad2d, tt,
                       st);
+    mark(ev, 5, st);
     launch_project_bwd(io->params, n, cfg->sh_degree, d_cams, V, p.proj, p.grad2d, io->grads, 0, st);
+    mark(ev, 6, st);
     gs_adam_cfg ac = cfg->adam;
     ac.d_step = io->d_step;
     ac.increment = 1;
     launch_adam(io->params, io->grads, io->adam_m, io->adam_v, n, ac, st);
+    mark(ev, 7, st);
     launch_delta(io->params, io->baseline, n, cfg->delta_thr, io->d_delta_idx, io->d_delta_records,
                  io->d_delta_count, p.delta, st);
+    mark(ev, 8, st);
     return launch_check();
 }
 
 gs_status_t gs_train_graph_capture(gs_ctx* ctx, const gs_camera* d_cams, const gs_train_io* io,
                                    const gs_train_cfg* cfg, void* stream) {
+    return gs_train_graph_capture_events(ctx, d_cams, io, cfg, nullptr, stream);
+}
+
+gs_status_t gs_train_graph_capture_events(gs_ctx* ctx, const gs_camera* d_cams, const gs_train_io* io,
+                                          const gs_train_cfg* cfg, void* const* events, void* stream) {
     if (!ctx) return GS_ERR_ARG;
     DeviceGuard g(ctx->device);
     if (cudaStreamSynchronize(S(stream)) != cudaSuccess) return GS_ERR_CUDA;
@@ -396,7 +425,7 @@ gs_status_t gs_train_graph_capture(gs_ctx* ctx, const gs_camera* d_cams, const g
     if (ctx->graph) { cudaGraphDestroy(ctx->graph); ctx->graph = nullptr; }
     if (cudaStreamBeginCapture(ctx->capture_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
         return GS_ERR_CUDA;
-    const gs_status_t s = gs_train_step(ctx, d_cams, io, cfg, ctx->capture_stream);
+    const gs_status_t s = gs_train_step_events(ctx, d_cams, io, cfg, events, ctx->capture_stream);
     cudaGraph_t graph = nullptr;
     const cudaError_t e = cudaStreamEndCapture(ctx->capture_stream, &graph);
     if (s != GS_OK) {
