@@ -219,6 +219,26 @@ gs_status_t gs_extract_delta(gs_ctx* ctx, const float* theta, float* baseline, i
                              float thr, uint32_t* d_idx, uint8_t* d_records,
                              uint32_t* d_count, void* stream);
 
+/* Largest n accepted by gs_extract_delta_noalloc. */
+#define GS_NOALLOC_MAX_GAUSSIANS 4194304
+
+/* gs_extract_delta for callers that cannot allocate device memory (the paper
+ * has no counterpart; this is a property of the library, not of the method).
+ * A sender on a real-time thread must not call cudaMalloc, which can block on
+ * the device, and a host whose device memory belongs to another allocator may
+ * have no workspace or context to give.  This call takes no context and
+ * allocates nothing: its scratch (about 4.3 MB) is a fixed device array in
+ * the library, held by every GPU that loads it until the process exits.
+ * Same arguments, outputs and results as gs_extract_delta.  n above
+ * GS_NOALLOC_MAX_GAUSSIANS returns GS_ERR_CAPACITY with nothing enqueued.
+ * All calls on a device share the array (its old contents never matter, so
+ * nothing is cleared); calls that overlap on the GPU race and must not be
+ * issued.  The first call on a device looks the array's address up with that
+ * device current; make it outside any stream capture. */
+gs_status_t gs_extract_delta_noalloc(const float* theta, float* baseline, int64_t n, float thr,
+                                     uint32_t* d_idx, uint8_t* d_records, uint32_t* d_count,
+                                     void* stream);
+
 /* --------------------------------------------------------------- serving */
 
 /* Forward-only render of R client viewpoints (any mix of resolutions) of a

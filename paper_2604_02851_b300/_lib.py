@@ -11,6 +11,7 @@ import os
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libgs.so")
 
+NOALLOC_MAX_GAUSSIANS = 4194304  # GS_NOALLOC_MAX_GAUSSIANS in include/gs.h
 GS_OK, GS_ERR_ARG, GS_ERR_CAPACITY, GS_ERR_CUDA, GS_ERR_OOM, GS_ERR_TIMEOUT = range(6)
 STATUS_NAMES = {0: "GS_OK", 1: "GS_ERR_ARG", 2: "GS_ERR_CAPACITY", 3: "GS_ERR_CUDA",
                 4: "GS_ERR_OOM", 5: "GS_ERR_TIMEOUT"}
@@ -22,7 +23,7 @@ EXPORTS = (
     "gs_render_fwd", "gs_loss", "gs_raster_bwd", "gs_project_bwd", "gs_render_bwd",
     "gs_adam_step", "gs_extract_delta", "gs_render_batch", "gs_train_step",
     "gs_train_graph_capture", "gs_graph_launch", "gs_train_step_events",
-    "gs_train_graph_capture_events",
+    "gs_train_graph_capture_events", "gs_extract_delta_noalloc",
 )
 
 
@@ -85,6 +86,7 @@ _SIGS = {
     "gs_render_bwd": [_P, C.POINTER(gs_scene), _P, _I32, _I64, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P],
     "gs_adam_step": [_P, _P, _P, _P, _P, _I64, C.POINTER(gs_adam_cfg), _P],
     "gs_extract_delta": [_P, _P, _P, _I64, _F, _P, _P, _P, _P],
+    "gs_extract_delta_noalloc": [_P, _P, _I64, _F, _P, _P, _P, _P],
     "gs_render_batch": [_P, C.POINTER(gs_scene), _P, _I32, _I64, _I64, _P, _P, _P],
     "gs_train_step": [_P, _P, C.POINTER(gs_train_io), C.POINTER(gs_train_cfg), _P],
     "gs_train_graph_capture": [_P, _P, C.POINTER(gs_train_io), C.POINTER(gs_train_cfg), _P],
