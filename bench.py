@@ -36,6 +36,7 @@ WORKLOADS = {
     "c3_1M_8x720p": (1_000_000, 3, 8, 1280, 720),
     "c2_100k_4x512": (100_000, 3, 4, 512, 512),
     "c1_10k_128": (10_000, 0, 1, 128, 128),
+    "prof_200k_8x720p": (200_000, 3, 8, 1280, 720),
 }
 DEFAULT_WORKLOAD = "c3_1M_8x720p"
 

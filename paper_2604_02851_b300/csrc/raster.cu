@@ -2,20 +2,22 @@
 //
 // Sec. 3.2.3: the model is refined by differentiable rendering as in the
 // cited 3DGS method.  One block owns one B x B pixel tile; its sorted list of
-// Gaussians is streamed through shared memory in batches of B*B records, one
-// record loaded per thread, and every pixel of the tile walks the batch.
+// Gaussians is streamed through shared memory in batches, and every pixel of
+// the tile walks each batch.  A thread owns a strip of B/4 pixels of one row,
+// so a fragment's shared-memory reads and its per-warp gradient reduction
+// serve several pixels.
 //
 // Forward: per pixel, alpha = min(0.99, o e^P) with P the conic quadratic
-// form, skipped when P > 0 or alpha < 1/255; compositing stops before the
-// fragment that would take T below 1e-4.  A block leaves as soon as every
-// pixel is done (block vote), a warp skips batches once all its pixels are.
+// form, skipped when P > 0 or alpha < 1/255 (tested as P < -ln(255 o) before
+// the exponential); compositing stops before the fragment that would take T
+// below 1e-4.  A block leaves as soon as every pixel is done (block vote).
 //
 // Backward: no per-fragment state is stored.  Each pixel starts from its
 // final transmittance and last-contributor position and walks its list
 // backwards, recovering T_j = T_{j+1} / (1 - alpha_j) and the colour behind
 // the fragment by the recursion R_{j-1} = alpha_j c_j + (1 - alpha_j) R_j
-// (R = background behind the last fragment).  Per fragment, the 9 gradient
-// values of the 32 pixels of a warp are summed with shuffles, the warp sums
+// (R = background behind the last fragment).  Per fragment, a thread sums its
+// pixels' 9 gradient values, the warp sums them with shuffles, the warp sums
 // of a batch are added in shared memory, and each batch ends with one set of
 // vector atomics per Gaussian into the per-view 2D gradient record.
 #include "gs_internal.cuh"
@@ -32,70 +34,98 @@ __device__ __forceinline__ int find_view(const ViewInfo* __restrict__ vt, int V,
     return lo;
 }
 
+// Thread layout: a B x B tile is covered by B rows of kTPR threads; each
+// thread owns a strip of PX = B / kTPR adjacent pixels of one row, so the
+// shared-memory reads of a fragment and the warp reductions of its gradient
+// are shared by PX pixels.
+constexpr int kTPR = 4;
+
+// The cut-off alpha < 1/255 is tested in the log domain before the
+// exponential: o e^P < 1/255  <=>  P < -ln(255 o).
+__device__ __forceinline__ float cutoff_log(float o) { return -__logf(255.f * o); }
+
 template <int B>
-__global__ void __launch_bounds__(B * B)
+__global__ void __launch_bounds__(B * kTPR)
 k_render_fwd(const float4* __restrict__ proj, const ViewInfo* __restrict__ vt, int V, int64_t n,
              const uint32_t* __restrict__ vals, const uint2* __restrict__ ranges, float3 bg,
              float* __restrict__ image, float* __restrict__ T_final, uint32_t* __restrict__ n_contrib) {
-    constexpr int NT = B * B;
-    __shared__ float4 s_a[NT];   // u, v, opacity
-    __shared__ float4 s_b[NT];   // conic A, B, C
-    __shared__ float4 s_c[NT];   // r, g, b
+    constexpr int NT = B * kTPR;       // threads per block
+    constexpr int PX = B / kTPR;       // pixels per thread
+    constexpr int BATCH = 2 * NT;      // fragments staged per round
+    __shared__ float4 s_a[BATCH];      // u, v, opacity, log cut-off
+    __shared__ float4 s_b[BATCH];      // conic A, B, C
+    __shared__ float4 s_c[BATCH];      // r, g, b
     const int64_t gt = blockIdx.x;
     if (gt >= vt[V].tile_off) return;
     const int v = find_view(vt, V, gt);
     const ViewInfo vi = vt[v];
     const int lt = (int)(gt - vi.tile_off);
-    const int px = (lt % vi.tx) * B + (int)threadIdx.x % B;
-    const int py = (lt / vi.tx) * B + (int)threadIdx.x / B;
-    const bool inside = px < vi.width && py < vi.height;
-    const float fx = (float)px + 0.5f, fy = (float)py + 0.5f;
+    const int row = (int)threadIdx.x / kTPR;
+    const int px0 = (lt % vi.tx) * B + ((int)threadIdx.x % kTPR) * PX;
+    const int py = (lt / vi.tx) * B + row;
+    const float fy = (float)py + 0.5f;
     const uint2 rg = ranges[gt];
     const int64_t rbase = (int64_t)v * n;
 
-    float T = 1.f, Cr = 0.f, Cg = 0.f, Cb = 0.f;
-    uint32_t last = 0;
-    bool done = !inside;
-    for (uint32_t start = rg.x; start < rg.y; start += NT) {
-        if (__syncthreads_count(done) == NT) break;
-        const uint32_t idx = start + threadIdx.x;
-        if (idx < rg.y) {
-            const int64_t r = (rbase + vals[idx]) * 4;
-            const float4 a = proj[r], b = proj[r + 1], c = proj[r + 2];
-            s_a[threadIdx.x] = make_float4(a.x, a.y, a.w, 0.f);
-            s_b[threadIdx.x] = b;
-            s_c[threadIdx.x] = c;
+    float T[PX], Cr[PX], Cg[PX], Cb[PX];
+    uint32_t last[PX];
+    uint32_t live = 0;  // bit k: pixel k still compositing
+#pragma unroll
+    for (int k = 0; k < PX; ++k) {
+        T[k] = 1.f; Cr[k] = Cg[k] = Cb[k] = 0.f; last[k] = 0;
+        if (px0 + k < vi.width && py < vi.height) live |= 1u << k;
+    }
+    for (uint32_t start = rg.x; start < rg.y; start += BATCH) {
+        if (__syncthreads_count(live != 0) == 0) break;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int slot = threadIdx.x + h * NT;
+            const uint32_t idx = start + slot;
+            if (idx < rg.y) {
+                const int64_t r = (rbase + vals[idx]) * 4;
+                const float4 a = proj[r], b = proj[r + 1], c = proj[r + 2];
+                s_a[slot] = make_float4(a.x, a.y, a.w, cutoff_log(a.w));
+                s_b[slot] = b;
+                s_c[slot] = c;
+            }
         }
         __syncthreads();
-        const int cnt = (int)min((uint32_t)NT, rg.y - start);
-        if (!done) {
-            for (int j = 0; j < cnt; ++j) {
-                const float4 a = s_a[j];
-                const float4 co = s_b[j];
-                const float dx = a.x - fx, dy = a.y - fy;
-                const float P = -0.5f * (co.x * dx * dx + co.z * dy * dy) - co.y * dx * dy;
-                if (P > 0.f) continue;
+        const int cnt = (int)min((uint32_t)BATCH, rg.y - start);
+        for (int j = 0; j < cnt && live; ++j) {
+            const float4 a = s_a[j];
+            const float4 co = s_b[j];
+            const float dy = a.y - fy;
+            const float cyy = -0.5f * co.z * dy * dy;
+            const float by = co.y * dy;
+#pragma unroll
+            for (int k = 0; k < PX; ++k) {
+                if (!(live & (1u << k))) continue;
+                const float dx = a.x - ((float)(px0 + k) + 0.5f);
+                const float P = (-0.5f * co.x * dx - by) * dx + cyy;
+                if (P > 0.f || P < a.w) continue;
                 const float al = fminf(kAlphaMax, a.z * __expf(P));
-                if (al < kAlphaMin) continue;
-                const float Tn = T * (1.f - al);
-                if (Tn < kTMin) { done = true; break; }
+                const float Tn = T[k] * (1.f - al);
+                if (Tn < kTMin) { live &= ~(1u << k); continue; }
                 const float4 c = s_c[j];
-                const float w = al * T;
-                Cr += c.x * w; Cg += c.y * w; Cb += c.z * w;
-                T = Tn;
-                last = start + j - rg.x + 1;
+                const float w = al * T[k];
+                Cr[k] += c.x * w; Cg[k] += c.y * w; Cb[k] += c.z * w;
+                T[k] = Tn;
+                last[k] = start + j - rg.x + 1;
             }
         }
     }
-    if (inside) {
-        const int64_t HW = (int64_t)vi.width * vi.height;
+    const int64_t HW = (int64_t)vi.width * vi.height;
+    float* img = image + 3 * vi.pix_off;
+#pragma unroll
+    for (int k = 0; k < PX; ++k) {
+        const int px = px0 + k;
+        if (px >= vi.width || py >= vi.height) continue;
         const int64_t pix = (int64_t)py * vi.width + px;
-        float* img = image + 3 * vi.pix_off;
-        img[pix] = Cr + T * bg.x;
-        img[HW + pix] = Cg + T * bg.y;
-        img[2 * HW + pix] = Cb + T * bg.z;
-        if (T_final) T_final[vi.pix_off + pix] = T;
-        if (n_contrib) n_contrib[vi.pix_off + pix] = last;
+        img[pix] = Cr[k] + T[k] * bg.x;
+        img[HW + pix] = Cg[k] + T[k] * bg.y;
+        img[2 * HW + pix] = Cb[k] + T[k] * bg.z;
+        if (T_final) T_final[vi.pix_off + pix] = T[k];
+        if (n_contrib) n_contrib[vi.pix_off + pix] = last[k];
     }
 }
 
@@ -106,97 +136,110 @@ __device__ __forceinline__ float warp_sum(float x) {
 }
 
 template <int B>
-__global__ void __launch_bounds__(B * B)
+__global__ void __launch_bounds__(B * kTPR)
 k_raster_bwd(const float4* __restrict__ proj, const ViewInfo* __restrict__ vt, int V, int64_t n,
              const uint32_t* __restrict__ vals, const uint2* __restrict__ ranges, float3 bg,
              const float* __restrict__ T_final, const uint32_t* __restrict__ n_contrib,
              const float* __restrict__ dimage, float* __restrict__ grad2d) {
-    constexpr int NT = B * B;
-    __shared__ float4 s_a[NT];   // u, v, opacity
-    __shared__ float4 s_b[NT];   // conic A, B, C
-    __shared__ float4 s_c[NT];   // r, g, b
-    __shared__ uint32_t s_g[NT];
-    __shared__ float s_acc[9][NT];
+    constexpr int NT = B * kTPR;
+    constexpr int PX = B / kTPR;
+    constexpr int BATCH = NT;
+    __shared__ float4 s_a[BATCH];   // u, v, opacity, log cut-off
+    __shared__ float4 s_b[BATCH];   // conic A, B, C
+    __shared__ float4 s_c[BATCH];   // r, g, b
+    __shared__ uint32_t s_g[BATCH];
+    __shared__ float s_acc[9][BATCH];
     __shared__ uint32_t s_max;
     const int64_t gt = blockIdx.x;
     if (gt >= vt[V].tile_off) return;
     const int v = find_view(vt, V, gt);
     const ViewInfo vi = vt[v];
     const int lt = (int)(gt - vi.tile_off);
-    const int px = (lt % vi.tx) * B + (int)threadIdx.x % B;
-    const int py = (lt / vi.tx) * B + (int)threadIdx.x / B;
-    const bool inside = px < vi.width && py < vi.height;
-    const float fx = (float)px + 0.5f, fy = (float)py + 0.5f;
+    const int row = (int)threadIdx.x / kTPR;
+    const int px0 = (lt % vi.tx) * B + ((int)threadIdx.x % kTPR) * PX;
+    const int py = (lt / vi.tx) * B + row;
+    const float fy = (float)py + 0.5f;
     const uint2 rg = ranges[gt];
     const int64_t rbase = (int64_t)v * n;
     const int lane = threadIdx.x & 31;
 
-    float T = 1.f, dCr = 0.f, dCg = 0.f, dCb = 0.f;
-    uint32_t last = 0;
-    if (inside) {
-        const int64_t HW = (int64_t)vi.width * vi.height;
-        const int64_t pix = (int64_t)py * vi.width + px;
-        T = T_final[vi.pix_off + pix];
-        last = n_contrib[vi.pix_off + pix];
-        const float* dimg = dimage + 3 * vi.pix_off;
-        dCr = dimg[pix]; dCg = dimg[HW + pix]; dCb = dimg[2 * HW + pix];
+    float T[PX], dCr[PX], dCg[PX], dCb[PX], Rr[PX], Rg[PX], Rb[PX];
+    uint32_t last[PX];
+    uint32_t mylast = 0;
+    const int64_t HW = (int64_t)vi.width * vi.height;
+    const float* dimg = dimage + 3 * vi.pix_off;
+#pragma unroll
+    for (int k = 0; k < PX; ++k) {
+        const int px = px0 + k;
+        T[k] = 1.f; dCr[k] = dCg[k] = dCb[k] = 0.f; last[k] = 0;
+        Rr[k] = bg.x; Rg[k] = bg.y; Rb[k] = bg.z;
+        if (px < vi.width && py < vi.height) {
+            const int64_t pix = (int64_t)py * vi.width + px;
+            T[k] = T_final[vi.pix_off + pix];
+            last[k] = n_contrib[vi.pix_off + pix];
+            dCr[k] = dimg[pix]; dCg[k] = dimg[HW + pix]; dCb[k] = dimg[2 * HW + pix];
+            mylast = max(mylast, last[k]);
+        }
     }
-    float Rr = bg.x, Rg = bg.y, Rb = bg.z;  // colour seen behind the current fragment
     if (threadIdx.x == 0) s_max = 0;
     __syncthreads();
-    if (last) atomicMax(&s_max, last);
+    if (mylast) atomicMax(&s_max, mylast);
     __syncthreads();
     const uint32_t maxl = s_max;
 
-    for (int64_t bend = maxl; bend > 0; bend -= NT) {
-        const uint32_t bstart = bend > NT ? (uint32_t)(bend - NT) : 0u;
+    for (int64_t bend = maxl; bend > 0; bend -= BATCH) {
+        const uint32_t bstart = bend > BATCH ? (uint32_t)(bend - BATCH) : 0u;
         const int cnt = (int)(bend - bstart);
         __syncthreads();  // the previous batch's flush is complete
         if ((int)threadIdx.x < cnt) {
             const uint32_t g = vals[rg.x + bstart + threadIdx.x];
             const int64_t r = (rbase + g) * 4;
             const float4 a = proj[r], b = proj[r + 1], c = proj[r + 2];
-            s_a[threadIdx.x] = make_float4(a.x, a.y, a.w, 0.f);
+            s_a[threadIdx.x] = make_float4(a.x, a.y, a.w, cutoff_log(a.w));
             s_b[threadIdx.x] = b;
             s_c[threadIdx.x] = c;
             s_g[threadIdx.x] = g;
 #pragma unroll
-            for (int k = 0; k < 9; ++k) s_acc[k][threadIdx.x] = 0.f;
+            for (int q = 0; q < 9; ++q) s_acc[q][threadIdx.x] = 0.f;
         }
         __syncthreads();
         for (int j = cnt - 1; j >= 0; --j) {
             const uint32_t pos = bstart + (uint32_t)j;
+            if (!__any_sync(0xFFFFFFFFu, pos < mylast)) continue;
+            const float4 a = s_a[j];
+            const float4 co = s_b[j];
+            const float4 c = s_c[j];
+            const float dy = a.y - fy;
+            const float cyy = -0.5f * co.z * dy * dy;
+            const float by = co.y * dy;
             float g0 = 0.f, g1 = 0.f, g2 = 0.f, g3 = 0.f, g4 = 0.f, g5 = 0.f, g6 = 0.f, g7 = 0.f, g8 = 0.f;
             bool contrib = false;
-            if (pos < last) {
-                const float4 a = s_a[j];
-                const float4 co = s_b[j];
-                const float dx = a.x - fx, dy = a.y - fy;
-                const float P = -0.5f * (co.x * dx * dx + co.z * dy * dy) - co.y * dx * dy;
-                if (P <= 0.f) {
-                    const float G = __expf(P);
-                    const float raw = a.z * G;
-                    const float al = fminf(kAlphaMax, raw);
-                    if (al >= kAlphaMin) {
-                        contrib = true;
-                        const float4 c = s_c[j];
-                        T = T / (1.f - al);  // T_j
-                        const float w = al * T;
-                        g6 = w * dCr; g7 = w * dCg; g8 = w * dCb;
-                        const float dal = T * (dCr * (c.x - Rr) + dCg * (c.y - Rg) + dCb * (c.z - Rb));
-                        Rr = al * c.x + (1.f - al) * Rr;
-                        Rg = al * c.y + (1.f - al) * Rg;
-                        Rb = al * c.z + (1.f - al) * Rb;
-                        if (raw <= kAlphaMax) {
-                            const float dP = dal * raw;
-                            g5 = dal * G;
-                            g2 = dP * (-0.5f * dx * dx);
-                            g3 = dP * (-dx * dy);
-                            g4 = dP * (-0.5f * dy * dy);
-                            g0 = dP * (-co.x * dx - co.y * dy);
-                            g1 = dP * (-co.z * dy - co.y * dx);
-                        }
-                    }
+#pragma unroll
+            for (int k = 0; k < PX; ++k) {
+                if (pos >= last[k]) continue;
+                const float dx = a.x - ((float)(px0 + k) + 0.5f);
+                const float P = (-0.5f * co.x * dx - by) * dx + cyy;
+                if (P > 0.f || P < a.w) continue;
+                contrib = true;
+                const float G = __expf(P);
+                const float raw = a.z * G;
+                const float al = fminf(kAlphaMax, raw);
+                const float Tj = T[k] / (1.f - al);
+                T[k] = Tj;
+                const float w = al * Tj;
+                g6 += w * dCr[k]; g7 += w * dCg[k]; g8 += w * dCb[k];
+                const float dal = Tj * (dCr[k] * (c.x - Rr[k]) + dCg[k] * (c.y - Rg[k]) + dCb[k] * (c.z - Rb[k]));
+                Rr[k] += al * (c.x - Rr[k]);
+                Rg[k] += al * (c.y - Rg[k]);
+                Rb[k] += al * (c.z - Rb[k]);
+                if (raw <= kAlphaMax) {
+                    const float dP = dal * raw;
+                    g5 += dal * G;
+                    g2 += dP * (-0.5f * dx * dx);
+                    g3 += dP * (-dx * dy);
+                    g4 += dP * (-0.5f * dy * dy);
+                    g0 += dP * (-co.x * dx - co.y * dy);
+                    g1 += dP * (-co.z * dy - co.y * dx);
                 }
             }
             if (__any_sync(0xFFFFFFFFu, contrib)) {
@@ -204,17 +247,23 @@ k_raster_bwd(const float4* __restrict__ proj, const ViewInfo* __restrict__ vt, i
                 g3 = warp_sum(g3); g4 = warp_sum(g4); g5 = warp_sum(g5);
                 g6 = warp_sum(g6); g7 = warp_sum(g7); g8 = warp_sum(g8);
                 if (lane == 0) {
-                    atomicAdd(&s_acc[0][j], g0); atomicAdd(&s_acc[1][j], g1); atomicAdd(&s_acc[2][j], g2);
-                    atomicAdd(&s_acc[3][j], g3); atomicAdd(&s_acc[4][j], g4); atomicAdd(&s_acc[5][j], g5);
-                    atomicAdd(&s_acc[6][j], g6); atomicAdd(&s_acc[7][j], g7); atomicAdd(&s_acc[8][j], g8);
+                    if (NT == 32) {
+                        s_acc[0][j] += g0; s_acc[1][j] += g1; s_acc[2][j] += g2;
+                        s_acc[3][j] += g3; s_acc[4][j] += g4; s_acc[5][j] += g5;
+                        s_acc[6][j] += g6; s_acc[7][j] += g7; s_acc[8][j] += g8;
+                    } else {
+                        atomicAdd(&s_acc[0][j], g0); atomicAdd(&s_acc[1][j], g1); atomicAdd(&s_acc[2][j], g2);
+                        atomicAdd(&s_acc[3][j], g3); atomicAdd(&s_acc[4][j], g4); atomicAdd(&s_acc[5][j], g5);
+                        atomicAdd(&s_acc[6][j], g6); atomicAdd(&s_acc[7][j], g7); atomicAdd(&s_acc[8][j], g8);
+                    }
                 }
             }
         }
         __syncthreads();
         if ((int)threadIdx.x < cnt) {
             const int t = threadIdx.x;
-            float4 A = make_float4(s_acc[0][t], s_acc[1][t], s_acc[2][t], s_acc[3][t]);
-            float4 Bv = make_float4(s_acc[4][t], s_acc[5][t], s_acc[6][t], s_acc[7][t]);
+            const float4 A = make_float4(s_acc[0][t], s_acc[1][t], s_acc[2][t], s_acc[3][t]);
+            const float4 Bv = make_float4(s_acc[4][t], s_acc[5][t], s_acc[6][t], s_acc[7][t]);
             const float Cv = s_acc[8][t];
             float* dst = grad2d + (rbase + s_g[t]) * kGradStride;
             if (A.x != 0.f || A.y != 0.f || A.z != 0.f || A.w != 0.f)
@@ -235,9 +284,9 @@ void launch_render_fwd(const float* proj, const ViewInfo* vt, int V, int64_t n, 
     const float4* p = reinterpret_cast<const float4*>(proj);
     const uint2* r = reinterpret_cast<const uint2*>(ranges);
     if (tile == 8)
-        k_render_fwd<8><<<(unsigned)total_tiles, 64, 0, st>>>(p, vt, V, n, vals, r, bg, image, T_final, n_contrib);
+        k_render_fwd<8><<<(unsigned)total_tiles, 8 * kTPR, 0, st>>>(p, vt, V, n, vals, r, bg, image, T_final, n_contrib);
     else
-        k_render_fwd<16><<<(unsigned)total_tiles, 256, 0, st>>>(p, vt, V, n, vals, r, bg, image, T_final, n_contrib);
+        k_render_fwd<16><<<(unsigned)total_tiles, 16 * kTPR, 0, st>>>(p, vt, V, n, vals, r, bg, image, T_final, n_contrib);
 }
 
 void launch_raster_bwd(const float* proj, const ViewInfo* vt, int V, int64_t n, int tile,
@@ -249,9 +298,9 @@ void launch_raster_bwd(const float* proj, const ViewInfo* vt, int V, int64_t n, 
     const float4* p = reinterpret_cast<const float4*>(proj);
     const uint2* r = reinterpret_cast<const uint2*>(ranges);
     if (tile == 8)
-        k_raster_bwd<8><<<(unsigned)total_tiles, 64, 0, st>>>(p, vt, V, n, vals, r, bg, T_final, n_contrib, dimage, grad2d);
+        k_raster_bwd<8><<<(unsigned)total_tiles, 8 * kTPR, 0, st>>>(p, vt, V, n, vals, r, bg, T_final, n_contrib, dimage, grad2d);
     else
-        k_raster_bwd<16><<<(unsigned)total_tiles, 256, 0, st>>>(p, vt, V, n, vals, r, bg, T_final, n_contrib, dimage, grad2d);
+        k_raster_bwd<16><<<(unsigned)total_tiles, 16 * kTPR, 0, st>>>(p, vt, V, n, vals, r, bg, T_final, n_contrib, dimage, grad2d);
 }
 
 }  // namespace gs
