@@ -61,7 +61,7 @@ void launch_project_bwd(const float* params, int64_t n, int sh_degree, const gs_
 struct SortScratch {
     uint32_t* dkeys[2];        // depth sort ping-pong, V*n each
     uint32_t* dvals[2];
-    uint32_t* block_sums;      // emission block sums (+1)
+    unsigned long long* emit_lookback;  // emission block look-back (one word per block)
     uint32_t* tkeys[3];        // tile-key input / temporary / default output, keys_cap each
     uint32_t* tvals[2];
     uint32_t* hist;            // [4][256]
@@ -69,6 +69,7 @@ struct SortScratch {
     unsigned long long* lookback;  // [4][max_tiles][256]
     int64_t max_sort_tiles;    // per pass
     uint32_t* d_count_depth;   // V*n as a device scalar
+    size_t bytes;              // total scratch size
 };
 
 size_t sort_scratch_bytes(int V, int64_t n, int64_t keys_cap);

@@ -13,13 +13,23 @@
 // K-sized sort moves 8 bytes per entry per pass over 1-2 passes instead of
 // 12 bytes over 6 passes.
 //
-// The sort is a onesweep radix sort: one histogram pass over the keys for all
-// digit passes, then per digit pass a single kernel that ranks a tile of keys
-// in shared memory (warp match-any ranking, stable), publishes its per-digit
-// counts, resolves its global digit offsets by decoupled look-back over the
-// preceding tiles, and scatters.  Blocks are persistent and take tiles from
-// an atomic counter in launch order, so a waited-on tile always belongs to a
-// running block; every wait is bounded and reports GS_ERR_TIMEOUT.
+// Emission is one pass: each block gathers 1024 depth-ordered Gaussians,
+// finds its output offset by decoupled look-back over the preceding blocks,
+// and expands the Gaussians' tile rectangles warp by warp into consecutive,
+// coalesced (key, value) writes; it also accumulates the digit histograms of
+// the tile-key sort, so that sort needs no counting pass of its own.
+//
+// The sort is a onesweep radix sort: per digit pass a single kernel ranks a
+// tile of keys in shared memory (warp match-any ranking, stable), publishes
+// its per-digit counts, resolves its global digit offsets by decoupled
+// look-back over the preceding tiles, and scatters.  The last pass of the
+// tile-key sort writes the values (and the keys only if asked) and records
+// each tile's [start, end) range with min/max atomics at run boundaries.
+// Blocks take work from atomic counters in launch order, so a waited-on tile
+// always belongs to a running block; every wait is bounded (about 1 s) and
+// reports GS_ERR_TIMEOUT.
+#include <algorithm>
+
 #include "gs_internal.cuh"
 
 namespace gs {
@@ -53,11 +63,42 @@ __device__ __forceinline__ int64_t clamp_count(const uint32_t* d_count, int64_t 
     return k < cap ? k : cap;
 }
 
+// Exclusive prefix of `mine` over the slots 0..slot-1 of a look-back array
+// whose slots hold (flag | count); publishes this slot's inclusive value.
+// Bounded: on time-out records GS_ERR_TIMEOUT and returns false.
+__device__ __forceinline__ bool look_back(unsigned long long* lb, int64_t slot, int stride,
+                                          unsigned long long mine, unsigned long long* excl_out,
+                                          DevStatus* status) {
+    unsigned long long excl = 0;
+    bool ok = true;
+    if (slot > 0) {
+        int64_t p = slot - 1;
+        const long long t0 = clock64();
+        for (;;) {
+            const unsigned long long x = ld_volatile(lb + p * stride);
+            if (x & (kFlagAgg | kFlagInc)) {
+                excl += x & kValMask;
+                if (x & kFlagInc) break;
+                --p;
+                continue;
+            }
+            if (clock64() - t0 > kSpinCycles) {
+                record_status(status, GS_ERR_TIMEOUT, slot);
+                ok = false;
+                break;
+            }
+        }
+        st_volatile(lb + slot * stride, kFlagInc | (excl + mine));
+    }
+    *excl_out = excl;
+    return ok;
+}
+
 // ------------------------------------------------------------ histograms
 template <int BITS>
 __global__ void __launch_bounds__(kThreads)
-k_hist(const uint32_t* __restrict__ keys, const uint32_t* d_count, int64_t cap, int begin_bit,
-       int passes, uint32_t* __restrict__ hist) {
+k_hist(const uint32_t* __restrict__ keys, const uint32_t* d_count, int64_t cap, int passes,
+       uint32_t* __restrict__ hist) {
     constexpr int R = 1 << BITS;
     __shared__ uint32_t sh[kWarps][kMaxPasses][R];
     for (int i = threadIdx.x; i < kWarps * kMaxPasses * R; i += kThreads) (&sh[0][0][0])[i] = 0;
@@ -67,7 +108,7 @@ k_hist(const uint32_t* __restrict__ keys, const uint32_t* d_count, int64_t cap, 
     for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < count;
          i += (int64_t)gridDim.x * kThreads) {
         const uint32_t k = keys[i];
-        for (int p = 0; p < passes; ++p) atomicAdd(&sh[w][p][(k >> (begin_bit + p * BITS)) & (R - 1)], 1u);
+        for (int p = 0; p < passes; ++p) atomicAdd(&sh[w][p][(k >> (p * BITS)) & (R - 1)], 1u);
     }
     __syncthreads();
     for (int i = threadIdx.x; i < passes * R; i += kThreads) {
@@ -97,12 +138,15 @@ __global__ void k_hist_scan(uint32_t* hist, int passes) {
 }
 
 // ------------------------------------------------------------ onesweep pass
+// kout may be null (keys not needed after this pass); ranges non-null makes
+// this the last pass of the tile-key sort, recording per-key [start, end).
 template <int BITS>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 2)
 k_onesweep(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
            uint32_t* __restrict__ kout, uint32_t* __restrict__ vout, const uint32_t* d_count,
            int64_t cap, int shift, const uint32_t* __restrict__ digit_off,
-           unsigned long long* __restrict__ lookback, uint32_t* tile_counter, DevStatus* status) {
+           unsigned long long* __restrict__ lookback, uint32_t* tile_counter,
+           uint32_t* __restrict__ ranges, DevStatus* status) {
     constexpr int R = 1 << BITS;
     constexpr uint32_t MASK = R - 1;
     __shared__ uint32_t s_keys[kTileKeys];
@@ -125,15 +169,13 @@ k_onesweep(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
         const int64_t tile = s_tile;
         if (tile >= n_tiles) break;
 
-        // ---- load (warp-striped: warp w owns a contiguous run of 32*kItems keys)
-        uint32_t key[kItems], val[kItems], rank[kItems];
+        // ---- load keys (warp-striped: warp w owns a contiguous run of 32*kItems)
+        uint32_t key[kItems], rank[kItems];
         const int64_t wbase = tile * kTileKeys + (int64_t)warp * 32 * kItems;
 #pragma unroll
         for (int j = 0; j < kItems; ++j) {
             const int64_t idx = wbase + j * 32 + lane;
-            const bool ok = idx < count;
-            key[j] = ok ? kin[idx] : 0xFFFFFFFFu;
-            val[j] = ok ? vin[idx] : 0u;
+            key[j] = idx < count ? kin[idx] : 0xFFFFFFFFu;
         }
         // ---- stable rank within the warp, item order j*32 + lane
 #pragma unroll
@@ -148,19 +190,18 @@ k_onesweep(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
         }
         __syncthreads();
 
-        // ---- per digit: prefix over warps, tile count, publish, look back
+        // ---- per digit: prefix over warps, tile count, publish
         uint32_t tile_cnt = 0;
         if (threadIdx.x < R) {
             const int d = threadIdx.x;
             uint32_t acc = 0;
             for (int w = 0; w < kWarps; ++w) { const uint32_t c = s_whist[w][d]; s_whist[w][d] = acc; acc += c; }
             tile_cnt = acc;
-            unsigned long long* slot = lookback + tile * R + d;
-            st_volatile(slot, (tile == 0 ? kFlagInc : kFlagAgg) | (unsigned long long)tile_cnt);
+            st_volatile(lookback + tile * R + d, (tile == 0 ? kFlagInc : kFlagAgg) | (unsigned long long)tile_cnt);
+            s_local[d] = tile_cnt;
         }
-        // tile-local digit starts: exclusive scan of tile_cnt over d (serial per warp chunk)
-        if (threadIdx.x < R) s_local[threadIdx.x] = tile_cnt;
         __syncthreads();
+        // tile-local digit starts: exclusive scan of the tile counts (warp 0)
         if (threadIdx.x < 32) {
             constexpr int PER = (R + 31) / 32;
             uint32_t loc[PER], sum = 0;
@@ -184,38 +225,21 @@ k_onesweep(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
                 run += loc[i];
             }
         }
+        // ---- look back over preceding tiles, one thread per digit
         if (threadIdx.x < R) {
-            const int d = threadIdx.x;
             unsigned long long excl = 0;
-            if (tile > 0) {
-                int64_t p = tile - 1;
-                const long long t0 = clock64();
-                for (;;) {
-                    const unsigned long long x = ld_volatile(lookback + p * R + d);
-                    if (x & (kFlagAgg | kFlagInc)) {
-                        excl += x & kValMask;
-                        if (x & kFlagInc) break;
-                        --p;
-                        continue;
-                    }
-                    if (clock64() - t0 > kSpinCycles) {
-                        record_status(status, GS_ERR_TIMEOUT, tile);
-                        s_abort = 1;
-                        break;
-                    }
-                }
-                st_volatile(lookback + tile * R + d, kFlagInc | (excl + tile_cnt));
-            }
-            s_gbase[d] = digit_off[d] + (uint32_t)excl;
+            if (!look_back(lookback + threadIdx.x, tile, R, tile_cnt, &excl, status)) s_abort = 1;
+            s_gbase[threadIdx.x] = digit_off[threadIdx.x] + (uint32_t)excl;
         }
         __syncthreads();
-        // ---- stage in shared memory in digit order
+        // ---- stage in shared memory in digit order (values are read here)
 #pragma unroll
         for (int j = 0; j < kItems; ++j) {
             const uint32_t d = (key[j] >> shift) & MASK;
             const uint32_t lp = s_local[d] + s_whist[warp][d] + rank[j];
+            const int64_t idx = wbase + j * 32 + lane;
             s_keys[lp] = key[j];
-            s_vals[lp] = val[j];
+            s_vals[lp] = idx < count ? vin[idx] : 0u;
         }
         __syncthreads();
         // ---- scatter (invalid tail keys are all-ones: they sit at the end of
@@ -227,8 +251,14 @@ k_onesweep(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
                 const uint32_t k = s_keys[i];
                 const uint32_t d = (k >> shift) & MASK;
                 const uint32_t pos = s_gbase[d] + (uint32_t)i - s_local[d];
-                kout[pos] = k;
+                if ((int64_t)pos >= count) continue;  // unreachable when the histogram matches the keys
+                if (kout) kout[pos] = k;
                 vout[pos] = s_vals[i];
+                if (ranges) {
+                    // runs of equal keys are contiguous both here and in the output
+                    if (i == 0 || s_keys[i - 1] != k) atomicMin(&ranges[2 * (size_t)k], pos);
+                    if (i == valid - 1 || s_keys[i + 1] != k) atomicMax(&ranges[2 * (size_t)k + 1], pos + 1);
+                }
             }
         }
         __syncthreads();
@@ -238,8 +268,8 @@ k_onesweep(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
 // ------------------------------------------------------------ utilities
 __global__ void k_set_u32(uint32_t* p, uint32_t v) { *p = v; }
 
-// Zero `per_tile` u64 words for each of `passes` look-back arrays, for the
-// tiles that the device count implies.
+// Zero `radix` u64 words per look-back tile for each of `passes` arrays, for
+// the tiles that the device count implies.
 __global__ void k_clear_lookback(unsigned long long* lb, const uint32_t* d_count, int64_t cap,
                                  int radix, int passes, int64_t max_tiles) {
     const int64_t count = clamp_count(d_count, cap);
@@ -251,107 +281,23 @@ __global__ void k_clear_lookback(unsigned long long* lb, const uint32_t* d_count
             lb[(int64_t)p * max_tiles * radix + i] = 0ULL;
 }
 
+// ranges := (0xFFFFFFFF, 0) so that min/max atomics can fill them.
+__global__ void k_ranges_init(uint2* r, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        r[i] = make_uint2(0xFFFFFFFFu, 0u);
+}
+
+// tiles no entry reached become the empty range (0, 0).
+__global__ void k_ranges_fix(uint2* r, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint2 x = r[i];
+        if (x.x == 0xFFFFFFFFu) r[i] = make_uint2(0u, 0u);
+    }
+}
+
 __global__ void k_clear_u32(uint32_t* p, int64_t n) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         p[i] = 0u;
-}
-
-// ------------------------------------------------------------ emission
-constexpr int kEmitThreads = 256;
-constexpr int kEmitItems = 4;
-constexpr int kEmitBlock = kEmitThreads * kEmitItems;
-
-__global__ void __launch_bounds__(kEmitThreads)
-k_emit_count(const uint32_t* __restrict__ dvals, int64_t total, const uint4* __restrict__ proj,
-             uint32_t* __restrict__ block_sums) {
-    const int64_t base = (int64_t)blockIdx.x * kEmitBlock;
-    uint32_t s = 0;
-    for (int i = threadIdx.x; i < kEmitBlock; i += kEmitThreads) {
-        const int64_t idx = base + i;
-        if (idx < total) s += proj[(size_t)dvals[idx] * 4 + 3].z;
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, o);
-    __shared__ uint32_t ws[kEmitThreads / 32];
-    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        uint32_t t = 0;
-        for (int w = 0; w < kEmitThreads / 32; ++w) t += ws[w];
-        block_sums[blockIdx.x] = t;
-    }
-}
-
-__global__ void __launch_bounds__(kEmitThreads)
-k_emit_keys(const uint32_t* __restrict__ dvals, int64_t total, int64_t n,
-            const uint4* __restrict__ proj, const ViewInfo* __restrict__ vt,
-            const uint32_t* __restrict__ block_off, int64_t cap, uint32_t* __restrict__ keys,
-            uint32_t* __restrict__ vals) {
-    __shared__ uint32_t s_off[kEmitBlock + 1];
-    __shared__ uint32_t s_lo[kEmitBlock], s_hi[kEmitBlock], s_g[kEmitBlock], s_kb[kEmitBlock],
-        s_tx[kEmitBlock];
-    __shared__ uint32_t s_wsum[kEmitThreads / 32];
-    const int64_t base = (int64_t)blockIdx.x * kEmitBlock;
-    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    // blocked: thread t owns items t*kEmitItems .. +kEmitItems-1
-    uint32_t cnt[kEmitItems], tsum = 0;
-#pragma unroll
-    for (int j = 0; j < kEmitItems; ++j) {
-        const int li = t * kEmitItems + j;
-        const int64_t idx = base + li;
-        cnt[j] = 0;
-        if (idx < total) {
-            const uint32_t r = dvals[idx];
-            const uint4 pr = proj[(size_t)r * 4 + 3];
-            cnt[j] = pr.z;
-            const uint32_t v = (uint32_t)(r / (uint64_t)n);
-            s_lo[li] = pr.x;
-            s_hi[li] = pr.y;
-            s_g[li] = r - v * (uint32_t)n;
-            s_kb[li] = (uint32_t)vt[v].tile_off;
-            s_tx[li] = (uint32_t)vt[v].tx;
-        }
-        tsum += cnt[j];
-    }
-    uint32_t incl = tsum;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-        if (lane >= o) incl += y;
-    }
-    if (lane == 31) s_wsum[warp] = incl;
-    __syncthreads();
-    uint32_t wbase = 0, btotal = 0;
-    for (int w = 0; w < kEmitThreads / 32; ++w) {
-        if (w < warp) wbase += s_wsum[w];
-        btotal += s_wsum[w];
-    }
-    uint32_t run = wbase + incl - tsum;
-#pragma unroll
-    for (int j = 0; j < kEmitItems; ++j) {
-        s_off[t * kEmitItems + j] = run;
-        run += cnt[j];
-    }
-    if (t == 0) s_off[kEmitBlock] = btotal;
-    __syncthreads();
-    const int64_t out0 = block_off[blockIdx.x];
-    for (uint32_t k = t; k < btotal; k += kEmitThreads) {
-        // last item whose offset <= k (it has a non-zero count)
-        int lo = 0, hi = kEmitBlock;  // s_off[lo] <= k < s_off[hi]
-        while (hi - lo > 1) {
-            const int mid = (lo + hi) >> 1;
-            if (s_off[mid] <= k) lo = mid; else hi = mid;
-        }
-        const uint32_t li = k - s_off[lo];
-        const uint32_t x0 = s_lo[lo] & 0xFFFFu, y0 = s_lo[lo] >> 16;
-        const uint32_t w = (s_hi[lo] & 0xFFFFu) - x0;
-        const uint32_t tx = x0 + li % w, ty = y0 + li / w;
-        const int64_t pos = out0 + k;
-        if (pos < cap) {
-            keys[pos] = s_kb[lo] + ty * s_tx[lo] + tx;
-            vals[pos] = s_g[lo];
-        }
-    }
 }
 
 // Depth-sort input from projection records: key = float32 depth bits of a
@@ -365,14 +311,169 @@ __global__ void k_depth_keys(const uint4* __restrict__ proj, int64_t items, uint
     vals[i] = (uint32_t)i;
 }
 
-__global__ void k_ranges(const uint32_t* __restrict__ keys, const uint32_t* d_count, int64_t cap,
-                         uint2* __restrict__ ranges) {
-    const int64_t count = clamp_count(d_count, cap);
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t k = keys[i];
-        if (i == 0 || keys[i - 1] != k) ranges[k].x = (uint32_t)i;
-        if (i == count - 1 || keys[i + 1] != k) ranges[k].y = (uint32_t)(i + 1);
+// ------------------------------------------------------------ emission
+constexpr int kEmitThreads = 256;
+constexpr int kEmitWarps = kEmitThreads / 32;
+constexpr int kEmitRounds = 4;
+constexpr int kEmitBlock = kEmitThreads * kEmitRounds;  // depth-ordered Gaussians per block
+
+__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t x, int lane) {
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+        if (lane >= o) x += y;
+    }
+    return x;
+}
+
+// Item index within a block: warp w, round r, lane l -> w*128 + r*32 + l, so
+// the 32 items of one (warp, round) are consecutive and their outputs form
+// one contiguous range.
+template <int BITS>
+__global__ void __launch_bounds__(kEmitThreads)
+k_emit(const uint32_t* __restrict__ dvals, int64_t total, int64_t n, const uint4* __restrict__ proj,
+       const ViewInfo* __restrict__ vt, int64_t cap, uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
+       unsigned long long* __restrict__ lookback, uint32_t* block_counter, uint32_t* d_num_keys,
+       int passes, uint32_t* __restrict__ hist, DevStatus* status) {
+    constexpr int R = 1 << BITS;
+    __shared__ uint32_t s_hist[kMaxPasses][R];
+    __shared__ int s_mark[kEmitWarps][32];
+    __shared__ uint32_t s_wtot[kEmitWarps];
+    __shared__ uint32_t s_blk;
+    __shared__ unsigned long long s_excl;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int i = threadIdx.x; i < kMaxPasses * R; i += kEmitThreads) (&s_hist[0][0])[i] = 0;
+    if (threadIdx.x == 0) s_blk = atomicAdd(block_counter, 1u);
+    __syncthreads();
+    const int64_t b = s_blk;
+    const int64_t nblk = (total + kEmitBlock - 1) / kEmitBlock;
+
+    uint32_t cnt[kEmitRounds], lo[kEmitRounds], hi[kEmitRounds], gi[kEmitRounds], kb[kEmitRounds],
+        tx[kEmitRounds], incl[kEmitRounds], rtot[kEmitRounds];
+    uint32_t wtot = 0;
+#pragma unroll
+    for (int r = 0; r < kEmitRounds; ++r) {
+        const int64_t idx = b * kEmitBlock + warp * (32 * kEmitRounds) + r * 32 + lane;
+        cnt[r] = lo[r] = hi[r] = gi[r] = kb[r] = 0;
+        tx[r] = 1;
+        if (idx < total) {
+            const uint32_t rr = dvals[idx];
+            const uint4 p3 = proj[(size_t)rr * 4 + 3];
+            const uint32_t v = (uint32_t)(rr / (uint64_t)n);
+            cnt[r] = p3.z;
+            lo[r] = p3.x;
+            hi[r] = p3.y;
+            gi[r] = rr - v * (uint32_t)n;
+            kb[r] = (uint32_t)vt[v].tile_off;
+            tx[r] = (uint32_t)vt[v].tx;
+        }
+        incl[r] = warp_incl_scan(cnt[r], lane);
+        rtot[r] = __shfl_sync(0xFFFFFFFFu, incl[r], 31);
+        wtot += rtot[r];
+    }
+    if (lane == 0) s_wtot[warp] = wtot;
+    __syncthreads();
+    uint32_t wexcl = 0, btot = 0;
+    for (int w = 0; w < kEmitWarps; ++w) {
+        if (w < warp) wexcl += s_wtot[w];
+        btot += s_wtot[w];
+    }
+    if (threadIdx.x == 0) {
+        st_volatile(lookback + b, (b == 0 ? kFlagInc : kFlagAgg) | (unsigned long long)btot);
+        unsigned long long excl = 0;
+        look_back(lookback, b, 1, btot, &excl, status);
+        s_excl = excl;
+        if (b == nblk - 1) {
+            const unsigned long long K = excl + btot;
+            *d_num_keys = (uint32_t)(K > 0xFFFFFFFFull ? 0xFFFFFFFFull : K);
+            if ((long long)K > cap) record_status(status, GS_ERR_CAPACITY, (long long)K);
+        }
+    }
+    __syncthreads();
+
+    // ---- expansion: 32 consecutive outputs per warp step, coalesced
+    uint64_t base = s_excl + wexcl;
+#pragma unroll
+    for (int r = 0; r < kEmitRounds; ++r) {
+        const uint32_t off = incl[r] - cnt[r];
+        const uint32_t w0 = (hi[r] & 0xFFFFu) - (lo[r] & 0xFFFFu);
+        const float rw = w0 ? 1.0f / (float)w0 : 0.f;
+        int carry = -1;
+        for (uint32_t c = 0; c < rtot[r]; c += 32) {
+            s_mark[warp][lane] = -1;
+            __syncwarp();
+            if (cnt[r] > 0 && off >= c && off < c + 32) s_mark[warp][off - c] = lane;
+            __syncwarp();
+            int m = s_mark[warp][lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xFFFFFFFFu, m, o);
+                if (lane >= o) m = max(m, y);
+            }
+            m = max(m, carry);
+            carry = __shfl_sync(0xFFFFFFFFu, m, 31);
+            const int owner = m < 0 ? 0 : m;
+            const uint32_t o_off = __shfl_sync(0xFFFFFFFFu, off, owner);
+            const uint32_t o_lo = __shfl_sync(0xFFFFFFFFu, lo[r], owner);
+            const uint32_t o_w = __shfl_sync(0xFFFFFFFFu, w0, owner);
+            const float o_rw = __shfl_sync(0xFFFFFFFFu, rw, owner);
+            const uint32_t o_kb = __shfl_sync(0xFFFFFFFFu, kb[r], owner);
+            const uint32_t o_tx = __shfl_sync(0xFFFFFFFFu, tx[r], owner);
+            const uint32_t o_g = __shfl_sync(0xFFFFFFFFu, gi[r], owner);
+            const uint32_t o = c + lane;
+            // only entries that fit the capacity are stored and counted, so the
+            // sort's digit offsets always describe exactly the stored prefix
+            const bool stored = o < rtot[r] && base + o < (uint64_t)cap;
+            uint32_t key = 0;
+            if (stored) {
+                const uint32_t j = o - o_off;
+                // j / w exactly: j < 2^16 and w < 2^16, so (j + 0.5) / w stays
+                // more than 0.5 / w away from an integer
+                const uint32_t ty = (uint32_t)(((float)j + 0.5f) * o_rw);
+                const uint32_t txx = j - ty * o_w;
+                key = o_kb + ((o_lo >> 16) + ty) * o_tx + (o_lo & 0xFFFFu) + txx;
+                const uint64_t pos = base + o;
+                keys[pos] = key;
+                vals[pos] = o_g;
+            }
+            const uint32_t act = __ballot_sync(0xFFFFFFFFu, stored);
+            if (stored) {
+                atomicAdd(&s_hist[0][key & (R - 1)], 1u);
+                for (int p = 1; p < passes; ++p) {
+                    const uint32_t d = (key >> (p * BITS)) & (R - 1);
+                    const uint32_t peers = __match_any_sync(act, d);
+                    if (lane == __ffs(peers) - 1) atomicAdd(&s_hist[p][d], __popc(peers));
+                }
+            }
+        }
+        base += rtot[r];
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < passes * R; i += kEmitThreads) {
+        const uint32_t c = (&s_hist[0][0])[i];
+        if (c) atomicAdd(&hist[(i / R) * 256 + (i % R)], c);
+    }
+}
+
+// ------------------------------------------------------------ drivers
+template <int BITS>
+void onesweep_passes(const uint32_t* kin, const uint32_t* vin, uint32_t* ktmp, uint32_t* vtmp, uint32_t* kout,
+                     uint32_t* vout, const uint32_t* d_count, int64_t cap, int passes, const SortScratch& s,
+                     uint32_t* ranges, DevStatus* status, int sm_count, cudaStream_t st) {
+    constexpr int R = 1 << BITS;
+    k_hist_scan<BITS><<<1, 256, 0, st>>>(s.hist, passes);
+    const uint32_t* src_k = kin;
+    const uint32_t* src_v = vin;
+    for (int p = 0; p < passes; ++p) {
+        const bool last = p == passes - 1;
+        const bool to_out = ((passes - 1 - p) % 2) == 0;
+        uint32_t* dk = to_out ? kout : ktmp;
+        uint32_t* dv = to_out ? vout : vtmp;
+        k_onesweep<BITS><<<sm_count * 2, kThreads, 0, st>>>(
+            src_k, src_v, dk, dv, d_count, cap, p * BITS, s.hist + p * 256,
+            s.lookback + (int64_t)p * s.max_sort_tiles * R, s.counters + p, last ? ranges : nullptr, status);
+        src_k = dk;
+        src_v = dv;
     }
 }
 
@@ -383,25 +484,37 @@ void sort_pairs_bits(const uint32_t* kin, const uint32_t* vin, uint32_t* ktmp, u
                      cudaStream_t st) {
     constexpr int R = 1 << BITS;
     const int passes = (key_bits + BITS - 1) / BITS;
-    const int grid_stream = sm_count * 4;
     cudaMemsetAsync(s.hist, 0, sizeof(uint32_t) * kMaxPasses * 256, st);
     cudaMemsetAsync(s.counters, 0, sizeof(uint32_t) * 8, st);
-    k_clear_lookback<<<grid_stream, 256, 0, st>>>(s.lookback, d_count, cap, R, passes, s.max_sort_tiles);
-    k_hist<BITS><<<grid_stream, kThreads, 0, st>>>(kin, d_count, cap, 0, passes, s.hist);
-    k_hist_scan<BITS><<<1, 256, 0, st>>>(s.hist, passes);
-    // destinations: the last pass writes (kout, vout); earlier ones alternate
-    const uint32_t* src_k = kin;
-    const uint32_t* src_v = vin;
-    for (int p = 0; p < passes; ++p) {
-        const bool to_out = ((passes - 1 - p) % 2) == 0;
-        uint32_t* dk = to_out ? kout : ktmp;
-        uint32_t* dv = to_out ? vout : vtmp;
-        k_onesweep<BITS><<<sm_count * 2, kThreads, 0, st>>>(
-            src_k, src_v, dk, dv, d_count, cap, p * BITS, s.hist + p * 256,
-            s.lookback + (int64_t)p * s.max_sort_tiles * R, s.counters + p, status);
-        src_k = dk;
-        src_v = dv;
-    }
+    k_clear_lookback<<<sm_count * 4, 256, 0, st>>>(s.lookback, d_count, cap, R, passes, s.max_sort_tiles);
+    k_hist<BITS><<<sm_count * 4, kThreads, 0, st>>>(kin, d_count, cap, passes, s.hist);
+    onesweep_passes<BITS>(kin, vin, ktmp, vtmp, kout, vout, d_count, cap, passes, s, nullptr, status, sm_count, st);
+}
+
+// Emission + tile-key sort + ranges, for one digit width.  The passes write
+// (keys, values) into tkeys/tvals temporaries and end in the caller's arrays:
+// an odd pass count goes input -> out, an even one input -> tmp -> out ...
+template <int BITS>
+void emit_and_sort(const uint32_t* dv_sorted, int64_t items, int64_t n, const uint4* pr, const ViewInfo* vt,
+                   int64_t keys_cap, int key_bits, const SortScratch& s, uint32_t* sorted_keys,
+                   uint32_t* sorted_vals, uint32_t* ranges, int64_t total_tiles, uint32_t* d_num_keys,
+                   DevStatus* status, int sm_count, cudaStream_t st) {
+    constexpr int R = 1 << BITS;
+    const int passes = (key_bits + BITS - 1) / BITS;
+    const int64_t nblk = (items + kEmitBlock - 1) / kEmitBlock;
+    cudaMemsetAsync(s.hist, 0, sizeof(uint32_t) * kMaxPasses * 256, st);
+    cudaMemsetAsync(s.counters, 0, sizeof(uint32_t) * 8, st);
+    cudaMemsetAsync(s.emit_lookback, 0, sizeof(unsigned long long) * (size_t)nblk, st);
+    k_emit<BITS><<<(unsigned)nblk, kEmitThreads, 0, st>>>(dv_sorted, items, n, pr, vt, keys_cap, s.tkeys[0],
+                                                          s.tvals[0], s.emit_lookback, s.counters + 7,
+                                                          d_num_keys, passes, s.hist, status);
+    k_clear_lookback<<<sm_count * 4, 256, 0, st>>>(s.lookback, d_num_keys, keys_cap, R, passes, s.max_sort_tiles);
+    k_ranges_init<<<sm_count * 2, 256, 0, st>>>(reinterpret_cast<uint2*>(ranges), total_tiles);
+    // with 3 or more passes the output keys also serve as a temporary
+    uint32_t* kout = sorted_keys ? sorted_keys : (passes >= 3 ? s.tkeys[2] : nullptr);
+    onesweep_passes<BITS>(s.tkeys[0], s.tvals[0], s.tkeys[1], s.tvals[1], kout, sorted_vals, d_num_keys,
+                          keys_cap, passes, s, ranges, status, sm_count, st);
+    k_ranges_fix<<<sm_count * 2, 256, 0, st>>>(reinterpret_cast<uint2*>(ranges), total_tiles);
 }
 
 }  // namespace
@@ -422,17 +535,9 @@ void sort_pairs(const uint32_t* kin, const uint32_t* vin, uint32_t* ktmp, uint32
 }
 
 size_t sort_scratch_bytes(int V, int64_t n, int64_t keys_cap) {
-    Carver c(nullptr);
-    const int64_t items = (int64_t)V * n;
-    c.take<uint32_t>(items); c.take<uint32_t>(items); c.take<uint32_t>(items); c.take<uint32_t>(items);
-    c.take<uint32_t>((items + kEmitBlock - 1) / kEmitBlock + 1);
-    for (int i = 0; i < 5; ++i) c.take<uint32_t>(keys_cap);
-    c.take<uint32_t>(kMaxPasses * 256);
-    c.take<uint32_t>(8);
-    const int64_t mx = (std::max(items, keys_cap) + kTileKeys - 1) / kTileKeys + 1;
-    c.take<unsigned long long>((size_t)kMaxPasses * mx * 256);
-    c.take<uint32_t>(1);
-    return c.off;
+    SortScratch s;
+    carve_sort_scratch(nullptr, V, n, keys_cap, &s);
+    return s.bytes;
 }
 
 void carve_sort_scratch(char* base, int V, int64_t n, int64_t keys_cap, SortScratch* s) {
@@ -442,7 +547,7 @@ void carve_sort_scratch(char* base, int V, int64_t n, int64_t keys_cap, SortScra
     s->dvals[0] = c.take<uint32_t>(items);
     s->dkeys[1] = c.take<uint32_t>(items);
     s->dvals[1] = c.take<uint32_t>(items);
-    s->block_sums = c.take<uint32_t>((items + kEmitBlock - 1) / kEmitBlock + 1);
+    s->emit_lookback = c.take<unsigned long long>((items + kEmitBlock - 1) / kEmitBlock + 1);
     s->tkeys[0] = c.take<uint32_t>(keys_cap);
     s->tvals[0] = c.take<uint32_t>(keys_cap);
     s->tkeys[1] = c.take<uint32_t>(keys_cap);
@@ -453,10 +558,8 @@ void carve_sort_scratch(char* base, int V, int64_t n, int64_t keys_cap, SortScra
     s->max_sort_tiles = (std::max(items, keys_cap) + kTileKeys - 1) / kTileKeys + 1;
     s->lookback = c.take<unsigned long long>((size_t)kMaxPasses * s->max_sort_tiles * 256);
     s->d_count_depth = c.take<uint32_t>(1);
+    s->bytes = c.off;
 }
-
-void launch_scan_sums(uint32_t* sums, int64_t count, uint32_t* d_total, long long cap,
-                      DevStatus* status, cudaStream_t st);
 
 void launch_bin_sort(const float* proj, const ViewInfo* vt, int V, int64_t n, int64_t keys_cap,
                      int64_t total_tiles, int sort_bits, const SortScratch& s, bool depth_ready,
@@ -464,9 +567,8 @@ void launch_bin_sort(const float* proj, const ViewInfo* vt, int V, int64_t n, in
                      uint32_t* d_num_keys, DevStatus* status, int sm_count, cudaStream_t st) {
     const int64_t items = (int64_t)V * n;
     const uint4* pr = reinterpret_cast<const uint4*>(proj);
-    // ranges start empty
-    k_clear_u32<<<sm_count * 2, 256, 0, st>>>(ranges, total_tiles * 2);
     if (items == 0) {
+        k_clear_u32<<<sm_count * 2, 256, 0, st>>>(ranges, total_tiles * 2);
         k_set_u32<<<1, 1, 0, st>>>(d_num_keys, 0u);
         return;
     }
@@ -477,22 +579,17 @@ void launch_bin_sort(const float* proj, const ViewInfo* vt, int V, int64_t n, in
     // 4 passes (even): in -> tmp -> out -> tmp -> out, so out may alias in
     sort_pairs(s.dkeys[0], s.dvals[0], s.dkeys[1], s.dvals[1], s.dkeys[0], s.dvals[0],
                s.d_count_depth, items, 32, 8, s, status, sm_count, st);
-    const uint32_t* dv_sorted = s.dvals[0];
-    // 2. emission in depth order
-    const int64_t nblk = (items + kEmitBlock - 1) / kEmitBlock;
-    k_emit_count<<<(unsigned)nblk, kEmitThreads, 0, st>>>(dv_sorted, items, pr, s.block_sums);
-    launch_scan_sums(s.block_sums, nblk, d_num_keys, (long long)keys_cap, status, st);
-    k_emit_keys<<<(unsigned)nblk, kEmitThreads, 0, st>>>(dv_sorted, items, n, pr, vt, s.block_sums,
-                                                         keys_cap, s.tkeys[0], s.tvals[0]);
-    // 3. stable sort by tile key: input tkeys[0], temporary tkeys[1], output
-    //    the caller's arrays (keys into tkeys[2] if the caller wants none)
+    // 2. emission in depth order with the tile-key histograms, 3. stable sort
+    //    by tile key into the caller's arrays with per-tile ranges
     int bits = 1;
     while ((1LL << bits) < total_tiles) ++bits;
-    uint32_t* kout = sorted_keys ? sorted_keys : s.tkeys[2];
-    sort_pairs(s.tkeys[0], s.tvals[0], s.tkeys[1], s.tvals[1], kout, sorted_vals, d_num_keys,
-               keys_cap, bits, sort_bits, s, status, sm_count, st);
-    // 4. per-tile ranges
-    k_ranges<<<sm_count * 4, 256, 0, st>>>(kout, d_num_keys, keys_cap, reinterpret_cast<uint2*>(ranges));
+    switch (sort_bits) {
+        case 4: emit_and_sort<4>(s.dvals[0], items, n, pr, vt, keys_cap, bits, s, sorted_keys, sorted_vals, ranges, total_tiles, d_num_keys, status, sm_count, st); break;
+        case 5: emit_and_sort<5>(s.dvals[0], items, n, pr, vt, keys_cap, bits, s, sorted_keys, sorted_vals, ranges, total_tiles, d_num_keys, status, sm_count, st); break;
+        case 6: emit_and_sort<6>(s.dvals[0], items, n, pr, vt, keys_cap, bits, s, sorted_keys, sorted_vals, ranges, total_tiles, d_num_keys, status, sm_count, st); break;
+        case 7: emit_and_sort<7>(s.dvals[0], items, n, pr, vt, keys_cap, bits, s, sorted_keys, sorted_vals, ranges, total_tiles, d_num_keys, status, sm_count, st); break;
+        default: emit_and_sort<8>(s.dvals[0], items, n, pr, vt, keys_cap, bits, s, sorted_keys, sorted_vals, ranges, total_tiles, d_num_keys, status, sm_count, st); break;
+    }
 }
 
 }  // namespace gs
