@@ -257,11 +257,11 @@ def run_ours(args, rank, world, local_rank):
     tparams = torch.from_numpy(target_planes).to(dev)
     drift = torch.from_numpy(signs).to(dev) * 1e-3
 
-    ctx = gs.Context(local_rank, 0, tile=args.tile, sort_bits=args.sort_bits)
+    ctx = gs.Context(local_rank, 0, tile=args.tile, sort_bits=args.sort_bits, sort_items=args.sort_items)
     keys_cap = estimate_keys(ctx, params, sh, cams, slack=1.3)
     tr = OnlineTrainer(params, sh, cams, keys_cap, ctx=ctx)
     packed = tr.packed
-    tctx = gs.Context(local_rank, 0, tile=args.tile, sort_bits=args.sort_bits)
+    tctx = gs.Context(local_rank, 0, tile=args.tile, sort_bits=args.sort_bits, sort_items=args.sort_items)
     tkeys = estimate_keys(tctx, tparams, sh, cams, slack=1.3)
     tctx.reserve(tctx.workspace_size(packed, n, tkeys))
 
@@ -363,7 +363,7 @@ def run_ours(args, rank, world, local_rank):
                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                "config": {"workload": args.workload, "gaussians": n, "sh_degree": sh, "views": V,
                           "resolution": [W, H], "keys_per_step": K, "keys_cap": keys_cap, "tile": args.tile,
-                          "sort_digit_bits": args.sort_bits, "graph": True,
+                          "sort_digit_bits": args.sort_bits, "sort_items": args.sort_items, "graph": True,
                           "l2": "inputs larger than L2 (params 240 MB, keys > 1 GB per step)",
                           "targets": "re-rendered each step by gs_render_batch outside the step's events",
                           "parallelism": "replicas" if world > 1 else "single"},
@@ -419,6 +419,7 @@ def main():
     ap.add_argument("--workload", choices=list(WORKLOADS), default=DEFAULT_WORKLOAD)
     ap.add_argument("--tile", type=int, default=16)
     ap.add_argument("--sort-bits", type=int, default=8)
+    ap.add_argument("--sort-items", type=int, default=16)
     ap.add_argument("--e2e-steps", type=int, default=30)
     ap.add_argument("--cpu-samples", type=int, default=12)
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -97,6 +97,9 @@ gs_status_t gs_ctx_reserve(gs_ctx* ctx, size_t bytes);
 gs_status_t gs_ctx_set_tile(gs_ctx* ctx, int32_t tile);
 /* Radix digit width of the tile-key sort (4..8 bits; default 8). */
 gs_status_t gs_ctx_set_sort_bits(gs_ctx* ctx, int32_t bits);
+/* Keys per thread of a tile-key sort pass (8, 12 or 16; default 16): larger
+ * tiles mean fewer look-back steps, smaller ones more resident blocks. */
+gs_status_t gs_ctx_set_sort_items(gs_ctx* ctx, int32_t items);
 /* Reads and clears the device status word (synchronises `stream`).
  * *status receives the first error a kernel recorded since the last read
  * (GS_OK if none); *detail receives the required size for GS_ERR_CAPACITY. */

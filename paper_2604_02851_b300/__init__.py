@@ -80,7 +80,8 @@ def total_pixels(cams) -> int:
 class Context:
     """Owns a gs_ctx (device workspace, status word, graph)."""
 
-    def __init__(self, device: int = 0, workspace_bytes: int = 0, tile: int = 16, sort_bits: int = 8):
+    def __init__(self, device: int = 0, workspace_bytes: int = 0, tile: int = 16, sort_bits: int = 8,
+                 sort_items: int = 16):
         L = _lib.lib()
         p = C.c_void_p()
         check("gs_ctx_create", L.gs_ctx_create(C.byref(p), device, workspace_bytes))
@@ -89,6 +90,7 @@ class Context:
         self.tile = tile
         check("gs_ctx_set_tile", L.gs_ctx_set_tile(p, tile))
         check("gs_ctx_set_sort_bits", L.gs_ctx_set_sort_bits(p, sort_bits))
+        check("gs_ctx_set_sort_items", L.gs_ctx_set_sort_items(p, sort_items))
 
     def reserve(self, nbytes: int) -> None:
         check("gs_ctx_reserve", _lib.lib().gs_ctx_reserve(self.ptr, int(nbytes)))

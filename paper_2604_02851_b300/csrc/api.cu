@@ -164,6 +164,12 @@ gs_status_t gs_ctx_set_sort_bits(gs_ctx* ctx, int32_t bits) {
     return GS_OK;
 }
 
+gs_status_t gs_ctx_set_sort_items(gs_ctx* ctx, int32_t items) {
+    if (!ctx || (items != 8 && items != 12 && items != 16)) return GS_ERR_ARG;
+    ctx->sort_items = items;
+    return GS_OK;
+}
+
 gs_status_t gs_get_status(gs_ctx* ctx, void* stream, int32_t* status, int64_t* detail) {
     if (!ctx || !status) return GS_ERR_ARG;
     DeviceGuard g(ctx->device);
@@ -224,7 +230,7 @@ gs_status_t gs_bin_sort(gs_ctx* ctx, const float* proj, const gs_camera* d_cams,
     SortScratch s;
     carve_sort_scratch(ss, n_views, n, keys_cap, &s);
     launch_view_table(d_cams, n_views, ctx->tile, vt, total_tiles, ctx->d_status, S(stream));
-    launch_bin_sort(proj, vt, n_views, n, keys_cap, total_tiles, ctx->sort_bits, s, false, sorted_keys,
+    launch_bin_sort(proj, vt, n_views, n, keys_cap, total_tiles, ctx->sort_bits, ctx->sort_items, s, false, sorted_keys,
                     sorted_vals, ranges, d_num_keys, ctx->d_status, ctx->sm_count, S(stream));
     return launch_check();
 }
@@ -340,7 +346,7 @@ gs_status_t gs_render_batch(gs_ctx* ctx, const gs_scene* scene, const gs_camera*
     launch_view_table(d_cams, n_requests, ctx->tile, p.vt, total_tiles, ctx->d_status, st);
     launch_project(scene->params, scene->n, scene->sh_degree, d_cams, p.vt, n_requests, ctx->tile, p.proj,
                    s.dkeys[0], s.dvals[0], st);
-    launch_bin_sort(p.proj, p.vt, n_requests, scene->n, keys_cap, total_tiles, ctx->sort_bits, s, true, nullptr,
+    launch_bin_sort(p.proj, p.vt, n_requests, scene->n, keys_cap, total_tiles, ctx->sort_bits, ctx->sort_items, s, true, nullptr,
                     p.vals, p.ranges, p.n_keys, ctx->d_status, ctx->sm_count, st);
     launch_render_fwd(p.proj, p.vt, n_requests, scene->n, ctx->tile, p.vals, p.ranges, b, image, nullptr,
                       nullptr, total_tiles, st);
@@ -387,7 +393,7 @@ gs_status_t gs_train_step_events(gs_ctx* ctx, const gs_camera* d_cams, const gs_
     launch_view_table(d_cams, V, B, p.vt, tt, ctx->d_status, st);
     launch_project(io->params, n, cfg->sh_degree, d_cams, p.vt, V, B, p.proj, s.dkeys[0], s.dvals[0], st);
     mark(ev, 1, st);
-    launch_bin_sort(p.proj, p.vt, V, n, cfg->keys_cap, tt, ctx->sort_bits, s, true, nullptr, p.vals, p.ranges,
+    launch_bin_sort(p.proj, p.vt, V, n, cfg->keys_cap, tt, ctx->sort_bits, ctx->sort_items, s, true, nullptr, p.vals, p.ranges,
                     p.n_keys, ctx->d_status, ctx->sm_count, st);
     mark(ev, 2, st);
     launch_render_fwd(p.proj, p.vt, V, n, B, p.vals, p.ranges, b, io->image, p.T_final, p.n_contrib, tt, st);

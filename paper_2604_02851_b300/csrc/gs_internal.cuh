@@ -77,7 +77,7 @@ void carve_sort_scratch(char* base, int V, int64_t n, int64_t keys_cap, SortScra
 
 // Full bin + sort: depth sort, key emission, tile-key sort, ranges.
 void launch_bin_sort(const float* proj, const ViewInfo* vt, int V, int64_t n, int64_t keys_cap,
-                     int64_t total_tiles, int sort_bits, const SortScratch& s, bool depth_ready,
+                     int64_t total_tiles, int sort_bits, int sort_items, const SortScratch& s, bool depth_ready,
                      uint32_t* sorted_keys, uint32_t* sorted_vals, uint32_t* ranges,
                      uint32_t* d_num_keys, DevStatus* status, int sm_count, cudaStream_t st);
 
@@ -139,6 +139,7 @@ struct gs_ctx {
     int sm_count = 148;
     int tile = 16;
     int sort_bits = 8;
+    int sort_items = 16;
     void* ws = nullptr;
     size_t ws_bytes = 0;
     gs::DevStatus* d_status = nullptr;

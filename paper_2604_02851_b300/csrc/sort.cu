@@ -20,7 +20,7 @@
 // the tile-key sort, so that sort needs no counting pass of its own.
 //
 // The sort is a onesweep radix sort: per digit pass a single kernel ranks a
-// tile of keys in shared memory (warp match-any ranking, stable), publishes
+// tile of keys in shared memory (stable warp ranking from digit-bit ballots), publishes
 // its per-digit counts, resolves its global digit offsets by decoupled
 // look-back over the preceding tiles, and scatters.  The last pass of the
 // tile-key sort writes the values (and the keys only if asked) and records
@@ -39,6 +39,7 @@ constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 constexpr int kItems = 16;                       // keys per thread per tile
 constexpr int kTileKeys = kThreads * kItems;     // 4096
+constexpr int kMinTileKeys = kThreads * 8;       // smallest onesweep tile (look-back sizing)
 constexpr int kMaxPasses = 4;
 constexpr unsigned long long kFlagAgg = 1ULL << 62;
 constexpr unsigned long long kFlagInc = 2ULL << 62;
@@ -65,7 +66,8 @@ __device__ __forceinline__ int64_t clamp_count(const uint32_t* d_count, int64_t 
 
 // Exclusive prefix of `mine` over the slots 0..slot-1 of a look-back array
 // whose slots hold (flag | count); publishes this slot's inclusive value.
-// Bounded: on time-out records GS_ERR_TIMEOUT and returns false.
+// Four predecessors are read per round trip.  Bounded: on time-out records
+// GS_ERR_TIMEOUT and returns false.
 __device__ __forceinline__ bool look_back(unsigned long long* lb, int64_t slot, int stride,
                                           unsigned long long mine, unsigned long long* excl_out,
                                           DevStatus* status) {
@@ -75,14 +77,22 @@ __device__ __forceinline__ bool look_back(unsigned long long* lb, int64_t slot, 
         int64_t p = slot - 1;
         const long long t0 = clock64();
         for (;;) {
-            const unsigned long long x = ld_volatile(lb + p * stride);
-            if (x & (kFlagAgg | kFlagInc)) {
-                excl += x & kValMask;
-                if (x & kFlagInc) break;
-                --p;
-                continue;
+            unsigned long long x[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) x[k] = (p - k >= 0) ? ld_volatile(lb + (p - k) * stride) : 0ULL;
+            bool done = false;
+            int used = 0;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                if (done || used < k) break;  // stop at the first slot that is not ready
+                if (!(x[k] & (kFlagAgg | kFlagInc))) break;
+                excl += x[k] & kValMask;
+                used = k + 1;
+                if (x[k] & kFlagInc) done = true;
             }
-            if (clock64() - t0 > kSpinCycles) {
+            if (done) break;
+            p -= used;
+            if (used == 0 && clock64() - t0 > kSpinCycles) {
                 record_status(status, GS_ERR_TIMEOUT, slot);
                 ok = false;
                 break;
@@ -138,9 +148,10 @@ __global__ void k_hist_scan(uint32_t* hist, int passes) {
 }
 
 // ------------------------------------------------------------ onesweep pass
-// kout may be null (keys not needed after this pass); ranges non-null makes
-// this the last pass of the tile-key sort, recording per-key [start, end).
-template <int BITS>
+// ITEMS keys per thread, 256 threads: a tile of 256*ITEMS keys.  kout may be
+// null (keys not needed after this pass); ranges non-null makes this the last
+// pass of the tile-key sort, recording per-key [start, end).
+template <int BITS, int ITEMS>
 __global__ void __launch_bounds__(kThreads, 2)
 k_onesweep(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
            uint32_t* __restrict__ kout, uint32_t* __restrict__ vout, const uint32_t* d_count,
@@ -149,8 +160,9 @@ k_onesweep(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
            uint32_t* __restrict__ ranges, DevStatus* status) {
     constexpr int R = 1 << BITS;
     constexpr uint32_t MASK = R - 1;
-    __shared__ uint32_t s_keys[kTileKeys];
-    __shared__ uint32_t s_vals[kTileKeys];
+    constexpr int TILE = kThreads * ITEMS;
+    __shared__ uint32_t s_keys[TILE];
+    __shared__ uint32_t s_vals[TILE];
     __shared__ uint32_t s_whist[kWarps][R];   // per-warp digit counts, then warp prefixes
     __shared__ uint32_t s_local[R];           // tile-local start of each digit
     __shared__ uint32_t s_gbase[R];           // global start of this tile's digit run
@@ -158,7 +170,7 @@ k_onesweep(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
     __shared__ int s_abort;
 
     const int64_t count = clamp_count(d_count, cap);
-    const int64_t n_tiles = (count + kTileKeys - 1) / kTileKeys;
+    const int64_t n_tiles = (count + TILE - 1) / TILE;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t lt = lanemask_lt();
 
@@ -169,24 +181,34 @@ k_onesweep(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
         const int64_t tile = s_tile;
         if (tile >= n_tiles) break;
 
-        // ---- load keys (warp-striped: warp w owns a contiguous run of 32*kItems)
-        uint32_t key[kItems], rank[kItems];
-        const int64_t wbase = tile * kTileKeys + (int64_t)warp * 32 * kItems;
+        // ---- load (warp-striped: warp w owns a contiguous run of 32*ITEMS)
+        uint32_t key[ITEMS], val[ITEMS], rank[ITEMS];
+        const int64_t wbase = tile * TILE + (int64_t)warp * 32 * ITEMS;
 #pragma unroll
-        for (int j = 0; j < kItems; ++j) {
+        for (int j = 0; j < ITEMS; ++j) {
             const int64_t idx = wbase + j * 32 + lane;
-            key[j] = idx < count ? kin[idx] : 0xFFFFFFFFu;
+            const bool ok = idx < count;
+            key[j] = ok ? kin[idx] : 0xFFFFFFFFu;
+            val[j] = ok ? vin[idx] : 0u;
         }
-        // ---- stable rank within the warp, item order j*32 + lane
+        // ---- stable rank within the warp, item order j*32 + lane: the lanes
+        //      holding the same digit are found with one ballot per digit bit;
+        //      the lowest of them adds the group size to the warp's counter
+        //      and shares the old value with its group
 #pragma unroll
-        for (int j = 0; j < kItems; ++j) {
+        for (int j = 0; j < ITEMS; ++j) {
             const uint32_t d = (key[j] >> shift) & MASK;
-            const uint32_t peers = __match_any_sync(0xFFFFFFFFu, d);
-            const uint32_t before = s_whist[warp][d];
+            uint32_t peers = 0xFFFFFFFFu;
+#pragma unroll
+            for (int bit = 0; bit < BITS; ++bit) {
+                const uint32_t b = __ballot_sync(0xFFFFFFFFu, (d >> bit) & 1u);
+                peers &= ((d >> bit) & 1u) ? b : ~b;
+            }
+            const int leader = __ffs(peers) - 1;
+            uint32_t before = 0;
+            if (lane == leader) before = atomicAdd(&s_whist[warp][d], (uint32_t)__popc(peers));
+            before = __shfl_sync(0xFFFFFFFFu, before, leader);
             rank[j] = before + __popc(peers & lt);
-            __syncwarp();
-            if (lane == __ffs(peers) - 1) s_whist[warp][d] = before + __popc(peers);
-            __syncwarp();
         }
         __syncthreads();
 
@@ -232,20 +254,19 @@ k_onesweep(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
             s_gbase[threadIdx.x] = digit_off[threadIdx.x] + (uint32_t)excl;
         }
         __syncthreads();
-        // ---- stage in shared memory in digit order (values are read here)
+        // ---- stage in shared memory in digit order
 #pragma unroll
-        for (int j = 0; j < kItems; ++j) {
+        for (int j = 0; j < ITEMS; ++j) {
             const uint32_t d = (key[j] >> shift) & MASK;
             const uint32_t lp = s_local[d] + s_whist[warp][d] + rank[j];
-            const int64_t idx = wbase + j * 32 + lane;
             s_keys[lp] = key[j];
-            s_vals[lp] = idx < count ? vin[idx] : 0u;
+            s_vals[lp] = val[j];
         }
         __syncthreads();
         // ---- scatter (invalid tail keys are all-ones: they sit at the end of
         //      the last digit's run, i.e. at staged positions >= valid)
-        const int64_t rem = count - tile * kTileKeys;
-        const int valid = rem < kTileKeys ? (int)rem : kTileKeys;
+        const int64_t rem = count - tile * TILE;
+        const int valid = rem < TILE ? (int)rem : TILE;
         if (!s_abort) {
             for (int i = threadIdx.x; i < valid; i += kThreads) {
                 const uint32_t k = s_keys[i];
@@ -271,9 +292,9 @@ __global__ void k_set_u32(uint32_t* p, uint32_t v) { *p = v; }
 // Zero `radix` u64 words per look-back tile for each of `passes` arrays, for
 // the tiles that the device count implies.
 __global__ void k_clear_lookback(unsigned long long* lb, const uint32_t* d_count, int64_t cap,
-                                 int radix, int passes, int64_t max_tiles) {
+                                 int radix, int passes, int64_t max_tiles, int tile_keys) {
     const int64_t count = clamp_count(d_count, cap);
-    const int64_t tiles = (count + kTileKeys - 1) / kTileKeys;
+    const int64_t tiles = (count + tile_keys - 1) / tile_keys;
     const int64_t words = tiles * radix;
     for (int p = 0; p < passes; ++p)
         for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < words;
@@ -456,11 +477,13 @@ k_emit(const uint32_t* __restrict__ dvals, int64_t total, int64_t n, const uint4
 }
 
 // ------------------------------------------------------------ drivers
-template <int BITS>
+template <int BITS, int ITEMS>
 void onesweep_passes(const uint32_t* kin, const uint32_t* vin, uint32_t* ktmp, uint32_t* vtmp, uint32_t* kout,
                      uint32_t* vout, const uint32_t* d_count, int64_t cap, int passes, const SortScratch& s,
                      uint32_t* ranges, DevStatus* status, int sm_count, cudaStream_t st) {
     constexpr int R = 1 << BITS;
+    k_clear_lookback<<<sm_count * 4, 256, 0, st>>>(s.lookback, d_count, cap, R, passes, s.max_sort_tiles,
+                                                   kThreads * ITEMS);
     k_hist_scan<BITS><<<1, 256, 0, st>>>(s.hist, passes);
     const uint32_t* src_k = kin;
     const uint32_t* src_v = vin;
@@ -469,7 +492,7 @@ void onesweep_passes(const uint32_t* kin, const uint32_t* vin, uint32_t* ktmp, u
         const bool to_out = ((passes - 1 - p) % 2) == 0;
         uint32_t* dk = to_out ? kout : ktmp;
         uint32_t* dv = to_out ? vout : vtmp;
-        k_onesweep<BITS><<<sm_count * 2, kThreads, 0, st>>>(
+        k_onesweep<BITS, ITEMS><<<sm_count * 2, kThreads, 0, st>>>(
             src_k, src_v, dk, dv, d_count, cap, p * BITS, s.hist + p * 256,
             s.lookback + (int64_t)p * s.max_sort_tiles * R, s.counters + p, last ? ranges : nullptr, status);
         src_k = dk;
@@ -486,15 +509,15 @@ void sort_pairs_bits(const uint32_t* kin, const uint32_t* vin, uint32_t* ktmp, u
     const int passes = (key_bits + BITS - 1) / BITS;
     cudaMemsetAsync(s.hist, 0, sizeof(uint32_t) * kMaxPasses * 256, st);
     cudaMemsetAsync(s.counters, 0, sizeof(uint32_t) * 8, st);
-    k_clear_lookback<<<sm_count * 4, 256, 0, st>>>(s.lookback, d_count, cap, R, passes, s.max_sort_tiles);
     k_hist<BITS><<<sm_count * 4, kThreads, 0, st>>>(kin, d_count, cap, passes, s.hist);
-    onesweep_passes<BITS>(kin, vin, ktmp, vtmp, kout, vout, d_count, cap, passes, s, nullptr, status, sm_count, st);
+    onesweep_passes<BITS, 16>(kin, vin, ktmp, vtmp, kout, vout, d_count, cap, passes, s, nullptr, status, sm_count,
+                              st);
 }
 
 // Emission + tile-key sort + ranges, for one digit width.  The passes write
 // (keys, values) into tkeys/tvals temporaries and end in the caller's arrays:
 // an odd pass count goes input -> out, an even one input -> tmp -> out ...
-template <int BITS>
+template <int BITS, int ITEMS>
 void emit_and_sort(const uint32_t* dv_sorted, int64_t items, int64_t n, const uint4* pr, const ViewInfo* vt,
                    int64_t keys_cap, int key_bits, const SortScratch& s, uint32_t* sorted_keys,
                    uint32_t* sorted_vals, uint32_t* ranges, int64_t total_tiles, uint32_t* d_num_keys,
@@ -508,12 +531,11 @@ void emit_and_sort(const uint32_t* dv_sorted, int64_t items, int64_t n, const ui
     k_emit<BITS><<<(unsigned)nblk, kEmitThreads, 0, st>>>(dv_sorted, items, n, pr, vt, keys_cap, s.tkeys[0],
                                                           s.tvals[0], s.emit_lookback, s.counters + 7,
                                                           d_num_keys, passes, s.hist, status);
-    k_clear_lookback<<<sm_count * 4, 256, 0, st>>>(s.lookback, d_num_keys, keys_cap, R, passes, s.max_sort_tiles);
     k_ranges_init<<<sm_count * 2, 256, 0, st>>>(reinterpret_cast<uint2*>(ranges), total_tiles);
     // with 3 or more passes the output keys also serve as a temporary
     uint32_t* kout = sorted_keys ? sorted_keys : (passes >= 3 ? s.tkeys[2] : nullptr);
-    onesweep_passes<BITS>(s.tkeys[0], s.tvals[0], s.tkeys[1], s.tvals[1], kout, sorted_vals, d_num_keys,
-                          keys_cap, passes, s, ranges, status, sm_count, st);
+    onesweep_passes<BITS, ITEMS>(s.tkeys[0], s.tvals[0], s.tkeys[1], s.tvals[1], kout, sorted_vals, d_num_keys,
+                                 keys_cap, passes, s, ranges, status, sm_count, st);
     k_ranges_fix<<<sm_count * 2, 256, 0, st>>>(reinterpret_cast<uint2*>(ranges), total_tiles);
 }
 
@@ -555,14 +577,14 @@ void carve_sort_scratch(char* base, int V, int64_t n, int64_t keys_cap, SortScra
     s->tkeys[2] = c.take<uint32_t>(keys_cap);
     s->hist = c.take<uint32_t>(kMaxPasses * 256);
     s->counters = c.take<uint32_t>(8);
-    s->max_sort_tiles = (std::max(items, keys_cap) + kTileKeys - 1) / kTileKeys + 1;
+    s->max_sort_tiles = (std::max(items, keys_cap) + kMinTileKeys - 1) / kMinTileKeys + 1;
     s->lookback = c.take<unsigned long long>((size_t)kMaxPasses * s->max_sort_tiles * 256);
     s->d_count_depth = c.take<uint32_t>(1);
     s->bytes = c.off;
 }
 
 void launch_bin_sort(const float* proj, const ViewInfo* vt, int V, int64_t n, int64_t keys_cap,
-                     int64_t total_tiles, int sort_bits, const SortScratch& s, bool depth_ready,
+                     int64_t total_tiles, int sort_bits, int sort_items, const SortScratch& s, bool depth_ready,
                      uint32_t* sorted_keys, uint32_t* sorted_vals, uint32_t* ranges,
                      uint32_t* d_num_keys, DevStatus* status, int sm_count, cudaStream_t st) {
     const int64_t items = (int64_t)V * n;
@@ -583,13 +605,27 @@ void launch_bin_sort(const float* proj, const ViewInfo* vt, int V, int64_t n, in
     //    by tile key into the caller's arrays with per-tile ranges
     int bits = 1;
     while ((1LL << bits) < total_tiles) ++bits;
-    switch (sort_bits) {
-        case 4: emit_and_sort<4>(s.dvals[0], items, n, pr, vt, keys_cap, bits, s, sorted_keys, sorted_vals, ranges, total_tiles, d_num_keys, status, sm_count, st); break;
-        case 5: emit_and_sort<5>(s.dvals[0], items, n, pr, vt, keys_cap, bits, s, sorted_keys, sorted_vals, ranges, total_tiles, d_num_keys, status, sm_count, st); break;
-        case 6: emit_and_sort<6>(s.dvals[0], items, n, pr, vt, keys_cap, bits, s, sorted_keys, sorted_vals, ranges, total_tiles, d_num_keys, status, sm_count, st); break;
-        case 7: emit_and_sort<7>(s.dvals[0], items, n, pr, vt, keys_cap, bits, s, sorted_keys, sorted_vals, ranges, total_tiles, d_num_keys, status, sm_count, st); break;
-        default: emit_and_sort<8>(s.dvals[0], items, n, pr, vt, keys_cap, bits, s, sorted_keys, sorted_vals, ranges, total_tiles, d_num_keys, status, sm_count, st); break;
+#define GS_EMIT_SORT(B, I) emit_and_sort<B, I>(s.dvals[0], items, n, pr, vt, keys_cap, bits, s, sorted_keys, \
+                                                 sorted_vals, ranges, total_tiles, d_num_keys, status, sm_count, st)
+    const int it = sort_items == 8 ? 8 : (sort_items == 16 ? 16 : 12);
+    switch (sort_bits * 100 + it) {
+        case 408: GS_EMIT_SORT(4, 8); break;
+        case 412: GS_EMIT_SORT(4, 12); break;
+        case 416: GS_EMIT_SORT(4, 16); break;
+        case 508: GS_EMIT_SORT(5, 8); break;
+        case 512: GS_EMIT_SORT(5, 12); break;
+        case 516: GS_EMIT_SORT(5, 16); break;
+        case 608: GS_EMIT_SORT(6, 8); break;
+        case 612: GS_EMIT_SORT(6, 12); break;
+        case 616: GS_EMIT_SORT(6, 16); break;
+        case 708: GS_EMIT_SORT(7, 8); break;
+        case 712: GS_EMIT_SORT(7, 12); break;
+        case 716: GS_EMIT_SORT(7, 16); break;
+        case 808: GS_EMIT_SORT(8, 8); break;
+        case 816: GS_EMIT_SORT(8, 16); break;
+        default: GS_EMIT_SORT(8, 12); break;
     }
+#undef GS_EMIT_SORT
 }
 
 }  // namespace gs
