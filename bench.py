@@ -350,6 +350,33 @@ def run_ours(args, rank, world, local_rank):
     if args.e2e_steps > 0:
         e2e = run_e2e(args, tr, next_targets, world)
 
+    # ---- the unbatched reference point: one view per launch sequence
+    plain = None
+    if args.plain_steps > 0:
+        for _ in range(3):
+            next_targets()
+            tr.step_plain()
+        torch.cuda.synchronize()
+        pe0, pe1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        plain_ms = 0.0
+        for _ in range(args.plain_steps):
+            next_targets()
+            pe0.record()
+            tr.step_plain()
+            pe1.record()
+            pe1.synchronize()
+            plain_ms += pe0.elapsed_time(pe1)
+        plain_ms /= args.plain_steps
+        plain = {"ms_per_step": plain_ms, "steps": args.plain_steps,
+                 "batched_graph_speedup": plain_ms / ms_per_step,
+                 "what": "per view: projection, bin/sort with a host read of the key count, compositing, "
+                         "loss, both adjoints as separate launches; then Adam and delta"}
+    del tr
+    serving = None
+    if args.serve_requests > 0:
+        torch.cuda.empty_cache()
+        serving = run_serving(args, local_rank, rank)
+
     out = None
     if rank == 0:
         cpu = None
@@ -368,11 +395,62 @@ def run_ours(args, rank, world, local_rank):
                           "targets": "re-rendered each step by gs_render_batch outside the step's events",
                           "parallelism": "replicas" if world > 1 else "single"},
                "roofline": roofline, "cpu_baseline": cpu, "clocks": clk, "e2e": e2e,
+               "plain_step": plain, "serving": serving,
                "gpu_launches": gpu_launches_per_step(tile_passes) * args.steps,
                "phases_ms": phase_avg, "kernels": kernels, "loss_last": loss_last, "delta_changed_last": changed,
                "wall_s_timed_loop": wall}
         print(json.dumps(out), flush=True)
     return out
+
+
+def run_serving(args, local_rank, rank):
+    """Config 4: forward-only renders of a static 2M-Gaussian SH-3 model for
+    64 clients with Poisson arrivals, resolutions mixed 1280x720 / 1920x1080 /
+    1440x1600 per eye, eyes within 0.3 of the ring of radius 3; continuous
+    batching on 3 slots.  Saturation is measured first with every request
+    queued at once; the open-loop run then offers args.serve_load of it."""
+    import torch
+    import paper_2604_02851_b300 as gs
+    from paper_2604_02851_b300.serve import RenderServer, Request, measure_keys_per_pixel, percentiles
+    dev = torch.device("cuda", local_rank)
+    n, sh = 2_000_000, 3
+    params = torch.from_numpy(gi.make_scene(n, sh, gi.SEED_SERVING + 1000 * rank)).to(dev)
+    probe = gi.cameras_from_eyes([(3.0 * math.sin(a), 0.0, 3.0 * math.cos(a)) for a in (0.3, 2.0)],
+                                 [1280, 1920], [720, 1080])
+    kpp = measure_keys_per_pixel(params, sh, probe)
+    srv = RenderServer(params, sh, kpp, slots=3, max_batch=6, max_pixels_per_batch=6_000_000,
+                       memory_budget=64 << 30, slack=1.3)
+
+    def requests(k, rate, seed):
+        out = []
+        for i, sp in enumerate(gi.serving_requests(k, rate_hz=rate, seed=seed)):
+            cams = gi.cameras_from_eyes([sp["eye"]], [sp["width"]], [sp["height"]])
+            out.append(Request(rid=i, width=sp["width"], height=sp["height"], cam=gs.pack_cameras(cams),
+                               t_arrival=sp["t_arrival"]))
+        return out
+
+    srv.run(requests(12, 1e6, gi.SEED_SERVING + 50), realtime=False)  # warm-up
+    done, el = srv.run(requests(args.serve_requests // 3 + 1, 1e6, gi.SEED_SERVING + 51), realtime=False)
+    saturation = len(done) / el
+    rate = args.serve_load * saturation
+    srv.batches = 0
+    srv.batch_sizes = []
+    srv.launch_while_busy = 0
+    srv.max_busy = 0
+    retries0 = srv.retries
+    done, el = srv.run(requests(args.serve_requests, rate, gi.SEED_SERVING + 52), realtime=True)
+    srv.check()
+    p50, p99, lat = percentiles(done)
+    res = {"model": "2M Gaussians, SH3", "clients": 64, "requests": len(done), "offered_rate_hz": rate,
+           "saturation_renders_per_s": saturation, "load": args.serve_load, "renders_per_s": len(done) / el,
+           "p50_ms": p50, "p99_ms": p99, "batches": srv.batches,
+           "mean_batch": float(np.mean(srv.batch_sizes)) if srv.batch_sizes else 0.0,
+           "max_slots_busy": srv.max_busy, "batches_started_while_busy": srv.launch_while_busy,
+           "capacity_retries": srv.retries - retries0,
+           "latency": "arrival to image in pinned host memory"}
+    del srv, params
+    torch.cuda.empty_cache()
+    return res
 
 
 def run_e2e(args, tr, next_targets, world):
@@ -422,6 +500,9 @@ def main():
     ap.add_argument("--sort-items", type=int, default=16)
     ap.add_argument("--e2e-steps", type=int, default=30)
     ap.add_argument("--cpu-samples", type=int, default=12)
+    ap.add_argument("--plain-steps", type=int, default=10)
+    ap.add_argument("--serve-requests", type=int, default=240)
+    ap.add_argument("--serve-load", type=float, default=0.5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
