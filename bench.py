@@ -61,8 +61,9 @@ def phase_model(n, V, K, total_tiles, npix, sum_nc, n_changed, tile_passes):
     vn = V * n
     return {
         "project": ("hbm", n * 240 + vn * (64 + 8)),
-        "bin_sort": ("hbm", vn * (4 * 16 + 4) + vn * (4 + 16 + 16) + K * 8 + K * (tile_passes * 16 + 4)
-                     + K * 4 + total_tiles * 8),
+        "depth_sort": ("hbm", vn * (4 * 16 + 4)),
+        "emit": ("hbm", vn * (4 + 32) + K * 8),
+        "tile_sort": ("hbm", K * (16 * (tile_passes - 1) + 12) + total_tiles * 16),
         "render_fwd": ("alu", sum_nc * RASTER_FWD_FLOP_PER_FRAGMENT),
         "loss": ("hbm", 3 * npix * 44),
         "raster_bwd": ("alu", sum_nc * RASTER_BWD_FLOP_PER_FRAGMENT),
@@ -70,6 +71,11 @@ def phase_model(n, V, K, total_tiles, npix, sum_nc, n_changed, tile_passes):
         "adam": ("hbm", 60 * n * 4 * 7),
         "delta": ("hbm", n * (480 + 2) + n_changed * (240 + 240 + 128 + 4)),
     }
+
+
+# phases that are one kernel (plus negligible set-up launches), by kernel name
+SINGLE_KERNEL_PHASES = {"project": "k_project", "emit": "k_emit", "render_fwd": "k_render_fwd",
+                        "raster_bwd": "k_raster_bwd", "project_bwd": "k_project_bwd", "adam": "k_adam"}
 
 
 def gpu_launches_per_step(tile_passes):
@@ -339,9 +345,10 @@ def run_ours(args, rank, world, local_rank):
             ach = work / (ms / 1e3) / 1e12
             kernels[name] = {"ms": ms, "bound": "alu", "achieved": ach, "unit": "TFLOP/s",
                              "peak": FP32_PEAK_TFLOPS, "frac": ach / FP32_PEAK_TFLOPS, "algorithmic_flop": work}
-    dom = max(phase_avg, key=phase_avg.get)
+    dom = max(SINGLE_KERNEL_PHASES, key=lambda p: phase_avg[p])
     dk = kernels[dom]
-    roofline = {"kernel": dom, "bound": dk["bound"], "achieved": dk["achieved"], "peak": dk["peak"],
+    roofline = {"kernel": SINGLE_KERNEL_PHASES[dom], "bound": dk["bound"], "achieved": dk["achieved"],
+                "peak": dk["peak"],
                 "unit": dk["unit"], "frac": dk["frac"], "traffic": None,
                 "peak_source": peak_src if dk["bound"] == "hbm" else "derived: 148 SMs x 128 FP32 lanes x 2 x 2032 MHz"}
 

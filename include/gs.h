@@ -292,10 +292,11 @@ gs_status_t gs_train_step(gs_ctx* ctx, const gs_camera* d_cams, const gs_train_i
                           const gs_train_cfg* cfg, void* stream);
 
 /* Number of phase boundaries gs_train_step can mark with events: before
- * projection, after projection, after bin/sort, after compositing, after the
+ * projection, after projection, after the depth sort, after key emission,
+ * after the tile-key sort (ranges included), after compositing, after the
  * loss, after the raster adjoint, after the projection adjoint, after Adam,
  * after delta extraction. */
-#define GS_TRAIN_PHASE_EVENTS 9
+#define GS_TRAIN_PHASE_EVENTS 11
 
 /* gs_train_step that also records `events` (GS_TRAIN_PHASE_EVENTS cudaEvent_t
  * handles passed as void*, created by the caller with timing enabled) at the

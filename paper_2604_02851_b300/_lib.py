@@ -95,8 +95,9 @@ _SIGS = {
     "gs_train_step_events": [_P, _P, C.POINTER(gs_train_io), C.POINTER(gs_train_cfg), C.POINTER(_P), _P],
     "gs_train_graph_capture_events": [_P, _P, C.POINTER(gs_train_io), C.POINTER(gs_train_cfg), C.POINTER(_P), _P],
 }
-TRAIN_PHASE_EVENTS = 9
-TRAIN_PHASES = ("project", "bin_sort", "render_fwd", "loss", "raster_bwd", "project_bwd", "adam", "delta")
+TRAIN_PHASE_EVENTS = 11
+TRAIN_PHASES = ("project", "depth_sort", "emit", "tile_sort", "render_fwd", "loss", "raster_bwd", "project_bwd",
+                "adam", "delta")
 _RESTYPES = {"gs_workspace_size": C.c_size_t, "gs_total_tiles": C.c_int64}
 _SIGS["gs_workspace_size"] = [_P, C.POINTER(gs_camera), _I32, _I64, _I64]
 _SIGS["gs_total_tiles"] = [_P, C.POINTER(gs_camera), _I32]

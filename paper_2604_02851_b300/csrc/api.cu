@@ -354,6 +354,7 @@ gs_status_t gs_render_batch(gs_ctx* ctx, const gs_scene* scene, const gs_camera*
 }
 
 static void mark(void* const* events, int i, cudaStream_t st) {
+    // phase boundary i of gs_train_step_events (null events: nothing recorded)
     if (!events || !events[i]) return;
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     cudaStreamIsCapturing(st, &cs);
@@ -393,27 +394,27 @@ gs_status_t gs_train_step_events(gs_ctx* ctx, const gs_camera* d_cams, const gs_
     launch_view_table(d_cams, V, B, p.vt, tt, ctx->d_status, st);
     launch_project(io->params, n, cfg->sh_degree, d_cams, p.vt, V, B, p.proj, s.dkeys[0], s.dvals[0], st);
     mark(ev, 1, st);
-    launch_bin_sort(p.proj, p.vt, V, n, cfg->keys_cap, tt, ctx->sort_bits, ctx->sort_items, s, true, nullptr, p.vals, p.ranges,
-                    p.n_keys, ctx->d_status, ctx->sm_count, st);
-    mark(ev, 2, st);
+    launch_bin_sort(p.proj, p.vt, V, n, cfg->keys_cap, tt, ctx->sort_bits, ctx->sort_items, s, true, nullptr,
+                    p.vals, p.ranges, p.n_keys, ctx->d_status, ctx->sm_count, st, ev ? mark : nullptr, ev, 2);
+    mark(ev, 4, st);
     launch_render_fwd(p.proj, p.vt, V, n, B, p.vals, p.ranges, b, io->image, p.T_final, p.n_contrib, tt, st);
-    mark(ev, 3, st);
+    mark(ev, 5, st);
     launch_loss(io->image, io->targets, V, cfg->height, cfg->width, cfg->w_l1, cfg->w_ssim, io->d_loss, p.dimage,
                 p.loss, st);
-    mark(ev, 4, st);
+    mark(ev, 6, st);
     launch_raster_bwd(p.proj, p.vt, V, n, B, p.vals, p.ranges, b, p.T_final, p.n_contrib, p.dimage, p.grad2d, tt,
                       st);
-    mark(ev, 5, st);
+    mark(ev, 7, st);
     launch_project_bwd(io->params, n, cfg->sh_degree, d_cams, V, p.proj, p.grad2d, io->grads, 0, st);
-    mark(ev, 6, st);
+    mark(ev, 8, st);
     gs_adam_cfg ac = cfg->adam;
     ac.d_step = io->d_step;
     ac.increment = 1;
     launch_adam(io->params, io->grads, io->adam_m, io->adam_v, n, ac, st);
-    mark(ev, 7, st);
+    mark(ev, 9, st);
     launch_delta(io->params, io->baseline, n, cfg->delta_thr, io->d_delta_idx, io->d_delta_records,
                  io->d_delta_count, p.delta, st);
-    mark(ev, 8, st);
+    mark(ev, 10, st);
     return launch_check();
 }
 

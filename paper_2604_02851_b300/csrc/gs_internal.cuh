@@ -79,7 +79,9 @@ void carve_sort_scratch(char* base, int V, int64_t n, int64_t keys_cap, SortScra
 void launch_bin_sort(const float* proj, const ViewInfo* vt, int V, int64_t n, int64_t keys_cap,
                      int64_t total_tiles, int sort_bits, int sort_items, const SortScratch& s, bool depth_ready,
                      uint32_t* sorted_keys, uint32_t* sorted_vals, uint32_t* ranges,
-                     uint32_t* d_num_keys, DevStatus* status, int sm_count, cudaStream_t st);
+                     uint32_t* d_num_keys, DevStatus* status, int sm_count, cudaStream_t st,
+                     void (*mark)(void* const*, int, cudaStream_t) = nullptr, void* const* events = nullptr,
+                     int first_event = 0);
 
 void launch_render_fwd(const float* proj, const ViewInfo* vt, int V, int64_t n, int tile,
                        const uint32_t* vals, const uint32_t* ranges, float3 bg, float* image,

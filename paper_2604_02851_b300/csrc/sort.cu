@@ -521,7 +521,8 @@ template <int BITS, int ITEMS>
 void emit_and_sort(const uint32_t* dv_sorted, int64_t items, int64_t n, const uint4* pr, const ViewInfo* vt,
                    int64_t keys_cap, int key_bits, const SortScratch& s, uint32_t* sorted_keys,
                    uint32_t* sorted_vals, uint32_t* ranges, int64_t total_tiles, uint32_t* d_num_keys,
-                   DevStatus* status, int sm_count, cudaStream_t st) {
+                   DevStatus* status, int sm_count, cudaStream_t st,
+                   void (*mark)(void* const*, int, cudaStream_t), void* const* events, int ev) {
     constexpr int R = 1 << BITS;
     const int passes = (key_bits + BITS - 1) / BITS;
     const int64_t nblk = (items + kEmitBlock - 1) / kEmitBlock;
@@ -531,6 +532,7 @@ void emit_and_sort(const uint32_t* dv_sorted, int64_t items, int64_t n, const ui
     k_emit<BITS><<<(unsigned)nblk, kEmitThreads, 0, st>>>(dv_sorted, items, n, pr, vt, keys_cap, s.tkeys[0],
                                                           s.tvals[0], s.emit_lookback, s.counters + 7,
                                                           d_num_keys, passes, s.hist, status);
+    if (mark) mark(events, ev, st);
     k_ranges_init<<<sm_count * 2, 256, 0, st>>>(reinterpret_cast<uint2*>(ranges), total_tiles);
     // with 3 or more passes the output keys also serve as a temporary
     uint32_t* kout = sorted_keys ? sorted_keys : (passes >= 3 ? s.tkeys[2] : nullptr);
@@ -586,7 +588,8 @@ void carve_sort_scratch(char* base, int V, int64_t n, int64_t keys_cap, SortScra
 void launch_bin_sort(const float* proj, const ViewInfo* vt, int V, int64_t n, int64_t keys_cap,
                      int64_t total_tiles, int sort_bits, int sort_items, const SortScratch& s, bool depth_ready,
                      uint32_t* sorted_keys, uint32_t* sorted_vals, uint32_t* ranges,
-                     uint32_t* d_num_keys, DevStatus* status, int sm_count, cudaStream_t st) {
+                     uint32_t* d_num_keys, DevStatus* status, int sm_count, cudaStream_t st,
+                     void (*mark)(void* const*, int, cudaStream_t), void* const* events, int first_event) {
     const int64_t items = (int64_t)V * n;
     const uint4* pr = reinterpret_cast<const uint4*>(proj);
     if (items == 0) {
@@ -601,12 +604,14 @@ void launch_bin_sort(const float* proj, const ViewInfo* vt, int V, int64_t n, in
     // 4 passes (even): in -> tmp -> out -> tmp -> out, so out may alias in
     sort_pairs(s.dkeys[0], s.dvals[0], s.dkeys[1], s.dvals[1], s.dkeys[0], s.dvals[0],
                s.d_count_depth, items, 32, 8, s, status, sm_count, st);
+    if (mark) mark(events, first_event, st);
     // 2. emission in depth order with the tile-key histograms, 3. stable sort
     //    by tile key into the caller's arrays with per-tile ranges
     int bits = 1;
     while ((1LL << bits) < total_tiles) ++bits;
 #define GS_EMIT_SORT(B, I) emit_and_sort<B, I>(s.dvals[0], items, n, pr, vt, keys_cap, bits, s, sorted_keys, \
-                                                 sorted_vals, ranges, total_tiles, d_num_keys, status, sm_count, st)
+                                                 sorted_vals, ranges, total_tiles, d_num_keys, status, sm_count, st, \
+                                                 mark, events, first_event + 1)
     const int it = sort_items == 8 ? 8 : (sort_items == 16 ? 16 : 12);
     switch (sort_bits * 100 + it) {
         case 408: GS_EMIT_SORT(4, 8); break;
