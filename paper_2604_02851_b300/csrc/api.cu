@@ -211,8 +211,8 @@ gs_status_t gs_project(gs_ctx* ctx, const gs_scene* scene, const gs_camera* d_ca
     if (check_ws(ctx, c.off)) return GS_ERR_CAPACITY;
     DeviceGuard g(ctx->device);
     launch_view_table(d_cams, n_views, ctx->tile, vt, -1, ctx->d_status, S(stream));
-    launch_project(scene->params, scene->n, scene->sh_degree, d_cams, vt, n_views, ctx->tile, proj,
-                   nullptr, nullptr, S(stream));
+    launch_project(scene->params, scene->n, scene->sh_degree, d_cams, vt, n_views, ctx->tile, proj, nullptr,
+                   S(stream));
     return launch_check();
 }
 
@@ -345,7 +345,7 @@ gs_status_t gs_render_batch(gs_ctx* ctx, const gs_scene* scene, const gs_camera*
     const float3 b = bg ? make_float3(bg[0], bg[1], bg[2]) : make_float3(0.f, 0.f, 0.f);
     launch_view_table(d_cams, n_requests, ctx->tile, p.vt, total_tiles, ctx->d_status, st);
     launch_project(scene->params, scene->n, scene->sh_degree, d_cams, p.vt, n_requests, ctx->tile, p.proj,
-                   s.dkeys[0], s.dvals[0], st);
+                   s.dkv[0], st);
     launch_bin_sort(p.proj, p.vt, n_requests, scene->n, keys_cap, total_tiles, ctx->sort_bits, ctx->sort_items, s, true, nullptr,
                     p.vals, p.ranges, p.n_keys, ctx->d_status, ctx->sm_count, st);
     launch_render_fwd(p.proj, p.vt, n_requests, scene->n, ctx->tile, p.vals, p.ranges, b, image, nullptr,
@@ -392,7 +392,7 @@ gs_status_t gs_train_step_events(gs_ctx* ctx, const gs_camera* d_cams, const gs_
     const float3 b = make_float3(cfg->bg[0], cfg->bg[1], cfg->bg[2]);
     mark(ev, 0, st);
     launch_view_table(d_cams, V, B, p.vt, tt, ctx->d_status, st);
-    launch_project(io->params, n, cfg->sh_degree, d_cams, p.vt, V, B, p.proj, s.dkeys[0], s.dvals[0], st);
+    launch_project(io->params, n, cfg->sh_degree, d_cams, p.vt, V, B, p.proj, s.dkv[0], st);
     mark(ev, 1, st);
     launch_bin_sort(p.proj, p.vt, V, n, cfg->keys_cap, tt, ctx->sort_bits, ctx->sort_items, s, true, nullptr,
                     p.vals, p.ranges, p.n_keys, ctx->d_status, ctx->sm_count, st, ev ? mark : nullptr, ev, 2);

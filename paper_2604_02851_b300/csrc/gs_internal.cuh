@@ -49,23 +49,23 @@ constexpr long long kSpinCycles = 2000000000LL;
 void launch_view_table(const gs_camera* d_cams, int V, int tile, ViewInfo* vt,
                        long long expect_tiles, DevStatus* status, cudaStream_t st);
 
+// depth_kv (may be null): packed (float32 depth bits << 32 | record index)
+// per (view, Gaussian), all-ones depth when culled, for the depth sort.
 void launch_project(const float* params, int64_t n, int sh_degree, const gs_camera* d_cams,
-                    const ViewInfo* vt, int V, int tile, float* proj, uint32_t* depth_keys,
-                    uint32_t* depth_vals, cudaStream_t st);
+                    const ViewInfo* vt, int V, int tile, float* proj, uint64_t* depth_kv, cudaStream_t st);
 
 void launch_project_bwd(const float* params, int64_t n, int sh_degree, const gs_camera* d_cams,
                         int V, const float* proj, const float* grad2d, float* dparams,
                         int accumulate, cudaStream_t st);
 
 // Scratch of the bin/sort stage (all device pointers inside the workspace).
+// Sorted items are packed (key << 32 | value).
 struct SortScratch {
-    uint32_t* dkeys[2];        // depth sort ping-pong, V*n each
-    uint32_t* dvals[2];
+    uint64_t* dkv[2];          // depth sort ping-pong, V*n each
     unsigned long long* emit_lookback;  // emission block look-back (one word per block)
-    uint32_t* tkeys[3];        // tile-key input / temporary / default output, keys_cap each
-    uint32_t* tvals[2];
+    uint64_t* tkv[2];          // tile-key sort ping-pong, keys_cap each
     uint32_t* hist;            // [4][256]
-    uint32_t* counters;        // [8] onesweep tile counters (+ misc)
+    uint32_t* counters;        // [8] onesweep tile counters (+ emission block counter)
     unsigned long long* lookback;  // [4][max_tiles][256]
     int64_t max_sort_tiles;    // per pass
     uint32_t* d_count_depth;   // V*n as a device scalar
@@ -103,15 +103,6 @@ void launch_adam(float* theta, const float* grad, float* m, float* v, int64_t n,
 size_t delta_scratch_bytes(int64_t n);
 void launch_delta(const float* theta, float* baseline, int64_t n, float thr, uint32_t* d_idx,
                   uint8_t* d_records, uint32_t* d_count, char* scratch, cudaStream_t st);
-
-// Stable sort of (key, value) pairs by the low key_bits bits of the key.
-// Pass p writes (kout, vout) when (passes - 1 - p) is even, else the
-// temporaries; the temporaries must differ from input and output, and the
-// output may alias the input only when the pass count is even.
-void sort_pairs(const uint32_t* kin, const uint32_t* vin, uint32_t* ktmp, uint32_t* vtmp,
-                uint32_t* kout, uint32_t* vout, const uint32_t* d_count, int64_t cap, int key_bits,
-                int digit_bits, const SortScratch& s, DevStatus* status, int sm_count,
-                cudaStream_t st);
 
 // Exclusive scan of `count` uint32 block sums in place (one block); the total
 // goes to *d_total; if cap >= 0 and the total exceeds it, GS_ERR_CAPACITY.

@@ -214,7 +214,7 @@ template <int D>
 __global__ void __launch_bounds__(256)
 k_project(const float4* __restrict__ P, int64_t n, const gs_camera* __restrict__ cams,
           const ViewInfo* __restrict__ vt, int V, int tile, float4* __restrict__ proj,
-          uint32_t* __restrict__ dkeys, uint32_t* __restrict__ dvals) {
+          uint64_t* __restrict__ dkv) {
     const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= n) return;
     constexpr int NB = (D + 1) * (D + 1);
@@ -248,10 +248,7 @@ k_project(const float4* __restrict__ P, int64_t n, const gs_camera* __restrict__
         if (!ok) {
             const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
             out[0] = z; out[1] = z; out[2] = z; out[3] = z;
-            if (dkeys) {
-                dkeys[rec] = 0xFFFFFFFFu;
-                dvals[rec] = (uint32_t)rec;
-            }
+            if (dkv) dkv[rec] = (0xFFFFFFFFull << 32) | (uint32_t)rec;
             continue;
         }
         float Y[16];
@@ -274,16 +271,13 @@ k_project(const float4* __restrict__ P, int64_t n, const gs_camera* __restrict__
         const uint32_t lo = (uint32_t)x0 | ((uint32_t)y0 << 16), hi = (uint32_t)x1 | ((uint32_t)y1 << 16);
         out[3] = make_float4(__uint_as_float(lo), __uint_as_float(hi),
                              __uint_as_float((uint32_t)((x1 - x0) * (y1 - y0))), 0.f);
-        if (dkeys) {
-            dkeys[rec] = __float_as_uint(Vg.tz);
-            dvals[rec] = (uint32_t)rec;
-        }
+        if (dkv) dkv[rec] = ((uint64_t)__float_as_uint(Vg.tz) << 32) | (uint32_t)rec;
     }
 }
 
 // ------------------------------------------------------------------ adjoint
 template <int D>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(128, 4)
 k_project_bwd(const float4* __restrict__ P, int64_t n, const gs_camera* __restrict__ cams, int V,
               const float4* __restrict__ proj, const float4* __restrict__ g2d,
               float4* __restrict__ dP, int accumulate) {
@@ -293,13 +287,11 @@ k_project_bwd(const float4* __restrict__ P, int64_t n, const gs_camera* __restri
     constexpr int NPL = (3 * NB + 3) / 4;
     Gauss G;
     load_gauss(P, n, g, G);
-    float sh[NPL * 4], dsh[NPL * 4];
+    // the SH coefficients are re-read per view (L1 hits) rather than held in
+    // registers next to their gradient, to keep the thread's footprint small
+    float dsh[NPL * 4];
 #pragma unroll
-    for (int pl = 0; pl < NPL; ++pl) {
-        const float4 c = P[(3 + pl) * n + g];
-        sh[4 * pl] = c.x; sh[4 * pl + 1] = c.y; sh[4 * pl + 2] = c.z; sh[4 * pl + 3] = c.w;
-        dsh[4 * pl] = dsh[4 * pl + 1] = dsh[4 * pl + 2] = dsh[4 * pl + 3] = 0.f;
-    }
+    for (int pl = 0; pl < NPL; ++pl) dsh[4 * pl] = dsh[4 * pl + 1] = dsh[4 * pl + 2] = dsh[4 * pl + 3] = 0.f;
     float dmx = 0.f, dmy = 0.f, dmz = 0.f, dlogit = 0.f;
     float D00 = 0.f, D01 = 0.f, D02 = 0.f, D11 = 0.f, D12 = 0.f, D22 = 0.f;  // dSigma + dSigma^T
     for (int v = 0; v < V; ++v) {
@@ -318,16 +310,23 @@ k_project_bwd(const float4* __restrict__ P, int64_t n, const gs_camera* __restri
         // colour -> SH coefficients and view direction
         float Y[16];
         sh_basis<D>(Vg.dir.x, Vg.dir.y, Vg.dir.z, Y);
+        float gm[3];
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) gm[ch] = (mask & (1u << ch)) ? 0.f : grgb[ch];
         float wsum[16];
 #pragma unroll
         for (int k = 0; k < 16; ++k) wsum[k] = 0.f;
 #pragma unroll
-        for (int ch = 0; ch < 3; ++ch) {
-            if (mask & (1u << ch)) continue;
+        for (int pl = 0; pl < NPL; ++pl) {
+            const float4 c4 = __ldg(&P[(3 + pl) * n + g]);
+            const float cv[4] = {c4.x, c4.y, c4.z, c4.w};
 #pragma unroll
-            for (int k = 0; k < NB; ++k) {
-                dsh[3 * k + ch] += grgb[ch] * Y[k];
-                wsum[k] += grgb[ch] * sh[3 * k + ch];
+            for (int e = 0; e < 4; ++e) {
+                const int j = 4 * pl + e;
+                if (j >= 3 * NB) break;
+                const int k = j / 3, ch = j % 3;
+                dsh[j] += gm[ch] * Y[k];
+                wsum[k] += gm[ch] * cv[e];
             }
         }
         const float3 ddir = sh_basis_vjp<D>(Vg.dir.x, Vg.dir.y, Vg.dir.z, wsum);
@@ -475,18 +474,17 @@ void launch_view_table(const gs_camera* d_cams, int V, int tile, ViewInfo* vt, l
 }
 
 void launch_project(const float* params, int64_t n, int sh_degree, const gs_camera* d_cams,
-                    const ViewInfo* vt, int V, int tile, float* proj, uint32_t* depth_keys,
-                    uint32_t* depth_vals, cudaStream_t st) {
+                    const ViewInfo* vt, int V, int tile, float* proj, uint64_t* depth_kv, cudaStream_t st) {
     if (n <= 0) return;
     const int threads = 256;
     const unsigned blocks = (unsigned)((n + threads - 1) / threads);
     const float4* P = reinterpret_cast<const float4*>(params);
     float4* out = reinterpret_cast<float4*>(proj);
     switch (sh_degree) {
-        case 0: k_project<0><<<blocks, threads, 0, st>>>(P, n, d_cams, vt, V, tile, out, depth_keys, depth_vals); break;
-        case 1: k_project<1><<<blocks, threads, 0, st>>>(P, n, d_cams, vt, V, tile, out, depth_keys, depth_vals); break;
-        case 2: k_project<2><<<blocks, threads, 0, st>>>(P, n, d_cams, vt, V, tile, out, depth_keys, depth_vals); break;
-        default: k_project<3><<<blocks, threads, 0, st>>>(P, n, d_cams, vt, V, tile, out, depth_keys, depth_vals); break;
+        case 0: k_project<0><<<blocks, threads, 0, st>>>(P, n, d_cams, vt, V, tile, out, depth_kv); break;
+        case 1: k_project<1><<<blocks, threads, 0, st>>>(P, n, d_cams, vt, V, tile, out, depth_kv); break;
+        case 2: k_project<2><<<blocks, threads, 0, st>>>(P, n, d_cams, vt, V, tile, out, depth_kv); break;
+        default: k_project<3><<<blocks, threads, 0, st>>>(P, n, d_cams, vt, V, tile, out, depth_kv); break;
     }
 }
 

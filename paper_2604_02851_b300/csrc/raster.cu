@@ -8,9 +8,9 @@
 // serve several pixels.
 //
 // Forward: per pixel, alpha = min(0.99, o e^P) with P the conic quadratic
-// form, skipped when P > 0 or alpha < 1/255 (tested as P < -ln(255 o) before
-// the exponential); compositing stops before the fragment that would take T
-// below 1e-4.  A block leaves as soon as every pixel is done (block vote).
+// form, skipped when P > 0 or alpha < 1/255 (tested as P log2(e) <
+// -log2(255 o) before the exponential, which is evaluated in base 2);
+// compositing stops before the fragment that would take T below 1e-4.  A block leaves as soon as every pixel is done (block vote).
 //
 // Backward: no per-fragment state is stored.  Each pixel starts from its
 // final transmittance and last-contributor position and walks its list
@@ -39,10 +39,20 @@ __device__ __forceinline__ int find_view(const ViewInfo* __restrict__ vt, int V,
 // shared-memory reads of a fragment and the warp reductions of its gradient
 // are shared by PX pixels.
 constexpr int kTPR = 4;
+constexpr float kLog2e = 1.4426950408889634f;
 
-// The cut-off alpha < 1/255 is tested in the log domain before the
-// exponential: o e^P < 1/255  <=>  P < -ln(255 o).
-__device__ __forceinline__ float cutoff_log(float o) { return -__logf(255.f * o); }
+// The exponent is evaluated in base 2: with q = -log2(e)/2 (A, 2B, C), the
+// quadratic form P log2(e) = (qA dx + qB dy) dx + qC dy^2 and e^P = 2^(P log2 e);
+// the cut-off alpha < 1/255, o e^P < 1/255, is P log2(e) < -log2(255 o).
+__device__ __forceinline__ float ex2(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float4 log2_conic(float4 co) {
+    return make_float4(-0.5f * kLog2e * co.x, -kLog2e * co.y, -0.5f * kLog2e * co.z, 0.f);
+}
+__device__ __forceinline__ float cutoff_log2(float o) { return -__log2f(255.f * o); }
 
 template <int B>
 __global__ void __launch_bounds__(B * kTPR)
@@ -52,8 +62,8 @@ k_render_fwd(const float4* __restrict__ proj, const ViewInfo* __restrict__ vt, i
     constexpr int NT = B * kTPR;       // threads per block
     constexpr int PX = B / kTPR;       // pixels per thread
     constexpr int BATCH = 2 * NT;      // fragments staged per round
-    __shared__ float4 s_a[BATCH];      // u, v, opacity, log cut-off
-    __shared__ float4 s_b[BATCH];      // conic A, B, C
+    __shared__ float4 s_a[BATCH];      // u, v, opacity, log2 cut-off
+    __shared__ float4 s_q[BATCH];      // base-2 conic coefficients
     __shared__ float4 s_c[BATCH];      // r, g, b
     const int64_t gt = blockIdx.x;
     if (gt >= vt[V].tile_off) return;
@@ -64,6 +74,7 @@ k_render_fwd(const float4* __restrict__ proj, const ViewInfo* __restrict__ vt, i
     const int px0 = (lt % vi.tx) * B + ((int)threadIdx.x % kTPR) * PX;
     const int py = (lt / vi.tx) * B + row;
     const float fy = (float)py + 0.5f;
+    const float fx0 = (float)px0 + 0.5f;
     const uint2 rg = ranges[gt];
     const int64_t rbase = (int64_t)v * n;
 
@@ -84,8 +95,8 @@ k_render_fwd(const float4* __restrict__ proj, const ViewInfo* __restrict__ vt, i
             if (idx < rg.y) {
                 const int64_t r = (rbase + vals[idx]) * 4;
                 const float4 a = proj[r], b = proj[r + 1], c = proj[r + 2];
-                s_a[slot] = make_float4(a.x, a.y, a.w, cutoff_log(a.w));
-                s_b[slot] = b;
+                s_a[slot] = make_float4(a.x, a.y, a.w, cutoff_log2(a.w));
+                s_q[slot] = log2_conic(b);
                 s_c[slot] = c;
             }
         }
@@ -93,17 +104,18 @@ k_render_fwd(const float4* __restrict__ proj, const ViewInfo* __restrict__ vt, i
         const int cnt = (int)min((uint32_t)BATCH, rg.y - start);
         for (int j = 0; j < cnt && live; ++j) {
             const float4 a = s_a[j];
-            const float4 co = s_b[j];
+            const float4 q = s_q[j];
             const float dy = a.y - fy;
-            const float cyy = -0.5f * co.z * dy * dy;
-            const float by = co.y * dy;
+            const float qb = q.y * dy;
+            const float qc = q.z * dy * dy;
+            const float dx0 = a.x - fx0;
 #pragma unroll
             for (int k = 0; k < PX; ++k) {
                 if (!(live & (1u << k))) continue;
-                const float dx = a.x - ((float)(px0 + k) + 0.5f);
-                const float P = (-0.5f * co.x * dx - by) * dx + cyy;
-                if (P > 0.f || P < a.w) continue;
-                const float al = fminf(kAlphaMax, a.z * __expf(P));
+                const float dx = dx0 - (float)k;
+                const float P2 = (q.x * dx + qb) * dx + qc;
+                if (P2 > 0.f || P2 < a.w) continue;
+                const float al = fminf(kAlphaMax, a.z * ex2(P2));
                 const float Tn = T[k] * (1.f - al);
                 if (Tn < kTMin) { live &= ~(1u << k); continue; }
                 const float4 c = s_c[j];
@@ -135,6 +147,13 @@ __device__ __forceinline__ float warp_sum(float x) {
     return x;
 }
 
+// Geometry gradients from five sums over a fragment's pixels:
+//   S1 = sum dP dx, S2 = sum dP dy, S3 = sum dP dx^2, S4 = sum dP dx dy,
+//   S5 = sum dP dy^2  (dP = dL/dP, dx = u - px, dy = v - py), so that
+//   dL/du = -A S1 - B S2, dL/dv = -C S2 - B S1,
+//   dL/dA = -S3 / 2, dL/dB = -S4, dL/dC = -S5 / 2.
+// A thread's pixels share one row (one dy): it keeps sum dP, sum dP dx and
+// sum dP dx^2 per pixel and forms S2, S4, S5 with its dy once per fragment.
 template <int B>
 __global__ void __launch_bounds__(B * kTPR)
 k_raster_bwd(const float4* __restrict__ proj, const ViewInfo* __restrict__ vt, int V, int64_t n,
@@ -144,7 +163,8 @@ k_raster_bwd(const float4* __restrict__ proj, const ViewInfo* __restrict__ vt, i
     constexpr int NT = B * kTPR;
     constexpr int PX = B / kTPR;
     constexpr int BATCH = NT;
-    __shared__ float4 s_a[BATCH];   // u, v, opacity, log cut-off
+    __shared__ float4 s_a[BATCH];   // u, v, opacity, log2 cut-off
+    __shared__ float4 s_q[BATCH];   // base-2 conic coefficients
     __shared__ float4 s_b[BATCH];   // conic A, B, C
     __shared__ float4 s_c[BATCH];   // r, g, b
     __shared__ uint32_t s_g[BATCH];
@@ -159,6 +179,7 @@ k_raster_bwd(const float4* __restrict__ proj, const ViewInfo* __restrict__ vt, i
     const int px0 = (lt % vi.tx) * B + ((int)threadIdx.x % kTPR) * PX;
     const int py = (lt / vi.tx) * B + row;
     const float fy = (float)py + 0.5f;
+    const float fx0 = (float)px0 + 0.5f;
     const uint2 rg = ranges[gt];
     const int64_t rbase = (int64_t)v * n;
     const int lane = threadIdx.x & 31;
@@ -195,7 +216,8 @@ k_raster_bwd(const float4* __restrict__ proj, const ViewInfo* __restrict__ vt, i
             const uint32_t g = vals[rg.x + bstart + threadIdx.x];
             const int64_t r = (rbase + g) * 4;
             const float4 a = proj[r], b = proj[r + 1], c = proj[r + 2];
-            s_a[threadIdx.x] = make_float4(a.x, a.y, a.w, cutoff_log(a.w));
+            s_a[threadIdx.x] = make_float4(a.x, a.y, a.w, cutoff_log2(a.w));
+            s_q[threadIdx.x] = log2_conic(b);
             s_b[threadIdx.x] = b;
             s_c[threadIdx.x] = c;
             s_g[threadIdx.x] = g;
@@ -207,53 +229,56 @@ k_raster_bwd(const float4* __restrict__ proj, const ViewInfo* __restrict__ vt, i
             const uint32_t pos = bstart + (uint32_t)j;
             if (!__any_sync(0xFFFFFFFFu, pos < mylast)) continue;
             const float4 a = s_a[j];
-            const float4 co = s_b[j];
+            const float4 q = s_q[j];
             const float4 c = s_c[j];
             const float dy = a.y - fy;
-            const float cyy = -0.5f * co.z * dy * dy;
-            const float by = co.y * dy;
-            float g0 = 0.f, g1 = 0.f, g2 = 0.f, g3 = 0.f, g4 = 0.f, g5 = 0.f, g6 = 0.f, g7 = 0.f, g8 = 0.f;
+            const float qb = q.y * dy;
+            const float qc = q.z * dy * dy;
+            const float dx0 = a.x - fx0;
+            float s0 = 0.f, s1 = 0.f, s2 = 0.f, g5 = 0.f, g6 = 0.f, g7 = 0.f, g8 = 0.f;
             bool contrib = false;
 #pragma unroll
             for (int k = 0; k < PX; ++k) {
                 if (pos >= last[k]) continue;
-                const float dx = a.x - ((float)(px0 + k) + 0.5f);
-                const float P = (-0.5f * co.x * dx - by) * dx + cyy;
-                if (P > 0.f || P < a.w) continue;
+                const float dx = dx0 - (float)k;
+                const float P2 = (q.x * dx + qb) * dx + qc;
+                if (P2 > 0.f || P2 < a.w) continue;
                 contrib = true;
-                const float G = __expf(P);
+                const float G = ex2(P2);
                 const float raw = a.z * G;
                 const float al = fminf(kAlphaMax, raw);
-                const float Tj = T[k] / (1.f - al);
+                const float Tj = T[k] * __frcp_rn(1.f - al);
                 T[k] = Tj;
                 const float w = al * Tj;
                 g6 += w * dCr[k]; g7 += w * dCg[k]; g8 += w * dCb[k];
-                const float dal = Tj * (dCr[k] * (c.x - Rr[k]) + dCg[k] * (c.y - Rg[k]) + dCb[k] * (c.z - Rb[k]));
-                Rr[k] += al * (c.x - Rr[k]);
-                Rg[k] += al * (c.y - Rg[k]);
-                Rb[k] += al * (c.z - Rb[k]);
-                if (raw <= kAlphaMax) {
-                    const float dP = dal * raw;
-                    g5 += dal * G;
-                    g2 += dP * (-0.5f * dx * dx);
-                    g3 += dP * (-dx * dy);
-                    g4 += dP * (-0.5f * dy * dy);
-                    g0 += dP * (-co.x * dx - co.y * dy);
-                    g1 += dP * (-co.z * dy - co.y * dx);
-                }
+                const float er = c.x - Rr[k], eg = c.y - Rg[k], eb = c.z - Rb[k];
+                const float dal = Tj * (dCr[k] * er + dCg[k] * eg + dCb[k] * eb);
+                Rr[k] += al * er;
+                Rg[k] += al * eg;
+                Rb[k] += al * eb;
+                const bool free = raw <= kAlphaMax;
+                const float dP = free ? dal * raw : 0.f;
+                g5 += free ? dal * G : 0.f;
+                const float t = dP * dx;
+                s0 += dP;
+                s1 += t;
+                s2 += t * dx;
             }
             if (__any_sync(0xFFFFFFFFu, contrib)) {
-                g0 = warp_sum(g0); g1 = warp_sum(g1); g2 = warp_sum(g2);
-                g3 = warp_sum(g3); g4 = warp_sum(g4); g5 = warp_sum(g5);
-                g6 = warp_sum(g6); g7 = warp_sum(g7); g8 = warp_sum(g8);
+                float S1 = warp_sum(s1), S2 = warp_sum(s0 * dy), S3 = warp_sum(s2);
+                float S4 = warp_sum(s1 * dy), S5 = warp_sum(s0 * dy * dy);
+                g5 = warp_sum(g5); g6 = warp_sum(g6); g7 = warp_sum(g7); g8 = warp_sum(g8);
                 if (lane == 0) {
+                    const float4 co = s_b[j];
+                    const float gu = -co.x * S1 - co.y * S2, gv = -co.z * S2 - co.y * S1;
+                    const float gA = -0.5f * S3, gB = -S4, gC = -0.5f * S5;
                     if (NT == 32) {
-                        s_acc[0][j] += g0; s_acc[1][j] += g1; s_acc[2][j] += g2;
-                        s_acc[3][j] += g3; s_acc[4][j] += g4; s_acc[5][j] += g5;
+                        s_acc[0][j] += gu; s_acc[1][j] += gv; s_acc[2][j] += gA;
+                        s_acc[3][j] += gB; s_acc[4][j] += gC; s_acc[5][j] += g5;
                         s_acc[6][j] += g6; s_acc[7][j] += g7; s_acc[8][j] += g8;
                     } else {
-                        atomicAdd(&s_acc[0][j], g0); atomicAdd(&s_acc[1][j], g1); atomicAdd(&s_acc[2][j], g2);
-                        atomicAdd(&s_acc[3][j], g3); atomicAdd(&s_acc[4][j], g4); atomicAdd(&s_acc[5][j], g5);
+                        atomicAdd(&s_acc[0][j], gu); atomicAdd(&s_acc[1][j], gv); atomicAdd(&s_acc[2][j], gA);
+                        atomicAdd(&s_acc[3][j], gB); atomicAdd(&s_acc[4][j], gC); atomicAdd(&s_acc[5][j], g5);
                         atomicAdd(&s_acc[6][j], g6); atomicAdd(&s_acc[7][j], g7); atomicAdd(&s_acc[8][j], g8);
                     }
                 }

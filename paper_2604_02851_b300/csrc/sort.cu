@@ -105,9 +105,10 @@ __device__ __forceinline__ bool look_back(unsigned long long* lb, int64_t slot, 
 }
 
 // ------------------------------------------------------------ histograms
+// Items are packed (key << 32 | value); digits are taken from the key.
 template <int BITS>
 __global__ void __launch_bounds__(kThreads)
-k_hist(const uint32_t* __restrict__ keys, const uint32_t* d_count, int64_t cap, int passes,
+k_hist(const uint64_t* __restrict__ items, const uint32_t* d_count, int64_t cap, int passes,
        uint32_t* __restrict__ hist) {
     constexpr int R = 1 << BITS;
     __shared__ uint32_t sh[kWarps][kMaxPasses][R];
@@ -117,7 +118,7 @@ k_hist(const uint32_t* __restrict__ keys, const uint32_t* d_count, int64_t cap, 
     const int w = threadIdx.x / 32;
     for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < count;
          i += (int64_t)gridDim.x * kThreads) {
-        const uint32_t k = keys[i];
+        const uint32_t k = (uint32_t)(items[i] >> 32);
         for (int p = 0; p < passes; ++p) atomicAdd(&sh[w][p][(k >> (p * BITS)) & (R - 1)], 1u);
     }
     __syncthreads();
@@ -148,21 +149,20 @@ __global__ void k_hist_scan(uint32_t* hist, int passes) {
 }
 
 // ------------------------------------------------------------ onesweep pass
-// ITEMS keys per thread, 256 threads: a tile of 256*ITEMS keys.  kout may be
-// null (keys not needed after this pass); ranges non-null makes this the last
-// pass of the tile-key sort, recording per-key [start, end).
+// ITEMS packed (key << 32 | value) items per thread, 256 threads: a tile of
+// 256*ITEMS.  Outputs: out (packed, for the next pass) and/or, on the last
+// pass of the tile-key sort, vout (values), kout (keys, may be null) and the
+// per-key [start, end) ranges.
 template <int BITS, int ITEMS>
 __global__ void __launch_bounds__(kThreads, 2)
-k_onesweep(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
-           uint32_t* __restrict__ kout, uint32_t* __restrict__ vout, const uint32_t* d_count,
-           int64_t cap, int shift, const uint32_t* __restrict__ digit_off,
-           unsigned long long* __restrict__ lookback, uint32_t* tile_counter,
-           uint32_t* __restrict__ ranges, DevStatus* status) {
+k_onesweep(const uint64_t* __restrict__ in, uint64_t* __restrict__ out, uint32_t* __restrict__ kout,
+           uint32_t* __restrict__ vout, const uint32_t* d_count, int64_t cap, int shift,
+           const uint32_t* __restrict__ digit_off, unsigned long long* __restrict__ lookback,
+           uint32_t* tile_counter, uint32_t* __restrict__ ranges, DevStatus* status) {
     constexpr int R = 1 << BITS;
     constexpr uint32_t MASK = R - 1;
     constexpr int TILE = kThreads * ITEMS;
-    __shared__ uint32_t s_keys[TILE];
-    __shared__ uint32_t s_vals[TILE];
+    __shared__ uint64_t s_items[TILE];
     __shared__ uint32_t s_whist[kWarps][R];   // per-warp digit counts, then warp prefixes
     __shared__ uint32_t s_local[R];           // tile-local start of each digit
     __shared__ uint32_t s_gbase[R];           // global start of this tile's digit run
@@ -173,6 +173,7 @@ k_onesweep(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
     const int64_t n_tiles = (count + TILE - 1) / TILE;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t lt = lanemask_lt();
+    const int kshift = 32 + shift;
 
     for (;;) {
         if (threadIdx.x == 0) { s_tile = atomicAdd(tile_counter, 1u); s_abort = 0; }
@@ -181,15 +182,19 @@ k_onesweep(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
         const int64_t tile = s_tile;
         if (tile >= n_tiles) break;
 
-        // ---- load (warp-striped: warp w owns a contiguous run of 32*ITEMS)
-        uint32_t key[ITEMS], val[ITEMS], rank[ITEMS];
+        // ---- load (warp-striped: warp w owns a contiguous run of 32*ITEMS);
+        //      missing tail items get the all-ones key
+        uint64_t item[ITEMS];
+        uint32_t rank[ITEMS];
         const int64_t wbase = tile * TILE + (int64_t)warp * 32 * ITEMS;
+        const uint64_t* src = in + wbase + lane;
+        const int64_t wrem = count - wbase - lane;  // items this lane may read: j*32 < wrem
+        if (wrem > 32 * (ITEMS - 1)) {
 #pragma unroll
-        for (int j = 0; j < ITEMS; ++j) {
-            const int64_t idx = wbase + j * 32 + lane;
-            const bool ok = idx < count;
-            key[j] = ok ? kin[idx] : 0xFFFFFFFFu;
-            val[j] = ok ? vin[idx] : 0u;
+            for (int j = 0; j < ITEMS; ++j) item[j] = src[j * 32];
+        } else {
+#pragma unroll
+            for (int j = 0; j < ITEMS; ++j) item[j] = (j * 32 < wrem) ? src[j * 32] : ~0ULL;
         }
         // ---- stable rank within the warp, item order j*32 + lane: the lanes
         //      holding the same digit are found with one ballot per digit bit;
@@ -197,7 +202,7 @@ k_onesweep(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
         //      and shares the old value with its group
 #pragma unroll
         for (int j = 0; j < ITEMS; ++j) {
-            const uint32_t d = (key[j] >> shift) & MASK;
+            const uint32_t d = (uint32_t)(item[j] >> kshift) & MASK;
             uint32_t peers = 0xFFFFFFFFu;
 #pragma unroll
             for (int bit = 0; bit < BITS; ++bit) {
@@ -257,28 +262,29 @@ k_onesweep(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
         // ---- stage in shared memory in digit order
 #pragma unroll
         for (int j = 0; j < ITEMS; ++j) {
-            const uint32_t d = (key[j] >> shift) & MASK;
-            const uint32_t lp = s_local[d] + s_whist[warp][d] + rank[j];
-            s_keys[lp] = key[j];
-            s_vals[lp] = val[j];
+            const uint32_t d = (uint32_t)(item[j] >> kshift) & MASK;
+            s_items[s_local[d] + s_whist[warp][d] + rank[j]] = item[j];
         }
         __syncthreads();
-        // ---- scatter (invalid tail keys are all-ones: they sit at the end of
+        // ---- scatter (missing tail items are all-ones: they sit at the end of
         //      the last digit's run, i.e. at staged positions >= valid)
         const int64_t rem = count - tile * TILE;
         const int valid = rem < TILE ? (int)rem : TILE;
         if (!s_abort) {
             for (int i = threadIdx.x; i < valid; i += kThreads) {
-                const uint32_t k = s_keys[i];
+                const uint64_t it = s_items[i];
+                const uint32_t k = (uint32_t)(it >> 32);
                 const uint32_t d = (k >> shift) & MASK;
                 const uint32_t pos = s_gbase[d] + (uint32_t)i - s_local[d];
                 if ((int64_t)pos >= count) continue;  // unreachable when the histogram matches the keys
+                if (out) out[pos] = it;
+                if (vout) vout[pos] = (uint32_t)it;
                 if (kout) kout[pos] = k;
-                vout[pos] = s_vals[i];
                 if (ranges) {
                     // runs of equal keys are contiguous both here and in the output
-                    if (i == 0 || s_keys[i - 1] != k) atomicMin(&ranges[2 * (size_t)k], pos);
-                    if (i == valid - 1 || s_keys[i + 1] != k) atomicMax(&ranges[2 * (size_t)k + 1], pos + 1);
+                    if (i == 0 || (uint32_t)(s_items[i - 1] >> 32) != k) atomicMin(&ranges[2 * (size_t)k], pos);
+                    if (i == valid - 1 || (uint32_t)(s_items[i + 1] >> 32) != k)
+                        atomicMax(&ranges[2 * (size_t)k + 1], pos + 1);
                 }
             }
         }
@@ -323,13 +329,12 @@ __global__ void k_clear_u32(uint32_t* p, int64_t n) {
 
 // Depth-sort input from projection records: key = float32 depth bits of a
 // visible (view, Gaussian), all-ones when culled; value = record index.
-__global__ void k_depth_keys(const uint4* __restrict__ proj, int64_t items, uint32_t* __restrict__ keys,
-                             uint32_t* __restrict__ vals) {
+__global__ void k_depth_keys(const uint4* __restrict__ proj, int64_t items, uint64_t* __restrict__ kv) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= items) return;
     const uint32_t tiles = proj[i * 4 + 3].z;
-    keys[i] = tiles ? proj[i * 4].z : 0xFFFFFFFFu;
-    vals[i] = (uint32_t)i;
+    const uint32_t key = tiles ? proj[i * 4].z : 0xFFFFFFFFu;
+    kv[i] = ((uint64_t)key << 32) | (uint32_t)i;
 }
 
 // ------------------------------------------------------------ emission
@@ -352,8 +357,8 @@ __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t x, int lane) {
 // one contiguous range.
 template <int BITS>
 __global__ void __launch_bounds__(kEmitThreads)
-k_emit(const uint32_t* __restrict__ dvals, int64_t total, int64_t n, const uint4* __restrict__ proj,
-       const ViewInfo* __restrict__ vt, int64_t cap, uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
+k_emit(const uint64_t* __restrict__ dsorted, int64_t total, int64_t n, const uint4* __restrict__ proj,
+       const ViewInfo* __restrict__ vt, int64_t cap, uint64_t* __restrict__ kv,
        unsigned long long* __restrict__ lookback, uint32_t* block_counter, uint32_t* d_num_keys,
        int passes, uint32_t* __restrict__ hist, DevStatus* status) {
     constexpr int R = 1 << BITS;
@@ -378,7 +383,7 @@ k_emit(const uint32_t* __restrict__ dvals, int64_t total, int64_t n, const uint4
         cnt[r] = lo[r] = hi[r] = gi[r] = kb[r] = 0;
         tx[r] = 1;
         if (idx < total) {
-            const uint32_t rr = dvals[idx];
+            const uint32_t rr = (uint32_t)dsorted[idx];
             const uint4 p3 = proj[(size_t)rr * 4 + 3];
             const uint32_t v = (uint32_t)(rr / (uint64_t)n);
             cnt[r] = p3.z;
@@ -453,9 +458,7 @@ k_emit(const uint32_t* __restrict__ dvals, int64_t total, int64_t n, const uint4
                 const uint32_t ty = (uint32_t)(((float)j + 0.5f) * o_rw);
                 const uint32_t txx = j - ty * o_w;
                 key = o_kb + ((o_lo >> 16) + ty) * o_tx + (o_lo & 0xFFFFu) + txx;
-                const uint64_t pos = base + o;
-                keys[pos] = key;
-                vals[pos] = o_g;
+                kv[base + o] = ((uint64_t)key << 32) | o_g;
             }
             const uint32_t act = __ballot_sync(0xFFFFFFFFu, stored);
             if (stored) {
@@ -477,86 +480,51 @@ k_emit(const uint32_t* __restrict__ dvals, int64_t total, int64_t n, const uint4
 }
 
 // ------------------------------------------------------------ drivers
+// Passes over packed items: non-last passes ping-pong between buf[0] and
+// buf[1] (input in buf[0]); the last pass writes `last_out` (packed) or the
+// caller's value / key arrays and ranges.
 template <int BITS, int ITEMS>
-void onesweep_passes(const uint32_t* kin, const uint32_t* vin, uint32_t* ktmp, uint32_t* vtmp, uint32_t* kout,
-                     uint32_t* vout, const uint32_t* d_count, int64_t cap, int passes, const SortScratch& s,
-                     uint32_t* ranges, DevStatus* status, int sm_count, cudaStream_t st) {
+void onesweep_passes(uint64_t* const buf[2], uint64_t* last_out, uint32_t* kout, uint32_t* vout,
+                     const uint32_t* d_count, int64_t cap, int passes, const SortScratch& s, uint32_t* ranges,
+                     DevStatus* status, int sm_count, cudaStream_t st) {
     constexpr int R = 1 << BITS;
     k_clear_lookback<<<sm_count * 4, 256, 0, st>>>(s.lookback, d_count, cap, R, passes, s.max_sort_tiles,
                                                    kThreads * ITEMS);
     k_hist_scan<BITS><<<1, 256, 0, st>>>(s.hist, passes);
-    const uint32_t* src_k = kin;
-    const uint32_t* src_v = vin;
     for (int p = 0; p < passes; ++p) {
         const bool last = p == passes - 1;
-        const bool to_out = ((passes - 1 - p) % 2) == 0;
-        uint32_t* dk = to_out ? kout : ktmp;
-        uint32_t* dv = to_out ? vout : vtmp;
+        const uint64_t* src = buf[p % 2];
+        uint64_t* dst = last ? last_out : buf[(p + 1) % 2];
         k_onesweep<BITS, ITEMS><<<sm_count * 2, kThreads, 0, st>>>(
-            src_k, src_v, dk, dv, d_count, cap, p * BITS, s.hist + p * 256,
+            src, dst, last ? kout : nullptr, last ? vout : nullptr, d_count, cap, p * BITS, s.hist + p * 256,
             s.lookback + (int64_t)p * s.max_sort_tiles * R, s.counters + p, last ? ranges : nullptr, status);
-        src_k = dk;
-        src_v = dv;
     }
 }
 
-template <int BITS>
-void sort_pairs_bits(const uint32_t* kin, const uint32_t* vin, uint32_t* ktmp, uint32_t* vtmp,
-                     uint32_t* kout, uint32_t* vout, const uint32_t* d_count, int64_t cap,
-                     int key_bits, const SortScratch& s, DevStatus* status, int sm_count,
-                     cudaStream_t st) {
-    constexpr int R = 1 << BITS;
-    const int passes = (key_bits + BITS - 1) / BITS;
-    cudaMemsetAsync(s.hist, 0, sizeof(uint32_t) * kMaxPasses * 256, st);
-    cudaMemsetAsync(s.counters, 0, sizeof(uint32_t) * 8, st);
-    k_hist<BITS><<<sm_count * 4, kThreads, 0, st>>>(kin, d_count, cap, passes, s.hist);
-    onesweep_passes<BITS, 16>(kin, vin, ktmp, vtmp, kout, vout, d_count, cap, passes, s, nullptr, status, sm_count,
-                              st);
-}
-
-// Emission + tile-key sort + ranges, for one digit width.  The passes write
-// (keys, values) into tkeys/tvals temporaries and end in the caller's arrays:
-// an odd pass count goes input -> out, an even one input -> tmp -> out ...
+// Emission + tile-key sort + ranges, for one digit width.
 template <int BITS, int ITEMS>
-void emit_and_sort(const uint32_t* dv_sorted, int64_t items, int64_t n, const uint4* pr, const ViewInfo* vt,
+void emit_and_sort(const uint64_t* dsorted, int64_t items, int64_t n, const uint4* pr, const ViewInfo* vt,
                    int64_t keys_cap, int key_bits, const SortScratch& s, uint32_t* sorted_keys,
                    uint32_t* sorted_vals, uint32_t* ranges, int64_t total_tiles, uint32_t* d_num_keys,
                    DevStatus* status, int sm_count, cudaStream_t st,
                    void (*mark)(void* const*, int, cudaStream_t), void* const* events, int ev) {
-    constexpr int R = 1 << BITS;
     const int passes = (key_bits + BITS - 1) / BITS;
     const int64_t nblk = (items + kEmitBlock - 1) / kEmitBlock;
     cudaMemsetAsync(s.hist, 0, sizeof(uint32_t) * kMaxPasses * 256, st);
     cudaMemsetAsync(s.counters, 0, sizeof(uint32_t) * 8, st);
     cudaMemsetAsync(s.emit_lookback, 0, sizeof(unsigned long long) * (size_t)nblk, st);
-    k_emit<BITS><<<(unsigned)nblk, kEmitThreads, 0, st>>>(dv_sorted, items, n, pr, vt, keys_cap, s.tkeys[0],
-                                                          s.tvals[0], s.emit_lookback, s.counters + 7,
-                                                          d_num_keys, passes, s.hist, status);
+    k_emit<BITS><<<(unsigned)nblk, kEmitThreads, 0, st>>>(dsorted, items, n, pr, vt, keys_cap, s.tkv[0],
+                                                          s.emit_lookback, s.counters + 7, d_num_keys, passes,
+                                                          s.hist, status);
     if (mark) mark(events, ev, st);
     k_ranges_init<<<sm_count * 2, 256, 0, st>>>(reinterpret_cast<uint2*>(ranges), total_tiles);
-    // with 3 or more passes the output keys also serve as a temporary
-    uint32_t* kout = sorted_keys ? sorted_keys : (passes >= 3 ? s.tkeys[2] : nullptr);
-    onesweep_passes<BITS, ITEMS>(s.tkeys[0], s.tvals[0], s.tkeys[1], s.tvals[1], kout, sorted_vals, d_num_keys,
-                                 keys_cap, passes, s, ranges, status, sm_count, st);
+    uint64_t* const buf[2] = {s.tkv[0], s.tkv[1]};
+    onesweep_passes<BITS, ITEMS>(buf, nullptr, sorted_keys, sorted_vals, d_num_keys, keys_cap, passes, s, ranges,
+                                 status, sm_count, st);
     k_ranges_fix<<<sm_count * 2, 256, 0, st>>>(reinterpret_cast<uint2*>(ranges), total_tiles);
 }
 
 }  // namespace
-
-// Sort (key, value) pairs by the low `key_bits` bits of the key, stably.
-void sort_pairs(const uint32_t* kin, const uint32_t* vin, uint32_t* ktmp, uint32_t* vtmp,
-                uint32_t* kout, uint32_t* vout, const uint32_t* d_count, int64_t cap, int key_bits,
-                int digit_bits, const SortScratch& s, DevStatus* status, int sm_count,
-                cudaStream_t st) {
-    if (key_bits < 1) key_bits = 1;
-    switch (digit_bits) {
-        case 4: sort_pairs_bits<4>(kin, vin, ktmp, vtmp, kout, vout, d_count, cap, key_bits, s, status, sm_count, st); break;
-        case 5: sort_pairs_bits<5>(kin, vin, ktmp, vtmp, kout, vout, d_count, cap, key_bits, s, status, sm_count, st); break;
-        case 6: sort_pairs_bits<6>(kin, vin, ktmp, vtmp, kout, vout, d_count, cap, key_bits, s, status, sm_count, st); break;
-        case 7: sort_pairs_bits<7>(kin, vin, ktmp, vtmp, kout, vout, d_count, cap, key_bits, s, status, sm_count, st); break;
-        default: sort_pairs_bits<8>(kin, vin, ktmp, vtmp, kout, vout, d_count, cap, key_bits, s, status, sm_count, st); break;
-    }
-}
 
 size_t sort_scratch_bytes(int V, int64_t n, int64_t keys_cap) {
     SortScratch s;
@@ -567,16 +535,11 @@ size_t sort_scratch_bytes(int V, int64_t n, int64_t keys_cap) {
 void carve_sort_scratch(char* base, int V, int64_t n, int64_t keys_cap, SortScratch* s) {
     Carver c(base);
     const int64_t items = (int64_t)V * n;
-    s->dkeys[0] = c.take<uint32_t>(items);
-    s->dvals[0] = c.take<uint32_t>(items);
-    s->dkeys[1] = c.take<uint32_t>(items);
-    s->dvals[1] = c.take<uint32_t>(items);
+    s->dkv[0] = c.take<uint64_t>(items);
+    s->dkv[1] = c.take<uint64_t>(items);
     s->emit_lookback = c.take<unsigned long long>((items + kEmitBlock - 1) / kEmitBlock + 1);
-    s->tkeys[0] = c.take<uint32_t>(keys_cap);
-    s->tvals[0] = c.take<uint32_t>(keys_cap);
-    s->tkeys[1] = c.take<uint32_t>(keys_cap);
-    s->tvals[1] = c.take<uint32_t>(keys_cap);
-    s->tkeys[2] = c.take<uint32_t>(keys_cap);
+    s->tkv[0] = c.take<uint64_t>(keys_cap);
+    s->tkv[1] = c.take<uint64_t>(keys_cap);
     s->hist = c.take<uint32_t>(kMaxPasses * 256);
     s->counters = c.take<uint32_t>(8);
     s->max_sort_tiles = (std::max(items, keys_cap) + kMinTileKeys - 1) / kMinTileKeys + 1;
@@ -597,19 +560,25 @@ void launch_bin_sort(const float* proj, const ViewInfo* vt, int V, int64_t n, in
         k_set_u32<<<1, 1, 0, st>>>(d_num_keys, 0u);
         return;
     }
-    // 1. depth sort of all (view, Gaussian) pairs (32-bit keys, 8-bit digits)
+    // 1. depth sort of all (view, Gaussian) pairs: 32-bit keys, 4 passes of
+    //    8-bit digits ending back in dkv[0]
     if (!depth_ready)
-        k_depth_keys<<<(unsigned)((items + 255) / 256), 256, 0, st>>>(pr, items, s.dkeys[0], s.dvals[0]);
+        k_depth_keys<<<(unsigned)((items + 255) / 256), 256, 0, st>>>(pr, items, s.dkv[0]);
     k_set_u32<<<1, 1, 0, st>>>(s.d_count_depth, (uint32_t)items);
-    // 4 passes (even): in -> tmp -> out -> tmp -> out, so out may alias in
-    sort_pairs(s.dkeys[0], s.dvals[0], s.dkeys[1], s.dvals[1], s.dkeys[0], s.dvals[0],
-               s.d_count_depth, items, 32, 8, s, status, sm_count, st);
+    cudaMemsetAsync(s.hist, 0, sizeof(uint32_t) * kMaxPasses * 256, st);
+    cudaMemsetAsync(s.counters, 0, sizeof(uint32_t) * 8, st);
+    k_hist<8><<<sm_count * 4, kThreads, 0, st>>>(s.dkv[0], s.d_count_depth, items, 4, s.hist);
+    {
+        uint64_t* const dbuf[2] = {s.dkv[0], s.dkv[1]};
+        onesweep_passes<8, 16>(dbuf, s.dkv[0], nullptr, nullptr, s.d_count_depth, items, 4, s, nullptr, status,
+                               sm_count, st);
+    }
     if (mark) mark(events, first_event, st);
     // 2. emission in depth order with the tile-key histograms, 3. stable sort
     //    by tile key into the caller's arrays with per-tile ranges
     int bits = 1;
     while ((1LL << bits) < total_tiles) ++bits;
-#define GS_EMIT_SORT(B, I) emit_and_sort<B, I>(s.dvals[0], items, n, pr, vt, keys_cap, bits, s, sorted_keys, \
+#define GS_EMIT_SORT(B, I) emit_and_sort<B, I>(s.dkv[0], items, n, pr, vt, keys_cap, bits, s, sorted_keys, \
                                                  sorted_vals, ranges, total_tiles, d_num_keys, status, sm_count, st, \
                                                  mark, events, first_event + 1)
     const int it = sort_items == 8 ? 8 : (sort_items == 16 ? 16 : 12);
