@@ -42,6 +42,10 @@ def lib():
         L.or_sh_basis_grad.argtypes = [_D, _D]
         L.or_rect.argtypes = [C.c_double, C.c_double, C.c_double, C.c_int, C.c_int, C.c_int, _I32]
         L.or_project.argtypes = [C.c_int64, C.c_int, _D, C.c_int, _D, C.c_int, _D]
+        L.or_project_dyn.argtypes = [C.c_int64, C.c_int, _D, C.c_int, _D, C.c_int, _I32, _D, C.c_void_p, _D,
+                                     C.c_double, C.c_double, _D]
+        L.or_project_bwd_dyn.argtypes = [C.c_int64, C.c_int, _D, C.c_int, _D, C.c_int, _D, _I32, _D, C.c_void_p,
+                                         _D, C.c_double, C.c_double, _D]
         L.or_bin_count.argtypes = [C.c_int, C.c_int64, _I32]
         L.or_bin_count.restype = C.c_int64
         L.or_bin_sort.argtypes = [C.c_int, C.c_int64, _D, C.c_int, _I32, _F, _U64, _U32, _U32]
@@ -121,13 +125,31 @@ def rect(u, v, r, width, height, tile=TILE):
     return out
 
 
-def project(planes, sh_degree: int, cams: dict, tile: int = TILE) -> np.ndarray:
-    """-> proj [V][n][16] float64 (fields PROJ_FIELDS; zero when culled)."""
+def _dyn_args(dyn):
+    """dyn: dict with group (int [n]), poses ([G][8] quaternion wxyz,
+    translation, 0), optional normals ([n][3]), light (3), ambient, diffuse."""
+    group = np.ascontiguousarray(dyn["group"], dtype=np.int32)
+    poses = _d(dyn["poses"])
+    normals = dyn.get("normals")
+    normals = None if normals is None else _d(normals)
+    light = _d(dyn.get("light", (0.0, 1.0, 0.0)))
+    keep = (group, poses, normals, light)
+    nptr = None if normals is None else normals.ctypes.data_as(C.c_void_p)
+    return keep, (group, poses, nptr, light, float(dyn.get("ambient", 0.3)), float(dyn.get("diffuse", 0.7)))
+
+
+def project(planes, sh_degree: int, cams: dict, tile: int = TILE, dyn=None) -> np.ndarray:
+    """-> proj [V][n][16] float64 (fields PROJ_FIELDS; zero when culled).
+    dyn: optional rigid-object poses and relighting (see _dyn_args)."""
     rows = _rows(planes)
     n = rows.shape[0]
     V = len(cams["fx"])
     out = np.zeros((V, n, 16))
-    lib().or_project(n, sh_degree, rows, V, cams_array(cams), tile, out)
+    if dyn is None:
+        lib().or_project(n, sh_degree, rows, V, cams_array(cams), tile, out)
+    else:
+        keep, a = _dyn_args(dyn)
+        lib().or_project_dyn(n, sh_degree, rows, V, cams_array(cams), tile, *a, out)
     return out
 
 
@@ -171,13 +193,17 @@ def render_bwd(cams: dict, proj, vals, ranges, dimage, bg=(0.0, 0.0, 0.0), tile:
     return g
 
 
-def project_bwd(planes, sh_degree: int, cams: dict, grad2d, tile: int = TILE) -> np.ndarray:
+def project_bwd(planes, sh_degree: int, cams: dict, grad2d, tile: int = TILE, dyn=None) -> np.ndarray:
     """-> parameter gradient as planes [15][n][4] float64."""
     rows = _rows(planes)
     n = rows.shape[0]
     V = len(cams["fx"])
     d = np.zeros((n, 60))
-    lib().or_project_bwd(n, sh_degree, rows, V, cams_array(cams), tile, _d(grad2d), d)
+    if dyn is None:
+        lib().or_project_bwd(n, sh_degree, rows, V, cams_array(cams), tile, _d(grad2d), d)
+    else:
+        keep, a = _dyn_args(dyn)
+        lib().or_project_bwd_dyn(n, sh_degree, rows, V, cams_array(cams), tile, _d(grad2d), *a, d)
     return rows_to_planes(d)
 
 
@@ -237,8 +263,8 @@ def decision_flips(cams, projA, valsA, rangesA, projB, valsB, rangesB, tile: int
 
 
 # ------------------------------------------------------------------ composed
-def forward(planes, sh_degree, cams, bg=(0.0, 0.0, 0.0), tile=TILE):
-    proj = project(planes, sh_degree, cams, tile)
+def forward(planes, sh_degree, cams, bg=(0.0, 0.0, 0.0), tile=TILE, dyn=None):
+    proj = project(planes, sh_degree, cams, tile, dyn)
     keys, vals, ranges = bin_sort(cams, rects_of(proj), proj[..., 2].astype(np.float32), tile)
     img, T, nc = render(cams, proj, vals, ranges, bg, tile)
     return {"proj": proj, "keys": keys, "vals": vals, "ranges": ranges,
@@ -246,20 +272,21 @@ def forward(planes, sh_degree, cams, bg=(0.0, 0.0, 0.0), tile=TILE):
 
 
 def loss_and_grad(planes, sh_degree, cams, target, w_l1=0.8, w_ssim=0.2,
-                  bg=(0.0, 0.0, 0.0), tile=TILE):
+                  bg=(0.0, 0.0, 0.0), tile=TILE, dyn=None):
     """Full FP64 chain: render, loss, image gradient, 2D and parameter gradients."""
-    f = forward(planes, sh_degree, cams, bg, tile)
+    f = forward(planes, sh_degree, cams, bg, tile, dyn)
     V = len(cams["fx"])
     H, W = int(cams["height"][0]), int(cams["width"][0])
     L, dimg = loss(f["image"], target, V, H, W, w_l1, w_ssim)
     g2 = render_bwd(cams, f["proj"], f["vals"], f["ranges"], dimg, bg, tile)
-    dp = project_bwd(planes, sh_degree, cams, g2, tile)
+    dp = project_bwd(planes, sh_degree, cams, g2, tile, dyn)
     f.update({"loss": L, "dimage": dimg, "grad2d": g2, "dparams": dp})
     return f
 
 
-def render_loss(planes, sh_degree, cams, target, w_l1=0.8, w_ssim=0.2, bg=(0.0, 0.0, 0.0), tile=TILE):
-    f = forward(planes, sh_degree, cams, bg, tile)
+def render_loss(planes, sh_degree, cams, target, w_l1=0.8, w_ssim=0.2, bg=(0.0, 0.0, 0.0), tile=TILE,
+                dyn=None):
+    f = forward(planes, sh_degree, cams, bg, tile, dyn)
     V = len(cams["fx"])
     H, W = int(cams["height"][0]), int(cams["width"][0])
     return loss(f["image"], target, V, H, W, w_l1, w_ssim)[0]

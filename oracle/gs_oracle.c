@@ -142,8 +142,61 @@ typedef struct {
     double M[6];      /* J W, 2x3 */
     double a, b, c, det;
     double dir[3], len;
+    double dir_sh[3];  /* view direction in the object frame */
     double Y[16];
 } view_geom;
+
+/* ------------------------------------------------------------------------
+ * Scene dynamics (Sec. 3.4).  Rigid objects (Sec. 3.4.2): every Gaussian
+ * belongs to one object (group); its mean and rotation are stored in the
+ * object's frame and the engine's current object pose (rotation R_g,
+ * translation t_g) is applied before each optimisation step:
+ *   mu_world = R_g mu + t_g,   Sigma_world = R_g Sigma R_g^T.
+ * Relighting (Sec. 3.4.1), READING: the diffuse (DC) SH coefficient is scaled
+ * by a Lambertian factor of the current directional light,
+ *   L = ambient + diffuse * max(0, (R_g n) . l),
+ * with n the Gaussian's object-frame unit normal and l the unit vector
+ * towards the light.  The poses and the light are inputs, not parameters.
+ * ---------------------------------------------------------------------- */
+typedef struct {
+    const int32_t* group;   /* [n] or NULL (static scene) */
+    const double* poses;    /* [G][8]: quaternion wxyz, translation xyz, 0 */
+    const double* normals;  /* [n][3] or NULL (no relighting) */
+    double light[3];
+    double ambient, diffuse;
+} dyn_t;
+
+static void quat_to_rot(const double* q, double* R);
+
+/* World-frame mean / covariance and DC factor of Gaussian g under `dyn`;
+ * Rg receives the object rotation (identity for a static scene). */
+static void apply_dynamics(const dyn_t* dyn, int64_t g, double* mu, double* Sig, double* Rg, double* L) {
+    for (int i = 0; i < 9; ++i) Rg[i] = (i % 4 == 0) ? 1.0 : 0.0;
+    *L = 1.0;
+    if (!dyn || !dyn->group) return;
+    const double* pose = dyn->poses + (int64_t)dyn->group[g] * 8;
+    double qn = sqrt(pose[0] * pose[0] + pose[1] * pose[1] + pose[2] * pose[2] + pose[3] * pose[3]);
+    double q[4] = {pose[0] / qn, pose[1] / qn, pose[2] / qn, pose[3] / qn};
+    quat_to_rot(q, Rg);
+    double m[3], S[9];
+    for (int i = 0; i < 3; ++i) m[i] = Rg[i * 3] * mu[0] + Rg[i * 3 + 1] * mu[1] + Rg[i * 3 + 2] * mu[2] + pose[4 + i];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double acc = 0.0;
+            for (int k = 0; k < 3; ++k)
+                for (int l = 0; l < 3; ++l) acc += Rg[i * 3 + k] * Sig[k * 3 + l] * Rg[j * 3 + l];
+            S[i * 3 + j] = acc;
+        }
+    memcpy(mu, m, sizeof(m));
+    memcpy(Sig, S, sizeof(S));
+    if (dyn->normals) {
+        const double* nl = dyn->normals + g * 3;
+        double nd = 0.0;
+        for (int i = 0; i < 3; ++i)
+            nd += (Rg[i * 3] * nl[0] + Rg[i * 3 + 1] * nl[1] + Rg[i * 3 + 2] * nl[2]) * dyn->light[i];
+        *L = dyn->ambient + dyn->diffuse * fmax(0.0, nd);
+    }
+}
 
 static void gauss_common(const double* p, double* mu, double* s, double* qhat, double* qnorm,
                          double* R, double* Sig, double* opac) {
@@ -163,8 +216,12 @@ static void gauss_common(const double* p, double* mu, double* s, double* qhat, d
         }
 }
 
-/* Returns 1 if the Gaussian survives the near-plane and determinant tests. */
-static int view_geometry(const double* mu, const double* Sig, const double* cam, view_geom* G) {
+/* Returns 1 if the Gaussian survives the near-plane and determinant tests.
+ * Rg (object rotation, NULL = identity): SH colour is evaluated at the view
+ * direction in the object's frame, Rg^T dir, so that an object's
+ * view-dependent appearance turns with it (READING, Sec. 3.4.2). */
+static int view_geometry(const double* mu, const double* Sig, const double* cam, const double* Rg,
+                         view_geom* G) {
     const double* W = cam;
     const double* tc = cam + 9;
     double fx = cam[12], fy = cam[13];
@@ -205,24 +262,29 @@ static int view_geometry(const double* mu, const double* Sig, const double* cam,
     double dv[3] = {mu[0] - cp[0], mu[1] - cp[1], mu[2] - cp[2]};
     G->len = sqrt(dv[0] * dv[0] + dv[1] * dv[1] + dv[2] * dv[2]);
     for (int i = 0; i < 3; ++i) G->dir[i] = dv[i] / G->len;
-    or_sh_basis(G->dir, G->Y);
+    double dl[3];
+    for (int i = 0; i < 3; ++i)
+        dl[i] = Rg ? Rg[i] * G->dir[0] + Rg[3 + i] * G->dir[1] + Rg[6 + i] * G->dir[2] : G->dir[i];
+    memcpy(G->dir_sh, dl, sizeof(dl));
+    or_sh_basis(dl, G->Y);
     return 1;
 }
 
-void or_project(int64_t n, int sh_degree, const double* rows, int V, const double* cams,
-                int tile, double* out) {
+static void project_impl(int64_t n, int sh_degree, const double* rows, int V, const double* cams, int tile,
+                         const dyn_t* dyn, double* out) {
     int nb = (sh_degree + 1) * (sh_degree + 1);
 #pragma omp parallel for schedule(dynamic, 1024)
     for (int64_t g = 0; g < n; ++g) {
         const double* p = rows + g * ROW;
-        double mu[3], s[3], q[4], qn, R[9], Sig[9], opac;
+        double mu[3], s[3], q[4], qn, R[9], Sig[9], opac, Rg[9], Ld;
         gauss_common(p, mu, s, q, &qn, R, Sig, &opac);
+        apply_dynamics(dyn, g, mu, Sig, Rg, &Ld);
         for (int v = 0; v < V; ++v) {
             const double* cam = cams + (int64_t)v * CAM_STRIDE;
             double* o = out + ((int64_t)v * n + g) * PROJ_STRIDE;
             memset(o, 0, sizeof(double) * PROJ_STRIDE);
             view_geom G;
-            if (!view_geometry(mu, Sig, cam, &G)) continue;
+            if (!view_geometry(mu, Sig, cam, Rg, &G)) continue;
             double mid = 0.5 * (G.a + G.c);
             double lam = mid + sqrt(fmax(0.1, mid * mid - G.det));
             double r = ceil(3.0 * sqrt(lam));
@@ -235,7 +297,7 @@ void or_project(int64_t n, int sh_degree, const double* rows, int V, const doubl
             int mask = 0;
             for (int ch = 0; ch < 3; ++ch) {
                 double acc = 0.0;
-                for (int k = 0; k < nb; ++k) acc += p[12 + 3 * k + ch] * G.Y[k];
+                for (int k = 0; k < nb; ++k) acc += p[12 + 3 * k + ch] * G.Y[k] * (k == 0 ? Ld : 1.0);
                 acc += 0.5;
                 if (acc < 0.0) { acc = 0.0; mask |= 1 << ch; }
                 rgb[ch] = acc;
@@ -246,6 +308,19 @@ void or_project(int64_t n, int sh_degree, const double* rows, int V, const doubl
             o[12] = rect[0]; o[13] = rect[1]; o[14] = rect[2]; o[15] = rect[3];
         }
     }
+}
+
+void or_project(int64_t n, int sh_degree, const double* rows, int V, const double* cams, int tile, double* out) {
+    project_impl(n, sh_degree, rows, V, cams, tile, NULL, out);
+}
+
+/* or_project with rigid-object dynamics and relighting (see apply_dynamics);
+ * group: int32 [n]; poses [G][8]; normals [n][3] or NULL; light[3]. */
+void or_project_dyn(int64_t n, int sh_degree, const double* rows, int V, const double* cams, int tile,
+                    const int32_t* group, const double* poses, const double* normals, const double* light,
+                    double ambient, double diffuse, double* out) {
+    dyn_t d = {group, poses, normals, {light[0], light[1], light[2]}, ambient, diffuse};
+    project_impl(n, sh_degree, rows, V, cams, tile, &d, out);
 }
 
 /* ------------------------------------------------------------------------
@@ -468,23 +543,24 @@ void or_render_bwd(int V, int64_t n, const double* cams, int tile, const double*
  * Adjoint of or_project: 2D gradients of every view -> parameter gradients
  * (mean, opacity logit, log-scale, quaternion, SH), summed over views.
  * ---------------------------------------------------------------------- */
-void or_project_bwd(int64_t n, int sh_degree, const double* rows, int V, const double* cams,
-                    int tile, const double* grad2d, double* drows) {
+static void project_bwd_impl(int64_t n, int sh_degree, const double* rows, int V, const double* cams,
+                             int tile, const double* grad2d, const dyn_t* dyn, double* drows) {
     int nb = (sh_degree + 1) * (sh_degree + 1);
 #pragma omp parallel for schedule(dynamic, 1024)
     for (int64_t g = 0; g < n; ++g) {
         const double* p = rows + g * ROW;
         double* dp = drows + g * ROW;
         memset(dp, 0, sizeof(double) * ROW);
-        double mu[3], s[3], q[4], qn, R[9], Sig[9], opac;
+        double mu[3], s[3], q[4], qn, R[9], Sig[9], opac, Rg[9], Ld;
         gauss_common(p, mu, s, q, &qn, R, Sig, &opac);
+        apply_dynamics(dyn, g, mu, Sig, Rg, &Ld);  /* mu, Sig are world-frame from here on */
         double dmu[3] = {0, 0, 0}, dSig[9] = {0}, dlogit = 0.0;
         for (int v = 0; v < V; ++v) {
             const double* cam = cams + (int64_t)v * CAM_STRIDE;
             const double* W = cam;
             double fx = cam[12], fy = cam[13];
             view_geom G;
-            if (!view_geometry(mu, Sig, cam, &G)) continue;
+            if (!view_geometry(mu, Sig, cam, Rg, &G)) continue;
             /* the same culling as the forward pass */
             double mid = 0.5 * (G.a + G.c);
             double r = ceil(3.0 * sqrt(mid + sqrt(fmax(0.1, mid * mid - G.det))));
@@ -497,18 +573,21 @@ void or_project_bwd(int64_t n, int sh_degree, const double* rows, int V, const d
             /* opacity = sigmoid(logit) */
             dlogit += go * opac * (1.0 - opac);
             /* colour: rgb_c = sum_k sh[k][c] Y_k(dir) + 0.5, clamped at 0 */
-            double ddir[3] = {0, 0, 0}, dY[48];
-            or_sh_basis_grad(G.dir, dY);
+            double ddl[3] = {0, 0, 0}, dY[48];  /* w.r.t. the object-frame direction */
+            or_sh_basis_grad(G.dir_sh, dY);
             for (int ch = 0; ch < 3; ++ch) {
                 double raw = 0.5;
-                for (int k = 0; k < nb; ++k) raw += p[12 + 3 * k + ch] * G.Y[k];
+                for (int k = 0; k < nb; ++k) raw += p[12 + 3 * k + ch] * G.Y[k] * (k == 0 ? Ld : 1.0);
                 if (raw < 0.0) continue;
                 double gc = gr[6 + ch];
                 for (int k = 0; k < nb; ++k) {
-                    dp[12 + 3 * k + ch] += gc * G.Y[k];
-                    for (int i = 0; i < 3; ++i) ddir[i] += gc * p[12 + 3 * k + ch] * dY[k * 3 + i];
+                    dp[12 + 3 * k + ch] += gc * G.Y[k] * (k == 0 ? Ld : 1.0);
+                    for (int i = 0; i < 3; ++i) ddl[i] += gc * p[12 + 3 * k + ch] * dY[k * 3 + i];
                 }
             }
+            /* dir_sh = Rg^T dir  ->  dL/ddir = Rg dL/ddir_sh */
+            double ddir[3];
+            for (int i = 0; i < 3; ++i) ddir[i] = Rg[i * 3] * ddl[0] + Rg[i * 3 + 1] * ddl[1] + Rg[i * 3 + 2] * ddl[2];
             double dd = G.dir[0] * ddir[0] + G.dir[1] * ddir[1] + G.dir[2] * ddir[2];
             for (int i = 0; i < 3; ++i) dmu[i] += (ddir[i] - G.dir[i] * dd) / G.len;
             /* conic (A, B, C) = (c, -b, a) / det */
@@ -551,6 +630,20 @@ void or_project_bwd(int64_t n, int sh_degree, const double* rows, int V, const d
             /* t = W mu + t_cam */
             for (int i = 0; i < 3; ++i) dmu[i] += W[i] * dt[0] + W[3 + i] * dt[1] + W[6 + i] * dt[2];
         }
+        /* back to the object frame: mu_w = Rg mu + t, Sigma_w = Rg Sigma Rg^T */
+        {
+            double m[3], D[9];
+            for (int i = 0; i < 3; ++i) m[i] = Rg[i] * dmu[0] + Rg[3 + i] * dmu[1] + Rg[6 + i] * dmu[2];
+            for (int i = 0; i < 3; ++i)
+                for (int j = 0; j < 3; ++j) {
+                    double acc = 0.0;
+                    for (int k = 0; k < 3; ++k)
+                        for (int l = 0; l < 3; ++l) acc += Rg[k * 3 + i] * dSig[k * 3 + l] * Rg[l * 3 + j];
+                    D[i * 3 + j] = acc;
+                }
+            memcpy(dmu, m, sizeof(m));
+            memcpy(dSig, D, sizeof(D));
+        }
         /* Sigma = R diag(s^2) R^T */
         double dR[9], ds[3];
         for (int aa = 0; aa < 3; ++aa)
@@ -579,6 +672,18 @@ void or_project_bwd(int64_t n, int sh_degree, const double* rows, int V, const d
         for (int i = 0; i < 3; ++i) dp[4 + i] = ds[i] * s[i];
         for (int i = 0; i < 4; ++i) dp[8 + i] = (dq[i] - q[i] * qd) / qn;
     }
+}
+
+void or_project_bwd(int64_t n, int sh_degree, const double* rows, int V, const double* cams, int tile,
+                    const double* grad2d, double* drows) {
+    project_bwd_impl(n, sh_degree, rows, V, cams, tile, grad2d, NULL, drows);
+}
+
+void or_project_bwd_dyn(int64_t n, int sh_degree, const double* rows, int V, const double* cams, int tile,
+                        const double* grad2d, const int32_t* group, const double* poses, const double* normals,
+                        const double* light, double ambient, double diffuse, double* drows) {
+    dyn_t d = {group, poses, normals, {light[0], light[1], light[2]}, ambient, diffuse};
+    project_bwd_impl(n, sh_degree, rows, V, cams, tile, grad2d, &d, drows);
 }
 
 /* ------------------------------------------------------------------------

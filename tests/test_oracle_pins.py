@@ -523,3 +523,102 @@ def test_decision_flips_finds_a_planted_threshold_crossing():
     p2[0, g, 3] *= 0.5
     flags, npix = O.decision_flips(cams, f["proj"], f["vals"], f["ranges"], p2, f["vals"], f["ranges"])
     assert npix > 0 and flags[0, g]
+
+
+# --------------------------------------------------------------- dynamics (Sec. 3.4)
+def _dyn(n, G, seed, normals=True, light=(0.3, 0.8, 0.52)):
+    rng = np.random.default_rng(seed)
+    poses = np.zeros((G, 8))
+    q = rng.normal(size=(G, 4)); q /= np.linalg.norm(q, axis=1, keepdims=True)
+    poses[:, :4] = q
+    poses[:, 4:7] = rng.uniform(-0.2, 0.2, (G, 3))
+    l = np.asarray(light, dtype=float); l /= np.linalg.norm(l)
+    d = {"group": np.arange(n) % G, "poses": poses, "light": l, "ambient": 0.3, "diffuse": 0.7}
+    if normals:
+        nn = rng.normal(size=(n, 3)); d["normals"] = nn / np.linalg.norm(nn, axis=1, keepdims=True)
+    return d
+
+
+def test_dynamics_identity_pose_is_static():
+    sc = gi.make_scene(300, 2, 21)
+    cams = gi.ring_cameras(2, 64, 48)
+    d = {"group": np.zeros(300, dtype=np.int32), "poses": np.array([[1, 0, 0, 0, 0, 0, 0, 0.0]])}
+    np.testing.assert_array_equal(O.project(sc, 2, cams, dyn=d), O.project(sc, 2, cams))
+
+
+def test_rigid_motion_equals_inverse_camera_motion():
+    """Moving every Gaussian by (R_g, t_g) renders what the camera moved by the
+    inverse motion sees: W' = W R_g, t' = W t_g + t (scipy builds R_g)."""
+    sc = gi.make_scene(500, 1, 22)
+    sc[1, :, :3] += 0.8
+    cams = gi.ring_cameras(2, 64, 48)
+    q = np.array([0.9, 0.2, -0.3, 0.25]); q /= np.linalg.norm(q)
+    t = np.array([0.05, -0.1, 0.08])
+    d = {"group": np.zeros(500, dtype=np.int32), "poses": np.array([[*q, *t, 0.0]])}
+    Rg = Rotation.from_quat([q[1], q[2], q[3], q[0]]).as_matrix()
+    cams2 = dict(cams)
+    cams2["R"] = np.array([R @ Rg for R in cams["R"]])
+    cams2["t"] = np.array([R @ t + tc for R, tc in zip(cams["R"], cams["t"])])
+    a = O.forward(sc, 1, cams, dyn=d)["image"]
+    b = O.forward(sc, 1, cams2)["image"]
+    np.testing.assert_allclose(a, b, atol=1e-10)
+
+
+def test_relight_factor_closed_form():
+    n = 64
+    sc = gi.make_scene(n, 0, 23)
+    cams = gi.ring_cameras(1, 64, 64)
+    d = _dyn(n, 4, 5)
+    pr = O.project(sc, 0, cams, dyn=d)
+    y00 = 0.5 / math.sqrt(math.pi)
+    rows = gi.planes_to_rows(sc).astype(np.float64)
+    for g in range(n):
+        if pr[0, g, 14] == pr[0, g, 12]:
+            continue
+        q = d["poses"][d["group"][g], :4]
+        Rg = Rotation.from_quat([q[1], q[2], q[3], q[0]]).as_matrix()
+        L = 0.3 + 0.7 * max(0.0, float((Rg @ d["normals"][g]) @ d["light"]))
+        expect = np.maximum(L * rows[g, 12:15] * y00 + 0.5, 0.0)
+        np.testing.assert_allclose(pr[0, g, 8:11], expect, atol=1e-12)
+
+
+def test_dynamic_gradient_matches_central_differences():
+    n = 50
+    sc = gi.make_scene(n, 1, 24).astype(np.float64)
+    sc[1, :, :3] += 1.2
+    sc[0, :, :3] *= 0.6
+    cams = gi.ring_cameras(2, 40, 32)
+    d = _dyn(n, 3, 6)
+    tgt = gi.make_scene(n, 1, 25).astype(np.float64)
+    tgt[1, :, :3] += 1.2
+    tgt[0, :, :3] *= 0.6
+    target = O.forward(tgt, 1, cams, dyn=d)["image"]
+    r = O.loss_and_grad(sc, 1, cams, target, dyn=d)
+    g = r["dparams"]
+    rng = np.random.default_rng(77)
+    errs, checked, tries = [], 0, 0
+    while checked < 40 and tries < 400:
+        tries += 1
+        p, i, c = int(rng.integers(0, 4)), int(rng.integers(0, n)), int(rng.integers(0, 4))
+        if (p == 1 and c == 3) or np.all(r["proj"][:, i, 14] == 0):
+            continue
+        th = sc[p, i, c]
+        h = 1e-6 * max(1.0, abs(th))
+        sp_ = sc.copy(); sp_[p, i, c] = th + h
+        sm_ = sc.copy(); sm_[p, i, c] = th - h
+        fp, fm = O.forward(sp_, 1, cams, dyn=d), O.forward(sm_, 1, cams, dyn=d)
+        if not (np.array_equal(fp["n_contrib"], r["n_contrib"]) and np.array_equal(fm["n_contrib"], r["n_contrib"])
+                and np.array_equal(fp["proj"][..., 12:16], r["proj"][..., 12:16])
+                and np.array_equal(fm["proj"][..., 12:16], r["proj"][..., 12:16])):
+            continue
+        Lp = O.loss(fp["image"], target, 2, 32, 40)[0]
+        Lm = O.loss(fm["image"], target, 2, 32, 40)[0]
+        fwd, bwd = (Lp - r["loss"]) / h, (r["loss"] - Lm) / h
+        if abs(fwd - bwd) > 1e-3 * max(abs(fwd), abs(bwd), 1e-8):
+            continue
+        fd = (Lp - Lm) / (2 * h)
+        noise = 100 * np.finfo(float).eps * abs(r["loss"]) / h
+        errs.append(max(abs(fd - g[p, i, c]) - noise, 0.0) / max(abs(fd), abs(g[p, i, c]), 1e-12))
+        checked += 1
+    assert checked >= 30
+    assert max(errs) <= 1e-5, sorted(errs)[-3:]
