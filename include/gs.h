@@ -75,11 +75,32 @@ typedef struct gs_camera {
     float _pad;
 } gs_camera;
 
+/* Scene dynamics (Sec. 3.4).  Rigid objects (Sec. 3.4.2): Gaussian i belongs
+ * to object group[i]; its mean, rotation and SH appearance are stored in that
+ * object's frame, and the object's current pose (rotation R_g, translation
+ * t_g) is applied before rendering: mean_world = R_g mean + t_g, covariance
+ * R_g Sigma R_g^T, SH evaluated at the view direction in the object frame.
+ * Relighting (Sec. 3.4.1), simplified to a Lambertian factor of one
+ * directional light on the DC coefficient:
+ *   DC_used = DC * (ambient + diffuse * max(0, (R_g normal) . light)).
+ * The poses and the light live in device memory so that a captured graph sees
+ * each frame's values; they are inputs, never differentiated. */
+typedef struct gs_dynamics {
+    int32_t n_groups;        /* objects, 1..256 */
+    int32_t _pad;
+    const uint8_t* group;    /* device [n]: object of each Gaussian */
+    const float* poses;      /* device [n_groups][8]: unit quaternion (w,x,y,z), translation (x,y,z), 0 */
+    const float* normals;    /* device [n][4]: object-frame unit normal (x,y,z), 0; NULL: no relighting */
+    const float* light;      /* device [4]: unit vector towards the light (world), 0 */
+    float ambient, diffuse;
+} gs_dynamics;
+
 typedef struct gs_scene {
     int64_t n;           /* number of Gaussians, >= 0 */
     int32_t sh_degree;   /* 0..3 */
     int32_t _pad;
     const float* params; /* device, [15][n][4] */
+    const gs_dynamics* dyn; /* host pointer; NULL: static scene */
 } gs_scene;
 
 /* ---------------------------------------------------------------- context */
@@ -272,6 +293,8 @@ typedef struct gs_train_io {
 } gs_train_io;
 
 typedef struct gs_train_cfg {
+    const gs_dynamics* dyn; /* host pointer; NULL: static scene.  Read when the
+                               step is enqueued (or captured): pointers fixed */
     int64_t n;
     int32_t sh_degree;
     int32_t n_views;

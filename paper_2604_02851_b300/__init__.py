@@ -127,18 +127,55 @@ class Context:
             pass
 
 
-def _scene(params, sh_degree):
+class Dynamics:
+    """Rigid-object poses and a directional light for a scene (gs_dynamics).
+
+    group: uint8 [n] object of each Gaussian; poses: float [G][8] (unit
+    quaternion w,x,y,z; translation x,y,z; 0); normals: float [n][3] or [n][4]
+    object-frame unit normals (None: no relighting); light: unit vector
+    towards the light.  Device copies are kept here; set_frame() overwrites
+    the poses and the light in place, so a captured graph sees new values."""
+
+    def __init__(self, group, poses, normals=None, light=(0.0, 1.0, 0.0), ambient=0.3, diffuse=0.7,
+                 device="cuda"):
+        torch = _torch()
+        self.group = torch.as_tensor(np.asarray(group, dtype=np.uint8)).to(device)
+        self.poses = torch.as_tensor(np.asarray(poses, dtype=np.float32).reshape(-1, 8)).to(device)
+        self.normals = None
+        if normals is not None:
+            nn = np.zeros((len(normals), 4), dtype=np.float32)
+            nn[:, :3] = np.asarray(normals, dtype=np.float32)[:, :3]
+            self.normals = torch.from_numpy(nn).to(device)
+        self.light = torch.zeros(4, dtype=torch.float32, device=device)
+        self.light[:3] = torch.as_tensor(np.asarray(light, dtype=np.float32))
+        self.struct = _lib.gs_dynamics(
+            n_groups=self.poses.shape[0], group=self.group.data_ptr(), poses=self.poses.data_ptr(),
+            normals=self.normals.data_ptr() if self.normals is not None else None,
+            light=self.light.data_ptr(), ambient=ambient, diffuse=diffuse)
+
+    def set_frame(self, poses=None, light=None):
+        torch = _torch()
+        if poses is not None:
+            self.poses.copy_(torch.as_tensor(np.asarray(poses, dtype=np.float32).reshape(-1, 8)))
+        if light is not None:
+            self.light[:3].copy_(torch.as_tensor(np.asarray(light, dtype=np.float32)))
+
+
+def _scene(params, sh_degree, dyn: "Dynamics | None" = None):
     n = params.shape[1] if params is not None else 0
-    return _lib.gs_scene(n=n, sh_degree=sh_degree, params=params.data_ptr() if n else None)
+    sc = _lib.gs_scene(n=n, sh_degree=sh_degree, params=params.data_ptr() if n else None)
+    if dyn is not None:
+        sc.dyn = C.pointer(dyn.struct)
+    return sc
 
 
 # ------------------------------------------------------------------ entry points
-def gs_project(ctx, params, sh_degree, d_cams, n_views, proj=None, stream=None):
+def gs_project(ctx, params, sh_degree, d_cams, n_views, proj=None, stream=None, dyn=None):
     torch = _torch()
     n = params.shape[1]
     if proj is None:
         proj = torch.empty((n_views, n, PROJ_STRIDE), dtype=torch.float32, device=params.device)
-    sc = _scene(params, sh_degree)
+    sc = _scene(params, sh_degree, dyn)
     check("gs_project", _lib.lib().gs_project(ctx.ptr, C.byref(sc), _ptr(d_cams), n_views, _ptr(proj),
                                               _stream(stream)))
     return proj
@@ -207,12 +244,12 @@ def gs_raster_bwd(ctx, proj, d_cams, n_views, n, total_tiles, sorted_vals, range
 
 
 def gs_project_bwd(ctx, params, sh_degree, d_cams, n_views, proj, grad2d, dparams=None, accumulate=False,
-                   stream=None):
+                   stream=None, dyn=None):
     torch = _torch()
     if dparams is None:
         dparams = torch.empty_like(params)
         accumulate = False
-    sc = _scene(params, sh_degree)
+    sc = _scene(params, sh_degree, dyn)
     check("gs_project_bwd", _lib.lib().gs_project_bwd(ctx.ptr, C.byref(sc), _ptr(d_cams), n_views, _ptr(proj),
                                                       _ptr(grad2d), _ptr(dparams), int(bool(accumulate)),
                                                       _stream(stream)))
@@ -220,14 +257,14 @@ def gs_project_bwd(ctx, params, sh_degree, d_cams, n_views, proj, grad2d, dparam
 
 
 def gs_render_bwd(ctx, params, sh_degree, d_cams, n_views, total_tiles, proj, sorted_vals, ranges, T_final,
-                  n_contrib, dimage, bg=None, grad2d=None, dparams=None, stream=None):
+                  n_contrib, dimage, bg=None, grad2d=None, dparams=None, stream=None, dyn=None):
     torch = _torch()
     n = params.shape[1]
     if grad2d is None:
         grad2d = torch.empty((n_views, n, GRAD2D_STRIDE), dtype=torch.float32, device=params.device)
     if dparams is None:
         dparams = torch.empty_like(params)
-    sc = _scene(params, sh_degree)
+    sc = _scene(params, sh_degree, dyn)
     check("gs_render_bwd", _lib.lib().gs_render_bwd(ctx.ptr, C.byref(sc), _ptr(d_cams), n_views, total_tiles,
                                                     _ptr(proj), _ptr(sorted_vals), _ptr(ranges), _bg(bg),
                                                     _ptr(T_final), _ptr(n_contrib), _ptr(dimage), _ptr(grad2d),
@@ -268,11 +305,11 @@ def gs_extract_delta(ctx, theta, baseline, thr=1e-3, d_idx=None, d_records=None,
 
 
 def gs_render_batch(ctx, params, sh_degree, d_cams, n_requests, total_tiles, keys_cap, npix, bg=None,
-                    image=None, stream=None):
+                    image=None, stream=None, dyn=None):
     torch = _torch()
     if image is None:
         image = torch.empty(3 * npix, dtype=torch.float32, device=params.device)
-    sc = _scene(params, sh_degree)
+    sc = _scene(params, sh_degree, dyn)
     check("gs_render_batch", _lib.lib().gs_render_batch(ctx.ptr, C.byref(sc), _ptr(d_cams), n_requests,
                                                         total_tiles, keys_cap, _bg(bg), _ptr(image),
                                                         _stream(stream)))
@@ -285,8 +322,10 @@ def train_io(params, grads, m, v, baseline, targets, image, d_loss, d_idx, d_rec
 
 
 def train_cfg(n, sh_degree, n_views, width, height, keys_cap, w_l1=0.8, w_ssim=0.2, bg=(0.0, 0.0, 0.0),
-              delta_thr=1e-3, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
+              delta_thr=1e-3, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, dyn: "Dynamics | None" = None):
     cfg = _lib.gs_train_cfg()
+    if dyn is not None:
+        cfg.dyn = C.pointer(dyn.struct)
     cfg.n, cfg.sh_degree, cfg.n_views, cfg.width, cfg.height = n, sh_degree, n_views, width, height
     cfg.keys_cap, cfg.w_l1, cfg.w_ssim, cfg.delta_thr = keys_cap, w_l1, w_ssim, delta_thr
     for i in range(3):

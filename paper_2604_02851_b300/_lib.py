@@ -39,9 +39,14 @@ class gs_camera(C.Structure):
                 ("near_plane", C.c_float), ("_pad", C.c_float)]
 
 
+class gs_dynamics(C.Structure):
+    _fields_ = [("n_groups", C.c_int32), ("_pad", C.c_int32), ("group", C.c_void_p), ("poses", C.c_void_p),
+                ("normals", C.c_void_p), ("light", C.c_void_p), ("ambient", C.c_float), ("diffuse", C.c_float)]
+
+
 class gs_scene(C.Structure):
     _fields_ = [("n", C.c_int64), ("sh_degree", C.c_int32), ("_pad", C.c_int32),
-                ("params", C.c_void_p)]
+                ("params", C.c_void_p), ("dyn", C.POINTER(gs_dynamics))]
 
 
 class gs_adam_cfg(C.Structure):
@@ -58,7 +63,7 @@ class gs_train_io(C.Structure):
 
 
 class gs_train_cfg(C.Structure):
-    _fields_ = [("n", C.c_int64), ("sh_degree", C.c_int32), ("n_views", C.c_int32),
+    _fields_ = [("dyn", C.POINTER(gs_dynamics)), ("n", C.c_int64), ("sh_degree", C.c_int32), ("n_views", C.c_int32),
                 ("width", C.c_int32), ("height", C.c_int32), ("keys_cap", C.c_int64),
                 ("w_l1", C.c_float), ("w_ssim", C.c_float), ("bg", C.c_float * 3),
                 ("delta_thr", C.c_float), ("adam", gs_adam_cfg)]

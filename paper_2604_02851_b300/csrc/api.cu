@@ -43,6 +43,11 @@ int64_t tiles_of(const gs_camera* cams, int V, int tile) {
 
 bool bad_views(int V) { return V < 1 || V > kMaxViews; }
 
+bool bad_dyn(const gs_dynamics* d) {
+    return d && (d->n_groups < 0 || d->n_groups > 256 || (d->n_groups > 0 && (!d->group || !d->poses)) ||
+                 (d->normals && !d->light));
+}
+
 // Workspace plan of the fused calls (render_batch, train_step).
 struct FusedPlan {
     ViewInfo* vt;
@@ -205,14 +210,14 @@ gs_status_t gs_project(gs_ctx* ctx, const gs_scene* scene, const gs_camera* d_ca
     if (!ctx || !scene || !d_cams || !proj || bad_views(n_views) || scene->n < 0 ||
         scene->sh_degree < 0 || scene->sh_degree > 3 || (scene->n > 0 && !scene->params))
         return GS_ERR_ARG;
-    if ((int64_t)n_views * scene->n >= (1LL << 32)) return GS_ERR_ARG;
+    if ((int64_t)n_views * scene->n >= (1LL << 32) || bad_dyn(scene->dyn)) return GS_ERR_ARG;
     Carver c(ctx->ws);
     ViewInfo* vt = c.take<ViewInfo>(n_views + 1);
     if (check_ws(ctx, c.off)) return GS_ERR_CAPACITY;
     DeviceGuard g(ctx->device);
     launch_view_table(d_cams, n_views, ctx->tile, vt, -1, ctx->d_status, S(stream));
-    launch_project(scene->params, scene->n, scene->sh_degree, d_cams, vt, n_views, ctx->tile, proj, nullptr,
-                   S(stream));
+    launch_project(scene->params, scene->n, scene->sh_degree, make_dyn(scene->dyn), d_cams, vt, n_views,
+                   ctx->tile, proj, nullptr, S(stream));
     return launch_check();
 }
 
@@ -286,10 +291,11 @@ gs_status_t gs_project_bwd(gs_ctx* ctx, const gs_scene* scene, const gs_camera* 
                            const float* proj, const float* grad2d, float* dparams, int32_t accumulate,
                            void* stream) {
     if (!ctx || !scene || !d_cams || !proj || !grad2d || !dparams || bad_views(n_views) || scene->n < 0 ||
-        scene->sh_degree < 0 || scene->sh_degree > 3 || (scene->n > 0 && !scene->params))
+        scene->sh_degree < 0 || scene->sh_degree > 3 || (scene->n > 0 && !scene->params) || bad_dyn(scene->dyn))
         return GS_ERR_ARG;
     DeviceGuard g(ctx->device);
-    launch_project_bwd(scene->params, scene->n, scene->sh_degree, d_cams, n_views, proj, grad2d, dparams,
+    launch_project_bwd(scene->params, scene->n, scene->sh_degree, make_dyn(scene->dyn), d_cams, n_views, proj,
+                       grad2d, dparams,
                        accumulate, S(stream));
     return launch_check();
 }
@@ -333,7 +339,7 @@ gs_status_t gs_render_batch(gs_ctx* ctx, const gs_scene* scene, const gs_camera*
                             void* stream) {
     if (!ctx || !scene || !d_cams || !image || bad_views(n_requests) || scene->n < 0 || total_tiles < 1 ||
         keys_cap < 0 || keys_cap >= (1LL << 32) || scene->sh_degree < 0 || scene->sh_degree > 3 ||
-        (scene->n > 0 && !scene->params) || (int64_t)n_requests * scene->n >= (1LL << 32))
+        (scene->n > 0 && !scene->params) || (int64_t)n_requests * scene->n >= (1LL << 32) || bad_dyn(scene->dyn))
         return GS_ERR_ARG;
     const FusedPlan p0 = plan_fused(nullptr, n_requests, scene->n, keys_cap, total_tiles, 0, 0, 0, false);
     if (check_ws(ctx, p0.bytes)) return GS_ERR_CAPACITY;
@@ -344,7 +350,8 @@ gs_status_t gs_render_batch(gs_ctx* ctx, const gs_scene* scene, const gs_camera*
     carve_sort_scratch(p.sort, n_requests, scene->n, keys_cap, &s);
     const float3 b = bg ? make_float3(bg[0], bg[1], bg[2]) : make_float3(0.f, 0.f, 0.f);
     launch_view_table(d_cams, n_requests, ctx->tile, p.vt, total_tiles, ctx->d_status, st);
-    launch_project(scene->params, scene->n, scene->sh_degree, d_cams, p.vt, n_requests, ctx->tile, p.proj,
+    launch_project(scene->params, scene->n, scene->sh_degree, make_dyn(scene->dyn), d_cams, p.vt, n_requests,
+                   ctx->tile, p.proj,
                    s.dkv[0], st);
     launch_bin_sort(p.proj, p.vt, n_requests, scene->n, keys_cap, total_tiles, ctx->sort_bits, ctx->sort_items, s, true, nullptr,
                     p.vals, p.ranges, p.n_keys, ctx->d_status, ctx->sm_count, st);
@@ -375,7 +382,8 @@ gs_status_t gs_train_step_events(gs_ctx* ctx, const gs_camera* d_cams, const gs_
         cfg->sh_degree > 3 || cfg->width < 1 || cfg->height < 1 || cfg->keys_cap < 0 ||
         cfg->keys_cap >= (1LL << 32) || (int64_t)cfg->n_views * cfg->n >= (1LL << 32) || !io->params ||
         !io->grads || !io->adam_m || !io->adam_v || !io->baseline || !io->targets || !io->image ||
-        !io->d_loss || !io->d_delta_idx || !io->d_delta_records || !io->d_delta_count || !io->d_step)
+        !io->d_loss || !io->d_delta_idx || !io->d_delta_records || !io->d_delta_count || !io->d_step ||
+        bad_dyn(cfg->dyn))
         return GS_ERR_ARG;
     const int V = cfg->n_views;
     const int64_t n = cfg->n;
@@ -392,7 +400,8 @@ gs_status_t gs_train_step_events(gs_ctx* ctx, const gs_camera* d_cams, const gs_
     const float3 b = make_float3(cfg->bg[0], cfg->bg[1], cfg->bg[2]);
     mark(ev, 0, st);
     launch_view_table(d_cams, V, B, p.vt, tt, ctx->d_status, st);
-    launch_project(io->params, n, cfg->sh_degree, d_cams, p.vt, V, B, p.proj, s.dkv[0], st);
+    const Dyn dyn = make_dyn(cfg->dyn);
+    launch_project(io->params, n, cfg->sh_degree, dyn, d_cams, p.vt, V, B, p.proj, s.dkv[0], st);
     mark(ev, 1, st);
     launch_bin_sort(p.proj, p.vt, V, n, cfg->keys_cap, tt, ctx->sort_bits, ctx->sort_items, s, true, nullptr,
                     p.vals, p.ranges, p.n_keys, ctx->d_status, ctx->sm_count, st, ev ? mark : nullptr, ev, 2);
@@ -405,7 +414,7 @@ gs_status_t gs_train_step_events(gs_ctx* ctx, const gs_camera* d_cams, const gs_
     launch_raster_bwd(p.proj, p.vt, V, n, B, p.vals, p.ranges, b, p.T_final, p.n_contrib, p.dimage, p.grad2d, tt,
                       st);
     mark(ev, 7, st);
-    launch_project_bwd(io->params, n, cfg->sh_degree, d_cams, V, p.proj, p.grad2d, io->grads, 0, st);
+    launch_project_bwd(io->params, n, cfg->sh_degree, dyn, d_cams, V, p.proj, p.grad2d, io->grads, 0, st);
     mark(ev, 8, st);
     gs_adam_cfg ac = cfg->adam;
     ac.d_step = io->d_step;

@@ -49,12 +49,36 @@ constexpr long long kSpinCycles = 2000000000LL;
 void launch_view_table(const gs_camera* d_cams, int V, int tile, ViewInfo* vt,
                        long long expect_tiles, DevStatus* status, cudaStream_t st);
 
+// Scene dynamics as the kernels take them (by value; group == nullptr: static).
+struct Dyn {
+    int n_groups;
+    const uint8_t* group;
+    const float4* poses;     // [G][2]: quaternion (w, x, y, z), translation (x, y, z, 0)
+    const float4* normals;   // nullptr: no relighting
+    const float4* light;
+    float ambient, diffuse;
+};
+
+inline Dyn make_dyn(const gs_dynamics* d) {
+    Dyn k{};
+    if (d && d->n_groups > 0 && d->group && d->poses) {
+        k.n_groups = d->n_groups;
+        k.group = d->group;
+        k.poses = reinterpret_cast<const float4*>(d->poses);
+        k.normals = (d->normals && d->light) ? reinterpret_cast<const float4*>(d->normals) : nullptr;
+        k.light = reinterpret_cast<const float4*>(d->light);
+        k.ambient = d->ambient;
+        k.diffuse = d->diffuse;
+    }
+    return k;
+}
+
 // depth_kv (may be null): packed (float32 depth bits << 32 | record index)
 // per (view, Gaussian), all-ones depth when culled, for the depth sort.
-void launch_project(const float* params, int64_t n, int sh_degree, const gs_camera* d_cams,
+void launch_project(const float* params, int64_t n, int sh_degree, const Dyn& dyn, const gs_camera* d_cams,
                     const ViewInfo* vt, int V, int tile, float* proj, uint64_t* depth_kv, cudaStream_t st);
 
-void launch_project_bwd(const float* params, int64_t n, int sh_degree, const gs_camera* d_cams,
+void launch_project_bwd(const float* params, int64_t n, int sh_degree, const Dyn& dyn, const gs_camera* d_cams,
                         int V, const float* proj, const float* grad2d, float* dparams,
                         int accumulate, cudaStream_t st);
 

@@ -108,14 +108,73 @@ __device__ __forceinline__ Cam load_cam(const gs_camera* __restrict__ c) {
 }
 
 struct Gauss {
-    float3 mu;
+    float3 mu;       // world frame once apply_dyn has run
     float logit, opac;
     float3 s;        // exp(log-scale)
-    float q[4];      // normalised quaternion
+    float q[4];      // normalised quaternion (object frame)
     float qn;        // |q|
     float Rq[9];
-    float S[6];      // Sigma: 00 01 02 11 12 22
+    float S[6];      // Sigma: 00 01 02 11 12 22 (world frame once apply_dyn has run)
+    bool moved;      // object pose applied
+    float Rg[9];     // object rotation
+    float L;         // relighting factor of the DC coefficient
 };
+
+__device__ __forceinline__ void quat_rot(float w, float x, float y, float z, float* R) {
+    const float n = rsqrtf(w * w + x * x + y * y + z * z);
+    w *= n; x *= n; y *= n; z *= n;
+    R[0] = 1.f - 2.f * (y * y + z * z); R[1] = 2.f * (x * y - w * z);       R[2] = 2.f * (x * z + w * y);
+    R[3] = 2.f * (x * y + w * z);       R[4] = 1.f - 2.f * (x * x + z * z); R[5] = 2.f * (y * z - w * x);
+    R[6] = 2.f * (x * z - w * y);       R[7] = 2.f * (y * z + w * x);       R[8] = 1.f - 2.f * (x * x + y * y);
+}
+
+// Object pose and relighting (Sec. 3.4): mean and covariance to the world
+// frame, Lambertian factor of the DC coefficient.
+__device__ __forceinline__ void apply_dyn(const Dyn& d, int64_t g, Gauss& G) {
+    G.moved = d.group != nullptr;
+    G.L = 1.f;
+    if (!G.moved) return;
+    const uint32_t grp = min((uint32_t)d.group[g], (uint32_t)(d.n_groups - 1));  // ids beyond the poses clamp
+    const float4 q = d.poses[2 * grp], t = d.poses[2 * grp + 1];
+    float* R = G.Rg;
+    quat_rot(q.x, q.y, q.z, q.w, R);
+    const float3 m = G.mu;
+    G.mu = make_float3(R[0] * m.x + R[1] * m.y + R[2] * m.z + t.x, R[3] * m.x + R[4] * m.y + R[5] * m.z + t.y,
+                       R[6] * m.x + R[7] * m.y + R[8] * m.z + t.z);
+    // Sigma_w = R Sigma R^T
+    const float* S = G.S;
+    const float Sf[9] = {S[0], S[1], S[2], S[1], S[3], S[4], S[2], S[4], S[5]};
+    float RS[9];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) RS[i * 3 + j] = R[i * 3] * Sf[j] + R[i * 3 + 1] * Sf[3 + j] + R[i * 3 + 2] * Sf[6 + j];
+    float W[6];
+    W[0] = RS[0] * R[0] + RS[1] * R[1] + RS[2] * R[2];
+    W[1] = RS[0] * R[3] + RS[1] * R[4] + RS[2] * R[5];
+    W[2] = RS[0] * R[6] + RS[1] * R[7] + RS[2] * R[8];
+    W[3] = RS[3] * R[3] + RS[4] * R[4] + RS[5] * R[5];
+    W[4] = RS[3] * R[6] + RS[4] * R[7] + RS[5] * R[8];
+    W[5] = RS[6] * R[6] + RS[7] * R[7] + RS[8] * R[8];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) G.S[i] = W[i];
+    if (d.normals) {
+        const float4 nl = d.normals[g];
+        const float4 l = *d.light;
+        const float nd = (R[0] * nl.x + R[1] * nl.y + R[2] * nl.z) * l.x +
+                         (R[3] * nl.x + R[4] * nl.y + R[5] * nl.z) * l.y +
+                         (R[6] * nl.x + R[7] * nl.y + R[8] * nl.z) * l.z;
+        G.L = d.ambient + d.diffuse * fmaxf(0.f, nd);
+    }
+}
+
+// View direction in the object frame (SH appearance turns with its object).
+__device__ __forceinline__ float3 sh_dir(const Gauss& G, float3 dw) {
+    if (!G.moved) return dw;
+    const float* R = G.Rg;
+    return make_float3(R[0] * dw.x + R[3] * dw.y + R[6] * dw.z, R[1] * dw.x + R[4] * dw.y + R[7] * dw.z,
+                       R[2] * dw.x + R[5] * dw.y + R[8] * dw.z);
+}
 
 __device__ __forceinline__ void load_gauss(const float4* __restrict__ P, int64_t n, int64_t g, Gauss& G) {
     const float4 p0 = P[g], p1 = P[n + g], p2 = P[2 * n + g];
@@ -212,7 +271,7 @@ __device__ __forceinline__ void tile_rect(float u, float v, float r, int TX, int
 
 template <int D>
 __global__ void __launch_bounds__(256)
-k_project(const float4* __restrict__ P, int64_t n, const gs_camera* __restrict__ cams,
+k_project(const float4* __restrict__ P, int64_t n, Dyn dyn, const gs_camera* __restrict__ cams,
           const ViewInfo* __restrict__ vt, int V, int tile, float4* __restrict__ proj,
           uint64_t* __restrict__ dkv) {
     const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -221,12 +280,14 @@ k_project(const float4* __restrict__ P, int64_t n, const gs_camera* __restrict__
     constexpr int NPL = (3 * NB + 3) / 4;
     Gauss G;
     load_gauss(P, n, g, G);
+    apply_dyn(dyn, g, G);
     float sh[NPL * 4];
 #pragma unroll
     for (int pl = 0; pl < NPL; ++pl) {
         const float4 c = P[(3 + pl) * n + g];
         sh[4 * pl] = c.x; sh[4 * pl + 1] = c.y; sh[4 * pl + 2] = c.z; sh[4 * pl + 3] = c.w;
     }
+    sh[0] *= G.L; sh[1] *= G.L; sh[2] *= G.L;
     for (int v = 0; v < V; ++v) {
         const Cam C = load_cam(cams + v);
         const int64_t rec = (int64_t)v * n + g;
@@ -252,7 +313,8 @@ k_project(const float4* __restrict__ P, int64_t n, const gs_camera* __restrict__
             continue;
         }
         float Y[16];
-        sh_basis<D>(Vg.dir.x, Vg.dir.y, Vg.dir.z, Y);
+        const float3 ds = sh_dir(G, Vg.dir);
+        sh_basis<D>(ds.x, ds.y, ds.z, Y);
         float rgb[3];
         uint32_t mask = 0;
 #pragma unroll
@@ -278,7 +340,7 @@ k_project(const float4* __restrict__ P, int64_t n, const gs_camera* __restrict__
 // ------------------------------------------------------------------ adjoint
 template <int D>
 __global__ void __launch_bounds__(128, 4)
-k_project_bwd(const float4* __restrict__ P, int64_t n, const gs_camera* __restrict__ cams, int V,
+k_project_bwd(const float4* __restrict__ P, int64_t n, Dyn dyn, const gs_camera* __restrict__ cams, int V,
               const float4* __restrict__ proj, const float4* __restrict__ g2d,
               float4* __restrict__ dP, int accumulate) {
     const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -287,6 +349,7 @@ k_project_bwd(const float4* __restrict__ P, int64_t n, const gs_camera* __restri
     constexpr int NPL = (3 * NB + 3) / 4;
     Gauss G;
     load_gauss(P, n, g, G);
+    apply_dyn(dyn, g, G);
     // the SH coefficients are re-read per view (L1 hits) rather than held in
     // registers next to their gradient, to keep the thread's footprint small
     float dsh[NPL * 4];
@@ -309,7 +372,8 @@ k_project_bwd(const float4* __restrict__ P, int64_t n, const gs_camera* __restri
         dlogit += go * G.opac * (1.f - G.opac);
         // colour -> SH coefficients and view direction
         float Y[16];
-        sh_basis<D>(Vg.dir.x, Vg.dir.y, Vg.dir.z, Y);
+        const float3 dsd = sh_dir(G, Vg.dir);
+        sh_basis<D>(dsd.x, dsd.y, dsd.z, Y);
         float gm[3];
 #pragma unroll
         for (int ch = 0; ch < 3; ++ch) gm[ch] = (mask & (1u << ch)) ? 0.f : grgb[ch];
@@ -325,11 +389,17 @@ k_project_bwd(const float4* __restrict__ P, int64_t n, const gs_camera* __restri
                 const int j = 4 * pl + e;
                 if (j >= 3 * NB) break;
                 const int k = j / 3, ch = j % 3;
-                dsh[j] += gm[ch] * Y[k];
+                dsh[j] += gm[ch] * Y[k] * (k == 0 ? G.L : 1.f);
                 wsum[k] += gm[ch] * cv[e];
             }
         }
-        const float3 ddir = sh_basis_vjp<D>(Vg.dir.x, Vg.dir.y, Vg.dir.z, wsum);
+        float3 ddir = sh_basis_vjp<D>(dsd.x, dsd.y, dsd.z, wsum);
+        if (G.moved) {  // the SH direction is R_g^T dir
+            const float* R = G.Rg;
+            ddir = make_float3(R[0] * ddir.x + R[1] * ddir.y + R[2] * ddir.z,
+                               R[3] * ddir.x + R[4] * ddir.y + R[5] * ddir.z,
+                               R[6] * ddir.x + R[7] * ddir.y + R[8] * ddir.z);
+        }
         const float dd = Vg.dir.x * ddir.x + Vg.dir.y * ddir.y + Vg.dir.z * ddir.z;
         const float il = 1.f / Vg.len;
         dmx += (ddir.x - Vg.dir.x * dd) * il;
@@ -382,6 +452,26 @@ k_project_bwd(const float4* __restrict__ P, int64_t n, const gs_camera* __restri
         dmx += W[0] * dtx + W[3] * dty + W[6] * dtz;
         dmy += W[1] * dtx + W[4] * dty + W[7] * dtz;
         dmz += W[2] * dtx + W[5] * dty + W[8] * dtz;
+    }
+    if (G.moved) {  // back to the object frame: mean_w = R_g mean + t_g, Sigma_w = R_g Sigma R_g^T
+        const float* Rg = G.Rg;
+        const float m0 = dmx, m1 = dmy, m2 = dmz;
+        dmx = Rg[0] * m0 + Rg[3] * m1 + Rg[6] * m2;
+        dmy = Rg[1] * m0 + Rg[4] * m1 + Rg[7] * m2;
+        dmz = Rg[2] * m0 + Rg[5] * m1 + Rg[8] * m2;
+        const float Dw[9] = {D00, D01, D02, D01, D11, D12, D02, D12, D22};
+        float T1[9];  // Dw R_g
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) T1[i * 3 + j] = Dw[i * 3] * Rg[j] + Dw[i * 3 + 1] * Rg[3 + j] + Dw[i * 3 + 2] * Rg[6 + j];
+        // R_g^T T1
+        D00 = Rg[0] * T1[0] + Rg[3] * T1[3] + Rg[6] * T1[6];
+        D01 = Rg[0] * T1[1] + Rg[3] * T1[4] + Rg[6] * T1[7];
+        D02 = Rg[0] * T1[2] + Rg[3] * T1[5] + Rg[6] * T1[8];
+        D11 = Rg[1] * T1[1] + Rg[4] * T1[4] + Rg[7] * T1[7];
+        D12 = Rg[1] * T1[2] + Rg[4] * T1[5] + Rg[7] * T1[8];
+        D22 = Rg[2] * T1[2] + Rg[5] * T1[5] + Rg[8] * T1[8];
     }
     // Sigma = R diag(s^2) R^T:  dR = (dS + dS^T) R diag(s^2),  ds_k = s_k (R^T (dS + dS^T) R)_kk
     const float* R = G.Rq;
@@ -473,7 +563,7 @@ void launch_view_table(const gs_camera* d_cams, int V, int tile, ViewInfo* vt, l
     k_view_table<<<1, 32, 0, st>>>(d_cams, V, tile, vt, expect_tiles, status);
 }
 
-void launch_project(const float* params, int64_t n, int sh_degree, const gs_camera* d_cams,
+void launch_project(const float* params, int64_t n, int sh_degree, const Dyn& dyn, const gs_camera* d_cams,
                     const ViewInfo* vt, int V, int tile, float* proj, uint64_t* depth_kv, cudaStream_t st) {
     if (n <= 0) return;
     const int threads = 256;
@@ -481,15 +571,15 @@ void launch_project(const float* params, int64_t n, int sh_degree, const gs_came
     const float4* P = reinterpret_cast<const float4*>(params);
     float4* out = reinterpret_cast<float4*>(proj);
     switch (sh_degree) {
-        case 0: k_project<0><<<blocks, threads, 0, st>>>(P, n, d_cams, vt, V, tile, out, depth_kv); break;
-        case 1: k_project<1><<<blocks, threads, 0, st>>>(P, n, d_cams, vt, V, tile, out, depth_kv); break;
-        case 2: k_project<2><<<blocks, threads, 0, st>>>(P, n, d_cams, vt, V, tile, out, depth_kv); break;
-        default: k_project<3><<<blocks, threads, 0, st>>>(P, n, d_cams, vt, V, tile, out, depth_kv); break;
+        case 0: k_project<0><<<blocks, threads, 0, st>>>(P, n, dyn, d_cams, vt, V, tile, out, depth_kv); break;
+        case 1: k_project<1><<<blocks, threads, 0, st>>>(P, n, dyn, d_cams, vt, V, tile, out, depth_kv); break;
+        case 2: k_project<2><<<blocks, threads, 0, st>>>(P, n, dyn, d_cams, vt, V, tile, out, depth_kv); break;
+        default: k_project<3><<<blocks, threads, 0, st>>>(P, n, dyn, d_cams, vt, V, tile, out, depth_kv); break;
     }
 }
 
-void launch_project_bwd(const float* params, int64_t n, int sh_degree, const gs_camera* d_cams, int V,
-                        const float* proj, const float* grad2d, float* dparams, int accumulate,
+void launch_project_bwd(const float* params, int64_t n, int sh_degree, const Dyn& dyn, const gs_camera* d_cams,
+                        int V, const float* proj, const float* grad2d, float* dparams, int accumulate,
                         cudaStream_t st) {
     if (n <= 0) return;
     const int threads = 128;
@@ -499,10 +589,10 @@ void launch_project_bwd(const float* params, int64_t n, int sh_degree, const gs_
     const float4* g2 = reinterpret_cast<const float4*>(grad2d);
     float4* dP = reinterpret_cast<float4*>(dparams);
     switch (sh_degree) {
-        case 0: k_project_bwd<0><<<blocks, threads, 0, st>>>(P, n, d_cams, V, pr, g2, dP, accumulate); break;
-        case 1: k_project_bwd<1><<<blocks, threads, 0, st>>>(P, n, d_cams, V, pr, g2, dP, accumulate); break;
-        case 2: k_project_bwd<2><<<blocks, threads, 0, st>>>(P, n, d_cams, V, pr, g2, dP, accumulate); break;
-        default: k_project_bwd<3><<<blocks, threads, 0, st>>>(P, n, d_cams, V, pr, g2, dP, accumulate); break;
+        case 0: k_project_bwd<0><<<blocks, threads, 0, st>>>(P, n, dyn, d_cams, V, pr, g2, dP, accumulate); break;
+        case 1: k_project_bwd<1><<<blocks, threads, 0, st>>>(P, n, dyn, d_cams, V, pr, g2, dP, accumulate); break;
+        case 2: k_project_bwd<2><<<blocks, threads, 0, st>>>(P, n, dyn, d_cams, V, pr, g2, dP, accumulate); break;
+        default: k_project_bwd<3><<<blocks, threads, 0, st>>>(P, n, dyn, d_cams, V, pr, g2, dP, accumulate); break;
     }
 }
 

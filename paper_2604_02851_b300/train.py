@@ -25,7 +25,8 @@ from . import (Context, RECORD_BYTES, GRAD2D_STRIDE, PROJ_STRIDE, _lib, _ptr, _s
 
 class OnlineTrainer:
     def __init__(self, params, sh_degree: int, cams: dict, keys_cap: int, lr=1e-3, w_l1=0.8, w_ssim=0.2,
-                 delta_thr=1e-3, bg=(0.0, 0.0, 0.0), tile=16, sort_bits=8, ctx: Context | None = None):
+                 delta_thr=1e-3, bg=(0.0, 0.0, 0.0), tile=16, sort_bits=8, ctx: Context | None = None,
+                 dyn=None):
         import torch
         self.torch = torch
         self.params = params
@@ -59,7 +60,9 @@ class OnlineTrainer:
         self.d_step = torch.ones(1, dtype=torch.int32, device=dev)
         self.io = train_io(params, self.grads, self.m, self.v, self.baseline, self.targets, self.image,
                            self.d_loss, self.d_idx, self.d_records, self.d_count, self.d_step)
-        self.cfg = train_cfg(n, sh_degree, V, self.W, self.H, self.keys_cap, w_l1, w_ssim, self.bg, delta_thr, lr)
+        self.dyn = dyn  # kept alive: the step reads its device buffers
+        self.cfg = train_cfg(n, sh_degree, V, self.W, self.H, self.keys_cap, w_l1, w_ssim, self.bg, delta_thr, lr,
+                             dyn=dyn)
         self._captured = False
         self._events = None
         self._plain = None
@@ -125,7 +128,7 @@ class OnlineTrainer:
         HW = self.W * self.H
         for v in range(self.V):
             pv = b["views"][v]
-            gs_project(self.ctx, self.params, self.sh, pv["cams"], 1, proj=b["proj"], stream=stream)
+            gs_project(self.ctx, self.params, self.sh, pv["cams"], 1, proj=b["proj"], stream=stream, dyn=self.dyn)
             gs_bin_sort(self.ctx, b["proj"], pv["cams"], 1, self.n, pv["tt"], self.keys_cap, sorted_vals=b["vals"],
                         ranges=b["ranges"], d_num_keys=b["nk"], want_keys=False, stream=stream)
             k = int(b["nk"].item())  # host read of the key count
@@ -140,7 +143,7 @@ class OnlineTrainer:
             gs_raster_bwd(self.ctx, b["proj"], pv["cams"], 1, self.n, pv["tt"], b["vals"], b["ranges"], b["T"],
                           b["nc"], b["dimg"], bg=self.bg, grad2d=b["grad2d"], stream=stream)
             gs_project_bwd(self.ctx, self.params, self.sh, pv["cams"], 1, b["proj"], b["grad2d"], dparams=self.grads,
-                           accumulate=v > 0, stream=stream)
+                           accumulate=v > 0, stream=stream, dyn=self.dyn)
         b["step"] += 1
         gs_adam_step(self.ctx, self.params, self.grads, self.m, self.v,
                      adam_cfg(self.lr, step=b["step"]), stream=stream)
