@@ -37,7 +37,9 @@ WORKLOADS = {
     "c2_100k_4x512": (100_000, 3, 4, 512, 512),
     "c1_10k_128": (10_000, 0, 1, 128, 128),
     "prof_200k_8x720p": (200_000, 3, 8, 1280, 720),
+    "c5_3M_8x1080p_dynamic": (3_000_000, 3, 8, 1920, 1080),
 }
+DYNAMIC_WORKLOADS = {"c5_3M_8x1080p_dynamic"}
 DEFAULT_WORKLOAD = "c3_1M_8x720p"
 
 
@@ -157,9 +159,15 @@ class OracleSampler:
     views per step; Adam is timed on a slice of the parameters and scaled to
     all of them."""
 
-    def __init__(self, n, sh, V, W, H, seed_offset=0):
+    def __init__(self, n, sh, V, W, H, seed_offset=0, dynamic=False):
         import oracle as O
         self.O = O
+        self.dyn = None
+        if dynamic:
+            # the scene at frame 1 of the dynamic workload (poses, light, normals)
+            self.dyn = {"group": gi.rigid_groups(n, 16), "poses": gi.frame_poses(2, 16)[1],
+                        "normals": gi.unit_normals(n), "light": gi.light_directions(2)[1],
+                        "ambient": 0.3, "diffuse": 0.7}
         self.n, self.sh, self.V, self.W, self.H = n, sh, V, W, H
         self.planes = gi.planes_to_rows(gi.make_scene(n, sh, gi.SEED_MODEL + seed_offset)).astype(np.float64)
         self.target_planes = gi.planes_to_rows(gi.make_scene(n, sh, gi.SEED_TARGET + seed_offset)).astype(np.float64)
@@ -178,9 +186,9 @@ class OracleSampler:
     def sample(self) -> float:
         cam = self._band_cam(self.k)
         self.k += 1
-        tgt = self.O.forward(self.target_planes, self.sh, cam)["image"]  # the reference view (not timed)
+        tgt = self.O.forward(self.target_planes, self.sh, cam, dyn=self.dyn)["image"]  # reference view, not timed
         t0 = time.perf_counter()
-        self.O.loss_and_grad(self.planes, self.sh, cam, tgt)
+        self.O.loss_and_grad(self.planes, self.sh, cam, tgt, dyn=self.dyn)
         return time.perf_counter() - t0
 
     def adam_seconds(self) -> float:
@@ -218,7 +226,7 @@ def run_reference(args, rank, world):
     if rank != 0:
         return
     n, sh, V, W, H = WORKLOADS[args.workload]
-    smp = OracleSampler(n, sh, V, W, H)
+    smp = OracleSampler(n, sh, V, W, H, dynamic=args.workload in DYNAMIC_WORKLOADS)
     one = smp.sample()
     budget_s = 150.0
     # one band sample is the smallest unit; when the requested steps do not
@@ -261,20 +269,38 @@ def run_ours(args, rank, world, local_rank):
     cams = gi.ring_cameras(V, W, H)
     params = torch.from_numpy(planes).to(dev)
     tparams = torch.from_numpy(target_planes).to(dev)
-    drift = torch.from_numpy(signs).to(dev) * 1e-3
+    dynamic = args.workload in DYNAMIC_WORKLOADS
+    # static scene: the target set drifts by 1e-3 per parameter per step;
+    # dynamic scene: 16 rigid objects move every frame and the light turns
+    drift = None if dynamic else torch.from_numpy(signs).to(dev) * 1e-3
+    dyn = None
+    if dynamic:
+        G = 16
+        frames = max(args.steps, 1) + args.warmup + args.e2e_steps + 16
+        poses = gi.frame_poses(frames, G)
+        lights = gi.light_directions(frames)
+        dyn = gs.Dynamics(gi.rigid_groups(n, G), poses[0], gi.unit_normals(n), lights[0], 0.3, 0.7, device=dev)
+        frame = [0]
 
-    ctx = gs.Context(local_rank, 0, tile=args.tile, sort_bits=args.sort_bits, sort_items=args.sort_items)
-    keys_cap = estimate_keys(ctx, params, sh, cams, slack=1.3)
-    tr = OnlineTrainer(params, sh, cams, keys_cap, ctx=ctx)
+    ctx = gs.Context(local_rank, 0, tile=args.tile, sort_bits=args.sort_bits, sort_items=args.sort_items,
+                     binning=args.binning)
+    keys_cap = estimate_keys(ctx, params, sh, cams, slack=1.3, dyn=dyn)
+    tr = OnlineTrainer(params, sh, cams, keys_cap, ctx=ctx, dyn=dyn)
     packed = tr.packed
-    tctx = gs.Context(local_rank, 0, tile=args.tile, sort_bits=args.sort_bits, sort_items=args.sort_items)
-    tkeys = estimate_keys(tctx, tparams, sh, cams, slack=1.3)
+    tctx = gs.Context(local_rank, 0, tile=args.tile, sort_bits=args.sort_bits, sort_items=args.sort_items,
+                     binning=args.binning)
+    tkeys = estimate_keys(tctx, tparams, sh, cams, slack=1.3, dyn=dyn)
     tctx.reserve(tctx.workspace_size(packed, n, tkeys))
 
     def next_targets():
-        # the engine side: drift the target model and render its reference views
-        tparams.add_(drift)
-        gs.gs_render_batch(tctx, tparams, sh, tr.d_cams, V, tr.total_tiles, tkeys, tr.npix, image=tr.targets)
+        # the engine side: move the scene and render its reference views
+        if dynamic:
+            frame[0] = (frame[0] + 1) % len(lights)
+            dyn.set_frame(poses[frame[0]], lights[frame[0]])
+        else:
+            tparams.add_(drift)
+        gs.gs_render_batch(tctx, tparams, sh, tr.d_cams, V, tr.total_tiles, tkeys, tr.npix, image=tr.targets,
+                           dyn=dyn)
 
     phase_ev = [torch.cuda.Event(enable_timing=True) for _ in range(gs._lib.TRAIN_PHASE_EVENTS)]
     next_targets()
@@ -324,7 +350,7 @@ def run_ours(args, rank, world, local_rank):
     phase_avg = {name: float(ms / args.steps) for name, ms in zip(gs._lib.TRAIN_PHASES, phase_ms)}
 
     # ---- work counts of the current model, for the roofline (outside the timed region)
-    proj = gs.gs_project(ctx, params, sh, tr.d_cams, V)
+    proj = gs.gs_project(ctx, params, sh, tr.d_cams, V, dyn=dyn)
     _, vals, ranges, nk = gs.gs_bin_sort(ctx, proj, tr.d_cams, V, n, tr.total_tiles, keys_cap, want_keys=False)
     _, T, nc = gs.gs_render_fwd(ctx, proj, tr.d_cams, V, n, tr.total_tiles, vals, ranges, tr.npix)
     torch.cuda.synchronize()
@@ -388,7 +414,7 @@ def run_ours(args, rank, world, local_rank):
     if rank == 0:
         cpu = None
         if world == 1 and not args.no_cpu_baseline:
-            smp = OracleSampler(n, sh, V, W, H)
+            smp = OracleSampler(n, sh, V, W, H, dynamic=dynamic)
             times = [smp.sample() for _ in range(args.cpu_samples)]
             cpu = {"value": 1.0 / smp.step_seconds(times), "unit": "steps/s", "cores": omp_cores(),
                    "kind": "oracle", "sample": smp.describe(args.cpu_samples)}
@@ -397,7 +423,12 @@ def run_ours(args, rank, world, local_rank):
                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                "config": {"workload": args.workload, "gaussians": n, "sh_degree": sh, "views": V,
                           "resolution": [W, H], "keys_per_step": K, "keys_cap": keys_cap, "tile": args.tile,
-                          "sort_digit_bits": args.sort_bits, "sort_items": args.sort_items, "graph": True,
+                          "dynamics": "16 rigid objects, new SE(3) pose per frame (spin <= 2 deg/frame, "
+                                      "sinusoidal translation 0.1), light at 45 deg zenith turning 1 deg/frame; "
+                                      "Lambertian relight of the DC term (ambient 0.3, diffuse 0.7)"
+                          if dynamic else None,
+                          "sort_digit_bits": args.sort_bits, "sort_items": args.sort_items, "binning": args.binning,
+                          "graph": True,
                           "l2": "inputs larger than L2 (params 240 MB, keys > 1 GB per step)",
                           "targets": "re-rendered each step by gs_render_batch outside the step's events",
                           "parallelism": "replicas" if world > 1 else "single"},
@@ -505,6 +536,7 @@ def main():
     ap.add_argument("--tile", type=int, default=16)
     ap.add_argument("--sort-bits", type=int, default=8)
     ap.add_argument("--sort-items", type=int, default=16)
+    ap.add_argument("--binning", choices=("two_level", "direct"), default="two_level")
     ap.add_argument("--e2e-steps", type=int, default=30)
     ap.add_argument("--cpu-samples", type=int, default=12)
     ap.add_argument("--plain-steps", type=int, default=10)

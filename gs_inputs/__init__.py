@@ -197,19 +197,30 @@ def unit_normals(n: int, seed: int = SEED_MODEL + 10) -> np.ndarray:
     return (v / np.linalg.norm(v, axis=1, keepdims=True)).astype(np.float32)
 
 
-def frame_rigid_motions(n_frames: int, n_groups: int = 16, max_deg: float = 2.0,
-                        max_trans: float = 0.02, seed: int = SEED_MODEL + 20):
-    """Per-frame, per-group random rigid motions: a rotation of angle
-    U[0, max_deg] degrees about a uniform axis (as a unit quaternion w, x, y, z)
-    and a translation with components U[-max_trans, max_trans].
-    Returns (quats [F, G, 4], trans [F, G, 3]) as float64."""
+def frame_poses(n_frames: int, n_groups: int = 16, max_deg_per_frame: float = 2.0,
+                amplitude: float = 0.1, period: int = 120, seed: int = SEED_MODEL + 20) -> np.ndarray:
+    """Absolute object poses for frames 0..n_frames-1, float64 [F, G, 8]
+    (unit quaternion w, x, y, z; translation x, y, z; 0).
+
+    Group g spins about a fixed uniform axis at a rate U[0.25, 1] x
+    max_deg_per_frame degrees per frame, and its translation follows
+    amplitude * sin(2 pi f / period + phase_g) along a fixed uniform direction,
+    so frame 0 is near identity and the objects stay within the camera ring."""
     rng = _rng(seed)
-    axis = rng.normal(size=(n_frames, n_groups, 3))
-    axis /= np.linalg.norm(axis, axis=2, keepdims=True)
-    ang = np.radians(rng.uniform(0.0, max_deg, size=(n_frames, n_groups)))
-    q = np.concatenate([np.cos(ang / 2)[..., None], np.sin(ang / 2)[..., None] * axis], axis=2)
-    tr = rng.uniform(-max_trans, max_trans, size=(n_frames, n_groups, 3))
-    return q, tr
+    axis = rng.normal(size=(n_groups, 3))
+    axis /= np.linalg.norm(axis, axis=1, keepdims=True)
+    rate = np.radians(rng.uniform(0.25, 1.0, size=n_groups) * max_deg_per_frame)
+    direc = rng.normal(size=(n_groups, 3))
+    direc /= np.linalg.norm(direc, axis=1, keepdims=True)
+    phase = rng.uniform(0.0, 2 * math.pi, size=n_groups)
+    f = np.arange(n_frames)[:, None]
+    ang = rate[None, :] * f
+    out = np.zeros((n_frames, n_groups, 8))
+    out[..., 0] = np.cos(ang / 2)
+    out[..., 1:4] = np.sin(ang / 2)[..., None] * axis[None]
+    out[..., 4:7] = (amplitude * (np.sin(2 * math.pi * f / period + phase[None]) - np.sin(phase[None])))[..., None] \
+        * direc[None]
+    return out
 
 
 def light_directions(n_frames: int, zenith_deg: float = 45.0, step_deg: float = 1.0):

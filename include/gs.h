@@ -113,7 +113,7 @@ gs_status_t gs_ctx_destroy(gs_ctx* ctx);
 /* Ensures the workspace holds at least `bytes`; reallocates (after a device
  * synchronise) if it does not.  Synchronous; never call during capture. */
 gs_status_t gs_ctx_reserve(gs_ctx* ctx, size_t bytes);
-/* Tile size B in pixels (8, 16 or 32; default 16).  Changes the tile grid
+/* Tile size B in pixels (8 or 16; default 16).  Changes the tile grid
  * seen by every later call. */
 gs_status_t gs_ctx_set_tile(gs_ctx* ctx, int32_t tile);
 /* Radix digit width of the tile-key sort (4..8 bits; default 8). */
@@ -121,6 +121,18 @@ gs_status_t gs_ctx_set_sort_bits(gs_ctx* ctx, int32_t bits);
 /* Keys per thread of a tile-key sort pass (8, 12 or 16; default 16): larger
  * tiles mean fewer look-back steps, smaller ones more resident blocks. */
 gs_status_t gs_ctx_set_sort_items(gs_ctx* ctx, int32_t items);
+/* How (tile, Gaussian) entries are binned; both give the identical sorted
+ * arrays and ranges.
+ *   GS_BINNING_TWO_LEVEL (default): one entry per touched super-tile of
+ *     8 x 8 tiles is emitted in depth order and sorted stably by super-tile;
+ *     each super-tile's list is then expanded into its tiles' lists, whose
+ *     offsets come from a count and a scan.  The radix sort moves roughly
+ *     (tiles per Gaussian / super-tiles per Gaussian) times fewer entries.
+ *   GS_BINNING_DIRECT: one entry per touched tile, sorted stably by tile key.
+ * Returns GS_ERR_ARG for any other mode. */
+#define GS_BINNING_TWO_LEVEL 0
+#define GS_BINNING_DIRECT 1
+gs_status_t gs_ctx_set_binning(gs_ctx* ctx, int32_t mode);
 /* Reads and clears the device status word (synchronises `stream`).
  * *status receives the first error a kernel recorded since the last read
  * (GS_OK if none); *detail receives the required size for GS_ERR_CAPACITY. */

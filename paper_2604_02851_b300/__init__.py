@@ -77,11 +77,15 @@ def total_pixels(cams) -> int:
 
 
 # ------------------------------------------------------------------ context
+# gs_ctx_set_binning modes
+BINNING = {"two_level": 0, "direct": 1}
+
+
 class Context:
     """Owns a gs_ctx (device workspace, status word, graph)."""
 
     def __init__(self, device: int = 0, workspace_bytes: int = 0, tile: int = 16, sort_bits: int = 8,
-                 sort_items: int = 16):
+                 sort_items: int = 16, binning: str = "two_level"):
         L = _lib.lib()
         p = C.c_void_p()
         check("gs_ctx_create", L.gs_ctx_create(C.byref(p), device, workspace_bytes))
@@ -91,6 +95,10 @@ class Context:
         check("gs_ctx_set_tile", L.gs_ctx_set_tile(p, tile))
         check("gs_ctx_set_sort_bits", L.gs_ctx_set_sort_bits(p, sort_bits))
         check("gs_ctx_set_sort_items", L.gs_ctx_set_sort_items(p, sort_items))
+        if binning not in BINNING:
+            raise ValueError(f"binning must be one of {sorted(BINNING)}")
+        self.binning = binning
+        check("gs_ctx_set_binning", L.gs_ctx_set_binning(p, BINNING[binning]))
 
     def reserve(self, nbytes: int) -> None:
         check("gs_ctx_reserve", _lib.lib().gs_ctx_reserve(self.ptr, int(nbytes)))

@@ -71,7 +71,7 @@ FusedPlan plan_fused(void* base, int V, int64_t n, int64_t keys_cap, int64_t tot
     FusedPlan p{};
     p.vt = c.take<ViewInfo>(V + 1);
     p.proj = c.take<float>((size_t)V * n * kProjStride);
-    p.sort = c.take<char>(sort_scratch_bytes(V, n, keys_cap));
+    p.sort = c.take<char>(sort_scratch_bytes(V, n, keys_cap, total_tiles));
     p.vals = c.take<uint32_t>(keys_cap);
     p.ranges = c.take<uint32_t>(total_tiles * 2);
     p.n_keys = c.take<uint32_t>(1);
@@ -175,6 +175,12 @@ gs_status_t gs_ctx_set_sort_items(gs_ctx* ctx, int32_t items) {
     return GS_OK;
 }
 
+gs_status_t gs_ctx_set_binning(gs_ctx* ctx, int32_t mode) {
+    if (!ctx || (mode != GS_BINNING_TWO_LEVEL && mode != GS_BINNING_DIRECT)) return GS_ERR_ARG;
+    ctx->binning = mode == GS_BINNING_DIRECT ? kBinDirect : kBinTwoLevel;
+    return GS_OK;
+}
+
 gs_status_t gs_get_status(gs_ctx* ctx, void* stream, int32_t* status, int64_t* detail) {
     if (!ctx || !status) return GS_ERR_ARG;
     DeviceGuard g(ctx->device);
@@ -229,13 +235,13 @@ gs_status_t gs_bin_sort(gs_ctx* ctx, const float* proj, const gs_camera* d_cams,
         return GS_ERR_ARG;
     Carver c(ctx->ws);
     ViewInfo* vt = c.take<ViewInfo>(n_views + 1);
-    char* ss = c.take<char>(sort_scratch_bytes(n_views, n, keys_cap));
+    char* ss = c.take<char>(sort_scratch_bytes(n_views, n, keys_cap, total_tiles));
     if (check_ws(ctx, c.off)) return GS_ERR_CAPACITY;
     DeviceGuard g(ctx->device);
     SortScratch s;
-    carve_sort_scratch(ss, n_views, n, keys_cap, &s);
+    carve_sort_scratch(ss, n_views, n, keys_cap, total_tiles, &s);
     launch_view_table(d_cams, n_views, ctx->tile, vt, total_tiles, ctx->d_status, S(stream));
-    launch_bin_sort(proj, vt, n_views, n, keys_cap, total_tiles, ctx->sort_bits, ctx->sort_items, s, false, sorted_keys,
+    launch_bin_sort(proj, vt, n_views, n, keys_cap, total_tiles, ctx->binning, ctx->sort_bits, ctx->sort_items, s, false, sorted_keys,
                     sorted_vals, ranges, d_num_keys, ctx->d_status, ctx->sm_count, S(stream));
     return launch_check();
 }
@@ -347,13 +353,13 @@ gs_status_t gs_render_batch(gs_ctx* ctx, const gs_scene* scene, const gs_camera*
     DeviceGuard g(ctx->device);
     cudaStream_t st = S(stream);
     SortScratch s;
-    carve_sort_scratch(p.sort, n_requests, scene->n, keys_cap, &s);
+    carve_sort_scratch(p.sort, n_requests, scene->n, keys_cap, total_tiles, &s);
     const float3 b = bg ? make_float3(bg[0], bg[1], bg[2]) : make_float3(0.f, 0.f, 0.f);
     launch_view_table(d_cams, n_requests, ctx->tile, p.vt, total_tiles, ctx->d_status, st);
     launch_project(scene->params, scene->n, scene->sh_degree, make_dyn(scene->dyn), d_cams, p.vt, n_requests,
                    ctx->tile, p.proj,
                    s.dkv[0], st);
-    launch_bin_sort(p.proj, p.vt, n_requests, scene->n, keys_cap, total_tiles, ctx->sort_bits, ctx->sort_items, s, true, nullptr,
+    launch_bin_sort(p.proj, p.vt, n_requests, scene->n, keys_cap, total_tiles, ctx->binning, ctx->sort_bits, ctx->sort_items, s, true, nullptr,
                     p.vals, p.ranges, p.n_keys, ctx->d_status, ctx->sm_count, st);
     launch_render_fwd(p.proj, p.vt, n_requests, scene->n, ctx->tile, p.vals, p.ranges, b, image, nullptr,
                       nullptr, total_tiles, st);
@@ -396,14 +402,14 @@ gs_status_t gs_train_step_events(gs_ctx* ctx, const gs_camera* d_cams, const gs_
     DeviceGuard g(ctx->device);
     cudaStream_t st = S(stream);
     SortScratch s;
-    carve_sort_scratch(p.sort, V, n, cfg->keys_cap, &s);
+    carve_sort_scratch(p.sort, V, n, cfg->keys_cap, tt, &s);
     const float3 b = make_float3(cfg->bg[0], cfg->bg[1], cfg->bg[2]);
     mark(ev, 0, st);
     launch_view_table(d_cams, V, B, p.vt, tt, ctx->d_status, st);
     const Dyn dyn = make_dyn(cfg->dyn);
     launch_project(io->params, n, cfg->sh_degree, dyn, d_cams, p.vt, V, B, p.proj, s.dkv[0], st);
     mark(ev, 1, st);
-    launch_bin_sort(p.proj, p.vt, V, n, cfg->keys_cap, tt, ctx->sort_bits, ctx->sort_items, s, true, nullptr,
+    launch_bin_sort(p.proj, p.vt, V, n, cfg->keys_cap, tt, ctx->binning, ctx->sort_bits, ctx->sort_items, s, true, nullptr,
                     p.vals, p.ranges, p.n_keys, ctx->d_status, ctx->sm_count, st, ev ? mark : nullptr, ev, 2);
     mark(ev, 4, st);
     launch_render_fwd(p.proj, p.vt, V, n, B, p.vals, p.ranges, b, io->image, p.T_final, p.n_contrib, tt, st);

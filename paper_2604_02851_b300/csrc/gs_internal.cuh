@@ -23,11 +23,17 @@ constexpr float kGuard = 1.3f;
 
 // Per-view derived geometry, computed on the device from the camera array.
 // Entry V holds the totals (tile_off = total tiles, pix_off = total pixels).
+// Super-tiles group kSuper x kSuper tiles for the two-level binning.
+constexpr int kSuperShift = 3;
+constexpr int kSuper = 1 << kSuperShift;
+
 struct ViewInfo {
     int32_t tx, ty;       // tiles along x / y
     int32_t width, height;
     int64_t tile_off;     // first global tile index of this view
     int64_t pix_off;      // first pixel (per channel) of this view
+    int32_t stx, sty;     // super-tiles along x / y
+    int64_t stile_off;    // first global super-tile index of this view
 };
 
 struct DevStatus {
@@ -93,15 +99,30 @@ struct SortScratch {
     unsigned long long* lookback;  // [4][max_tiles][256]
     int64_t max_sort_tiles;    // per pass
     uint32_t* d_count_depth;   // V*n as a device scalar
+    // two-level binning (super-tile lists, then per-tile lists)
+    uint2* cranges;            // [total_tiles] bound on super-tiles: coarse [start, end)
+    uint32_t* chunk_first;     // [total_tiles + 1] first chunk of each super-tile
+    uint32_t* chunk_s;         // [max_chunks] super-tile of each chunk
+    uint32_t* chunk_off;       // [max_chunks][64] per-tile counts, then offsets
+    uint32_t* tile_count;      // [total_tiles]
+    uint32_t* d_count_coarse;  // coarse entries stored
+    uint32_t* d_n_chunks;
+    unsigned long long* d_fine_total;  // fine entries implied by the rectangles
+    int64_t max_chunks;
     size_t bytes;              // total scratch size
 };
 
-size_t sort_scratch_bytes(int V, int64_t n, int64_t keys_cap);
-void carve_sort_scratch(char* base, int V, int64_t n, int64_t keys_cap, SortScratch* s);
+size_t sort_scratch_bytes(int V, int64_t n, int64_t keys_cap, int64_t total_tiles);
+void carve_sort_scratch(char* base, int V, int64_t n, int64_t keys_cap, int64_t total_tiles, SortScratch* s);
+
+// Binning modes (gs_ctx_set_binning).
+constexpr int kBinTwoLevel = 0;
+constexpr int kBinDirect = 1;
 
 // Full bin + sort: depth sort, key emission, tile-key sort, ranges.
 void launch_bin_sort(const float* proj, const ViewInfo* vt, int V, int64_t n, int64_t keys_cap,
-                     int64_t total_tiles, int sort_bits, int sort_items, const SortScratch& s, bool depth_ready,
+                     int64_t total_tiles, int binning, int sort_bits, int sort_items, const SortScratch& s,
+                     bool depth_ready,
                      uint32_t* sorted_keys, uint32_t* sorted_vals, uint32_t* ranges,
                      uint32_t* d_num_keys, DevStatus* status, int sm_count, cudaStream_t st,
                      void (*mark)(void* const*, int, cudaStream_t) = nullptr, void* const* events = nullptr,
@@ -157,6 +178,7 @@ struct gs_ctx {
     int tile = 16;
     int sort_bits = 8;
     int sort_items = 16;
+    int binning = gs::kBinTwoLevel;
     void* ws = nullptr;
     size_t ws_bytes = 0;
     gs::DevStatus* d_status = nullptr;

@@ -535,7 +535,7 @@ k_project_bwd(const float4* __restrict__ P, int64_t n, Dyn dyn, const gs_camera*
 __global__ void k_view_table(const gs_camera* __restrict__ cams, int V, int tile, ViewInfo* vt,
                              long long expect_tiles, DevStatus* status) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    int64_t toff = 0, poff = 0;
+    int64_t toff = 0, poff = 0, soff = 0;
     for (int v = 0; v < V; ++v) {
         ViewInfo vi;
         vi.width = cams[v].width;
@@ -544,14 +544,19 @@ __global__ void k_view_table(const gs_camera* __restrict__ cams, int V, int tile
         vi.ty = (vi.height + tile - 1) / tile;
         vi.tile_off = toff;
         vi.pix_off = poff;
+        vi.stx = (vi.tx + kSuper - 1) >> kSuperShift;
+        vi.sty = (vi.ty + kSuper - 1) >> kSuperShift;
+        vi.stile_off = soff;
         vt[v] = vi;
         toff += (int64_t)vi.tx * vi.ty;
         poff += (int64_t)vi.width * vi.height;
+        soff += (int64_t)vi.stx * vi.sty;
     }
     ViewInfo tot;
-    tot.tx = tot.ty = tot.width = tot.height = 0;
+    tot.tx = tot.ty = tot.width = tot.height = tot.stx = tot.sty = 0;
     tot.tile_off = toff;
     tot.pix_off = poff;
+    tot.stile_off = soff;
     vt[V] = tot;
     if (expect_tiles >= 0 && toff != expect_tiles) record_status(status, GS_ERR_ARG, toff);
 }

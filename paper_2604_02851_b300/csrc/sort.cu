@@ -360,7 +360,8 @@ __global__ void __launch_bounds__(kEmitThreads)
 k_emit(const uint64_t* __restrict__ dsorted, int64_t total, int64_t n, const uint4* __restrict__ proj,
        const ViewInfo* __restrict__ vt, int64_t cap, uint64_t* __restrict__ kv,
        unsigned long long* __restrict__ lookback, uint32_t* block_counter, uint32_t* d_num_keys,
-       int passes, uint32_t* __restrict__ hist, DevStatus* status) {
+       int passes, uint32_t* __restrict__ hist, int sshift, unsigned long long* fine_total, uint32_t key_bound,
+       DevStatus* status) {
     constexpr int R = 1 << BITS;
     __shared__ uint32_t s_hist[kMaxPasses][R];
     __shared__ int s_mark[kEmitWarps][32];
@@ -377,6 +378,7 @@ k_emit(const uint64_t* __restrict__ dsorted, int64_t total, int64_t n, const uin
     uint32_t cnt[kEmitRounds], lo[kEmitRounds], hi[kEmitRounds], gi[kEmitRounds], kb[kEmitRounds],
         tx[kEmitRounds], incl[kEmitRounds], rtot[kEmitRounds];
     uint32_t wtot = 0;
+    unsigned long long fine = 0;
 #pragma unroll
     for (int r = 0; r < kEmitRounds; ++r) {
         const int64_t idx = b * kEmitBlock + warp * (32 * kEmitRounds) + r * 32 + lane;
@@ -392,12 +394,29 @@ k_emit(const uint64_t* __restrict__ dsorted, int64_t total, int64_t n, const uin
             gi[r] = rr - v * (uint32_t)n;
             kb[r] = (uint32_t)vt[v].tile_off;
             tx[r] = (uint32_t)vt[v].tx;
+            fine += p3.z;
+            if (sshift && p3.z) {
+                // super-tile rectangle covering the tile rectangle
+                const uint32_t sx0 = (p3.x & 0xFFFFu) >> sshift, sy0 = (p3.x >> 16) >> sshift;
+                const uint32_t sx1 = (((p3.y & 0xFFFFu) - 1u) >> sshift) + 1u;
+                const uint32_t sy1 = (((p3.y >> 16) - 1u) >> sshift) + 1u;
+                lo[r] = sx0 | (sy0 << 16);
+                hi[r] = sx1 | (sy1 << 16);
+                cnt[r] = (sx1 - sx0) * (sy1 - sy0);
+                kb[r] = (uint32_t)vt[v].stile_off;
+                tx[r] = (uint32_t)vt[v].stx;
+            }
         }
         incl[r] = warp_incl_scan(cnt[r], lane);
         rtot[r] = __shfl_sync(0xFFFFFFFFu, incl[r], 31);
         wtot += rtot[r];
     }
     if (lane == 0) s_wtot[warp] = wtot;
+    if (fine_total) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) fine += __shfl_xor_sync(0xFFFFFFFFu, fine, o);
+        if (lane == 0 && fine) atomicAdd(fine_total, fine);
+    }
     __syncthreads();
     uint32_t wexcl = 0, btot = 0;
     for (int w = 0; w < kEmitWarps; ++w) {
@@ -412,7 +431,8 @@ k_emit(const uint64_t* __restrict__ dsorted, int64_t total, int64_t n, const uin
         if (b == nblk - 1) {
             const unsigned long long K = excl + btot;
             *d_num_keys = (uint32_t)(K > 0xFFFFFFFFull ? 0xFFFFFFFFull : K);
-            if ((long long)K > cap) record_status(status, GS_ERR_CAPACITY, (long long)K);
+            // two-level: the fine total decides capacity (k_fine_total)
+            if (!fine_total && (long long)K > cap) record_status(status, GS_ERR_CAPACITY, (long long)K);
         }
     }
     __syncthreads();
@@ -458,6 +478,9 @@ k_emit(const uint64_t* __restrict__ dsorted, int64_t total, int64_t n, const uin
                 const uint32_t ty = (uint32_t)(((float)j + 0.5f) * o_rw);
                 const uint32_t txx = j - ty * o_w;
                 key = o_kb + ((o_lo >> 16) + ty) * o_tx + (o_lo & 0xFFFFu) + txx;
+                // a view table larger than the caller's tile count (reported
+                // by k_view_table) must not index past the ranges arrays
+                if (key >= key_bound) key = key_bound - 1u;
                 kv[base + o] = ((uint64_t)key << 32) | o_g;
             }
             const uint32_t act = __ballot_sync(0xFFFFFFFFu, stored);
@@ -476,6 +499,341 @@ k_emit(const uint64_t* __restrict__ dsorted, int64_t total, int64_t n, const uin
     for (int i = threadIdx.x; i < passes * R; i += kEmitThreads) {
         const uint32_t c = (&s_hist[0][0])[i];
         if (c) atomicAdd(&hist[(i / R) * 256 + (i % R)], c);
+    }
+}
+
+// ------------------------------------------------------------ two-level binning
+// Coarse entries (super-tile, Gaussian) are emitted in depth order and sorted
+// stably by super-tile; each super-tile's depth-ordered list is then cut into
+// chunks of kFineChunk entries and expanded into its kSuper x kSuper tiles'
+// lists (one warp per chunk).  Per chunk, k_fine_count counts the entries of
+// every tile; the counts are scanned over the chunks of a super-tile
+// (k_fine_prefix) and over all tiles (k_tile_scan, which also writes the
+// ranges); k_fine_write then
+// writes each chunk's entries at its offsets, in chunk order and, within a
+// chunk, in list order -- the stable (tile, depth, index) order.
+constexpr int kFineThreads = 256;
+constexpr int kFineChunk = 256;
+
+// Fine total from the rectangles: number of stored entries, capacity check.
+__global__ void k_fine_total(const unsigned long long* fine_total, int64_t cap, uint32_t* d_num_keys,
+                             DevStatus* status) {
+    const unsigned long long K = *fine_total;
+    *d_num_keys = (uint32_t)(K > 0xFFFFFFFFull ? 0xFFFFFFFFull : K);
+    if ((long long)K > cap) record_status(status, GS_ERR_CAPACITY, (long long)K);
+}
+
+__device__ __forceinline__ int find_super_view(const ViewInfo* __restrict__ vt, int V, int64_t s) {
+    int lo = 0, hi = V - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (vt[mid].stile_off <= s) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Chunk table (one block): chunk_first[s] = first chunk of super-tile s,
+// chunk_s[c] = super-tile of chunk c, *d_n_chunks = total (clamped).
+__global__ void __launch_bounds__(1024)
+k_fine_chunks(const uint2* __restrict__ cranges, const ViewInfo* __restrict__ vt, int V, int64_t ns_bound,
+              uint32_t* __restrict__ chunk_first, uint32_t* __restrict__ chunk_s, uint32_t* d_n_chunks,
+              int64_t max_chunks) {
+    __shared__ uint32_t s_part[1024];
+    const int64_t ns = vt[V].stile_off < ns_bound ? vt[V].stile_off : ns_bound;
+    const int64_t per = (ns + blockDim.x - 1) / blockDim.x;
+    const int64_t a = (int64_t)threadIdx.x * per;
+    const int64_t e = a + per < ns ? a + per : ns;
+    uint32_t sum = 0;
+    for (int64_t s = a; s < e; ++s) {
+        const uint2 r = cranges[s];
+        sum += (r.y > r.x ? r.y - r.x + kFineChunk - 1 : 0u) / kFineChunk;
+    }
+    s_part[threadIdx.x] = sum;
+    __syncthreads();
+    for (int o = 1; o < (int)blockDim.x; o <<= 1) {
+        const uint32_t y = threadIdx.x >= (unsigned)o ? s_part[threadIdx.x - o] : 0u;
+        __syncthreads();
+        s_part[threadIdx.x] += y;
+        __syncthreads();
+    }
+    uint32_t run = s_part[threadIdx.x] - sum;
+    for (int64_t s = a; s < e; ++s) {
+        const uint2 r = cranges[s];
+        const uint32_t nc = (r.y > r.x ? r.y - r.x + kFineChunk - 1 : 0u) / kFineChunk;
+        chunk_first[s] = run;
+        for (uint32_t c = 0; c < nc; ++c)
+            if ((int64_t)run + c < max_chunks) chunk_s[run + c] = (uint32_t)s;
+        run += nc;
+    }
+    if (threadIdx.x == blockDim.x - 1) {
+        chunk_first[ns] = s_part[threadIdx.x];
+        const uint32_t tot = s_part[threadIdx.x];
+        *d_n_chunks = (int64_t)tot < max_chunks ? tot : (uint32_t)max_chunks;
+    }
+}
+
+// Bit k = 8*ky + kx of the result: tile (ox + kx, oy + ky) lies in the tile
+// rectangle packed in (lo, hi).
+__device__ __forceinline__ uint64_t rect_mask(uint32_t lo, uint32_t hi, int ox, int oy) {
+    const int x0 = max((int)(lo & 0xFFFFu) - ox, 0), x1 = min((int)(hi & 0xFFFFu) - ox, kSuper);
+    const int y0 = max((int)(lo >> 16) - oy, 0), y1 = min((int)(hi >> 16) - oy, kSuper);
+    if (x1 <= x0 || y1 <= y0) return 0ULL;
+    const uint64_t row = (uint64_t)(((1u << x1) - 1u) & ~((1u << x0) - 1u)) * 0x0101010101010101ULL;
+    const uint64_t hi_rows = y1 >= kSuper ? ~0ULL : ((1ULL << (8 * y1)) - 1ULL);
+    const uint64_t lo_rows = (1ULL << (8 * y0)) - 1ULL;
+    return row & hi_rows & ~lo_rows;
+}
+
+// 32 x 32 bit-matrix transpose across a warp: on return bit j of lane k's
+// word is bit k of lane j's input word (recursive block swaps, 5 rounds).
+__device__ __forceinline__ uint32_t transpose32(uint32_t x, int lane) {
+    const uint32_t masks[5] = {0x0000FFFFu, 0x00FF00FFu, 0x0F0F0F0Fu, 0x33333333u, 0x55555555u};
+#pragma unroll
+    for (int r = 0; r < 5; ++r) {
+        const int sh = 16 >> r;
+        const uint32_t m = masks[r];
+        const uint32_t y = __shfl_xor_sync(0xFFFFFFFFu, x, sh);
+        x = (lane & sh) ? ((x & ~m) | ((y & ~m) >> sh)) : ((x & m) | ((y & m) << sh));
+    }
+    return x;
+}
+
+// Chunk geometry shared by the count and write passes.
+struct FineChunk {
+    uint32_t a, e;          // coarse entries [a, e)
+    int v, ox, oy;          // view, tile origin of the super-tile
+    uint32_t t0, t1;        // this lane's tiles (k = lane, k = lane + 32)
+    bool in0, in1;
+    uint64_t valid;         // tiles of the super-tile inside the view
+};
+
+__device__ __forceinline__ FineChunk fine_chunk(uint32_t c, const uint2* __restrict__ cranges,
+                                                const uint32_t* __restrict__ chunk_first,
+                                                const uint32_t* __restrict__ chunk_s, const ViewInfo* __restrict__ vt,
+                                                int V, int64_t total_tiles, int lane) {
+    FineChunk f;
+    const uint32_t s = chunk_s[c];
+    const uint2 cr = cranges[s];
+    f.a = cr.x + (c - chunk_first[s]) * (uint32_t)kFineChunk;
+    f.e = min(cr.y, f.a + (uint32_t)kFineChunk);
+    f.v = find_super_view(vt, V, s);
+    const ViewInfo vi = vt[f.v];
+    const int ls = (int)(s - vi.stile_off);
+    f.ox = (ls % vi.stx) << kSuperShift;
+    f.oy = (ls / vi.stx) << kSuperShift;
+    const int x = f.ox + (lane & (kSuper - 1));
+    const int y0 = f.oy + (lane >> kSuperShift), y1 = y0 + 4;
+    const int64_t tt0 = vi.tile_off + (int64_t)y0 * vi.tx + x, tt1 = vi.tile_off + (int64_t)y1 * vi.tx + x;
+    f.in0 = x < vi.tx && y0 < vi.ty && tt0 < total_tiles;
+    f.in1 = x < vi.tx && y1 < vi.ty && tt1 < total_tiles;
+    f.t0 = f.in0 ? (uint32_t)tt0 : 0u;
+    f.t1 = f.in1 ? (uint32_t)tt1 : 0u;
+    f.valid = (uint64_t)__ballot_sync(0xFFFFFFFFu, f.in0) | ((uint64_t)__ballot_sync(0xFFFFFFFFu, f.in1) << 32);
+    return f;
+}
+
+// Group `grp` of a chunk: lane's entry value and its super-tile tile mask,
+// transposed so that lane l holds the group's entries covering tile l (c0)
+// and tile l + 32 (c1), bit j = group entry j.
+__device__ __forceinline__ void fine_group(const FineChunk& f, uint32_t grp, const uint32_t* __restrict__ cvals,
+                                           const uint4* __restrict__ proj, int64_t n, int lane, uint32_t& gval,
+                                           uint32_t& c0, uint32_t& c1) {
+    const uint32_t i = f.a + grp * 32u + (uint32_t)lane;
+    uint64_t m = 0;
+    gval = 0;
+    if (i < f.e) {
+        gval = cvals[i];
+        const uint4 p3 = proj[((size_t)f.v * (size_t)n + gval) * 4 + 3];
+        m = rect_mask(p3.x, p3.y, f.ox, f.oy) & f.valid;
+    }
+    c0 = transpose32((uint32_t)m, lane);
+    c1 = transpose32((uint32_t)(m >> 32), lane);
+}
+
+// Count pass, one warp per chunk: chunk_off[c][k] := entries of chunk c in
+// tile k of its super-tile.
+__global__ void __launch_bounds__(kFineThreads)
+k_fine_count(const uint32_t* __restrict__ cvals, const uint2* __restrict__ cranges,
+             const uint32_t* __restrict__ chunk_first, const uint32_t* __restrict__ chunk_s,
+             const uint32_t* __restrict__ d_n_chunks, const uint4* __restrict__ proj, int64_t n,
+             const ViewInfo* __restrict__ vt, int V, int64_t total_tiles, uint32_t* __restrict__ chunk_off) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t nchunks = *d_n_chunks;
+    const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < nchunks; c += nw) {
+        const FineChunk f = fine_chunk(c, cranges, chunk_first, chunk_s, vt, V, total_tiles, lane);
+        uint32_t n0 = 0, n1 = 0;
+        for (uint32_t grp = 0; f.a + grp * 32u < f.e; ++grp) {
+            uint32_t gval, c0, c1;
+            fine_group(f, grp, cvals, proj, n, lane, gval, c0, c1);
+            n0 += __popc(c0);
+            n1 += __popc(c1);
+        }
+        chunk_off[(size_t)c * 64 + lane] = n0;
+        chunk_off[(size_t)c * 64 + 32 + lane] = n1;
+    }
+}
+
+// Index of the set bit of rank `r` (0-based) in x; x has more than r bits.
+__device__ __forceinline__ uint32_t select_bit(uint32_t x, uint32_t r) {
+    uint32_t pos = 0;
+#pragma unroll
+    for (int w = 16; w > 0; w >>= 1) {
+        const uint32_t c = __popc(x & ((1u << w) - 1u));
+        if (r >= c) {
+            r -= c;
+            x >>= w;
+            pos += w;
+        }
+    }
+    return pos;
+}
+
+// Write pass, one warp per chunk.  The chunk's transposed columns, per-group
+// prefix counts and values are kept in shared memory; the lanes then walk
+// the chunk's output in tile-major order, 32 consecutive outputs per step, so
+// each store covers consecutive addresses of a few tile lists (scattered
+// partial-sector stores are what limits the simpler per-tile formulations).
+// Output o belongs to tile k = max{k : soff[k] <= o}; its rank r = o - soff[k]
+// lies in group grp = max{g : pre[g][k] <= r}; the entry is the set bit of
+// rank r - pre[grp][k] in that group's column for k.
+constexpr int kFineGroups = kFineChunk / 32;
+constexpr int kFineWarps = kFineThreads / 32;
+
+struct FineSmem {
+    uint32_t col[kFineGroups][64];
+    uint32_t pre[kFineGroups][64];
+    uint32_t gv[kFineGroups * 32];
+    uint32_t soff[64];
+    uint32_t base[64];
+    uint32_t tile[64];
+};
+
+__global__ void __launch_bounds__(kFineThreads)
+k_fine_write(const uint32_t* __restrict__ cvals, const uint2* __restrict__ cranges,
+             const uint32_t* __restrict__ chunk_first, const uint32_t* __restrict__ chunk_s,
+             const uint32_t* __restrict__ d_n_chunks, const uint4* __restrict__ proj, int64_t n,
+             const ViewInfo* __restrict__ vt, int V, int64_t total_tiles, const uint32_t* __restrict__ chunk_off,
+             const uint2* __restrict__ ranges, int64_t cap, uint32_t* __restrict__ vout,
+             uint32_t* __restrict__ kout) {
+    __shared__ FineSmem sm_all[kFineWarps];
+    const int lane = threadIdx.x & 31;
+    FineSmem& sm = sm_all[threadIdx.x >> 5];
+    const uint32_t nchunks = *d_n_chunks;
+    const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < nchunks; c += nw) {
+        const FineChunk f = fine_chunk(c, cranges, chunk_first, chunk_s, vt, V, total_tiles, lane);
+        sm.base[lane] = f.in0 ? ranges[f.t0].x + chunk_off[(size_t)c * 64 + lane] : 0u;
+        sm.base[lane + 32] = f.in1 ? ranges[f.t1].x + chunk_off[(size_t)c * 64 + 32 + lane] : 0u;
+        sm.tile[lane] = f.t0;
+        sm.tile[lane + 32] = f.t1;
+        uint32_t n0 = 0, n1 = 0;
+        uint32_t grp = 0;
+        for (; f.a + grp * 32u < f.e; ++grp) {
+            uint32_t gval, c0, c1;
+            fine_group(f, grp, cvals, proj, n, lane, gval, c0, c1);
+            sm.col[grp][lane] = c0;
+            sm.col[grp][lane + 32] = c1;
+            sm.pre[grp][lane] = n0;
+            sm.pre[grp][lane + 32] = n1;
+            sm.gv[grp * 32 + lane] = gval;
+            n0 += __popc(c0);
+            n1 += __popc(c1);
+        }
+        for (uint32_t g2 = grp; g2 < (uint32_t)kFineGroups; ++g2) {  // past the last group: never chosen
+            sm.pre[g2][lane] = n0;
+            sm.pre[g2][lane + 32] = n1;
+        }
+        // tile-major output offsets within the chunk
+        uint32_t i0 = n0, i1 = n1;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y0 = __shfl_up_sync(0xFFFFFFFFu, i0, o);
+            const uint32_t y1 = __shfl_up_sync(0xFFFFFFFFu, i1, o);
+            if (lane >= o) { i0 += y0; i1 += y1; }
+        }
+        const uint32_t low = __shfl_sync(0xFFFFFFFFu, i0, 31);
+        const uint32_t P = low + __shfl_sync(0xFFFFFFFFu, i1, 31);
+        sm.soff[lane] = i0 - n0;
+        sm.soff[lane + 32] = low + i1 - n1;
+        __syncwarp();
+        for (uint32_t o = (uint32_t)lane; o < P; o += 32) {
+            int k = 0;  // soff[0] = 0 <= o
+#pragma unroll
+            for (int w = 32; w > 0; w >>= 1)
+                if (k + w <= 63 && sm.soff[k + w] <= o) k += w;
+            const uint32_t r = o - sm.soff[k];
+            int gsel = 0;
+#pragma unroll
+            for (int w = kFineGroups / 2; w > 0; w >>= 1)
+                if (gsel + w < kFineGroups && sm.pre[gsel + w][k] <= r) gsel += w;
+            const uint32_t j = select_bit(sm.col[gsel][k], r - sm.pre[gsel][k]);
+            const uint32_t val = sm.gv[gsel * 32 + j];
+            const uint32_t pos = sm.base[k] + r;
+            if ((int64_t)pos < cap) {
+                vout[pos] = val;
+                if (kout) kout[pos] = sm.tile[k];
+            }
+        }
+        __syncwarp();
+    }
+}
+
+// Per (super-tile, tile): exclusive prefix of the chunk counts in place, and
+// the tile's total.
+__global__ void k_fine_prefix(const uint32_t* __restrict__ chunk_first, const uint32_t* __restrict__ d_n_chunks,
+                              const ViewInfo* __restrict__ vt, int V, int64_t total_tiles,
+                              uint32_t* __restrict__ chunk_off, uint32_t* __restrict__ tile_count) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t ns = vt[V].stile_off < total_tiles ? vt[V].stile_off : total_tiles;
+    if (idx >= ns * 64) return;
+    const int64_t s = idx >> 6;
+    const int k = (int)(idx & 63);
+    const uint32_t nch = *d_n_chunks;
+    const uint32_t c0 = chunk_first[s];
+    const uint32_t c1 = min(chunk_first[s + 1], nch);
+    uint32_t run = 0;
+    for (uint32_t c = c0; c < c1; ++c) {
+        const uint32_t x = chunk_off[(size_t)c * 64 + k];
+        chunk_off[(size_t)c * 64 + k] = run;
+        run += x;
+    }
+    const int v = find_super_view(vt, V, s);
+    const ViewInfo vi = vt[v];
+    const int ls = (int)(s - vi.stile_off);
+    const int x = ((ls % vi.stx) << kSuperShift) + (k & (kSuper - 1));
+    const int y = ((ls / vi.stx) << kSuperShift) + (k >> kSuperShift);
+    const int64_t t = vi.tile_off + (int64_t)y * vi.tx + x;
+    if (x < vi.tx && y < vi.ty && t < total_tiles) tile_count[t] = run;
+}
+
+// Exclusive scan of the tile counts (one block) into the ranges; empty
+// tiles get (0, 0).  Ranges are clamped to the capacity: after an overflow
+// (reported by k_fine_total) compositing reads only stored entries.
+__global__ void __launch_bounds__(1024)
+k_tile_scan(const uint32_t* __restrict__ tile_count, int64_t total_tiles, int64_t cap,
+            uint2* __restrict__ ranges) {
+    __shared__ unsigned long long s_part[1024];
+    const int64_t per = (total_tiles + blockDim.x - 1) / blockDim.x;
+    const int64_t a = (int64_t)threadIdx.x * per;
+    const int64_t e = a + per < total_tiles ? a + per : total_tiles;
+    unsigned long long sum = 0;
+    for (int64_t t = a; t < e; ++t) sum += tile_count[t];
+    s_part[threadIdx.x] = sum;
+    __syncthreads();
+    for (int o = 1; o < (int)blockDim.x; o <<= 1) {
+        const unsigned long long y = threadIdx.x >= (unsigned)o ? s_part[threadIdx.x - o] : 0ULL;
+        __syncthreads();
+        s_part[threadIdx.x] += y;
+        __syncthreads();
+    }
+    unsigned long long run = s_part[threadIdx.x] - sum;
+    for (int64_t t = a; t < e; ++t) {
+        const uint32_t k = tile_count[t];
+        const uint32_t st = (uint32_t)min(run, (unsigned long long)cap);
+        const uint32_t en = (uint32_t)min(run + k, (unsigned long long)cap);
+        ranges[t] = k ? make_uint2(st, en) : make_uint2(0u, 0u);
+        run += k;
     }
 }
 
@@ -515,7 +873,7 @@ void emit_and_sort(const uint64_t* dsorted, int64_t items, int64_t n, const uint
     cudaMemsetAsync(s.emit_lookback, 0, sizeof(unsigned long long) * (size_t)nblk, st);
     k_emit<BITS><<<(unsigned)nblk, kEmitThreads, 0, st>>>(dsorted, items, n, pr, vt, keys_cap, s.tkv[0],
                                                           s.emit_lookback, s.counters + 7, d_num_keys, passes,
-                                                          s.hist, status);
+                                                          s.hist, 0, nullptr, (uint32_t)total_tiles, status);
     if (mark) mark(events, ev, st);
     k_ranges_init<<<sm_count * 2, 256, 0, st>>>(reinterpret_cast<uint2*>(ranges), total_tiles);
     uint64_t* const buf[2] = {s.tkv[0], s.tkv[1]};
@@ -524,15 +882,63 @@ void emit_and_sort(const uint64_t* dsorted, int64_t items, int64_t n, const uint
     k_ranges_fix<<<sm_count * 2, 256, 0, st>>>(reinterpret_cast<uint2*>(ranges), total_tiles);
 }
 
+// Two-level binning: coarse emission and super-tile sort, then the fine
+// expansion into the caller's arrays and ranges.
+template <int BITS, int ITEMS>
+void emit_two_level(const uint64_t* dsorted, int64_t items, int64_t n, const uint4* pr, const ViewInfo* vt, int V,
+                    int64_t keys_cap, const SortScratch& s, uint32_t* sorted_keys,
+                    uint32_t* sorted_vals, uint32_t* ranges, int64_t total_tiles, uint32_t* d_num_keys,
+                    DevStatus* status, int sm_count, cudaStream_t st,
+                    void (*mark)(void* const*, int, cudaStream_t), void* const* events, int ev) {
+    // the host knows the tile count only: super-tiles never outnumber tiles,
+    // so it bounds their count (the kernels read the exact one from vt[V])
+    const int64_t n_super = total_tiles;
+    int bits = 1;
+    while ((1LL << bits) < n_super) ++bits;
+    const int passes = (bits + BITS - 1) / BITS;
+    const int64_t nblk = (items + kEmitBlock - 1) / kEmitBlock;
+    cudaMemsetAsync(s.hist, 0, sizeof(uint32_t) * kMaxPasses * 256, st);
+    cudaMemsetAsync(s.counters, 0, sizeof(uint32_t) * 8, st);
+    cudaMemsetAsync(s.emit_lookback, 0, sizeof(unsigned long long) * (size_t)nblk, st);
+    cudaMemsetAsync(s.d_fine_total, 0, sizeof(unsigned long long), st);
+    k_emit<BITS><<<(unsigned)nblk, kEmitThreads, 0, st>>>(dsorted, items, n, pr, vt, keys_cap, s.tkv[0],
+                                                          s.emit_lookback, s.counters + 7, s.d_count_coarse,
+                                                          passes, s.hist, kSuperShift, s.d_fine_total,
+                                                          (uint32_t)n_super, status);
+    k_fine_total<<<1, 1, 0, st>>>(s.d_fine_total, keys_cap, d_num_keys, status);
+    if (mark) mark(events, ev, st);
+    // stable sort by super-tile; the values land in the ping-pong buffer the
+    // last pass does not read
+    k_ranges_init<<<sm_count, 256, 0, st>>>(s.cranges, n_super);
+    uint64_t* const buf[2] = {s.tkv[0], s.tkv[1]};
+    uint32_t* cvals = reinterpret_cast<uint32_t*>(buf[passes % 2]);
+    onesweep_passes<BITS, ITEMS>(buf, nullptr, nullptr, cvals, s.d_count_coarse, keys_cap, passes, s,
+                                 reinterpret_cast<uint32_t*>(s.cranges), status, sm_count, st);
+    k_ranges_fix<<<sm_count, 256, 0, st>>>(s.cranges, n_super);
+    // fine expansion
+    k_fine_chunks<<<1, 1024, 0, st>>>(s.cranges, vt, V, n_super, s.chunk_first, s.chunk_s, s.d_n_chunks,
+                                      s.max_chunks);
+    const unsigned fgrid = (unsigned)(sm_count * 8);
+    k_fine_count<<<fgrid, kFineThreads, 0, st>>>(cvals, s.cranges, s.chunk_first, s.chunk_s, s.d_n_chunks, pr, n,
+                                                 vt, V, total_tiles, s.chunk_off);
+    k_fine_prefix<<<(unsigned)((n_super * 64 + 255) / 256), 256, 0, st>>>(s.chunk_first, s.d_n_chunks, vt, V,
+                                                                         total_tiles, s.chunk_off, s.tile_count);
+    k_tile_scan<<<1, 1024, 0, st>>>(s.tile_count, total_tiles, keys_cap, reinterpret_cast<uint2*>(ranges));
+    k_fine_write<<<fgrid, kFineThreads, 0, st>>>(cvals, s.cranges, s.chunk_first, s.chunk_s, s.d_n_chunks, pr, n,
+                                                 vt, V, total_tiles, s.chunk_off,
+                                                 reinterpret_cast<const uint2*>(ranges), keys_cap, sorted_vals,
+                                                 sorted_keys);
+}
+
 }  // namespace
 
-size_t sort_scratch_bytes(int V, int64_t n, int64_t keys_cap) {
+size_t sort_scratch_bytes(int V, int64_t n, int64_t keys_cap, int64_t total_tiles) {
     SortScratch s;
-    carve_sort_scratch(nullptr, V, n, keys_cap, &s);
+    carve_sort_scratch(nullptr, V, n, keys_cap, total_tiles, &s);
     return s.bytes;
 }
 
-void carve_sort_scratch(char* base, int V, int64_t n, int64_t keys_cap, SortScratch* s) {
+void carve_sort_scratch(char* base, int V, int64_t n, int64_t keys_cap, int64_t total_tiles, SortScratch* s) {
     Carver c(base);
     const int64_t items = (int64_t)V * n;
     s->dkv[0] = c.take<uint64_t>(items);
@@ -545,11 +951,23 @@ void carve_sort_scratch(char* base, int V, int64_t n, int64_t keys_cap, SortScra
     s->max_sort_tiles = (std::max(items, keys_cap) + kMinTileKeys - 1) / kMinTileKeys + 1;
     s->lookback = c.take<unsigned long long>((size_t)kMaxPasses * s->max_sort_tiles * 256);
     s->d_count_depth = c.take<uint32_t>(1);
+    // super-tiles never outnumber tiles
+    const int64_t ns = total_tiles > 0 ? total_tiles : 1;
+    s->max_chunks = keys_cap / kFineChunk + ns + 1;
+    s->cranges = c.take<uint2>(ns);
+    s->chunk_first = c.take<uint32_t>(ns + 1);
+    s->chunk_s = c.take<uint32_t>(s->max_chunks);
+    s->chunk_off = c.take<uint32_t>((size_t)s->max_chunks * 64);
+    s->tile_count = c.take<uint32_t>(ns);
+    s->d_count_coarse = c.take<uint32_t>(1);
+    s->d_n_chunks = c.take<uint32_t>(1);
+    s->d_fine_total = c.take<unsigned long long>(1);
     s->bytes = c.off;
 }
 
 void launch_bin_sort(const float* proj, const ViewInfo* vt, int V, int64_t n, int64_t keys_cap,
-                     int64_t total_tiles, int sort_bits, int sort_items, const SortScratch& s, bool depth_ready,
+                     int64_t total_tiles, int binning, int sort_bits, int sort_items, const SortScratch& s,
+                     bool depth_ready,
                      uint32_t* sorted_keys, uint32_t* sorted_vals, uint32_t* ranges,
                      uint32_t* d_num_keys, DevStatus* status, int sm_count, cudaStream_t st,
                      void (*mark)(void* const*, int, cudaStream_t), void* const* events, int first_event) {
@@ -574,13 +992,20 @@ void launch_bin_sort(const float* proj, const ViewInfo* vt, int V, int64_t n, in
                                sm_count, st);
     }
     if (mark) mark(events, first_event, st);
-    // 2. emission in depth order with the tile-key histograms, 3. stable sort
-    //    by tile key into the caller's arrays with per-tile ranges
+    // 2. emission in depth order with the key histograms, 3. stable sort by
+    //    tile key (direct) or by super-tile key followed by the expansion
+    //    into tiles (two-level), into the caller's arrays with ranges
     int bits = 1;
     while ((1LL << bits) < total_tiles) ++bits;
-#define GS_EMIT_SORT(B, I) emit_and_sort<B, I>(s.dkv[0], items, n, pr, vt, keys_cap, bits, s, sorted_keys, \
-                                                 sorted_vals, ranges, total_tiles, d_num_keys, status, sm_count, st, \
-                                                 mark, events, first_event + 1)
+#define GS_EMIT_SORT(B, I)                                                                                      \
+    do {                                                                                                        \
+        if (binning == kBinDirect)                                                                              \
+            emit_and_sort<B, I>(s.dkv[0], items, n, pr, vt, keys_cap, bits, s, sorted_keys, sorted_vals, ranges, \
+                                total_tiles, d_num_keys, status, sm_count, st, mark, events, first_event + 1);  \
+        else                                                                                                    \
+            emit_two_level<B, I>(s.dkv[0], items, n, pr, vt, V, keys_cap, s, sorted_keys, sorted_vals, ranges,  \
+                                 total_tiles, d_num_keys, status, sm_count, st, mark, events, first_event + 1); \
+    } while (0)
     const int it = sort_items == 8 ? 8 : (sort_items == 16 ? 16 : 12);
     switch (sort_bits * 100 + it) {
         case 408: GS_EMIT_SORT(4, 8); break;

@@ -162,9 +162,10 @@ class OnlineTrainer:
         self.ctx.raise_status()
 
 
-def estimate_keys(ctx: Context, params, sh_degree: int, cams, slack: float = 1.25) -> int:
-    """Key count of one bin/sort of the current model (through the C ABI),
-    scaled by `slack` to leave room for the model to move."""
+def estimate_keys(ctx: Context, params, sh_degree: int, cams, slack: float = 1.25, dyn=None) -> int:
+    """Key count of one bin/sort of the current model (through the C ABI,
+    with the scene's current object poses when `dyn` is given), scaled by
+    `slack` to leave room for the model to move."""
     import torch
     packed = cams if isinstance(cams, np.ndarray) else pack_cameras(cams)
     V = len(packed)
@@ -174,7 +175,7 @@ def estimate_keys(ctx: Context, params, sh_degree: int, cams, slack: float = 1.2
     cap = 1 << 20
     while True:
         ctx.reserve(ctx.workspace_size(packed, n, cap))
-        proj = gs_project(ctx, params, sh_degree, d_cams, V)
+        proj = gs_project(ctx, params, sh_degree, d_cams, V, dyn=dyn)
         _, vals, ranges, nk = gs_bin_sort(ctx, proj, d_cams, V, n, tt, cap, want_keys=False)
         torch.cuda.synchronize()
         code, detail = ctx.status()

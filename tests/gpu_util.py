@@ -45,6 +45,41 @@ def oracle_grad2d_to_gpu_order(g9: np.ndarray) -> np.ndarray:
     return out
 
 
+# |x - y| below which the sign of the L1 term is not fixed by a float32
+# render: the compositing error of one pixel is ~1e-7..1e-6 (image rel-L2
+# ~6e-7 at these sizes), so 1e-5 leaves a margin of ten.
+L1_TIE_TAU = 1e-5
+
+
+def l1_sign_expected(O, planes, sh, cams, r, target, image_gpu, w_l1=0.8, tau=L1_TIE_TAU, dyn=None):
+    """The oracle's parameter gradient with the L1 sign taken as the float32
+    render takes it, where that choice is one of the correct ones.
+
+    The L1 term's derivative is w_l1 sign(x - y) / M.  Where the FP64 image
+    lies within `tau` of the target (and is not equal to it), a float32
+    render may land on either side of the target or on it, so sign -1, 0 and
+    +1 are all correct results of the method there.  The float32 decision
+    sign(x32 - y32) is exact given the float32 image; it must agree with the
+    oracle's everywhere else (asserted).  The adjoint is linear in dL/dimage
+    for a fixed forward pass, so the oracle's gradient for the float32 signs
+    is its own gradient plus its adjoint of the sign changes at the ties.
+    Returns (expected dparams, number of tie elements whose sign differs)."""
+    img = np.asarray(r["image"], dtype=np.float64).ravel()
+    tgt32 = np.asarray(target, dtype=np.float32).ravel()
+    tgt = tgt32.astype(np.float64)
+    s_o = np.sign(img - tgt)
+    s_g = np.sign(np.asarray(image_gpu, dtype=np.float32).ravel() - tgt32).astype(np.float64)
+    differ = s_o != s_g
+    if not differ.any():
+        return r["dparams"], 0
+    gap = np.abs(img - tgt)[differ]
+    assert np.all(gap <= tau), f"L1 sign differs at |x - y| = {gap.max():.3g}, above the tie band {tau}"
+    c = np.zeros(img.size)
+    c[differ] = (s_g - s_o)[differ] * w_l1 / img.size
+    g2 = O.render_bwd(cams, r["proj"], r["vals"], r["ranges"], c)
+    return r["dparams"] + O.project_bwd(planes, sh, cams, g2, dyn=dyn), int(differ.sum())
+
+
 class GpuRun:
     """One pass of the whole CUDA path on a small case, all intermediates kept."""
 
