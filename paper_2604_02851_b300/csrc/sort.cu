@@ -156,7 +156,7 @@ __global__ void k_hist_scan(uint32_t* hist, int passes) {
 template <int BITS, int ITEMS>
 __global__ void __launch_bounds__(kThreads, 2)
 k_onesweep(const uint64_t* __restrict__ in, uint64_t* __restrict__ out, uint32_t* __restrict__ kout,
-           uint32_t* __restrict__ vout, const uint32_t* d_count, int64_t cap, int shift,
+           uint32_t* __restrict__ vout, const uint32_t* d_count, int64_t cap, int shift, uint32_t kmask,
            const uint32_t* __restrict__ digit_off, unsigned long long* __restrict__ lookback,
            uint32_t* tile_counter, uint32_t* __restrict__ ranges, DevStatus* status) {
     constexpr int R = 1 << BITS;
@@ -173,7 +173,6 @@ k_onesweep(const uint64_t* __restrict__ in, uint64_t* __restrict__ out, uint32_t
     const int64_t n_tiles = (count + TILE - 1) / TILE;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t lt = lanemask_lt();
-    const int kshift = 32 + shift;
 
     for (;;) {
         if (threadIdx.x == 0) { s_tile = atomicAdd(tile_counter, 1u); s_abort = 0; }
@@ -202,7 +201,7 @@ k_onesweep(const uint64_t* __restrict__ in, uint64_t* __restrict__ out, uint32_t
         //      and shares the old value with its group
 #pragma unroll
         for (int j = 0; j < ITEMS; ++j) {
-            const uint32_t d = (uint32_t)(item[j] >> kshift) & MASK;
+            const uint32_t d = (((uint32_t)(item[j] >> 32) & kmask) >> shift) & MASK;
             uint32_t peers = 0xFFFFFFFFu;
 #pragma unroll
             for (int bit = 0; bit < BITS; ++bit) {
@@ -262,7 +261,7 @@ k_onesweep(const uint64_t* __restrict__ in, uint64_t* __restrict__ out, uint32_t
         // ---- stage in shared memory in digit order
 #pragma unroll
         for (int j = 0; j < ITEMS; ++j) {
-            const uint32_t d = (uint32_t)(item[j] >> kshift) & MASK;
+            const uint32_t d = (((uint32_t)(item[j] >> 32) & kmask) >> shift) & MASK;
             s_items[s_local[d] + s_whist[warp][d] + rank[j]] = item[j];
         }
         __syncthreads();
@@ -273,7 +272,7 @@ k_onesweep(const uint64_t* __restrict__ in, uint64_t* __restrict__ out, uint32_t
         if (!s_abort) {
             for (int i = threadIdx.x; i < valid; i += kThreads) {
                 const uint64_t it = s_items[i];
-                const uint32_t k = (uint32_t)(it >> 32);
+                const uint32_t k = (uint32_t)(it >> 32) & kmask;
                 const uint32_t d = (k >> shift) & MASK;
                 const uint32_t pos = s_gbase[d] + (uint32_t)i - s_local[d];
                 if ((int64_t)pos >= count) continue;  // unreachable when the histogram matches the keys
@@ -282,8 +281,9 @@ k_onesweep(const uint64_t* __restrict__ in, uint64_t* __restrict__ out, uint32_t
                 if (kout) kout[pos] = k;
                 if (ranges) {
                     // runs of equal keys are contiguous both here and in the output
-                    if (i == 0 || (uint32_t)(s_items[i - 1] >> 32) != k) atomicMin(&ranges[2 * (size_t)k], pos);
-                    if (i == valid - 1 || (uint32_t)(s_items[i + 1] >> 32) != k)
+                    if (i == 0 || ((uint32_t)(s_items[i - 1] >> 32) & kmask) != k)
+                        atomicMin(&ranges[2 * (size_t)k], pos);
+                    if (i == valid - 1 || ((uint32_t)(s_items[i + 1] >> 32) & kmask) != k)
                         atomicMax(&ranges[2 * (size_t)k + 1], pos + 1);
                 }
             }
@@ -338,6 +338,11 @@ __global__ void k_depth_keys(const uint4* __restrict__ proj, int64_t items, uint
 }
 
 // ------------------------------------------------------------ emission
+// Two-level entries carry their tile rectangle within the super-tile (local
+// x0, x1 - 1, y0, y1 - 1, 3 bits each) in bits 52..63, above keys of up to
+// 20 bits; sorts of such entries mask the key.
+constexpr int kRectShift = 52;
+constexpr int kMaxCoarseKeyBits = kRectShift - 32;
 constexpr int kEmitThreads = 256;
 constexpr int kEmitWarps = kEmitThreads / 32;
 constexpr int kEmitRounds = 4;
@@ -376,13 +381,13 @@ k_emit(const uint64_t* __restrict__ dsorted, int64_t total, int64_t n, const uin
     const int64_t nblk = (total + kEmitBlock - 1) / kEmitBlock;
 
     uint32_t cnt[kEmitRounds], lo[kEmitRounds], hi[kEmitRounds], gi[kEmitRounds], kb[kEmitRounds],
-        tx[kEmitRounds], incl[kEmitRounds], rtot[kEmitRounds];
+        tx[kEmitRounds], incl[kEmitRounds], rtot[kEmitRounds], flo[kEmitRounds], fhi[kEmitRounds];
     uint32_t wtot = 0;
     unsigned long long fine = 0;
 #pragma unroll
     for (int r = 0; r < kEmitRounds; ++r) {
         const int64_t idx = b * kEmitBlock + warp * (32 * kEmitRounds) + r * 32 + lane;
-        cnt[r] = lo[r] = hi[r] = gi[r] = kb[r] = 0;
+        cnt[r] = lo[r] = hi[r] = gi[r] = kb[r] = flo[r] = fhi[r] = 0;
         tx[r] = 1;
         if (idx < total) {
             const uint32_t rr = (uint32_t)dsorted[idx];
@@ -395,6 +400,8 @@ k_emit(const uint64_t* __restrict__ dsorted, int64_t total, int64_t n, const uin
             kb[r] = (uint32_t)vt[v].tile_off;
             tx[r] = (uint32_t)vt[v].tx;
             fine += p3.z;
+            flo[r] = p3.x;
+            fhi[r] = p3.y;
             if (sshift && p3.z) {
                 // super-tile rectangle covering the tile rectangle
                 const uint32_t sx0 = (p3.x & 0xFFFFu) >> sshift, sy0 = (p3.x >> 16) >> sshift;
@@ -466,6 +473,8 @@ k_emit(const uint64_t* __restrict__ dsorted, int64_t total, int64_t n, const uin
             const uint32_t o_kb = __shfl_sync(0xFFFFFFFFu, kb[r], owner);
             const uint32_t o_tx = __shfl_sync(0xFFFFFFFFu, tx[r], owner);
             const uint32_t o_g = __shfl_sync(0xFFFFFFFFu, gi[r], owner);
+            const uint32_t o_flo = __shfl_sync(0xFFFFFFFFu, flo[r], owner);
+            const uint32_t o_fhi = __shfl_sync(0xFFFFFFFFu, fhi[r], owner);
             const uint32_t o = c + lane;
             // only entries that fit the capacity are stored and counted, so the
             // sort's digit offsets always describe exactly the stored prefix
@@ -481,7 +490,19 @@ k_emit(const uint64_t* __restrict__ dsorted, int64_t total, int64_t n, const uin
                 // a view table larger than the caller's tile count (reported
                 // by k_view_table) must not index past the ranges arrays
                 if (key >= key_bound) key = key_bound - 1u;
-                kv[base + o] = ((uint64_t)key << 32) | o_g;
+                uint64_t extra = 0;
+                if (sshift) {
+                    // the tile rectangle clipped to this super-tile, in its
+                    // local tile coordinates, above the key bits
+                    const int ox = (int)(((o_lo & 0xFFFFu) + txx) << sshift);
+                    const int oy = (int)(((o_lo >> 16) + ty) << sshift);
+                    const int S = 1 << sshift;
+                    const int x0 = max((int)(o_flo & 0xFFFFu) - ox, 0), x1 = min((int)(o_fhi & 0xFFFFu) - ox, S);
+                    const int y0 = max((int)(o_flo >> 16) - oy, 0), y1 = min((int)(o_fhi >> 16) - oy, S);
+                    extra = (uint64_t)((uint32_t)x0 | ((uint32_t)(x1 - 1) << 3) | ((uint32_t)y0 << 6) |
+                                       ((uint32_t)(y1 - 1) << 9)) << kRectShift;
+                }
+                kv[base + o] = extra | ((uint64_t)key << 32) | o_g;
             }
             const uint32_t act = __ballot_sync(0xFFFFFFFFu, stored);
             if (stored) {
@@ -572,18 +593,6 @@ k_fine_chunks(const uint2* __restrict__ cranges, const ViewInfo* __restrict__ vt
     }
 }
 
-// Bit k = 8*ky + kx of the result: tile (ox + kx, oy + ky) lies in the tile
-// rectangle packed in (lo, hi).
-__device__ __forceinline__ uint64_t rect_mask(uint32_t lo, uint32_t hi, int ox, int oy) {
-    const int x0 = max((int)(lo & 0xFFFFu) - ox, 0), x1 = min((int)(hi & 0xFFFFu) - ox, kSuper);
-    const int y0 = max((int)(lo >> 16) - oy, 0), y1 = min((int)(hi >> 16) - oy, kSuper);
-    if (x1 <= x0 || y1 <= y0) return 0ULL;
-    const uint64_t row = (uint64_t)(((1u << x1) - 1u) & ~((1u << x0) - 1u)) * 0x0101010101010101ULL;
-    const uint64_t hi_rows = y1 >= kSuper ? ~0ULL : ((1ULL << (8 * y1)) - 1ULL);
-    const uint64_t lo_rows = (1ULL << (8 * y0)) - 1ULL;
-    return row & hi_rows & ~lo_rows;
-}
-
 // 32 x 32 bit-matrix transpose across a warp: on return bit j of lane k's
 // word is bit k of lane j's input word (recursive block swaps, 5 rounds).
 __device__ __forceinline__ uint32_t transpose32(uint32_t x, int lane) {
@@ -632,19 +641,26 @@ __device__ __forceinline__ FineChunk fine_chunk(uint32_t c, const uint2* __restr
     return f;
 }
 
+// Mask of the tiles (bit 8 * y + x) inside a packed local rectangle.
+__device__ __forceinline__ uint64_t rect12_mask(uint32_t r) {
+    const uint32_t x0 = r & 7u, x1 = ((r >> 3) & 7u) + 1u, y0 = (r >> 6) & 7u, y1 = ((r >> 9) & 7u) + 1u;
+    const uint64_t row = (uint64_t)(((1u << x1) - 1u) & ~((1u << x0) - 1u)) * 0x0101010101010101ULL;
+    const uint64_t below = y1 >= 8u ? ~0ULL : ((1ULL << (8u * y1)) - 1ULL);
+    return row & below & ~((1ULL << (8u * y0)) - 1ULL);
+}
+
 // Group `grp` of a chunk: lane's entry value and its super-tile tile mask,
 // transposed so that lane l holds the group's entries covering tile l (c0)
 // and tile l + 32 (c1), bit j = group entry j.
-__device__ __forceinline__ void fine_group(const FineChunk& f, uint32_t grp, const uint32_t* __restrict__ cvals,
-                                           const uint4* __restrict__ proj, int64_t n, int lane, uint32_t& gval,
-                                           uint32_t& c0, uint32_t& c1) {
+__device__ __forceinline__ void fine_group(const FineChunk& f, uint32_t grp, const uint64_t* __restrict__ citems,
+                                           int lane, uint32_t& gval, uint32_t& c0, uint32_t& c1) {
     const uint32_t i = f.a + grp * 32u + (uint32_t)lane;
     uint64_t m = 0;
     gval = 0;
     if (i < f.e) {
-        gval = cvals[i];
-        const uint4 p3 = proj[((size_t)f.v * (size_t)n + gval) * 4 + 3];
-        m = rect_mask(p3.x, p3.y, f.ox, f.oy) & f.valid;
+        const uint64_t it = citems[i];
+        gval = (uint32_t)it;
+        m = rect12_mask((uint32_t)(it >> kRectShift)) & f.valid;
     }
     c0 = transpose32((uint32_t)m, lane);
     c1 = transpose32((uint32_t)(m >> 32), lane);
@@ -653,10 +669,10 @@ __device__ __forceinline__ void fine_group(const FineChunk& f, uint32_t grp, con
 // Count pass, one warp per chunk: chunk_off[c][k] := entries of chunk c in
 // tile k of its super-tile.
 __global__ void __launch_bounds__(kFineThreads)
-k_fine_count(const uint32_t* __restrict__ cvals, const uint2* __restrict__ cranges,
+k_fine_count(const uint64_t* __restrict__ citems, const uint2* __restrict__ cranges,
              const uint32_t* __restrict__ chunk_first, const uint32_t* __restrict__ chunk_s,
-             const uint32_t* __restrict__ d_n_chunks, const uint4* __restrict__ proj, int64_t n,
-             const ViewInfo* __restrict__ vt, int V, int64_t total_tiles, uint32_t* __restrict__ chunk_off) {
+             const uint32_t* __restrict__ d_n_chunks, const ViewInfo* __restrict__ vt, int V,
+             int64_t total_tiles, uint32_t* __restrict__ chunk_off) {
     const int lane = threadIdx.x & 31;
     const uint32_t nchunks = *d_n_chunks;
     const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
@@ -665,7 +681,7 @@ k_fine_count(const uint32_t* __restrict__ cvals, const uint2* __restrict__ crang
         uint32_t n0 = 0, n1 = 0;
         for (uint32_t grp = 0; f.a + grp * 32u < f.e; ++grp) {
             uint32_t gval, c0, c1;
-            fine_group(f, grp, cvals, proj, n, lane, gval, c0, c1);
+            fine_group(f, grp, citems, lane, gval, c0, c1);
             n0 += __popc(c0);
             n1 += __popc(c1);
         }
@@ -674,108 +690,70 @@ k_fine_count(const uint32_t* __restrict__ cvals, const uint2* __restrict__ crang
     }
 }
 
-// Index of the set bit of rank `r` (0-based) in x; x has more than r bits.
-__device__ __forceinline__ uint32_t select_bit(uint32_t x, uint32_t r) {
-    uint32_t pos = 0;
-#pragma unroll
-    for (int w = 16; w > 0; w >>= 1) {
-        const uint32_t c = __popc(x & ((1u << w) - 1u));
-        if (r >= c) {
-            r -= c;
-            x >>= w;
-            pos += w;
-        }
-    }
-    return pos;
-}
-
-// Write pass, one warp per chunk.  The chunk's transposed columns, per-group
-// prefix counts and values are kept in shared memory; the lanes then walk
-// the chunk's output in tile-major order, 32 consecutive outputs per step, so
-// each store covers consecutive addresses of a few tile lists (scattered
-// partial-sector stores are what limits the simpler per-tile formulations).
-// Output o belongs to tile k = max{k : soff[k] <= o}; its rank r = o - soff[k]
-// lies in group grp = max{g : pre[g][k] <= r}; the entry is the set bit of
-// rank r - pre[grp][k] in that group's column for k.
+// Write pass, one block per chunk.  Warp w transposes group w (entries
+// 32w .. 32w + 31 of the chunk) into shared memory: col[w][k] holds, bit j,
+// whether entry 32w + j covers tile k.  Warp w then builds the runs of tiles
+// k = w, w + 8, ..., w + 56: per tile, group by group, each lane whose entry
+// is in the column writes it at run position + (set bits below it) into the
+// warp's staging area, and the finished run (at most kFineChunk entries) is
+// copied to the output with consecutive stores.
 constexpr int kFineGroups = kFineChunk / 32;
 constexpr int kFineWarps = kFineThreads / 32;
-
-struct FineSmem {
-    uint32_t col[kFineGroups][64];
-    uint32_t pre[kFineGroups][64];
-    uint32_t gv[kFineGroups * 32];
-    uint32_t soff[64];
-    uint32_t base[64];
-    uint32_t tile[64];
-};
+constexpr int kFineStage = kFineChunk;
+static_assert(kFineWarps == kFineGroups, "one warp per group of the chunk");
 
 __global__ void __launch_bounds__(kFineThreads)
-k_fine_write(const uint32_t* __restrict__ cvals, const uint2* __restrict__ cranges,
+k_fine_write(const uint64_t* __restrict__ citems, const uint2* __restrict__ cranges,
              const uint32_t* __restrict__ chunk_first, const uint32_t* __restrict__ chunk_s,
-             const uint32_t* __restrict__ d_n_chunks, const uint4* __restrict__ proj, int64_t n,
-             const ViewInfo* __restrict__ vt, int V, int64_t total_tiles, const uint32_t* __restrict__ chunk_off,
+             const uint32_t* __restrict__ d_n_chunks, const ViewInfo* __restrict__ vt, int V,
+             int64_t total_tiles, const uint32_t* __restrict__ chunk_off,
              const uint2* __restrict__ ranges, int64_t cap, uint32_t* __restrict__ vout,
              uint32_t* __restrict__ kout) {
-    __shared__ FineSmem sm_all[kFineWarps];
-    const int lane = threadIdx.x & 31;
-    FineSmem& sm = sm_all[threadIdx.x >> 5];
+    __shared__ uint32_t s_col[kFineGroups][64];
+    __shared__ uint32_t s_gv[kFineGroups][32];
+    __shared__ uint32_t s_base[64], s_tile[64];
+    __shared__ uint32_t s_stage[kFineWarps][kFineStage];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t lt = lanemask_lt();
+    uint32_t* stage = s_stage[warp];
     const uint32_t nchunks = *d_n_chunks;
-    const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
-    for (uint32_t c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < nchunks; c += nw) {
+    for (uint32_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
         const FineChunk f = fine_chunk(c, cranges, chunk_first, chunk_s, vt, V, total_tiles, lane);
-        sm.base[lane] = f.in0 ? ranges[f.t0].x + chunk_off[(size_t)c * 64 + lane] : 0u;
-        sm.base[lane + 32] = f.in1 ? ranges[f.t1].x + chunk_off[(size_t)c * 64 + 32 + lane] : 0u;
-        sm.tile[lane] = f.t0;
-        sm.tile[lane + 32] = f.t1;
-        uint32_t n0 = 0, n1 = 0;
-        uint32_t grp = 0;
-        for (; f.a + grp * 32u < f.e; ++grp) {
-            uint32_t gval, c0, c1;
-            fine_group(f, grp, cvals, proj, n, lane, gval, c0, c1);
-            sm.col[grp][lane] = c0;
-            sm.col[grp][lane + 32] = c1;
-            sm.pre[grp][lane] = n0;
-            sm.pre[grp][lane + 32] = n1;
-            sm.gv[grp * 32 + lane] = gval;
-            n0 += __popc(c0);
-            n1 += __popc(c1);
+        if (warp == 0) {
+            s_base[lane] = f.in0 ? ranges[f.t0].x + chunk_off[(size_t)c * 64 + lane] : 0u;
+            s_base[lane + 32] = f.in1 ? ranges[f.t1].x + chunk_off[(size_t)c * 64 + 32 + lane] : 0u;
+            s_tile[lane] = f.t0;
+            s_tile[lane + 32] = f.t1;
         }
-        for (uint32_t g2 = grp; g2 < (uint32_t)kFineGroups; ++g2) {  // past the last group: never chosen
-            sm.pre[g2][lane] = n0;
-            sm.pre[g2][lane + 32] = n1;
-        }
-        // tile-major output offsets within the chunk
-        uint32_t i0 = n0, i1 = n1;
+        uint32_t gval = 0, c0 = 0, c1 = 0;
+        if (f.a + (uint32_t)warp * 32u < f.e) fine_group(f, (uint32_t)warp, citems, lane, gval, c0, c1);
+        s_col[warp][lane] = c0;
+        s_col[warp][lane + 32] = c1;
+        s_gv[warp][lane] = gval;
+        __syncthreads();
+        uint32_t gv[kFineGroups];  // this lane's entry of every group
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y0 = __shfl_up_sync(0xFFFFFFFFu, i0, o);
-            const uint32_t y1 = __shfl_up_sync(0xFFFFFFFFu, i1, o);
-            if (lane >= o) { i0 += y0; i1 += y1; }
-        }
-        const uint32_t low = __shfl_sync(0xFFFFFFFFu, i0, 31);
-        const uint32_t P = low + __shfl_sync(0xFFFFFFFFu, i1, 31);
-        sm.soff[lane] = i0 - n0;
-        sm.soff[lane + 32] = low + i1 - n1;
-        __syncwarp();
-        for (uint32_t o = (uint32_t)lane; o < P; o += 32) {
-            int k = 0;  // soff[0] = 0 <= o
+        for (int g = 0; g < kFineGroups; ++g) gv[g] = s_gv[g][lane];
+        for (int k = warp; k < 64; k += kFineWarps) {
+            uint32_t cnt = 0;
 #pragma unroll
-            for (int w = 32; w > 0; w >>= 1)
-                if (k + w <= 63 && sm.soff[k + w] <= o) k += w;
-            const uint32_t r = o - sm.soff[k];
-            int gsel = 0;
-#pragma unroll
-            for (int w = kFineGroups / 2; w > 0; w >>= 1)
-                if (gsel + w < kFineGroups && sm.pre[gsel + w][k] <= r) gsel += w;
-            const uint32_t j = select_bit(sm.col[gsel][k], r - sm.pre[gsel][k]);
-            const uint32_t val = sm.gv[gsel * 32 + j];
-            const uint32_t pos = sm.base[k] + r;
-            if ((int64_t)pos < cap) {
-                vout[pos] = val;
-                if (kout) kout[pos] = sm.tile[k];
+            for (int g = 0; g < kFineGroups; ++g) {
+                const uint32_t word = s_col[g][k];
+                if ((word >> lane) & 1u) stage[cnt + __popc(word & lt)] = gv[g];
+                cnt += __popc(word);
             }
+            __syncwarp();
+            const uint32_t base = s_base[k], t = s_tile[k];
+            for (uint32_t i = (uint32_t)lane; i < cnt; i += 32) {
+                const uint32_t o = base + i;
+                if ((int64_t)o < cap) {
+                    vout[o] = stage[i];
+                    if (kout) kout[o] = t;
+                }
+            }
+            __syncwarp();
         }
-        __syncwarp();
+        __syncthreads();
     }
 }
 
@@ -793,7 +771,18 @@ __global__ void k_fine_prefix(const uint32_t* __restrict__ chunk_first, const ui
     const uint32_t c0 = chunk_first[s];
     const uint32_t c1 = min(chunk_first[s + 1], nch);
     uint32_t run = 0;
-    for (uint32_t c = c0; c < c1; ++c) {
+    uint32_t c = c0;
+    for (; c + 8 <= c1; c += 8) {  // eight loads in flight
+        uint32_t x[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) x[q] = chunk_off[(size_t)(c + q) * 64 + k];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            chunk_off[(size_t)(c + q) * 64 + k] = run;
+            run += x[q];
+        }
+    }
+    for (; c < c1; ++c) {
         const uint32_t x = chunk_off[(size_t)c * 64 + k];
         chunk_off[(size_t)c * 64 + k] = run;
         run += x;
@@ -844,7 +833,7 @@ k_tile_scan(const uint32_t* __restrict__ tile_count, int64_t total_tiles, int64_
 template <int BITS, int ITEMS>
 void onesweep_passes(uint64_t* const buf[2], uint64_t* last_out, uint32_t* kout, uint32_t* vout,
                      const uint32_t* d_count, int64_t cap, int passes, const SortScratch& s, uint32_t* ranges,
-                     DevStatus* status, int sm_count, cudaStream_t st) {
+                     DevStatus* status, int sm_count, cudaStream_t st, uint32_t kmask = 0xFFFFFFFFu) {
     constexpr int R = 1 << BITS;
     k_clear_lookback<<<sm_count * 4, 256, 0, st>>>(s.lookback, d_count, cap, R, passes, s.max_sort_tiles,
                                                    kThreads * ITEMS);
@@ -854,7 +843,7 @@ void onesweep_passes(uint64_t* const buf[2], uint64_t* last_out, uint32_t* kout,
         const uint64_t* src = buf[p % 2];
         uint64_t* dst = last ? last_out : buf[(p + 1) % 2];
         k_onesweep<BITS, ITEMS><<<sm_count * 2, kThreads, 0, st>>>(
-            src, dst, last ? kout : nullptr, last ? vout : nullptr, d_count, cap, p * BITS, s.hist + p * 256,
+            src, dst, last ? kout : nullptr, last ? vout : nullptr, d_count, cap, p * BITS, kmask, s.hist + p * 256,
             s.lookback + (int64_t)p * s.max_sort_tiles * R, s.counters + p, last ? ranges : nullptr, status);
     }
 }
@@ -911,21 +900,22 @@ void emit_two_level(const uint64_t* dsorted, int64_t items, int64_t n, const uin
     // last pass does not read
     k_ranges_init<<<sm_count, 256, 0, st>>>(s.cranges, n_super);
     uint64_t* const buf[2] = {s.tkv[0], s.tkv[1]};
-    uint32_t* cvals = reinterpret_cast<uint32_t*>(buf[passes % 2]);
-    onesweep_passes<BITS, ITEMS>(buf, nullptr, nullptr, cvals, s.d_count_coarse, keys_cap, passes, s,
-                                 reinterpret_cast<uint32_t*>(s.cranges), status, sm_count, st);
+    const uint64_t* citems = buf[passes % 2];
+    onesweep_passes<BITS, ITEMS>(buf, buf[passes % 2], nullptr, nullptr, s.d_count_coarse, keys_cap, passes, s,
+                                 reinterpret_cast<uint32_t*>(s.cranges), status, sm_count, st,
+                                 (uint32_t)((1ull << bits) - 1ull));
     k_ranges_fix<<<sm_count, 256, 0, st>>>(s.cranges, n_super);
     // fine expansion
     k_fine_chunks<<<1, 1024, 0, st>>>(s.cranges, vt, V, n_super, s.chunk_first, s.chunk_s, s.d_n_chunks,
                                       s.max_chunks);
     const unsigned fgrid = (unsigned)(sm_count * 8);
-    k_fine_count<<<fgrid, kFineThreads, 0, st>>>(cvals, s.cranges, s.chunk_first, s.chunk_s, s.d_n_chunks, pr, n,
-                                                 vt, V, total_tiles, s.chunk_off);
+    k_fine_count<<<fgrid, kFineThreads, 0, st>>>(citems, s.cranges, s.chunk_first, s.chunk_s, s.d_n_chunks, vt, V,
+                                                 total_tiles, s.chunk_off);
     k_fine_prefix<<<(unsigned)((n_super * 64 + 255) / 256), 256, 0, st>>>(s.chunk_first, s.d_n_chunks, vt, V,
                                                                          total_tiles, s.chunk_off, s.tile_count);
     k_tile_scan<<<1, 1024, 0, st>>>(s.tile_count, total_tiles, keys_cap, reinterpret_cast<uint2*>(ranges));
-    k_fine_write<<<fgrid, kFineThreads, 0, st>>>(cvals, s.cranges, s.chunk_first, s.chunk_s, s.d_n_chunks, pr, n,
-                                                 vt, V, total_tiles, s.chunk_off,
+    k_fine_write<<<(unsigned)(sm_count * 8), kFineThreads, 0, st>>>(citems, s.cranges, s.chunk_first, s.chunk_s, s.d_n_chunks, vt, V,
+                                                 total_tiles, s.chunk_off,
                                                  reinterpret_cast<const uint2*>(ranges), keys_cap, sorted_vals,
                                                  sorted_keys);
 }
@@ -999,7 +989,7 @@ void launch_bin_sort(const float* proj, const ViewInfo* vt, int V, int64_t n, in
     while ((1LL << bits) < total_tiles) ++bits;
 #define GS_EMIT_SORT(B, I)                                                                                      \
     do {                                                                                                        \
-        if (binning == kBinDirect)                                                                              \
+        if (binning == kBinDirect || bits > kMaxCoarseKeyBits)                                                  \
             emit_and_sort<B, I>(s.dkv[0], items, n, pr, vt, keys_cap, bits, s, sorted_keys, sorted_vals, ranges, \
                                 total_tiles, d_num_keys, status, sm_count, st, mark, events, first_event + 1);  \
         else                                                                                                    \
