@@ -283,12 +283,12 @@ def run_ours(args, rank, world, local_rank):
         frame = [0]
 
     ctx = gs.Context(local_rank, 0, tile=args.tile, sort_bits=args.sort_bits, sort_items=args.sort_items,
-                     binning=args.binning)
+                     binning=args.binning, raster_threads=args.raster_threads)
     keys_cap = estimate_keys(ctx, params, sh, cams, slack=1.3, dyn=dyn)
     tr = OnlineTrainer(params, sh, cams, keys_cap, ctx=ctx, dyn=dyn)
     packed = tr.packed
     tctx = gs.Context(local_rank, 0, tile=args.tile, sort_bits=args.sort_bits, sort_items=args.sort_items,
-                     binning=args.binning)
+                     binning=args.binning, raster_threads=args.raster_threads)
     tkeys = estimate_keys(tctx, tparams, sh, cams, slack=1.3, dyn=dyn)
     tctx.reserve(tctx.workspace_size(packed, n, tkeys))
 
@@ -428,6 +428,7 @@ def run_ours(args, rank, world, local_rank):
                                       "Lambertian relight of the DC term (ambient 0.3, diffuse 0.7)"
                           if dynamic else None,
                           "sort_digit_bits": args.sort_bits, "sort_items": args.sort_items, "binning": args.binning,
+                          "raster_threads_per_row": args.raster_threads,
                           "graph": True,
                           "l2": "inputs larger than L2 (params 240 MB, keys > 1 GB per step)",
                           "targets": "re-rendered each step by gs_render_batch outside the step's events",
@@ -537,6 +538,7 @@ def main():
     ap.add_argument("--sort-bits", type=int, default=8)
     ap.add_argument("--sort-items", type=int, default=16)
     ap.add_argument("--binning", choices=("two_level", "direct"), default="two_level")
+    ap.add_argument("--raster-threads", type=int, choices=(2, 4), default=4)
     ap.add_argument("--e2e-steps", type=int, default=30)
     ap.add_argument("--cpu-samples", type=int, default=12)
     ap.add_argument("--plain-steps", type=int, default=10)

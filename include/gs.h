@@ -133,6 +133,12 @@ gs_status_t gs_ctx_set_sort_items(gs_ctx* ctx, int32_t items);
 #define GS_BINNING_TWO_LEVEL 0
 #define GS_BINNING_DIRECT 1
 gs_status_t gs_ctx_set_binning(gs_ctx* ctx, int32_t mode);
+/* Threads per pixel row of a 16 x 16 tile in compositing and its adjoint (2
+ * or 4; default 4): each thread owns 16 / threads_per_row adjacent pixels.
+ * Fewer threads per row share each fragment's loads and gradient reduction
+ * among more pixels.  8 x 8 tiles always use 4.  Results are identical up to
+ * the order of floating-point gradient sums. */
+gs_status_t gs_ctx_set_raster_threads(gs_ctx* ctx, int32_t threads_per_row);
 /* Reads and clears the device status word (synchronises `stream`).
  * *status receives the first error a kernel recorded since the last read
  * (GS_OK if none); *detail receives the required size for GS_ERR_CAPACITY. */

@@ -85,7 +85,7 @@ class Context:
     """Owns a gs_ctx (device workspace, status word, graph)."""
 
     def __init__(self, device: int = 0, workspace_bytes: int = 0, tile: int = 16, sort_bits: int = 8,
-                 sort_items: int = 16, binning: str = "two_level"):
+                 sort_items: int = 16, binning: str = "two_level", raster_threads: int = 4):
         L = _lib.lib()
         p = C.c_void_p()
         check("gs_ctx_create", L.gs_ctx_create(C.byref(p), device, workspace_bytes))
@@ -99,6 +99,8 @@ class Context:
             raise ValueError(f"binning must be one of {sorted(BINNING)}")
         self.binning = binning
         check("gs_ctx_set_binning", L.gs_ctx_set_binning(p, BINNING[binning]))
+        self.raster_threads = raster_threads
+        check("gs_ctx_set_raster_threads", L.gs_ctx_set_raster_threads(p, raster_threads))
 
     def reserve(self, nbytes: int) -> None:
         check("gs_ctx_reserve", _lib.lib().gs_ctx_reserve(self.ptr, int(nbytes)))

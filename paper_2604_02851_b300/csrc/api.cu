@@ -181,6 +181,12 @@ gs_status_t gs_ctx_set_binning(gs_ctx* ctx, int32_t mode) {
     return GS_OK;
 }
 
+gs_status_t gs_ctx_set_raster_threads(gs_ctx* ctx, int32_t threads_per_row) {
+    if (!ctx || (threads_per_row != 2 && threads_per_row != 4)) return GS_ERR_ARG;
+    ctx->raster_tpr = threads_per_row;
+    return GS_OK;
+}
+
 gs_status_t gs_get_status(gs_ctx* ctx, void* stream, int32_t* status, int64_t* detail) {
     if (!ctx || !status) return GS_ERR_ARG;
     DeviceGuard g(ctx->device);
@@ -258,7 +264,7 @@ gs_status_t gs_render_fwd(gs_ctx* ctx, const float* proj, const gs_camera* d_cam
     DeviceGuard g(ctx->device);
     const float3 b = bg ? make_float3(bg[0], bg[1], bg[2]) : make_float3(0.f, 0.f, 0.f);
     launch_view_table(d_cams, n_views, ctx->tile, vt, total_tiles, ctx->d_status, S(stream));
-    launch_render_fwd(proj, vt, n_views, n, ctx->tile, sorted_vals, ranges, b, image, T_final, n_contrib,
+    launch_render_fwd(proj, vt, n_views, n, ctx->tile, ctx->raster_tpr, sorted_vals, ranges, b, image, T_final, n_contrib,
                       total_tiles, S(stream));
     return launch_check();
 }
@@ -288,7 +294,7 @@ gs_status_t gs_raster_bwd(gs_ctx* ctx, const float* proj, const gs_camera* d_cam
     DeviceGuard g(ctx->device);
     const float3 b = bg ? make_float3(bg[0], bg[1], bg[2]) : make_float3(0.f, 0.f, 0.f);
     launch_view_table(d_cams, n_views, ctx->tile, vt, total_tiles, ctx->d_status, S(stream));
-    launch_raster_bwd(proj, vt, n_views, n, ctx->tile, sorted_vals, ranges, b, T_final, n_contrib, dimage,
+    launch_raster_bwd(proj, vt, n_views, n, ctx->tile, ctx->raster_tpr, sorted_vals, ranges, b, T_final, n_contrib, dimage,
                       grad2d, total_tiles, S(stream));
     return launch_check();
 }
@@ -361,7 +367,7 @@ gs_status_t gs_render_batch(gs_ctx* ctx, const gs_scene* scene, const gs_camera*
                    s.dkv[0], st);
     launch_bin_sort(p.proj, p.vt, n_requests, scene->n, keys_cap, total_tiles, ctx->binning, ctx->sort_bits, ctx->sort_items, s, true, nullptr,
                     p.vals, p.ranges, p.n_keys, ctx->d_status, ctx->sm_count, st);
-    launch_render_fwd(p.proj, p.vt, n_requests, scene->n, ctx->tile, p.vals, p.ranges, b, image, nullptr,
+    launch_render_fwd(p.proj, p.vt, n_requests, scene->n, ctx->tile, ctx->raster_tpr, p.vals, p.ranges, b, image, nullptr,
                       nullptr, total_tiles, st);
     return launch_check();
 }
@@ -412,12 +418,12 @@ gs_status_t gs_train_step_events(gs_ctx* ctx, const gs_camera* d_cams, const gs_
     launch_bin_sort(p.proj, p.vt, V, n, cfg->keys_cap, tt, ctx->binning, ctx->sort_bits, ctx->sort_items, s, true, nullptr,
                     p.vals, p.ranges, p.n_keys, ctx->d_status, ctx->sm_count, st, ev ? mark : nullptr, ev, 2);
     mark(ev, 4, st);
-    launch_render_fwd(p.proj, p.vt, V, n, B, p.vals, p.ranges, b, io->image, p.T_final, p.n_contrib, tt, st);
+    launch_render_fwd(p.proj, p.vt, V, n, B, ctx->raster_tpr, p.vals, p.ranges, b, io->image, p.T_final, p.n_contrib, tt, st);
     mark(ev, 5, st);
     launch_loss(io->image, io->targets, V, cfg->height, cfg->width, cfg->w_l1, cfg->w_ssim, io->d_loss, p.dimage,
                 p.loss, st);
     mark(ev, 6, st);
-    launch_raster_bwd(p.proj, p.vt, V, n, B, p.vals, p.ranges, b, p.T_final, p.n_contrib, p.dimage, p.grad2d, tt,
+    launch_raster_bwd(p.proj, p.vt, V, n, B, ctx->raster_tpr, p.vals, p.ranges, b, p.T_final, p.n_contrib, p.dimage, p.grad2d, tt,
                       st);
     mark(ev, 7, st);
     launch_project_bwd(io->params, n, cfg->sh_degree, dyn, d_cams, V, p.proj, p.grad2d, io->grads, 0, st);

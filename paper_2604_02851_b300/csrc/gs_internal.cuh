@@ -128,12 +128,13 @@ void launch_bin_sort(const float* proj, const ViewInfo* vt, int V, int64_t n, in
                      void (*mark)(void* const*, int, cudaStream_t) = nullptr, void* const* events = nullptr,
                      int first_event = 0);
 
-void launch_render_fwd(const float* proj, const ViewInfo* vt, int V, int64_t n, int tile,
+// tpr: threads per pixel row of a 16 x 16 tile (2 or 4); 8 x 8 tiles use 4.
+void launch_render_fwd(const float* proj, const ViewInfo* vt, int V, int64_t n, int tile, int tpr,
                        const uint32_t* vals, const uint32_t* ranges, float3 bg, float* image,
                        float* T_final, uint32_t* n_contrib, int64_t total_tiles,
                        cudaStream_t st);
 
-void launch_raster_bwd(const float* proj, const ViewInfo* vt, int V, int64_t n, int tile,
+void launch_raster_bwd(const float* proj, const ViewInfo* vt, int V, int64_t n, int tile, int tpr,
                        const uint32_t* vals, const uint32_t* ranges, float3 bg,
                        const float* T_final, const uint32_t* n_contrib, const float* dimage,
                        float* grad2d, int64_t total_tiles, cudaStream_t st);
@@ -179,6 +180,7 @@ struct gs_ctx {
     int sort_bits = 8;
     int sort_items = 16;
     int binning = gs::kBinTwoLevel;
+    int raster_tpr = 4;
     void* ws = nullptr;
     size_t ws_bytes = 0;
     gs::DevStatus* d_status = nullptr;

@@ -34,11 +34,10 @@ __device__ __forceinline__ int find_view(const ViewInfo* __restrict__ vt, int V,
     return lo;
 }
 
-// Thread layout: a B x B tile is covered by B rows of kTPR threads; each
-// thread owns a strip of PX = B / kTPR adjacent pixels of one row, so the
+// Thread layout: a B x B tile is covered by B rows of TPR threads; each
+// thread owns a strip of PX = B / TPR adjacent pixels of one row, so the
 // shared-memory reads of a fragment and the warp reductions of its gradient
-// are shared by PX pixels.
-constexpr int kTPR = 4;
+// are shared by PX pixels.  B * TPR is a multiple of 32 (whole warps).
 constexpr float kLog2e = 1.4426950408889634f;
 
 // The exponent is evaluated in base 2: with q = -log2(e)/2 (A, 2B, C), the
@@ -54,13 +53,14 @@ __device__ __forceinline__ float4 log2_conic(float4 co) {
 }
 __device__ __forceinline__ float cutoff_log2(float o) { return -__log2f(255.f * o); }
 
-template <int B>
-__global__ void __launch_bounds__(B * kTPR)
+template <int B, int TPR>
+__global__ void __launch_bounds__(B * TPR)
 k_render_fwd(const float4* __restrict__ proj, const ViewInfo* __restrict__ vt, int V, int64_t n,
              const uint32_t* __restrict__ vals, const uint2* __restrict__ ranges, float3 bg,
              float* __restrict__ image, float* __restrict__ T_final, uint32_t* __restrict__ n_contrib) {
-    constexpr int NT = B * kTPR;       // threads per block
-    constexpr int PX = B / kTPR;       // pixels per thread
+    constexpr int NT = B * TPR;        // threads per block
+    constexpr int PX = B / TPR;        // pixels per thread
+    static_assert(NT % 32 == 0, "whole warps");
     constexpr int BATCH = 2 * NT;      // fragments staged per round
     __shared__ float4 s_a[BATCH];      // u, v, opacity, log2 cut-off
     __shared__ float4 s_q[BATCH];      // base-2 conic coefficients
@@ -70,8 +70,8 @@ k_render_fwd(const float4* __restrict__ proj, const ViewInfo* __restrict__ vt, i
     const int v = find_view(vt, V, gt);
     const ViewInfo vi = vt[v];
     const int lt = (int)(gt - vi.tile_off);
-    const int row = (int)threadIdx.x / kTPR;
-    const int px0 = (lt % vi.tx) * B + ((int)threadIdx.x % kTPR) * PX;
+    const int row = (int)threadIdx.x / TPR;
+    const int px0 = (lt % vi.tx) * B + ((int)threadIdx.x % TPR) * PX;
     const int py = (lt / vi.tx) * B + row;
     const float fy = (float)py + 0.5f;
     const float fx0 = (float)px0 + 0.5f;
@@ -147,6 +147,40 @@ __device__ __forceinline__ float warp_sum(float x) {
     return x;
 }
 
+// Warp sums of 8 values at once (reduce-scatter): at the exchanges over lane
+// bits 4, 3 and 2 a lane keeps half of its partial vector and receives the
+// partner's sums of that half; two full exchanges over bits 1 and 0 finish.
+// On return every lane l holds the warp sum of value l >> 2.  14 shuffles
+// instead of 40.
+__device__ __forceinline__ float warp_sum8(const float (&v)[8], int lane) {
+    float a[4], b[2];
+    const bool u4 = lane & 16, u3 = lane & 8, u2 = lane & 4;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float send = u4 ? v[i] : v[i + 4];
+        const float keep = u4 ? v[i + 4] : v[i];
+        a[i] = keep + __shfl_xor_sync(0xFFFFFFFFu, send, 16);
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const float send = u3 ? a[i] : a[i + 2];
+        const float keep = u3 ? a[i + 2] : a[i];
+        b[i] = keep + __shfl_xor_sync(0xFFFFFFFFu, send, 8);
+    }
+    const float send = u2 ? b[0] : b[1];
+    float c = (u2 ? b[1] : b[0]) + __shfl_xor_sync(0xFFFFFFFFu, send, 4);
+    c += __shfl_xor_sync(0xFFFFFFFFu, c, 2);
+    c += __shfl_xor_sync(0xFFFFFFFFu, c, 1);
+    return c;
+}
+
+// Approximate reciprocal (relative error below 2^-22).
+__device__ __forceinline__ float rcp_approx(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 // Geometry gradients from five sums over a fragment's pixels:
 //   S1 = sum dP dx, S2 = sum dP dy, S3 = sum dP dx^2, S4 = sum dP dx dy,
 //   S5 = sum dP dy^2  (dP = dL/dP, dx = u - px, dy = v - py), so that
@@ -154,14 +188,15 @@ __device__ __forceinline__ float warp_sum(float x) {
 //   dL/dA = -S3 / 2, dL/dB = -S4, dL/dC = -S5 / 2.
 // A thread's pixels share one row (one dy): it keeps sum dP, sum dP dx and
 // sum dP dx^2 per pixel and forms S2, S4, S5 with its dy once per fragment.
-template <int B>
-__global__ void __launch_bounds__(B * kTPR)
+template <int B, int TPR>
+__global__ void __launch_bounds__(B * TPR)
 k_raster_bwd(const float4* __restrict__ proj, const ViewInfo* __restrict__ vt, int V, int64_t n,
              const uint32_t* __restrict__ vals, const uint2* __restrict__ ranges, float3 bg,
              const float* __restrict__ T_final, const uint32_t* __restrict__ n_contrib,
              const float* __restrict__ dimage, float* __restrict__ grad2d) {
-    constexpr int NT = B * kTPR;
-    constexpr int PX = B / kTPR;
+    constexpr int NT = B * TPR;
+    constexpr int PX = B / TPR;
+    static_assert(NT % 32 == 0, "whole warps");
     constexpr int BATCH = NT;
     __shared__ float4 s_a[BATCH];   // u, v, opacity, log2 cut-off
     __shared__ float4 s_q[BATCH];   // base-2 conic coefficients
@@ -175,8 +210,8 @@ k_raster_bwd(const float4* __restrict__ proj, const ViewInfo* __restrict__ vt, i
     const int v = find_view(vt, V, gt);
     const ViewInfo vi = vt[v];
     const int lt = (int)(gt - vi.tile_off);
-    const int row = (int)threadIdx.x / kTPR;
-    const int px0 = (lt % vi.tx) * B + ((int)threadIdx.x % kTPR) * PX;
+    const int row = (int)threadIdx.x / TPR;
+    const int px0 = (lt % vi.tx) * B + ((int)threadIdx.x % TPR) * PX;
     const int py = (lt / vi.tx) * B + row;
     const float fy = (float)py + 0.5f;
     const float fx0 = (float)px0 + 0.5f;
@@ -247,7 +282,7 @@ k_raster_bwd(const float4* __restrict__ proj, const ViewInfo* __restrict__ vt, i
                 const float G = ex2(P2);
                 const float raw = a.z * G;
                 const float al = fminf(kAlphaMax, raw);
-                const float Tj = T[k] * __frcp_rn(1.f - al);
+                const float Tj = T[k] * rcp_approx(1.f - al);
                 T[k] = Tj;
                 const float w = al * Tj;
                 g6 += w * dCr[k]; g7 += w * dCg[k]; g8 += w * dCb[k];
@@ -265,22 +300,30 @@ k_raster_bwd(const float4* __restrict__ proj, const ViewInfo* __restrict__ vt, i
                 s2 += t * dx;
             }
             if (__any_sync(0xFFFFFFFFu, contrib)) {
-                float S1 = warp_sum(s1), S2 = warp_sum(s0 * dy), S3 = warp_sum(s2);
-                float S4 = warp_sum(s1 * dy), S5 = warp_sum(s0 * dy * dy);
-                g5 = warp_sum(g5); g6 = warp_sum(g6); g7 = warp_sum(g7); g8 = warp_sum(g8);
-                if (lane == 0) {
+                // lane 4q ends with sum q of (S1, S2, S3, S4, S5, g5, g6, g7)
+                const float vals8[8] = {s1, s0 * dy, s2, s1 * dy, s0 * dy * dy, g5, g6, g7};
+                const float mine = warp_sum8(vals8, lane);
+                const float S1 = __shfl_sync(0xFFFFFFFFu, mine, 0), S2 = __shfl_sync(0xFFFFFFFFu, mine, 4);
+                g8 = warp_sum(g8);
+                const int q = lane >> 2;
+                if ((lane & 3) == 0 || lane == 1) {
+                    // the conic and mean gradients from the five sums:
+                    // dL/du = -A S1 - B S2, dL/dv = -C S2 - B S1,
+                    // dL/dA = -S3 / 2, dL/dB = -S4, dL/dC = -S5 / 2
                     const float4 co = s_b[j];
-                    const float gu = -co.x * S1 - co.y * S2, gv = -co.z * S2 - co.y * S1;
-                    const float gA = -0.5f * S3, gB = -S4, gC = -0.5f * S5;
-                    if (NT == 32) {
-                        s_acc[0][j] += gu; s_acc[1][j] += gv; s_acc[2][j] += gA;
-                        s_acc[3][j] += gB; s_acc[4][j] += gC; s_acc[5][j] += g5;
-                        s_acc[6][j] += g6; s_acc[7][j] += g7; s_acc[8][j] += g8;
-                    } else {
-                        atomicAdd(&s_acc[0][j], gu); atomicAdd(&s_acc[1][j], gv); atomicAdd(&s_acc[2][j], gA);
-                        atomicAdd(&s_acc[3][j], gB); atomicAdd(&s_acc[4][j], gC); atomicAdd(&s_acc[5][j], g5);
-                        atomicAdd(&s_acc[6][j], g6); atomicAdd(&s_acc[7][j], g7); atomicAdd(&s_acc[8][j], g8);
+                    float val;
+                    int slot;
+                    if (lane == 1) { val = g8; slot = 8; }
+                    else {
+                        slot = q;
+                        val = q == 0 ? -co.x * S1 - co.y * S2
+                            : q == 1 ? -co.z * S2 - co.y * S1
+                            : q == 2 ? -0.5f * mine
+                            : q == 3 ? -mine
+                            : q == 4 ? -0.5f * mine : mine;
                     }
+                    if (NT == 32) s_acc[slot][j] += val;
+                    else atomicAdd(&s_acc[slot][j], val);
                 }
             }
         }
@@ -302,19 +345,22 @@ k_raster_bwd(const float4* __restrict__ proj, const ViewInfo* __restrict__ vt, i
 
 }  // namespace
 
-void launch_render_fwd(const float* proj, const ViewInfo* vt, int V, int64_t n, int tile,
+void launch_render_fwd(const float* proj, const ViewInfo* vt, int V, int64_t n, int tile, int tpr,
                        const uint32_t* vals, const uint32_t* ranges, float3 bg, float* image,
                        float* T_final, uint32_t* n_contrib, int64_t total_tiles, cudaStream_t st) {
     if (total_tiles <= 0) return;
     const float4* p = reinterpret_cast<const float4*>(proj);
     const uint2* r = reinterpret_cast<const uint2*>(ranges);
+    const unsigned nb = (unsigned)total_tiles;
     if (tile == 8)
-        k_render_fwd<8><<<(unsigned)total_tiles, 8 * kTPR, 0, st>>>(p, vt, V, n, vals, r, bg, image, T_final, n_contrib);
+        k_render_fwd<8, 4><<<nb, 32, 0, st>>>(p, vt, V, n, vals, r, bg, image, T_final, n_contrib);
+    else if (tpr == 2)
+        k_render_fwd<16, 2><<<nb, 32, 0, st>>>(p, vt, V, n, vals, r, bg, image, T_final, n_contrib);
     else
-        k_render_fwd<16><<<(unsigned)total_tiles, 16 * kTPR, 0, st>>>(p, vt, V, n, vals, r, bg, image, T_final, n_contrib);
+        k_render_fwd<16, 4><<<nb, 64, 0, st>>>(p, vt, V, n, vals, r, bg, image, T_final, n_contrib);
 }
 
-void launch_raster_bwd(const float* proj, const ViewInfo* vt, int V, int64_t n, int tile,
+void launch_raster_bwd(const float* proj, const ViewInfo* vt, int V, int64_t n, int tile, int tpr,
                        const uint32_t* vals, const uint32_t* ranges, float3 bg, const float* T_final,
                        const uint32_t* n_contrib, const float* dimage, float* grad2d,
                        int64_t total_tiles, cudaStream_t st) {
@@ -322,10 +368,13 @@ void launch_raster_bwd(const float* proj, const ViewInfo* vt, int V, int64_t n, 
     if (total_tiles <= 0) return;
     const float4* p = reinterpret_cast<const float4*>(proj);
     const uint2* r = reinterpret_cast<const uint2*>(ranges);
+    const unsigned nb = (unsigned)total_tiles;
     if (tile == 8)
-        k_raster_bwd<8><<<(unsigned)total_tiles, 8 * kTPR, 0, st>>>(p, vt, V, n, vals, r, bg, T_final, n_contrib, dimage, grad2d);
+        k_raster_bwd<8, 4><<<nb, 32, 0, st>>>(p, vt, V, n, vals, r, bg, T_final, n_contrib, dimage, grad2d);
+    else if (tpr == 2)
+        k_raster_bwd<16, 2><<<nb, 32, 0, st>>>(p, vt, V, n, vals, r, bg, T_final, n_contrib, dimage, grad2d);
     else
-        k_raster_bwd<16><<<(unsigned)total_tiles, 16 * kTPR, 0, st>>>(p, vt, V, n, vals, r, bg, T_final, n_contrib, dimage, grad2d);
+        k_raster_bwd<16, 4><<<nb, 64, 0, st>>>(p, vt, V, n, vals, r, bg, T_final, n_contrib, dimage, grad2d);
 }
 
 }  // namespace gs

@@ -295,3 +295,20 @@ def test_tile_size_8_matches_16():
     np.testing.assert_array_equal(b.sorted_vals(), vals)
     np.testing.assert_array_equal(b.ranges_np(), ranges)
     a.close(); b.close()
+
+
+def test_raster_threads_per_row_2_matches_4():
+    """Two or four threads per pixel row change only which thread owns which
+    pixels: the images, transmittances and contributor counts are identical
+    and the 2D gradients agree up to the order of the float32 sums."""
+    planes = scene(20_000, 2, 6)
+    cams = gi.ring_cameras(2, 200, 136)
+    target = O.forward(scene(20_000, 2, 7), 2, cams32(cams))["image"]
+    a = GpuRun(planes, 2, cams, target, raster_threads=4)
+    b = GpuRun(planes, 2, cams, target, raster_threads=2)
+    np.testing.assert_array_equal(a.np("image"), b.np("image"))
+    np.testing.assert_array_equal(a.np("T"), b.np("T"))
+    np.testing.assert_array_equal(a.np("nc"), b.np("nc"))
+    assert rel_l2(b.np("grad2d"), a.np("grad2d")) <= 1e-5
+    assert rel_l2(b.np("dparams"), a.np("dparams")) <= 1e-5
+    a.close(); b.close()
