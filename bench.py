@@ -58,14 +58,25 @@ RASTER_BWD_FLOP_PER_FRAGMENT = 60     # one (pixel, fragment) adjoint evaluation
 FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12  # SMs x FP32 lanes x FMA x max SM clock
 
 
-def phase_model(n, V, K, total_tiles, npix, sum_nc, n_changed, tile_passes):
-    """Algorithmic bytes (HBM) or FLOPs per launch of each phase."""
+def phase_model(n, V, K, total_tiles, npix, sum_nc, n_changed, binning, passes, Kc, chunks):
+    """Algorithmic bytes (HBM) or FLOPs per launch of each phase.
+
+    K fine (tile, Gaussian) entries; two-level binning also moves Kc coarse
+    (super-tile, Gaussian) entries through `passes` radix passes and writes
+    per-chunk tile counts (chunks x 64); direct binning moves the K entries
+    through `passes` passes."""
     vn = V * n
+    if binning == "two_level":
+        emit = vn * (8 + 16) + Kc * 8
+        sort = Kc * 16 * passes + 2 * Kc * 8 + K * 4 + total_tiles * 8 + chunks * 64 * 4 * 3
+    else:
+        emit = vn * (8 + 16) + K * 8
+        sort = K * (16 * (passes - 1) + 12) + total_tiles * 16
     return {
         "project": ("hbm", n * 240 + vn * (64 + 8)),
         "depth_sort": ("hbm", vn * (4 * 16 + 4)),
-        "emit": ("hbm", vn * (4 + 32) + K * 8),
-        "tile_sort": ("hbm", K * (16 * (tile_passes - 1) + 12) + total_tiles * 16),
+        "emit": ("hbm", emit),
+        "tile_sort": ("hbm", sort),
         "render_fwd": ("alu", sum_nc * RASTER_FWD_FLOP_PER_FRAGMENT),
         "loss": ("hbm", 3 * npix * 44),
         "raster_bwd": ("alu", sum_nc * RASTER_BWD_FLOP_PER_FRAGMENT),
@@ -80,11 +91,28 @@ SINGLE_KERNEL_PHASES = {"project": "k_project", "emit": "k_emit", "render_fwd": 
                         "raster_bwd": "k_raster_bwd", "project_bwd": "k_project_bwd", "adam": "k_adam"}
 
 
-def gpu_launches_per_step(tile_passes):
-    # view table 1, projection 1, bin/sort (ranges clear, depth count, depth sort 7,
-    # emission 3, tile sort 3 + passes, ranges) 14 + passes, render 1, loss 2,
-    # raster adjoint 1, projection adjoint 1, Adam 2, delta 3
-    return 1 + 1 + (14 + tile_passes) + 1 + 2 + 1 + 1 + 2 + 3
+def gpu_launches_per_step(binning, passes):
+    """Kernels of one train step, counted from the launch sequence: view
+    table, projection, depth sort (count, histogram, look-back clear, scan,
+    4 passes), emission and sort (two-level: emission, fine total, ranges
+    init, look-back clear, scan, passes, ranges fix, chunk table, count,
+    prefix, tile scan, write; direct: emission, ranges init, look-back clear,
+    scan, passes, ranges fix), compositing, loss (2), adjoints (2), Adam (2),
+    delta (3)."""
+    depth = 8
+    sort = (11 + passes) if binning == "two_level" else (5 + passes)
+    return 1 + 1 + depth + sort + 1 + 2 + 1 + 1 + 2 + 3
+
+
+def coarse_work(torch, proj, V, n):
+    """Super-tile entries of a projection (a work count for the roofline)."""
+    b = proj.view(torch.int32).view(V * n, 16)
+    lo = b[:, 12].to(torch.int64) & 0xFFFFFFFF
+    hi = b[:, 13].to(torch.int64) & 0xFFFFFFFF
+    vis = b[:, 14] > 0
+    x0, y0, x1, y1 = lo & 0xFFFF, lo >> 16, hi & 0xFFFF, hi >> 16
+    per = ((((x1 - 1) >> 3) - (x0 >> 3) + 1) * (((y1 - 1) >> 3) - (y0 >> 3) + 1)) * vis
+    return int(per.sum().item())
 
 
 _CUDART = None
@@ -285,6 +313,17 @@ def run_ours(args, rank, world, local_rank):
     ctx = gs.Context(local_rank, 0, tile=args.tile, sort_bits=args.sort_bits, sort_items=args.sort_items,
                      binning=args.binning, raster_threads=args.raster_threads)
     keys_cap = estimate_keys(ctx, params, sh, cams, slack=1.3, dyn=dyn)
+    tuned = None
+    if args.autotune:
+        # pick binning, digit width, items per thread and raster layout for this
+        # workload (gs_autotune); the step graph is captured afterwards
+        ctx.reserve(ctx.workspace_size(cams, n, keys_cap))
+        best, entries = gs.gs_autotune(ctx, params, sh, cams, keys_cap, reps=2, dyn=dyn)
+        args.binning, args.sort_bits = best["binning"], best["sort_bits"]
+        args.sort_items, args.raster_threads = best["sort_items"], best["raster_threads"]
+        worst = max(e["ms"] for e in entries)
+        tuned = {"configs_tried": len(entries), "best_ms": best["ms"], "worst_ms": worst,
+                 "timed": "projection + bin/sort + compositing + its adjoint"}
     tr = OnlineTrainer(params, sh, cams, keys_cap, ctx=ctx, dyn=dyn)
     packed = tr.packed
     tctx = gs.Context(local_rank, 0, tile=args.tile, sort_bits=args.sort_bits, sort_items=args.sort_items,
@@ -356,9 +395,14 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     K = int(nk.item())
     sum_nc = int(nc.to(torch.int64).sum().item())
+    Kc = coarse_work(torch, proj, V, n)
+    st_px = args.tile * 8
+    n_super = sum(((int(w) + st_px - 1) // st_px) * ((int(h) + st_px - 1) // st_px)
+                  for w, h in zip(packed["width"], packed["height"]))
+    chunks = Kc // 256 + n_super
     del proj, vals, ranges, T, nc
     tile_passes = math.ceil(math.ceil(math.log2(max(tr.total_tiles, 2))) / args.sort_bits)
-    model = phase_model(n, V, K, tr.total_tiles, tr.npix, sum_nc, changed, tile_passes)
+    model = phase_model(n, V, K, tr.total_tiles, tr.npix, sum_nc, changed, args.binning, tile_passes, Kc, chunks)
     hbm_peak, peak_src = _peaks()
     kernels = {}
     for name, ms in phase_avg.items():
@@ -422,20 +466,21 @@ def run_ours(args, rank, world, local_rank):
                "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                "config": {"workload": args.workload, "gaussians": n, "sh_degree": sh, "views": V,
-                          "resolution": [W, H], "keys_per_step": K, "keys_cap": keys_cap, "tile": args.tile,
+                          "resolution": [W, H], "keys_per_step": K, "coarse_keys_per_step": Kc,
+                          "keys_cap": keys_cap, "tile": args.tile,
                           "dynamics": "16 rigid objects, new SE(3) pose per frame (spin <= 2 deg/frame, "
                                       "sinusoidal translation 0.1), light at 45 deg zenith turning 1 deg/frame; "
                                       "Lambertian relight of the DC term (ambient 0.3, diffuse 0.7)"
                           if dynamic else None,
                           "sort_digit_bits": args.sort_bits, "sort_items": args.sort_items, "binning": args.binning,
-                          "raster_threads_per_row": args.raster_threads,
+                          "raster_threads_per_row": args.raster_threads, "autotune": tuned,
                           "graph": True,
                           "l2": "inputs larger than L2 (params 240 MB, keys > 1 GB per step)",
                           "targets": "re-rendered each step by gs_render_batch outside the step's events",
                           "parallelism": "replicas" if world > 1 else "single"},
                "roofline": roofline, "cpu_baseline": cpu, "clocks": clk, "e2e": e2e,
                "plain_step": plain, "serving": serving,
-               "gpu_launches": gpu_launches_per_step(tile_passes) * args.steps,
+               "gpu_launches": gpu_launches_per_step(args.binning, tile_passes) * args.steps,
                "phases_ms": phase_avg, "kernels": kernels, "loss_last": loss_last, "delta_changed_last": changed,
                "wall_s_timed_loop": wall}
         print(json.dumps(out), flush=True)
@@ -539,6 +584,8 @@ def main():
     ap.add_argument("--sort-items", type=int, default=16)
     ap.add_argument("--binning", choices=("two_level", "direct"), default="two_level")
     ap.add_argument("--raster-threads", type=int, choices=(2, 4), default=4)
+    ap.add_argument("--autotune", action=argparse.BooleanOptionalAction, default=True,
+                    help="choose binning / sort / raster settings with gs_autotune before timing")
     ap.add_argument("--e2e-steps", type=int, default=30)
     ap.add_argument("--cpu-samples", type=int, default=12)
     ap.add_argument("--plain-steps", type=int, default=10)

@@ -139,6 +139,33 @@ gs_status_t gs_ctx_set_binning(gs_ctx* ctx, int32_t mode);
  * among more pixels.  8 x 8 tiles always use 4.  Results are identical up to
  * the order of floating-point gradient sums. */
 gs_status_t gs_ctx_set_raster_threads(gs_ctx* ctx, int32_t threads_per_row);
+/* One configuration timed by gs_autotune. */
+typedef struct gs_tune_entry {
+    int32_t binning;         /* GS_BINNING_* */
+    int32_t sort_bits;       /* radix digit width */
+    int32_t sort_items;      /* keys per thread per sort tile */
+    int32_t raster_threads;  /* threads per pixel row */
+    float ms;                /* mean time of one pass */
+} gs_tune_entry;
+
+/* Autotuner.  Times projection, binning and sorting, compositing and the
+ * compositing adjoint of `scene` for the cameras (device copy d_cams, host copy
+ * host_cams) under every combination of binning {two-level, direct} x digit
+ * bits {8, 7, 6} x items per thread {16, 12, 8} x threads per pixel row
+ * {4, 2} (8-px tiles: 4 only), `reps` passes each after one warm-up pass, and
+ * leaves the context set to the fastest.  The tile size is kept (it defines the
+ * caller's tile grid).  The adjoint is fed the rendered image as its image
+ * gradient; its cost does not depend on the values.  Workspace: gs_workspace_size(ctx, host_cams, V,
+ * n, keys_cap).  Synchronous (it waits on events), so not for stream capture;
+ * a graph captured earlier keeps its old configuration until captured again.
+ * results (may be NULL when max_results is 0) receives up to max_results
+ * entries in the order tried, *n_results (may be NULL) their number.  A kernel
+ * error (for example GS_ERR_CAPACITY when keys_cap is too small) stops the
+ * search, restores the previous settings and is returned (the status word
+ * keeps it). */
+gs_status_t gs_autotune(gs_ctx* ctx, const gs_scene* scene, const gs_camera* d_cams, const gs_camera* host_cams,
+                        int32_t n_views, int64_t keys_cap, int32_t reps, gs_tune_entry* results,
+                        int32_t max_results, int32_t* n_results, void* stream);
 /* Reads and clears the device status word (synchronises `stream`).
  * *status receives the first error a kernel recorded since the last read
  * (GS_OK if none); *detail receives the required size for GS_ERR_CAPACITY. */

@@ -326,6 +326,26 @@ def gs_render_batch(ctx, params, sh_degree, d_cams, n_requests, total_tiles, key
     return image
 
 
+def gs_autotune(ctx, params, sh_degree, cams, keys_cap, reps=3, stream=None, dyn=None):
+    """Time the render/adjoint path over the tunables (gs_autotune) and leave
+    `ctx` set to the fastest.  Returns (best, entries): dicts with binning,
+    sort_bits, sort_items, raster_threads and ms."""
+    packed, host = _host_cams(cams)
+    V = len(packed)
+    d_cams = cameras_to_device(packed, params.device)
+    out = (_lib.gs_tune_entry * 64)()
+    cnt = C.c_int32(0)
+    sc = _scene(params, sh_degree, dyn)
+    check("gs_autotune", _lib.lib().gs_autotune(ctx.ptr, C.byref(sc), _ptr(d_cams), host, V, int(keys_cap),
+                                                int(reps), out, 64, C.byref(cnt), _stream(stream)))
+    names = {v: k for k, v in BINNING.items()}
+    entries = [{"binning": names[e.binning], "sort_bits": e.sort_bits, "sort_items": e.sort_items,
+                "raster_threads": e.raster_threads, "ms": float(e.ms)} for e in out[:cnt.value]]
+    best = min(entries, key=lambda e: e["ms"])
+    ctx.binning, ctx.raster_threads = best["binning"], best["raster_threads"]
+    return best, entries
+
+
 def train_io(params, grads, m, v, baseline, targets, image, d_loss, d_idx, d_records, d_count, d_step):
     return _lib.gs_train_io(*(t.data_ptr() for t in (params, grads, m, v, baseline, targets, image, d_loss,
                                                      d_idx, d_records, d_count, d_step)))

@@ -23,7 +23,7 @@ EXPORTS = (
     "gs_render_fwd", "gs_loss", "gs_raster_bwd", "gs_project_bwd", "gs_render_bwd",
     "gs_adam_step", "gs_extract_delta", "gs_render_batch", "gs_train_step",
     "gs_train_graph_capture", "gs_graph_launch", "gs_train_step_events",
-    "gs_train_graph_capture_events", "gs_extract_delta_noalloc",
+    "gs_train_graph_capture_events", "gs_extract_delta_noalloc", "gs_autotune",
 )
 
 
@@ -47,6 +47,11 @@ class gs_dynamics(C.Structure):
 class gs_scene(C.Structure):
     _fields_ = [("n", C.c_int64), ("sh_degree", C.c_int32), ("_pad", C.c_int32),
                 ("params", C.c_void_p), ("dyn", C.POINTER(gs_dynamics))]
+
+
+class gs_tune_entry(C.Structure):
+    _fields_ = [("binning", C.c_int32), ("sort_bits", C.c_int32), ("sort_items", C.c_int32),
+                ("raster_threads", C.c_int32), ("ms", C.c_float)]
 
 
 class gs_adam_cfg(C.Structure):
@@ -101,6 +106,8 @@ _SIGS = {
     "gs_graph_launch": [_P, _P],
     "gs_train_step_events": [_P, _P, C.POINTER(gs_train_io), C.POINTER(gs_train_cfg), C.POINTER(_P), _P],
     "gs_train_graph_capture_events": [_P, _P, C.POINTER(gs_train_io), C.POINTER(gs_train_cfg), C.POINTER(_P), _P],
+    "gs_autotune": [_P, C.POINTER(gs_scene), _P, C.POINTER(gs_camera), _I32, _I64, _I32, C.POINTER(gs_tune_entry),
+                    _I32, C.POINTER(_I32), _P],
 }
 TRAIN_PHASE_EVENTS = 11
 TRAIN_PHASES = ("project", "depth_sort", "emit", "tile_sort", "render_fwd", "loss", "raster_bwd", "project_bwd",

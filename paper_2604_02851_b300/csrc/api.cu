@@ -439,6 +439,103 @@ gs_status_t gs_train_step_events(gs_ctx* ctx, const gs_camera* d_cams, const gs_
     return launch_check();
 }
 
+gs_status_t gs_autotune(gs_ctx* ctx, const gs_scene* scene, const gs_camera* d_cams, const gs_camera* host_cams,
+                        int32_t n_views, int64_t keys_cap, int32_t reps, gs_tune_entry* results,
+                        int32_t max_results, int32_t* n_results, void* stream) {
+    if (!ctx || !scene || !d_cams || !host_cams || bad_views(n_views) || scene->n < 0 || scene->sh_degree < 0 ||
+        scene->sh_degree > 3 || (scene->n > 0 && !scene->params) || keys_cap < 0 || keys_cap >= (1LL << 32) ||
+        (int64_t)n_views * scene->n >= (1LL << 32) || reps < 1 || max_results < 0 ||
+        (max_results > 0 && !results) || bad_dyn(scene->dyn))
+        return GS_ERR_ARG;
+    const int V = n_views;
+    const int64_t n = scene->n;
+    const int B = ctx->tile;
+    const int64_t tt = tiles_of(host_cams, V, B);
+    int64_t px = 0;
+    for (int v = 0; v < V; ++v) px += (int64_t)host_cams[v].width * host_cams[v].height;
+    const FusedPlan p0 = plan_fused(nullptr, V, n, keys_cap, tt, px, host_cams[0].height, host_cams[0].width, true);
+    if (check_ws(ctx, p0.bytes)) return GS_ERR_CAPACITY;
+    const FusedPlan p = plan_fused(ctx->ws, V, n, keys_cap, tt, px, host_cams[0].height, host_cams[0].width, true);
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = S(stream);
+    SortScratch s;
+    carve_sort_scratch(p.sort, V, n, keys_cap, tt, &s);
+    const Dyn dyn = make_dyn(scene->dyn);
+    // the image is not read back: it goes to the image-gradient buffer, which
+    // the adjoint then reads (its cost does not depend on the values)
+    float* image = p.dimage;
+    const float3 bg = make_float3(0.f, 0.f, 0.f);
+    auto run = [&]() {
+        launch_view_table(d_cams, V, B, p.vt, tt, ctx->d_status, st);
+        launch_project(scene->params, n, scene->sh_degree, dyn, d_cams, p.vt, V, B, p.proj, s.dkv[0], st);
+        launch_bin_sort(p.proj, p.vt, V, n, keys_cap, tt, ctx->binning, ctx->sort_bits, ctx->sort_items, s, true,
+                        nullptr, p.vals, p.ranges, p.n_keys, ctx->d_status, ctx->sm_count, st);
+        launch_render_fwd(p.proj, p.vt, V, n, B, ctx->raster_tpr, p.vals, p.ranges, bg, image, p.T_final,
+                          p.n_contrib, tt, st);
+        launch_raster_bwd(p.proj, p.vt, V, n, B, ctx->raster_tpr, p.vals, p.ranges, bg, p.T_final, p.n_contrib,
+                          p.dimage, p.grad2d, tt, st);
+    };
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return GS_ERR_CUDA;
+    if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return GS_ERR_CUDA; }
+    const int keep_bin = ctx->binning, keep_bits = ctx->sort_bits, keep_items = ctx->sort_items,
+              keep_tpr = ctx->raster_tpr;
+    const int bins[2] = {kBinTwoLevel, kBinDirect};
+    const int bitss[3] = {8, 7, 6};
+    const int itemss[3] = {16, 12, 8};
+    const int tprs[2] = {4, 2};
+    float best = -1.f;
+    int bb = keep_bin, bbits = keep_bits, bitems = keep_items, btpr = keep_tpr;
+    int32_t count = 0;
+    gs_status_t rc = GS_OK;
+    for (int ib = 0; ib < 2 && rc == GS_OK; ++ib)
+        for (int ibits = 0; ibits < 3 && rc == GS_OK; ++ibits)
+            for (int iit = 0; iit < 3 && rc == GS_OK; ++iit)
+                for (int itp = 0; itp < 2 && rc == GS_OK; ++itp) {
+                    if (B == 8 && tprs[itp] != 4) continue;  // 8-px tiles have one layout
+                    ctx->binning = bins[ib];
+                    ctx->sort_bits = bitss[ibits];
+                    ctx->sort_items = itemss[iit];
+                    ctx->raster_tpr = tprs[itp];
+                    run();  // warm-up
+                    cudaEventRecord(e0, st);
+                    for (int r = 0; r < reps; ++r) run();
+                    cudaEventRecord(e1, st);
+                    if (cudaEventSynchronize(e1) != cudaSuccess) { rc = GS_ERR_CUDA; break; }
+                    DevStatus h{};
+                    if (cudaMemcpy(&h, ctx->d_status, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess) {
+                        rc = GS_ERR_CUDA;
+                        break;
+                    }
+                    if (h.code != GS_OK) { rc = (gs_status_t)h.code; break; }  // left in the status word
+                    float ms = 0.f;
+                    cudaEventElapsedTime(&ms, e0, e1);
+                    ms /= (float)reps;
+                    if (count < max_results) {
+                        gs_tune_entry& t = results[count];
+                        t.binning = bins[ib] == kBinDirect ? GS_BINNING_DIRECT : GS_BINNING_TWO_LEVEL;
+                        t.sort_bits = bitss[ibits];
+                        t.sort_items = itemss[iit];
+                        t.raster_threads = tprs[itp];
+                        t.ms = ms;
+                    }
+                    ++count;
+                    if (best < 0.f || ms < best) {
+                        best = ms;
+                        bb = bins[ib]; bbits = bitss[ibits]; bitems = itemss[iit]; btpr = tprs[itp];
+                    }
+                }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (n_results) *n_results = count < max_results ? count : max_results;
+    if (rc != GS_OK) {
+        ctx->binning = keep_bin; ctx->sort_bits = keep_bits; ctx->sort_items = keep_items; ctx->raster_tpr = keep_tpr;
+        return rc;
+    }
+    ctx->binning = bb; ctx->sort_bits = bbits; ctx->sort_items = bitems; ctx->raster_tpr = btpr;
+    return launch_check();
+}
+
 gs_status_t gs_train_graph_capture(gs_ctx* ctx, const gs_camera* d_cams, const gs_train_io* io,
                                    const gs_train_cfg* cfg, void* stream) {
     return gs_train_graph_capture_events(ctx, d_cams, io, cfg, nullptr, stream);

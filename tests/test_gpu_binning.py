@@ -123,3 +123,37 @@ def test_render_after_overflow_reads_stored_entries_only(mode):
     code, detail = ctx.status()
     assert code == 2 and detail == int(nk.item()) > cap
     ctx.close()
+
+
+def test_autotune_times_every_configuration_and_keeps_results_exact():
+    """gs_autotune tries 2 binnings x 3 digit widths x 3 item counts x 2 raster
+    layouts, leaves the context on the fastest, and the sort it then produces is
+    still the oracle's."""
+    import torch
+    import paper_2604_02851_b300 as gs
+    n, sh = 30_000, 1
+    planes = scene(n, sh, 13)
+    cams = gi.ring_cameras(3, 256, 160)
+    ctx = gs.Context(0, 0)
+    cap = 1 << 22
+    ctx.reserve(ctx.workspace_size(cams, n, cap))
+    params = torch.from_numpy(planes).cuda()
+    best, entries = gs.gs_autotune(ctx, params, sh, cams, cap, reps=2)
+    assert len(entries) == 36
+    assert {(e["binning"], e["sort_bits"], e["sort_items"], e["raster_threads"]) for e in entries} == {
+        (b, bits, it, t) for b in ("two_level", "direct") for bits in (8, 7, 6) for it in (16, 12, 8) for t in (4, 2)}
+    assert all(e["ms"] > 0 for e in entries)
+    assert best["ms"] == min(e["ms"] for e in entries)
+    assert ctx.status()[0] == 0
+    d_cams = gs.cameras_to_device(cams)
+    tt = ctx.total_tiles(cams)
+    proj = gs.gs_project(ctx, params, sh, d_cams, 3)
+    keys, vals, ranges, nk = gs.gs_bin_sort(ctx, proj, d_cams, 3, n, tt, cap)
+    torch.cuda.synchronize()
+    K = int(nk.item())
+    gp = gpu_proj_to_oracle(proj.cpu().numpy())
+    okeys, ovals, oranges = O.bin_sort(cams32(cams), gp[..., 12:16].astype(np.int32),
+                                       proj.cpu().numpy()[..., 2].astype(np.float32))
+    np.testing.assert_array_equal(vals.cpu().numpy()[:K].view(np.uint32), ovals)
+    np.testing.assert_array_equal(ranges.cpu().numpy().view(np.uint32), oranges)
+    ctx.close()
