@@ -7,7 +7,8 @@
 // channel and view.
 //
 // Two tiled kernels, 32x32 outputs per block with a 5-pixel halo staged in
-// shared memory and separable 11-tap sums:
+// shared memory and separable 11-tap sums (register-blocked, 4 outputs per
+// thread and pass, two moments per packed FP32 instruction):
 //   k_ssim_fwd: the five window moments -> SSIM map value and its partials
 //     dS/dmu_x, dS/dE[x^2], dS/dE[xy] (three maps), plus per-block sums of S
 //     and |x - y|;
@@ -22,17 +23,30 @@ namespace {
 
 constexpr int TW = 32;                 // output tile width / height
 constexpr int HALO = 5;
-constexpr int SW = TW + 2 * HALO;      // 42
+constexpr int SW = TW + 2 * HALO;      // 42 staged rows / columns
+constexpr int SP = SW + 1;             // staged row pitch (43): conflict-free blocked reads
+constexpr int HP = TW + 1;             // horizontal-pass row pitch (33)
+constexpr int RB = 4;                  // outputs per thread along a pass
 constexpr float C1 = 0.0001f, C2 = 0.0009f;
 
 struct Win { float g[11]; };
 
+__device__ __forceinline__ float rcp_approx(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Both kernels: 32 x 32 outputs per block of 256 threads.  The horizontal
+// 11-tap pass runs on the 42 staged rows, a thread producing RB adjacent
+// columns of one row from 14 staged values; the vertical pass gives each
+// thread RB adjacent rows of one column from 14 horizontal sums.
 __global__ void __launch_bounds__(256)
 k_ssim_fwd(const float* __restrict__ x, const float* __restrict__ y, int H, int W, Win win,
            float* __restrict__ dm0, float* __restrict__ dm1, float* __restrict__ dm2,
            float2* __restrict__ partial) {
-    __shared__ float sx[SW][SW], sy[SW][SW];
-    __shared__ float hs[5][SW][TW];
+    __shared__ float sx[SW][SP], sy[SW][SP];
+    __shared__ float hs[5][SW][HP];
     const int plane = blockIdx.z;
     const int64_t HW = (int64_t)H * W;
     const float* xp = x + plane * HW;
@@ -46,39 +60,75 @@ k_ssim_fwd(const float* __restrict__ x, const float* __restrict__ y, int H, int 
         sy[r][c] = in ? yp[(int64_t)gy * W + gx] : 0.f;
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < SW * TW; i += 256) {
-        const int r = i / TW, c = i % TW;
-        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f, a4 = 0.f;
+    // horizontal: task = (row r of 42, column group of RB)
+    for (int t = threadIdx.x; t < SW * (TW / RB); t += 256) {
+        const int r = t / (TW / RB), c0 = (t % (TW / RB)) * RB;
+        // (x, y), (x^2, y^2) and xy of the 14 inputs; pairs use packed FP32
+        float2 v[RB + 10], v2[RB + 10];
+        float vxy[RB + 10];
 #pragma unroll
-        for (int k = 0; k < 11; ++k) {
-            const float w = win.g[k], xv = sx[r][c + k], yv = sy[r][c + k];
-            a0 += w * xv; a1 += w * yv; a2 += w * xv * xv; a3 += w * yv * yv; a4 += w * xv * yv;
+        for (int j = 0; j < RB + 10; ++j) {
+            v[j] = make_float2(sx[r][c0 + j], sy[r][c0 + j]);
+            v2[j] = __fmul2_rn(v[j], v[j]);
+            vxy[j] = v[j].x * v[j].y;
         }
-        hs[0][r][c] = a0; hs[1][r][c] = a1; hs[2][r][c] = a2; hs[3][r][c] = a3; hs[4][r][c] = a4;
+#pragma unroll
+        for (int i = 0; i < RB; ++i) {
+            float2 a01 = make_float2(0.f, 0.f), a23 = make_float2(0.f, 0.f);
+            float a4 = 0.f;
+#pragma unroll
+            for (int k = 0; k < 11; ++k) {
+                const float2 w2 = make_float2(win.g[k], win.g[k]);
+                a01 = __ffma2_rn(w2, v[i + k], a01);
+                a23 = __ffma2_rn(w2, v2[i + k], a23);
+                a4 = fmaf(win.g[k], vxy[i + k], a4);
+            }
+            hs[0][r][c0 + i] = a01.x; hs[1][r][c0 + i] = a01.y; hs[2][r][c0 + i] = a23.x;
+            hs[3][r][c0 + i] = a23.y; hs[4][r][c0 + i] = a4;
+        }
     }
     __syncthreads();
+    // vertical: thread = (column c, row group of RB)
     float ssum = 0.f, l1 = 0.f;
-    for (int i = threadIdx.x; i < TW * TW; i += 256) {
-        const int r = i / TW, c = i % TW;
-        const int gy = oy + r, gx = ox + c;
-        if (gy >= H || gx >= W) continue;
-        float mx = 0.f, my = 0.f, exx = 0.f, eyy = 0.f, exy = 0.f;
+    {
+        const int c = threadIdx.x % TW, r0 = (threadIdx.x / TW) * RB;
+        float2 m01[RB], m23[RB];
+        float m4[RB];
 #pragma unroll
-        for (int k = 0; k < 11; ++k) {
-            const float w = win.g[k];
-            mx += w * hs[0][r + k][c]; my += w * hs[1][r + k][c];
-            exx += w * hs[2][r + k][c]; eyy += w * hs[3][r + k][c]; exy += w * hs[4][r + k][c];
+        for (int i = 0; i < RB; ++i) { m01[i] = m23[i] = make_float2(0.f, 0.f); m4[i] = 0.f; }
+#pragma unroll
+        for (int j = 0; j < RB + 10; ++j) {
+            const float2 h01 = make_float2(hs[0][r0 + j][c], hs[1][r0 + j][c]);
+            const float2 h23 = make_float2(hs[2][r0 + j][c], hs[3][r0 + j][c]);
+            const float h4 = hs[4][r0 + j][c];
+#pragma unroll
+            for (int i = 0; i < RB; ++i) {
+                const int k = j - i;
+                if (k < 0 || k > 10) continue;
+                const float2 w2 = make_float2(win.g[k], win.g[k]);
+                m01[i] = __ffma2_rn(w2, h01, m01[i]);
+                m23[i] = __ffma2_rn(w2, h23, m23[i]);
+                m4[i] = fmaf(win.g[k], h4, m4[i]);
+            }
         }
-        const float sxx = exx - mx * mx, syy = eyy - my * my, sxy = exy - mx * my;
-        const float n1 = 2.f * mx * my + C1, n2 = 2.f * sxy + C2;
-        const float d1 = mx * mx + my * my + C1, d2 = sxx + syy + C2;
-        const float S = (n1 * n2) / (d1 * d2);
-        const int64_t p = plane * HW + (int64_t)gy * W + gx;
-        dm0[p] = S * (2.f * my / n1 - 2.f * my / n2 - 2.f * mx / d1 + 2.f * mx / d2);
-        dm1[p] = -S / d2;
-        dm2[p] = 2.f * S / n2;
-        ssum += S;
-        l1 += fabsf(sx[r + HALO][c + HALO] - sy[r + HALO][c + HALO]);
+        const int gx = ox + c;
+#pragma unroll
+        for (int i = 0; i < RB; ++i) {
+            const int gy = oy + r0 + i;
+            if (gy >= H || gx >= W) continue;
+            const float mx = m01[i].x, my = m01[i].y;
+            const float sxx = m23[i].x - mx * mx, syy = m23[i].y - my * my, sxy = m4[i] - mx * my;
+            const float n1 = 2.f * mx * my + C1, n2 = 2.f * sxy + C2;
+            const float d1 = mx * mx + my * my + C1, d2 = sxx + syy + C2;
+            const float rn1 = rcp_approx(n1), rn2 = rcp_approx(n2), rd1 = rcp_approx(d1), rd2 = rcp_approx(d2);
+            const float S = n1 * n2 * rd1 * rd2;
+            const int64_t p = plane * HW + (int64_t)gy * W + gx;
+            dm0[p] = 2.f * S * (my * rn1 - my * rn2 - mx * rd1 + mx * rd2);
+            dm1[p] = -S * rd2;
+            dm2[p] = 2.f * S * rn2;
+            ssum += S;
+            l1 += fabsf(sx[r0 + i + HALO][c + HALO] - sy[r0 + i + HALO][c + HALO]);
+        }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -100,8 +150,8 @@ k_ssim_bwd(const float* __restrict__ x, const float* __restrict__ y, int H, int 
            const float* __restrict__ dm0, const float* __restrict__ dm1, const float* __restrict__ dm2,
            float inv_m, float w_l1, float w_ssim, float* __restrict__ dx,
            const float2* __restrict__ partial, int64_t n_partial, double m_total, float* __restrict__ d_loss) {
-    __shared__ float sm[3][SW][SW];
-    __shared__ float hs[3][SW][TW];
+    __shared__ float sm[3][SW][SP];
+    __shared__ float hs[3][SW][HP];
     const int plane = blockIdx.z;
     const int64_t HW = (int64_t)H * W;
     const int ox = blockIdx.x * TW, oy = blockIdx.y * TW;
@@ -115,32 +165,57 @@ k_ssim_bwd(const float* __restrict__ x, const float* __restrict__ y, int H, int 
         sm[2][r][c] = in ? dm2[p] : 0.f;
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < SW * TW; i += 256) {
-        const int r = i / TW, c = i % TW;
-        float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+    for (int t = threadIdx.x; t < SW * (TW / RB); t += 256) {
+        const int r = t / (TW / RB), c0 = (t % (TW / RB)) * RB;
+        float2 v01[RB + 10];
+        float v2[RB + 10];
 #pragma unroll
-        for (int k = 0; k < 11; ++k) {
-            const float w = win.g[k];
-            a0 += w * sm[0][r][c + k]; a1 += w * sm[1][r][c + k]; a2 += w * sm[2][r][c + k];
+        for (int j = 0; j < RB + 10; ++j) {
+            v01[j] = make_float2(sm[0][r][c0 + j], sm[1][r][c0 + j]);
+            v2[j] = sm[2][r][c0 + j];
         }
-        hs[0][r][c] = a0; hs[1][r][c] = a1; hs[2][r][c] = a2;
+#pragma unroll
+        for (int i = 0; i < RB; ++i) {
+            float2 a01 = make_float2(0.f, 0.f);
+            float a2 = 0.f;
+#pragma unroll
+            for (int k = 0; k < 11; ++k) {
+                a01 = __ffma2_rn(make_float2(win.g[k], win.g[k]), v01[i + k], a01);
+                a2 = fmaf(win.g[k], v2[i + k], a2);
+            }
+            hs[0][r][c0 + i] = a01.x; hs[1][r][c0 + i] = a01.y; hs[2][r][c0 + i] = a2;
+        }
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < TW * TW; i += 256) {
-        const int r = i / TW, c = i % TW;
-        const int gy = oy + r, gx = ox + c;
-        if (gy >= H || gx >= W) continue;
-        float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+    {
+        const int c = threadIdx.x % TW, r0 = (threadIdx.x / TW) * RB;
+        float2 a01[RB];
+        float a2[RB];
 #pragma unroll
-        for (int k = 0; k < 11; ++k) {
-            const float w = win.g[k];
-            a0 += w * hs[0][r + k][c]; a1 += w * hs[1][r + k][c]; a2 += w * hs[2][r + k][c];
+        for (int i = 0; i < RB; ++i) { a01[i] = make_float2(0.f, 0.f); a2[i] = 0.f; }
+#pragma unroll
+        for (int j = 0; j < RB + 10; ++j) {
+            const float2 h01 = make_float2(hs[0][r0 + j][c], hs[1][r0 + j][c]);
+            const float h2 = hs[2][r0 + j][c];
+#pragma unroll
+            for (int i = 0; i < RB; ++i) {
+                const int k = j - i;
+                if (k < 0 || k > 10) continue;
+                a01[i] = __ffma2_rn(make_float2(win.g[k], win.g[k]), h01, a01[i]);
+                a2[i] = fmaf(win.g[k], h2, a2[i]);
+            }
         }
-        const int64_t p = plane * HW + (int64_t)gy * W + gx;
-        const float xv = x[p], yv = y[p];
-        const float d = xv - yv;
-        const float sgn = d > 0.f ? 1.f : (d < 0.f ? -1.f : 0.f);
-        dx[p] = (w_l1 * sgn - w_ssim * (a0 + 2.f * xv * a1 + yv * a2)) * inv_m;
+        const int gx = ox + c;
+#pragma unroll
+        for (int i = 0; i < RB; ++i) {
+            const int gy = oy + r0 + i;
+            if (gy >= H || gx >= W) continue;
+            const int64_t p = plane * HW + (int64_t)gy * W + gx;
+            const float xv = x[p], yv = y[p];
+            const float d = xv - yv;
+            const float sgn = d > 0.f ? 1.f : (d < 0.f ? -1.f : 0.f);
+            dx[p] = (w_l1 * sgn - w_ssim * (a01[i].x + 2.f * xv * a01[i].y + yv * a2[i])) * inv_m;
+        }
     }
     if (blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0) {
         __shared__ double rs[256], rl[256];

@@ -26,7 +26,10 @@ from . import (Context, RECORD_BYTES, GRAD2D_STRIDE, PROJ_STRIDE, _lib, _ptr, _s
 class OnlineTrainer:
     def __init__(self, params, sh_degree: int, cams: dict, keys_cap: int, lr=1e-3, w_l1=0.8, w_ssim=0.2,
                  delta_thr=1e-3, bg=(0.0, 0.0, 0.0), tile=16, sort_bits=8, ctx: Context | None = None,
-                 dyn=None):
+                 dyn=None, share: "OnlineTrainer | None" = None):
+        """share: another trainer of the same model whose gradient, Adam
+        moments, delta baseline and step counter this one uses (a second
+        graph slot with its own targets, image and delta outputs)."""
         import torch
         self.torch = torch
         self.params = params
@@ -47,17 +50,20 @@ class OnlineTrainer:
         self.total_tiles = self.ctx.total_tiles(self.packed)
         self.npix = V * self.W * self.H
         f32 = dict(dtype=torch.float32, device=dev)
-        self.grads = torch.zeros_like(params)
-        self.m = torch.zeros_like(params)
-        self.v = torch.zeros_like(params)
-        self.baseline = params.clone()
+        if share is not None:
+            self.grads, self.m, self.v, self.baseline = share.grads, share.m, share.v, share.baseline
+        else:
+            self.grads = torch.zeros_like(params)
+            self.m = torch.zeros_like(params)
+            self.v = torch.zeros_like(params)
+            self.baseline = params.clone()
         self.targets = torch.zeros(3 * self.npix, **f32)
         self.image = torch.zeros(3 * self.npix, **f32)
         self.d_loss = torch.zeros(1, **f32)
         self.d_idx = torch.zeros(max(n, 1), dtype=torch.int32, device=dev)
         self.d_records = torch.zeros((max(n, 1), RECORD_BYTES), dtype=torch.uint8, device=dev)
         self.d_count = torch.zeros(1, dtype=torch.int32, device=dev)
-        self.d_step = torch.ones(1, dtype=torch.int32, device=dev)
+        self.d_step = share.d_step if share is not None else torch.ones(1, dtype=torch.int32, device=dev)
         self.io = train_io(params, self.grads, self.m, self.v, self.baseline, self.targets, self.image,
                            self.d_loss, self.d_idx, self.d_records, self.d_count, self.d_step)
         self.dyn = dyn  # kept alive: the step reads its device buffers
@@ -160,6 +166,101 @@ class OnlineTrainer:
 
     def raise_status(self):
         self.ctx.raise_status()
+
+
+class StreamingTrainer:
+    """The server loop with host I/O overlapped (Sec. 3.1, 3.5): reference
+    images arrive in host memory, changed-Gaussian records leave to host
+    memory.  Two graph slots share one model (parameters, Adam state, delta
+    baseline, step counter) and alternate: while slot k % 2 computes step k,
+    the copy stream uploads the targets of step k + 1 into the other slot and
+    the records of step k - 1 come back.  Steps run in order on one compute
+    stream, so the result equals the one-slot loop.
+
+    `make_ctx()` returns a fresh Context configured like the first slot's."""
+
+    def __init__(self, params, sh_degree: int, cams: dict, keys_cap: int, make_ctx, dyn=None, **kw):
+        import torch
+        self.torch = torch
+        self.slots = [OnlineTrainer(params, sh_degree, cams, keys_cap, ctx=make_ctx(), dyn=dyn, **kw)]
+        self.slots.append(OnlineTrainer(params, sh_degree, cams, keys_cap, ctx=make_ctx(), dyn=dyn,
+                                        share=self.slots[0], **kw))
+        dev = params.device
+        self.compute = torch.cuda.Stream(device=dev)
+        self.h2d = torch.cuda.Stream(device=dev)
+        self.d2h = torch.cuda.Stream(device=dev)
+        n = self.slots[0].n
+        self.host_loss = [torch.empty(1, dtype=torch.float32).pin_memory() for _ in range(2)]
+        self.host_cnt = [torch.empty(1, dtype=torch.int32).pin_memory() for _ in range(2)]
+        self.host_rec = [torch.empty((max(n, 1), RECORD_BYTES), dtype=torch.uint8).pin_memory() for _ in range(2)]
+        self.h2d_bytes = 0
+        self.d2h_bytes = 0
+
+    def capture(self):
+        for t in self.slots:
+            t.capture(self.compute)
+        self.torch.cuda.synchronize()
+
+    def run(self, host_targets, steps: int, on_delta=None):
+        """Run `steps` steps; host_targets(k) gives step k's targets as a
+        pinned host tensor (planar [V][3][H][W] floats).  on_delta(k, loss,
+        count, records) receives each step's outputs in host memory (the
+        records view is valid during the call).  Returns the loss of the last
+        step."""
+        torch = self.torch
+        Ev = torch.cuda.Event
+        slot_free = [Ev(), Ev()]       # the slot's records have been copied out
+        uploaded = [Ev(), Ev()]
+        done = [Ev(), Ev()]
+        counted = [Ev(), Ev()]
+        for e in slot_free:
+            e.record(self.compute)
+        last_loss = None
+
+        def drain(k):
+            nonlocal last_loss
+            s = k % 2
+            counted[s].synchronize()
+            m = int(self.host_cnt[s].item())
+            with torch.cuda.stream(self.d2h):
+                if m:
+                    self.host_rec[s][:m].copy_(self.slots[s].d_records[:m], non_blocking=True)
+                slot_free[s].record(self.d2h)
+            slot_free[s].synchronize()
+            self.d2h_bytes += 8 + m * RECORD_BYTES
+            last_loss = float(self.host_loss[s].item())
+            if on_delta is not None:
+                on_delta(k, last_loss, m, self.host_rec[s][:m])
+
+        for k in range(steps):
+            s = k % 2
+            t = self.slots[s]
+            src = host_targets(k)
+            with torch.cuda.stream(self.h2d):
+                self.h2d.wait_event(slot_free[s])
+                t.targets.copy_(src, non_blocking=True)
+                uploaded[s].record(self.h2d)
+            self.h2d_bytes += t.targets.numel() * 4
+            self.compute.wait_event(uploaded[s])
+            self.compute.wait_event(slot_free[s])
+            t.step(self.compute)
+            done[s].record(self.compute)
+            # step k - 1's records go out before step k's read-backs are queued
+            # on the (in-order) read-back stream, so they do not wait for step k
+            if k >= 1:
+                drain(k - 1)
+            with torch.cuda.stream(self.d2h):
+                self.d2h.wait_event(done[s])
+                self.host_loss[s].copy_(t.d_loss, non_blocking=True)
+                self.host_cnt[s].copy_(t.d_count, non_blocking=True)
+                counted[s].record(self.d2h)
+        if steps:
+            drain(steps - 1)
+        return last_loss
+
+    def raise_status(self):
+        for t in self.slots:
+            t.raise_status()
 
 
 def estimate_keys(ctx: Context, params, sh_degree: int, cams, slack: float = 1.25, dyn=None) -> int:
