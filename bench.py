@@ -86,6 +86,29 @@ def phase_model(n, V, K, total_tiles, npix, sum_nc, n_changed, binning, passes, 
     }
 
 
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum, one ncu
+# capture at full size; profiles/train_step_1M_8x720p_traffic.md), valid while
+# the kernel's source file is unchanged (first 12 hex digits of its SHA-1).
+MEASURED_TRAFFIC = {
+    ("c3_1M_8x720p", "k_raster_bwd"): (282.6e6, "csrc/raster.cu", "c37a0b537010"),
+}
+
+
+def measured_traffic(workload, kernel):
+    import hashlib
+    ent = MEASURED_TRAFFIC.get((workload, kernel))
+    if ent is None:
+        return None
+    nbytes, src, sha = ent
+    path = os.path.join(ROOT, "paper_2604_02851_b300", src)
+    try:
+        with open(path, "rb") as f:
+            cur = hashlib.sha1(f.read()).hexdigest()[:12]
+    except OSError:
+        return None
+    return nbytes if cur == sha else None
+
+
 # phases that are one kernel (plus negligible set-up launches), by kernel name
 SINGLE_KERNEL_PHASES = {"project": "k_project", "emit": "k_emit", "render_fwd": "k_render_fwd",
                         "raster_bwd": "k_raster_bwd", "project_bwd": "k_project_bwd", "adam": "k_adam"}
@@ -419,7 +442,8 @@ def run_ours(args, rank, world, local_rank):
     dk = kernels[dom]
     roofline = {"kernel": SINGLE_KERNEL_PHASES[dom], "bound": dk["bound"], "achieved": dk["achieved"],
                 "peak": dk["peak"],
-                "unit": dk["unit"], "frac": dk["frac"], "traffic": None,
+                "unit": dk["unit"], "frac": dk["frac"],
+                "traffic": measured_traffic(args.workload, SINGLE_KERNEL_PHASES[dom]),
                 "peak_source": peak_src if dk["bound"] == "hbm" else "derived: 148 SMs x 128 FP32 lanes x 2 x 2032 MHz"}
 
     # ---- end to end through the public API: host targets in, loss + delta out
