@@ -127,6 +127,23 @@ def gpu_launches_per_step(binning, passes):
     return 1 + 1 + depth + sort + 1 + 2 + 1 + 1 + 2 + 3
 
 
+def replica_seeds(rank: int):
+    """Seeds of rank r's replica: each rank trains its own model (independent
+    problems, no data-path collective)."""
+    return gi.SEED_MODEL + 1000 * rank, gi.SEED_TARGET + 1000 * rank
+
+
+def replica_throughput(my_ms: float, steps: int, world: int, device):
+    """Whole-job throughput of `world` replicas: the slowest rank's time for
+    its `steps` steps (MAX over ranks), and world * steps over that time."""
+    import torch
+    t = torch.tensor([my_ms], dtype=torch.float64, device=device)
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    total_ms = float(t.item())
+    return total_ms, world * steps / (total_ms / 1e3)
+
+
 def coarse_work(torch, proj, V, n):
     """Super-tile entries of a projection (a work count for the roofline)."""
     b = proj.view(torch.int32).view(V * n, 16)
@@ -314,8 +331,9 @@ def run_ours(args, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     n, sh, V, W, H = WORKLOADS[args.workload]
     # replicas: rank r trains its own seeded model (independent problems)
-    planes = gi.make_scene(n, sh, gi.SEED_MODEL + 1000 * rank)
-    target_planes = gi.make_scene(n, sh, gi.SEED_TARGET + 1000 * rank)
+    seed_model, seed_target = replica_seeds(rank)
+    planes = gi.make_scene(n, sh, seed_model)
+    target_planes = gi.make_scene(n, sh, seed_target)
     signs = gi.drift_signs(n)
     cams = gi.ring_cameras(V, W, H)
     params = torch.from_numpy(planes).to(dev)
@@ -397,16 +415,11 @@ def run_ours(args, rank, world, local_rank):
     if world > 1:
         torch.distributed.barrier()
     step_ms = np.array([a.elapsed_time(b) for a, b in zip(ev0, ev1)])
-    total_ms = float(step_ms.sum())
-    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-    total_ms = float(t.item())
     code, detail = tr.ctx.status()
     if code != 0:
         raise RuntimeError(f"device status {code} ({detail}) during the timed region")
+    total_ms, value = replica_throughput(float(step_ms.sum()), args.steps, world, dev)
     ms_per_step = total_ms / args.steps
-    value = world * args.steps / (total_ms / 1e3)
     loss_last = tr.loss()
     changed = tr.delta_count()
     phase_avg = {name: float(ms / args.steps) for name, ms in zip(gs._lib.TRAIN_PHASES, phase_ms)}

@@ -58,6 +58,13 @@ def lib():
         L.or_loss.restype = C.c_double
         L.or_adam.argtypes = [C.c_int64, _D, _D, _D, _D, _D, C.c_double, C.c_double, C.c_double, C.c_int]
         L.or_f32_to_f16.argtypes = [C.c_float]
+        L.or_f16_to_f32.argtypes = [C.c_uint16]
+        L.or_f16_to_f32.restype = C.c_float
+        L.or_tensor_record_bytes.argtypes = [C.c_int]
+        L.or_tensor_delta.argtypes = [C.c_int64, _F, _F, C.c_int, C.c_float, _U32, _U8]
+        L.or_tensor_delta.restype = C.c_int64
+        L.or_apply_tensor_delta.argtypes = [C.c_int64, _F, C.c_int, C.c_int64, _U32, _U8]
+        L.or_apply_delta.argtypes = [C.c_int64, _F, C.c_int64, _U8]
         L.or_f32_to_f16.restype = C.c_uint16
         L.or_delta.argtypes = [C.c_int64, _F, _F, C.c_float, _U32, _U8]
         L.or_delta.restype = C.c_int64
@@ -246,6 +253,45 @@ def delta(theta_planes, base_planes, thr: float = 1e-3):
     rec = np.zeros((max(n, 1), 128), dtype=np.uint8)
     M = int(lib().or_delta(n, th, base, np.float32(thr), idx, rec))
     return idx[:M], rec[:M], rows_to_planes(base)
+
+
+ATTR_GROUPS = {"mean": 1, "opacity": 2, "scale": 4, "rotation": 8, "dc": 16, "sh_rest": 32}
+
+
+def f16_bits_to_f32(bits) -> np.ndarray:
+    b = np.asarray(bits, dtype=np.uint16).ravel()
+    return np.array([lib().or_f16_to_f32(int(v)) for v in b], dtype=np.float32)
+
+
+def tensor_record_bytes(attr: int) -> int:
+    return int(lib().or_tensor_record_bytes(int(attr)))
+
+
+def tensor_delta(theta_planes, base_planes, attr: int, thr: float = 1e-3):
+    """-> (idx u32[M], vals u8[M][record bytes], new baseline planes)."""
+    th = np.ascontiguousarray(planes_to_rows(theta_planes), dtype=np.float32)
+    base = np.ascontiguousarray(planes_to_rows(base_planes), dtype=np.float32)
+    n = th.shape[0]
+    rb = tensor_record_bytes(attr)
+    idx = np.zeros(max(n, 1), dtype=np.uint32)
+    vals = np.zeros((max(n, 1), rb), dtype=np.uint8)
+    M = int(lib().or_tensor_delta(n, th, base, int(attr), np.float32(thr), idx, vals))
+    return idx[:M], vals[:M], rows_to_planes(base)
+
+
+def apply_tensor_delta(params_planes, attr: int, idx, vals):
+    rows = np.ascontiguousarray(planes_to_rows(params_planes), dtype=np.float32)
+    idx = np.ascontiguousarray(idx, dtype=np.uint32)
+    vals = np.ascontiguousarray(vals, dtype=np.uint8)
+    lib().or_apply_tensor_delta(rows.shape[0], rows, int(attr), len(idx), idx, vals)
+    return rows_to_planes(rows)
+
+
+def apply_delta(params_planes, records):
+    rows = np.ascontiguousarray(planes_to_rows(params_planes), dtype=np.float32)
+    rec = np.ascontiguousarray(records, dtype=np.uint8)
+    lib().or_apply_delta(rows.shape[0], rows, len(rec), rec)
+    return rows_to_planes(rows)
 
 
 def decision_flips(cams, projA, valsA, rangesA, projB, valsB, rangesB, tile: int = TILE):

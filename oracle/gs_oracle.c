@@ -853,6 +853,123 @@ int64_t or_delta(int64_t n, const float* theta, float* base, float thr, uint32_t
 }
 
 /* ------------------------------------------------------------------------
+ * Tensor deltas per attribute group and their client-side replay (Sec. 3.5:
+ * attribute-specific delta encoders on the server, matching replay objects on
+ * the client; opacity and DC every frame, the other tensors less often).
+ * Groups (bit, flat floats of a Gaussian's row, encoding):
+ *   1 mean      0..2    float32
+ *   2 opacity   3       float16 (logit)
+ *   4 scale     4..6    float16 (log-scale)
+ *   8 rotation  8..11   float16 (quaternion)
+ *  16 dc        12..14  float16 (SH degree 0)
+ *  32 sh_rest   15..59  float16 (SH degrees 1..3)
+ * A Gaussian is sent for a group when max over the group's floats of
+ * |theta - base| > thr; sent Gaussians ascend; their group floats become the
+ * new baseline.  Records are the group's values, packed densely.
+ * ---------------------------------------------------------------------- */
+static int group_floats(int attr, int* lo, int* hi, int* f32) {
+    *f32 = 0;
+    switch (attr) {
+        case 1: *lo = 0; *hi = 3; *f32 = 1; return 1;
+        case 2: *lo = 3; *hi = 4; return 1;
+        case 4: *lo = 4; *hi = 7; return 1;
+        case 8: *lo = 8; *hi = 12; return 1;
+        case 16: *lo = 12; *hi = 15; return 1;
+        case 32: *lo = 15; *hi = 60; return 1;
+        default: return 0;
+    }
+}
+
+/* IEEE binary16 -> float: sign, 5-bit exponent (bias 15), 10-bit fraction;
+ * subnormals are fraction * 2^-24; exponent 31 is inf / NaN. */
+float or_f16_to_f32(uint16_t h) {
+    const int s = (h >> 15) & 1, e = (h >> 10) & 31, f = h & 1023;
+    double v;
+    if (e == 0) v = ldexp((double)f, -24);
+    else if (e == 31) v = f ? NAN : INFINITY;
+    else v = ldexp(1024.0 + (double)f, e - 25);
+    return (float)(s ? -v : v);
+}
+
+int or_tensor_record_bytes(int attr) {
+    int lo, hi, f32;
+    if (!group_floats(attr, &lo, &hi, &f32)) return -1;
+    return (hi - lo) * (f32 ? 4 : 2);
+}
+
+int64_t or_tensor_delta(int64_t n, const float* theta, float* base, int attr, float thr, uint32_t* idx,
+                        uint8_t* vals) {
+    int lo, hi, f32;
+    if (!group_floats(attr, &lo, &hi, &f32)) return -1;
+    const int rb = (hi - lo) * (f32 ? 4 : 2);
+    int64_t cnt = 0;
+    for (int64_t g = 0; g < n; ++g) {
+        const float* t = theta + g * ROW;
+        float* b = base + g * ROW;
+        int changed = 0;
+        for (int k = lo; k < hi; ++k)
+            if (fabsf(t[k] - b[k]) > thr) changed = 1;
+        if (!changed) continue;
+        idx[cnt] = (uint32_t)g;
+        uint8_t* r = vals + cnt * rb;
+        for (int k = lo; k < hi; ++k) {
+            if (f32) {
+                memcpy(r + 4 * (k - lo), &t[k], 4);
+            } else {
+                const uint16_t h = or_f32_to_f16(t[k]);
+                memcpy(r + 2 * (k - lo), &h, 2);
+            }
+            b[k] = t[k];
+        }
+        ++cnt;
+    }
+    return cnt;
+}
+
+void or_apply_tensor_delta(int64_t n, float* params, int attr, int64_t m, const uint32_t* idx,
+                           const uint8_t* vals) {
+    int lo, hi, f32;
+    if (!group_floats(attr, &lo, &hi, &f32)) return;
+    const int rb = (hi - lo) * (f32 ? 4 : 2);
+    for (int64_t i = 0; i < m; ++i) {
+        if ((int64_t)idx[i] >= n) continue;
+        float* row = params + (int64_t)idx[i] * ROW;
+        const uint8_t* r = vals + i * rb;
+        for (int k = lo; k < hi; ++k) {
+            if (f32) {
+                memcpy(&row[k], r + 4 * (k - lo), 4);
+            } else {
+                uint16_t h;
+                memcpy(&h, r + 2 * (k - lo), 2);
+                row[k] = or_f16_to_f32(h);
+            }
+        }
+    }
+}
+
+/* Replay of the full 128-byte records of or_delta. */
+void or_apply_delta(int64_t n, float* params, int64_t m, const uint8_t* rec) {
+    for (int64_t i = 0; i < m; ++i) {
+        const uint8_t* r = rec + i * 128;
+        uint32_t g;
+        memcpy(&g, r, 4);
+        if ((int64_t)g >= n) continue;
+        float* row = params + (int64_t)g * ROW;
+        memcpy(row, r + 4, 12);
+        int order[56], o = 0;
+        for (int k = 4; k < 7; ++k) order[o++] = k;
+        for (int k = 8; k < 12; ++k) order[o++] = k;
+        order[o++] = 3;
+        for (int k = 12; k < 60; ++k) order[o++] = k;
+        for (int k = 0; k < 56; ++k) {
+            uint16_t h;
+            memcpy(&h, r + 16 + 2 * k, 2);
+            row[order[k]] = or_f16_to_f32(h);
+        }
+    }
+}
+
+/* ------------------------------------------------------------------------
  * Discrete-state comparison for end-to-end tests.  The alpha cut-off and the
  * termination test are decisions taken by floating point; two evaluations of
  * the same scene (e.g. float64 projections and a float32 producer's) can keep

@@ -510,6 +510,94 @@ def test_delta_against_numpy_definition():
     np.testing.assert_array_equal(nbr[keep], rows_b[keep])
 
 
+GROUP_FLOATS = {"mean": (0, 3), "opacity": (3, 4), "scale": (4, 7), "rotation": (8, 12), "dc": (12, 15),
+                "sh_rest": (15, 60)}
+
+
+def test_f16_decode_matches_numpy_for_every_bit_pattern():
+    bits = np.arange(65536, dtype=np.uint32).astype(np.uint16)
+    ref = bits.view(np.float16).astype(np.float32)
+    got = O.f16_bits_to_f32(bits)
+    nan = np.isnan(ref)
+    assert np.array_equal(np.isnan(got), nan)
+    np.testing.assert_array_equal(got[~nan].view(np.uint32), ref[~nan].view(np.uint32))
+
+
+def _perturbed(n, seed, groups_hit):
+    th = gi.make_scene(n, 3, seed)
+    base = th.copy()
+    rows = gi.planes_to_rows(th).astype(np.float32)
+    rng = np.random.default_rng(seed)
+    hit = {}
+    for name, (lo, hi) in GROUP_FLOATS.items():
+        pick = np.nonzero(rng.random(n) < groups_hit)[0]
+        col = rng.integers(lo, hi, len(pick))
+        rows[pick, col] += rng.choice([2e-3, -5e-3, 9e-4], len(pick)).astype(np.float32)
+        hit[name] = pick
+    return gi.rows_to_planes(rows), base, hit
+
+
+@pytest.mark.parametrize("name", list(GROUP_FLOATS))
+def test_tensor_delta_against_numpy_definition(name):
+    n = 800
+    th, base, _ = _perturbed(n, 31, 0.2)
+    attr = O.ATTR_GROUPS[name]
+    lo, hi = GROUP_FLOATS[name]
+    idx, vals, nb = O.tensor_delta(th, base, attr, 1e-3)
+    rt = gi.planes_to_rows(th).astype(np.float32)
+    rb = gi.planes_to_rows(base).astype(np.float32)
+    expect = np.nonzero((np.abs(rt[:, lo:hi] - rb[:, lo:hi]) > np.float32(1e-3)).any(axis=1))[0]
+    np.testing.assert_array_equal(idx, expect)
+    assert vals.shape[1] == (hi - lo) * (4 if name == "mean" else 2)
+    if name == "mean":
+        np.testing.assert_array_equal(vals.view(np.float32).reshape(-1, 3), rt[expect, lo:hi])
+    else:
+        np.testing.assert_array_equal(vals.view(np.float16).reshape(-1, hi - lo), rt[expect, lo:hi].astype(np.float16))
+    nbr = gi.planes_to_rows(nb)
+    # only the group's floats of the sent Gaussians move to theta
+    want = rb.copy()
+    want[np.ix_(expect, np.arange(lo, hi))] = rt[np.ix_(expect, np.arange(lo, hi))]
+    np.testing.assert_array_equal(nbr, want)
+
+
+def test_tensor_deltas_replay_on_the_client():
+    """Client replay of every group's delta reproduces the server's values
+    within the record encoding (float32 mean, float16 others); Gaussians that
+    were not sent keep the client's values."""
+    n = 600
+    th, base, _ = _perturbed(n, 37, 0.3)
+    client = base.copy()
+    rt = gi.planes_to_rows(th).astype(np.float32)
+    for name, attr in O.ATTR_GROUPS.items():
+        idx, vals, base = O.tensor_delta(th, base, attr, 1e-3)
+        client = O.apply_tensor_delta(client, attr, idx, vals)
+        lo, hi = GROUP_FLOATS[name]
+        cr = gi.planes_to_rows(client)
+        enc = rt[idx, lo:hi] if name == "mean" else rt[idx, lo:hi].astype(np.float16).astype(np.float32)
+        np.testing.assert_array_equal(cr[idx, lo:hi], enc)
+    # every float of the client is within the threshold or the float16 step of the server
+    cr = gi.planes_to_rows(client)
+    err = np.abs(cr - rt)
+    tol = np.float32(1e-3) + np.abs(rt) * np.float32(2.0 ** -11)
+    assert np.all(err[:, :7] <= tol[:, :7]) and np.all(err[:, 8:] <= tol[:, 8:])
+
+
+def test_full_record_replay_matches_record_fields():
+    n = 400
+    th, base, _ = _perturbed(n, 41, 0.25)
+    idx, rec, _ = O.delta(th, base, 1e-3)
+    client = O.apply_delta(base.copy(), rec)
+    rt = gi.planes_to_rows(th).astype(np.float32)
+    rb = gi.planes_to_rows(base).astype(np.float32)
+    cr = gi.planes_to_rows(client)
+    np.testing.assert_array_equal(cr[idx, :3], rt[idx, :3])
+    cols = [3, 4, 5, 6] + list(range(8, 60))
+    np.testing.assert_array_equal(cr[np.ix_(idx, cols)], rt[np.ix_(idx, cols)].astype(np.float16).astype(np.float32))
+    keep = np.setdiff1d(np.arange(n), idx)
+    np.testing.assert_array_equal(cr[keep], rb[keep])
+    np.testing.assert_array_equal(cr[:, 7], rb[:, 7])
+
+
 def test_decision_flips_finds_a_planted_threshold_crossing():
     sc = gi.make_scene(200, 0, 9)
     sc[1, :, :3] += 1.0
