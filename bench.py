@@ -392,6 +392,7 @@ def run_ours(args, rank, world, local_rank):
     tr.raise_status()
     tctx.raise_status()
 
+    snapshot = params.clone()  # the model before the timed steps (tensor-delta measurement)
     # ---- timed region: K steps, device time of each step by CUDA events
     ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
@@ -458,6 +459,10 @@ def run_ours(args, rank, world, local_rank):
                 "unit": dk["unit"], "frac": dk["frac"],
                 "traffic": measured_traffic(args.workload, SINGLE_KERNEL_PHASES[dom]),
                 "peak_source": peak_src if dk["bound"] == "hbm" else "derived: 148 SMs x 128 FP32 lanes x 2 x 2032 MHz"}
+
+    # ---- tensor deltas per attribute group since the start of the timed steps
+    tensor_deltas = measure_tensor_deltas(gs, torch, params, snapshot, _peaks()[0]) if args.tensor_deltas else None
+    del snapshot
 
     # ---- end to end through the public API: host targets in, loss + delta out
     host_targets = None
@@ -533,6 +538,7 @@ def run_ours(args, rank, world, local_rank):
                "roofline": roofline, "cpu_baseline": cpu, "clocks": clk, "e2e": e2e,
                "plain_step": plain, "serving": serving,
                "gpu_launches": gpu_launches_per_step(args.binning, tile_passes) * args.steps,
+               "tensor_deltas": tensor_deltas,
                "phases_ms": phase_avg, "kernels": kernels, "loss_last": loss_last, "delta_changed_last": changed,
                "wall_s_timed_loop": wall}
         print(json.dumps(out), flush=True)
@@ -589,6 +595,50 @@ def run_serving(args, local_rank, rank):
     return res
 
 
+TENSOR_GROUPS = (("mean", 0, 3, 4), ("opacity", 3, 4, 2), ("scale", 4, 7, 2), ("rotation", 8, 12, 2),
+                 ("dc", 12, 15, 2), ("sh_rest", 15, 60, 2))
+
+
+def measure_tensor_deltas(gs, torch, params, snapshot, hbm_peak, reps=5):
+    """Per attribute group: extraction of the changes since `snapshot` and
+    their client-side replay, timed with CUDA events (outside the timed
+    steps).  Algorithmic bytes: the group's planes of theta and baseline read
+    (16 B per plane per Gaussian each), index + record written and the
+    baseline planes rewritten per sent Gaussian; replay reads index + record
+    and rewrites the group's planes per sent Gaussian."""
+    n = params.shape[1]
+    ctx = gs.Context(params.device.index or 0, 1 << 26)
+    out = {}
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    for name, lo, hi, width in TENSOR_GROUPS:
+        planes = (hi - 1) // 4 - lo // 4 + 1
+        rb = (hi - lo) * width
+        base = snapshot.clone()
+        idx, vals, cnt = gs.gs_extract_tensor_delta(ctx, params, base, name)
+        torch.cuda.synchronize()
+        m = int(cnt.item())
+        ms_x = ms_a = 0.0
+        client = snapshot.clone()
+        for _ in range(reps):
+            base.copy_(snapshot)
+            ev[0].record()
+            gs.gs_extract_tensor_delta(ctx, params, base, name, d_idx=idx, d_vals=vals, d_count=cnt)
+            ev[1].record()
+            gs.gs_apply_tensor_delta(ctx, client, name, idx, vals, cnt)
+            ev[2].record()
+            ev[2].synchronize()
+            ms_x += ev[0].elapsed_time(ev[1]) / reps
+            ms_a += ev[1].elapsed_time(ev[2]) / reps
+        bx = n * planes * 32 + m * (4 + rb + planes * 16)
+        ba = m * (4 + rb + planes * 32)
+        out[name] = {"sent": m, "record_bytes": rb, "extract_ms": ms_x, "apply_ms": ms_a,
+                     "extract_frac_hbm": bx / (ms_x / 1e3) / 1e9 / hbm_peak,
+                     "apply_frac_hbm": ba / (ms_a / 1e3) / 1e9 / hbm_peak if ms_a > 0 else None}
+    ctx.raise_status()
+    ctx.close()
+    return out
+
+
 def run_e2e(args, host_targets, params, sh, cams, keys_cap, make_ctx, dyn, world):
     """The same metric through the public API with host buffers: every step
     uploads its targets from pinned host memory and returns its loss, delta
@@ -639,6 +689,8 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=240)
     ap.add_argument("--serve-load", type=float, default=0.5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tensor-deltas", action=argparse.BooleanOptionalAction, default=True,
+                    help="time per-attribute tensor-delta extraction and replay after the timed steps")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 

@@ -288,6 +288,44 @@ gs_status_t gs_extract_delta(gs_ctx* ctx, const float* theta, float* baseline, i
                              float thr, uint32_t* d_idx, uint8_t* d_records,
                              uint32_t* d_count, void* stream);
 
+/* Attribute groups of a Gaussian's 60 stored floats, for tensor deltas
+ * (Sec. 3.5: tensor-delta packets per attribute, each tensor on its own
+ * schedule; opacity and DC every frame, the others less often).  Flat float
+ * indices and record encoding per group: */
+#define GS_ATTR_MEAN 1      /* floats 0..2, float32 (12-byte record) */
+#define GS_ATTR_OPACITY 2   /* float 3 (logit), float16 (2 B) */
+#define GS_ATTR_SCALE 4     /* floats 4..6 (log-scale), float16 (6 B) */
+#define GS_ATTR_ROTATION 8  /* floats 8..11 (quaternion), float16 (8 B) */
+#define GS_ATTR_DC 16       /* floats 12..14 (SH degree 0), float16 (6 B) */
+#define GS_ATTR_SH_REST 32  /* floats 15..59 (SH degrees 1-3), float16 (90 B) */
+
+/* Record size in bytes of one group's tensor delta; -1 if `attr` is not one
+ * GS_ATTR_* value. */
+int32_t gs_tensor_record_bytes(int32_t attr);
+
+/* Tensor delta of one attribute group.  Gaussian i is sent when max over the
+ * group's floats of |theta - baseline| > thr (float32 compare).  Outputs, in
+ * ascending index order: d_idx uint32[M], d_vals M records of
+ * gs_tensor_record_bytes(attr) bytes packed densely (the group's floats in
+ * flat order, float32 for GS_ATTR_MEAN, float16 round-to-nearest-even
+ * otherwise), *d_count = M.  The sent Gaussians' group floats in `baseline`
+ * take theta's values; its other floats are untouched.  Buffers hold n
+ * entries.  Workspace as gs_extract_delta.  GS_ERR_ARG for a bad attr. */
+gs_status_t gs_extract_tensor_delta(gs_ctx* ctx, const float* theta, float* baseline, int64_t n, int32_t attr,
+                                    float thr, uint32_t* d_idx, void* d_vals, uint32_t* d_count, void* stream);
+/* Client-side replay of a tensor delta into `params` (planes [15][n][4]):
+ * the first *d_count records' decoded values replace the group's floats of
+ * Gaussian d_idx[i].  Indices >= n are skipped and recorded as GS_ERR_ARG in
+ * the status word.  No workspace. */
+gs_status_t gs_apply_tensor_delta(gs_ctx* ctx, float* params, int64_t n, int32_t attr, const uint32_t* d_idx,
+                                  const void* d_vals, const uint32_t* d_count, void* stream);
+/* Client-side replay of gs_extract_delta's 128-byte records: mean exactly,
+ * log-scale, quaternion, opacity logit and SH decoded from float16; the pad
+ * float is untouched.  Indices >= n are skipped (GS_ERR_ARG in the status
+ * word). */
+gs_status_t gs_apply_delta(gs_ctx* ctx, float* params, int64_t n, const uint8_t* d_records,
+                           const uint32_t* d_count, void* stream);
+
 /* Largest n accepted by gs_extract_delta_noalloc. */
 #define GS_NOALLOC_MAX_GAUSSIANS 4194304
 

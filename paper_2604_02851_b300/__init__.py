@@ -314,6 +314,50 @@ def gs_extract_delta(ctx, theta, baseline, thr=1e-3, d_idx=None, d_records=None,
     return d_idx, d_records, d_count
 
 
+# attribute groups of tensor deltas (GS_ATTR_* in include/gs.h)
+ATTR = {"mean": 1, "opacity": 2, "scale": 4, "rotation": 8, "dc": 16, "sh_rest": 32}
+
+
+def tensor_record_bytes(attr) -> int:
+    a = ATTR[attr] if isinstance(attr, str) else int(attr)
+    return int(_lib.lib().gs_tensor_record_bytes(a))
+
+
+def gs_extract_tensor_delta(ctx, theta, baseline, attr, thr=1e-3, d_idx=None, d_vals=None, d_count=None,
+                            stream=None):
+    """-> (d_idx, d_vals, d_count): the group's changed Gaussians (GS_ATTR_*)."""
+    torch = _torch()
+    a = ATTR[attr] if isinstance(attr, str) else int(attr)
+    n = theta.shape[1]
+    rb = tensor_record_bytes(a)
+    if rb < 0:
+        check("gs_extract_tensor_delta", _lib.GS_ERR_ARG)  # not one GS_ATTR_* group
+    dev = theta.device
+    if d_idx is None:
+        d_idx = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
+    if d_vals is None:
+        d_vals = torch.empty((max(n, 1), rb), dtype=torch.uint8, device=dev)
+    if d_count is None:
+        d_count = torch.zeros(1, dtype=torch.int32, device=dev)
+    check("gs_extract_tensor_delta", _lib.lib().gs_extract_tensor_delta(
+        ctx.ptr, _ptr(theta), _ptr(baseline), n, a, float(thr), _ptr(d_idx), _ptr(d_vals), _ptr(d_count),
+        _stream(stream)))
+    return d_idx, d_vals, d_count
+
+
+def gs_apply_tensor_delta(ctx, params, attr, d_idx, d_vals, d_count, stream=None):
+    a = ATTR[attr] if isinstance(attr, str) else int(attr)
+    check("gs_apply_tensor_delta", _lib.lib().gs_apply_tensor_delta(
+        ctx.ptr, _ptr(params), params.shape[1], a, _ptr(d_idx), _ptr(d_vals), _ptr(d_count), _stream(stream)))
+    return params
+
+
+def gs_apply_delta(ctx, params, d_records, d_count, stream=None):
+    check("gs_apply_delta", _lib.lib().gs_apply_delta(ctx.ptr, _ptr(params), params.shape[1], _ptr(d_records),
+                                                      _ptr(d_count), _stream(stream)))
+    return params
+
+
 def gs_render_batch(ctx, params, sh_degree, d_cams, n_requests, total_tiles, keys_cap, npix, bg=None,
                     image=None, stream=None, dyn=None):
     torch = _torch()

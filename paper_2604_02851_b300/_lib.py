@@ -23,7 +23,8 @@ EXPORTS = (
     "gs_render_fwd", "gs_loss", "gs_raster_bwd", "gs_project_bwd", "gs_render_bwd",
     "gs_adam_step", "gs_extract_delta", "gs_render_batch", "gs_train_step",
     "gs_train_graph_capture", "gs_graph_launch", "gs_train_step_events",
-    "gs_train_graph_capture_events", "gs_extract_delta_noalloc", "gs_autotune",
+    "gs_train_graph_capture_events", "gs_extract_delta_noalloc", "gs_autotune", "gs_tensor_record_bytes",
+    "gs_extract_tensor_delta", "gs_apply_tensor_delta", "gs_apply_delta",
 )
 
 
@@ -108,11 +109,15 @@ _SIGS = {
     "gs_train_graph_capture_events": [_P, _P, C.POINTER(gs_train_io), C.POINTER(gs_train_cfg), C.POINTER(_P), _P],
     "gs_autotune": [_P, C.POINTER(gs_scene), _P, C.POINTER(gs_camera), _I32, _I64, _I32, C.POINTER(gs_tune_entry),
                     _I32, C.POINTER(_I32), _P],
+    "gs_tensor_record_bytes": [_I32],
+    "gs_extract_tensor_delta": [_P, _P, _P, _I64, _I32, _F, _P, _P, _P, _P],
+    "gs_apply_tensor_delta": [_P, _P, _I64, _I32, _P, _P, _P, _P],
+    "gs_apply_delta": [_P, _P, _I64, _P, _P, _P],
 }
 TRAIN_PHASE_EVENTS = 11
 TRAIN_PHASES = ("project", "depth_sort", "emit", "tile_sort", "render_fwd", "loss", "raster_bwd", "project_bwd",
                 "adam", "delta")
-_RESTYPES = {"gs_workspace_size": C.c_size_t, "gs_total_tiles": C.c_int64}
+_RESTYPES = {"gs_workspace_size": C.c_size_t, "gs_total_tiles": C.c_int64, "gs_tensor_record_bytes": C.c_int32}
 _SIGS["gs_workspace_size"] = [_P, C.POINTER(gs_camera), _I32, _I64, _I64]
 _SIGS["gs_total_tiles"] = [_P, C.POINTER(gs_camera), _I32]
 

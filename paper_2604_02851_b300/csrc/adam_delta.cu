@@ -120,6 +120,132 @@ k_delta_emit(const float4* __restrict__ theta, float4* __restrict__ base, int64_
     for (int i = 0; i < 8; ++i) rec[i] = make_uint4(w[4 * i], w[4 * i + 1], w[4 * i + 2], w[4 * i + 3]);
 }
 
+// ---------------------------------------------------------------- tensor deltas
+// One attribute group of the 60 floats of a Gaussian (flat indices [lo, hi),
+// planes lo/4 .. (hi-1)/4), sent as float32 (mean) or float16 RNE.
+struct Group {
+    int lo, hi, f32;
+};
+
+__device__ __forceinline__ float lane_of(const float4& a, int l) {
+    return l == 0 ? a.x : (l == 1 ? a.y : (l == 2 ? a.z : a.w));
+}
+__device__ __forceinline__ void set_lane(float4& a, int l, float v) {
+    if (l == 0) a.x = v; else if (l == 1) a.y = v; else if (l == 2) a.z = v; else a.w = v;
+}
+
+__global__ void __launch_bounds__(kDeltaThreads)
+k_tdelta_flags(const float4* __restrict__ theta, const float4* __restrict__ base, int64_t n, Group gr, float thr,
+               uint8_t* __restrict__ flags, uint32_t* __restrict__ block_sums) {
+    const int64_t g = (int64_t)blockIdx.x * kDeltaThreads + threadIdx.x;
+    uint32_t changed = 0;
+    if (g < n) {
+        for (int p = gr.lo >> 2; p <= (gr.hi - 1) >> 2; ++p) {
+            const float4 a = theta[p * n + g], b = base[p * n + g];
+#pragma unroll
+            for (int l = 0; l < 4; ++l) {
+                const int f = 4 * p + l;
+                if (f >= gr.lo && f < gr.hi && fabsf(lane_of(a, l) - lane_of(b, l)) > thr) changed = 1u;
+            }
+        }
+        flags[g] = (uint8_t)changed;
+    }
+    const uint32_t cnt = __syncthreads_count(changed);
+    if (threadIdx.x == 0) block_sums[blockIdx.x] = cnt;
+}
+
+__global__ void __launch_bounds__(kDeltaThreads)
+k_tdelta_emit(const float4* __restrict__ theta, float4* __restrict__ base, int64_t n, Group gr,
+              const uint8_t* __restrict__ flags, const uint32_t* __restrict__ block_off,
+              uint32_t* __restrict__ d_idx, uint8_t* __restrict__ d_vals) {
+    const int64_t g = (int64_t)blockIdx.x * kDeltaThreads + threadIdx.x;
+    const bool ch = g < n && flags[g];
+    const uint32_t ballot = __ballot_sync(0xFFFFFFFFu, ch);
+    __shared__ uint32_t s_w[kDeltaThreads / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) s_w[warp] = __popc(ballot);
+    __syncthreads();
+    uint32_t off = block_off[blockIdx.x];
+    for (int w = 0; w < warp; ++w) off += s_w[w];
+    off += __popc(ballot & ((1u << lane) - 1u));
+    if (!ch) return;
+    d_idx[off] = (uint32_t)g;
+    const int rb = (gr.hi - gr.lo) * (gr.f32 ? 4 : 2);
+    uint8_t* rec = d_vals + (size_t)off * rb;
+    for (int p = gr.lo >> 2; p <= (gr.hi - 1) >> 2; ++p) {
+        const float4 a = theta[p * n + g];
+        float4 b = base[p * n + g];
+#pragma unroll
+        for (int l = 0; l < 4; ++l) {
+            const int f = 4 * p + l;
+            if (f < gr.lo || f >= gr.hi) continue;
+            const float v = lane_of(a, l);
+            if (gr.f32) reinterpret_cast<float*>(rec)[f - gr.lo] = v;
+            else reinterpret_cast<__half*>(rec)[f - gr.lo] = __float2half_rn(v);
+            set_lane(b, l, v);
+        }
+        base[p * n + g] = b;
+    }
+}
+
+// Client-side replay: decoded values of the first *d_count records into
+// the params planes; an index >= n records GS_ERR_ARG and is skipped.
+__global__ void __launch_bounds__(256)
+k_apply_tdelta(float4* __restrict__ params, int64_t n, Group gr, const uint32_t* __restrict__ d_idx,
+               const uint8_t* __restrict__ d_vals, const uint32_t* __restrict__ d_count, DevStatus* status) {
+    const int64_t m = *d_count;
+    const int rb = (gr.hi - gr.lo) * (gr.f32 ? 4 : 2);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t g = d_idx[i];
+        if ((int64_t)g >= n) { record_status(status, GS_ERR_ARG, (long long)g); continue; }
+        const uint8_t* rec = d_vals + (size_t)i * rb;
+        for (int p = gr.lo >> 2; p <= (gr.hi - 1) >> 2; ++p) {
+            float4 a = params[p * n + g];
+#pragma unroll
+            for (int l = 0; l < 4; ++l) {
+                const int f = 4 * p + l;
+                if (f < gr.lo || f >= gr.hi) continue;
+                const float v = gr.f32 ? reinterpret_cast<const float*>(rec)[f - gr.lo]
+                                       : __half2float(reinterpret_cast<const __half*>(rec)[f - gr.lo]);
+                set_lane(a, l, v);
+            }
+            params[p * n + g] = a;
+        }
+    }
+}
+
+// Replay of the full 128-byte records (gs_extract_delta's layout).
+__global__ void __launch_bounds__(256)
+k_apply_delta(float4* __restrict__ params, int64_t n, const uint4* __restrict__ recs,
+              const uint32_t* __restrict__ d_count, DevStatus* status) {
+    const int64_t m = *d_count;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t w[32];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const uint4 u = recs[i * 8 + q];
+            w[4 * q] = u.x; w[4 * q + 1] = u.y; w[4 * q + 2] = u.z; w[4 * q + 3] = u.w;
+        }
+        const uint32_t g = w[0];
+        if ((int64_t)g >= n) { record_status(status, GS_ERR_ARG, (long long)g); continue; }
+        float h[56];
+#pragma unroll
+        for (int k = 0; k < 28; ++k) {
+            h[2 * k] = __half2float(__ushort_as_half((unsigned short)(w[4 + k] & 0xFFFFu)));
+            h[2 * k + 1] = __half2float(__ushort_as_half((unsigned short)(w[4 + k] >> 16)));
+        }
+        // h: log-scale (3), quaternion (4), opacity logit (1), SH (48)
+        params[g] = make_float4(__uint_as_float(w[1]), __uint_as_float(w[2]), __uint_as_float(w[3]), h[7]);
+        float4 sc = params[n + g];
+        sc.x = h[0]; sc.y = h[1]; sc.z = h[2];
+        params[n + g] = sc;
+        params[2 * n + g] = make_float4(h[3], h[4], h[5], h[6]);
+#pragma unroll
+        for (int p = 0; p < 12; ++p)
+            params[(3 + p) * n + g] = make_float4(h[8 + 4 * p], h[9 + 4 * p], h[10 + 4 * p], h[11 + 4 * p]);
+    }
+}
+
 // ---------------------------------------------------------------- scan
 __global__ void __launch_bounds__(1024)
 k_scan_sums(uint32_t* sums, int64_t count, uint32_t* d_total, long long cap, DevStatus* status) {
@@ -208,6 +334,52 @@ void launch_delta(const float* theta, float* baseline, int64_t n, float thr, uin
     k_delta_flags<<<(unsigned)nblk, kDeltaThreads, 0, st>>>(th, b, n, thr, flags, sums);
     k_scan_sums<<<1, 1024, 0, st>>>(sums, nblk, d_count, -1, nullptr);
     k_delta_emit<<<(unsigned)nblk, kDeltaThreads, 0, st>>>(th, b, n, flags, sums, d_idx, d_records);
+}
+
+bool attr_group(int attr, int* lo, int* hi, int* f32) {
+    switch (attr) {
+        case GS_ATTR_MEAN: *lo = 0; *hi = 3; *f32 = 1; return true;
+        case GS_ATTR_OPACITY: *lo = 3; *hi = 4; *f32 = 0; return true;
+        case GS_ATTR_SCALE: *lo = 4; *hi = 7; *f32 = 0; return true;
+        case GS_ATTR_ROTATION: *lo = 8; *hi = 12; *f32 = 0; return true;
+        case GS_ATTR_DC: *lo = 12; *hi = 15; *f32 = 0; return true;
+        case GS_ATTR_SH_REST: *lo = 15; *hi = 60; *f32 = 0; return true;
+        default: return false;
+    }
+}
+
+void launch_tensor_delta(const float* theta, float* baseline, int64_t n, int attr, float thr, uint32_t* d_idx,
+                         uint8_t* d_vals, uint32_t* d_count, char* scratch, cudaStream_t st) {
+    Group gr;
+    attr_group(attr, &gr.lo, &gr.hi, &gr.f32);
+    Carver c(scratch);
+    uint8_t* flags = c.take<uint8_t>(n > 0 ? n : 1);
+    const int64_t nblk = (n + kDeltaThreads - 1) / kDeltaThreads;
+    uint32_t* sums = c.take<uint32_t>(nblk + 1);
+    if (n <= 0) {
+        cudaMemsetAsync(d_count, 0, sizeof(uint32_t), st);
+        return;
+    }
+    const float4* th = reinterpret_cast<const float4*>(theta);
+    float4* b = reinterpret_cast<float4*>(baseline);
+    k_tdelta_flags<<<(unsigned)nblk, kDeltaThreads, 0, st>>>(th, b, n, gr, thr, flags, sums);
+    k_scan_sums<<<1, 1024, 0, st>>>(sums, nblk, d_count, -1, nullptr);
+    k_tdelta_emit<<<(unsigned)nblk, kDeltaThreads, 0, st>>>(th, b, n, gr, flags, sums, d_idx, d_vals);
+}
+
+void launch_apply_tensor_delta(float* params, int64_t n, int attr, const uint32_t* d_idx, const uint8_t* d_vals,
+                               const uint32_t* d_count, DevStatus* status, int sm_count, cudaStream_t st) {
+    Group gr;
+    attr_group(attr, &gr.lo, &gr.hi, &gr.f32);
+    k_apply_tdelta<<<(unsigned)(sm_count * 4), 256, 0, st>>>(reinterpret_cast<float4*>(params), n, gr, d_idx, d_vals,
+                                                              d_count, status);
+}
+
+void launch_apply_delta(float* params, int64_t n, const uint8_t* d_records, const uint32_t* d_count,
+                        DevStatus* status, int sm_count, cudaStream_t st) {
+    k_apply_delta<<<(unsigned)(sm_count * 4), 256, 0, st>>>(reinterpret_cast<float4*>(params), n,
+                                                             reinterpret_cast<const uint4*>(d_records), d_count,
+                                                             status);
 }
 
 }  // namespace gs

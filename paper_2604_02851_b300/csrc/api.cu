@@ -346,6 +346,48 @@ gs_status_t gs_extract_delta(gs_ctx* ctx, const float* theta, float* baseline, i
     return launch_check();
 }
 
+int32_t gs_tensor_record_bytes(int32_t attr) {
+    int lo, hi, f32;
+    if (!attr_group(attr, &lo, &hi, &f32)) return -1;
+    return (hi - lo) * (f32 ? 4 : 2);
+}
+
+gs_status_t gs_extract_tensor_delta(gs_ctx* ctx, const float* theta, float* baseline, int64_t n, int32_t attr,
+                                    float thr, uint32_t* d_idx, void* d_vals, uint32_t* d_count, void* stream) {
+    int lo, hi, f32;
+    if (!ctx || n < 0 || !d_count || (n > 0 && (!theta || !baseline || !d_idx || !d_vals)) ||
+        n >= (1LL << 32) || !(thr >= 0.f) || !attr_group(attr, &lo, &hi, &f32))
+        return GS_ERR_ARG;
+    Carver c(ctx->ws);
+    char* ds = c.take<char>(delta_scratch_bytes(n));
+    if (check_ws(ctx, c.off)) return GS_ERR_CAPACITY;
+    DeviceGuard g(ctx->device);
+    launch_tensor_delta(theta, baseline, n, attr, thr, d_idx, static_cast<uint8_t*>(d_vals), d_count, ds,
+                        S(stream));
+    return launch_check();
+}
+
+gs_status_t gs_apply_tensor_delta(gs_ctx* ctx, float* params, int64_t n, int32_t attr, const uint32_t* d_idx,
+                                  const void* d_vals, const uint32_t* d_count, void* stream) {
+    int lo, hi, f32;
+    if (!ctx || n < 0 || !d_count || (n > 0 && (!params || !d_idx || !d_vals)) || !attr_group(attr, &lo, &hi, &f32))
+        return GS_ERR_ARG;
+    if (n == 0) return GS_OK;
+    DeviceGuard g(ctx->device);
+    launch_apply_tensor_delta(params, n, attr, d_idx, static_cast<const uint8_t*>(d_vals), d_count, ctx->d_status,
+                              ctx->sm_count, S(stream));
+    return launch_check();
+}
+
+gs_status_t gs_apply_delta(gs_ctx* ctx, float* params, int64_t n, const uint8_t* d_records,
+                           const uint32_t* d_count, void* stream) {
+    if (!ctx || n < 0 || !d_count || (n > 0 && (!params || !d_records))) return GS_ERR_ARG;
+    if (n == 0) return GS_OK;
+    DeviceGuard g(ctx->device);
+    launch_apply_delta(params, n, d_records, d_count, ctx->d_status, ctx->sm_count, S(stream));
+    return launch_check();
+}
+
 gs_status_t gs_render_batch(gs_ctx* ctx, const gs_scene* scene, const gs_camera* d_cams, int32_t n_requests,
                             int64_t total_tiles, int64_t keys_cap, const float* bg, float* image,
                             void* stream) {

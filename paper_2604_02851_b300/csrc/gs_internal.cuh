@@ -150,6 +150,15 @@ size_t delta_scratch_bytes(int64_t n);
 void launch_delta(const float* theta, float* baseline, int64_t n, float thr, uint32_t* d_idx,
                   uint8_t* d_records, uint32_t* d_count, char* scratch, cudaStream_t st);
 
+// Tensor deltas of one attribute group (GS_ATTR_*) and client-side replay.
+bool attr_group(int attr, int* lo, int* hi, int* f32);
+void launch_tensor_delta(const float* theta, float* baseline, int64_t n, int attr, float thr, uint32_t* d_idx,
+                         uint8_t* d_vals, uint32_t* d_count, char* scratch, cudaStream_t st);
+void launch_apply_tensor_delta(float* params, int64_t n, int attr, const uint32_t* d_idx, const uint8_t* d_vals,
+                               const uint32_t* d_count, DevStatus* status, int sm_count, cudaStream_t st);
+void launch_apply_delta(float* params, int64_t n, const uint8_t* d_records, const uint32_t* d_count,
+                        DevStatus* status, int sm_count, cudaStream_t st);
+
 // Exclusive scan of `count` uint32 block sums in place (one block); the total
 // goes to *d_total; if cap >= 0 and the total exceeds it, GS_ERR_CAPACITY.
 void launch_scan_sums(uint32_t* sums, int64_t count, uint32_t* d_total, long long cap,

@@ -13,7 +13,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def _declared():
     src = open(os.path.join(ROOT, "include", "gs.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"^\s*(?:gs_status_t|size_t|int64_t)\s+(gs_\w+)\s*\(", src, flags=re.M)))
+    return sorted(set(re.findall(r"^\s*(?:gs_status_t|size_t|int64_t|int32_t)\s+(gs_\w+)\s*\(", src, flags=re.M)))
 
 
 def test_header_declarations_are_exported():
