@@ -58,7 +58,7 @@ RASTER_BWD_FLOP_PER_FRAGMENT = 60     # one (pixel, fragment) adjoint evaluation
 FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12  # SMs x FP32 lanes x FMA x max SM clock
 
 
-def phase_model(n, V, K, total_tiles, npix, sum_nc, n_changed, binning, passes, Kc, chunks):
+def phase_model(n, V, K, total_tiles, npix, sum_nc, n_changed, binning, passes, Kc, chunks, n_train=None):
     """Algorithmic bytes (HBM) or FLOPs per launch of each phase.
 
     K fine (tile, Gaussian) entries; two-level binning also moves Kc coarse
@@ -66,6 +66,7 @@ def phase_model(n, V, K, total_tiles, npix, sum_nc, n_changed, binning, passes, 
     per-chunk tile counts (chunks x 64); direct binning moves the K entries
     through `passes` passes."""
     vn = V * n
+    nt = n if n_train is None else n_train  # Gaussians that are trained (the active pool)
     if binning == "two_level":
         emit = vn * (8 + 16) + Kc * 8
         sort = Kc * 16 * passes + 2 * Kc * 8 + K * 4 + total_tiles * 8 + chunks * 64 * 4 * 3
@@ -80,9 +81,9 @@ def phase_model(n, V, K, total_tiles, npix, sum_nc, n_changed, binning, passes, 
         "render_fwd": ("alu", sum_nc * RASTER_FWD_FLOP_PER_FRAGMENT),
         "loss": ("hbm", 3 * npix * 44),
         "raster_bwd": ("alu", sum_nc * RASTER_BWD_FLOP_PER_FRAGMENT),
-        "project_bwd": ("hbm", n * 480 + vn * (48 + 32)),
-        "adam": ("hbm", 60 * n * 4 * 7),
-        "delta": ("hbm", n * (480 + 2) + n_changed * (240 + 240 + 128 + 4)),
+        "project_bwd": ("hbm", nt * 480 + V * nt * (48 + 32)),
+        "adam": ("hbm", 60 * nt * 4 * 7),
+        "delta": ("hbm", nt * (480 + 2) + n_changed * (240 + 240 + 128 + 4)),
     }
 
 
@@ -365,7 +366,13 @@ def run_ours(args, rank, world, local_rank):
         worst = max(e["ms"] for e in entries)
         tuned = {"configs_tried": len(entries), "best_ms": best["ms"], "worst_ms": worst,
                  "timed": "projection + bin/sort + compositing + its adjoint"}
-    tr = OnlineTrainer(params, sh, cams, keys_cap, ctx=ctx, dyn=dyn)
+    frozen = None
+    if args.frozen_frac > 0:
+        # Gaussian freezing: the last part of the model is an inference-only pool
+        na = int(round(n * (1.0 - args.frozen_frac)))
+        frozen = params[:, na:].contiguous()
+        params = params[:, :na].contiguous()
+    tr = OnlineTrainer(params, sh, cams, keys_cap, ctx=ctx, dyn=dyn, frozen=frozen)
     packed = tr.packed
     tctx = gs.Context(local_rank, 0, tile=args.tile, sort_bits=args.sort_bits, sort_items=args.sort_items,
                      binning=args.binning, raster_threads=args.raster_threads)
@@ -426,7 +433,8 @@ def run_ours(args, rank, world, local_rank):
     phase_avg = {name: float(ms / args.steps) for name, ms in zip(gs._lib.TRAIN_PHASES, phase_ms)}
 
     # ---- work counts of the current model, for the roofline (outside the timed region)
-    proj = gs.gs_project(ctx, params, sh, tr.d_cams, V, dyn=dyn)
+    wc_params = params if frozen is None else torch.cat([params, frozen], 1)  # every rendered Gaussian
+    proj = gs.gs_project(ctx, wc_params, sh, tr.d_cams, V, dyn=dyn)
     _, vals, ranges, nk = gs.gs_bin_sort(ctx, proj, tr.d_cams, V, n, tr.total_tiles, keys_cap, want_keys=False)
     _, T, nc = gs.gs_render_fwd(ctx, proj, tr.d_cams, V, n, tr.total_tiles, vals, ranges, tr.npix)
     torch.cuda.synchronize()
@@ -439,7 +447,9 @@ def run_ours(args, rank, world, local_rank):
     chunks = Kc // 256 + n_super
     del proj, vals, ranges, T, nc
     tile_passes = math.ceil(math.ceil(math.log2(max(tr.total_tiles, 2))) / args.sort_bits)
-    model = phase_model(n, V, K, tr.total_tiles, tr.npix, sum_nc, changed, args.binning, tile_passes, Kc, chunks)
+    del wc_params
+    model = phase_model(n, V, K, tr.total_tiles, tr.npix, sum_nc, changed, args.binning, tile_passes, Kc, chunks,
+                        n_train=params.shape[1])
     hbm_peak, peak_src = _peaks()
     kernels = {}
     for name, ms in phase_avg.items():
@@ -531,6 +541,7 @@ def run_ours(args, rank, world, local_rank):
                           if dynamic else None,
                           "sort_digit_bits": args.sort_bits, "sort_items": args.sort_items, "binning": args.binning,
                           "raster_threads_per_row": args.raster_threads, "autotune": tuned,
+                          "frozen_fraction": args.frozen_frac,
                           "graph": True,
                           "l2": "inputs larger than L2 (params 240 MB, keys > 1 GB per step)",
                           "targets": "re-rendered each step by gs_render_batch outside the step's events",
@@ -689,6 +700,8 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=240)
     ap.add_argument("--serve-load", type=float, default=0.5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--frozen-frac", type=float, default=0.0,
+                    help="fraction of the model held in the inference-only (frozen) pool")
     ap.add_argument("--tensor-deltas", action=argparse.BooleanOptionalAction, default=True,
                     help="time per-attribute tensor-delta extraction and replay after the timed steps")
     args = ap.parse_args()

@@ -373,6 +373,7 @@ typedef struct gs_train_io {
     uint8_t* d_delta_records;/* [n][128] */
     uint32_t* d_delta_count; /* 1 uint32 */
     int32_t* d_step;      /* Adam step counter, incremented each step */
+    const float* frozen;  /* [15][n_frozen][4] inference-only pool, or NULL */
 } gs_train_io;
 
 typedef struct gs_train_cfg {
@@ -387,13 +388,20 @@ typedef struct gs_train_cfg {
     float bg[3];
     float delta_thr;
     gs_adam_cfg adam;     /* d_step / step fields are ignored: io.d_step is used */
+    int64_t n_frozen;     /* Gaussians in io.frozen (0: none) */
 } gs_train_cfg;
 
 /* One whole optimisation step over all V reference views (Sec. 3.1: "iterates
  * over ready reference cameras, optionally grouping them as mini batches"):
  * project, bin/sort, composite, loss, backward, Adam, delta extraction.
  * Enqueue-only, no host synchronisation and no allocation: safe to capture
- * into a CUDA graph.  Workspace: gs_workspace_size(ctx, cams, V, n, keys_cap). */
+ * into a CUDA graph.
+ * Gaussian freezing (Sec. 3.3): the n_frozen Gaussians of io.frozen are
+ * rendered with the n active ones (they follow them as indices n ..
+ * n + n_frozen - 1 of the sorted lists, and of the dynamics arrays when the
+ * scene is dynamic) but get no gradient, no Adam update and no delta; only the
+ * active pool needs grads, Adam moments and a baseline.
+ * Workspace: gs_workspace_size(ctx, cams, V, n + n_frozen, keys_cap). */
 gs_status_t gs_train_step(gs_ctx* ctx, const gs_camera* d_cams, const gs_train_io* io,
                           const gs_train_cfg* cfg, void* stream);
 

@@ -390,14 +390,19 @@ def gs_autotune(ctx, params, sh_degree, cams, keys_cap, reps=3, stream=None, dyn
     return best, entries
 
 
-def train_io(params, grads, m, v, baseline, targets, image, d_loss, d_idx, d_records, d_count, d_step):
-    return _lib.gs_train_io(*(t.data_ptr() for t in (params, grads, m, v, baseline, targets, image, d_loss,
-                                                     d_idx, d_records, d_count, d_step)))
+def train_io(params, grads, m, v, baseline, targets, image, d_loss, d_idx, d_records, d_count, d_step, frozen=None):
+    io = _lib.gs_train_io(*(t.data_ptr() for t in (params, grads, m, v, baseline, targets, image, d_loss,
+                                                   d_idx, d_records, d_count, d_step)))
+    if frozen is not None and frozen.shape[1] > 0:
+        io.frozen = frozen.data_ptr()
+    return io
 
 
 def train_cfg(n, sh_degree, n_views, width, height, keys_cap, w_l1=0.8, w_ssim=0.2, bg=(0.0, 0.0, 0.0),
-              delta_thr=1e-3, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, dyn: "Dynamics | None" = None):
+              delta_thr=1e-3, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, dyn: "Dynamics | None" = None,
+              n_frozen: int = 0):
     cfg = _lib.gs_train_cfg()
+    cfg.n_frozen = int(n_frozen)
     if dyn is not None:
         cfg.dyn = C.pointer(dyn.struct)
     cfg.n, cfg.sh_degree, cfg.n_views, cfg.width, cfg.height = n, sh_degree, n_views, width, height

@@ -65,14 +65,15 @@ class gs_train_io(C.Structure):
     _fields_ = [("params", C.c_void_p), ("grads", C.c_void_p), ("adam_m", C.c_void_p),
                 ("adam_v", C.c_void_p), ("baseline", C.c_void_p), ("targets", C.c_void_p),
                 ("image", C.c_void_p), ("d_loss", C.c_void_p), ("d_delta_idx", C.c_void_p),
-                ("d_delta_records", C.c_void_p), ("d_delta_count", C.c_void_p), ("d_step", C.c_void_p)]
+                ("d_delta_records", C.c_void_p), ("d_delta_count", C.c_void_p), ("d_step", C.c_void_p),
+                ("frozen", C.c_void_p)]
 
 
 class gs_train_cfg(C.Structure):
     _fields_ = [("dyn", C.POINTER(gs_dynamics)), ("n", C.c_int64), ("sh_degree", C.c_int32), ("n_views", C.c_int32),
                 ("width", C.c_int32), ("height", C.c_int32), ("keys_cap", C.c_int64),
                 ("w_l1", C.c_float), ("w_ssim", C.c_float), ("bg", C.c_float * 3),
-                ("delta_thr", C.c_float), ("adam", gs_adam_cfg)]
+                ("delta_thr", C.c_float), ("adam", gs_adam_cfg), ("n_frozen", C.c_int64)]
 
 
 assert C.sizeof(gs_camera) == 80

@@ -437,10 +437,12 @@ gs_status_t gs_train_step_events(gs_ctx* ctx, const gs_camera* d_cams, const gs_
         cfg->keys_cap >= (1LL << 32) || (int64_t)cfg->n_views * cfg->n >= (1LL << 32) || !io->params ||
         !io->grads || !io->adam_m || !io->adam_v || !io->baseline || !io->targets || !io->image ||
         !io->d_loss || !io->d_delta_idx || !io->d_delta_records || !io->d_delta_count || !io->d_step ||
-        bad_dyn(cfg->dyn))
+        bad_dyn(cfg->dyn) || cfg->n_frozen < 0 || (cfg->n_frozen > 0 && !io->frozen) ||
+        (int64_t)cfg->n_views * (cfg->n + cfg->n_frozen) >= (1LL << 32))
         return GS_ERR_ARG;
     const int V = cfg->n_views;
-    const int64_t n = cfg->n;
+    const int64_t na = cfg->n;                  // active pool
+    const int64_t n = cfg->n + cfg->n_frozen;   // every rendered Gaussian
     const int B = ctx->tile;
     const int64_t tt = (int64_t)V * ((cfg->width + B - 1) / B) * ((cfg->height + B - 1) / B);
     const int64_t px = (int64_t)V * cfg->width * cfg->height;
@@ -455,7 +457,10 @@ gs_status_t gs_train_step_events(gs_ctx* ctx, const gs_camera* d_cams, const gs_
     mark(ev, 0, st);
     launch_view_table(d_cams, V, B, p.vt, tt, ctx->d_status, st);
     const Dyn dyn = make_dyn(cfg->dyn);
-    launch_project(io->params, n, cfg->sh_degree, dyn, d_cams, p.vt, V, B, p.proj, s.dkv[0], st);
+    launch_project(io->params, na, cfg->sh_degree, dyn, d_cams, p.vt, V, B, p.proj, s.dkv[0], st, 0, n);
+    if (cfg->n_frozen > 0)
+        launch_project(io->frozen, cfg->n_frozen, cfg->sh_degree, dyn, d_cams, p.vt, V, B, p.proj, s.dkv[0], st,
+                       na, n);
     mark(ev, 1, st);
     launch_bin_sort(p.proj, p.vt, V, n, cfg->keys_cap, tt, ctx->binning, ctx->sort_bits, ctx->sort_items, s, true, nullptr,
                     p.vals, p.ranges, p.n_keys, ctx->d_status, ctx->sm_count, st, ev ? mark : nullptr, ev, 2);
@@ -466,16 +471,16 @@ gs_status_t gs_train_step_events(gs_ctx* ctx, const gs_camera* d_cams, const gs_
                 p.loss, st);
     mark(ev, 6, st);
     launch_raster_bwd(p.proj, p.vt, V, n, B, ctx->raster_tpr, p.vals, p.ranges, b, p.T_final, p.n_contrib, p.dimage, p.grad2d, tt,
-                      st);
+                      st, na);
     mark(ev, 7, st);
-    launch_project_bwd(io->params, n, cfg->sh_degree, dyn, d_cams, V, p.proj, p.grad2d, io->grads, 0, st);
+    launch_project_bwd(io->params, na, cfg->sh_degree, dyn, d_cams, V, p.proj, p.grad2d, io->grads, 0, st, n);
     mark(ev, 8, st);
     gs_adam_cfg ac = cfg->adam;
     ac.d_step = io->d_step;
     ac.increment = 1;
-    launch_adam(io->params, io->grads, io->adam_m, io->adam_v, n, ac, st);
+    launch_adam(io->params, io->grads, io->adam_m, io->adam_v, na, ac, st);
     mark(ev, 9, st);
-    launch_delta(io->params, io->baseline, n, cfg->delta_thr, io->d_delta_idx, io->d_delta_records,
+    launch_delta(io->params, io->baseline, na, cfg->delta_thr, io->d_delta_idx, io->d_delta_records,
                  io->d_delta_count, p.delta, st);
     mark(ev, 10, st);
     return launch_check();

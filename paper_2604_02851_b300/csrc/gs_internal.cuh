@@ -81,12 +81,17 @@ inline Dyn make_dyn(const gs_dynamics* d) {
 
 // depth_kv (may be null): packed (float32 depth bits << 32 | record index)
 // per (view, Gaussian), all-ones depth when culled, for the depth sort.
+// Records of Gaussian g of `params` (plane stride n) go to record v*n_out +
+// g_off + g (n_out < 0: n_out = n), so that two pools can share one record
+// array; dynamics arrays are indexed by g_off + g.
 void launch_project(const float* params, int64_t n, int sh_degree, const Dyn& dyn, const gs_camera* d_cams,
-                    const ViewInfo* vt, int V, int tile, float* proj, uint64_t* depth_kv, cudaStream_t st);
+                    const ViewInfo* vt, int V, int tile, float* proj, uint64_t* depth_kv, cudaStream_t st,
+                    int64_t g_off = 0, int64_t n_out = -1);
 
+// Adjoint of the first n records of each view (record stride n_out).
 void launch_project_bwd(const float* params, int64_t n, int sh_degree, const Dyn& dyn, const gs_camera* d_cams,
                         int V, const float* proj, const float* grad2d, float* dparams,
-                        int accumulate, cudaStream_t st);
+                        int accumulate, cudaStream_t st, int64_t n_out = -1);
 
 // Scratch of the bin/sort stage (all device pointers inside the workspace).
 // Sorted items are packed (key << 32 | value).
@@ -129,6 +134,8 @@ void launch_bin_sort(const float* proj, const ViewInfo* vt, int V, int64_t n, in
                      int first_event = 0);
 
 // tpr: threads per pixel row of a 16 x 16 tile (2 or 4); 8 x 8 tiles use 4.
+// Adjoint: Gaussians with index >= n_active (a frozen pool appended after the
+// active one) get no 2D gradient (n_active < 0: all of them do).
 void launch_render_fwd(const float* proj, const ViewInfo* vt, int V, int64_t n, int tile, int tpr,
                        const uint32_t* vals, const uint32_t* ranges, float3 bg, float* image,
                        float* T_final, uint32_t* n_contrib, int64_t total_tiles,
@@ -137,7 +144,7 @@ void launch_render_fwd(const float* proj, const ViewInfo* vt, int V, int64_t n, 
 void launch_raster_bwd(const float* proj, const ViewInfo* vt, int V, int64_t n, int tile, int tpr,
                        const uint32_t* vals, const uint32_t* ranges, float3 bg,
                        const float* T_final, const uint32_t* n_contrib, const float* dimage,
-                       float* grad2d, int64_t total_tiles, cudaStream_t st);
+                       float* grad2d, int64_t total_tiles, cudaStream_t st, int64_t n_active = -1);
 
 size_t loss_scratch_bytes(int V, int H, int W);
 void launch_loss(const float* image, const float* target, int V, int H, int W, float w_l1,

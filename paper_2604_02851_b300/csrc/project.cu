@@ -271,16 +271,16 @@ __device__ __forceinline__ void tile_rect(float u, float v, float r, int TX, int
 
 template <int D>
 __global__ void __launch_bounds__(256)
-k_project(const float4* __restrict__ P, int64_t n, Dyn dyn, const gs_camera* __restrict__ cams,
-          const ViewInfo* __restrict__ vt, int V, int tile, float4* __restrict__ proj,
-          uint64_t* __restrict__ dkv) {
+k_project(const float4* __restrict__ P, int64_t n, int64_t g_off, int64_t n_out, Dyn dyn,
+          const gs_camera* __restrict__ cams, const ViewInfo* __restrict__ vt, int V, int tile,
+          float4* __restrict__ proj, uint64_t* __restrict__ dkv) {
     const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= n) return;
     constexpr int NB = (D + 1) * (D + 1);
     constexpr int NPL = (3 * NB + 3) / 4;
     Gauss G;
     load_gauss(P, n, g, G);
-    apply_dyn(dyn, g, G);
+    apply_dyn(dyn, g_off + g, G);
     float sh[NPL * 4];
 #pragma unroll
     for (int pl = 0; pl < NPL; ++pl) {
@@ -290,7 +290,7 @@ k_project(const float4* __restrict__ P, int64_t n, Dyn dyn, const gs_camera* __r
     sh[0] *= G.L; sh[1] *= G.L; sh[2] *= G.L;
     for (int v = 0; v < V; ++v) {
         const Cam C = load_cam(cams + v);
-        const int64_t rec = (int64_t)v * n + g;
+        const int64_t rec = (int64_t)v * n_out + g_off + g;
         float4* out = proj + rec * 4;
         ViewGeom Vg;
         bool ok = view_geom(G, C, Vg);
@@ -340,7 +340,8 @@ k_project(const float4* __restrict__ P, int64_t n, Dyn dyn, const gs_camera* __r
 // ------------------------------------------------------------------ adjoint
 template <int D>
 __global__ void __launch_bounds__(128, 4)
-k_project_bwd(const float4* __restrict__ P, int64_t n, Dyn dyn, const gs_camera* __restrict__ cams, int V,
+k_project_bwd(const float4* __restrict__ P, int64_t n, int64_t n_out, Dyn dyn, const gs_camera* __restrict__ cams,
+              int V,
               const float4* __restrict__ proj, const float4* __restrict__ g2d,
               float4* __restrict__ dP, int accumulate) {
     const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -358,7 +359,7 @@ k_project_bwd(const float4* __restrict__ P, int64_t n, Dyn dyn, const gs_camera*
     float dmx = 0.f, dmy = 0.f, dmz = 0.f, dlogit = 0.f;
     float D00 = 0.f, D01 = 0.f, D02 = 0.f, D11 = 0.f, D12 = 0.f, D22 = 0.f;  // dSigma + dSigma^T
     for (int v = 0; v < V; ++v) {
-        const int64_t rec = (int64_t)v * n + g;
+        const int64_t rec = (int64_t)v * n_out + g;
         const float4 pr3 = proj[rec * 4 + 3];
         if (__float_as_uint(pr3.z) == 0u) continue;  // culled in this view
         const float4 ga = g2d[rec * 3], gb = g2d[rec * 3 + 1], gc = g2d[rec * 3 + 2];
@@ -569,24 +570,27 @@ void launch_view_table(const gs_camera* d_cams, int V, int tile, ViewInfo* vt, l
 }
 
 void launch_project(const float* params, int64_t n, int sh_degree, const Dyn& dyn, const gs_camera* d_cams,
-                    const ViewInfo* vt, int V, int tile, float* proj, uint64_t* depth_kv, cudaStream_t st) {
+                    const ViewInfo* vt, int V, int tile, float* proj, uint64_t* depth_kv, cudaStream_t st,
+                    int64_t g_off, int64_t n_out) {
     if (n <= 0) return;
+    if (n_out < 0) n_out = n;
     const int threads = 256;
     const unsigned blocks = (unsigned)((n + threads - 1) / threads);
     const float4* P = reinterpret_cast<const float4*>(params);
     float4* out = reinterpret_cast<float4*>(proj);
     switch (sh_degree) {
-        case 0: k_project<0><<<blocks, threads, 0, st>>>(P, n, dyn, d_cams, vt, V, tile, out, depth_kv); break;
-        case 1: k_project<1><<<blocks, threads, 0, st>>>(P, n, dyn, d_cams, vt, V, tile, out, depth_kv); break;
-        case 2: k_project<2><<<blocks, threads, 0, st>>>(P, n, dyn, d_cams, vt, V, tile, out, depth_kv); break;
-        default: k_project<3><<<blocks, threads, 0, st>>>(P, n, dyn, d_cams, vt, V, tile, out, depth_kv); break;
+        case 0: k_project<0><<<blocks, threads, 0, st>>>(P, n, g_off, n_out, dyn, d_cams, vt, V, tile, out, depth_kv); break;
+        case 1: k_project<1><<<blocks, threads, 0, st>>>(P, n, g_off, n_out, dyn, d_cams, vt, V, tile, out, depth_kv); break;
+        case 2: k_project<2><<<blocks, threads, 0, st>>>(P, n, g_off, n_out, dyn, d_cams, vt, V, tile, out, depth_kv); break;
+        default: k_project<3><<<blocks, threads, 0, st>>>(P, n, g_off, n_out, dyn, d_cams, vt, V, tile, out, depth_kv); break;
     }
 }
 
 void launch_project_bwd(const float* params, int64_t n, int sh_degree, const Dyn& dyn, const gs_camera* d_cams,
                         int V, const float* proj, const float* grad2d, float* dparams, int accumulate,
-                        cudaStream_t st) {
+                        cudaStream_t st, int64_t n_out) {
     if (n <= 0) return;
+    if (n_out < 0) n_out = n;
     const int threads = 128;
     const unsigned blocks = (unsigned)((n + threads - 1) / threads);
     const float4* P = reinterpret_cast<const float4*>(params);
@@ -594,10 +598,10 @@ void launch_project_bwd(const float* params, int64_t n, int sh_degree, const Dyn
     const float4* g2 = reinterpret_cast<const float4*>(grad2d);
     float4* dP = reinterpret_cast<float4*>(dparams);
     switch (sh_degree) {
-        case 0: k_project_bwd<0><<<blocks, threads, 0, st>>>(P, n, dyn, d_cams, V, pr, g2, dP, accumulate); break;
-        case 1: k_project_bwd<1><<<blocks, threads, 0, st>>>(P, n, dyn, d_cams, V, pr, g2, dP, accumulate); break;
-        case 2: k_project_bwd<2><<<blocks, threads, 0, st>>>(P, n, dyn, d_cams, V, pr, g2, dP, accumulate); break;
-        default: k_project_bwd<3><<<blocks, threads, 0, st>>>(P, n, dyn, d_cams, V, pr, g2, dP, accumulate); break;
+        case 0: k_project_bwd<0><<<blocks, threads, 0, st>>>(P, n, n_out, dyn, d_cams, V, pr, g2, dP, accumulate); break;
+        case 1: k_project_bwd<1><<<blocks, threads, 0, st>>>(P, n, n_out, dyn, d_cams, V, pr, g2, dP, accumulate); break;
+        case 2: k_project_bwd<2><<<blocks, threads, 0, st>>>(P, n, n_out, dyn, d_cams, V, pr, g2, dP, accumulate); break;
+        default: k_project_bwd<3><<<blocks, threads, 0, st>>>(P, n, n_out, dyn, d_cams, V, pr, g2, dP, accumulate); break;
     }
 }
 

@@ -193,7 +193,7 @@ __global__ void __launch_bounds__(B * TPR)
 k_raster_bwd(const float4* __restrict__ proj, const ViewInfo* __restrict__ vt, int V, int64_t n,
              const uint32_t* __restrict__ vals, const uint2* __restrict__ ranges, float3 bg,
              const float* __restrict__ T_final, const uint32_t* __restrict__ n_contrib,
-             const float* __restrict__ dimage, float* __restrict__ grad2d) {
+             const float* __restrict__ dimage, float* __restrict__ grad2d, int64_t n_active) {
     constexpr int NT = B * TPR;
     constexpr int PX = B / TPR;
     static_assert(NT % 32 == 0, "whole warps");
@@ -299,7 +299,9 @@ k_raster_bwd(const float4* __restrict__ proj, const ViewInfo* __restrict__ vt, i
                 s1 += t;
                 s2 += t * dx;
             }
-            if (__any_sync(0xFFFFFFFFu, contrib)) {
+            // frozen Gaussians (index >= n_active) take part in the
+            // recursion but need no gradient
+            if (s_g[j] < n_active && __any_sync(0xFFFFFFFFu, contrib)) {
                 // lane 4q ends with sum q of (S1, S2, S3, S4, S5, g5, g6, g7)
                 const float vals8[8] = {s1, s0 * dy, s2, s1 * dy, s0 * dy * dy, g5, g6, g7};
                 const float mine = warp_sum8(vals8, lane);
@@ -363,18 +365,19 @@ void launch_render_fwd(const float* proj, const ViewInfo* vt, int V, int64_t n, 
 void launch_raster_bwd(const float* proj, const ViewInfo* vt, int V, int64_t n, int tile, int tpr,
                        const uint32_t* vals, const uint32_t* ranges, float3 bg, const float* T_final,
                        const uint32_t* n_contrib, const float* dimage, float* grad2d,
-                       int64_t total_tiles, cudaStream_t st) {
+                       int64_t total_tiles, cudaStream_t st, int64_t n_active) {
+    if (n_active < 0) n_active = n;
     cudaMemsetAsync(grad2d, 0, sizeof(float) * kGradStride * (size_t)V * (size_t)n, st);
     if (total_tiles <= 0) return;
     const float4* p = reinterpret_cast<const float4*>(proj);
     const uint2* r = reinterpret_cast<const uint2*>(ranges);
     const unsigned nb = (unsigned)total_tiles;
     if (tile == 8)
-        k_raster_bwd<8, 4><<<nb, 32, 0, st>>>(p, vt, V, n, vals, r, bg, T_final, n_contrib, dimage, grad2d);
+        k_raster_bwd<8, 4><<<nb, 32, 0, st>>>(p, vt, V, n, vals, r, bg, T_final, n_contrib, dimage, grad2d, n_active);
     else if (tpr == 2)
-        k_raster_bwd<16, 2><<<nb, 32, 0, st>>>(p, vt, V, n, vals, r, bg, T_final, n_contrib, dimage, grad2d);
+        k_raster_bwd<16, 2><<<nb, 32, 0, st>>>(p, vt, V, n, vals, r, bg, T_final, n_contrib, dimage, grad2d, n_active);
     else
-        k_raster_bwd<16, 4><<<nb, 64, 0, st>>>(p, vt, V, n, vals, r, bg, T_final, n_contrib, dimage, grad2d);
+        k_raster_bwd<16, 4><<<nb, 64, 0, st>>>(p, vt, V, n, vals, r, bg, T_final, n_contrib, dimage, grad2d, n_active);
 }
 
 }  // namespace gs

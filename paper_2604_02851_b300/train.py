@@ -26,10 +26,13 @@ from . import (Context, RECORD_BYTES, GRAD2D_STRIDE, PROJ_STRIDE, _lib, _ptr, _s
 class OnlineTrainer:
     def __init__(self, params, sh_degree: int, cams: dict, keys_cap: int, lr=1e-3, w_l1=0.8, w_ssim=0.2,
                  delta_thr=1e-3, bg=(0.0, 0.0, 0.0), tile=16, sort_bits=8, ctx: Context | None = None,
-                 dyn=None, share: "OnlineTrainer | None" = None):
+                 dyn=None, share: "OnlineTrainer | None" = None, frozen=None):
         """share: another trainer of the same model whose gradient, Adam
         moments, delta baseline and step counter this one uses (a second
-        graph slot with its own targets, image and delta outputs)."""
+        graph slot with its own targets, image and delta outputs).
+        frozen: planes [15][m][4] of an inference-only pool (Sec. 3.3,
+        Gaussian freezing): rendered with `params`, never updated; gradients,
+        Adam state and deltas cover `params` only."""
         import torch
         self.torch = torch
         self.params = params
@@ -45,7 +48,9 @@ class OnlineTrainer:
         self.lr, self.w_l1, self.w_ssim, self.delta_thr, self.bg = lr, w_l1, w_ssim, delta_thr, tuple(bg)
         dev = params.device
         self.ctx = ctx or Context(dev.index or 0, 0, tile=tile, sort_bits=sort_bits)
-        self.ctx.reserve(self.ctx.workspace_size(self.packed, n, self.keys_cap))
+        self.frozen = frozen
+        self.n_frozen = 0 if frozen is None else int(frozen.shape[1])
+        self.ctx.reserve(self.ctx.workspace_size(self.packed, n + self.n_frozen, self.keys_cap))
         self.d_cams = cameras_to_device(self.packed, dev)
         self.total_tiles = self.ctx.total_tiles(self.packed)
         self.npix = V * self.W * self.H
@@ -65,10 +70,10 @@ class OnlineTrainer:
         self.d_count = torch.zeros(1, dtype=torch.int32, device=dev)
         self.d_step = share.d_step if share is not None else torch.ones(1, dtype=torch.int32, device=dev)
         self.io = train_io(params, self.grads, self.m, self.v, self.baseline, self.targets, self.image,
-                           self.d_loss, self.d_idx, self.d_records, self.d_count, self.d_step)
+                           self.d_loss, self.d_idx, self.d_records, self.d_count, self.d_step, frozen=frozen)
         self.dyn = dyn  # kept alive: the step reads its device buffers
         self.cfg = train_cfg(n, sh_degree, V, self.W, self.H, self.keys_cap, w_l1, w_ssim, self.bg, delta_thr, lr,
-                             dyn=dyn)
+                             dyn=dyn, n_frozen=self.n_frozen)
         self._captured = False
         self._events = None
         self._plain = None
@@ -130,6 +135,8 @@ class OnlineTrainer:
 
     def step_plain(self, stream=None) -> float:
         """One view per launch sequence, host read of each view's key count."""
+        if self.n_frozen:
+            raise ValueError("the plain step has no frozen pool")
         b = self._plain_buffers()
         HW = self.W * self.H
         for v in range(self.V):

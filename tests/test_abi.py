@@ -35,6 +35,9 @@ def test_struct_layouts_match_header():
     assert _lib.gs_dynamics.ambient.offset == 40
     # gs_adam_cfg: 60 lr + 3 floats + step + pointer + 2 ints
     assert _lib.gs_adam_cfg.d_step.offset == 256
+    assert ctypes.sizeof(_lib.gs_train_io) == 104 and _lib.gs_train_io.frozen.offset == 96
+    assert ctypes.sizeof(_lib.gs_train_cfg) == 344 and _lib.gs_train_cfg.n_frozen.offset == 336
+    assert ctypes.sizeof(_lib.gs_tune_entry) == 20
 
 
 def test_missing_library_fails_loudly(monkeypatch):
