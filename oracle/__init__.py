@@ -59,6 +59,10 @@ def lib():
         L.or_adam.argtypes = [C.c_int64, _D, _D, _D, _D, _D, C.c_double, C.c_double, C.c_double, C.c_int]
         L.or_f32_to_f16.argtypes = [C.c_float]
         L.or_f16_to_f32.argtypes = [C.c_uint16]
+        L.or_cell_of.argtypes = [_F, _F, C.c_float, _I32]
+        L.or_cell_of.restype = C.c_int64
+        L.or_depth_mips.argtypes = [_F, C.c_int, C.c_int, _F]
+        L.or_cell_visible.argtypes = [C.c_int, _F, _F, _F, C.c_float, _I32, _U8]
         L.or_f16_to_f32.restype = C.c_float
         L.or_tensor_record_bytes.argtypes = [C.c_int]
         L.or_tensor_delta.argtypes = [C.c_int64, _F, _F, C.c_int, C.c_float, _U32, _U8]
@@ -253,6 +257,44 @@ def delta(theta_planes, base_planes, thr: float = 1e-3):
     rec = np.zeros((max(n, 1), 128), dtype=np.uint8)
     M = int(lib().or_delta(n, th, base, np.float32(thr), idx, rec))
     return idx[:M], rec[:M], rows_to_planes(base)
+
+
+def cell_of(points, origin, size: float, dims):
+    """Cell index of each point (float32 arithmetic, clamped)."""
+    pts = np.ascontiguousarray(points, dtype=np.float32).reshape(-1, 3)
+    o = np.ascontiguousarray(origin, dtype=np.float32)
+    d = np.ascontiguousarray(dims, dtype=np.int32)
+    return np.array([lib().or_cell_of(p, o, np.float32(size), d) for p in pts], dtype=np.int64)
+
+
+def depth_mips(depth):
+    """Max pyramid of one [H][W] buffer: list of levels (float32)."""
+    dpt = np.ascontiguousarray(depth, dtype=np.float32)
+    H, W = dpt.shape
+    tot, w, h, shapes = 0, W, H, []
+    while True:
+        shapes.append((h, w)); tot += w * h
+        if w == 1 and h == 1:
+            break
+        w, h = (w + 1) // 2, (h + 1) // 2
+    out = np.zeros(tot, dtype=np.float32)
+    lib().or_depth_mips(dpt, W, H, out)
+    levels, off = [], 0
+    for h, w in shapes:
+        levels.append(out[off:off + h * w].reshape(h, w)); off += h * w
+    return levels
+
+
+def cell_visible(cams: dict, depths, origin, size: float, dims) -> np.ndarray:
+    """Kept cells (uint8 [nz][ny][nx]) of the preculling test for the views'
+    depth buffers (list of [H][W] float32)."""
+    ca = np.ascontiguousarray(cams_array(cams), dtype=np.float32)
+    dep = np.ascontiguousarray(np.concatenate([np.asarray(d, dtype=np.float32).ravel() for d in depths]))
+    d = np.ascontiguousarray(dims, dtype=np.int32)
+    vis = np.zeros(int(np.prod(dims)), dtype=np.uint8)
+    lib().or_cell_visible(len(cams["fx"]), ca, dep, np.ascontiguousarray(origin, dtype=np.float32),
+                          np.float32(size), d, vis)
+    return vis.reshape(int(dims[2]), int(dims[1]), int(dims[0]))
 
 
 ATTR_GROUPS = {"mean": 1, "opacity": 2, "scale": 4, "rotation": 8, "dc": 16, "sh_rest": 32}

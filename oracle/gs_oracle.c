@@ -970,6 +970,143 @@ void or_apply_delta(int64_t n, float* params, int64_t m, const uint8_t* rec) {
 }
 
 /* ------------------------------------------------------------------------
+ * Preculling (Sec. 3.3): Gaussians belong to cells of a regular 3D grid; each
+ * camera keeps the cells that pass a depth test against its depth buffer;
+ * only Gaussians of kept cells are rendered and optimised.  Reading (the
+ * paper names no test): a conservative hierarchical depth test, evaluated in
+ * float32 with explicit fused multiply-adds so that the decision is the one a
+ * float32 producer takes:
+ *   - the cell of a point is floor((p - origin) / size) per axis, clamped;
+ *   - per view, the cell's 8 corners are moved to camera space
+ *     (z = R[6] x + R[7] y + R[8] z + t[2] as nested fmaf, likewise x, y);
+ *     all corners at z <= near: not seen; some: the whole image at depth
+ *     near; else u = fmaf(fx, x / z, cx), v likewise, and the pixels
+ *     floor(min u) .. floor(max u) by floor(min v) .. floor(max v), clipped
+ *     to the image (empty: not seen), at depth min z;
+ *   - the depth buffer's max pyramid: level 0 is the buffer, level k + 1 of
+ *     size ((w + 1) / 2, (h + 1) / 2) holds the max of each 2x2 block;
+ *   - the level L is the first at which the pixel range spans at most two
+ *     texels per axis; the cell is seen when its depth <= the max over those
+ *     (up to 4) texels.
+ * A cell is kept when some view sees it.
+ * ---------------------------------------------------------------------- */
+int64_t or_cell_of(const float* p, const float* origin, float size, const int* dims) {
+    int c[3];
+    for (int a = 0; a < 3; ++a) {
+        const float d = (p[a] - origin[a]) / size;
+        long long k = (long long)floorf(d);
+        if (k < 0) k = 0;
+        if (k > dims[a] - 1) k = dims[a] - 1;
+        c[a] = (int)k;
+    }
+    return ((int64_t)c[2] * dims[1] + c[1]) * dims[0] + c[0];
+}
+
+/* Max pyramid of one W x H buffer into out (levels back to back, level 0
+ * first); returns the number of levels. */
+int or_depth_mips(const float* depth, int W, int H, float* out) {
+    memcpy(out, depth, sizeof(float) * (size_t)W * H);
+    float* prev = out;
+    int w = W, h = H, levels = 1;
+    float* cur = out + (size_t)W * H;
+    while (w > 1 || h > 1) {
+        const int w2 = (w + 1) / 2, h2 = (h + 1) / 2;
+        for (int j = 0; j < h2; ++j)
+            for (int i = 0; i < w2; ++i) {
+                float m = -INFINITY;
+                for (int dj = 0; dj < 2; ++dj)
+                    for (int di = 0; di < 2; ++di) {
+                        const int y = 2 * j + dj, x = 2 * i + di;
+                        if (y < h && x < w) m = fmaxf(m, prev[(size_t)y * w + x]);
+                    }
+                cur[(size_t)j * w2 + i] = m;
+            }
+        prev = cur;
+        cur += (size_t)w2 * h2;
+        w = w2; h = h2;
+        ++levels;
+    }
+    return levels;
+}
+
+static int mip_count(int W, int H) {
+    int l = 1;
+    while (W > 1 || H > 1) { W = (W + 1) / 2; H = (H + 1) / 2; ++l; }
+    return l;
+}
+
+static size_t mip_floats(int W, int H) {
+    size_t s = 0;
+    for (;;) {
+        s += (size_t)W * H;
+        if (W == 1 && H == 1) break;
+        W = (W + 1) / 2; H = (H + 1) / 2;
+    }
+    return s;
+}
+
+/* cams: float32 camera records [V][20] (oracle layout); depth: the views'
+ * buffers back to back; vis: [nz][ny][nx]. */
+void or_cell_visible(int V, const float* cams, const float* depth, const float* origin, float size,
+                     const int* dims, uint8_t* vis) {
+    const int64_t ncell = (int64_t)dims[0] * dims[1] * dims[2];
+    memset(vis, 0, (size_t)ncell);
+    size_t doff = 0;
+    for (int v = 0; v < V; ++v) {
+        const float* c = cams + (int64_t)v * CAM_STRIDE;
+        const int W = (int)c[16], H = (int)c[17];
+        const float near = c[18];
+        float* mips = (float*)malloc(sizeof(float) * mip_floats(W, H));
+        or_depth_mips(depth + doff, W, H, mips);
+        const int levels = mip_count(W, H);
+        for (int64_t cell = 0; cell < ncell; ++cell) {
+            if (vis[cell]) continue;
+            const int cx = (int)(cell % dims[0]), cy = (int)((cell / dims[0]) % dims[1]),
+                      cz = (int)(cell / ((int64_t)dims[0] * dims[1]));
+            float umin = INFINITY, umax = -INFINITY, vmin = INFINITY, vmax = -INFINITY, zmin = INFINITY;
+            int behind = 0;
+            for (int k = 0; k < 8; ++k) {
+                const float px = fmaf(size, (float)(cx + (k & 1)), origin[0]);
+                const float py = fmaf(size, (float)(cy + ((k >> 1) & 1)), origin[1]);
+                const float pz = fmaf(size, (float)(cz + ((k >> 2) & 1)), origin[2]);
+                const float X = fmaf(c[0], px, fmaf(c[1], py, fmaf(c[2], pz, c[9])));
+                const float Y = fmaf(c[3], px, fmaf(c[4], py, fmaf(c[5], pz, c[10])));
+                const float Z = fmaf(c[6], px, fmaf(c[7], py, fmaf(c[8], pz, c[11])));
+                if (Z <= near) { ++behind; continue; }
+                const float u = fmaf(c[12], X / Z, c[14]), w = fmaf(c[13], Y / Z, c[15]);
+                umin = fminf(umin, u); umax = fmaxf(umax, u);
+                vmin = fminf(vmin, w); vmax = fmaxf(vmax, w);
+                zmin = fminf(zmin, Z);
+            }
+            if (behind == 8) continue;
+            long long x0, x1, y0, y1;
+            if (behind) { x0 = 0; x1 = W - 1; y0 = 0; y1 = H - 1; zmin = near; }
+            else {
+                x0 = (long long)floorf(umin); x1 = (long long)floorf(umax);
+                y0 = (long long)floorf(vmin); y1 = (long long)floorf(vmax);
+                if (x1 < 0 || y1 < 0 || x0 > W - 1 || y0 > H - 1) continue;
+                if (x0 < 0) x0 = 0;
+                if (y0 < 0) y0 = 0;
+                if (x1 > W - 1) x1 = W - 1;
+                if (y1 > H - 1) y1 = H - 1;
+            }
+            int L = 0;
+            while (L < levels - 1 && (((x1 >> L) - (x0 >> L)) > 1 || ((y1 >> L) - (y0 >> L)) > 1)) ++L;
+            /* the level's buffer and width */
+            size_t off = 0;
+            int w = W, h = H;
+            for (int l = 0; l < L; ++l) { off += (size_t)w * h; w = (w + 1) / 2; h = (h + 1) / 2; }
+            float m = -INFINITY;
+            for (long long j = y0 >> L; j <= (y1 >> L); ++j)
+                for (long long i = x0 >> L; i <= (x1 >> L); ++i) m = fmaxf(m, mips[off + (size_t)j * w + i]);
+            if (zmin <= m) vis[cell] = 1;
+        }
+        free(mips);
+        doff += (size_t)W * H;
+    }
+}
+
+/* ------------------------------------------------------------------------
  * Discrete-state comparison for end-to-end tests.  The alpha cut-off and the
  * termination test are decisions taken by floating point; two evaluations of
  * the same scene (e.g. float64 projections and a float32 producer's) can keep

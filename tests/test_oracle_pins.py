@@ -710,3 +710,130 @@ def test_dynamic_gradient_matches_central_differences():
         checked += 1
     assert checked >= 30
     assert max(errs) <= 1e-5, sorted(errs)[-3:]
+
+
+# ---------------------------------------------------------------- preculling
+def _maxpool_levels(a):
+    levels = [a]
+    while a.shape != (1, 1):
+        h, w = a.shape
+        h2, w2 = (h + 1) // 2, (w + 1) // 2
+        p = np.full((2 * h2, 2 * w2), -np.inf, dtype=np.float32)
+        p[:h, :w] = a
+        a = p.reshape(h2, 2, w2, 2).max(axis=(1, 3))
+        levels.append(a)
+    return levels
+
+
+def test_depth_pyramid_is_numpy_max_pooling():
+    rng = np.random.default_rng(5)
+    for H, W in [(1, 1), (3, 5), (17, 30), (64, 64), (45, 80)]:
+        d = rng.random((H, W)).astype(np.float32)
+        got = O.depth_mips(d)
+        ref = _maxpool_levels(d)
+        assert len(got) == len(ref)
+        for g, r in zip(got, ref):
+            np.testing.assert_array_equal(g, r)
+
+
+def test_cell_of_matches_float32_floor_and_clamp():
+    rng = np.random.default_rng(6)
+    pts = rng.uniform(-3, 3, size=(500, 3)).astype(np.float32)
+    origin = np.array([-2.0, -1.5, -2.5], dtype=np.float32)
+    size, dims = np.float32(0.37), np.array([9, 11, 13])
+    c = np.floor((pts - origin) / size).astype(np.int64)
+    c = np.clip(c, 0, dims - 1)
+    ref = (c[:, 2] * dims[1] + c[:, 1]) * dims[0] + c[:, 0]
+    np.testing.assert_array_equal(O.cell_of(pts, origin, size, dims), ref)
+
+
+def _grid_cams():
+    cams = gi.ring_cameras(3, 96, 64, radius=4.0)
+    return gi.subset_cameras(cams, [0, 1, 2])
+
+
+def test_cell_visibility_against_a_constant_wall():
+    """A depth buffer that is a wall at camera depth D everywhere: a cell the
+    view's frustum reaches is kept exactly when its nearest corner lies at or
+    in front of D."""
+    cams = gi.ring_cameras(1, 80, 60, radius=4.0)
+    origin, size, dims = np.array([-2, -2, -2], dtype=np.float32), 0.5, np.array([8, 8, 8])
+    inf = O.cell_visible(cams, [np.full((60, 80), np.inf, np.float32)], origin, size, dims)
+    for D in (3.0, 4.0, 5.5):
+        vis = O.cell_visible(cams, [np.full((60, 80), D, np.float32)], origin, size, dims)
+        # nearest corner depth per cell (camera 0 looks along -z from (0, 0, 4))
+        zs = np.arange(8, dtype=np.float64) * 0.5 - 2.0
+        zmin_axis = 4.0 - (zs + 0.5)            # the cell's corner with the largest world z
+        zmin = np.broadcast_to(zmin_axis[:, None, None], (8, 8, 8))
+        expect = inf.astype(bool) & (zmin <= D + 1e-6)
+        # cells straddling the near plane use depth near; none here (near 0.2)
+        np.testing.assert_array_equal(vis.astype(bool), expect)
+
+
+def test_cell_visibility_is_conservative():
+    """Every cell that an exact test (max of the depth buffer over the cell's
+    full pixel rectangle, in float64) sees is kept; random depth buffers with
+    occluders."""
+    rng = np.random.default_rng(8)
+    cams = _grid_cams()
+    origin, size, dims = np.array([-3, -1.5, -3], dtype=np.float32), 0.6, np.array([10, 5, 10])
+    depths = []
+    for v in range(3):
+        d = np.full((64, 96), np.inf, np.float32)
+        for _ in range(6):
+            y0, x0 = rng.integers(0, 64), rng.integers(0, 96)
+            d[y0:y0 + rng.integers(5, 40), x0:x0 + rng.integers(5, 60)] = rng.uniform(2.0, 6.0)
+        depths.append(d)
+    vis = O.cell_visible(cams, depths, origin, size, dims).astype(bool)
+    exact = np.zeros_like(vis)
+    for v in range(3):
+        R, t = np.asarray(cams["R"][v]), np.asarray(cams["t"][v])
+        fx, fy, cx, cy = (float(cams[k][v]) for k in ("fx", "fy", "cx", "cy"))
+        for cz in range(dims[2]):
+            for cy_ in range(dims[1]):
+                for cx_ in range(dims[0]):
+                    corners = np.array([[cx_ + (k & 1), cy_ + ((k >> 1) & 1), cz + ((k >> 2) & 1)]
+                                        for k in range(8)]) * size + origin
+                    cc = corners @ R.T + t
+                    if np.any(cc[:, 2] <= 0.2):
+                        continue  # near-plane cells are kept conservatively; not tested here
+                    u = fx * cc[:, 0] / cc[:, 2] + cx
+                    w = fy * cc[:, 1] / cc[:, 2] + cy
+                    x0, x1 = int(np.floor(u.min())), int(np.floor(u.max()))
+                    y0, y1 = int(np.floor(w.min())), int(np.floor(w.max()))
+                    if x1 < 0 or y1 < 0 or x0 > 95 or y0 > 63:
+                        continue
+                    x0, y0, x1, y1 = max(x0, 0), max(y0, 0), min(x1, 95), min(y1, 63)
+                    m = depths[v][y0:y1 + 1, x0:x1 + 1].max()
+                    if cc[:, 2].min() * (1 + 1e-5) <= m:
+                        exact[cz, cy_, cx_] = True
+    assert exact.any() and not exact.all()
+    assert np.all(vis[exact])
+    assert vis.sum() < vis.size   # something is culled
+
+
+def test_cell_visibility_keeps_every_cell_a_sampled_point_shows():
+    """No occluders: a cell is kept when any of its 5^3 sample points projects
+    into an image in front of the near plane (the test may keep more)."""
+    cams = _grid_cams()
+    origin, size, dims = np.array([-6, -3, -6], dtype=np.float32), 1.0, np.array([12, 6, 12])
+    depths = [np.full((64, 96), np.inf, np.float32)] * 3
+    vis = O.cell_visible(cams, depths, origin, size, dims).astype(bool)
+    f = np.linspace(0.02, 0.98, 5)
+    off = np.stack(np.meshgrid(f, f, f, indexing="ij"), -1).reshape(-1, 3)
+    for cz in range(dims[2]):
+        for cy_ in range(dims[1]):
+            for cx_ in range(dims[0]):
+                pts = (np.array([cx_, cy_, cz]) + off) * size + origin
+                seen = False
+                for v in range(3):
+                    cc = pts @ np.asarray(cams["R"][v]).T + np.asarray(cams["t"][v])
+                    ok = cc[:, 2] > 0.2
+                    u = cams["fx"][v] * cc[ok, 0] / cc[ok, 2] + cams["cx"][v]
+                    w = cams["fy"][v] * cc[ok, 1] / cc[ok, 2] + cams["cy"][v]
+                    if np.any((u >= 0) & (u < 96) & (w >= 0) & (w < 64)):
+                        seen = True
+                        break
+                if seen:
+                    assert vis[cz, cy_, cx_], (cz, cy_, cx_)
+    assert not vis.all()
