@@ -38,7 +38,11 @@ WORKLOADS = {
     "c1_10k_128": (10_000, 0, 1, 128, 128),
     "prof_200k_8x720p": (200_000, 3, 8, 1280, 720),
     "c5_3M_8x1080p_dynamic": (3_000_000, 3, 8, 1920, 1080),
+    # config 3 plus 3M Gaussians above the scene, outside every view (a large
+    # world of which the cameras see a part; Sec. 3.3 preculling)
+    "c3_far3M_8x720p": (4_000_000, 3, 8, 1280, 720),
 }
+FAR_WORKLOADS = {"c3_far3M_8x720p": 3_000_000}
 DYNAMIC_WORKLOADS = {"c5_3M_8x1080p_dynamic"}
 DEFAULT_WORKLOAD = "c3_1M_8x720p"
 
@@ -335,6 +339,12 @@ def run_ours(args, rank, world, local_rank):
     seed_model, seed_target = replica_seeds(rank)
     planes = gi.make_scene(n, sh, seed_model)
     target_planes = gi.make_scene(n, sh, seed_target)
+    n_far = FAR_WORKLOADS.get(args.workload, 0)
+    if n_far:
+        # the last n_far Gaussians move to y in [3, 9], above the scene: every
+        # view's frustum misses them
+        for pl in (planes, target_planes):
+            pl[0, n - n_far:, 1] = pl[0, n - n_far:, 1] * 3.0 + 6.0
     signs = gi.drift_signs(n)
     cams = gi.ring_cameras(V, W, H)
     params = torch.from_numpy(planes).to(dev)
@@ -372,7 +382,18 @@ def run_ours(args, rank, world, local_rank):
         na = int(round(n * (1.0 - args.frozen_frac)))
         frozen = params[:, na:].contiguous()
         params = params[:, :na].contiguous()
-    tr = OnlineTrainer(params, sh, cams, keys_cap, ctx=ctx, dyn=dyn, frozen=frozen)
+    precull = None
+    if args.precull:
+        # grid over the whole world; kept cells from the views' depth buffers
+        # (empty here: the frustum decides), computed once for the fixed rig
+        precull = gs.Precull((-3.0, -3.0, -3.0), 0.5, (12, 26, 12), device=dev)
+        far = torch.full((V * H * W,), float("inf"), dtype=torch.float32, device=dev)
+        pctx = gs.Context(local_rank, 0)
+        precull.update(pctx, cams, far)
+        torch.cuda.synchronize()
+        pctx.close()
+        del far
+    tr = OnlineTrainer(params, sh, cams, keys_cap, ctx=ctx, dyn=dyn, frozen=frozen, precull=precull)
     packed = tr.packed
     tctx = gs.Context(local_rank, 0, tile=args.tile, sort_bits=args.sort_bits, sort_items=args.sort_items,
                      binning=args.binning, raster_threads=args.raster_threads)
@@ -541,7 +562,8 @@ def run_ours(args, rank, world, local_rank):
                           if dynamic else None,
                           "sort_digit_bits": args.sort_bits, "sort_items": args.sort_items, "binning": args.binning,
                           "raster_threads_per_row": args.raster_threads, "autotune": tuned,
-                          "frozen_fraction": args.frozen_frac,
+                          "frozen_fraction": args.frozen_frac, "precull": bool(args.precull),
+                          "far_gaussians": n_far,
                           "graph": True,
                           "l2": "inputs larger than L2 (params 240 MB, keys > 1 GB per step)",
                           "targets": "re-rendered each step by gs_render_batch outside the step's events",
@@ -700,6 +722,8 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=240)
     ap.add_argument("--serve-load", type=float, default=0.5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--precull", action="store_true",
+                    help="preculling grid (Sec. 3.3): Gaussians outside the views' cells are not processed")
     ap.add_argument("--frozen-frac", type=float, default=0.0,
                     help="fraction of the model held in the inference-only (frozen) pool")
     ap.add_argument("--tensor-deltas", action=argparse.BooleanOptionalAction, default=True,

@@ -95,12 +95,25 @@ typedef struct gs_dynamics {
     float ambient, diffuse;
 } gs_dynamics;
 
+/* Preculling (Sec. 3.3): Gaussians belong to the cells of a regular grid
+ * (cell of a world-space mean p: floor((p - origin) / cell_size) per axis,
+ * float32, clamped to the grid); only Gaussians of kept cells are rendered and
+ * optimised.  cell_visible comes from gs_cell_visibility (or the caller). */
+typedef struct gs_precull {
+    const uint8_t* cell_visible; /* device, [dims[2]][dims[1]][dims[0]], nonzero: kept */
+    float origin[3];             /* world position of the grid's lowest corner */
+    float cell_size;
+    int32_t dims[3];
+    int32_t _pad;
+} gs_precull;
+
 typedef struct gs_scene {
     int64_t n;           /* number of Gaussians, >= 0 */
     int32_t sh_degree;   /* 0..3 */
     int32_t _pad;
     const float* params; /* device, [15][n][4] */
     const gs_dynamics* dyn; /* host pointer; NULL: static scene */
+    const gs_precull* precull; /* host pointer; NULL: every Gaussian takes part */
 } gs_scene;
 
 /* ---------------------------------------------------------------- context */
@@ -166,6 +179,26 @@ typedef struct gs_tune_entry {
 gs_status_t gs_autotune(gs_ctx* ctx, const gs_scene* scene, const gs_camera* d_cams, const gs_camera* host_cams,
                         int32_t n_views, int64_t keys_cap, int32_t reps, gs_tune_entry* results,
                         int32_t max_results, int32_t* n_results, void* stream);
+/* Preculling visibility (Sec. 3.3: "each camera determines a set of visible
+ * cells using depth testing").  d_depth holds each view's depth buffer
+ * (camera-space z of the nearest surface, +inf where empty), views back to
+ * back as [height][width] floats.  A cell is kept (d_cell_visible[c] = 1) when
+ * some view sees it by a conservative hierarchical depth test, evaluated in
+ * float32 with fused multiply-adds:
+ *   - the 8 corners go to camera space (z = R[6]x + R[7]y + R[8]z + t[2] as
+ *     nested FMAs); all at z <= near: not seen; some: the whole image at depth
+ *     near; otherwise u = fx * (x / z) + cx (FMA), v likewise, and the pixel
+ *     range floor(min u)..floor(max u) x floor(min v)..floor(max v), clipped
+ *     (empty: not seen), at depth min z;
+ *   - in the buffer's max pyramid (level k + 1 of size ((w+1)/2, (h+1)/2)
+ *     holds 2x2 maxima), the first level at which the range spans at most 2
+ *     texels per axis; seen when depth <= the max of those texels.
+ * It never drops a cell whose pixels show something at or behind the cell.
+ * Workspace: gs_precull_workspace_size(host_cams, V) bytes. */
+gs_status_t gs_cell_visibility(gs_ctx* ctx, const gs_camera* d_cams, const gs_camera* host_cams, int32_t n_views,
+                               const float* d_depth, const gs_precull* grid, uint8_t* d_cell_visible,
+                               void* stream);
+size_t gs_precull_workspace_size(const gs_camera* host_cams, int32_t n_views);
 /* Reads and clears the device status word (synchronises `stream`).
  * *status receives the first error a kernel recorded since the last read
  * (GS_OK if none); *detail receives the required size for GS_ERR_CAPACITY. */
@@ -389,6 +422,9 @@ typedef struct gs_train_cfg {
     float delta_thr;
     gs_adam_cfg adam;     /* d_step / step fields are ignored: io.d_step is used */
     int64_t n_frozen;     /* Gaussians in io.frozen (0: none) */
+    const gs_precull* precull; /* host pointer; NULL: no preculling.  Gaussians of
+                               culled cells are not rendered and get no Adam
+                               update (their parameters and moments stay) */
 } gs_train_cfg;
 
 /* One whole optimisation step over all V reference views (Sec. 3.1: "iterates

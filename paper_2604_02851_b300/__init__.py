@@ -171,21 +171,52 @@ class Dynamics:
             self.light[:3].copy_(torch.as_tensor(np.asarray(light, dtype=np.float32)))
 
 
-def _scene(params, sh_degree, dyn: "Dynamics | None" = None):
+class Precull:
+    """Preculling grid (gs_precull): cell of a mean p is floor((p - origin) /
+    cell_size) per axis, clamped; `visible` (uint8 [nz][ny][nx] on the
+    device) marks the kept cells, filled by update() (gs_cell_visibility) or by
+    the caller.  The struct holds the buffer's address, so a captured graph
+    sees later updates."""
+
+    def __init__(self, origin, cell_size: float, dims, device="cuda"):
+        torch = _torch()
+        self.dims = tuple(int(d) for d in dims)
+        self.visible = torch.ones(self.dims[::-1], dtype=torch.uint8, device=device)
+        self.struct = _lib.gs_precull(cell_visible=self.visible.data_ptr(), cell_size=float(cell_size))
+        for a in range(3):
+            self.struct.origin[a] = float(origin[a])
+            self.struct.dims[a] = self.dims[a]
+
+    def update(self, ctx, cams, depth, stream=None):
+        """Keep the cells that some view sees (depth: the views' buffers of
+        camera-space z, +inf where empty, back to back)."""
+        packed, host = _host_cams(cams)
+        d_cams = cameras_to_device(packed, depth.device)
+        need = int(_lib.lib().gs_precull_workspace_size(host, len(packed)))
+        ctx.reserve(need)
+        check("gs_cell_visibility", _lib.lib().gs_cell_visibility(
+            ctx.ptr, _ptr(d_cams), host, len(packed), _ptr(depth), C.byref(self.struct), _ptr(self.visible),
+            _stream(stream)))
+        return self.visible
+
+
+def _scene(params, sh_degree, dyn: "Dynamics | None" = None, precull: "Precull | None" = None):
     n = params.shape[1] if params is not None else 0
     sc = _lib.gs_scene(n=n, sh_degree=sh_degree, params=params.data_ptr() if n else None)
     if dyn is not None:
         sc.dyn = C.pointer(dyn.struct)
+    if precull is not None:
+        sc.precull = C.pointer(precull.struct)
     return sc
 
 
 # ------------------------------------------------------------------ entry points
-def gs_project(ctx, params, sh_degree, d_cams, n_views, proj=None, stream=None, dyn=None):
+def gs_project(ctx, params, sh_degree, d_cams, n_views, proj=None, stream=None, dyn=None, precull=None):
     torch = _torch()
     n = params.shape[1]
     if proj is None:
         proj = torch.empty((n_views, n, PROJ_STRIDE), dtype=torch.float32, device=params.device)
-    sc = _scene(params, sh_degree, dyn)
+    sc = _scene(params, sh_degree, dyn, precull)
     check("gs_project", _lib.lib().gs_project(ctx.ptr, C.byref(sc), _ptr(d_cams), n_views, _ptr(proj),
                                               _stream(stream)))
     return proj
@@ -359,11 +390,11 @@ def gs_apply_delta(ctx, params, d_records, d_count, stream=None):
 
 
 def gs_render_batch(ctx, params, sh_degree, d_cams, n_requests, total_tiles, keys_cap, npix, bg=None,
-                    image=None, stream=None, dyn=None):
+                    image=None, stream=None, dyn=None, precull=None):
     torch = _torch()
     if image is None:
         image = torch.empty(3 * npix, dtype=torch.float32, device=params.device)
-    sc = _scene(params, sh_degree, dyn)
+    sc = _scene(params, sh_degree, dyn, precull)
     check("gs_render_batch", _lib.lib().gs_render_batch(ctx.ptr, C.byref(sc), _ptr(d_cams), n_requests,
                                                         total_tiles, keys_cap, _bg(bg), _ptr(image),
                                                         _stream(stream)))
@@ -400,9 +431,11 @@ def train_io(params, grads, m, v, baseline, targets, image, d_loss, d_idx, d_rec
 
 def train_cfg(n, sh_degree, n_views, width, height, keys_cap, w_l1=0.8, w_ssim=0.2, bg=(0.0, 0.0, 0.0),
               delta_thr=1e-3, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, dyn: "Dynamics | None" = None,
-              n_frozen: int = 0):
+              n_frozen: int = 0, precull: "Precull | None" = None):
     cfg = _lib.gs_train_cfg()
     cfg.n_frozen = int(n_frozen)
+    if precull is not None:
+        cfg.precull = C.pointer(precull.struct)
     if dyn is not None:
         cfg.dyn = C.pointer(dyn.struct)
     cfg.n, cfg.sh_degree, cfg.n_views, cfg.width, cfg.height = n, sh_degree, n_views, width, height

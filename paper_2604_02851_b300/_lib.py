@@ -24,7 +24,8 @@ EXPORTS = (
     "gs_adam_step", "gs_extract_delta", "gs_render_batch", "gs_train_step",
     "gs_train_graph_capture", "gs_graph_launch", "gs_train_step_events",
     "gs_train_graph_capture_events", "gs_extract_delta_noalloc", "gs_autotune", "gs_tensor_record_bytes",
-    "gs_extract_tensor_delta", "gs_apply_tensor_delta", "gs_apply_delta",
+    "gs_extract_tensor_delta", "gs_apply_tensor_delta", "gs_apply_delta", "gs_cell_visibility",
+    "gs_precull_workspace_size",
 )
 
 
@@ -45,9 +46,14 @@ class gs_dynamics(C.Structure):
                 ("normals", C.c_void_p), ("light", C.c_void_p), ("ambient", C.c_float), ("diffuse", C.c_float)]
 
 
+class gs_precull(C.Structure):
+    _fields_ = [("cell_visible", C.c_void_p), ("origin", C.c_float * 3), ("cell_size", C.c_float),
+                ("dims", C.c_int32 * 3), ("_pad", C.c_int32)]
+
+
 class gs_scene(C.Structure):
     _fields_ = [("n", C.c_int64), ("sh_degree", C.c_int32), ("_pad", C.c_int32),
-                ("params", C.c_void_p), ("dyn", C.POINTER(gs_dynamics))]
+                ("params", C.c_void_p), ("dyn", C.POINTER(gs_dynamics)), ("precull", C.POINTER(gs_precull))]
 
 
 class gs_tune_entry(C.Structure):
@@ -73,7 +79,8 @@ class gs_train_cfg(C.Structure):
     _fields_ = [("dyn", C.POINTER(gs_dynamics)), ("n", C.c_int64), ("sh_degree", C.c_int32), ("n_views", C.c_int32),
                 ("width", C.c_int32), ("height", C.c_int32), ("keys_cap", C.c_int64),
                 ("w_l1", C.c_float), ("w_ssim", C.c_float), ("bg", C.c_float * 3),
-                ("delta_thr", C.c_float), ("adam", gs_adam_cfg), ("n_frozen", C.c_int64)]
+                ("delta_thr", C.c_float), ("adam", gs_adam_cfg), ("n_frozen", C.c_int64),
+                ("precull", C.POINTER(gs_precull))]
 
 
 assert C.sizeof(gs_camera) == 80
@@ -114,11 +121,14 @@ _SIGS = {
     "gs_extract_tensor_delta": [_P, _P, _P, _I64, _I32, _F, _P, _P, _P, _P],
     "gs_apply_tensor_delta": [_P, _P, _I64, _I32, _P, _P, _P, _P],
     "gs_apply_delta": [_P, _P, _I64, _P, _P, _P],
+    "gs_cell_visibility": [_P, _P, C.POINTER(gs_camera), _I32, _P, C.POINTER(gs_precull), _P, _P],
+    "gs_precull_workspace_size": [C.POINTER(gs_camera), _I32],
 }
 TRAIN_PHASE_EVENTS = 11
 TRAIN_PHASES = ("project", "depth_sort", "emit", "tile_sort", "render_fwd", "loss", "raster_bwd", "project_bwd",
                 "adam", "delta")
-_RESTYPES = {"gs_workspace_size": C.c_size_t, "gs_total_tiles": C.c_int64, "gs_tensor_record_bytes": C.c_int32}
+_RESTYPES = {"gs_workspace_size": C.c_size_t, "gs_total_tiles": C.c_int64, "gs_tensor_record_bytes": C.c_int32,
+             "gs_precull_workspace_size": C.c_size_t}
 _SIGS["gs_workspace_size"] = [_P, C.POINTER(gs_camera), _I32, _I64, _I64]
 _SIGS["gs_total_tiles"] = [_P, C.POINTER(gs_camera), _I32]
 

@@ -24,7 +24,7 @@ struct LrTable { float lr[60]; };
 __global__ void __launch_bounds__(256)
 k_adam(float4* __restrict__ theta, const float4* __restrict__ grad, float4* __restrict__ m,
        float4* __restrict__ v, int64_t n, LrTable lr, float b1, float b2, float eps, int host_step,
-       const int32_t* __restrict__ d_step) {
+       const int32_t* __restrict__ d_step, const uint8_t* __restrict__ fwd) {
     const int step = d_step ? *d_step : host_step;
     const float bc1 = 1.f - powf(b1, (float)step);
     const float bc2 = 1.f - powf(b2, (float)step);
@@ -33,6 +33,7 @@ k_adam(float4* __restrict__ theta, const float4* __restrict__ grad, float4* __re
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
          i += (int64_t)gridDim.x * blockDim.x) {
         const int plane = (int)(i / n);
+        if (fwd && !fwd[i - (int64_t)plane * n]) continue;  // preculled: no update
         const float4 g = grad[i];
         float4 mm = m[i], vv = v[i], th = theta[i];
         const float* l = lr.lr + 4 * plane;
@@ -297,7 +298,7 @@ void launch_scan_sums(uint32_t* sums, int64_t count, uint32_t* d_total, long lon
 }
 
 void launch_adam(float* theta, const float* grad, float* m, float* v, int64_t n, const gs_adam_cfg& cfg,
-                 cudaStream_t st) {
+                 cudaStream_t st, const uint8_t* fwd) {
     if (n > 0) {
         LrTable lr;
         for (int i = 0; i < 60; ++i) lr.lr[i] = cfg.lr[i];
@@ -307,7 +308,7 @@ void launch_adam(float* theta, const float* grad, float* m, float* v, int64_t n,
         k_adam<<<(unsigned)blocks, 256, 0, st>>>(
             reinterpret_cast<float4*>(theta), reinterpret_cast<const float4*>(grad),
             reinterpret_cast<float4*>(m), reinterpret_cast<float4*>(v), n, lr, cfg.beta1, cfg.beta2,
-            cfg.eps, cfg.step, cfg.d_step);
+            cfg.eps, cfg.step, cfg.d_step, fwd);
     }
     if (cfg.d_step && cfg.increment) k_inc_step<<<1, 1, 0, st>>>(const_cast<int32_t*>(cfg.d_step));
 }

@@ -43,6 +43,11 @@ int64_t tiles_of(const gs_camera* cams, int V, int tile) {
 
 bool bad_views(int V) { return V < 1 || V > kMaxViews; }
 
+bool bad_precull(const gs_precull* p) {
+    return p && (!p->cell_visible || !(p->cell_size > 0.f) || p->dims[0] < 1 || p->dims[1] < 1 || p->dims[2] < 1 ||
+                 (int64_t)p->dims[0] * p->dims[1] * p->dims[2] >= (1LL << 40));
+}
+
 bool bad_dyn(const gs_dynamics* d) {
     return d && (d->n_groups < 0 || d->n_groups > 256 || (d->n_groups > 0 && (!d->group || !d->poses)) ||
                  (d->normals && !d->light));
@@ -62,6 +67,7 @@ struct FusedPlan {
     char* loss;
     float* grad2d;
     char* delta;
+    uint8_t* fwd;
     size_t bytes;
 };
 
@@ -82,6 +88,7 @@ FusedPlan plan_fused(void* base, int V, int64_t n, int64_t keys_cap, int64_t tot
         p.loss = c.take<char>(loss_scratch_bytes(V, H, W));
         p.grad2d = c.take<float>((size_t)V * n * kGradStride);
         p.delta = c.take<char>(delta_scratch_bytes(n));
+        p.fwd = c.take<uint8_t>(n > 0 ? n : 1);
     }
     p.bytes = c.off;
     return p;
@@ -222,13 +229,13 @@ gs_status_t gs_project(gs_ctx* ctx, const gs_scene* scene, const gs_camera* d_ca
     if (!ctx || !scene || !d_cams || !proj || bad_views(n_views) || scene->n < 0 ||
         scene->sh_degree < 0 || scene->sh_degree > 3 || (scene->n > 0 && !scene->params))
         return GS_ERR_ARG;
-    if ((int64_t)n_views * scene->n >= (1LL << 32) || bad_dyn(scene->dyn)) return GS_ERR_ARG;
+    if ((int64_t)n_views * scene->n >= (1LL << 32) || bad_dyn(scene->dyn) || bad_precull(scene->precull)) return GS_ERR_ARG;
     Carver c(ctx->ws);
     ViewInfo* vt = c.take<ViewInfo>(n_views + 1);
     if (check_ws(ctx, c.off)) return GS_ERR_CAPACITY;
     DeviceGuard g(ctx->device);
     launch_view_table(d_cams, n_views, ctx->tile, vt, -1, ctx->d_status, S(stream));
-    launch_project(scene->params, scene->n, scene->sh_degree, make_dyn(scene->dyn), d_cams, vt, n_views,
+    launch_project(scene->params, scene->n, scene->sh_degree, make_dyn(scene->dyn, scene->precull), d_cams, vt, n_views,
                    ctx->tile, proj, nullptr, S(stream));
     return launch_check();
 }
@@ -303,10 +310,10 @@ gs_status_t gs_project_bwd(gs_ctx* ctx, const gs_scene* scene, const gs_camera* 
                            const float* proj, const float* grad2d, float* dparams, int32_t accumulate,
                            void* stream) {
     if (!ctx || !scene || !d_cams || !proj || !grad2d || !dparams || bad_views(n_views) || scene->n < 0 ||
-        scene->sh_degree < 0 || scene->sh_degree > 3 || (scene->n > 0 && !scene->params) || bad_dyn(scene->dyn))
+        scene->sh_degree < 0 || scene->sh_degree > 3 || (scene->n > 0 && !scene->params) || bad_dyn(scene->dyn) || bad_precull(scene->precull))
         return GS_ERR_ARG;
     DeviceGuard g(ctx->device);
-    launch_project_bwd(scene->params, scene->n, scene->sh_degree, make_dyn(scene->dyn), d_cams, n_views, proj,
+    launch_project_bwd(scene->params, scene->n, scene->sh_degree, make_dyn(scene->dyn, scene->precull), d_cams, n_views, proj,
                        grad2d, dparams,
                        accumulate, S(stream));
     return launch_check();
@@ -393,7 +400,7 @@ gs_status_t gs_render_batch(gs_ctx* ctx, const gs_scene* scene, const gs_camera*
                             void* stream) {
     if (!ctx || !scene || !d_cams || !image || bad_views(n_requests) || scene->n < 0 || total_tiles < 1 ||
         keys_cap < 0 || keys_cap >= (1LL << 32) || scene->sh_degree < 0 || scene->sh_degree > 3 ||
-        (scene->n > 0 && !scene->params) || (int64_t)n_requests * scene->n >= (1LL << 32) || bad_dyn(scene->dyn))
+        (scene->n > 0 && !scene->params) || (int64_t)n_requests * scene->n >= (1LL << 32) || bad_dyn(scene->dyn) || bad_precull(scene->precull))
         return GS_ERR_ARG;
     const FusedPlan p0 = plan_fused(nullptr, n_requests, scene->n, keys_cap, total_tiles, 0, 0, 0, false);
     if (check_ws(ctx, p0.bytes)) return GS_ERR_CAPACITY;
@@ -404,11 +411,12 @@ gs_status_t gs_render_batch(gs_ctx* ctx, const gs_scene* scene, const gs_camera*
     carve_sort_scratch(p.sort, n_requests, scene->n, keys_cap, total_tiles, &s);
     const float3 b = bg ? make_float3(bg[0], bg[1], bg[2]) : make_float3(0.f, 0.f, 0.f);
     launch_view_table(d_cams, n_requests, ctx->tile, p.vt, total_tiles, ctx->d_status, st);
-    launch_project(scene->params, scene->n, scene->sh_degree, make_dyn(scene->dyn), d_cams, p.vt, n_requests,
+    launch_project(scene->params, scene->n, scene->sh_degree, make_dyn(scene->dyn, scene->precull), d_cams, p.vt, n_requests,
                    ctx->tile, p.proj,
                    s.dkv[0], st);
     launch_bin_sort(p.proj, p.vt, n_requests, scene->n, keys_cap, total_tiles, ctx->binning, ctx->sort_bits, ctx->sort_items, s, true, nullptr,
-                    p.vals, p.ranges, p.n_keys, ctx->d_status, ctx->sm_count, st);
+                    p.vals, p.ranges, p.n_keys, ctx->d_status, ctx->sm_count, st, nullptr, nullptr, 0,
+                    scene->precull != nullptr);
     launch_render_fwd(p.proj, p.vt, n_requests, scene->n, ctx->tile, ctx->raster_tpr, p.vals, p.ranges, b, image, nullptr,
                       nullptr, total_tiles, st);
     return launch_check();
@@ -437,7 +445,7 @@ gs_status_t gs_train_step_events(gs_ctx* ctx, const gs_camera* d_cams, const gs_
         cfg->keys_cap >= (1LL << 32) || (int64_t)cfg->n_views * cfg->n >= (1LL << 32) || !io->params ||
         !io->grads || !io->adam_m || !io->adam_v || !io->baseline || !io->targets || !io->image ||
         !io->d_loss || !io->d_delta_idx || !io->d_delta_records || !io->d_delta_count || !io->d_step ||
-        bad_dyn(cfg->dyn) || cfg->n_frozen < 0 || (cfg->n_frozen > 0 && !io->frozen) ||
+        bad_dyn(cfg->dyn) || bad_precull(cfg->precull) || cfg->n_frozen < 0 || (cfg->n_frozen > 0 && !io->frozen) ||
         (int64_t)cfg->n_views * (cfg->n + cfg->n_frozen) >= (1LL << 32))
         return GS_ERR_ARG;
     const int V = cfg->n_views;
@@ -456,14 +464,15 @@ gs_status_t gs_train_step_events(gs_ctx* ctx, const gs_camera* d_cams, const gs_
     const float3 b = make_float3(cfg->bg[0], cfg->bg[1], cfg->bg[2]);
     mark(ev, 0, st);
     launch_view_table(d_cams, V, B, p.vt, tt, ctx->d_status, st);
-    const Dyn dyn = make_dyn(cfg->dyn);
+    const Dyn dyn = make_dyn(cfg->dyn, cfg->precull, p.fwd);
     launch_project(io->params, na, cfg->sh_degree, dyn, d_cams, p.vt, V, B, p.proj, s.dkv[0], st, 0, n);
     if (cfg->n_frozen > 0)
         launch_project(io->frozen, cfg->n_frozen, cfg->sh_degree, dyn, d_cams, p.vt, V, B, p.proj, s.dkv[0], st,
                        na, n);
     mark(ev, 1, st);
     launch_bin_sort(p.proj, p.vt, V, n, cfg->keys_cap, tt, ctx->binning, ctx->sort_bits, ctx->sort_items, s, true, nullptr,
-                    p.vals, p.ranges, p.n_keys, ctx->d_status, ctx->sm_count, st, ev ? mark : nullptr, ev, 2);
+                    p.vals, p.ranges, p.n_keys, ctx->d_status, ctx->sm_count, st, ev ? mark : nullptr, ev, 2,
+                    cfg->precull != nullptr);
     mark(ev, 4, st);
     launch_render_fwd(p.proj, p.vt, V, n, B, ctx->raster_tpr, p.vals, p.ranges, b, io->image, p.T_final, p.n_contrib, tt, st);
     mark(ev, 5, st);
@@ -478,7 +487,7 @@ gs_status_t gs_train_step_events(gs_ctx* ctx, const gs_camera* d_cams, const gs_
     gs_adam_cfg ac = cfg->adam;
     ac.d_step = io->d_step;
     ac.increment = 1;
-    launch_adam(io->params, io->grads, io->adam_m, io->adam_v, na, ac, st);
+    launch_adam(io->params, io->grads, io->adam_m, io->adam_v, na, ac, st, cfg->precull ? p.fwd : nullptr);
     mark(ev, 9, st);
     launch_delta(io->params, io->baseline, na, cfg->delta_thr, io->d_delta_idx, io->d_delta_records,
                  io->d_delta_count, p.delta, st);
@@ -492,7 +501,7 @@ gs_status_t gs_autotune(gs_ctx* ctx, const gs_scene* scene, const gs_camera* d_c
     if (!ctx || !scene || !d_cams || !host_cams || bad_views(n_views) || scene->n < 0 || scene->sh_degree < 0 ||
         scene->sh_degree > 3 || (scene->n > 0 && !scene->params) || keys_cap < 0 || keys_cap >= (1LL << 32) ||
         (int64_t)n_views * scene->n >= (1LL << 32) || reps < 1 || max_results < 0 ||
-        (max_results > 0 && !results) || bad_dyn(scene->dyn))
+        (max_results > 0 && !results) || bad_dyn(scene->dyn) || bad_precull(scene->precull))
         return GS_ERR_ARG;
     const int V = n_views;
     const int64_t n = scene->n;
@@ -507,7 +516,7 @@ gs_status_t gs_autotune(gs_ctx* ctx, const gs_scene* scene, const gs_camera* d_c
     cudaStream_t st = S(stream);
     SortScratch s;
     carve_sort_scratch(p.sort, V, n, keys_cap, tt, &s);
-    const Dyn dyn = make_dyn(scene->dyn);
+    const Dyn dyn = make_dyn(scene->dyn, scene->precull);
     // the image is not read back: it goes to the image-gradient buffer, which
     // the adjoint then reads (its cost does not depend on the values)
     float* image = p.dimage;
@@ -516,7 +525,8 @@ gs_status_t gs_autotune(gs_ctx* ctx, const gs_scene* scene, const gs_camera* d_c
         launch_view_table(d_cams, V, B, p.vt, tt, ctx->d_status, st);
         launch_project(scene->params, n, scene->sh_degree, dyn, d_cams, p.vt, V, B, p.proj, s.dkv[0], st);
         launch_bin_sort(p.proj, p.vt, V, n, keys_cap, tt, ctx->binning, ctx->sort_bits, ctx->sort_items, s, true,
-                        nullptr, p.vals, p.ranges, p.n_keys, ctx->d_status, ctx->sm_count, st);
+                        nullptr, p.vals, p.ranges, p.n_keys, ctx->d_status, ctx->sm_count, st, nullptr, nullptr, 0,
+                        scene->precull != nullptr);
         launch_render_fwd(p.proj, p.vt, V, n, B, ctx->raster_tpr, p.vals, p.ranges, bg, image, p.T_final,
                           p.n_contrib, tt, st);
         launch_raster_bwd(p.proj, p.vt, V, n, B, ctx->raster_tpr, p.vals, p.ranges, bg, p.T_final, p.n_contrib,
@@ -580,6 +590,27 @@ gs_status_t gs_autotune(gs_ctx* ctx, const gs_scene* scene, const gs_camera* d_c
         return rc;
     }
     ctx->binning = bb; ctx->sort_bits = bbits; ctx->sort_items = bitems; ctx->raster_tpr = btpr;
+    return launch_check();
+}
+
+size_t gs_precull_workspace_size(const gs_camera* host_cams, int32_t n_views) {
+    if (!host_cams || bad_views(n_views)) return 0;
+    return precull_scratch_bytes(host_cams, n_views) + 4096;
+}
+
+gs_status_t gs_cell_visibility(gs_ctx* ctx, const gs_camera* d_cams, const gs_camera* host_cams, int32_t n_views,
+                               const float* d_depth, const gs_precull* grid, uint8_t* d_cell_visible,
+                               void* stream) {
+    if (!ctx || !d_cams || !host_cams || bad_views(n_views) || !d_depth || !grid || !d_cell_visible ||
+        !(grid->cell_size > 0.f) || grid->dims[0] < 1 || grid->dims[1] < 1 || grid->dims[2] < 1 ||
+        (int64_t)grid->dims[0] * grid->dims[1] * grid->dims[2] >= (1LL << 40))
+        return GS_ERR_ARG;
+    for (int v = 0; v < n_views; ++v)
+        if (host_cams[v].width < 1 || host_cams[v].height < 1) return GS_ERR_ARG;
+    if (check_ws(ctx, precull_scratch_bytes(host_cams, n_views))) return GS_ERR_CAPACITY;
+    DeviceGuard g(ctx->device);
+    launch_cell_visibility(d_cams, host_cams, n_views, d_depth, *grid, d_cell_visible,
+                           static_cast<char*>(ctx->ws), S(stream));
     return launch_check();
 }
 

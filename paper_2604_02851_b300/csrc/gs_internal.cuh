@@ -55,7 +55,10 @@ constexpr long long kSpinCycles = 2000000000LL;
 void launch_view_table(const gs_camera* d_cams, int V, int tile, ViewInfo* vt,
                        long long expect_tiles, DevStatus* status, cudaStream_t st);
 
-// Scene dynamics as the kernels take them (by value; group == nullptr: static).
+// Per-scene extras as the projection kernels take them (by value):
+// dynamics (group == nullptr: static) and preculling (cell_vis == nullptr:
+// none; fwd, when set, receives 1 for kept and 0 for culled Gaussians of the
+// pool projected at offset 0).
 struct Dyn {
     int n_groups;
     const uint8_t* group;
@@ -63,10 +66,21 @@ struct Dyn {
     const float4* normals;   // nullptr: no relighting
     const float4* light;
     float ambient, diffuse;
+    const uint8_t* cell_vis;
+    float grid_o[3];
+    float grid_size;
+    int grid_dims[3];
+    uint8_t* fwd;
 };
 
-inline Dyn make_dyn(const gs_dynamics* d) {
+inline Dyn make_dyn(const gs_dynamics* d, const gs_precull* pc = nullptr, uint8_t* fwd = nullptr) {
     Dyn k{};
+    if (pc && pc->cell_visible) {
+        k.cell_vis = pc->cell_visible;
+        for (int a = 0; a < 3; ++a) { k.grid_o[a] = pc->origin[a]; k.grid_dims[a] = pc->dims[a]; }
+        k.grid_size = pc->cell_size;
+        k.fwd = fwd;
+    }
     if (d && d->n_groups > 0 && d->group && d->poses) {
         k.n_groups = d->n_groups;
         k.group = d->group;
@@ -103,7 +117,8 @@ struct SortScratch {
     uint32_t* counters;        // [8] onesweep tile counters (+ emission block counter)
     unsigned long long* lookback;  // [4][max_tiles][256]
     int64_t max_sort_tiles;    // per pass
-    uint32_t* d_count_depth;   // V*n as a device scalar
+    uint32_t* d_count_depth;   // depth-sort items (V*n, or those kept by the compaction)
+    uint32_t* keep_sums;       // block sums of the depth-item compaction
     // two-level binning (super-tile lists, then per-tile lists)
     uint2* cranges;            // [total_tiles] bound on super-tiles: coarse [start, end)
     uint32_t* chunk_first;     // [total_tiles + 1] first chunk of each super-tile
@@ -131,7 +146,7 @@ void launch_bin_sort(const float* proj, const ViewInfo* vt, int V, int64_t n, in
                      uint32_t* sorted_keys, uint32_t* sorted_vals, uint32_t* ranges,
                      uint32_t* d_num_keys, DevStatus* status, int sm_count, cudaStream_t st,
                      void (*mark)(void* const*, int, cudaStream_t) = nullptr, void* const* events = nullptr,
-                     int first_event = 0);
+                     int first_event = 0, bool compact = false);
 
 // tpr: threads per pixel row of a 16 x 16 tile (2 or 4); 8 x 8 tiles use 4.
 // Adjoint: Gaussians with index >= n_active (a frozen pool appended after the
@@ -150,8 +165,15 @@ size_t loss_scratch_bytes(int V, int H, int W);
 void launch_loss(const float* image, const float* target, int V, int H, int W, float w_l1,
                  float w_ssim, float* d_loss, float* dimage, char* scratch, cudaStream_t st);
 
+// fwd (may be null): Gaussians with fwd[g] == 0 are left untouched.
 void launch_adam(float* theta, const float* grad, float* m, float* v, int64_t n,
-                 const gs_adam_cfg& cfg, cudaStream_t st);
+                 const gs_adam_cfg& cfg, cudaStream_t st, const uint8_t* fwd = nullptr);
+
+// Preculling visibility: max pyramids of the views' depth buffers in
+// `scratch` (precull_scratch_bytes), then one thread per cell.
+size_t precull_scratch_bytes(const gs_camera* host_cams, int V);
+void launch_cell_visibility(const gs_camera* d_cams, const gs_camera* host_cams, int V, const float* depth,
+                            const gs_precull& grid, uint8_t* vis, char* scratch, cudaStream_t st);
 
 size_t delta_scratch_bytes(int64_t n);
 void launch_delta(const float* theta, float* baseline, int64_t n, float thr, uint32_t* d_idx,

@@ -281,6 +281,22 @@ k_project(const float4* __restrict__ P, int64_t n, int64_t g_off, int64_t n_out,
     Gauss G;
     load_gauss(P, n, g, G);
     apply_dyn(dyn, g_off + g, G);
+    // preculling: the Gaussian takes part only when its (world) cell is kept
+    bool kept = true;
+    if (dyn.cell_vis) {
+        const float pm[3] = {G.mu.x, G.mu.y, G.mu.z};
+        int cidx[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const float d = (pm[a] - dyn.grid_o[a]) / dyn.grid_size;
+            long long k = (long long)floorf(d);
+            k = k < 0 ? 0 : (k > dyn.grid_dims[a] - 1 ? dyn.grid_dims[a] - 1 : k);
+            cidx[a] = (int)k;
+        }
+        const int64_t cell = ((int64_t)cidx[2] * dyn.grid_dims[1] + cidx[1]) * dyn.grid_dims[0] + cidx[0];
+        kept = dyn.cell_vis[cell] != 0;
+        if (dyn.fwd && g_off == 0) dyn.fwd[g] = kept ? 1 : 0;
+    }
     float sh[NPL * 4];
 #pragma unroll
     for (int pl = 0; pl < NPL; ++pl) {
@@ -293,7 +309,7 @@ k_project(const float4* __restrict__ P, int64_t n, int64_t g_off, int64_t n_out,
         const int64_t rec = (int64_t)v * n_out + g_off + g;
         float4* out = proj + rec * 4;
         ViewGeom Vg;
-        bool ok = view_geom(G, C, Vg);
+        bool ok = kept && view_geom(G, C, Vg);
         float u = 0.f, vv = 0.f, r = 0.f;
         int x0 = 0, y0 = 0, x1 = 0, y1 = 0;
         if (ok) {

@@ -337,6 +337,63 @@ __global__ void k_depth_keys(const uint4* __restrict__ proj, int64_t items, uint
     kv[i] = ((uint64_t)key << 32) | (uint32_t)i;
 }
 
+// Compaction of depth-sort items: the items with a key other than all ones
+// (Gaussians some earlier stage culled for every view, e.g. by preculling),
+// in order.  Blocks of kKeepBlock items: count, scan of the block sums, emit.
+constexpr int kKeepBlock = 1024;
+
+__global__ void __launch_bounds__(256)
+k_keep_count(const uint64_t* __restrict__ in, int64_t items, uint32_t* __restrict__ block_sums) {
+    const int64_t b0 = (int64_t)blockIdx.x * kKeepBlock;
+    uint32_t mine = 0;
+#pragma unroll
+    for (int r = 0; r < kKeepBlock / 256; ++r) {
+        const int64_t i = b0 + r * 256 + threadIdx.x;
+        mine += (i < items && (uint32_t)(in[i] >> 32) != 0xFFFFFFFFu) ? 1u : 0u;
+    }
+    __shared__ uint32_t s_w[8];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mine += __shfl_xor_sync(0xFFFFFFFFu, mine, o);
+    if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = mine;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t t = 0;
+        for (int w = 0; w < 8; ++w) t += s_w[w];
+        block_sums[blockIdx.x] = t;
+    }
+}
+
+__global__ void __launch_bounds__(256)
+k_keep_emit(const uint64_t* __restrict__ in, int64_t items, const uint32_t* __restrict__ block_off,
+            uint64_t* __restrict__ out) {
+    __shared__ uint32_t s_w[8];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t base = block_off[blockIdx.x];
+    const int64_t b0 = (int64_t)blockIdx.x * kKeepBlock;
+#pragma unroll
+    for (int r = 0; r < kKeepBlock / 256; ++r) {
+        const int64_t i = b0 + r * 256 + threadIdx.x;
+        uint64_t it = 0;
+        bool keep = false;
+        if (i < items) {
+            it = in[i];
+            keep = (uint32_t)(it >> 32) != 0xFFFFFFFFu;
+        }
+        const uint32_t bal = __ballot_sync(0xFFFFFFFFu, keep);
+        if (lane == 0) s_w[warp] = __popc(bal);
+        __syncthreads();
+        uint32_t off = base;
+        uint32_t tot = 0;
+        for (int w = 0; w < 8; ++w) {
+            if (w < warp) off += s_w[w];
+            tot += s_w[w];
+        }
+        if (keep) out[off + __popc(bal & lanemask_lt())] = it;
+        base += tot;
+        __syncthreads();
+    }
+}
+
 // ------------------------------------------------------------ emission
 // Two-level entries carry their tile rectangle within the super-tile (local
 // x0, x1 - 1, y0, y1 - 1, 3 bits each) in bits 52..63, above keys of up to
@@ -366,7 +423,7 @@ k_emit(const uint64_t* __restrict__ dsorted, int64_t total, int64_t n, const uin
        const ViewInfo* __restrict__ vt, int64_t cap, uint64_t* __restrict__ kv,
        unsigned long long* __restrict__ lookback, uint32_t* block_counter, uint32_t* d_num_keys,
        int passes, uint32_t* __restrict__ hist, int sshift, unsigned long long* fine_total, uint32_t key_bound,
-       DevStatus* status) {
+       const uint32_t* d_total, DevStatus* status) {
     constexpr int R = 1 << BITS;
     __shared__ uint32_t s_hist[kMaxPasses][R];
     __shared__ int s_mark[kEmitWarps][32];
@@ -379,6 +436,9 @@ k_emit(const uint64_t* __restrict__ dsorted, int64_t total, int64_t n, const uin
     __syncthreads();
     const int64_t b = s_blk;
     const int64_t nblk = (total + kEmitBlock - 1) / kEmitBlock;
+    // after a compaction only the first *d_total items are filled (the grid
+    // still covers `total`; blocks past them publish empty counts)
+    if (d_total && (int64_t)*d_total < total) total = (int64_t)*d_total;
 
     uint32_t cnt[kEmitRounds], lo[kEmitRounds], hi[kEmitRounds], gi[kEmitRounds], kb[kEmitRounds],
         tx[kEmitRounds], incl[kEmitRounds], rtot[kEmitRounds], flo[kEmitRounds], fhi[kEmitRounds];
@@ -850,7 +910,8 @@ void onesweep_passes(uint64_t* const buf[2], uint64_t* last_out, uint32_t* kout,
 
 // Emission + tile-key sort + ranges, for one digit width.
 template <int BITS, int ITEMS>
-void emit_and_sort(const uint64_t* dsorted, int64_t items, int64_t n, const uint4* pr, const ViewInfo* vt,
+void emit_and_sort(const uint64_t* dsorted, int64_t items, const uint32_t* d_items, int64_t n, const uint4* pr,
+                   const ViewInfo* vt,
                    int64_t keys_cap, int key_bits, const SortScratch& s, uint32_t* sorted_keys,
                    uint32_t* sorted_vals, uint32_t* ranges, int64_t total_tiles, uint32_t* d_num_keys,
                    DevStatus* status, int sm_count, cudaStream_t st,
@@ -862,7 +923,8 @@ void emit_and_sort(const uint64_t* dsorted, int64_t items, int64_t n, const uint
     cudaMemsetAsync(s.emit_lookback, 0, sizeof(unsigned long long) * (size_t)nblk, st);
     k_emit<BITS><<<(unsigned)nblk, kEmitThreads, 0, st>>>(dsorted, items, n, pr, vt, keys_cap, s.tkv[0],
                                                           s.emit_lookback, s.counters + 7, d_num_keys, passes,
-                                                          s.hist, 0, nullptr, (uint32_t)total_tiles, status);
+                                                          s.hist, 0, nullptr, (uint32_t)total_tiles, d_items,
+                                                          status);
     if (mark) mark(events, ev, st);
     k_ranges_init<<<sm_count * 2, 256, 0, st>>>(reinterpret_cast<uint2*>(ranges), total_tiles);
     uint64_t* const buf[2] = {s.tkv[0], s.tkv[1]};
@@ -874,7 +936,8 @@ void emit_and_sort(const uint64_t* dsorted, int64_t items, int64_t n, const uint
 // Two-level binning: coarse emission and super-tile sort, then the fine
 // expansion into the caller's arrays and ranges.
 template <int BITS, int ITEMS>
-void emit_two_level(const uint64_t* dsorted, int64_t items, int64_t n, const uint4* pr, const ViewInfo* vt, int V,
+void emit_two_level(const uint64_t* dsorted, int64_t items, const uint32_t* d_items, int64_t n, const uint4* pr,
+                    const ViewInfo* vt, int V,
                     int64_t keys_cap, const SortScratch& s, uint32_t* sorted_keys,
                     uint32_t* sorted_vals, uint32_t* ranges, int64_t total_tiles, uint32_t* d_num_keys,
                     DevStatus* status, int sm_count, cudaStream_t st,
@@ -893,7 +956,7 @@ void emit_two_level(const uint64_t* dsorted, int64_t items, int64_t n, const uin
     k_emit<BITS><<<(unsigned)nblk, kEmitThreads, 0, st>>>(dsorted, items, n, pr, vt, keys_cap, s.tkv[0],
                                                           s.emit_lookback, s.counters + 7, s.d_count_coarse,
                                                           passes, s.hist, kSuperShift, s.d_fine_total,
-                                                          (uint32_t)n_super, status);
+                                                          (uint32_t)n_super, d_items, status);
     k_fine_total<<<1, 1, 0, st>>>(s.d_fine_total, keys_cap, d_num_keys, status);
     if (mark) mark(events, ev, st);
     // stable sort by super-tile; the values land in the ping-pong buffer the
@@ -941,6 +1004,7 @@ void carve_sort_scratch(char* base, int V, int64_t n, int64_t keys_cap, int64_t 
     s->max_sort_tiles = (std::max(items, keys_cap) + kMinTileKeys - 1) / kMinTileKeys + 1;
     s->lookback = c.take<unsigned long long>((size_t)kMaxPasses * s->max_sort_tiles * 256);
     s->d_count_depth = c.take<uint32_t>(1);
+    s->keep_sums = c.take<uint32_t>((items + kKeepBlock - 1) / kKeepBlock + 1);
     // super-tiles never outnumber tiles
     const int64_t ns = total_tiles > 0 ? total_tiles : 1;
     s->max_chunks = keys_cap / kFineChunk + ns + 1;
@@ -960,7 +1024,8 @@ void launch_bin_sort(const float* proj, const ViewInfo* vt, int V, int64_t n, in
                      bool depth_ready,
                      uint32_t* sorted_keys, uint32_t* sorted_vals, uint32_t* ranges,
                      uint32_t* d_num_keys, DevStatus* status, int sm_count, cudaStream_t st,
-                     void (*mark)(void* const*, int, cudaStream_t), void* const* events, int first_event) {
+                     void (*mark)(void* const*, int, cudaStream_t), void* const* events, int first_event,
+                     bool compact) {
     const int64_t items = (int64_t)V * n;
     const uint4* pr = reinterpret_cast<const uint4*>(proj);
     if (items == 0) {
@@ -972,11 +1037,25 @@ void launch_bin_sort(const float* proj, const ViewInfo* vt, int V, int64_t n, in
     //    8-bit digits ending back in dkv[0]
     if (!depth_ready)
         k_depth_keys<<<(unsigned)((items + 255) / 256), 256, 0, st>>>(pr, items, s.dkv[0]);
-    k_set_u32<<<1, 1, 0, st>>>(s.d_count_depth, (uint32_t)items);
+    // with compaction the kept items move to dkv[1] and the sort ends there
+    const uint64_t* dsorted = s.dkv[0];
+    const uint32_t* d_items = nullptr;
     cudaMemsetAsync(s.hist, 0, sizeof(uint32_t) * kMaxPasses * 256, st);
     cudaMemsetAsync(s.counters, 0, sizeof(uint32_t) * 8, st);
-    k_hist<8><<<sm_count * 4, kThreads, 0, st>>>(s.dkv[0], s.d_count_depth, items, 4, s.hist);
-    {
+    if (compact) {
+        const int64_t nb = (items + kKeepBlock - 1) / kKeepBlock;
+        k_keep_count<<<(unsigned)nb, 256, 0, st>>>(s.dkv[0], items, s.keep_sums);
+        launch_scan_sums(s.keep_sums, nb, s.d_count_depth, -1, nullptr, st);
+        k_keep_emit<<<(unsigned)nb, 256, 0, st>>>(s.dkv[0], items, s.keep_sums, s.dkv[1]);
+        k_hist<8><<<sm_count * 4, kThreads, 0, st>>>(s.dkv[1], s.d_count_depth, items, 4, s.hist);
+        uint64_t* const dbuf[2] = {s.dkv[1], s.dkv[0]};
+        onesweep_passes<8, 16>(dbuf, s.dkv[1], nullptr, nullptr, s.d_count_depth, items, 4, s, nullptr, status,
+                               sm_count, st);
+        dsorted = s.dkv[1];
+        d_items = s.d_count_depth;
+    } else {
+        k_set_u32<<<1, 1, 0, st>>>(s.d_count_depth, (uint32_t)items);
+        k_hist<8><<<sm_count * 4, kThreads, 0, st>>>(s.dkv[0], s.d_count_depth, items, 4, s.hist);
         uint64_t* const dbuf[2] = {s.dkv[0], s.dkv[1]};
         onesweep_passes<8, 16>(dbuf, s.dkv[0], nullptr, nullptr, s.d_count_depth, items, 4, s, nullptr, status,
                                sm_count, st);
@@ -990,10 +1069,12 @@ void launch_bin_sort(const float* proj, const ViewInfo* vt, int V, int64_t n, in
 #define GS_EMIT_SORT(B, I)                                                                                      \
     do {                                                                                                        \
         if (binning == kBinDirect || bits > kMaxCoarseKeyBits)                                                  \
-            emit_and_sort<B, I>(s.dkv[0], items, n, pr, vt, keys_cap, bits, s, sorted_keys, sorted_vals, ranges, \
+            emit_and_sort<B, I>(dsorted, items, d_items, n, pr, vt, keys_cap, bits, s, sorted_keys, sorted_vals,  \
+                                ranges,                                                                         \
                                 total_tiles, d_num_keys, status, sm_count, st, mark, events, first_event + 1);  \
         else                                                                                                    \
-            emit_two_level<B, I>(s.dkv[0], items, n, pr, vt, V, keys_cap, s, sorted_keys, sorted_vals, ranges,  \
+            emit_two_level<B, I>(dsorted, items, d_items, n, pr, vt, V, keys_cap, s, sorted_keys, sorted_vals,  \
+                                 ranges,                                                                        \
                                  total_tiles, d_num_keys, status, sm_count, st, mark, events, first_event + 1); \
     } while (0)
     const int it = sort_items == 8 ? 8 : (sort_items == 16 ? 16 : 12);

@@ -26,13 +26,15 @@ from . import (Context, RECORD_BYTES, GRAD2D_STRIDE, PROJ_STRIDE, _lib, _ptr, _s
 class OnlineTrainer:
     def __init__(self, params, sh_degree: int, cams: dict, keys_cap: int, lr=1e-3, w_l1=0.8, w_ssim=0.2,
                  delta_thr=1e-3, bg=(0.0, 0.0, 0.0), tile=16, sort_bits=8, ctx: Context | None = None,
-                 dyn=None, share: "OnlineTrainer | None" = None, frozen=None):
+                 dyn=None, share: "OnlineTrainer | None" = None, frozen=None, precull=None):
         """share: another trainer of the same model whose gradient, Adam
         moments, delta baseline and step counter this one uses (a second
         graph slot with its own targets, image and delta outputs).
         frozen: planes [15][m][4] of an inference-only pool (Sec. 3.3,
         Gaussian freezing): rendered with `params`, never updated; gradients,
-        Adam state and deltas cover `params` only."""
+        Adam state and deltas cover `params` only.
+        precull: a Precull grid (Sec. 3.3): Gaussians of culled cells are not
+        rendered and keep their parameters and Adam state this step."""
         import torch
         self.torch = torch
         self.params = params
@@ -72,8 +74,9 @@ class OnlineTrainer:
         self.io = train_io(params, self.grads, self.m, self.v, self.baseline, self.targets, self.image,
                            self.d_loss, self.d_idx, self.d_records, self.d_count, self.d_step, frozen=frozen)
         self.dyn = dyn  # kept alive: the step reads its device buffers
+        self.precull = precull
         self.cfg = train_cfg(n, sh_degree, V, self.W, self.H, self.keys_cap, w_l1, w_ssim, self.bg, delta_thr, lr,
-                             dyn=dyn, n_frozen=self.n_frozen)
+                             dyn=dyn, n_frozen=self.n_frozen, precull=precull)
         self._captured = False
         self._events = None
         self._plain = None

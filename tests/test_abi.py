@@ -30,13 +30,13 @@ def test_header_declarations_are_exported():
 def test_struct_layouts_match_header():
     assert ctypes.sizeof(_lib.gs_camera) == 80
     assert gs.CAMERA_DTYPE.itemsize == 80
-    assert ctypes.sizeof(_lib.gs_scene) == 32
+    assert ctypes.sizeof(_lib.gs_scene) == 40 and ctypes.sizeof(_lib.gs_precull) == 40
     assert ctypes.sizeof(_lib.gs_dynamics) == 48
     assert _lib.gs_dynamics.ambient.offset == 40
     # gs_adam_cfg: 60 lr + 3 floats + step + pointer + 2 ints
     assert _lib.gs_adam_cfg.d_step.offset == 256
     assert ctypes.sizeof(_lib.gs_train_io) == 104 and _lib.gs_train_io.frozen.offset == 96
-    assert ctypes.sizeof(_lib.gs_train_cfg) == 344 and _lib.gs_train_cfg.n_frozen.offset == 336
+    assert ctypes.sizeof(_lib.gs_train_cfg) == 352 and _lib.gs_train_cfg.n_frozen.offset == 336
     assert ctypes.sizeof(_lib.gs_tune_entry) == 20
 
 
