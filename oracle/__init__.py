@@ -46,6 +46,12 @@ def lib():
                                      C.c_double, C.c_double, _D]
         L.or_project_bwd_dyn.argtypes = [C.c_int64, C.c_int, _D, C.c_int, _D, C.c_int, _D, _I32, _D, C.c_void_p,
                                          _D, C.c_double, C.c_double, _D]
+        L.or_project_lit.argtypes = [C.c_int64, C.c_int, _D, C.c_int, _D, C.c_int, C.c_void_p, C.c_void_p, _D,
+                                     C.c_void_p, _D]
+        L.or_project_bwd_lit.argtypes = [C.c_int64, C.c_int, _D, C.c_int, _D, C.c_int, _D, C.c_void_p,
+                                         C.c_void_p, _D, C.c_void_p, _D]
+        L.or_light_depth.argtypes = [C.c_int64, _D, C.c_void_p, C.c_void_p, _D, C.c_double, C.c_int, _D]
+        L.or_light_visibility.argtypes = [C.c_int64, _D, C.c_void_p, C.c_void_p, _D, _D, _U8, C.c_void_p]
         L.or_bin_count.argtypes = [C.c_int, C.c_int64, _I32]
         L.or_bin_count.restype = C.c_int64
         L.or_bin_sort.argtypes = [C.c_int, C.c_int64, _D, C.c_int, _I32, _F, _U64, _U32, _U32]
@@ -149,15 +155,87 @@ def _dyn_args(dyn):
     return keep, (group, poses, nptr, light, float(dyn.get("ambient", 0.3)), float(dyn.get("diffuse", 0.7)))
 
 
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def _lit_args(dyn, n):
+    """SH relighting inputs of dyn: sh_light [56] (environment SH e[16][3],
+    light direction xyz + 0, radiance rgb + 0), optional visibility (uint8
+    [n]), optional group / poses (rigid objects)."""
+    if dyn.get("normals") is not None:
+        raise ValueError("SH relighting and the Lambertian DC factor are exclusive")
+    L = _d(dyn["sh_light"])
+    if L.shape != (56,):
+        raise ValueError("sh_light must hold 56 values")
+    vis = dyn.get("visibility")
+    vis = None if vis is None else np.ascontiguousarray(vis, dtype=np.uint8)
+    if vis is not None and vis.shape != (n,):
+        raise ValueError("visibility must hold one value per Gaussian")
+    group = dyn.get("group")
+    group = None if group is None else np.ascontiguousarray(group, dtype=np.int32)
+    poses = None if group is None else _d(dyn["poses"])
+    keep = (L, vis, group, poses)
+    return keep, (_ptr(group), _ptr(poses), L, _ptr(vis))
+
+
+def light_cam_array(lcam: dict) -> np.ndarray:
+    """Light camera dict (R [3][3] world -> light, origin [3], texel, width,
+    height, alpha_min, bias) -> the oracle's [17] layout."""
+    a = np.zeros(17)
+    a[0:9] = np.asarray(lcam["R"], dtype=np.float64).reshape(9)
+    a[9:12] = np.asarray(lcam["origin"], dtype=np.float64)
+    a[12] = float(lcam["texel"])
+    a[13] = int(lcam["width"])
+    a[14] = int(lcam["height"])
+    a[15] = float(lcam["alpha_min"])
+    a[16] = float(lcam["bias"])
+    return a
+
+
+def _group_poses(dyn):
+    if dyn is None or dyn.get("group") is None:
+        return (None, None), (None, None)
+    group = np.ascontiguousarray(dyn["group"], dtype=np.int32)
+    poses = _d(dyn["poses"])
+    return (group, poses), (_ptr(group), _ptr(poses))
+
+
+def light_depth(planes, lcam: dict, dyn=None, slack: float = 0.0, brute: bool = False) -> np.ndarray:
+    """Light-space depth map [H][W] float64 (+inf where no Gaussian covers)."""
+    rows = _rows(planes)
+    lc = light_cam_array(lcam)
+    out = np.zeros((int(lcam["height"]), int(lcam["width"])))
+    keep, gp = _group_poses(dyn)
+    lib().or_light_depth(rows.shape[0], rows, gp[0], gp[1], lc, float(slack), int(bool(brute)), out)
+    return out
+
+
+def light_visibility(planes, lcam: dict, depth, dyn=None):
+    """-> (visibility uint8 [n], uvz [n][3] light-map position and depth)."""
+    rows = _rows(planes)
+    n = rows.shape[0]
+    lc = light_cam_array(lcam)
+    vis = np.zeros(max(n, 1), dtype=np.uint8)
+    uvz = np.zeros((max(n, 1), 3))
+    keep, gp = _group_poses(dyn)
+    lib().or_light_visibility(n, rows, gp[0], gp[1], lc, _d(depth), vis, _ptr(uvz))
+    return vis[:n], uvz[:n]
+
+
 def project(planes, sh_degree: int, cams: dict, tile: int = TILE, dyn=None) -> np.ndarray:
     """-> proj [V][n][16] float64 (fields PROJ_FIELDS; zero when culled).
-    dyn: optional rigid-object poses and relighting (see _dyn_args)."""
+    dyn: optional rigid-object poses and relighting (see _dyn_args, or
+    _lit_args when it holds sh_light)."""
     rows = _rows(planes)
     n = rows.shape[0]
     V = len(cams["fx"])
     out = np.zeros((V, n, 16))
     if dyn is None:
         lib().or_project(n, sh_degree, rows, V, cams_array(cams), tile, out)
+    elif dyn.get("sh_light") is not None:
+        keep, a = _lit_args(dyn, n)
+        lib().or_project_lit(n, sh_degree, rows, V, cams_array(cams), tile, *a, out)
     else:
         keep, a = _dyn_args(dyn)
         lib().or_project_dyn(n, sh_degree, rows, V, cams_array(cams), tile, *a, out)
@@ -212,6 +290,9 @@ def project_bwd(planes, sh_degree: int, cams: dict, grad2d, tile: int = TILE, dy
     d = np.zeros((n, 60))
     if dyn is None:
         lib().or_project_bwd(n, sh_degree, rows, V, cams_array(cams), tile, _d(grad2d), d)
+    elif dyn.get("sh_light") is not None:
+        keep, a = _lit_args(dyn, n)
+        lib().or_project_bwd_lit(n, sh_degree, rows, V, cams_array(cams), tile, _d(grad2d), *a, d)
     else:
         keep, a = _dyn_args(dyn)
         lib().or_project_bwd_dyn(n, sh_degree, rows, V, cams_array(cams), tile, _d(grad2d), *a, d)

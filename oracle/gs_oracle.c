@@ -164,6 +164,8 @@ typedef struct {
     const double* normals;  /* [n][3] or NULL (no relighting) */
     double light[3];
     double ambient, diffuse;
+    const double* sh_light; /* [56] SH lighting (see relit_colour) or NULL */
+    const uint8_t* vis;     /* [n] light visibility 0..255, or NULL (all lit) */
 } dyn_t;
 
 static void quat_to_rot(const double* q, double* R);
@@ -270,6 +272,95 @@ static int view_geometry(const double* mu, const double* Sig, const double* cam,
     return 1;
 }
 
+/* ------------------------------------------------------------------------
+ * SH relighting (Sec. 3.4.1).  The Gaussian's SH coefficients are read as its
+ * diffuse radiance transfer T_c(w) = sum_k c_{k,c} Y_k(w) (object frame), and
+ * the lighting is given as SH coefficients too.  READING: the relit colour is
+ * the integral over the sphere of the transfer times the lighting that
+ * reaches the object, expressed in the object's frame:
+ *   rgb_c = max(0, int T_c(w) [Lenv_c(R_g w) + v E_c delta(R_g w, l)] dw + 0.5)
+ * with Lenv_c(w) = sum_{k<16} e_{k,c} Y_k(w) the world-frame environment
+ * lighting, l the unit vector towards the directional light of radiance E_c,
+ * and v = vis / 255 the Gaussian's light visibility, which attenuates the
+ * direct light only.  The delta term integrates to v E_c T_c(R_g^T l).  The
+ * environment term is integrated exactly by a product rule (4-point
+ * Gauss-Legendre in cos(theta) times 8 equally spaced azimuths is exact for
+ * the band-limited integrand of degree <= 6).  The +0.5 is the colour offset
+ * of the SH parameterisation, kept as in the view-dependent colour, so a unit
+ * light along the view direction with no environment gives that colour back.
+ * Lighting layout: e[16][3], then l (x, y, z, 0), then E (r, g, b, 0).
+ * ---------------------------------------------------------------------- */
+#define SPHERE_NQ 32
+static void sphere_rule(double dirs[SPHERE_NQ][3], double w[SPHERE_NQ]) {
+    const double PI = 3.14159265358979323846;
+    /* Gauss-Legendre nodes and weights of order 4, closed forms */
+    const double a = sqrt(3.0 / 7.0 - 2.0 / 7.0 * sqrt(6.0 / 5.0));
+    const double b = sqrt(3.0 / 7.0 + 2.0 / 7.0 * sqrt(6.0 / 5.0));
+    const double wa = (18.0 + sqrt(30.0)) / 36.0, wb = (18.0 - sqrt(30.0)) / 36.0;
+    const double z[4] = {-b, -a, a, b}, wz[4] = {wb, wa, wa, wb};
+    int q = 0;
+    for (int i = 0; i < 4; ++i)
+        for (int j = 0; j < 8; ++j, ++q) {
+            double phi = 2.0 * PI * j / 8.0, rho = sqrt(1.0 - z[i] * z[i]);
+            dirs[q][0] = rho * cos(phi);
+            dirs[q][1] = rho * sin(phi);
+            dirs[q][2] = z[i];
+            w[q] = wz[i] * 2.0 * PI / 8.0;
+        }
+}
+
+static double vis_of(const dyn_t* dyn, int64_t g) { return dyn->vis ? dyn->vis[g] / 255.0 : 1.0; }
+
+/* raw[c] = int T_c(w) L_obj,c(w) dw (without the offset and the clamp) */
+static void relit_raw(const double* p, int nb, const double* Rg, const double* L, double v, double* raw) {
+    double dirs[SPHERE_NQ][3], wq[SPHERE_NQ];
+    sphere_rule(dirs, wq);
+    raw[0] = raw[1] = raw[2] = 0.0;
+    for (int q = 0; q < SPHERE_NQ; ++q) {
+        double ww[3], Yo[16], Yw[16];
+        for (int i = 0; i < 3; ++i) ww[i] = Rg[i * 3] * dirs[q][0] + Rg[i * 3 + 1] * dirs[q][1] + Rg[i * 3 + 2] * dirs[q][2];
+        or_sh_basis(dirs[q], Yo);
+        or_sh_basis(ww, Yw);
+        for (int ch = 0; ch < 3; ++ch) {
+            double T = 0.0, Le = 0.0;
+            for (int k = 0; k < nb; ++k) T += p[12 + 3 * k + ch] * Yo[k];
+            for (int k = 0; k < 16; ++k) Le += L[3 * k + ch] * Yw[k];
+            raw[ch] += wq[q] * T * Le;
+        }
+    }
+    double lo[3], Yl[16];
+    for (int i = 0; i < 3; ++i) lo[i] = Rg[i] * L[48] + Rg[3 + i] * L[49] + Rg[6 + i] * L[50];
+    or_sh_basis(lo, Yl);
+    for (int ch = 0; ch < 3; ++ch) {
+        double T = 0.0;
+        for (int k = 0; k < nb; ++k) T += p[12 + 3 * k + ch] * Yl[k];
+        raw[ch] += v * L[52 + ch] * T;
+    }
+}
+
+/* dp[12 + 3k + c] += gc[c] * d raw_c / d c_{k,c} for the channels with gc != 0 */
+static void relit_grad(int nb, const double* Rg, const double* L, double v, const double* gc, double* dp) {
+    double dirs[SPHERE_NQ][3], wq[SPHERE_NQ];
+    sphere_rule(dirs, wq);
+    for (int q = 0; q < SPHERE_NQ; ++q) {
+        double ww[3], Yo[16], Yw[16];
+        for (int i = 0; i < 3; ++i) ww[i] = Rg[i * 3] * dirs[q][0] + Rg[i * 3 + 1] * dirs[q][1] + Rg[i * 3 + 2] * dirs[q][2];
+        or_sh_basis(dirs[q], Yo);
+        or_sh_basis(ww, Yw);
+        for (int ch = 0; ch < 3; ++ch) {
+            if (gc[ch] == 0.0) continue;
+            double Le = 0.0;
+            for (int k = 0; k < 16; ++k) Le += L[3 * k + ch] * Yw[k];
+            for (int k = 0; k < nb; ++k) dp[12 + 3 * k + ch] += gc[ch] * wq[q] * Yo[k] * Le;
+        }
+    }
+    double lo[3], Yl[16];
+    for (int i = 0; i < 3; ++i) lo[i] = Rg[i] * L[48] + Rg[3 + i] * L[49] + Rg[6 + i] * L[50];
+    or_sh_basis(lo, Yl);
+    for (int ch = 0; ch < 3; ++ch)
+        for (int k = 0; k < nb; ++k) dp[12 + 3 * k + ch] += gc[ch] * v * L[52 + ch] * Yl[k];
+}
+
 static void project_impl(int64_t n, int sh_degree, const double* rows, int V, const double* cams, int tile,
                          const dyn_t* dyn, double* out) {
     int nb = (sh_degree + 1) * (sh_degree + 1);
@@ -293,11 +384,15 @@ static void project_impl(int64_t n, int sh_degree, const double* rows, int V, co
             int32_t rect[4];
             or_rect(u, vv, r, (int)cam[16], (int)cam[17], tile, rect);
             if ((rect[2] - rect[0]) * (rect[3] - rect[1]) == 0) continue;
-            double rgb[3];
+            double rgb[3], raw[3];
             int mask = 0;
+            if (dyn && dyn->sh_light) relit_raw(p, nb, Rg, dyn->sh_light, vis_of(dyn, g), raw);
             for (int ch = 0; ch < 3; ++ch) {
                 double acc = 0.0;
-                for (int k = 0; k < nb; ++k) acc += p[12 + 3 * k + ch] * G.Y[k] * (k == 0 ? Ld : 1.0);
+                if (dyn && dyn->sh_light)
+                    acc = raw[ch];
+                else
+                    for (int k = 0; k < nb; ++k) acc += p[12 + 3 * k + ch] * G.Y[k] * (k == 0 ? Ld : 1.0);
                 acc += 0.5;
                 if (acc < 0.0) { acc = 0.0; mask |= 1 << ch; }
                 rgb[ch] = acc;
@@ -319,7 +414,16 @@ void or_project(int64_t n, int sh_degree, const double* rows, int V, const doubl
 void or_project_dyn(int64_t n, int sh_degree, const double* rows, int V, const double* cams, int tile,
                     const int32_t* group, const double* poses, const double* normals, const double* light,
                     double ambient, double diffuse, double* out) {
-    dyn_t d = {group, poses, normals, {light[0], light[1], light[2]}, ambient, diffuse};
+    dyn_t d = {group, poses, normals, {light[0], light[1], light[2]}, ambient, diffuse, NULL, NULL};
+    project_impl(n, sh_degree, rows, V, cams, tile, &d, out);
+}
+
+/* or_project with SH relighting; group / poses may be NULL (static scene),
+ * vis NULL means every Gaussian is lit. */
+void or_project_lit(int64_t n, int sh_degree, const double* rows, int V, const double* cams, int tile,
+                    const int32_t* group, const double* poses, const double* sh_light, const uint8_t* vis,
+                    double* out) {
+    dyn_t d = {group, poses, NULL, {0, 0, 0}, 0.0, 0.0, sh_light, vis};
     project_impl(n, sh_degree, rows, V, cams, tile, &d, out);
 }
 
@@ -575,7 +679,14 @@ static void project_bwd_impl(int64_t n, int sh_degree, const double* rows, int V
             /* colour: rgb_c = sum_k sh[k][c] Y_k(dir) + 0.5, clamped at 0 */
             double ddl[3] = {0, 0, 0}, dY[48];  /* w.r.t. the object-frame direction */
             or_sh_basis_grad(G.dir_sh, dY);
-            for (int ch = 0; ch < 3; ++ch) {
+            if (dyn && dyn->sh_light) {
+                /* relit colour: no view dependence, linear in the coefficients */
+                double raw[3], gcol[3];
+                relit_raw(p, nb, Rg, dyn->sh_light, vis_of(dyn, g), raw);
+                for (int ch = 0; ch < 3; ++ch) gcol[ch] = raw[ch] + 0.5 < 0.0 ? 0.0 : gr[6 + ch];
+                relit_grad(nb, Rg, dyn->sh_light, vis_of(dyn, g), gcol, dp);
+            }
+            for (int ch = 0; ch < 3 && !(dyn && dyn->sh_light); ++ch) {
                 double raw = 0.5;
                 for (int k = 0; k < nb; ++k) raw += p[12 + 3 * k + ch] * G.Y[k] * (k == 0 ? Ld : 1.0);
                 if (raw < 0.0) continue;
@@ -682,8 +793,124 @@ void or_project_bwd(int64_t n, int sh_degree, const double* rows, int V, const d
 void or_project_bwd_dyn(int64_t n, int sh_degree, const double* rows, int V, const double* cams, int tile,
                         const double* grad2d, const int32_t* group, const double* poses, const double* normals,
                         const double* light, double ambient, double diffuse, double* drows) {
-    dyn_t d = {group, poses, normals, {light[0], light[1], light[2]}, ambient, diffuse};
+    dyn_t d = {group, poses, normals, {light[0], light[1], light[2]}, ambient, diffuse, NULL, NULL};
     project_bwd_impl(n, sh_degree, rows, V, cams, tile, grad2d, &d, drows);
+}
+
+void or_project_bwd_lit(int64_t n, int sh_degree, const double* rows, int V, const double* cams, int tile,
+                        const double* grad2d, const int32_t* group, const double* poses, const double* sh_light,
+                        const uint8_t* vis, double* drows) {
+    dyn_t d = {group, poses, NULL, {0, 0, 0}, 0.0, 0.0, sh_light, vis};
+    project_bwd_impl(n, sh_degree, rows, V, cams, tile, grad2d, &d, drows);
+}
+
+/* ------------------------------------------------------------------------
+ * Light visibility (Sec. 3.4.1): an orthographic camera attached to the
+ * directional light renders a light-space depth map, and every Gaussian
+ * centre is projected into it and tested against the stored depth.
+ * READING (the paper's map is the engine's shadow pass over its meshes, which
+ * this build does not have): the map is rendered from the Gaussians
+ * themselves.  Texel (i, j) holds the smallest light-space depth of the
+ * Gaussians whose splat alpha at the texel centre reaches alpha_min,
+ *   alpha = min(0.99, o exp(-q / 2)),   q = d^T Sigma2^{-1} d,
+ * Sigma2 the orthographic image of the world covariance in texel units plus
+ * the renderer's 0.3 low-pass, d = texel centre - projected centre; +inf
+ * where no Gaussian reaches alpha_min.  With alpha_min <= 0.99 the test is
+ * q <= tau = 2 ln(o / alpha_min).  A Gaussian is lit (255) when its centre
+ * falls outside the map or its depth is at most the stored depth plus bias,
+ * else shadowed (0).
+ * Light camera: x_l = R (mu_world - origin); u = x_l / texel + W / 2,
+ * v = y_l / texel + H / 2, depth z_l; texel (i, j) is sampled at
+ * (i + 0.5, j + 0.5).  lcam[17]: R[9] (rows: map x, map y, depth axis),
+ * origin[3], texel, W, H, alpha_min, bias.
+ * slack (tests only) moves the bound to q <= tau + slack; brute = 1 tests
+ * every texel instead of the footprint's bounding box.
+ * ---------------------------------------------------------------------- */
+typedef struct {
+    double u, v, z;
+    double A, B, C;   /* conic in texel units */
+    double tau;
+    double lmax;      /* larger eigenvalue of Sigma2 */
+} light_splat;
+
+static void light_project(const double* p, const dyn_t* dyn, int64_t g, const double* lc, light_splat* S) {
+    double mu[3], s[3], q[4], qn, R[9], Sig[9], opac, Rg[9], Ld;
+    gauss_common(p, mu, s, q, &qn, R, Sig, &opac);
+    apply_dynamics(dyn, g, mu, Sig, Rg, &Ld);
+    const double* Rl = lc;
+    double h = lc[12], W = lc[13], H = lc[14];
+    double d[3] = {mu[0] - lc[9], mu[1] - lc[10], mu[2] - lc[11]};
+    double xl[3];
+    for (int i = 0; i < 3; ++i) xl[i] = Rl[i * 3] * d[0] + Rl[i * 3 + 1] * d[1] + Rl[i * 3 + 2] * d[2];
+    S->u = xl[0] / h + W / 2.0;
+    S->v = xl[1] / h + H / 2.0;
+    S->z = xl[2];
+    /* Sigma2 = (1 / h^2) R_2 Sigma R_2^T + 0.3 I */
+    double a = 0.0, b = 0.0, c = 0.0;
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            a += Rl[i] * Sig[i * 3 + j] * Rl[j];
+            b += Rl[i] * Sig[i * 3 + j] * Rl[3 + j];
+            c += Rl[3 + i] * Sig[i * 3 + j] * Rl[3 + j];
+        }
+    a = a / (h * h) + DILATION;
+    b = b / (h * h);
+    c = c / (h * h) + DILATION;
+    double det = a * c - b * b;
+    S->A = c / det; S->B = -b / det; S->C = a / det;
+    double mid = 0.5 * (a + c);
+    S->lmax = mid + sqrt(fmax(0.0, mid * mid - det));
+    S->tau = 2.0 * log(opac / lc[15]);
+}
+
+static void light_depth_impl(int64_t n, const double* rows, const dyn_t* dyn, const double* lc, double slack,
+                             int brute, double* depth) {
+    int W = (int)lc[13], H = (int)lc[14];
+    for (int64_t t = 0; t < (int64_t)W * H; ++t) depth[t] = INFINITY;
+    for (int64_t g = 0; g < n; ++g) {
+        light_splat S;
+        light_project(rows + g * ROW, dyn, g, lc, &S);
+        double bound = S.tau + slack;
+        if (!(bound >= 0.0) || !isfinite(S.z)) continue;
+        int i0 = 0, i1 = W - 1, j0 = 0, j1 = H - 1;
+        if (!brute) {
+            /* q <= bound implies |d|^2 <= bound * lmax */
+            double r = sqrt(bound * S.lmax);
+            i0 = (int)fmax(0.0, ceil(S.u - r - 0.5));
+            i1 = (int)fmin(W - 1.0, floor(S.u + r - 0.5));
+            j0 = (int)fmax(0.0, ceil(S.v - r - 0.5));
+            j1 = (int)fmin(H - 1.0, floor(S.v + r - 0.5));
+        }
+        for (int j = j0; j <= j1; ++j)
+            for (int i = i0; i <= i1; ++i) {
+                double dx = i + 0.5 - S.u, dy = j + 0.5 - S.v;
+                double qf = S.A * dx * dx + 2.0 * S.B * dx * dy + S.C * dy * dy;
+                if (qf <= bound && S.z < depth[(int64_t)j * W + i]) depth[(int64_t)j * W + i] = S.z;
+            }
+    }
+}
+
+/* depth [H][W]; group / poses may be NULL (static scene) */
+void or_light_depth(int64_t n, const double* rows, const int32_t* group, const double* poses, const double* lcam,
+                    double slack, int brute, double* depth) {
+    dyn_t d = {group, poses, NULL, {0, 0, 0}, 0.0, 0.0, NULL, NULL};
+    light_depth_impl(n, rows, &d, lcam, slack, brute, depth);
+}
+
+/* vis [n] (255 lit, 0 shadowed); uvz [n][3] (may be NULL) receives u, v, z */
+void or_light_visibility(int64_t n, const double* rows, const int32_t* group, const double* poses,
+                         const double* lcam, const double* depth, uint8_t* vis, double* uvz) {
+    dyn_t d = {group, poses, NULL, {0, 0, 0}, 0.0, 0.0, NULL, NULL};
+    int W = (int)lcam[13], H = (int)lcam[14];
+    for (int64_t g = 0; g < n; ++g) {
+        light_splat S;
+        light_project(rows + g * ROW, &d, g, lcam, &S);
+        if (uvz) { uvz[g * 3] = S.u; uvz[g * 3 + 1] = S.v; uvz[g * 3 + 2] = S.z; }
+        double fi = floor(S.u), fj = floor(S.v);
+        if (!(fi >= 0.0 && fi < W && fj >= 0.0 && fj < H)) { vis[g] = 255; continue; }
+        double D = depth[(int64_t)fj * W + (int64_t)fi];
+        vis[g] = S.z <= D + lcam[16] ? 255 : 0;
+    }
 }
 
 /* ------------------------------------------------------------------------

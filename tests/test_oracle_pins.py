@@ -837,3 +837,273 @@ def test_cell_visibility_keeps_every_cell_a_sampled_point_shows():
                 if seen:
                     assert vis[cz, cy_, cx_], (cz, cy_, cx_)
     assert not vis.all()
+
+
+# ---------------------------------------------------------------- SH relighting (Sec. 3.4.1)
+def _sh_light(env=None, direction=(0.0, 1.0, 0.0), radiance=(0.0, 0.0, 0.0)):
+    L = np.zeros(56)
+    if env is not None:
+        L[:48] = np.asarray(env, dtype=float).reshape(48)
+    d = np.asarray(direction, dtype=float)
+    L[48:51] = d / np.linalg.norm(d)
+    L[52:55] = radiance
+    return L
+
+
+def _visible(pr, v=0):
+    return np.nonzero(pr[v, :, 14] > pr[v, :, 12])[0]
+
+
+def test_relit_unit_lighting_is_orthonormality_of_the_basis():
+    """Environment e_j (channel 0) against transfer e_k gives delta_jk: the
+    exact sphere rule and the orthonormal basis together."""
+    n = 256
+    sc = gi.make_scene(n, 3, 40)
+    sc[0, :, :3] *= 0.3
+    sc[3:, :, :] = 0.0
+    rows = gi.planes_to_rows(sc)
+    for g in range(n):
+        rows[g, 12 + 3 * (g % 16)] = 1.0  # transfer coefficient k = g % 16, channel 0
+    cams = gi.ring_cameras(1, 64, 64)
+    for j in (0, 2, 5, 9, 15):
+        env = np.zeros((16, 3)); env[j, 0] = 1.0
+        pr = O.project(gi.rows_to_planes(rows), 3, cams, dyn={"sh_light": _sh_light(env)})
+        vis = _visible(pr)
+        assert len(vis) > 200
+        k = vis % 16
+        np.testing.assert_allclose(pr[0, vis, 8], 0.5 + (k == j), atol=1e-13)
+        np.testing.assert_allclose(pr[0, vis, 9:11], 0.5, atol=1e-13)
+
+
+def test_relit_environment_term_matches_dense_integration_in_scipy():
+    """int T(w) Lenv(R_g w) dw by numpy's 24-point Gauss-Legendre x 48
+    azimuths with scipy's spherical harmonics and rotation."""
+    rng = np.random.default_rng(41)
+    n = 6
+    sc = gi.make_scene(n, 3, 41, sh_std=0.5)
+    sc[0, :, :3] *= 0.3
+    env = rng.normal(size=(16, 3))
+    q = rng.normal(size=4); q /= np.linalg.norm(q)
+    d = {"sh_light": _sh_light(env), "group": np.zeros(n, dtype=np.int32),
+         "poses": np.array([[*q, 0.0, 0.0, 0.0, 0.0]])}
+    pr = O.project(sc, 3, gi.ring_cameras(1, 64, 64), dyn=d)
+    Rg = Rotation.from_quat([q[1], q[2], q[3], q[0]]).as_matrix()
+    z, wz = np.polynomial.legendre.leggauss(24)
+    rows = gi.planes_to_rows(sc).astype(np.float64)
+    acc = np.zeros((n, 3))
+    for zi, wi in zip(z, wz):
+        for j in range(48):
+            ph = 2 * math.pi * j / 48
+            w = np.array([math.sqrt(1 - zi * zi) * math.cos(ph), math.sqrt(1 - zi * zi) * math.sin(ph), zi])
+            Yo = _real_sh_scipy(w)
+            Yw = _real_sh_scipy(Rg @ w)
+            Le = Yw @ env
+            T = rows[:, 12:60].reshape(n, 16, 3).transpose(0, 2, 1) @ Yo
+            acc += wi * (2 * math.pi / 48) * T * Le
+    expect = np.maximum(acc + 0.5, 0.0)
+    vis = _visible(pr)
+    assert len(vis) == n
+    np.testing.assert_allclose(pr[0, :, 8:11], expect, atol=1e-11)
+
+
+def test_relit_light_along_the_view_reproduces_view_dependent_colour():
+    """No environment, unit radiance from the view direction, fully visible:
+    int T(w) delta(R_g w, dir) dw = T(R_g^T dir), the view-dependent colour."""
+    n = 24
+    sc = gi.make_scene(n, 3, 42, sh_std=0.4)
+    cams = gi.ring_cameras(1, 64, 64)
+    dd = _dyn(n, 3, 8, normals=False)
+    base = O.project(sc, 3, cams, dyn=dd)
+    rows = gi.planes_to_rows(sc).astype(np.float64)
+    checked = 0
+    for g in _visible(base):
+        q = dd["poses"][dd["group"][g], :4]
+        Rg = Rotation.from_quat([q[1], q[2], q[3], q[0]]).as_matrix()
+        mu = Rg @ rows[g, :3] + dd["poses"][dd["group"][g], 4:7]
+        centre = -cams["R"][0].T @ cams["t"][0]
+        dirv = (mu - centre) / np.linalg.norm(mu - centre)
+        d = {"sh_light": _sh_light(None, dirv, (1.0, 1.0, 1.0)), "group": dd["group"], "poses": dd["poses"]}
+        pr = O.project(sc, 3, cams, dyn=d)
+        np.testing.assert_allclose(pr[0, g, 8:12], base[0, g, 8:12], atol=1e-12)
+        checked += 1
+    assert checked > 15
+
+
+def test_relit_visibility_attenuates_the_direct_light_only():
+    n = 40
+    sc = gi.make_scene(n, 2, 43)
+    sc[3, :, :3] += 4.0  # a large DC transfer keeps every channel above the clamp
+    cams = gi.ring_cameras(1, 64, 64)
+    rng = np.random.default_rng(43)
+    env = rng.normal(0, 0.3, (16, 3))
+    env[0] = 1.0  # a positive ambient term
+    L = _sh_light(env, (0.2, 0.9, -0.3), (0.9, 0.7, 0.5))
+    out = {}
+    for v in (0, 128, 255):
+        out[v] = O.project(sc, 2, cams, dyn={"sh_light": L, "visibility": np.full(n, v, np.uint8)})[0, :, 8:11]
+    assert np.all(out[0] > 0)
+    np.testing.assert_allclose(out[128], out[0] + 128 / 255 * (out[255] - out[0]), atol=1e-12)
+    none = O.project(sc, 2, cams, dyn={"sh_light": L})[0, :, 8:11]
+    np.testing.assert_array_equal(none, out[255])
+    # no light at all: only the offset is left
+    dark = O.project(sc, 2, cams, dyn={"sh_light": _sh_light()})[0, _visible(O.project(sc, 2, cams)), 8:11]
+    np.testing.assert_allclose(dark, 0.5, atol=1e-13)
+
+
+def test_relit_gradient_matches_central_differences():
+    n = 40
+    sc = gi.make_scene(n, 2, 44, sh_std=0.3).astype(np.float64)
+    sc[1, :, :3] += 1.2
+    sc[0, :, :3] *= 0.6
+    cams = gi.ring_cameras(2, 40, 32)
+    rng = np.random.default_rng(44)
+    dd = _dyn(n, 3, 9, normals=False)
+    d = {"sh_light": _sh_light(rng.normal(0, 0.4, (16, 3)), (0.3, 0.8, 0.2), (0.8, 0.6, 0.9)),
+         "visibility": rng.integers(0, 256, n).astype(np.uint8), "group": dd["group"], "poses": dd["poses"]}
+    tgt = gi.make_scene(n, 2, 45).astype(np.float64)
+    tgt[1, :, :3] += 1.2
+    tgt[0, :, :3] *= 0.6
+    target = O.forward(tgt, 2, cams, dyn=d)["image"]
+    r = O.loss_and_grad(sc, 2, cams, target, dyn=d)
+    g = r["dparams"]
+    errs, checked, tries = [], 0, 0
+    while checked < 40 and tries < 400:
+        tries += 1
+        p, i, c = int(rng.integers(0, 10)), int(rng.integers(0, n)), int(rng.integers(0, 4))
+        if (p == 1 and c == 3) or np.all(r["proj"][:, i, 14] == 0):
+            continue
+        th = sc[p, i, c]
+        h = 1e-6 * max(1.0, abs(th))
+        sp_ = sc.copy(); sp_[p, i, c] = th + h
+        sm_ = sc.copy(); sm_[p, i, c] = th - h
+        fp, fm = O.forward(sp_, 2, cams, dyn=d), O.forward(sm_, 2, cams, dyn=d)
+        if not (np.array_equal(fp["n_contrib"], r["n_contrib"]) and np.array_equal(fm["n_contrib"], r["n_contrib"])
+                and np.array_equal(fp["proj"][..., 11:16], r["proj"][..., 11:16])
+                and np.array_equal(fm["proj"][..., 11:16], r["proj"][..., 11:16])):
+            continue
+        Lp = O.loss(fp["image"], target, 2, 32, 40)[0]
+        Lm = O.loss(fm["image"], target, 2, 32, 40)[0]
+        fwd, bwd = (Lp - r["loss"]) / h, (r["loss"] - Lm) / h
+        if abs(fwd - bwd) > 1e-3 * max(abs(fwd), abs(bwd), 1e-8):
+            continue
+        fd = (Lp - Lm) / (2 * h)
+        noise = 100 * np.finfo(float).eps * abs(r["loss"]) / h
+        errs.append(max(abs(fd - g[p, i, c]) - noise, 0.0) / max(abs(fd), abs(g[p, i, c]), 1e-12))
+        checked += 1
+    assert checked >= 30
+    assert max(errs) <= 1e-5, sorted(errs)[-3:]
+
+
+# ---------------------------------------------------------------- light visibility (Sec. 3.4.1)
+def _light_cam(R, origin=(0.0, 0.0, 0.0), texel=0.05, W=48, H=40, alpha_min=0.5, bias=0.01):
+    return {"R": np.asarray(R, dtype=float), "origin": np.asarray(origin, dtype=float), "texel": texel,
+            "width": W, "height": H, "alpha_min": alpha_min, "bias": bias}
+
+
+def _tilted_R():
+    R, _ = gi.look_at((1.0, 2.0, 0.5))
+    return R
+
+
+def test_light_depth_bounding_box_equals_brute_force():
+    sc = gi.make_scene(300, 0, 46)
+    sc[1, :, :3] += 1.5
+    lc = _light_cam(_tilted_R())
+    for dyn in (None, _dyn(300, 4, 10, normals=False)):
+        a = O.light_depth(sc, lc, dyn=dyn)
+        b = O.light_depth(sc, lc, dyn=dyn, brute=True)
+        np.testing.assert_array_equal(a, b)
+        assert np.isfinite(a).mean() > 0.2
+
+
+def _lone_gaussian(mean, scales, quat, logit):
+    sc = np.zeros((15, 1, 4), dtype=np.float64)
+    sc[0, 0] = [*mean, logit]
+    sc[1, 0, :3] = np.log(scales)
+    sc[2, 0] = quat
+    return sc
+
+
+def test_light_depth_footprint_closed_forms():
+    """An isotropic Gaussian covers the disc |d|^2 <= tau ((s/h)^2 + 0.3); an
+    axis-aligned anisotropic one covers the ellipse with the semi-axes its
+    scales give along the light camera's x and y."""
+    R = np.eye(3)
+    h = 0.02
+    lc = _light_cam(R, texel=h, W=64, H=48)
+    o = 0.95
+    logit = math.log(o / (1 - o))
+    tau = 2 * math.log(o / 0.5)
+    ii, jj = np.meshgrid(np.arange(64) + 0.5, np.arange(48) + 0.5)
+    # isotropic; the quaternion is irrelevant
+    mean = np.array([0.013, -0.021, 0.7])
+    sc = _lone_gaussian(mean, [0.1, 0.1, 0.1], [0.3, 0.5, -0.2, 0.7], logit)
+    u, v = mean[0] / h + 32, mean[1] / h + 24
+    r2 = (ii - u) ** 2 + (jj - v) ** 2
+    lim = tau * ((0.1 / h) ** 2 + 0.3)
+    D = O.light_depth(sc, lc)
+    sure = r2 < lim * (1 - 1e-9)
+    out = r2 > lim * (1 + 1e-9)
+    assert sure.sum() > 50
+    assert np.all(D[sure] == mean[2]) and np.all(np.isinf(D[out]))
+    # anisotropic: rotate 90 degrees about z, so the Gaussian's x axis lies along the map's y
+    sx, sy = 0.15, 0.05
+    qz = [math.cos(math.pi / 4), 0.0, 0.0, math.sin(math.pi / 4)]
+    sc = _lone_gaussian(mean, [sx, sy, 0.01], qz, logit)
+    qf = (ii - u) ** 2 / ((sy / h) ** 2 + 0.3) + (jj - v) ** 2 / ((sx / h) ** 2 + 0.3)
+    D = O.light_depth(sc, lc)
+    sure = qf < tau * (1 - 1e-9)
+    out = qf > tau * (1 + 1e-9)
+    assert sure.sum() > 50
+    assert np.all(D[sure] == mean[2]) and np.all(np.isinf(D[out]))
+    # below alpha_min nothing is covered
+    sc[0, 0, 3] = math.log(0.4 / 0.6)
+    assert np.all(np.isinf(O.light_depth(sc, lc)))
+
+
+def test_light_depth_is_invariant_under_a_rigid_motion_of_scene_and_light():
+    """Moving every Gaussian by (R_g, t_g) and the light camera by the same
+    motion (R_l' = R_l R_g^T, origin' = R_g origin + t_g) leaves the map as it was."""
+    sc = gi.make_scene(200, 0, 47)
+    sc[1, :, :3] += 1.5
+    lc = _light_cam(_tilted_R(), origin=(0.1, -0.05, 0.2))
+    q = np.array([0.8, -0.3, 0.4, 0.33]); q /= np.linalg.norm(q)
+    t = np.array([0.2, -0.1, 0.15])
+    Rg = Rotation.from_quat([q[1], q[2], q[3], q[0]]).as_matrix()
+    d = {"group": np.zeros(200, dtype=np.int32), "poses": np.array([[*q, *t, 0.0]])}
+    lc2 = dict(lc)
+    lc2["R"] = lc["R"] @ Rg.T
+    lc2["origin"] = Rg @ lc["origin"] + t
+    moved = O.light_depth(sc, lc2, dyn=d)
+    lo = O.light_depth(sc, lc, slack=1e-9)
+    hi = O.light_depth(sc, lc, slack=-1e-9)
+    fin = np.isfinite(moved)
+    assert np.all((moved >= lo - 1e-12) | ~fin) and np.all((moved <= hi + 1e-12) | np.isinf(hi))
+    assert fin.mean() > 0.2
+
+
+def test_light_visibility_occluder_scene():
+    """A large opaque Gaussian at depth 0.5 shadows a small one behind it at
+    depth 1.5; itself, a small Gaussian beside it, one outside the map and one
+    behind a faint (alpha < alpha_min) Gaussian are lit."""
+    R = np.eye(3)
+    lc = _light_cam(R, texel=0.02, W=64, H=64, bias=0.01)
+    big = _lone_gaussian([0.0, 0.0, 0.5], [0.15, 0.15, 0.02], [1, 0, 0, 0], 4.0)
+    parts = [big,
+             _lone_gaussian([0.01, -0.01, 1.5], [0.01] * 3, [1, 0, 0, 0], 4.0),    # shadowed
+             _lone_gaussian([0.5, 0.5, 1.5], [0.01] * 3, [1, 0, 0, 0], 4.0),       # beside: lit
+             _lone_gaussian([2.0, 0.0, 1.5], [0.01] * 3, [1, 0, 0, 0], 4.0),       # outside the map: lit
+             _lone_gaussian([-0.4, 0.4, 0.2], [0.1] * 3, [1, 0, 0, 0], -2.0),      # faint occluder
+             _lone_gaussian([-0.4, 0.4, 1.0], [0.01] * 3, [1, 0, 0, 0], 4.0)]      # behind the faint one: lit
+    sc = np.concatenate(parts, axis=1)
+    D = O.light_depth(sc, lc)
+    vis, uvz = O.light_visibility(sc, lc, D)
+    np.testing.assert_array_equal(vis, [255, 0, 255, 255, 255, 255])
+    np.testing.assert_allclose(uvz[1], [0.01 / 0.02 + 32, -0.01 / 0.02 + 32, 1.5], atol=1e-12)
+    # every Gaussian alone in the scene is lit (bias >= 0)
+    for g in range(sc.shape[1]):
+        one = sc[:, g:g + 1]
+        assert O.light_visibility(one, lc, O.light_depth(one, lc))[0][0] == 255
+    # an empty map (+inf) lights everything
+    v2, _ = O.light_visibility(sc, lc, np.full((64, 64), np.inf))
+    assert np.all(v2 == 255)
