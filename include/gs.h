@@ -107,6 +107,28 @@ typedef struct gs_precull {
     int32_t _pad;
 } gs_precull;
 
+/* SH relighting (Sec. 3.4.1).  The Gaussian's SH coefficients are read as
+ * its diffuse radiance transfer T_c(w) = sum_k c_{k,c} Y_k(w) in its object's
+ * frame, and the lighting is given as SH coefficients as well.  The colour is
+ * the integral over the sphere of the transfer times the incident lighting,
+ * seen from the object's frame (rotation R_g of gs_dynamics, identity for a
+ * static scene):
+ *   rgb_c = max(0, sum_k c_{k,c} (e'_{k,c} + v E_c Y_k(R_g^T l)) + 0.5),
+ * e' the world-frame environment coefficients e rotated into the object's
+ * frame (Lenv'(w) = Lenv(R_g w)), l the unit vector towards the directional
+ * light of radiance E_c, v = visibility / 255 its per-Gaussian light
+ * visibility (only the direct light is attenuated).  The colour does not
+ * depend on the view; the SH coefficients get its gradient, the mean none.
+ * Exclusive with the Lambertian factor of gs_dynamics (normals must be NULL).
+ * The buffers live in device memory so that a captured graph sees each
+ * frame's values. */
+typedef struct gs_lighting {
+    const float* light;          /* device [56]: e[16][3] (k-major, rgb), then l (x, y, z, 0),
+                                    then E (r, g, b, 0) */
+    const uint8_t* visibility;   /* device [n] (train step: [n + n_frozen], active pool
+                                    first), 255 = lit; NULL: every Gaussian lit */
+} gs_lighting;
+
 typedef struct gs_scene {
     int64_t n;           /* number of Gaussians, >= 0 */
     int32_t sh_degree;   /* 0..3 */
@@ -114,7 +136,22 @@ typedef struct gs_scene {
     const float* params; /* device, [15][n][4] */
     const gs_dynamics* dyn; /* host pointer; NULL: static scene */
     const gs_precull* precull; /* host pointer; NULL: every Gaussian takes part */
+    const gs_lighting* lighting; /* host pointer; NULL: view-dependent SH colour */
 } gs_scene;
+
+/* Orthographic camera attached to the directional light (Sec. 3.4.1).  A
+ * world point x maps to x_l = R (x - origin); texel coordinates
+ * u = x_l / texel + width / 2, v = y_l / texel + height / 2, light depth
+ * z_l; texel (i, j) is sampled at (i + 0.5, j + 0.5).  72 bytes. */
+typedef struct gs_light_camera {
+    float R[9];          /* row-major world -> light rotation: map x, map y, depth axis */
+    float origin[3];     /* world point at the map's centre and depth 0 */
+    float texel;         /* world units per texel, > 0 */
+    int32_t width, height; /* texels, 1..16384 each */
+    float alpha_min;     /* footprint threshold, 0 < alpha_min <= 0.99 */
+    float bias;          /* depth bias of the visibility test (world units), >= 0 */
+    float _pad;
+} gs_light_camera;
 
 /* ---------------------------------------------------------------- context */
 
@@ -199,6 +236,24 @@ gs_status_t gs_cell_visibility(gs_ctx* ctx, const gs_camera* d_cams, const gs_ca
                                const float* d_depth, const gs_precull* grid, uint8_t* d_cell_visible,
                                void* stream);
 size_t gs_precull_workspace_size(const gs_camera* host_cams, int32_t n_views);
+/* Light-space depth map (Sec. 3.4.1), rendered from the Gaussians of
+ * `scene` (the paper's engine renders it from its meshes).  Texel (i, j) of
+ * depth [height][width] (float32, device) receives the smallest light depth
+ * z_l of the Gaussians whose splat alpha at the texel centre reaches
+ * alpha_min: o exp(-q / 2) >= alpha_min, q = d^T Sigma2^-1 d, Sigma2 the
+ * orthographic image of the world covariance in texel units plus 0.3 I,
+ * d = texel centre - (u, v) of the mean.  Texels no Gaussian covers hold
+ * +inf.  accumulate = 0 first fills the map with +inf; 1 adds this scene's
+ * Gaussians to the map as it is (a second pool).  The scene's dynamics apply;
+ * preculling and lighting are ignored (every Gaussian casts a shadow).  The
+ * result does not depend on the order of the Gaussians.  No workspace. */
+gs_status_t gs_light_depth_map(gs_ctx* ctx, const gs_scene* scene, const gs_light_camera* lcam, float* depth,
+                               int32_t accumulate, void* stream);
+/* Per-Gaussian light visibility (Sec. 3.4.1): visibility[i] (uint8, device)
+ * = 255 when the mean of Gaussian i falls outside the map or its light depth
+ * is at most depth[floor(v)][floor(u)] + bias, else 0.  No workspace. */
+gs_status_t gs_light_visibility(gs_ctx* ctx, const gs_scene* scene, const gs_light_camera* lcam,
+                                const float* depth, uint8_t* visibility, void* stream);
 /* Reads and clears the device status word (synchronises `stream`).
  * *status receives the first error a kernel recorded since the last read
  * (GS_OK if none); *detail receives the required size for GS_ERR_CAPACITY. */
@@ -425,6 +480,7 @@ typedef struct gs_train_cfg {
     const gs_precull* precull; /* host pointer; NULL: no preculling.  Gaussians of
                                culled cells are not rendered and get no Adam
                                update (their parameters and moments stay) */
+    const gs_lighting* lighting; /* host pointer; NULL: view-dependent SH colour */
 } gs_train_cfg;
 
 /* One whole optimisation step over all V reference views (Sec. 3.1: "iterates

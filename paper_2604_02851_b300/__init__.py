@@ -200,23 +200,133 @@ class Precull:
         return self.visible
 
 
-def _scene(params, sh_degree, dyn: "Dynamics | None" = None, precull: "Precull | None" = None):
+class Lighting:
+    """SH relighting inputs (gs_lighting, Sec. 3.4.1): the world-frame
+    environment SH e[16][3], the unit vector towards the directional light and
+    its radiance in one device buffer of 56 floats, and an optional uint8
+    light visibility per Gaussian (255 = lit).  set() overwrites the buffer in
+    place and update_visibility() recomputes the visibility from a light-space
+    depth map, so a captured graph sees each frame's values."""
+
+    def __init__(self, n: int, env=None, direction=(0.0, 1.0, 0.0), radiance=(1.0, 1.0, 1.0),
+                 with_visibility: bool = True, device="cuda"):
+        torch = _torch()
+        self.light = torch.zeros(56, dtype=torch.float32, device=device)
+        self.visibility = (torch.full((max(int(n), 1),), 255, dtype=torch.uint8, device=device)
+                           if with_visibility else None)
+        self.n = int(n)
+        self.set(env if env is not None else np.zeros((16, 3)), direction, radiance)
+        self.struct = _lib.gs_lighting(light=self.light.data_ptr(),
+                                       visibility=self.visibility.data_ptr() if with_visibility else None)
+
+    @staticmethod
+    def pack(env, direction, radiance) -> np.ndarray:
+        buf = np.zeros(56, dtype=np.float32)
+        buf[:48] = np.asarray(env, dtype=np.float32).reshape(48)
+        d = np.asarray(direction, dtype=np.float64)
+        buf[48:51] = d / np.linalg.norm(d)
+        buf[52:55] = np.asarray(radiance, dtype=np.float32)
+        return buf
+
+    def set(self, env=None, direction=None, radiance=None):
+        torch = _torch()
+        cur = self.light.cpu().numpy()
+        e = cur[:48] if env is None else env
+        d = cur[48:51] if direction is None else direction
+        r = cur[52:55] if radiance is None else radiance
+        self.light.copy_(torch.from_numpy(self.pack(e, d, r)))
+
+    def update_visibility(self, ctx, params, lcam, depth=None, dyn=None, stream=None, frozen=None):
+        """Render the light-space depth map of params (and the frozen pool, if
+        given) and test every centre against it; returns the depth map."""
+        depth = gs_light_depth_map(ctx, params, lcam, depth, dyn=dyn, stream=stream)
+        if frozen is not None and frozen.shape[1] > 0:
+            gs_light_depth_map(ctx, frozen, lcam, depth, accumulate=True, stream=stream)
+        n = params.shape[1]
+        gs_light_visibility(ctx, params, lcam, depth, dyn=dyn, out=self.visibility[:n], stream=stream)
+        if frozen is not None and frozen.shape[1] > 0:
+            gs_light_visibility(ctx, frozen, lcam, depth, out=self.visibility[n:n + frozen.shape[1]],
+                                stream=stream)
+        return depth
+
+
+def light_camera(R=None, origin=(0.0, 0.0, 0.0), texel=0.01, width=1024, height=1024, alpha_min=0.5,
+                 bias=0.01, direction=None, extent=None):
+    """gs_light_camera.  Either R (world -> light rows: map x, map y, depth
+    axis) or direction (unit vector towards the light: the depth axis points
+    along the light's travel, -direction); extent (world units covered by the
+    larger map side) sets texel when given."""
+    if R is None:
+        d = -np.asarray(direction, dtype=np.float64)
+        d /= np.linalg.norm(d)
+        up = np.array([0.0, 1.0, 0.0]) if abs(d[1]) < 0.9 else np.array([1.0, 0.0, 0.0])
+        x = np.cross(up, d); x /= np.linalg.norm(x)
+        y = np.cross(d, x)
+        R = np.stack([x, y, d])
+    if extent is not None:
+        texel = float(extent) / max(int(width), int(height))
+    c = _lib.gs_light_camera()
+    Rf = np.asarray(R, dtype=np.float64).reshape(9)
+    for i in range(9):
+        c.R[i] = float(Rf[i])
+    for i in range(3):
+        c.origin[i] = float(origin[i])
+    c.texel, c.width, c.height = float(texel), int(width), int(height)
+    c.alpha_min, c.bias = float(alpha_min), float(bias)
+    return c
+
+
+def light_camera_dict(c) -> dict:
+    """The fields of a gs_light_camera as a dict of floats / ints."""
+    return {"R": np.array(c.R[:], dtype=np.float64).reshape(3, 3), "origin": np.array(c.origin[:], dtype=np.float64),
+            "texel": float(c.texel), "width": int(c.width), "height": int(c.height),
+            "alpha_min": float(c.alpha_min), "bias": float(c.bias)}
+
+
+def _scene(params, sh_degree, dyn: "Dynamics | None" = None, precull: "Precull | None" = None,
+           lighting: "Lighting | None" = None):
     n = params.shape[1] if params is not None else 0
     sc = _lib.gs_scene(n=n, sh_degree=sh_degree, params=params.data_ptr() if n else None)
     if dyn is not None:
         sc.dyn = C.pointer(dyn.struct)
     if precull is not None:
         sc.precull = C.pointer(precull.struct)
+    if lighting is not None:
+        sc.lighting = C.pointer(lighting.struct)
     return sc
 
 
+def gs_light_depth_map(ctx, params, lcam, depth=None, accumulate=False, dyn=None, stream=None):
+    """Light-space depth map [height][width] float32 (+inf where empty)."""
+    torch = _torch()
+    if depth is None:
+        depth = torch.empty((lcam.height, lcam.width), dtype=torch.float32, device=params.device)
+        accumulate = False
+    sc = _scene(params, 0, dyn)
+    check("gs_light_depth_map", _lib.lib().gs_light_depth_map(ctx.ptr, C.byref(sc), C.byref(lcam), _ptr(depth),
+                                                              int(bool(accumulate)), _stream(stream)))
+    return depth
+
+
+def gs_light_visibility(ctx, params, lcam, depth, dyn=None, out=None, stream=None):
+    """uint8 [n]: 255 where the centre is lit, 0 where the map occludes it."""
+    torch = _torch()
+    if out is None:
+        out = torch.empty(max(params.shape[1], 1), dtype=torch.uint8, device=params.device)
+    sc = _scene(params, 0, dyn)
+    check("gs_light_visibility", _lib.lib().gs_light_visibility(ctx.ptr, C.byref(sc), C.byref(lcam), _ptr(depth),
+                                                                _ptr(out), _stream(stream)))
+    return out[:params.shape[1]]
+
+
 # ------------------------------------------------------------------ entry points
-def gs_project(ctx, params, sh_degree, d_cams, n_views, proj=None, stream=None, dyn=None, precull=None):
+def gs_project(ctx, params, sh_degree, d_cams, n_views, proj=None, stream=None, dyn=None, precull=None,
+               lighting=None):
     torch = _torch()
     n = params.shape[1]
     if proj is None:
         proj = torch.empty((n_views, n, PROJ_STRIDE), dtype=torch.float32, device=params.device)
-    sc = _scene(params, sh_degree, dyn, precull)
+    sc = _scene(params, sh_degree, dyn, precull, lighting)
     check("gs_project", _lib.lib().gs_project(ctx.ptr, C.byref(sc), _ptr(d_cams), n_views, _ptr(proj),
                                               _stream(stream)))
     return proj
@@ -285,12 +395,12 @@ def gs_raster_bwd(ctx, proj, d_cams, n_views, n, total_tiles, sorted_vals, range
 
 
 def gs_project_bwd(ctx, params, sh_degree, d_cams, n_views, proj, grad2d, dparams=None, accumulate=False,
-                   stream=None, dyn=None):
+                   stream=None, dyn=None, lighting=None):
     torch = _torch()
     if dparams is None:
         dparams = torch.empty_like(params)
         accumulate = False
-    sc = _scene(params, sh_degree, dyn)
+    sc = _scene(params, sh_degree, dyn, None, lighting)
     check("gs_project_bwd", _lib.lib().gs_project_bwd(ctx.ptr, C.byref(sc), _ptr(d_cams), n_views, _ptr(proj),
                                                       _ptr(grad2d), _ptr(dparams), int(bool(accumulate)),
                                                       _stream(stream)))
@@ -298,14 +408,14 @@ def gs_project_bwd(ctx, params, sh_degree, d_cams, n_views, proj, grad2d, dparam
 
 
 def gs_render_bwd(ctx, params, sh_degree, d_cams, n_views, total_tiles, proj, sorted_vals, ranges, T_final,
-                  n_contrib, dimage, bg=None, grad2d=None, dparams=None, stream=None, dyn=None):
+                  n_contrib, dimage, bg=None, grad2d=None, dparams=None, stream=None, dyn=None, lighting=None):
     torch = _torch()
     n = params.shape[1]
     if grad2d is None:
         grad2d = torch.empty((n_views, n, GRAD2D_STRIDE), dtype=torch.float32, device=params.device)
     if dparams is None:
         dparams = torch.empty_like(params)
-    sc = _scene(params, sh_degree, dyn)
+    sc = _scene(params, sh_degree, dyn, None, lighting)
     check("gs_render_bwd", _lib.lib().gs_render_bwd(ctx.ptr, C.byref(sc), _ptr(d_cams), n_views, total_tiles,
                                                     _ptr(proj), _ptr(sorted_vals), _ptr(ranges), _bg(bg),
                                                     _ptr(T_final), _ptr(n_contrib), _ptr(dimage), _ptr(grad2d),
@@ -390,18 +500,18 @@ def gs_apply_delta(ctx, params, d_records, d_count, stream=None):
 
 
 def gs_render_batch(ctx, params, sh_degree, d_cams, n_requests, total_tiles, keys_cap, npix, bg=None,
-                    image=None, stream=None, dyn=None, precull=None):
+                    image=None, stream=None, dyn=None, precull=None, lighting=None):
     torch = _torch()
     if image is None:
         image = torch.empty(3 * npix, dtype=torch.float32, device=params.device)
-    sc = _scene(params, sh_degree, dyn, precull)
+    sc = _scene(params, sh_degree, dyn, precull, lighting)
     check("gs_render_batch", _lib.lib().gs_render_batch(ctx.ptr, C.byref(sc), _ptr(d_cams), n_requests,
                                                         total_tiles, keys_cap, _bg(bg), _ptr(image),
                                                         _stream(stream)))
     return image
 
 
-def gs_autotune(ctx, params, sh_degree, cams, keys_cap, reps=3, stream=None, dyn=None):
+def gs_autotune(ctx, params, sh_degree, cams, keys_cap, reps=3, stream=None, dyn=None, lighting=None):
     """Time the render/adjoint path over the tunables (gs_autotune) and leave
     `ctx` set to the fastest.  Returns (best, entries): dicts with binning,
     sort_bits, sort_items, raster_threads and ms."""
@@ -410,7 +520,7 @@ def gs_autotune(ctx, params, sh_degree, cams, keys_cap, reps=3, stream=None, dyn
     d_cams = cameras_to_device(packed, params.device)
     out = (_lib.gs_tune_entry * 64)()
     cnt = C.c_int32(0)
-    sc = _scene(params, sh_degree, dyn)
+    sc = _scene(params, sh_degree, dyn, None, lighting)
     check("gs_autotune", _lib.lib().gs_autotune(ctx.ptr, C.byref(sc), _ptr(d_cams), host, V, int(keys_cap),
                                                 int(reps), out, 64, C.byref(cnt), _stream(stream)))
     names = {v: k for k, v in BINNING.items()}
@@ -431,9 +541,11 @@ def train_io(params, grads, m, v, baseline, targets, image, d_loss, d_idx, d_rec
 
 def train_cfg(n, sh_degree, n_views, width, height, keys_cap, w_l1=0.8, w_ssim=0.2, bg=(0.0, 0.0, 0.0),
               delta_thr=1e-3, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, dyn: "Dynamics | None" = None,
-              n_frozen: int = 0, precull: "Precull | None" = None):
+              n_frozen: int = 0, precull: "Precull | None" = None, lighting: "Lighting | None" = None):
     cfg = _lib.gs_train_cfg()
     cfg.n_frozen = int(n_frozen)
+    if lighting is not None:
+        cfg.lighting = C.pointer(lighting.struct)
     if precull is not None:
         cfg.precull = C.pointer(precull.struct)
     if dyn is not None:

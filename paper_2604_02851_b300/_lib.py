@@ -25,7 +25,7 @@ EXPORTS = (
     "gs_train_graph_capture", "gs_graph_launch", "gs_train_step_events",
     "gs_train_graph_capture_events", "gs_extract_delta_noalloc", "gs_autotune", "gs_tensor_record_bytes",
     "gs_extract_tensor_delta", "gs_apply_tensor_delta", "gs_apply_delta", "gs_cell_visibility",
-    "gs_precull_workspace_size",
+    "gs_precull_workspace_size", "gs_light_depth_map", "gs_light_visibility",
 )
 
 
@@ -51,9 +51,19 @@ class gs_precull(C.Structure):
                 ("dims", C.c_int32 * 3), ("_pad", C.c_int32)]
 
 
+class gs_lighting(C.Structure):
+    _fields_ = [("light", C.c_void_p), ("visibility", C.c_void_p)]
+
+
+class gs_light_camera(C.Structure):
+    _fields_ = [("R", C.c_float * 9), ("origin", C.c_float * 3), ("texel", C.c_float), ("width", C.c_int32),
+                ("height", C.c_int32), ("alpha_min", C.c_float), ("bias", C.c_float), ("_pad", C.c_float)]
+
+
 class gs_scene(C.Structure):
     _fields_ = [("n", C.c_int64), ("sh_degree", C.c_int32), ("_pad", C.c_int32),
-                ("params", C.c_void_p), ("dyn", C.POINTER(gs_dynamics)), ("precull", C.POINTER(gs_precull))]
+                ("params", C.c_void_p), ("dyn", C.POINTER(gs_dynamics)), ("precull", C.POINTER(gs_precull)),
+                ("lighting", C.POINTER(gs_lighting))]
 
 
 class gs_tune_entry(C.Structure):
@@ -80,10 +90,11 @@ class gs_train_cfg(C.Structure):
                 ("width", C.c_int32), ("height", C.c_int32), ("keys_cap", C.c_int64),
                 ("w_l1", C.c_float), ("w_ssim", C.c_float), ("bg", C.c_float * 3),
                 ("delta_thr", C.c_float), ("adam", gs_adam_cfg), ("n_frozen", C.c_int64),
-                ("precull", C.POINTER(gs_precull))]
+                ("precull", C.POINTER(gs_precull)), ("lighting", C.POINTER(gs_lighting))]
 
 
 assert C.sizeof(gs_camera) == 80
+assert C.sizeof(gs_light_camera) == 72
 
 _P = C.c_void_p
 _I32 = C.c_int32
@@ -123,6 +134,8 @@ _SIGS = {
     "gs_apply_delta": [_P, _P, _I64, _P, _P, _P],
     "gs_cell_visibility": [_P, _P, C.POINTER(gs_camera), _I32, _P, C.POINTER(gs_precull), _P, _P],
     "gs_precull_workspace_size": [C.POINTER(gs_camera), _I32],
+    "gs_light_depth_map": [_P, C.POINTER(gs_scene), C.POINTER(gs_light_camera), _P, _I32, _P],
+    "gs_light_visibility": [_P, C.POINTER(gs_scene), C.POINTER(gs_light_camera), _P, _P, _P],
 }
 TRAIN_PHASE_EVENTS = 11
 TRAIN_PHASES = ("project", "depth_sort", "emit", "tile_sort", "render_fwd", "loss", "raster_bwd", "project_bwd",

@@ -53,6 +53,25 @@ bool bad_dyn(const gs_dynamics* d) {
                  (d->normals && !d->light));
 }
 
+bool bad_lighting(const gs_lighting* lt, const gs_dynamics* d) {
+    return lt && (!lt->light || (d && d->normals));
+}
+
+bool bad_light_cam(const gs_light_camera* c) {
+    return !c || !(c->texel > 0.f) || !(c->texel < 3.0e38f) || c->width < 1 || c->width > 16384 || c->height < 1 ||
+           c->height > 16384 || !(c->alpha_min > 0.f) || !(c->alpha_min <= 0.99f) || !(c->bias >= 0.f) ||
+           !(c->bias < 3.0e38f);
+}
+
+// Projection extras of a scene; fills the context's relighting table first
+// when the scene is relit.
+Dyn scene_dyn(gs_ctx* ctx, const gs_dynamics* d, const gs_precull* pc, uint8_t* fwd, const gs_lighting* lt,
+              cudaStream_t st) {
+    const Dyn k = make_dyn(d, pc, fwd, lt, ctx->d_light_tab);
+    if (k.lit_tab) launch_light_table(k, lt->light, ctx->d_light_tab, st);
+    return k;
+}
+
 // Workspace plan of the fused calls (render_batch, train_step).
 struct FusedPlan {
     ViewInfo* vt;
@@ -117,8 +136,14 @@ gs_status_t gs_ctx_create(gs_ctx** out, int device, size_t workspace_bytes) {
         delete c;
         return GS_ERR_OOM;
     }
+    if (cudaMalloc(&c->d_light_tab, sizeof(float) * kMaxGroups * kLitTab) != cudaSuccess) {
+        cudaFree(c->d_status);
+        delete c;
+        return GS_ERR_OOM;
+    }
     cudaMemset(c->d_status, 0, sizeof(DevStatus));
     if (cudaStreamCreateWithFlags(&c->capture_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaFree(c->d_light_tab);
         cudaFree(c->d_status);
         delete c;
         return GS_ERR_CUDA;
@@ -143,6 +168,7 @@ gs_status_t gs_ctx_destroy(gs_ctx* ctx) {
     if (ctx->graph) cudaGraphDestroy(ctx->graph);
     if (ctx->ws) cudaFree(ctx->ws);
     if (ctx->d_status) cudaFree(ctx->d_status);
+    if (ctx->d_light_tab) cudaFree(ctx->d_light_tab);
     if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
     delete ctx;
     return GS_OK;
@@ -229,14 +255,17 @@ gs_status_t gs_project(gs_ctx* ctx, const gs_scene* scene, const gs_camera* d_ca
     if (!ctx || !scene || !d_cams || !proj || bad_views(n_views) || scene->n < 0 ||
         scene->sh_degree < 0 || scene->sh_degree > 3 || (scene->n > 0 && !scene->params))
         return GS_ERR_ARG;
-    if ((int64_t)n_views * scene->n >= (1LL << 32) || bad_dyn(scene->dyn) || bad_precull(scene->precull)) return GS_ERR_ARG;
+    if ((int64_t)n_views * scene->n >= (1LL << 32) || bad_dyn(scene->dyn) || bad_precull(scene->precull) ||
+        bad_lighting(scene->lighting, scene->dyn))
+        return GS_ERR_ARG;
     Carver c(ctx->ws);
     ViewInfo* vt = c.take<ViewInfo>(n_views + 1);
     if (check_ws(ctx, c.off)) return GS_ERR_CAPACITY;
     DeviceGuard g(ctx->device);
     launch_view_table(d_cams, n_views, ctx->tile, vt, -1, ctx->d_status, S(stream));
-    launch_project(scene->params, scene->n, scene->sh_degree, make_dyn(scene->dyn, scene->precull), d_cams, vt, n_views,
-                   ctx->tile, proj, nullptr, S(stream));
+    const Dyn dyn = scene_dyn(ctx, scene->dyn, scene->precull, nullptr, scene->lighting, S(stream));
+    launch_project(scene->params, scene->n, scene->sh_degree, dyn, d_cams, vt, n_views, ctx->tile, proj, nullptr,
+                   S(stream));
     return launch_check();
 }
 
@@ -310,11 +339,12 @@ gs_status_t gs_project_bwd(gs_ctx* ctx, const gs_scene* scene, const gs_camera* 
                            const float* proj, const float* grad2d, float* dparams, int32_t accumulate,
                            void* stream) {
     if (!ctx || !scene || !d_cams || !proj || !grad2d || !dparams || bad_views(n_views) || scene->n < 0 ||
-        scene->sh_degree < 0 || scene->sh_degree > 3 || (scene->n > 0 && !scene->params) || bad_dyn(scene->dyn) || bad_precull(scene->precull))
+        scene->sh_degree < 0 || scene->sh_degree > 3 || (scene->n > 0 && !scene->params) || bad_dyn(scene->dyn) ||
+        bad_precull(scene->precull) || bad_lighting(scene->lighting, scene->dyn))
         return GS_ERR_ARG;
     DeviceGuard g(ctx->device);
-    launch_project_bwd(scene->params, scene->n, scene->sh_degree, make_dyn(scene->dyn, scene->precull), d_cams, n_views, proj,
-                       grad2d, dparams,
+    const Dyn dyn = scene_dyn(ctx, scene->dyn, scene->precull, nullptr, scene->lighting, S(stream));
+    launch_project_bwd(scene->params, scene->n, scene->sh_degree, dyn, d_cams, n_views, proj, grad2d, dparams,
                        accumulate, S(stream));
     return launch_check();
 }
@@ -400,7 +430,8 @@ gs_status_t gs_render_batch(gs_ctx* ctx, const gs_scene* scene, const gs_camera*
                             void* stream) {
     if (!ctx || !scene || !d_cams || !image || bad_views(n_requests) || scene->n < 0 || total_tiles < 1 ||
         keys_cap < 0 || keys_cap >= (1LL << 32) || scene->sh_degree < 0 || scene->sh_degree > 3 ||
-        (scene->n > 0 && !scene->params) || (int64_t)n_requests * scene->n >= (1LL << 32) || bad_dyn(scene->dyn) || bad_precull(scene->precull))
+        (scene->n > 0 && !scene->params) || (int64_t)n_requests * scene->n >= (1LL << 32) || bad_dyn(scene->dyn) ||
+        bad_precull(scene->precull) || bad_lighting(scene->lighting, scene->dyn))
         return GS_ERR_ARG;
     const FusedPlan p0 = plan_fused(nullptr, n_requests, scene->n, keys_cap, total_tiles, 0, 0, 0, false);
     if (check_ws(ctx, p0.bytes)) return GS_ERR_CAPACITY;
@@ -411,8 +442,8 @@ gs_status_t gs_render_batch(gs_ctx* ctx, const gs_scene* scene, const gs_camera*
     carve_sort_scratch(p.sort, n_requests, scene->n, keys_cap, total_tiles, &s);
     const float3 b = bg ? make_float3(bg[0], bg[1], bg[2]) : make_float3(0.f, 0.f, 0.f);
     launch_view_table(d_cams, n_requests, ctx->tile, p.vt, total_tiles, ctx->d_status, st);
-    launch_project(scene->params, scene->n, scene->sh_degree, make_dyn(scene->dyn, scene->precull), d_cams, p.vt, n_requests,
-                   ctx->tile, p.proj,
+    const Dyn dyn = scene_dyn(ctx, scene->dyn, scene->precull, nullptr, scene->lighting, st);
+    launch_project(scene->params, scene->n, scene->sh_degree, dyn, d_cams, p.vt, n_requests, ctx->tile, p.proj,
                    s.dkv[0], st);
     launch_bin_sort(p.proj, p.vt, n_requests, scene->n, keys_cap, total_tiles, ctx->binning, ctx->sort_bits, ctx->sort_items, s, true, nullptr,
                     p.vals, p.ranges, p.n_keys, ctx->d_status, ctx->sm_count, st, nullptr, nullptr, 0,
@@ -445,7 +476,8 @@ gs_status_t gs_train_step_events(gs_ctx* ctx, const gs_camera* d_cams, const gs_
         cfg->keys_cap >= (1LL << 32) || (int64_t)cfg->n_views * cfg->n >= (1LL << 32) || !io->params ||
         !io->grads || !io->adam_m || !io->adam_v || !io->baseline || !io->targets || !io->image ||
         !io->d_loss || !io->d_delta_idx || !io->d_delta_records || !io->d_delta_count || !io->d_step ||
-        bad_dyn(cfg->dyn) || bad_precull(cfg->precull) || cfg->n_frozen < 0 || (cfg->n_frozen > 0 && !io->frozen) ||
+        bad_dyn(cfg->dyn) || bad_precull(cfg->precull) || bad_lighting(cfg->lighting, cfg->dyn) ||
+        cfg->n_frozen < 0 || (cfg->n_frozen > 0 && !io->frozen) ||
         (int64_t)cfg->n_views * (cfg->n + cfg->n_frozen) >= (1LL << 32))
         return GS_ERR_ARG;
     const int V = cfg->n_views;
@@ -464,7 +496,7 @@ gs_status_t gs_train_step_events(gs_ctx* ctx, const gs_camera* d_cams, const gs_
     const float3 b = make_float3(cfg->bg[0], cfg->bg[1], cfg->bg[2]);
     mark(ev, 0, st);
     launch_view_table(d_cams, V, B, p.vt, tt, ctx->d_status, st);
-    const Dyn dyn = make_dyn(cfg->dyn, cfg->precull, p.fwd);
+    const Dyn dyn = scene_dyn(ctx, cfg->dyn, cfg->precull, p.fwd, cfg->lighting, st);
     launch_project(io->params, na, cfg->sh_degree, dyn, d_cams, p.vt, V, B, p.proj, s.dkv[0], st, 0, n);
     if (cfg->n_frozen > 0)
         launch_project(io->frozen, cfg->n_frozen, cfg->sh_degree, dyn, d_cams, p.vt, V, B, p.proj, s.dkv[0], st,
@@ -501,7 +533,8 @@ gs_status_t gs_autotune(gs_ctx* ctx, const gs_scene* scene, const gs_camera* d_c
     if (!ctx || !scene || !d_cams || !host_cams || bad_views(n_views) || scene->n < 0 || scene->sh_degree < 0 ||
         scene->sh_degree > 3 || (scene->n > 0 && !scene->params) || keys_cap < 0 || keys_cap >= (1LL << 32) ||
         (int64_t)n_views * scene->n >= (1LL << 32) || reps < 1 || max_results < 0 ||
-        (max_results > 0 && !results) || bad_dyn(scene->dyn) || bad_precull(scene->precull))
+        (max_results > 0 && !results) || bad_dyn(scene->dyn) || bad_precull(scene->precull) ||
+        bad_lighting(scene->lighting, scene->dyn))
         return GS_ERR_ARG;
     const int V = n_views;
     const int64_t n = scene->n;
@@ -516,7 +549,7 @@ gs_status_t gs_autotune(gs_ctx* ctx, const gs_scene* scene, const gs_camera* d_c
     cudaStream_t st = S(stream);
     SortScratch s;
     carve_sort_scratch(p.sort, V, n, keys_cap, tt, &s);
-    const Dyn dyn = make_dyn(scene->dyn, scene->precull);
+    const Dyn dyn = scene_dyn(ctx, scene->dyn, scene->precull, nullptr, scene->lighting, st);
     // the image is not read back: it goes to the image-gradient buffer, which
     // the adjoint then reads (its cost does not depend on the values)
     float* image = p.dimage;
@@ -590,6 +623,27 @@ gs_status_t gs_autotune(gs_ctx* ctx, const gs_scene* scene, const gs_camera* d_c
         return rc;
     }
     ctx->binning = bb; ctx->sort_bits = bbits; ctx->sort_items = bitems; ctx->raster_tpr = btpr;
+    return launch_check();
+}
+
+gs_status_t gs_light_depth_map(gs_ctx* ctx, const gs_scene* scene, const gs_light_camera* lcam, float* depth,
+                               int32_t accumulate, void* stream) {
+    if (!ctx || !scene || !depth || bad_light_cam(lcam) || scene->n < 0 || (scene->n > 0 && !scene->params) ||
+        bad_dyn(scene->dyn))
+        return GS_ERR_ARG;
+    DeviceGuard g(ctx->device);
+    launch_light_depth(scene->params, scene->n, make_dyn(scene->dyn), *lcam, depth, accumulate ? 0 : 1, S(stream));
+    return launch_check();
+}
+
+gs_status_t gs_light_visibility(gs_ctx* ctx, const gs_scene* scene, const gs_light_camera* lcam,
+                                const float* depth, uint8_t* visibility, void* stream) {
+    if (!ctx || !scene || !depth || bad_light_cam(lcam) || scene->n < 0 ||
+        (scene->n > 0 && (!scene->params || !visibility)) || bad_dyn(scene->dyn))
+        return GS_ERR_ARG;
+    if (scene->n == 0) return GS_OK;
+    DeviceGuard g(ctx->device);
+    launch_light_visibility(scene->params, scene->n, make_dyn(scene->dyn), *lcam, depth, visibility, S(stream));
     return launch_check();
 }
 

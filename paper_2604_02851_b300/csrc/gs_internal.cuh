@@ -71,10 +71,22 @@ struct Dyn {
     float grid_size;
     int grid_dims[3];
     uint8_t* fwd;
+    const float* lit_tab;    // SH relighting: per group kLitTab floats (launch_light_table); nullptr: off
+    const uint8_t* vis;      // light visibility, indexed like the dynamics arrays; nullptr: all lit
 };
 
-inline Dyn make_dyn(const gs_dynamics* d, const gs_precull* pc = nullptr, uint8_t* fwd = nullptr) {
+// Per-group relighting table: the environment coefficients rotated into the
+// object's frame (e'[16][3]), then E_c Y_k(R_g^T l) ([16][3]).
+constexpr int kLitTab = 96;
+constexpr int kMaxGroups = 256;
+
+inline Dyn make_dyn(const gs_dynamics* d, const gs_precull* pc = nullptr, uint8_t* fwd = nullptr,
+                    const gs_lighting* lt = nullptr, const float* lit_tab = nullptr) {
     Dyn k{};
+    if (lt && lt->light && lit_tab) {
+        k.lit_tab = lit_tab;
+        k.vis = lt->visibility;
+    }
     if (pc && pc->cell_visible) {
         k.cell_vis = pc->cell_visible;
         for (int a = 0; a < 3; ++a) { k.grid_o[a] = pc->origin[a]; k.grid_dims[a] = pc->dims[a]; }
@@ -106,6 +118,17 @@ void launch_project(const float* params, int64_t n, int sh_degree, const Dyn& dy
 void launch_project_bwd(const float* params, int64_t n, int sh_degree, const Dyn& dyn, const gs_camera* d_cams,
                         int V, const float* proj, const float* grad2d, float* dparams,
                         int accumulate, cudaStream_t st, int64_t n_out = -1);
+
+// Fills tab ([max(1, n_groups)][kLitTab]) from the device lighting buffer
+// (gs_lighting.light) and the group poses of `dyn`.
+void launch_light_table(const Dyn& dyn, const float* light, float* tab, cudaStream_t st);
+
+// Light-space depth map and per-Gaussian visibility (gs_light_depth_map /
+// gs_light_visibility); dynamics arrays are indexed by Gaussian.
+void launch_light_depth(const float* params, int64_t n, const Dyn& dyn, const gs_light_camera& lc, float* depth,
+                        int clear, cudaStream_t st);
+void launch_light_visibility(const float* params, int64_t n, const Dyn& dyn, const gs_light_camera& lc,
+                             const float* depth, uint8_t* vis, cudaStream_t st);
 
 // Scratch of the bin/sort stage (all device pointers inside the workspace).
 // Sorted items are packed (key << 32 | value).
@@ -222,6 +245,7 @@ struct gs_ctx {
     void* ws = nullptr;
     size_t ws_bytes = 0;
     gs::DevStatus* d_status = nullptr;
+    float* d_light_tab = nullptr;   // [kMaxGroups][kLitTab] relighting table
     cudaStream_t capture_stream = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t graph_exec = nullptr;

@@ -8,196 +8,10 @@
 // One thread owns one Gaussian: its 60 parameters are read once (coalesced
 // float4 planes) and every view is projected from registers, so the model is
 // read from HBM once per step however many reference views there are.
-#include "gs_internal.cuh"
+#include "gauss.cuh"
 
 namespace gs {
 namespace {
-
-// Real SH normalisation constants: sqrt((2l+1)/(4 pi) (l-|m|)!/(l+|m|)!)
-// times the polynomial factor, for the Condon-Shortley-phase real basis.
-constexpr float kY0 = 0.28209479177387814f;   // sqrt(1/(4 pi))
-constexpr float kY1 = 0.48860251190291992f;   // sqrt(3/(4 pi))
-constexpr float kY2a = 1.0925484305920792f;   // sqrt(15/(4 pi))
-constexpr float kY2b = 0.31539156525252005f;  // sqrt(5/(16 pi))
-constexpr float kY2c = 0.54627421529603959f;  // sqrt(15/(16 pi))
-constexpr float kY3a = 0.59004358992664352f;  // sqrt(35/(32 pi))
-constexpr float kY3b = 2.8906114426405538f;   // sqrt(105/(4 pi))
-constexpr float kY3c = 0.45704579946446572f;  // sqrt(21/(32 pi))
-constexpr float kY3d = 0.3731763325901154f;   // sqrt(7/(16 pi))
-constexpr float kY3e = 1.4453057213202769f;   // sqrt(105/(16 pi))
-
-template <int D>
-__device__ __forceinline__ void sh_basis(float x, float y, float z, float* Y) {
-    Y[0] = kY0;
-    if (D >= 1) {
-        Y[1] = -kY1 * y;
-        Y[2] = kY1 * z;
-        Y[3] = -kY1 * x;
-    }
-    if (D >= 2) {
-        const float xx = x * x, yy = y * y, zz = z * z;
-        Y[4] = kY2a * x * y;
-        Y[5] = -kY2a * y * z;
-        Y[6] = kY2b * (2.f * zz - xx - yy);
-        Y[7] = -kY2a * x * z;
-        Y[8] = kY2c * (xx - yy);
-        if (D >= 3) {
-            Y[9] = -kY3a * y * (3.f * xx - yy);
-            Y[10] = kY3b * x * y * z;
-            Y[11] = -kY3c * y * (4.f * zz - xx - yy);
-            Y[12] = kY3d * z * (2.f * zz - 3.f * xx - 3.f * yy);
-            Y[13] = -kY3c * x * (4.f * zz - xx - yy);
-            Y[14] = kY3e * z * (xx - yy);
-            Y[15] = -kY3a * x * (xx - 3.f * yy);
-        }
-    }
-}
-
-// sum_k w_k * grad Y_k at (x, y, z) (gradient of the polynomial forms above).
-template <int D>
-__device__ __forceinline__ float3 sh_basis_vjp(float x, float y, float z, const float* w) {
-    float gx = 0.f, gy = 0.f, gz = 0.f;
-    if (D >= 1) {
-        gy += -kY1 * w[1];
-        gz += kY1 * w[2];
-        gx += -kY1 * w[3];
-    }
-    if (D >= 2) {
-        const float xx = x * x, yy = y * y, zz = z * z;
-        gx += kY2a * y * w[4];                 gy += kY2a * x * w[4];
-        gy += -kY2a * z * w[5];                gz += -kY2a * y * w[5];
-        gx += -2.f * kY2b * x * w[6];          gy += -2.f * kY2b * y * w[6];     gz += 4.f * kY2b * z * w[6];
-        gx += -kY2a * z * w[7];                gz += -kY2a * x * w[7];
-        gx += 2.f * kY2c * x * w[8];           gy += -2.f * kY2c * y * w[8];
-        if (D >= 3) {
-            gx += -kY3a * 6.f * x * y * w[9];
-            gy += -kY3a * 3.f * (xx - yy) * w[9];
-            gx += kY3b * y * z * w[10];  gy += kY3b * x * z * w[10];  gz += kY3b * x * y * w[10];
-            gx += kY3c * 2.f * x * y * w[11];
-            gy += -kY3c * (4.f * zz - xx - 3.f * yy) * w[11];
-            gz += -kY3c * 8.f * y * z * w[11];
-            gx += -kY3d * 6.f * x * z * w[12];
-            gy += -kY3d * 6.f * y * z * w[12];
-            gz += kY3d * (6.f * zz - 3.f * xx - 3.f * yy) * w[12];
-            gx += -kY3c * (4.f * zz - 3.f * xx - yy) * w[13];
-            gy += kY3c * 2.f * x * y * w[13];
-            gz += -kY3c * 8.f * x * z * w[13];
-            gx += 2.f * kY3e * x * z * w[14];  gy += -2.f * kY3e * y * z * w[14];  gz += kY3e * (xx - yy) * w[14];
-            gx += -kY3a * 3.f * (xx - yy) * w[15];
-            gy += kY3a * 6.f * x * y * w[15];
-        }
-    }
-    return make_float3(gx, gy, gz);
-}
-
-struct Cam {
-    float R[9], t[3], fx, fy, cx, cy, near;
-    int W, H;
-};
-
-__device__ __forceinline__ Cam load_cam(const gs_camera* __restrict__ c) {
-    Cam k;
-#pragma unroll
-    for (int i = 0; i < 9; ++i) k.R[i] = __ldg(&c->R[i]);
-#pragma unroll
-    for (int i = 0; i < 3; ++i) k.t[i] = __ldg(&c->t[i]);
-    k.fx = __ldg(&c->fx); k.fy = __ldg(&c->fy); k.cx = __ldg(&c->cx); k.cy = __ldg(&c->cy);
-    k.near = __ldg(&c->near_plane);
-    k.W = __ldg(&c->width); k.H = __ldg(&c->height);
-    return k;
-}
-
-struct Gauss {
-    float3 mu;       // world frame once apply_dyn has run
-    float logit, opac;
-    float3 s;        // exp(log-scale)
-    float q[4];      // normalised quaternion (object frame)
-    float qn;        // |q|
-    float Rq[9];
-    float S[6];      // Sigma: 00 01 02 11 12 22 (world frame once apply_dyn has run)
-    bool moved;      // object pose applied
-    float Rg[9];     // object rotation
-    float L;         // relighting factor of the DC coefficient
-};
-
-__device__ __forceinline__ void quat_rot(float w, float x, float y, float z, float* R) {
-    const float n = rsqrtf(w * w + x * x + y * y + z * z);
-    w *= n; x *= n; y *= n; z *= n;
-    R[0] = 1.f - 2.f * (y * y + z * z); R[1] = 2.f * (x * y - w * z);       R[2] = 2.f * (x * z + w * y);
-    R[3] = 2.f * (x * y + w * z);       R[4] = 1.f - 2.f * (x * x + z * z); R[5] = 2.f * (y * z - w * x);
-    R[6] = 2.f * (x * z - w * y);       R[7] = 2.f * (y * z + w * x);       R[8] = 1.f - 2.f * (x * x + y * y);
-}
-
-// Object pose and relighting (Sec. 3.4): mean and covariance to the world
-// frame, Lambertian factor of the DC coefficient.
-__device__ __forceinline__ void apply_dyn(const Dyn& d, int64_t g, Gauss& G) {
-    G.moved = d.group != nullptr;
-    G.L = 1.f;
-    if (!G.moved) return;
-    const uint32_t grp = min((uint32_t)d.group[g], (uint32_t)(d.n_groups - 1));  // ids beyond the poses clamp
-    const float4 q = d.poses[2 * grp], t = d.poses[2 * grp + 1];
-    float* R = G.Rg;
-    quat_rot(q.x, q.y, q.z, q.w, R);
-    const float3 m = G.mu;
-    G.mu = make_float3(R[0] * m.x + R[1] * m.y + R[2] * m.z + t.x, R[3] * m.x + R[4] * m.y + R[5] * m.z + t.y,
-                       R[6] * m.x + R[7] * m.y + R[8] * m.z + t.z);
-    // Sigma_w = R Sigma R^T
-    const float* S = G.S;
-    const float Sf[9] = {S[0], S[1], S[2], S[1], S[3], S[4], S[2], S[4], S[5]};
-    float RS[9];
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int j = 0; j < 3; ++j) RS[i * 3 + j] = R[i * 3] * Sf[j] + R[i * 3 + 1] * Sf[3 + j] + R[i * 3 + 2] * Sf[6 + j];
-    float W[6];
-    W[0] = RS[0] * R[0] + RS[1] * R[1] + RS[2] * R[2];
-    W[1] = RS[0] * R[3] + RS[1] * R[4] + RS[2] * R[5];
-    W[2] = RS[0] * R[6] + RS[1] * R[7] + RS[2] * R[8];
-    W[3] = RS[3] * R[3] + RS[4] * R[4] + RS[5] * R[5];
-    W[4] = RS[3] * R[6] + RS[4] * R[7] + RS[5] * R[8];
-    W[5] = RS[6] * R[6] + RS[7] * R[7] + RS[8] * R[8];
-#pragma unroll
-    for (int i = 0; i < 6; ++i) G.S[i] = W[i];
-    if (d.normals) {
-        const float4 nl = d.normals[g];
-        const float4 l = *d.light;
-        const float nd = (R[0] * nl.x + R[1] * nl.y + R[2] * nl.z) * l.x +
-                         (R[3] * nl.x + R[4] * nl.y + R[5] * nl.z) * l.y +
-                         (R[6] * nl.x + R[7] * nl.y + R[8] * nl.z) * l.z;
-        G.L = d.ambient + d.diffuse * fmaxf(0.f, nd);
-    }
-}
-
-// View direction in the object frame (SH appearance turns with its object).
-__device__ __forceinline__ float3 sh_dir(const Gauss& G, float3 dw) {
-    if (!G.moved) return dw;
-    const float* R = G.Rg;
-    return make_float3(R[0] * dw.x + R[3] * dw.y + R[6] * dw.z, R[1] * dw.x + R[4] * dw.y + R[7] * dw.z,
-                       R[2] * dw.x + R[5] * dw.y + R[8] * dw.z);
-}
-
-__device__ __forceinline__ void load_gauss(const float4* __restrict__ P, int64_t n, int64_t g, Gauss& G) {
-    const float4 p0 = P[g], p1 = P[n + g], p2 = P[2 * n + g];
-    G.mu = make_float3(p0.x, p0.y, p0.z);
-    G.logit = p0.w;
-    G.opac = 1.f / (1.f + expf(-p0.w));
-    G.s = make_float3(expf(p1.x), expf(p1.y), expf(p1.z));
-    G.qn = sqrtf(p2.x * p2.x + p2.y * p2.y + p2.z * p2.z + p2.w * p2.w);
-    const float w = p2.x / G.qn, x = p2.y / G.qn, y = p2.z / G.qn, z = p2.w / G.qn;
-    G.q[0] = w; G.q[1] = x; G.q[2] = y; G.q[3] = z;
-    float* R = G.Rq;
-    R[0] = 1.f - 2.f * (y * y + z * z); R[1] = 2.f * (x * y - w * z);       R[2] = 2.f * (x * z + w * y);
-    R[3] = 2.f * (x * y + w * z);       R[4] = 1.f - 2.f * (x * x + z * z); R[5] = 2.f * (y * z - w * x);
-    R[6] = 2.f * (x * z - w * y);       R[7] = 2.f * (y * z + w * x);       R[8] = 1.f - 2.f * (x * x + y * y);
-    const float s0 = G.s.x * G.s.x, s1 = G.s.y * G.s.y, s2 = G.s.z * G.s.z;
-    // Sigma = R diag(s^2) R^T
-    G.S[0] = R[0] * R[0] * s0 + R[1] * R[1] * s1 + R[2] * R[2] * s2;
-    G.S[1] = R[0] * R[3] * s0 + R[1] * R[4] * s1 + R[2] * R[5] * s2;
-    G.S[2] = R[0] * R[6] * s0 + R[1] * R[7] * s1 + R[2] * R[8] * s2;
-    G.S[3] = R[3] * R[3] * s0 + R[4] * R[4] * s1 + R[5] * R[5] * s2;
-    G.S[4] = R[3] * R[6] * s0 + R[4] * R[7] * s1 + R[5] * R[8] * s2;
-    G.S[5] = R[6] * R[6] * s0 + R[7] * R[7] * s1 + R[8] * R[8] * s2;
-}
 
 // Geometry of one Gaussian in one view; returns false when culled by the
 // near plane or a non-positive 2D determinant.
@@ -269,7 +83,113 @@ __device__ __forceinline__ void tile_rect(float u, float v, float r, int TX, int
     y1 = (int)fminf(fmaxf(floorf((v + r + ft - 1.f) / ft), 0.f), (float)TY);
 }
 
-template <int D>
+// ------------------------------------------------------------ relighting
+// Per-group relighting table (Sec. 3.4.1).  The environment seen from the
+// object's frame is Lenv'(w) = Lenv(R_g w); rotation keeps each SH band, so
+// band l of e' is the least-squares fit of Lenv restricted to band l, sampled
+// at R_g w_j, over the band's basis at 20 spiral directions w_j (the fit is
+// exact: the rotated band lies in the band's span; its normal matrices have
+// condition numbers below 2).  The directional light enters as
+// E_c Y_k(R_g^T l).  One thread per group; float32 throughout.
+constexpr int kFitDirs = 20;
+
+__device__ __forceinline__ void spiral_dir(int j, float* w) {
+    const float z = 1.f - (2.f * j + 1.f) / (float)kFitDirs;
+    const float r = sqrtf(fmaxf(0.f, 1.f - z * z));
+    float sn, cs;
+    sincosf(2.3999632297286533f * (float)j, &sn, &cs);  // golden angle
+    w[0] = r * cs; w[1] = r * sn; w[2] = z;
+}
+
+__global__ void k_light_table(Dyn d, const float* __restrict__ light, float* __restrict__ tab, int G) {
+    const int grp = blockIdx.x * blockDim.x + threadIdx.x;
+    if (grp >= G) return;
+    float R[9] = {1.f, 0.f, 0.f, 0.f, 1.f, 0.f, 0.f, 0.f, 1.f};
+    if (d.group) {
+        const float4 q = d.poses[2 * grp];
+        quat_rot(q.x, q.y, q.z, q.w, R);
+    }
+    float* out = tab + (size_t)grp * kLitTab;
+    for (int c = 0; c < 3; ++c) out[c] = light[c];  // band 0 is rotation invariant
+    for (int l = 1; l <= 3; ++l) {
+        const int nb = 2 * l + 1, o = l * l;
+        float M[7][7], rhs[7][3];
+        for (int a = 0; a < nb; ++a) {
+            for (int b = 0; b < nb; ++b) M[a][b] = 0.f;
+            rhs[a][0] = rhs[a][1] = rhs[a][2] = 0.f;
+        }
+        for (int j = 0; j < kFitDirs; ++j) {
+            float w[3], Y[16], Yr[16];
+            spiral_dir(j, w);
+            sh_basis<3>(w[0], w[1], w[2], Y);
+            sh_basis<3>(R[0] * w[0] + R[1] * w[1] + R[2] * w[2], R[3] * w[0] + R[4] * w[1] + R[5] * w[2],
+                        R[6] * w[0] + R[7] * w[1] + R[8] * w[2], Yr);
+            float Lb[3] = {0.f, 0.f, 0.f};
+            for (int m = 0; m < nb; ++m)
+                for (int c = 0; c < 3; ++c) Lb[c] += light[3 * (o + m) + c] * Yr[o + m];
+            for (int a = 0; a < nb; ++a) {
+                for (int b = 0; b < nb; ++b) M[a][b] += Y[o + a] * Y[o + b];
+                for (int c = 0; c < 3; ++c) rhs[a][c] += Y[o + a] * Lb[c];
+            }
+        }
+        // Gaussian elimination with partial pivoting
+        for (int col = 0; col < nb; ++col) {
+            int piv = col;
+            for (int r = col + 1; r < nb; ++r)
+                if (fabsf(M[r][col]) > fabsf(M[piv][col])) piv = r;
+            if (piv != col) {
+                for (int b = 0; b < nb; ++b) { const float t = M[col][b]; M[col][b] = M[piv][b]; M[piv][b] = t; }
+                for (int c = 0; c < 3; ++c) { const float t = rhs[col][c]; rhs[col][c] = rhs[piv][c]; rhs[piv][c] = t; }
+            }
+            const float inv = 1.f / M[col][col];
+            for (int r = col + 1; r < nb; ++r) {
+                const float f = M[r][col] * inv;
+                for (int b = col; b < nb; ++b) M[r][b] -= f * M[col][b];
+                for (int c = 0; c < 3; ++c) rhs[r][c] -= f * rhs[col][c];
+            }
+        }
+        for (int r = nb - 1; r >= 0; --r)
+            for (int c = 0; c < 3; ++c) {
+                float acc = rhs[r][c];
+                for (int b = r + 1; b < nb; ++b) acc -= M[r][b] * out[3 * (o + b) + c];
+                out[3 * (o + r) + c] = acc / M[r][r];
+            }
+    }
+    // directional light in the object frame: R_g^T l
+    const float lx = light[48], ly = light[49], lz = light[50];
+    float Y[16];
+    sh_basis<3>(R[0] * lx + R[3] * ly + R[6] * lz, R[1] * lx + R[4] * ly + R[7] * lz,
+                R[2] * lx + R[5] * ly + R[8] * lz, Y);
+    for (int k = 0; k < 16; ++k)
+        for (int c = 0; c < 3; ++c) out[48 + 3 * k + c] = light[52 + c] * Y[k];
+}
+
+// Relit colour of one Gaussian (view-independent): weights w_j = e'_j + v E Y_j.
+template <int NB>
+__device__ __forceinline__ void relit_rgb(const float* sh, const float* __restrict__ lt, float v, float* rgb,
+                                          uint32_t& mask) {
+    mask = 0;
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) {
+        float acc = 0.f;
+#pragma unroll
+        for (int k = 0; k < NB; ++k) acc += sh[3 * k + ch] * (__ldg(&lt[3 * k + ch]) + v * __ldg(&lt[48 + 3 * k + ch]));
+        acc += 0.5f;
+        if (acc < 0.f) { acc = 0.f; mask |= 1u << ch; }
+        rgb[ch] = acc;
+    }
+}
+
+__device__ __forceinline__ const float* lit_row(const Dyn& d, int64_t g) {
+    const uint32_t grp = d.group ? min((uint32_t)d.group[g], (uint32_t)(d.n_groups - 1)) : 0u;
+    return d.lit_tab + (size_t)grp * kLitTab;
+}
+
+__device__ __forceinline__ float lit_vis(const Dyn& d, int64_t g) {
+    return d.vis ? (float)d.vis[g] * (1.f / 255.f) : 1.f;
+}
+
+template <int D, bool LIT>
 __global__ void __launch_bounds__(256)
 k_project(const float4* __restrict__ P, int64_t n, int64_t g_off, int64_t n_out, Dyn dyn,
           const gs_camera* __restrict__ cams, const ViewInfo* __restrict__ vt, int V, int tile,
@@ -304,6 +224,9 @@ k_project(const float4* __restrict__ P, int64_t n, int64_t g_off, int64_t n_out,
         sh[4 * pl] = c.x; sh[4 * pl + 1] = c.y; sh[4 * pl + 2] = c.z; sh[4 * pl + 3] = c.w;
     }
     sh[0] *= G.L; sh[1] *= G.L; sh[2] *= G.L;
+    float lrgb[3] = {0.f, 0.f, 0.f};
+    uint32_t lmask = 0;
+    if (LIT) relit_rgb<NB>(sh, lit_row(dyn, g_off + g), lit_vis(dyn, g_off + g), lrgb, lmask);
     for (int v = 0; v < V; ++v) {
         const Cam C = load_cam(cams + v);
         const int64_t rec = (int64_t)v * n_out + g_off + g;
@@ -328,19 +251,21 @@ k_project(const float4* __restrict__ P, int64_t n, int64_t g_off, int64_t n_out,
             if (dkv) dkv[rec] = (0xFFFFFFFFull << 32) | (uint32_t)rec;
             continue;
         }
-        float Y[16];
-        const float3 ds = sh_dir(G, Vg.dir);
-        sh_basis<D>(ds.x, ds.y, ds.z, Y);
-        float rgb[3];
-        uint32_t mask = 0;
+        float rgb[3] = {lrgb[0], lrgb[1], lrgb[2]};
+        uint32_t mask = lmask;
+        if (!LIT) {
+            float Y[16];
+            const float3 ds = sh_dir(G, Vg.dir);
+            sh_basis<D>(ds.x, ds.y, ds.z, Y);
 #pragma unroll
-        for (int ch = 0; ch < 3; ++ch) {
-            float acc = 0.f;
+            for (int ch = 0; ch < 3; ++ch) {
+                float acc = 0.f;
 #pragma unroll
-            for (int k = 0; k < NB; ++k) acc += sh[3 * k + ch] * Y[k];
-            acc += 0.5f;
-            if (acc < 0.f) { acc = 0.f; mask |= 1u << ch; }
-            rgb[ch] = acc;
+                for (int k = 0; k < NB; ++k) acc += sh[3 * k + ch] * Y[k];
+                acc += 0.5f;
+                if (acc < 0.f) { acc = 0.f; mask |= 1u << ch; }
+                rgb[ch] = acc;
+            }
         }
         const float idet = 1.f / Vg.det;
         out[0] = make_float4(u, vv, Vg.tz, G.opac);
@@ -354,7 +279,7 @@ k_project(const float4* __restrict__ P, int64_t n, int64_t g_off, int64_t n_out,
 }
 
 // ------------------------------------------------------------------ adjoint
-template <int D>
+template <int D, bool LIT>
 __global__ void __launch_bounds__(128, 4)
 k_project_bwd(const float4* __restrict__ P, int64_t n, int64_t n_out, Dyn dyn, const gs_camera* __restrict__ cams,
               int V,
@@ -373,6 +298,8 @@ k_project_bwd(const float4* __restrict__ P, int64_t n, int64_t n_out, Dyn dyn, c
 #pragma unroll
     for (int pl = 0; pl < NPL; ++pl) dsh[4 * pl] = dsh[4 * pl + 1] = dsh[4 * pl + 2] = dsh[4 * pl + 3] = 0.f;
     float dmx = 0.f, dmy = 0.f, dmz = 0.f, dlogit = 0.f;
+    const float* lt = LIT ? lit_row(dyn, g) : nullptr;
+    const float lv = LIT ? lit_vis(dyn, g) : 0.f;
     float D00 = 0.f, D01 = 0.f, D02 = 0.f, D11 = 0.f, D12 = 0.f, D22 = 0.f;  // dSigma + dSigma^T
     for (int v = 0; v < V; ++v) {
         const int64_t rec = (int64_t)v * n_out + g;
@@ -387,13 +314,19 @@ k_project_bwd(const float4* __restrict__ P, int64_t n, int64_t n_out, Dyn dyn, c
         const float grgb[3] = {gb.z, gb.w, gc.x};
         // opacity = sigmoid(logit)
         dlogit += go * G.opac * (1.f - G.opac);
+        float gm[3];
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) gm[ch] = (mask & (1u << ch)) ? 0.f : grgb[ch];
+        if (LIT) {
+            // relit colour: linear in the coefficients, no view dependence
+#pragma unroll
+            for (int j = 0; j < 3 * NB; ++j)
+                dsh[j] += gm[j % 3] * (__ldg(&lt[j]) + lv * __ldg(&lt[48 + j]));
+        } else {
         // colour -> SH coefficients and view direction
         float Y[16];
         const float3 dsd = sh_dir(G, Vg.dir);
         sh_basis<D>(dsd.x, dsd.y, dsd.z, Y);
-        float gm[3];
-#pragma unroll
-        for (int ch = 0; ch < 3; ++ch) gm[ch] = (mask & (1u << ch)) ? 0.f : grgb[ch];
         float wsum[16];
 #pragma unroll
         for (int k = 0; k < 16; ++k) wsum[k] = 0.f;
@@ -422,6 +355,7 @@ k_project_bwd(const float4* __restrict__ P, int64_t n, int64_t n_out, Dyn dyn, c
         dmx += (ddir.x - Vg.dir.x * dd) * il;
         dmy += (ddir.y - Vg.dir.y * dd) * il;
         dmz += (ddir.z - Vg.dir.z * dd) * il;
+        }
         // conic (A, B, C) = (c, -b, a) / det
         const float a = Vg.a, b = Vg.b, c = Vg.c, id = 1.f / Vg.det, id2 = id * id;
         const float da = gA * (-c * c * id2) + gB * (b * c * id2) + gC * (id - a * c * id2);
@@ -594,12 +528,17 @@ void launch_project(const float* params, int64_t n, int sh_degree, const Dyn& dy
     const unsigned blocks = (unsigned)((n + threads - 1) / threads);
     const float4* P = reinterpret_cast<const float4*>(params);
     float4* out = reinterpret_cast<float4*>(proj);
+    const bool lit = dyn.lit_tab != nullptr;
+#define GS_PROJ(DD)                                                                                              \
+    (lit ? k_project<DD, true><<<blocks, threads, 0, st>>>(P, n, g_off, n_out, dyn, d_cams, vt, V, tile, out, depth_kv) \
+         : k_project<DD, false><<<blocks, threads, 0, st>>>(P, n, g_off, n_out, dyn, d_cams, vt, V, tile, out, depth_kv))
     switch (sh_degree) {
-        case 0: k_project<0><<<blocks, threads, 0, st>>>(P, n, g_off, n_out, dyn, d_cams, vt, V, tile, out, depth_kv); break;
-        case 1: k_project<1><<<blocks, threads, 0, st>>>(P, n, g_off, n_out, dyn, d_cams, vt, V, tile, out, depth_kv); break;
-        case 2: k_project<2><<<blocks, threads, 0, st>>>(P, n, g_off, n_out, dyn, d_cams, vt, V, tile, out, depth_kv); break;
-        default: k_project<3><<<blocks, threads, 0, st>>>(P, n, g_off, n_out, dyn, d_cams, vt, V, tile, out, depth_kv); break;
+        case 0: GS_PROJ(0); break;
+        case 1: GS_PROJ(1); break;
+        case 2: GS_PROJ(2); break;
+        default: GS_PROJ(3); break;
     }
+#undef GS_PROJ
 }
 
 void launch_project_bwd(const float* params, int64_t n, int sh_degree, const Dyn& dyn, const gs_camera* d_cams,
@@ -613,12 +552,26 @@ void launch_project_bwd(const float* params, int64_t n, int sh_degree, const Dyn
     const float4* pr = reinterpret_cast<const float4*>(proj);
     const float4* g2 = reinterpret_cast<const float4*>(grad2d);
     float4* dP = reinterpret_cast<float4*>(dparams);
+    const bool lit = dyn.lit_tab != nullptr;
+#define GS_PROJ_BWD(DD)                                                                                          \
+    (lit ? k_project_bwd<DD, true><<<blocks, threads, 0, st>>>(P, n, n_out, dyn, d_cams, V, pr, g2, dP, accumulate) \
+         : k_project_bwd<DD, false><<<blocks, threads, 0, st>>>(P, n, n_out, dyn, d_cams, V, pr, g2, dP, accumulate))
     switch (sh_degree) {
-        case 0: k_project_bwd<0><<<blocks, threads, 0, st>>>(P, n, n_out, dyn, d_cams, V, pr, g2, dP, accumulate); break;
-        case 1: k_project_bwd<1><<<blocks, threads, 0, st>>>(P, n, n_out, dyn, d_cams, V, pr, g2, dP, accumulate); break;
-        case 2: k_project_bwd<2><<<blocks, threads, 0, st>>>(P, n, n_out, dyn, d_cams, V, pr, g2, dP, accumulate); break;
-        default: k_project_bwd<3><<<blocks, threads, 0, st>>>(P, n, n_out, dyn, d_cams, V, pr, g2, dP, accumulate); break;
+        case 0: GS_PROJ_BWD(0); break;
+        case 1: GS_PROJ_BWD(1); break;
+        case 2: GS_PROJ_BWD(2); break;
+        default: GS_PROJ_BWD(3); break;
     }
+#undef GS_PROJ_BWD
+}
+
+}  // namespace gs
+
+namespace gs {
+
+void launch_light_table(const Dyn& dyn, const float* light, float* tab, cudaStream_t st) {
+    const int G = dyn.group ? dyn.n_groups : 1;
+    k_light_table<<<(G + 63) / 64, 64, 0, st>>>(dyn, light, tab, G);
 }
 
 }  // namespace gs

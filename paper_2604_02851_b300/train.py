@@ -26,7 +26,7 @@ from . import (Context, RECORD_BYTES, GRAD2D_STRIDE, PROJ_STRIDE, _lib, _ptr, _s
 class OnlineTrainer:
     def __init__(self, params, sh_degree: int, cams: dict, keys_cap: int, lr=1e-3, w_l1=0.8, w_ssim=0.2,
                  delta_thr=1e-3, bg=(0.0, 0.0, 0.0), tile=16, sort_bits=8, ctx: Context | None = None,
-                 dyn=None, share: "OnlineTrainer | None" = None, frozen=None, precull=None):
+                 dyn=None, share: "OnlineTrainer | None" = None, frozen=None, precull=None, lighting=None):
         """share: another trainer of the same model whose gradient, Adam
         moments, delta baseline and step counter this one uses (a second
         graph slot with its own targets, image and delta outputs).
@@ -34,7 +34,9 @@ class OnlineTrainer:
         Gaussian freezing): rendered with `params`, never updated; gradients,
         Adam state and deltas cover `params` only.
         precull: a Precull grid (Sec. 3.3): Gaussians of culled cells are not
-        rendered and keep their parameters and Adam state this step."""
+        rendered and keep their parameters and Adam state this step.
+        lighting: a Lighting (Sec. 3.4.1): colours are the SH-lighting
+        product, attenuated by its per-Gaussian light visibility."""
         import torch
         self.torch = torch
         self.params = params
@@ -75,8 +77,9 @@ class OnlineTrainer:
                            self.d_loss, self.d_idx, self.d_records, self.d_count, self.d_step, frozen=frozen)
         self.dyn = dyn  # kept alive: the step reads its device buffers
         self.precull = precull
+        self.lighting = lighting
         self.cfg = train_cfg(n, sh_degree, V, self.W, self.H, self.keys_cap, w_l1, w_ssim, self.bg, delta_thr, lr,
-                             dyn=dyn, n_frozen=self.n_frozen, precull=precull)
+                             dyn=dyn, n_frozen=self.n_frozen, precull=precull, lighting=lighting)
         self._captured = False
         self._events = None
         self._plain = None

@@ -84,7 +84,7 @@ class GpuRun:
     """One pass of the whole CUDA path on a small case, all intermediates kept."""
 
     def __init__(self, planes, sh_degree, cams, target=None, keys_cap=None, bg=(0.0, 0.0, 0.0),
-                 tile=16, sort_bits=8, w_l1=0.8, w_ssim=0.2, dyn=None, raster_threads=4):
+                 tile=16, sort_bits=8, w_l1=0.8, w_ssim=0.2, dyn=None, raster_threads=4, lighting=None):
         import torch
         import paper_2604_02851_b300 as gs
         self.gs = gs
@@ -103,7 +103,8 @@ class GpuRun:
             keys_cap = 1 << 16
         self.ctx.reserve(self.ctx.workspace_size(cams, n, keys_cap))
         self.dyn = dyn
-        self.proj = gs.gs_project(self.ctx, self.params, sh_degree, self.d_cams, V, dyn=dyn)
+        self.lighting = lighting
+        self.proj = gs.gs_project(self.ctx, self.params, sh_degree, self.d_cams, V, dyn=dyn, lighting=lighting)
         self.keys, self.vals, self.ranges, self.nk = gs.gs_bin_sort(
             self.ctx, self.proj, self.d_cams, V, n, self.tt, keys_cap)
         torch.cuda.synchronize()
@@ -125,7 +126,7 @@ class GpuRun:
             self.loss, self.dimage = gs.gs_loss(self.ctx, self.image, self.target, V, H, W, w_l1, w_ssim)
             self.grad2d, self.dparams = gs.gs_render_bwd(
                 self.ctx, self.params, sh_degree, self.d_cams, V, self.tt, self.proj, self.vals, self.ranges,
-                self.T, self.nc, self.dimage, bg=bg, dyn=dyn)
+                self.T, self.nc, self.dimage, bg=bg, dyn=dyn, lighting=lighting)
         torch.cuda.synchronize()
         code, detail = self.ctx.status()
         assert code == 0, (code, detail)
