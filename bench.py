@@ -232,7 +232,7 @@ class OracleSampler:
     views per step; Adam is timed on a slice of the parameters and scaled to
     all of them."""
 
-    def __init__(self, n, sh, V, W, H, seed_offset=0, dynamic=False):
+    def __init__(self, n, sh, V, W, H, seed_offset=0, dynamic=False, relight=False):
         import oracle as O
         self.O = O
         self.dyn = None
@@ -241,6 +241,15 @@ class OracleSampler:
             self.dyn = {"group": gi.rigid_groups(n, 16), "poses": gi.frame_poses(2, 16)[1],
                         "normals": gi.unit_normals(n), "light": gi.light_directions(2)[1],
                         "ambient": 0.3, "diffuse": 0.7}
+        if relight:
+            # SH-lighting product with every Gaussian lit (the map is not sampled)
+            L = np.zeros(56)
+            L[:48] = relight_env().reshape(48)
+            L[48:51] = gi.light_directions(2)[1]
+            L[52:55] = RELIGHT_RADIANCE
+            self.dyn = {"sh_light": L}
+            if dynamic:
+                self.dyn.update(group=gi.rigid_groups(n, 16), poses=gi.frame_poses(2, 16)[1])
         self.n, self.sh, self.V, self.W, self.H = n, sh, V, W, H
         self.planes = gi.planes_to_rows(gi.make_scene(n, sh, gi.SEED_MODEL + seed_offset)).astype(np.float64)
         self.target_planes = gi.planes_to_rows(gi.make_scene(n, sh, gi.SEED_TARGET + seed_offset)).astype(np.float64)
@@ -285,6 +294,19 @@ class OracleSampler:
                 f"Adam on {self.adam_floats} floats scaled to {self.n * 60}")
 
 
+RELIGHT_RADIANCE = (1.0, 0.95, 0.9)
+RELIGHT_MAP = 2048          # light-space depth map, texels per side
+RELIGHT_EXTENT = 4.0        # world units the map covers (the scene and its motion)
+
+
+def relight_env():
+    """Seeded world-frame environment SH [16][3]: a positive ambient term and
+    small higher bands."""
+    env = np.random.default_rng(gi.SEED_MODEL + 30).normal(0.0, 0.1, (16, 3))
+    env[0] = 1.0
+    return env
+
+
 def omp_cores():
     try:
         return int(os.environ.get("OMP_NUM_THREADS", "")) or os.cpu_count()
@@ -299,7 +321,7 @@ def run_reference(args, rank, world):
     if rank != 0:
         return
     n, sh, V, W, H = WORKLOADS[args.workload]
-    smp = OracleSampler(n, sh, V, W, H, dynamic=args.workload in DYNAMIC_WORKLOADS)
+    smp = OracleSampler(n, sh, V, W, H, dynamic=args.workload in DYNAMIC_WORKLOADS, relight=args.relight)
     one = smp.sample()
     budget_s = 150.0
     # one band sample is the smallest unit; when the requested steps do not
@@ -354,13 +376,23 @@ def run_ours(args, rank, world, local_rank):
     # dynamic scene: 16 rigid objects move every frame and the light turns
     drift = None if dynamic else torch.from_numpy(signs).to(dev) * 1e-3
     dyn = None
+    frames = max(args.steps, 1) + args.warmup + args.e2e_steps + 16
+    lights = gi.light_directions(frames)
+    frame = [0]
     if dynamic:
         G = 16
-        frames = max(args.steps, 1) + args.warmup + args.e2e_steps + 16
         poses = gi.frame_poses(frames, G)
-        lights = gi.light_directions(frames)
-        dyn = gs.Dynamics(gi.rigid_groups(n, G), poses[0], gi.unit_normals(n), lights[0], 0.3, 0.7, device=dev)
-        frame = [0]
+        # relighting by the SH-lighting product replaces the Lambertian DC factor
+        normals = None if args.relight else gi.unit_normals(n)
+        dyn = gs.Dynamics(gi.rigid_groups(n, G), poses[0], normals, lights[0], 0.3, 0.7, device=dev)
+    lighting = tlight = None
+    if args.relight:
+        # Sec. 3.4.1: SH lighting (environment + directional light turning
+        # 1 deg per frame) and a per-Gaussian light visibility from a
+        # light-space depth map, recomputed every frame inside the timed step
+        lighting = gs.Lighting(n, relight_env(), lights[0], RELIGHT_RADIANCE, device=dev)
+        tlight = gs.Lighting(n, relight_env(), lights[0], RELIGHT_RADIANCE, with_visibility=False, device=dev)
+        ldepth = torch.empty((RELIGHT_MAP, RELIGHT_MAP), dtype=torch.float32, device=dev)
 
     ctx = gs.Context(local_rank, 0, tile=args.tile, sort_bits=args.sort_bits, sort_items=args.sort_items,
                      binning=args.binning, raster_threads=args.raster_threads)
@@ -370,7 +402,7 @@ def run_ours(args, rank, world, local_rank):
         # pick binning, digit width, items per thread and raster layout for this
         # workload (gs_autotune); the step graph is captured afterwards
         ctx.reserve(ctx.workspace_size(cams, n, keys_cap))
-        best, entries = gs.gs_autotune(ctx, params, sh, cams, keys_cap, reps=2, dyn=dyn)
+        best, entries = gs.gs_autotune(ctx, params, sh, cams, keys_cap, reps=2, dyn=dyn, lighting=lighting)
         args.binning, args.sort_bits = best["binning"], best["sort_bits"]
         args.sort_items, args.raster_threads = best["sort_items"], best["raster_threads"]
         worst = max(e["ms"] for e in entries)
@@ -393,7 +425,8 @@ def run_ours(args, rank, world, local_rank):
         torch.cuda.synchronize()
         pctx.close()
         del far
-    tr = OnlineTrainer(params, sh, cams, keys_cap, ctx=ctx, dyn=dyn, frozen=frozen, precull=precull)
+    tr = OnlineTrainer(params, sh, cams, keys_cap, ctx=ctx, dyn=dyn, frozen=frozen, precull=precull,
+                       lighting=lighting)
     packed = tr.packed
     tctx = gs.Context(local_rank, 0, tile=args.tile, sort_bits=args.sort_bits, sort_items=args.sort_items,
                      binning=args.binning, raster_threads=args.raster_threads)
@@ -402,19 +435,32 @@ def run_ours(args, rank, world, local_rank):
 
     def next_targets():
         # the engine side: move the scene and render its reference views
-        if dynamic:
+        if dynamic or args.relight:
             frame[0] = (frame[0] + 1) % len(lights)
+        if dynamic:
             dyn.set_frame(poses[frame[0]], lights[frame[0]])
         else:
             tparams.add_(drift)
+        if args.relight:
+            lighting.set(direction=lights[frame[0]])
+            tlight.set(direction=lights[frame[0]])
         gs.gs_render_batch(tctx, tparams, sh, tr.d_cams, V, tr.total_tiles, tkeys, tr.npix, image=tr.targets,
-                           dyn=dyn)
+                           dyn=dyn, lighting=tlight)
+
+    def light_camera():
+        return gs.light_camera(direction=lights[frame[0]], width=RELIGHT_MAP, height=RELIGHT_MAP,
+                               extent=RELIGHT_EXTENT, alpha_min=0.5, bias=2.0 * RELIGHT_EXTENT / RELIGHT_MAP)
+
+    def update_visibility():
+        lighting.update_visibility(tr.ctx, params, light_camera(), ldepth, dyn=dyn, frozen=frozen)
 
     phase_ev = [torch.cuda.Event(enable_timing=True) for _ in range(gs._lib.TRAIN_PHASE_EVENTS)]
     next_targets()
     tr.capture(phase_events=phase_ev)
     for _ in range(args.warmup):
         next_targets()
+        if args.relight:
+            update_visibility()
         tr.step()
     torch.cuda.synchronize()
     tr.raise_status()
@@ -425,6 +471,8 @@ def run_ours(args, rank, world, local_rank):
     ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     phase_ms = np.zeros(len(phase_ev) - 1)
+    lv_ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    vis_ms = 0.0
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
@@ -433,11 +481,17 @@ def run_ours(args, rank, world, local_rank):
     for k in range(args.steps):
         next_targets()
         ev0[k].record()
+        if args.relight:
+            lv_ev[0].record()
+            update_visibility()
+            lv_ev[1].record()
         tr.step()
         ev1[k].record()
         ev1[k].synchronize()
         for i in range(len(phase_ev) - 1):
             phase_ms[i] += event_ms(phase_ev[i], phase_ev[i + 1])
+        if args.relight:
+            vis_ms += event_ms(lv_ev[0], lv_ev[1])
     torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
     clk = clocks.stop()
@@ -452,10 +506,21 @@ def run_ours(args, rank, world, local_rank):
     loss_last = tr.loss()
     changed = tr.delta_count()
     phase_avg = {name: float(ms / args.steps) for name, ms in zip(gs._lib.TRAIN_PHASES, phase_ms)}
+    relight = None
+    if args.relight:
+        vis_host = lighting.visibility[:n].cpu().numpy()
+        dmap = ldepth.cpu().numpy()
+        relight = {"visibility_ms": vis_ms / args.steps, "light_map": [RELIGHT_MAP, RELIGHT_MAP],
+                   "extent": RELIGHT_EXTENT, "alpha_min": 0.5, "covered_texels": float(np.isfinite(dmap).mean()),
+                   "shadowed_fraction": float((vis_host == 0).mean()),
+                   "what": "per frame, inside each timed step: light-space depth map of every Gaussian "
+                           "(clear + warp-per-Gaussian splat) and the centre test; the step's projection "
+                           "evaluates the SH-lighting product (environment rotated per object + directional "
+                           "light x visibility)"}
 
     # ---- work counts of the current model, for the roofline (outside the timed region)
     wc_params = params if frozen is None else torch.cat([params, frozen], 1)  # every rendered Gaussian
-    proj = gs.gs_project(ctx, wc_params, sh, tr.d_cams, V, dyn=dyn)
+    proj = gs.gs_project(ctx, wc_params, sh, tr.d_cams, V, dyn=dyn, lighting=lighting)
     _, vals, ranges, nk = gs.gs_bin_sort(ctx, proj, tr.d_cams, V, n, tr.total_tiles, keys_cap, want_keys=False)
     _, T, nc = gs.gs_render_fwd(ctx, proj, tr.d_cams, V, n, tr.total_tiles, vals, ranges, tr.npix)
     torch.cuda.synchronize()
@@ -535,7 +600,7 @@ def run_ours(args, rank, world, local_rank):
         def make_ctx():
             return gs.Context(local_rank, 0, tile=args.tile, sort_bits=args.sort_bits, sort_items=args.sort_items,
                               binning=args.binning, raster_threads=args.raster_threads)
-        e2e = run_e2e(args, host_targets, params, sh, cams, keys_cap, make_ctx, dyn, world)
+        e2e = run_e2e(args, host_targets, params, sh, cams, keys_cap, make_ctx, dyn, world, lighting)
         del host_targets
     serving = None
     if args.serve_requests > 0:
@@ -546,7 +611,7 @@ def run_ours(args, rank, world, local_rank):
     if rank == 0:
         cpu = None
         if world == 1 and not args.no_cpu_baseline:
-            smp = OracleSampler(n, sh, V, W, H, dynamic=dynamic)
+            smp = OracleSampler(n, sh, V, W, H, dynamic=dynamic, relight=args.relight)
             times = [smp.sample() for _ in range(args.cpu_samples)]
             cpu = {"value": 1.0 / smp.step_seconds(times), "unit": "steps/s", "cores": omp_cores(),
                    "kind": "oracle", "sample": smp.describe(args.cpu_samples)}
@@ -558,8 +623,11 @@ def run_ours(args, rank, world, local_rank):
                           "keys_cap": keys_cap, "tile": args.tile,
                           "dynamics": "16 rigid objects, new SE(3) pose per frame (spin <= 2 deg/frame, "
                                       "sinusoidal translation 0.1), light at 45 deg zenith turning 1 deg/frame; "
-                                      "Lambertian relight of the DC term (ambient 0.3, diffuse 0.7)"
+                                      + ("SH-lighting product with per-Gaussian light visibility"
+                                         if args.relight else
+                                         "Lambertian relight of the DC term (ambient 0.3, diffuse 0.7)")
                           if dynamic else None,
+                          "relight": relight,
                           "sort_digit_bits": args.sort_bits, "sort_items": args.sort_items, "binning": args.binning,
                           "raster_threads_per_row": args.raster_threads, "autotune": tuned,
                           "frozen_fraction": args.frozen_frac, "precull": bool(args.precull),
@@ -570,7 +638,9 @@ def run_ours(args, rank, world, local_rank):
                           "parallelism": "replicas" if world > 1 else "single"},
                "roofline": roofline, "cpu_baseline": cpu, "clocks": clk, "e2e": e2e,
                "plain_step": plain, "serving": serving,
-               "gpu_launches": gpu_launches_per_step(args.binning, tile_passes) * args.steps,
+               "gpu_launches": (gpu_launches_per_step(args.binning, tile_passes)
+                                + (1 + 3 + (2 if frozen is not None else 0) if args.relight else 0)
+                                + (1 if frozen is not None else 0)) * args.steps,
                "tensor_deltas": tensor_deltas,
                "phases_ms": phase_avg, "kernels": kernels, "loss_last": loss_last, "delta_changed_last": changed,
                "wall_s_timed_loop": wall}
@@ -672,7 +742,7 @@ def measure_tensor_deltas(gs, torch, params, snapshot, hbm_peak, reps=5):
     return out
 
 
-def run_e2e(args, host_targets, params, sh, cams, keys_cap, make_ctx, dyn, world):
+def run_e2e(args, host_targets, params, sh, cams, keys_cap, make_ctx, dyn, world, lighting=None):
     """The same metric through the public API with host buffers: every step
     uploads its targets from pinned host memory and returns its loss, delta
     count and delta records to pinned host memory.  The copies overlap the
@@ -680,7 +750,7 @@ def run_e2e(args, host_targets, params, sh, cams, keys_cap, make_ctx, dyn, world
     runs from the first upload to the last record read-back."""
     import torch
     from paper_2604_02851_b300.train import StreamingTrainer
-    st = StreamingTrainer(params, sh, cams, keys_cap, make_ctx, dyn=dyn)
+    st = StreamingTrainer(params, sh, cams, keys_cap, make_ctx, dyn=dyn, lighting=lighting)
     st.capture()
     st.run(lambda k: host_targets[k % 2], 3)  # warm-up
     torch.cuda.synchronize()
@@ -726,6 +796,8 @@ def main():
                     help="preculling grid (Sec. 3.3): Gaussians outside the views' cells are not processed")
     ap.add_argument("--frozen-frac", type=float, default=0.0,
                     help="fraction of the model held in the inference-only (frozen) pool")
+    ap.add_argument("--relight", action="store_true",
+                    help="SH-lighting product and per-frame light visibility (Sec. 3.4.1) in every step")
     ap.add_argument("--tensor-deltas", action=argparse.BooleanOptionalAction, default=True,
                     help="time per-attribute tensor-delta extraction and replay after the timed steps")
     args = ap.parse_args()

@@ -215,7 +215,8 @@ class Lighting:
         self.visibility = (torch.full((max(int(n), 1),), 255, dtype=torch.uint8, device=device)
                            if with_visibility else None)
         self.n = int(n)
-        self.set(env if env is not None else np.zeros((16, 3)), direction, radiance)
+        self._host = self.pack(env if env is not None else np.zeros((16, 3)), direction, radiance)
+        self.light.copy_(torch.from_numpy(self._host))
         self.struct = _lib.gs_lighting(light=self.light.data_ptr(),
                                        visibility=self.visibility.data_ptr() if with_visibility else None)
 
@@ -229,16 +230,21 @@ class Lighting:
         return buf
 
     def set(self, env=None, direction=None, radiance=None):
+        """Overwrite the given parts of the lighting (the others stay)."""
         torch = _torch()
-        cur = self.light.cpu().numpy()
+        cur = self._host
         e = cur[:48] if env is None else env
         d = cur[48:51] if direction is None else direction
         r = cur[52:55] if radiance is None else radiance
-        self.light.copy_(torch.from_numpy(self.pack(e, d, r)))
+        self._host = self.pack(e, d, r)
+        self.light.copy_(torch.from_numpy(self._host))
 
     def update_visibility(self, ctx, params, lcam, depth=None, dyn=None, stream=None, frozen=None):
         """Render the light-space depth map of params (and the frozen pool, if
-        given) and test every centre against it; returns the depth map."""
+        given) and test every centre against it; returns the depth map.  The
+        frozen pool is taken as static (dyn applies to params only)."""
+        if dyn is not None and frozen is not None and frozen.shape[1] > 0:
+            raise ValueError("update_visibility: a frozen pool with rigid-object dynamics is not supported")
         depth = gs_light_depth_map(ctx, params, lcam, depth, dyn=dyn, stream=stream)
         if frozen is not None and frozen.shape[1] > 0:
             gs_light_depth_map(ctx, frozen, lcam, depth, accumulate=True, stream=stream)

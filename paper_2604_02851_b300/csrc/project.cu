@@ -165,25 +165,35 @@ __global__ void k_light_table(Dyn d, const float* __restrict__ light, float* __r
 }
 
 // Relit colour of one Gaussian (view-independent): weights w_j = e'_j + v E Y_j.
+// lt: the group's table row, in shared or global memory.
 template <int NB>
-__device__ __forceinline__ void relit_rgb(const float* sh, const float* __restrict__ lt, float v, float* rgb,
-                                          uint32_t& mask) {
+__device__ __forceinline__ void relit_rgb(const float* sh, const float* lt, float v, float* rgb, uint32_t& mask) {
     mask = 0;
 #pragma unroll
     for (int ch = 0; ch < 3; ++ch) {
         float acc = 0.f;
 #pragma unroll
-        for (int k = 0; k < NB; ++k) acc += sh[3 * k + ch] * (__ldg(&lt[3 * k + ch]) + v * __ldg(&lt[48 + 3 * k + ch]));
+        for (int k = 0; k < NB; ++k) acc += sh[3 * k + ch] * (lt[3 * k + ch] + v * lt[48 + 3 * k + ch]);
         acc += 0.5f;
         if (acc < 0.f) { acc = 0.f; mask |= 1u << ch; }
         rgb[ch] = acc;
     }
 }
 
-__device__ __forceinline__ const float* lit_row(const Dyn& d, int64_t g) {
-    const uint32_t grp = d.group ? min((uint32_t)d.group[g], (uint32_t)(d.n_groups - 1)) : 0u;
-    return d.lit_tab + (size_t)grp * kLitTab;
+__device__ __forceinline__ uint32_t lit_group(const Dyn& d, int64_t g) {
+    return d.group ? min((uint32_t)d.group[g], (uint32_t)(d.n_groups - 1)) : 0u;
 }
+
+__device__ __forceinline__ const float* lit_row(const Dyn& d, int64_t g) {
+    return d.lit_tab + (size_t)lit_group(d, g) * kLitTab;
+}
+
+// Groups whose table rows the relit projection stages in shared memory (row
+// stride 97 floats: the rows of a warp's groups fall in different banks).
+constexpr int kStageGroups = 64;
+constexpr int kStageStride = kLitTab + 1;
+
+inline int lit_groups(const Dyn& d) { return d.group ? d.n_groups : 1; }
 
 __device__ __forceinline__ float lit_vis(const Dyn& d, int64_t g) {
     return d.vis ? (float)d.vis[g] * (1.f / 255.f) : 1.f;
@@ -195,6 +205,17 @@ k_project(const float4* __restrict__ P, int64_t n, int64_t g_off, int64_t n_out,
           const gs_camera* __restrict__ cams, const ViewInfo* __restrict__ vt, int V, int tile,
           float4* __restrict__ proj, uint64_t* __restrict__ dkv) {
     const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    extern __shared__ float s_lt[];
+    bool staged = false;
+    if (LIT) {
+        const int Gs = dyn.group ? dyn.n_groups : 1;
+        staged = Gs <= kStageGroups;
+        if (staged) {
+            for (int i = threadIdx.x; i < Gs * kLitTab; i += blockDim.x)
+                s_lt[(i / kLitTab) * kStageStride + i % kLitTab] = __ldg(&dyn.lit_tab[i]);
+            __syncthreads();
+        }
+    }
     if (g >= n) return;
     constexpr int NB = (D + 1) * (D + 1);
     constexpr int NPL = (3 * NB + 3) / 4;
@@ -226,7 +247,10 @@ k_project(const float4* __restrict__ P, int64_t n, int64_t g_off, int64_t n_out,
     sh[0] *= G.L; sh[1] *= G.L; sh[2] *= G.L;
     float lrgb[3] = {0.f, 0.f, 0.f};
     uint32_t lmask = 0;
-    if (LIT) relit_rgb<NB>(sh, lit_row(dyn, g_off + g), lit_vis(dyn, g_off + g), lrgb, lmask);
+    if (LIT) {
+        const float* lt = staged ? s_lt + lit_group(dyn, g_off + g) * kStageStride : lit_row(dyn, g_off + g);
+        relit_rgb<NB>(sh, lt, lit_vis(dyn, g_off + g), lrgb, lmask);
+    }
     for (int v = 0; v < V; ++v) {
         const Cam C = load_cam(cams + v);
         const int64_t rec = (int64_t)v * n_out + g_off + g;
@@ -298,8 +322,7 @@ k_project_bwd(const float4* __restrict__ P, int64_t n, int64_t n_out, Dyn dyn, c
 #pragma unroll
     for (int pl = 0; pl < NPL; ++pl) dsh[4 * pl] = dsh[4 * pl + 1] = dsh[4 * pl + 2] = dsh[4 * pl + 3] = 0.f;
     float dmx = 0.f, dmy = 0.f, dmz = 0.f, dlogit = 0.f;
-    const float* lt = LIT ? lit_row(dyn, g) : nullptr;
-    const float lv = LIT ? lit_vis(dyn, g) : 0.f;
+    float gsum[3] = {0.f, 0.f, 0.f};  // relit: colour gradient summed over the views
     float D00 = 0.f, D01 = 0.f, D02 = 0.f, D11 = 0.f, D12 = 0.f, D22 = 0.f;  // dSigma + dSigma^T
     for (int v = 0; v < V; ++v) {
         const int64_t rec = (int64_t)v * n_out + g;
@@ -318,10 +341,9 @@ k_project_bwd(const float4* __restrict__ P, int64_t n, int64_t n_out, Dyn dyn, c
 #pragma unroll
         for (int ch = 0; ch < 3; ++ch) gm[ch] = (mask & (1u << ch)) ? 0.f : grgb[ch];
         if (LIT) {
-            // relit colour: linear in the coefficients, no view dependence
-#pragma unroll
-            for (int j = 0; j < 3 * NB; ++j)
-                dsh[j] += gm[j % 3] * (__ldg(&lt[j]) + lv * __ldg(&lt[48 + j]));
+            // relit colour: the same in every view and linear in the
+            // coefficients, so its gradient is summed first
+            gsum[0] += gm[0]; gsum[1] += gm[1]; gsum[2] += gm[2];
         } else {
         // colour -> SH coefficients and view direction
         float Y[16];
@@ -403,6 +425,12 @@ k_project_bwd(const float4* __restrict__ P, int64_t n, int64_t n_out, Dyn dyn, c
         dmx += W[0] * dtx + W[3] * dty + W[6] * dtz;
         dmy += W[1] * dtx + W[4] * dty + W[7] * dtz;
         dmz += W[2] * dtx + W[5] * dty + W[8] * dtz;
+    }
+    if (LIT) {
+        const float* lt = lit_row(dyn, g);
+        const float lv = lit_vis(dyn, g);
+#pragma unroll
+        for (int j = 0; j < 3 * NB; ++j) dsh[j] = gsum[j % 3] * (__ldg(&lt[j]) + lv * __ldg(&lt[48 + j]));
     }
     if (G.moved) {  // back to the object frame: mean_w = R_g mean + t_g, Sigma_w = R_g Sigma R_g^T
         const float* Rg = G.Rg;
@@ -529,8 +557,9 @@ void launch_project(const float* params, int64_t n, int sh_degree, const Dyn& dy
     const float4* P = reinterpret_cast<const float4*>(params);
     float4* out = reinterpret_cast<float4*>(proj);
     const bool lit = dyn.lit_tab != nullptr;
+    const size_t smem = lit && lit_groups(dyn) <= kStageGroups ? sizeof(float) * lit_groups(dyn) * kStageStride : 0;
 #define GS_PROJ(DD)                                                                                              \
-    (lit ? k_project<DD, true><<<blocks, threads, 0, st>>>(P, n, g_off, n_out, dyn, d_cams, vt, V, tile, out, depth_kv) \
+    (lit ? k_project<DD, true><<<blocks, threads, smem, st>>>(P, n, g_off, n_out, dyn, d_cams, vt, V, tile, out, depth_kv) \
          : k_project<DD, false><<<blocks, threads, 0, st>>>(P, n, g_off, n_out, dyn, d_cams, vt, V, tile, out, depth_kv))
     switch (sh_degree) {
         case 0: GS_PROJ(0); break;
