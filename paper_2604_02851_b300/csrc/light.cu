@@ -5,9 +5,10 @@
 // The paper takes the map from the engine's shadow pass over its meshes; here
 // it is rendered from the Gaussians: texel (i, j) keeps the smallest light
 // depth of the Gaussians whose splat alpha o exp(-q/2) at the texel centre
-// reaches alpha_min.  One warp splats one Gaussian: the lanes stride over the
-// texels of the footprint's bounding box and merge their depth with a float
-// atomic min, so the map does not depend on the order of the Gaussians.
+// reaches alpha_min.  Each lane sets up one Gaussian's footprint, then the
+// warp splats its 32 Gaussians in turn, the lanes striding over the texels of
+// each bounding box and merging depths with a float atomic min, so the map
+// does not depend on the order of the Gaussians.
 #include "gauss.cuh"
 
 namespace gs {
@@ -38,18 +39,23 @@ __device__ __forceinline__ float3 to_light(const gs_light_camera& lc, float3 mu)
     return make_float3(xl / lc.texel + 0.5f * (float)lc.width, yl / lc.texel + 0.5f * (float)lc.height, zl);
 }
 
-__global__ void __launch_bounds__(256)
-k_light_depth(const float4* __restrict__ P, int64_t n, Dyn dyn, gs_light_camera lc, float* __restrict__ depth) {
-    const int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (g >= n) return;
+// Footprint of one Gaussian on the map: centre (u, v), light depth z, conic
+// (A, B, C) in texel units, bound tau = 2 ln(o / alpha_min), and the texel
+// box [i0, i0 + nw) x [j0, j0 + nh).  Returns false when nothing is covered.
+struct Splat {
+    float u, v, z, A, B, C, tau;
+    int i0, j0, nw, nh;
+};
+
+__device__ __forceinline__ bool light_splat(const float4* __restrict__ P, int64_t n, const Dyn& dyn,
+                                            const gs_light_camera& lc, int64_t g, Splat& s) {
     Gauss G;
     load_gauss(P, n, g, G);
     apply_dyn(dyn, g, G);
     const float3 p = to_light(lc, G.mu);
-    // tau = 2 ln(o / alpha_min); nothing is covered below alpha_min
-    const float tau = 2.f * logf(G.opac / lc.alpha_min);
-    if (!(tau >= 0.f) || !isfinite(p.x) || !isfinite(p.y) || !isfinite(p.z)) return;
+    // nothing is covered below alpha_min
+    s.tau = 2.f * logf(G.opac / lc.alpha_min);
+    if (!(s.tau >= 0.f) || !isfinite(p.x) || !isfinite(p.y) || !isfinite(p.z)) return false;
     // Sigma2 = R_2 Sigma R_2^T / texel^2 + 0.3 I
     const float* S = G.S;
     const float* R = lc.R;
@@ -62,26 +68,55 @@ k_light_depth(const float4* __restrict__ P, int64_t n, Dyn dyn, gs_light_camera 
     const float b = (R[3] * S0[0] + R[4] * S0[1] + R[5] * S0[2]) * ih2;
     const float c = (R[3] * S1[0] + R[4] * S1[1] + R[5] * S1[2]) * ih2 + kDilation;
     const float det = a * c - b * b;
-    if (!(det > 0.f)) return;
+    if (!(det > 0.f)) return false;
     const float id = 1.f / det;
-    const float A = c * id, B = -b * id, C = a * id;
+    s.A = c * id; s.B = -b * id; s.C = a * id;
     // q <= tau implies |d|^2 <= tau * lmax; widened a little against rounding
     const float mid = 0.5f * (a + c);
     const float lmax = mid + sqrtf(fmaxf(0.f, mid * mid - det));
-    const float r = sqrtf(tau * lmax) * 1.0001f + 0.01f;
+    const float r = sqrtf(s.tau * lmax) * 1.0001f + 0.01f;
     const float W = (float)lc.width, H = (float)lc.height;
-    const int i0 = (int)fminf(fmaxf(ceilf(p.x - r - 0.5f), 0.f), W);
+    s.i0 = (int)fminf(fmaxf(ceilf(p.x - r - 0.5f), 0.f), W);
     const int i1 = (int)fminf(fmaxf(floorf(p.x + r - 0.5f), -1.f), W - 1.f);
-    const int j0 = (int)fminf(fmaxf(ceilf(p.y - r - 0.5f), 0.f), H);
+    s.j0 = (int)fminf(fmaxf(ceilf(p.y - r - 0.5f), 0.f), H);
     const int j1 = (int)fminf(fmaxf(floorf(p.y + r - 0.5f), -1.f), H - 1.f);
-    if (i1 < i0 || j1 < j0) return;
-    const int nw = i1 - i0 + 1;
-    const int64_t total = (int64_t)nw * (j1 - j0 + 1);
-    for (int64_t t = lane; t < total; t += 32) {
-        const int j = j0 + (int)(t / nw), i = i0 + (int)(t % nw);
-        const float dx = (float)i + 0.5f - p.x, dy = (float)j + 0.5f - p.y;
-        const float q = A * dx * dx + 2.f * B * dx * dy + C * dy * dy;
-        if (q <= tau) atomic_min_float(depth + (int64_t)j * lc.width + i, p.z);
+    s.nw = i1 - s.i0 + 1;
+    s.nh = j1 - s.j0 + 1;
+    s.u = p.x; s.v = p.y; s.z = p.z;
+    return s.nw > 0 && s.nh > 0;
+}
+
+// Each lane sets up one Gaussian's footprint; the warp then walks the
+// footprints one after another, its lanes striding over the texels of each.
+__global__ void __launch_bounds__(256)
+k_light_depth(const float4* __restrict__ P, int64_t n, Dyn dyn, gs_light_camera lc, float* __restrict__ depth) {
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    Splat mine{};
+    const bool ok = g < n && light_splat(P, n, dyn, lc, g, mine);
+    unsigned todo = __ballot_sync(0xffffffffu, ok);
+    while (todo) {
+        const int src = __ffs(todo) - 1;
+        todo &= todo - 1;
+        const float u = __shfl_sync(0xffffffffu, mine.u, src), v = __shfl_sync(0xffffffffu, mine.v, src);
+        const float z = __shfl_sync(0xffffffffu, mine.z, src), tau = __shfl_sync(0xffffffffu, mine.tau, src);
+        const float A = __shfl_sync(0xffffffffu, mine.A, src), B = __shfl_sync(0xffffffffu, mine.B, src);
+        const float C = __shfl_sync(0xffffffffu, mine.C, src);
+        const int i0 = __shfl_sync(0xffffffffu, mine.i0, src), j0 = __shfl_sync(0xffffffffu, mine.j0, src);
+        const int nw = __shfl_sync(0xffffffffu, mine.nw, src), nh = __shfl_sync(0xffffffffu, mine.nh, src);
+        const int total = nw * nh;  // <= 16384^2
+        // texel t = lane + 32 k of the box, row-major; (i, j) advance by 32
+        // texels without a division per step
+        int j = lane / nw, i = lane - j * nw;
+        const int dj = 32 / nw, di = 32 - dj * nw;
+        for (int t = lane; t < total; t += 32) {
+            const float dx = (float)(i0 + i) + 0.5f - u, dy = (float)(j0 + j) + 0.5f - v;
+            const float q = A * dx * dx + 2.f * B * dx * dy + C * dy * dy;
+            if (q <= tau) atomic_min_float(depth + (int64_t)(j0 + j) * lc.width + (i0 + i), z);
+            i += di;
+            j += dj;
+            if (i >= nw) { i -= nw; ++j; }
+        }
     }
 }
 
@@ -119,7 +154,7 @@ void launch_light_depth(const float* params, int64_t n, const Dyn& dyn, const gs
     if (clear) k_light_clear<<<(unsigned)((count + 255) / 256), 256, 0, st>>>(depth, count);
     if (n <= 0) return;
     const int threads = 256;
-    const unsigned blocks = (unsigned)((n * 32 + threads - 1) / threads);
+    const unsigned blocks = (unsigned)((n + threads - 1) / threads);
     k_light_depth<<<blocks, threads, 0, st>>>(reinterpret_cast<const float4*>(params), n, dyn, lc, depth);
 }
 
