@@ -395,7 +395,8 @@ def run_ours(args, rank, world, local_rank):
         ldepth = torch.empty((RELIGHT_MAP, RELIGHT_MAP), dtype=torch.float32, device=dev)
 
     ctx = gs.Context(local_rank, 0, tile=args.tile, sort_bits=args.sort_bits, sort_items=args.sort_items,
-                     binning=args.binning, raster_threads=args.raster_threads)
+                     binning=args.binning, raster_threads=args.raster_threads,
+                     raster_bwd_threads=args.raster_bwd_threads)
     keys_cap = estimate_keys(ctx, params, sh, cams, slack=1.3, dyn=dyn)
     tuned = None
     if args.autotune:
@@ -405,8 +406,9 @@ def run_ours(args, rank, world, local_rank):
         best, entries = gs.gs_autotune(ctx, params, sh, cams, keys_cap, reps=2, dyn=dyn, lighting=lighting)
         args.binning, args.sort_bits = best["binning"], best["sort_bits"]
         args.sort_items, args.raster_threads = best["sort_items"], best["raster_threads"]
+        args.raster_bwd_threads = best["raster_bwd_threads"]
         worst = max(e["ms"] for e in entries)
-        tuned = {"configs_tried": len(entries), "best_ms": best["ms"], "worst_ms": worst,
+        tuned = {"configs_tried": len(entries), "best_ms": min(e["ms"] for e in entries), "worst_ms": worst,
                  "timed": "projection + bin/sort + compositing + its adjoint"}
     frozen = None
     if args.frozen_frac > 0:
@@ -429,7 +431,8 @@ def run_ours(args, rank, world, local_rank):
                        lighting=lighting)
     packed = tr.packed
     tctx = gs.Context(local_rank, 0, tile=args.tile, sort_bits=args.sort_bits, sort_items=args.sort_items,
-                     binning=args.binning, raster_threads=args.raster_threads)
+                     binning=args.binning, raster_threads=args.raster_threads,
+                     raster_bwd_threads=args.raster_bwd_threads)
     tkeys = estimate_keys(tctx, tparams, sh, cams, slack=1.3, dyn=dyn)
     tctx.reserve(tctx.workspace_size(packed, n, tkeys))
 
@@ -599,7 +602,8 @@ def run_ours(args, rank, world, local_rank):
     if args.e2e_steps > 0:
         def make_ctx():
             return gs.Context(local_rank, 0, tile=args.tile, sort_bits=args.sort_bits, sort_items=args.sort_items,
-                              binning=args.binning, raster_threads=args.raster_threads)
+                              binning=args.binning, raster_threads=args.raster_threads,
+                     raster_bwd_threads=args.raster_bwd_threads)
         e2e = run_e2e(args, host_targets, params, sh, cams, keys_cap, make_ctx, dyn, world, lighting)
         del host_targets
     serving = None
@@ -629,7 +633,8 @@ def run_ours(args, rank, world, local_rank):
                           if dynamic else None,
                           "relight": relight,
                           "sort_digit_bits": args.sort_bits, "sort_items": args.sort_items, "binning": args.binning,
-                          "raster_threads_per_row": args.raster_threads, "autotune": tuned,
+                          "raster_threads_per_row": args.raster_threads,
+                          "raster_bwd_threads_per_row": args.raster_bwd_threads, "autotune": tuned,
                           "frozen_fraction": args.frozen_frac, "precull": bool(args.precull),
                           "far_gaussians": n_far,
                           "graph": True,
@@ -784,6 +789,8 @@ def main():
     ap.add_argument("--sort-items", type=int, default=16)
     ap.add_argument("--binning", choices=("two_level", "direct"), default="two_level")
     ap.add_argument("--raster-threads", type=int, choices=(2, 4), default=4)
+    ap.add_argument("--raster-bwd-threads", type=int, choices=(2, 4), default=None,
+                    help="threads per pixel row of the compositing adjoint (default: --raster-threads)")
     ap.add_argument("--autotune", action=argparse.BooleanOptionalAction, default=True,
                     help="choose binning / sort / raster settings with gs_autotune before timing")
     ap.add_argument("--e2e-steps", type=int, default=30)
@@ -802,6 +809,8 @@ def main():
                     help="time per-attribute tensor-delta extraction and replay after the timed steps")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    if args.raster_bwd_threads is None:
+        args.raster_bwd_threads = args.raster_threads
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -183,27 +183,40 @@ gs_status_t gs_ctx_set_sort_items(gs_ctx* ctx, int32_t items);
 #define GS_BINNING_TWO_LEVEL 0
 #define GS_BINNING_DIRECT 1
 gs_status_t gs_ctx_set_binning(gs_ctx* ctx, int32_t mode);
-/* Threads per pixel row of a 16 x 16 tile in compositing and its adjoint (2
- * or 4; default 4): each thread owns 16 / threads_per_row adjacent pixels.
+/* Threads per pixel row of a 16 x 16 tile (2 or 4; default 4) in compositing
+ * and in its adjoint: each thread owns 16 / threads_per_row adjacent pixels.
  * Fewer threads per row share each fragment's loads and gradient reduction
- * among more pixels.  8 x 8 tiles always use 4.  Results are identical up to
- * the order of floating-point gradient sums. */
+ * among more pixels; more threads per row give more warps per tile.  8 x 8
+ * tiles always use 4.  Results are identical up to the order of
+ * floating-point gradient sums.  gs_ctx_set_raster_threads sets both kernels,
+ * gs_ctx_set_raster_bwd_threads the adjoint alone. */
 gs_status_t gs_ctx_set_raster_threads(gs_ctx* ctx, int32_t threads_per_row);
+gs_status_t gs_ctx_set_raster_bwd_threads(gs_ctx* ctx, int32_t threads_per_row);
+/* The context's current binning mode (GS_BINNING_*), digit width, items per
+ * thread and the compositing / adjoint threads per row (any pointer may be
+ * NULL). */
+gs_status_t gs_ctx_get_tuning(const gs_ctx* ctx, int32_t* binning, int32_t* sort_bits, int32_t* sort_items,
+                              int32_t* raster_threads, int32_t* raster_bwd_threads);
 /* One configuration timed by gs_autotune. */
 typedef struct gs_tune_entry {
     int32_t binning;         /* GS_BINNING_* */
     int32_t sort_bits;       /* radix digit width */
     int32_t sort_items;      /* keys per thread per sort tile */
-    int32_t raster_threads;  /* threads per pixel row */
+    int32_t raster_threads;  /* threads per pixel row (both compositing kernels) */
     float ms;                /* mean time of one pass */
+    float ms_render_fwd;     /* of which compositing */
+    float ms_render_bwd;     /* of which its adjoint */
 } gs_tune_entry;
 
 /* Autotuner.  Times projection, binning and sorting, compositing and the
  * compositing adjoint of `scene` for the cameras (device copy d_cams, host copy
  * host_cams) under every combination of binning {two-level, direct} x digit
  * bits {8, 7, 6} x items per thread {16, 12, 8} x threads per pixel row
- * {4, 2} (8-px tiles: 4 only), `reps` passes each after one warm-up pass, and
- * leaves the context set to the fastest.  The tile size is kept (it defines the
+ * {4, 2} (8-px tiles: 4 only), `reps` passes each after one warm-up pass.  It
+ * leaves the context set to the binning and sort settings with the smallest
+ * time outside compositing (the sorted lists, and so the compositing cost, do
+ * not depend on them), and to the compositing and adjoint layouts that are
+ * fastest on their own.  The tile size is kept (it defines the
  * caller's tile grid).  The adjoint is fed the rendered image as its image
  * gradient; its cost does not depend on the values.  Workspace: gs_workspace_size(ctx, host_cams, V,
  * n, keys_cap).  Synchronous (it waits on events), so not for stream capture;

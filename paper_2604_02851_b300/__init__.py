@@ -85,7 +85,8 @@ class Context:
     """Owns a gs_ctx (device workspace, status word, graph)."""
 
     def __init__(self, device: int = 0, workspace_bytes: int = 0, tile: int = 16, sort_bits: int = 8,
-                 sort_items: int = 16, binning: str = "two_level", raster_threads: int = 4):
+                 sort_items: int = 16, binning: str = "two_level", raster_threads: int = 4,
+                 raster_bwd_threads: "int | None" = None):
         L = _lib.lib()
         p = C.c_void_p()
         check("gs_ctx_create", L.gs_ctx_create(C.byref(p), device, workspace_bytes))
@@ -101,6 +102,16 @@ class Context:
         check("gs_ctx_set_binning", L.gs_ctx_set_binning(p, BINNING[binning]))
         self.raster_threads = raster_threads
         check("gs_ctx_set_raster_threads", L.gs_ctx_set_raster_threads(p, raster_threads))
+        self.raster_bwd_threads = raster_threads if raster_bwd_threads is None else raster_bwd_threads
+        check("gs_ctx_set_raster_bwd_threads", L.gs_ctx_set_raster_bwd_threads(p, self.raster_bwd_threads))
+
+    def tuning(self) -> dict:
+        """The context's current tunables (gs_ctx_get_tuning)."""
+        v = [C.c_int32() for _ in range(5)]
+        check("gs_ctx_get_tuning", _lib.lib().gs_ctx_get_tuning(self.ptr, *(C.byref(x) for x in v)))
+        names = {val: k for k, val in BINNING.items()}
+        return {"binning": names[v[0].value], "sort_bits": v[1].value, "sort_items": v[2].value,
+                "raster_threads": v[3].value, "raster_bwd_threads": v[4].value}
 
     def reserve(self, nbytes: int) -> None:
         check("gs_ctx_reserve", _lib.lib().gs_ctx_reserve(self.ptr, int(nbytes)))
@@ -519,8 +530,10 @@ def gs_render_batch(ctx, params, sh_degree, d_cams, n_requests, total_tiles, key
 
 def gs_autotune(ctx, params, sh_degree, cams, keys_cap, reps=3, stream=None, dyn=None, lighting=None):
     """Time the render/adjoint path over the tunables (gs_autotune) and leave
-    `ctx` set to the fastest.  Returns (best, entries): dicts with binning,
-    sort_bits, sort_items, raster_threads and ms."""
+    `ctx` set to the fastest: binning and sort settings by their time outside
+    compositing, the compositing and adjoint layouts each on its own.  Returns
+    (chosen, entries): chosen is ctx.tuning(); entries are dicts with binning,
+    sort_bits, sort_items, raster_threads, ms, ms_render_fwd, ms_render_bwd."""
     packed, host = _host_cams(cams)
     V = len(packed)
     d_cams = cameras_to_device(packed, params.device)
@@ -531,10 +544,12 @@ def gs_autotune(ctx, params, sh_degree, cams, keys_cap, reps=3, stream=None, dyn
                                                 int(reps), out, 64, C.byref(cnt), _stream(stream)))
     names = {v: k for k, v in BINNING.items()}
     entries = [{"binning": names[e.binning], "sort_bits": e.sort_bits, "sort_items": e.sort_items,
-                "raster_threads": e.raster_threads, "ms": float(e.ms)} for e in out[:cnt.value]]
-    best = min(entries, key=lambda e: e["ms"])
-    ctx.binning, ctx.raster_threads = best["binning"], best["raster_threads"]
-    return best, entries
+                "raster_threads": e.raster_threads, "ms": float(e.ms), "ms_render_fwd": float(e.ms_render_fwd),
+                "ms_render_bwd": float(e.ms_render_bwd)} for e in out[:cnt.value]]
+    chosen = ctx.tuning()
+    ctx.binning, ctx.raster_threads = chosen["binning"], chosen["raster_threads"]
+    ctx.raster_bwd_threads = chosen["raster_bwd_threads"]
+    return chosen, entries
 
 
 def train_io(params, grads, m, v, baseline, targets, image, d_loss, d_idx, d_records, d_count, d_step, frozen=None):

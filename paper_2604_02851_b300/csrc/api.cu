@@ -217,6 +217,24 @@ gs_status_t gs_ctx_set_binning(gs_ctx* ctx, int32_t mode) {
 gs_status_t gs_ctx_set_raster_threads(gs_ctx* ctx, int32_t threads_per_row) {
     if (!ctx || (threads_per_row != 2 && threads_per_row != 4)) return GS_ERR_ARG;
     ctx->raster_tpr = threads_per_row;
+    ctx->raster_bwd_tpr = threads_per_row;
+    return GS_OK;
+}
+
+gs_status_t gs_ctx_set_raster_bwd_threads(gs_ctx* ctx, int32_t threads_per_row) {
+    if (!ctx || (threads_per_row != 2 && threads_per_row != 4)) return GS_ERR_ARG;
+    ctx->raster_bwd_tpr = threads_per_row;
+    return GS_OK;
+}
+
+gs_status_t gs_ctx_get_tuning(const gs_ctx* ctx, int32_t* binning, int32_t* sort_bits, int32_t* sort_items,
+                              int32_t* raster_threads, int32_t* raster_bwd_threads) {
+    if (!ctx) return GS_ERR_ARG;
+    if (binning) *binning = ctx->binning == kBinDirect ? GS_BINNING_DIRECT : GS_BINNING_TWO_LEVEL;
+    if (sort_bits) *sort_bits = ctx->sort_bits;
+    if (sort_items) *sort_items = ctx->sort_items;
+    if (raster_threads) *raster_threads = ctx->raster_tpr;
+    if (raster_bwd_threads) *raster_bwd_threads = ctx->raster_bwd_tpr;
     return GS_OK;
 }
 
@@ -330,7 +348,7 @@ gs_status_t gs_raster_bwd(gs_ctx* ctx, const float* proj, const gs_camera* d_cam
     DeviceGuard g(ctx->device);
     const float3 b = bg ? make_float3(bg[0], bg[1], bg[2]) : make_float3(0.f, 0.f, 0.f);
     launch_view_table(d_cams, n_views, ctx->tile, vt, total_tiles, ctx->d_status, S(stream));
-    launch_raster_bwd(proj, vt, n_views, n, ctx->tile, ctx->raster_tpr, sorted_vals, ranges, b, T_final, n_contrib, dimage,
+    launch_raster_bwd(proj, vt, n_views, n, ctx->tile, ctx->raster_bwd_tpr, sorted_vals, ranges, b, T_final, n_contrib, dimage,
                       grad2d, total_tiles, S(stream));
     return launch_check();
 }
@@ -511,7 +529,7 @@ gs_status_t gs_train_step_events(gs_ctx* ctx, const gs_camera* d_cams, const gs_
     launch_loss(io->image, io->targets, V, cfg->height, cfg->width, cfg->w_l1, cfg->w_ssim, io->d_loss, p.dimage,
                 p.loss, st);
     mark(ev, 6, st);
-    launch_raster_bwd(p.proj, p.vt, V, n, B, ctx->raster_tpr, p.vals, p.ranges, b, p.T_final, p.n_contrib, p.dimage, p.grad2d, tt,
+    launch_raster_bwd(p.proj, p.vt, V, n, B, ctx->raster_bwd_tpr, p.vals, p.ranges, b, p.T_final, p.n_contrib, p.dimage, p.grad2d, tt,
                       st, na);
     mark(ev, 7, st);
     launch_project_bwd(io->params, na, cfg->sh_degree, dyn, d_cams, V, p.proj, p.grad2d, io->grads, 0, st, n);
@@ -554,28 +572,46 @@ gs_status_t gs_autotune(gs_ctx* ctx, const gs_scene* scene, const gs_camera* d_c
     // the adjoint then reads (its cost does not depend on the values)
     float* image = p.dimage;
     const float3 bg = make_float3(0.f, 0.f, 0.f);
-    auto run = [&]() {
+    // ev (may be null): recorded before compositing, between compositing and
+    // its adjoint, and after the adjoint
+    auto run = [&](cudaEvent_t* ev) {
         launch_view_table(d_cams, V, B, p.vt, tt, ctx->d_status, st);
         launch_project(scene->params, n, scene->sh_degree, dyn, d_cams, p.vt, V, B, p.proj, s.dkv[0], st);
         launch_bin_sort(p.proj, p.vt, V, n, keys_cap, tt, ctx->binning, ctx->sort_bits, ctx->sort_items, s, true,
                         nullptr, p.vals, p.ranges, p.n_keys, ctx->d_status, ctx->sm_count, st, nullptr, nullptr, 0,
                         scene->precull != nullptr);
+        if (ev) cudaEventRecord(ev[0], st);
         launch_render_fwd(p.proj, p.vt, V, n, B, ctx->raster_tpr, p.vals, p.ranges, bg, image, p.T_final,
                           p.n_contrib, tt, st);
-        launch_raster_bwd(p.proj, p.vt, V, n, B, ctx->raster_tpr, p.vals, p.ranges, bg, p.T_final, p.n_contrib,
+        if (ev) cudaEventRecord(ev[1], st);
+        launch_raster_bwd(p.proj, p.vt, V, n, B, ctx->raster_bwd_tpr, p.vals, p.ranges, bg, p.T_final, p.n_contrib,
                           p.dimage, p.grad2d, tt, st);
+        if (ev) cudaEventRecord(ev[2], st);
     };
-    cudaEvent_t e0, e1;
-    if (cudaEventCreate(&e0) != cudaSuccess) return GS_ERR_CUDA;
-    if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return GS_ERR_CUDA; }
+    constexpr int kMaxReps = 16;
+    const int nrep = reps < kMaxReps ? reps : kMaxReps;
+    cudaEvent_t ev[2 + 3 * kMaxReps];
+    int made = 0;
+    while (made < 2 + 3 * nrep && cudaEventCreate(&ev[made]) == cudaSuccess) ++made;
+    auto destroy_events = [&]() {
+        for (int i = 0; i < made; ++i) cudaEventDestroy(ev[i]);
+    };
+    if (made < 2 + 3 * nrep) {
+        destroy_events();
+        return GS_ERR_CUDA;
+    }
+    cudaEvent_t e0 = ev[0], e1 = ev[1];
+    cudaEvent_t(*er)[3] = reinterpret_cast<cudaEvent_t(*)[3]>(ev + 2);
     const int keep_bin = ctx->binning, keep_bits = ctx->sort_bits, keep_items = ctx->sort_items,
-              keep_tpr = ctx->raster_tpr;
+              keep_tpr = ctx->raster_tpr, keep_btpr = ctx->raster_bwd_tpr;
     const int bins[2] = {kBinTwoLevel, kBinDirect};
     const int bitss[3] = {8, 7, 6};
     const int itemss[3] = {16, 12, 8};
     const int tprs[2] = {4, 2};
-    float best = -1.f;
-    int bb = keep_bin, bbits = keep_bits, bitems = keep_items, btpr = keep_tpr;
+    // per configuration: time outside compositing; per layout: the best
+    // compositing and adjoint times seen
+    float best_pre = -1.f, best_fwd[2] = {-1.f, -1.f}, best_bwd[2] = {-1.f, -1.f};
+    int bb = keep_bin, bbits = keep_bits, bitems = keep_items;
     int32_t count = 0;
     gs_status_t rc = GS_OK;
     for (int ib = 0; ib < 2 && rc == GS_OK; ++ib)
@@ -587,9 +623,10 @@ gs_status_t gs_autotune(gs_ctx* ctx, const gs_scene* scene, const gs_camera* d_c
                     ctx->sort_bits = bitss[ibits];
                     ctx->sort_items = itemss[iit];
                     ctx->raster_tpr = tprs[itp];
-                    run();  // warm-up
+                    ctx->raster_bwd_tpr = tprs[itp];
+                    run(nullptr);  // warm-up
                     cudaEventRecord(e0, st);
-                    for (int r = 0; r < reps; ++r) run();
+                    for (int r = 0; r < reps; ++r) run(r < nrep ? er[r] : nullptr);
                     cudaEventRecord(e1, st);
                     if (cudaEventSynchronize(e1) != cudaSuccess) { rc = GS_ERR_CUDA; break; }
                     DevStatus h{};
@@ -598,9 +635,18 @@ gs_status_t gs_autotune(gs_ctx* ctx, const gs_scene* scene, const gs_camera* d_c
                         break;
                     }
                     if (h.code != GS_OK) { rc = (gs_status_t)h.code; break; }  // left in the status word
-                    float ms = 0.f;
+                    float ms = 0.f, fwd = 0.f, bwd = 0.f;
                     cudaEventElapsedTime(&ms, e0, e1);
                     ms /= (float)reps;
+                    for (int r = 0; r < nrep; ++r) {
+                        float a = 0.f, b = 0.f;
+                        cudaEventElapsedTime(&a, er[r][0], er[r][1]);
+                        cudaEventElapsedTime(&b, er[r][1], er[r][2]);
+                        fwd += a;
+                        bwd += b;
+                    }
+                    fwd /= (float)nrep;
+                    bwd /= (float)nrep;
                     if (count < max_results) {
                         gs_tune_entry& t = results[count];
                         t.binning = bins[ib] == kBinDirect ? GS_BINNING_DIRECT : GS_BINNING_TWO_LEVEL;
@@ -608,21 +654,29 @@ gs_status_t gs_autotune(gs_ctx* ctx, const gs_scene* scene, const gs_camera* d_c
                         t.sort_items = itemss[iit];
                         t.raster_threads = tprs[itp];
                         t.ms = ms;
+                        t.ms_render_fwd = fwd;
+                        t.ms_render_bwd = bwd;
                     }
                     ++count;
-                    if (best < 0.f || ms < best) {
-                        best = ms;
-                        bb = bins[ib]; bbits = bitss[ibits]; bitems = itemss[iit]; btpr = tprs[itp];
+                    const float pre = ms - fwd - bwd;
+                    if (best_pre < 0.f || pre < best_pre) {
+                        best_pre = pre;
+                        bb = bins[ib]; bbits = bitss[ibits]; bitems = itemss[iit];
                     }
+                    if (best_fwd[itp] < 0.f || fwd < best_fwd[itp]) best_fwd[itp] = fwd;
+                    if (best_bwd[itp] < 0.f || bwd < best_bwd[itp]) best_bwd[itp] = bwd;
                 }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
+    destroy_events();
     if (n_results) *n_results = count < max_results ? count : max_results;
     if (rc != GS_OK) {
-        ctx->binning = keep_bin; ctx->sort_bits = keep_bits; ctx->sort_items = keep_items; ctx->raster_tpr = keep_tpr;
+        ctx->binning = keep_bin; ctx->sort_bits = keep_bits; ctx->sort_items = keep_items;
+        ctx->raster_tpr = keep_tpr; ctx->raster_bwd_tpr = keep_btpr;
         return rc;
     }
-    ctx->binning = bb; ctx->sort_bits = bbits; ctx->sort_items = bitems; ctx->raster_tpr = btpr;
+    ctx->binning = bb; ctx->sort_bits = bbits; ctx->sort_items = bitems;
+    // a layout never timed (8-px tiles) keeps -1 and loses
+    ctx->raster_tpr = (best_fwd[1] >= 0.f && best_fwd[1] < best_fwd[0]) ? tprs[1] : tprs[0];
+    ctx->raster_bwd_tpr = (best_bwd[1] >= 0.f && best_bwd[1] < best_bwd[0]) ? tprs[1] : tprs[0];
     return launch_check();
 }
 

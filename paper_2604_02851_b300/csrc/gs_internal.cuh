@@ -241,7 +241,8 @@ struct gs_ctx {
     int sort_bits = 8;
     int sort_items = 16;
     int binning = gs::kBinTwoLevel;
-    int raster_tpr = 4;
+    int raster_tpr = 4;       // compositing: threads per pixel row
+    int raster_bwd_tpr = 4;   // its adjoint
     void* ws = nullptr;
     size_t ws_bytes = 0;
     gs::DevStatus* d_status = nullptr;

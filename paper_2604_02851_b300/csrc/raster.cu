@@ -8,9 +8,12 @@
 // serve several pixels.
 //
 // Forward: per pixel, alpha = min(0.99, o e^P) with P the conic quadratic
-// form, skipped when P > 0 or alpha < 1/255 (tested as P log2(e) <
-// -log2(255 o) before the exponential, which is evaluated in base 2);
-// compositing stops before the fragment that would take T below 1e-4.  A block leaves as soon as every pixel is done (block vote).
+// form (P <= 0: the conic is positive definite), skipped when alpha < 1/255
+// (tested as P log2(e) < -log2(255 o) before the exponential, which is
+// evaluated in base 2); compositing stops before the fragment that would take
+// T below 1e-4.  A block leaves as soon as every pixel is done (block vote).
+// A thread's pixels are processed in pairs with packed float2 arithmetic
+// (one instruction for both pixels of a pair), without a branch per pixel.
 //
 // Backward: no per-fragment state is stored.  Each pixel starts from its
 // final transmittance and last-contributor position and walks its list
@@ -60,7 +63,8 @@ k_render_fwd(const float4* __restrict__ proj, const ViewInfo* __restrict__ vt, i
              float* __restrict__ image, float* __restrict__ T_final, uint32_t* __restrict__ n_contrib) {
     constexpr int NT = B * TPR;        // threads per block
     constexpr int PX = B / TPR;        // pixels per thread
-    static_assert(NT % 32 == 0, "whole warps");
+    constexpr int NP = PX / 2;         // pixel pairs per thread
+    static_assert(NT % 32 == 0 && PX % 2 == 0, "whole warps, pixel pairs");
     constexpr int BATCH = 2 * NT;      // fragments staged per round
     __shared__ float4 s_a[BATCH];      // u, v, opacity, log2 cut-off
     __shared__ float4 s_q[BATCH];      // base-2 conic coefficients
@@ -78,16 +82,26 @@ k_render_fwd(const float4* __restrict__ proj, const ViewInfo* __restrict__ vt, i
     const uint2 rg = ranges[gt];
     const int64_t rbase = (int64_t)v * n;
 
-    float T[PX], Cr[PX], Cg[PX], Cb[PX];
+    // pixel pairs (2p, 2p + 1) in packed float2 registers.  pen is added to
+    // a pixel's exponent: 0 while it composites, -inf once it has stopped (or
+    // lies outside the image), which fails the alpha cut-off test.
+    const float kNegInf = __int_as_float(0xff800000);
+    float2 T[NP], Cr[NP], Cg[NP], Cb[NP], pen[NP];
     uint32_t last[PX];
-    uint32_t live = 0;  // bit k: pixel k still compositing
+    int nlive = 0;  // pixels of this thread still compositing
 #pragma unroll
-    for (int k = 0; k < PX; ++k) {
-        T[k] = 1.f; Cr[k] = Cg[k] = Cb[k] = 0.f; last[k] = 0;
-        if (px0 + k < vi.width && py < vi.height) live |= 1u << k;
+    for (int p = 0; p < NP; ++p) {
+        T[p] = make_float2(1.f, 1.f);
+        Cr[p] = Cg[p] = Cb[p] = make_float2(0.f, 0.f);
+        const bool in0 = px0 + 2 * p < vi.width && py < vi.height;
+        const bool in1 = px0 + 2 * p + 1 < vi.width && py < vi.height;
+        pen[p] = make_float2(in0 ? 0.f : kNegInf, in1 ? 0.f : kNegInf);
+        nlive += (int)in0 + (int)in1;
     }
+#pragma unroll
+    for (int k = 0; k < PX; ++k) last[k] = 0;
     for (uint32_t start = rg.x; start < rg.y; start += BATCH) {
-        if (__syncthreads_count(live != 0) == 0) break;
+        if (__syncthreads_count(nlive != 0) == 0) break;
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const int slot = threadIdx.x + h * NT;
@@ -102,27 +116,43 @@ k_render_fwd(const float4* __restrict__ proj, const ViewInfo* __restrict__ vt, i
         }
         __syncthreads();
         const int cnt = (int)min((uint32_t)BATCH, rg.y - start);
-        for (int j = 0; j < cnt && live; ++j) {
+        for (int j = 0; j < cnt && nlive; ++j) {
             const float4 a = s_a[j];
             const float4 q = s_q[j];
             const float dy = a.y - fy;
             const float qb = q.y * dy;
             const float qc = q.z * dy * dy;
             const float dx0 = a.x - fx0;
+            const float2 qx2 = make_float2(q.x, q.x), qb2 = make_float2(qb, qb), qc2 = make_float2(qc, qc);
+            const float2 o2 = make_float2(a.z, a.z);
+            const uint32_t pos1 = start + j - rg.x + 1;
 #pragma unroll
-            for (int k = 0; k < PX; ++k) {
-                if (!(live & (1u << k))) continue;
-                const float dx = dx0 - (float)k;
-                const float P2 = (q.x * dx + qb) * dx + qc;
-                if (P2 > 0.f || P2 < a.w) continue;
-                const float al = fminf(kAlphaMax, a.z * ex2(P2));
-                const float Tn = T[k] * (1.f - al);
-                if (Tn < kTMin) { live &= ~(1u << k); continue; }
+            for (int p = 0; p < NP; ++p) {
+                const int k0 = 2 * p, k1 = 2 * p + 1;
+                const float2 dx = make_float2(dx0 - (float)k0, dx0 - (float)k1);
+                // the conic is positive definite, so P2 <= 0 up to rounding;
+                // the fragment counts where alpha >= 1/255
+                const float2 P2 = __fadd2_rn(__ffma2_rn(__ffma2_rn(qx2, dx, qb2), dx, qc2), pen[p]);
+                bool v0 = P2.x >= a.w, v1 = P2.y >= a.w;
+                if (!(v0 || v1)) continue;
+                const float2 raw = __fmul2_rn(o2, make_float2(v0 ? ex2(P2.x) : 0.f, v1 ? ex2(P2.y) : 0.f));
+                float2 al = make_float2(fminf(kAlphaMax, raw.x), fminf(kAlphaMax, raw.y));
+                float2 Tn = __fmul2_rn(T[p], __ffma2_rn(al, make_float2(-1.f, -1.f), make_float2(1.f, 1.f)));
+                // T >= 1e-4 holds for every pixel still compositing, and a pixel
+                // this fragment misses keeps its T: only a covered pixel can
+                // fall below.  It stops before this fragment.
+                if (Tn.x < kTMin || Tn.y < kTMin) {
+                    if (Tn.x < kTMin) { al.x = 0.f; Tn.x = T[p].x; pen[p].x = kNegInf; v0 = false; --nlive; }
+                    if (Tn.y < kTMin) { al.y = 0.f; Tn.y = T[p].y; pen[p].y = kNegInf; v1 = false; --nlive; }
+                }
                 const float4 c = s_c[j];
-                const float w = al * T[k];
-                Cr[k] += c.x * w; Cg[k] += c.y * w; Cb[k] += c.z * w;
-                T[k] = Tn;
-                last[k] = start + j - rg.x + 1;
+                const float2 w = __fmul2_rn(al, T[p]);
+                Cr[p] = __ffma2_rn(w, make_float2(c.x, c.x), Cr[p]);
+                Cg[p] = __ffma2_rn(w, make_float2(c.y, c.y), Cg[p]);
+                Cb[p] = __ffma2_rn(w, make_float2(c.z, c.z), Cb[p]);
+                T[p] = Tn;
+                if (v0) last[k0] = pos1;
+                if (v1) last[k1] = pos1;
             }
         }
     }
@@ -133,10 +163,12 @@ k_render_fwd(const float4* __restrict__ proj, const ViewInfo* __restrict__ vt, i
         const int px = px0 + k;
         if (px >= vi.width || py >= vi.height) continue;
         const int64_t pix = (int64_t)py * vi.width + px;
-        img[pix] = Cr[k] + T[k] * bg.x;
-        img[HW + pix] = Cg[k] + T[k] * bg.y;
-        img[2 * HW + pix] = Cb[k] + T[k] * bg.z;
-        if (T_final) T_final[vi.pix_off + pix] = T[k];
+        const float2 t2 = T[k >> 1], r2 = Cr[k >> 1], g2 = Cg[k >> 1], b2 = Cb[k >> 1];
+        const float Tk = (k & 1) ? t2.y : t2.x;
+        img[pix] = ((k & 1) ? r2.y : r2.x) + Tk * bg.x;
+        img[HW + pix] = ((k & 1) ? g2.y : g2.x) + Tk * bg.y;
+        img[2 * HW + pix] = ((k & 1) ? b2.y : b2.x) + Tk * bg.z;
+        if (T_final) T_final[vi.pix_off + pix] = Tk;
         if (n_contrib) n_contrib[vi.pix_off + pix] = last[k];
     }
 }
@@ -196,7 +228,8 @@ k_raster_bwd(const float4* __restrict__ proj, const ViewInfo* __restrict__ vt, i
              const float* __restrict__ dimage, float* __restrict__ grad2d, int64_t n_active) {
     constexpr int NT = B * TPR;
     constexpr int PX = B / TPR;
-    static_assert(NT % 32 == 0, "whole warps");
+    constexpr int NP = PX / 2;
+    static_assert(NT % 32 == 0 && PX % 2 == 0, "whole warps, pixel pairs");
     constexpr int BATCH = NT;
     __shared__ float4 s_a[BATCH];   // u, v, opacity, log2 cut-off
     __shared__ float4 s_q[BATCH];   // base-2 conic coefficients
@@ -219,23 +252,31 @@ k_raster_bwd(const float4* __restrict__ proj, const ViewInfo* __restrict__ vt, i
     const int64_t rbase = (int64_t)v * n;
     const int lane = threadIdx.x & 31;
 
-    float T[PX], dCr[PX], dCg[PX], dCb[PX], Rr[PX], Rg[PX], Rb[PX];
+    // pixel pairs (2p, 2p + 1) in packed float2 registers
+    float2 T[NP], dCr[NP], dCg[NP], dCb[NP], Rr[NP], Rg[NP], Rb[NP];
     uint32_t last[PX];
     uint32_t mylast = 0;
     const int64_t HW = (int64_t)vi.width * vi.height;
     const float* dimg = dimage + 3 * vi.pix_off;
 #pragma unroll
-    for (int k = 0; k < PX; ++k) {
-        const int px = px0 + k;
-        T[k] = 1.f; dCr[k] = dCg[k] = dCb[k] = 0.f; last[k] = 0;
-        Rr[k] = bg.x; Rg[k] = bg.y; Rb[k] = bg.z;
-        if (px < vi.width && py < vi.height) {
-            const int64_t pix = (int64_t)py * vi.width + px;
-            T[k] = T_final[vi.pix_off + pix];
-            last[k] = n_contrib[vi.pix_off + pix];
-            dCr[k] = dimg[pix]; dCg[k] = dimg[HW + pix]; dCb[k] = dimg[2 * HW + pix];
-            mylast = max(mylast, last[k]);
+    for (int p = 0; p < NP; ++p) {
+        float t[2] = {1.f, 1.f}, r[2] = {0.f, 0.f}, g[2] = {0.f, 0.f}, b[2] = {0.f, 0.f};
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const int k = 2 * p + e;
+            const int px = px0 + k;
+            last[k] = 0;
+            if (px < vi.width && py < vi.height) {
+                const int64_t pix = (int64_t)py * vi.width + px;
+                t[e] = T_final[vi.pix_off + pix];
+                last[k] = n_contrib[vi.pix_off + pix];
+                r[e] = dimg[pix]; g[e] = dimg[HW + pix]; b[e] = dimg[2 * HW + pix];
+                mylast = max(mylast, last[k]);
+            }
         }
+        T[p] = make_float2(t[0], t[1]);
+        dCr[p] = make_float2(r[0], r[1]); dCg[p] = make_float2(g[0], g[1]); dCb[p] = make_float2(b[0], b[1]);
+        Rr[p] = make_float2(bg.x, bg.x); Rg[p] = make_float2(bg.y, bg.y); Rb[p] = make_float2(bg.z, bg.z);
     }
     if (threadIdx.x == 0) s_max = 0;
     __syncthreads();
@@ -270,43 +311,56 @@ k_raster_bwd(const float4* __restrict__ proj, const ViewInfo* __restrict__ vt, i
             const float qb = q.y * dy;
             const float qc = q.z * dy * dy;
             const float dx0 = a.x - fx0;
-            float s0 = 0.f, s1 = 0.f, s2 = 0.f, g5 = 0.f, g6 = 0.f, g7 = 0.f, g8 = 0.f;
+            const float2 qx2 = make_float2(q.x, q.x), qb2 = make_float2(qb, qb), qc2 = make_float2(qc, qc);
+            const float2 o2 = make_float2(a.z, a.z), m1 = make_float2(-1.f, -1.f), one = make_float2(1.f, 1.f);
+            const float2 cr = make_float2(c.x, c.x), cg = make_float2(c.y, c.y), cb = make_float2(c.z, c.z);
+            const float2 zero = make_float2(0.f, 0.f);
+            float2 s0 = zero, s1 = zero, s2 = zero, g6 = zero, g7 = zero, g8 = zero;
             bool contrib = false;
 #pragma unroll
-            for (int k = 0; k < PX; ++k) {
-                if (pos >= last[k]) continue;
-                const float dx = dx0 - (float)k;
-                const float P2 = (q.x * dx + qb) * dx + qc;
-                if (P2 > 0.f || P2 < a.w) continue;
+            for (int p = 0; p < NP; ++p) {
+                const int k0 = 2 * p, k1 = 2 * p + 1;
+                const float2 dx = make_float2(dx0 - (float)k0, dx0 - (float)k1);
+                const float2 P2 = __ffma2_rn(__ffma2_rn(qx2, dx, qb2), dx, qc2);
+                const bool v0 = pos < last[k0] && P2.x >= a.w;
+                const bool v1 = pos < last[k1] && P2.y >= a.w;
+                if (!(v0 || v1)) continue;
                 contrib = true;
-                const float G = ex2(P2);
-                const float raw = a.z * G;
-                const float al = fminf(kAlphaMax, raw);
-                const float Tj = T[k] * rcp_approx(1.f - al);
-                T[k] = Tj;
-                const float w = al * Tj;
-                g6 += w * dCr[k]; g7 += w * dCg[k]; g8 += w * dCb[k];
-                const float er = c.x - Rr[k], eg = c.y - Rg[k], eb = c.z - Rb[k];
-                const float dal = Tj * (dCr[k] * er + dCg[k] * eg + dCb[k] * eb);
-                Rr[k] += al * er;
-                Rg[k] += al * eg;
-                Rb[k] += al * eb;
-                const bool free = raw <= kAlphaMax;
-                const float dP = free ? dal * raw : 0.f;
-                g5 += free ? dal * G : 0.f;
-                const float t = dP * dx;
-                s0 += dP;
-                s1 += t;
-                s2 += t * dx;
+                const float2 raw = __fmul2_rn(o2, make_float2(v0 ? ex2(P2.x) : 0.f, v1 ? ex2(P2.y) : 0.f));
+                const float2 al = make_float2(fminf(kAlphaMax, raw.x), fminf(kAlphaMax, raw.y));
+                const float2 om = __ffma2_rn(al, m1, one);  // 1 - alpha
+                const float2 Tj = make_float2(v0 ? T[p].x * rcp_approx(om.x) : T[p].x,
+                                              v1 ? T[p].y * rcp_approx(om.y) : T[p].y);
+                T[p] = Tj;
+                const float2 w = __fmul2_rn(al, Tj);
+                g6 = __ffma2_rn(w, dCr[p], g6);
+                g7 = __ffma2_rn(w, dCg[p], g7);
+                g8 = __ffma2_rn(w, dCb[p], g8);
+                const float2 er = __ffma2_rn(Rr[p], m1, cr), eg = __ffma2_rn(Rg[p], m1, cg),
+                             eb = __ffma2_rn(Rb[p], m1, cb);
+                const float2 dal =
+                    __fmul2_rn(Tj, __ffma2_rn(dCb[p], eb, __ffma2_rn(dCg[p], eg, __fmul2_rn(dCr[p], er))));
+                Rr[p] = __ffma2_rn(al, er, Rr[p]);
+                Rg[p] = __ffma2_rn(al, eg, Rg[p]);
+                Rb[p] = __ffma2_rn(al, eb, Rb[p]);
+                // dL/dP = dL/dalpha * alpha where alpha is not clamped
+                const float2 dP = __fmul2_rn(dal, make_float2(raw.x <= kAlphaMax ? raw.x : 0.f,
+                                                              raw.y <= kAlphaMax ? raw.y : 0.f));
+                const float2 t = __fmul2_rn(dP, dx);
+                s0 = __fadd2_rn(s0, dP);
+                s1 = __fadd2_rn(s1, t);
+                s2 = __ffma2_rn(t, dx, s2);
             }
             // frozen Gaussians (index >= n_active) take part in the
             // recursion but need no gradient
             if (s_g[j] < n_active && __any_sync(0xFFFFFFFFu, contrib)) {
-                // lane 4q ends with sum q of (S1, S2, S3, S4, S5, g5, g6, g7)
-                const float vals8[8] = {s1, s0 * dy, s2, s1 * dy, s0 * dy * dy, g5, g6, g7};
+                // lane 4q ends with sum q of (S1, S2, S3, S4, S5, S0, g6, g7)
+                const float f0 = s0.x + s0.y, f1 = s1.x + s1.y;
+                const float vals8[8] = {f1, f0 * dy, s2.x + s2.y, f1 * dy, f0 * dy * dy, f0, g6.x + g6.y,
+                                        g7.x + g7.y};
                 const float mine = warp_sum8(vals8, lane);
                 const float S1 = __shfl_sync(0xFFFFFFFFu, mine, 0), S2 = __shfl_sync(0xFFFFFFFFu, mine, 4);
-                g8 = warp_sum(g8);
+                const float gb = warp_sum(g8.x + g8.y);
                 const int q = lane >> 2;
                 if ((lane & 3) == 0 || lane == 1) {
                     // the conic and mean gradients from the five sums:
@@ -315,14 +369,16 @@ k_raster_bwd(const float4* __restrict__ proj, const ViewInfo* __restrict__ vt, i
                     const float4 co = s_b[j];
                     float val;
                     int slot;
-                    if (lane == 1) { val = g8; slot = 8; }
+                    if (lane == 1) { val = gb; slot = 8; }
                     else {
+                        // opacity: sum dL/dalpha * G = S0 / o (G = alpha / o unclamped)
                         slot = q;
                         val = q == 0 ? -co.x * S1 - co.y * S2
                             : q == 1 ? -co.z * S2 - co.y * S1
                             : q == 2 ? -0.5f * mine
                             : q == 3 ? -mine
-                            : q == 4 ? -0.5f * mine : mine;
+                            : q == 4 ? -0.5f * mine
+                            : q == 5 ? mine / a.z : mine;
                     }
                     if (NT == 32) s_acc[slot][j] += val;
                     else atomicAdd(&s_acc[slot][j], val);

@@ -39,7 +39,7 @@ def test_struct_layouts_match_header():
     assert ctypes.sizeof(_lib.gs_train_io) == 104 and _lib.gs_train_io.frozen.offset == 96
     assert ctypes.sizeof(_lib.gs_train_cfg) == 360 and _lib.gs_train_cfg.n_frozen.offset == 336
     assert _lib.gs_train_cfg.lighting.offset == 352
-    assert ctypes.sizeof(_lib.gs_tune_entry) == 20
+    assert ctypes.sizeof(_lib.gs_tune_entry) == 28
 
 
 def test_missing_library_fails_loudly(monkeypatch):
