@@ -19,7 +19,8 @@
 // final transmittance and last-contributor position and walks its list
 // backwards, recovering T_j = T_{j+1} / (1 - alpha_j) and the colour behind
 // the fragment by the recursion R_{j-1} = alpha_j c_j + (1 - alpha_j) R_j
-// (R = background behind the last fragment).  Per fragment, a thread sums its
+// (R = background behind the last fragment), kept as its product with the
+// pixel's fixed dL/dC.  Per fragment, a thread sums its
 // pixels' 9 gradient values, the warp sums them with shuffles, the warp sums
 // of a batch are added in shared memory, and each batch ends with one set of
 // vector atomics per Gaussian into the per-view 2D gradient record.
@@ -220,8 +221,14 @@ __device__ __forceinline__ float rcp_approx(float x) {
 //   dL/dA = -S3 / 2, dL/dB = -S4, dL/dC = -S5 / 2.
 // A thread's pixels share one row (one dy): it keeps sum dP, sum dP dx and
 // sum dP dx^2 per pixel and forms S2, S4, S5 with its dy once per fragment.
+// Blocks per SM the adjoint is compiled for: with 8-pixel strips (one warp
+// per tile) the register budget is set so that 24 tiles fit on an SM, with
+// 4-pixel strips 1024 threads.
 template <int B, int TPR>
-__global__ void __launch_bounds__(B * TPR)
+constexpr int bwd_min_blocks() { return B * TPR == 32 ? 24 : 1024 / (B * TPR); }
+
+template <int B, int TPR>
+__global__ void __launch_bounds__(B * TPR, bwd_min_blocks<B, TPR>())
 k_raster_bwd(const float4* __restrict__ proj, const ViewInfo* __restrict__ vt, int V, int64_t n,
              const uint32_t* __restrict__ vals, const uint2* __restrict__ ranges, float3 bg,
              const float* __restrict__ T_final, const uint32_t* __restrict__ n_contrib,
@@ -252,8 +259,11 @@ k_raster_bwd(const float4* __restrict__ proj, const ViewInfo* __restrict__ vt, i
     const int64_t rbase = (int64_t)v * n;
     const int lane = threadIdx.x & 31;
 
-    // pixel pairs (2p, 2p + 1) in packed float2 registers
-    float2 T[NP], dCr[NP], dCg[NP], dCb[NP], Rr[NP], Rg[NP], Rb[NP];
+    // pixel pairs (2p, 2p + 1) in packed float2 registers.  The colour behind
+    // a fragment, R, enters the gradient only as dL/dC . R (dL/dC is fixed per
+    // pixel), so the walk keeps that scalar X instead of R:
+    //   dL/dalpha_j = T_j (dL/dC . c_j - X_j),  X_{j-1} = X_j + alpha_j (dL/dC . c_j - X_j).
+    float2 T[NP], dCr[NP], dCg[NP], dCb[NP], X[NP];
     uint32_t last[PX];
     uint32_t mylast = 0;
     const int64_t HW = (int64_t)vi.width * vi.height;
@@ -276,7 +286,7 @@ k_raster_bwd(const float4* __restrict__ proj, const ViewInfo* __restrict__ vt, i
         }
         T[p] = make_float2(t[0], t[1]);
         dCr[p] = make_float2(r[0], r[1]); dCg[p] = make_float2(g[0], g[1]); dCb[p] = make_float2(b[0], b[1]);
-        Rr[p] = make_float2(bg.x, bg.x); Rg[p] = make_float2(bg.y, bg.y); Rb[p] = make_float2(bg.z, bg.z);
+        X[p] = make_float2(r[0] * bg.x + g[0] * bg.y + b[0] * bg.z, r[1] * bg.x + g[1] * bg.y + b[1] * bg.z);
     }
     if (threadIdx.x == 0) s_max = 0;
     __syncthreads();
@@ -336,13 +346,10 @@ k_raster_bwd(const float4* __restrict__ proj, const ViewInfo* __restrict__ vt, i
                 g6 = __ffma2_rn(w, dCr[p], g6);
                 g7 = __ffma2_rn(w, dCg[p], g7);
                 g8 = __ffma2_rn(w, dCb[p], g8);
-                const float2 er = __ffma2_rn(Rr[p], m1, cr), eg = __ffma2_rn(Rg[p], m1, cg),
-                             eb = __ffma2_rn(Rb[p], m1, cb);
-                const float2 dal =
-                    __fmul2_rn(Tj, __ffma2_rn(dCb[p], eb, __ffma2_rn(dCg[p], eg, __fmul2_rn(dCr[p], er))));
-                Rr[p] = __ffma2_rn(al, er, Rr[p]);
-                Rg[p] = __ffma2_rn(al, eg, Rg[p]);
-                Rb[p] = __ffma2_rn(al, eb, Rb[p]);
+                // e = dL/dC . (c - R)
+                const float2 e = __ffma2_rn(dCb[p], cb, __ffma2_rn(dCg[p], cg, __ffma2_rn(dCr[p], cr, __fmul2_rn(X[p], m1))));
+                const float2 dal = __fmul2_rn(Tj, e);
+                X[p] = __ffma2_rn(al, e, X[p]);
                 // dL/dP = dL/dalpha * alpha where alpha is not clamped
                 const float2 dP = __fmul2_rn(dal, make_float2(raw.x <= kAlphaMax ? raw.x : 0.f,
                                                               raw.y <= kAlphaMax ? raw.y : 0.f));
