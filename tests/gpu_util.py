@@ -84,7 +84,8 @@ class GpuRun:
     """One pass of the whole CUDA path on a small case, all intermediates kept."""
 
     def __init__(self, planes, sh_degree, cams, target=None, keys_cap=None, bg=(0.0, 0.0, 0.0),
-                 tile=16, sort_bits=8, w_l1=0.8, w_ssim=0.2, dyn=None, raster_threads=4, lighting=None):
+                 tile=16, sort_bits=8, w_l1=0.8, w_ssim=0.2, dyn=None, raster_threads=4, lighting=None,
+                 raster_bwd_threads=None):
         import torch
         import paper_2604_02851_b300 as gs
         self.gs = gs
@@ -94,7 +95,8 @@ class GpuRun:
         self.n = n = planes.shape[1]
         self.sh = sh_degree
         self.bg = bg
-        self.ctx = gs.Context(0, 0, tile=tile, sort_bits=sort_bits, raster_threads=raster_threads)
+        self.ctx = gs.Context(0, 0, tile=tile, sort_bits=sort_bits, raster_threads=raster_threads,
+                              raster_bwd_threads=raster_bwd_threads)
         self.params = torch.from_numpy(np.ascontiguousarray(planes, dtype=np.float32)).cuda()
         self.d_cams = gs.cameras_to_device(cams)
         self.tt = self.ctx.total_tiles(cams)

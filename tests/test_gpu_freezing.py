@@ -13,19 +13,21 @@ from gpu_util import cams32, gpu_proj_to_oracle, l1_sign_expected, rel_l2, scene
 pytestmark = pytest.mark.gpu
 
 
-def test_frozen_pool_step_equals_union_step_with_frozen_rows_fixed():
+@pytest.mark.parametrize("bwd_threads", [4, 2])
+def test_frozen_pool_step_equals_union_step_with_frozen_rows_fixed(bwd_threads):
+    """bwd_threads: the compositing adjoint's layout in the fused step."""
     import torch
     import paper_2604_02851_b300 as gs
     from paper_2604_02851_b300.train import OnlineTrainer, estimate_keys
     na, nf, sh = 12_000, 8_000, 2
-    cams = gi.ring_cameras(3, 160, 112)
+    cams = gi.ring_cameras(3, 176, 112)
     union = scene(na + nf, sh, 80)
     active = np.ascontiguousarray(union[:, :na])
     frozen = np.ascontiguousarray(union[:, na:])
     target = O.forward(scene(na + nf, sh, 81), sh, cams32(cams))["image"].astype(np.float32)
 
     # fused step with the frozen pool
-    ctx = gs.Context(0, 0)
+    ctx = gs.Context(0, 0, raster_bwd_threads=bwd_threads)
     t_union = torch.from_numpy(union).cuda()
     keys = estimate_keys(ctx, t_union, sh, cams, slack=1.5)
     t_active = torch.from_numpy(active).cuda()
@@ -46,7 +48,7 @@ def test_frozen_pool_step_equals_union_step_with_frozen_rows_fixed():
     _, vals, ranges, nk = gs.gs_bin_sort(c2, proj, d_cams, 3, na + nf, tt, keys, want_keys=False)
     image, T, nc = gs.gs_render_fwd(c2, proj, d_cams, 3, na + nf, tt, vals, ranges, npix)
     tgt = torch.from_numpy(target.ravel()).cuda()
-    loss, dimg = gs.gs_loss(c2, image, tgt, 3, 112, 160)
+    loss, dimg = gs.gs_loss(c2, image, tgt, 3, 112, 176)
     _, dpar = gs.gs_render_bwd(c2, t_union, sh, d_cams, 3, tt, proj, vals, ranges, T, nc, dimg)
     ga = dpar[:, :na].contiguous()
     th = torch.from_numpy(active).cuda()
