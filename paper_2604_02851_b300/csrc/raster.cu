@@ -57,8 +57,44 @@ __device__ __forceinline__ float4 log2_conic(float4 co) {
 }
 __device__ __forceinline__ float cutoff_log2(float o) { return -__log2f(255.f * o); }
 
+// Tile culling of staged fragments.  A tile's list holds every Gaussian whose
+// 3-sigma square meets the tile; many of them reach no pixel of it with
+// alpha >= 1/255 (an elongated or faint splat misses the corner tiles of its
+// square).  The largest base-2 exponent over the tile's pixel-centre box
+// decides: P2 = qA dx^2 + qB dx dy + qC dy^2 (qA, qC < 0) is concave, so its
+// maximum over the box is 0 when the centre lies inside and otherwise the
+// largest of the maxima along the four edges.  A fragment is dropped when
+// that maximum lies below the cut-off by more than kCullMargin, far beyond
+// the rounding of either evaluation, so every pixel's own test would have
+// rejected it: images, transmittances, contributor counts and gradients are
+// unchanged.  Kept fragments carry their position in the list.
+constexpr float kCullMargin = 0.01f;
+
+__device__ __forceinline__ float box_max_exponent(float4 q, float dxl, float dxh, float dyl, float dyh) {
+    if (dxl <= 0.f && dxh >= 0.f && dyl <= 0.f && dyh >= 0.f) return 0.f;
+    const float ia = 0.5f / q.x, ic = 0.5f / q.z;
+    float best = __int_as_float(0xff800000);
+    const float ex[2] = {dxl, dxh}, ey[2] = {dyl, dyh};
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+        const float D = ex[e];  // edge dx = D: dP/ddy = 0 at dy = -qB D / (2 qC)
+        const float dy = fminf(fmaxf(-q.y * D * ic, dyl), dyh);
+        best = fmaxf(best, (q.x * D + q.y * dy) * D + q.z * dy * dy);
+        const float E = ey[e];  // edge dy = E
+        const float dx = fminf(fmaxf(-q.y * E * ia, dxl), dxh);
+        best = fmaxf(best, (q.x * dx + q.y * E) * dx + q.z * E * E);
+    }
+    return best;
+}
+
+// true when the fragment can reach a pixel centre of the tile whose pixel
+// centres span [x0, x1] x [y0, y1]
+__device__ __forceinline__ bool reaches_tile(float4 a, float4 q, float x0, float x1, float y0, float y1) {
+    return box_max_exponent(q, a.x - x1, a.x - x0, a.y - y1, a.y - y0) >= a.w - kCullMargin;
+}
+
 template <int B, int TPR>
-__global__ void __launch_bounds__(B * TPR)
+__global__ void __launch_bounds__(B * TPR, 768 / (B * TPR))
 k_render_fwd(const float4* __restrict__ proj, const ViewInfo* __restrict__ vt, int V, int64_t n,
              const uint32_t* __restrict__ vals, const uint2* __restrict__ ranges, float3 bg,
              float* __restrict__ image, float* __restrict__ T_final, uint32_t* __restrict__ n_contrib) {
@@ -67,9 +103,12 @@ k_render_fwd(const float4* __restrict__ proj, const ViewInfo* __restrict__ vt, i
     constexpr int NP = PX / 2;         // pixel pairs per thread
     static_assert(NT % 32 == 0 && PX % 2 == 0, "whole warps, pixel pairs");
     constexpr int BATCH = 2 * NT;      // fragments staged per round
+    constexpr int NW = NT / 32;
     __shared__ float4 s_a[BATCH];      // u, v, opacity, log2 cut-off
     __shared__ float4 s_q[BATCH];      // base-2 conic coefficients
     __shared__ float4 s_c[BATCH];      // r, g, b
+    __shared__ uint32_t s_pos[BATCH];  // position in the tile's list
+    __shared__ int s_wcnt[2 * NW];
     const int64_t gt = blockIdx.x;
     if (gt >= vt[V].tile_off) return;
     const int v = find_view(vt, V, gt);
@@ -78,6 +117,8 @@ k_render_fwd(const float4* __restrict__ proj, const ViewInfo* __restrict__ vt, i
     const int row = (int)threadIdx.x / TPR;
     const int px0 = (lt % vi.tx) * B + ((int)threadIdx.x % TPR) * PX;
     const int py = (lt / vi.tx) * B + row;
+    const float tx0 = (float)((lt % vi.tx) * B) + 0.5f, ty0 = (float)((lt / vi.tx) * B) + 0.5f;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const float fy = (float)py + 0.5f;
     const float fx0 = (float)px0 + 0.5f;
     const uint2 rg = ranges[gt];
@@ -103,20 +144,42 @@ k_render_fwd(const float4* __restrict__ proj, const ViewInfo* __restrict__ vt, i
     for (int k = 0; k < PX; ++k) last[k] = 0;
     for (uint32_t start = rg.x; start < rg.y; start += BATCH) {
         if (__syncthreads_count(nlive != 0) == 0) break;
+        // stage the fragments of this round that reach the tile, in list order
+        float4 ra[2], rq[2], rc[2];
+        bool keep[2];
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-            const int slot = threadIdx.x + h * NT;
-            const uint32_t idx = start + slot;
+            const uint32_t idx = start + threadIdx.x + h * NT;
+            keep[h] = false;
             if (idx < rg.y) {
                 const int64_t r = (rbase + vals[idx]) * 4;
-                const float4 a = proj[r], b = proj[r + 1], c = proj[r + 2];
-                s_a[slot] = make_float4(a.x, a.y, a.w, cutoff_log2(a.w));
-                s_q[slot] = log2_conic(b);
-                s_c[slot] = c;
+                const float4 a = proj[r], b = proj[r + 1];
+                rc[h] = proj[r + 2];
+                ra[h] = make_float4(a.x, a.y, a.w, cutoff_log2(a.w));
+                rq[h] = log2_conic(b);
+                keep[h] = reaches_tile(ra[h], rq[h], tx0, tx0 + (float)(B - 1), ty0, ty0 + (float)(B - 1));
             }
         }
+        const uint32_t m0 = __ballot_sync(0xFFFFFFFFu, keep[0]), m1 = __ballot_sync(0xFFFFFFFFu, keep[1]);
+        if (lane == 0) { s_wcnt[warp] = __popc(m0); s_wcnt[NW + warp] = __popc(m1); }
         __syncthreads();
-        const int cnt = (int)min((uint32_t)BATCH, rg.y - start);
+        int cnt = 0, off0 = 0, off1 = 0;
+#pragma unroll
+        for (int w = 0; w < 2 * NW; ++w) {
+            if (w < warp) off0 += s_wcnt[w];
+            if (w < NW + warp) off1 += s_wcnt[w];
+            cnt += s_wcnt[w];
+        }
+        const uint32_t ltm = (1u << lane) - 1u;
+        if (keep[0]) {
+            const int d = off0 + __popc(m0 & ltm);
+            s_a[d] = ra[0]; s_q[d] = rq[0]; s_c[d] = rc[0]; s_pos[d] = start + threadIdx.x - rg.x;
+        }
+        if (keep[1]) {
+            const int d = off1 + __popc(m1 & ltm);
+            s_a[d] = ra[1]; s_q[d] = rq[1]; s_c[d] = rc[1]; s_pos[d] = start + threadIdx.x + NT - rg.x;
+        }
+        __syncthreads();
         for (int j = 0; j < cnt && nlive; ++j) {
             const float4 a = s_a[j];
             const float4 q = s_q[j];
@@ -126,7 +189,7 @@ k_render_fwd(const float4* __restrict__ proj, const ViewInfo* __restrict__ vt, i
             const float dx0 = a.x - fx0;
             const float2 qx2 = make_float2(q.x, q.x), qb2 = make_float2(qb, qb), qc2 = make_float2(qc, qc);
             const float2 o2 = make_float2(a.z, a.z);
-            const uint32_t pos1 = start + j - rg.x + 1;
+            const uint32_t pos1 = s_pos[j] + 1;
 #pragma unroll
             for (int p = 0; p < NP; ++p) {
                 const int k0 = 2 * p, k1 = 2 * p + 1;
@@ -243,8 +306,10 @@ k_raster_bwd(const float4* __restrict__ proj, const ViewInfo* __restrict__ vt, i
     __shared__ float4 s_b[BATCH];   // conic A, B, C
     __shared__ float4 s_c[BATCH];   // r, g, b
     __shared__ uint32_t s_g[BATCH];
+    __shared__ uint32_t s_pos[BATCH];  // position in the tile's list
     __shared__ float s_acc[9][BATCH];
     __shared__ uint32_t s_max;
+    __shared__ int s_wcnt[NT / 32];
     const int64_t gt = blockIdx.x;
     if (gt >= vt[V].tile_off) return;
     const int v = find_view(vt, V, gt);
@@ -255,9 +320,10 @@ k_raster_bwd(const float4* __restrict__ proj, const ViewInfo* __restrict__ vt, i
     const int py = (lt / vi.tx) * B + row;
     const float fy = (float)py + 0.5f;
     const float fx0 = (float)px0 + 0.5f;
+    const float tx0 = (float)((lt % vi.tx) * B) + 0.5f, ty0 = (float)((lt / vi.tx) * B) + 0.5f;
     const uint2 rg = ranges[gt];
     const int64_t rbase = (int64_t)v * n;
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
     // pixel pairs (2p, 2p + 1) in packed float2 registers.  The colour behind
     // a fragment, R, enters the gradient only as dL/dC . R (dL/dC is fixed per
@@ -296,23 +362,46 @@ k_raster_bwd(const float4* __restrict__ proj, const ViewInfo* __restrict__ vt, i
 
     for (int64_t bend = maxl; bend > 0; bend -= BATCH) {
         const uint32_t bstart = bend > BATCH ? (uint32_t)(bend - BATCH) : 0u;
-        const int cnt = (int)(bend - bstart);
+        const int nslot = (int)(bend - bstart);
         __syncthreads();  // the previous batch's flush is complete
-        if ((int)threadIdx.x < cnt) {
-            const uint32_t g = vals[rg.x + bstart + threadIdx.x];
+        // stage the fragments of this round that reach the tile, in list order
+        bool keep = false;
+        uint32_t g = 0;
+        float4 a, b, c, aq, qq;
+        if ((int)threadIdx.x < nslot) {
+            g = vals[rg.x + bstart + threadIdx.x];
             const int64_t r = (rbase + g) * 4;
-            const float4 a = proj[r], b = proj[r + 1], c = proj[r + 2];
-            s_a[threadIdx.x] = make_float4(a.x, a.y, a.w, cutoff_log2(a.w));
-            s_q[threadIdx.x] = log2_conic(b);
-            s_b[threadIdx.x] = b;
-            s_c[threadIdx.x] = c;
-            s_g[threadIdx.x] = g;
+            a = proj[r]; b = proj[r + 1]; c = proj[r + 2];
+            aq = make_float4(a.x, a.y, a.w, cutoff_log2(a.w));
+            qq = log2_conic(b);
+            keep = reaches_tile(aq, qq, tx0, tx0 + (float)(B - 1), ty0, ty0 + (float)(B - 1));
+        }
+        const uint32_t km = __ballot_sync(0xFFFFFFFFu, keep);
+        int off = 0, cnt = __popc(km);
+        if (NT > 32) {
+            if (lane == 0) s_wcnt[warp] = __popc(km);
+            __syncthreads();
+            cnt = 0;
 #pragma unroll
-            for (int q = 0; q < 9; ++q) s_acc[q][threadIdx.x] = 0.f;
+            for (int w = 0; w < NT / 32; ++w) {
+                if (w < warp) off += s_wcnt[w];
+                cnt += s_wcnt[w];
+            }
+        }
+        if (keep) {
+            const int d = off + __popc(km & ((1u << lane) - 1u));
+            s_a[d] = aq;
+            s_q[d] = qq;
+            s_b[d] = b;
+            s_c[d] = c;
+            s_g[d] = g;
+            s_pos[d] = bstart + threadIdx.x;
+#pragma unroll
+            for (int q = 0; q < 9; ++q) s_acc[q][d] = 0.f;
         }
         __syncthreads();
         for (int j = cnt - 1; j >= 0; --j) {
-            const uint32_t pos = bstart + (uint32_t)j;
+            const uint32_t pos = s_pos[j];
             if (!__any_sync(0xFFFFFFFFu, pos < mylast)) continue;
             const float4 a = s_a[j];
             const float4 q = s_q[j];
