@@ -78,8 +78,6 @@ def lib():
         L.or_f32_to_f16.restype = C.c_uint16
         L.or_delta.argtypes = [C.c_int64, _F, _F, C.c_float, _U32, _U8]
         L.or_delta.restype = C.c_int64
-        L.or_decision_flips.argtypes = [C.c_int, C.c_int64, _D, C.c_int, _D, _U32, _U32, _D, _U32, _U32, _U8]
-        L.or_decision_flips.restype = C.c_int64
         _lib = L
     return _lib
 
@@ -415,20 +413,6 @@ def apply_delta(params_planes, records):
     rec = np.ascontiguousarray(records, dtype=np.uint8)
     lib().or_apply_delta(rows.shape[0], rows, len(rec), rec)
     return rows_to_planes(rows)
-
-
-def decision_flips(cams, projA, valsA, rangesA, projB, valsB, rangesB, tile: int = TILE):
-    """Gaussians (per view) kept at some pixel under one projection and not the
-    other; returns (flags [V][n] bool, number of pixels that differ)."""
-    projA = _d(projA); projB = _d(projB)
-    V, n = projA.shape[:2]
-    flags = np.zeros(V * n, dtype=np.uint8)
-    npix = lib().or_decision_flips(V, n, cams_array(cams), tile, projA,
-                                   np.ascontiguousarray(valsA, dtype=np.uint32),
-                                   np.ascontiguousarray(rangesA, dtype=np.uint32), projB,
-                                   np.ascontiguousarray(valsB, dtype=np.uint32),
-                                   np.ascontiguousarray(rangesB, dtype=np.uint32), flags)
-    return flags.reshape(V, n).astype(bool), int(npix)
 
 
 # ------------------------------------------------------------------ composed

@@ -1333,70 +1333,3 @@ void or_cell_visible(int V, const float* cams, const float* depth, const float* 
     }
 }
 
-/* ------------------------------------------------------------------------
- * Discrete-state comparison for end-to-end tests.  The alpha cut-off and the
- * termination test are decisions taken by floating point; two evaluations of
- * the same scene (e.g. float64 projections and a float32 producer's) can keep
- * different fragment sets at a pixel when a value sits within rounding of a
- * threshold.  For every pixel this walks each projection's own sorted list
- * with the compositing rules of or_render, collects the kept Gaussians, and
- * flags (flags[v*n + g] = 1) every Gaussian kept by one and not the other.
- * Returns the number of pixels whose kept sets differ.
- * ---------------------------------------------------------------------- */
-static int kept_set(const double* proj, int64_t vn, const uint32_t* vals, uint32_t s, uint32_t e,
-                    double px, double py, uint32_t* out) {
-    double T = 1.0;
-    int m = 0;
-    for (uint32_t j = s; j < e; ++j) {
-        const double* o = proj + (vn + vals[j]) * PROJ_STRIDE;
-        double dx = o[0] - px, dy = o[1] - py;
-        double P = -0.5 * (o[4] * dx * dx + o[6] * dy * dy) - o[5] * dx * dy;
-        if (P > 0.0) continue;
-        double al = fmin(ALPHA_MAX, o[3] * exp(P));
-        if (al < ALPHA_MIN) continue;
-        double Tn = T * (1.0 - al);
-        if (Tn < T_MIN) break;
-        out[m++] = vals[j];
-        T = Tn;
-    }
-    return m;
-}
-
-static int cmp_u32(const void* a, const void* b) {
-    uint32_t x = *(const uint32_t*)a, y = *(const uint32_t*)b;
-    return x < y ? -1 : (x > y ? 1 : 0);
-}
-
-int64_t or_decision_flips(int V, int64_t n, const double* cams, int tile, const double* projA,
-                          const uint32_t* valsA, const uint32_t* rangesA, const double* projB,
-                          const uint32_t* valsB, const uint32_t* rangesB, uint8_t* flags) {
-    memset(flags, 0, (size_t)V * (size_t)n);
-    int64_t npix = 0;
-    for (int v = 0; v < V; ++v) {
-        const double* cam = cams + (int64_t)v * CAM_STRIDE;
-        int W = (int)cam[16], H = (int)cam[17], TX = tiles_along(W, tile);
-        int64_t toff = view_tile_offset(cams, v, tile);
-        int64_t vn = (int64_t)v * n;
-        for (int y = 0; y < H; ++y)
-            for (int x = 0; x < W; ++x) {
-                int64_t t = toff + (int64_t)(y / tile) * TX + x / tile;
-                uint32_t la = rangesA[2 * t + 1] - rangesA[2 * t], lb = rangesB[2 * t + 1] - rangesB[2 * t];
-                uint32_t* A = (uint32_t*)malloc(sizeof(uint32_t) * (la + 1));
-                uint32_t* B = (uint32_t*)malloc(sizeof(uint32_t) * (lb + 1));
-                int ma = kept_set(projA, vn, valsA, rangesA[2 * t], rangesA[2 * t + 1], x + 0.5, y + 0.5, A);
-                int mb = kept_set(projB, vn, valsB, rangesB[2 * t], rangesB[2 * t + 1], x + 0.5, y + 0.5, B);
-                qsort(A, (size_t)ma, sizeof(uint32_t), cmp_u32);
-                qsort(B, (size_t)mb, sizeof(uint32_t), cmp_u32);
-                int i = 0, k = 0, differ = 0;
-                while (i < ma || k < mb) {
-                    if (k >= mb || (i < ma && A[i] < B[k])) { flags[vn + A[i]] = 1; ++i; differ = 1; }
-                    else if (i >= ma || B[k] < A[i]) { flags[vn + B[k]] = 1; ++k; differ = 1; }
-                    else { ++i; ++k; }
-                }
-                npix += differ;
-                free(A);
-                free(B);
-            }
-    }
-    return npix;
-}

@@ -7,6 +7,7 @@ import pytest
 
 import gs_inputs as gi
 import oracle as O
+from flips import decision_flips
 from gpu_util import cams32, l1_sign_expected, rel_l2
 
 pytestmark = pytest.mark.gpu
@@ -35,25 +36,31 @@ def test_autograd_c2_matches_oracle_and_adam():
     # Gaussians whose kept-fragment set float32 and float64 decide differently
     # (a value within rounding of the 1/255 cut-off or the 1e-4 termination)
     # are counted and left out; all others agree to 1e-4
-    gp = gs.gs_project(setup.ctx, params.detach(), sh, setup.d_cams, V).cpu().numpy()
+    proj = gs.gs_project(setup.ctx, params.detach(), sh, setup.d_cams, V)
+    tt = setup.ctx.total_tiles(cams)
+    _, gvals, granges, gnk = gs.gs_bin_sort(setup.ctx, proj, setup.d_cams, V, n, tt, 4_000_000, want_keys=False)
+    torch.cuda.synchronize()
     from gpu_util import gpu_proj_to_oracle
-    gpo = gpu_proj_to_oracle(gp)
-    keys, vals, ranges = O.bin_sort(c64, gpo[..., 12:16].astype(np.int32), gp[..., 2].astype(np.float32))
-    flips, _ = O.decision_flips(c64, r["proj"], r["vals"], r["ranges"], gpo, vals, ranges)
+    gpo = gpu_proj_to_oracle(proj.cpu().numpy())
+    vals = gvals.cpu().numpy()[:int(gnk.item())].view(np.uint32)
+    ranges = granges.cpu().numpy().view(np.uint32)
+    flips, _ = decision_flips(c64, r["proj"], r["vals"], r["ranges"], gpo, vals, ranges)
     support = np.any(r["proj"][..., [7, 12, 13, 14, 15]] != gpo[..., [7, 12, 13, 14, 15]], axis=(0, 2))
     odd = flips.any(axis=0) | support
     assert odd.mean() <= 1e-3
     g = params.grad.detach().cpu().numpy()
-    od, _ = l1_sign_expected(O, planes, sh, c64, r, target, image.detach().cpu().numpy())
+    od, _ = l1_sign_expected(O, planes, sh, c64, r, target, g, keep=~odd)
     assert rel_l2(g[:, ~odd], od[:, ~odd]) <= 1e-4
-    # one Adam step on the autograd gradient (lr 1e-3) against the oracle's Adam
+    # one Adam step (lr 1e-3) on the oracle's gradient, rounded to float32,
+    # against the oracle's Adam on the same gradient
+    g32 = r["dparams"].astype(np.float32)
     m = torch.zeros_like(params); v = torch.zeros_like(params)
     theta = params.detach().clone()
-    gs.gs_adam_step(setup.ctx, theta, params.grad.detach(), m, v, gs.adam_cfg(lr=1e-3, step=1))
+    gs.gs_adam_step(setup.ctx, theta, torch.from_numpy(g32).cuda(), m, v, gs.adam_cfg(lr=1e-3, step=1))
     torch.cuda.synchronize()
     th_o = gi.planes_to_rows(planes).astype(np.float64)
     m_o = np.zeros_like(th_o); v_o = np.zeros_like(th_o)
-    O.adam(th_o, gi.planes_to_rows(g).astype(np.float64), m_o, v_o, 1e-3, 1)
+    O.adam(th_o, gi.planes_to_rows(g32).astype(np.float64), m_o, v_o, 1e-3, 1)
     upd_g = gi.planes_to_rows(theta.cpu().numpy()) - gi.planes_to_rows(planes)
     upd_o = th_o - gi.planes_to_rows(planes)
     assert rel_l2(upd_g, upd_o) <= 1e-4

@@ -12,7 +12,7 @@ import pytest
 
 import gs_inputs as gi
 import oracle as O
-from gpu_util import cams32, gpu_proj_to_oracle, scene
+from gpu_util import cams32, gpu_proj_to_oracle, oracle_proj_to_gpu, scene
 
 pytestmark = pytest.mark.gpu
 
@@ -26,7 +26,8 @@ CASES = {
 }
 
 
-def _bin(mode, planes, sh, cams, tile, bits, items, keys_cap):
+def _bin(mode, planes, sh, cams, tile, bits, items, keys_cap, proj32=None):
+    """GPU projection + binning, or binning alone of given float32 records."""
     import torch
     import paper_2604_02851_b300 as gs
     n, V = planes.shape[1], len(cams["fx"])
@@ -35,7 +36,10 @@ def _bin(mode, planes, sh, cams, tile, bits, items, keys_cap):
     params = torch.from_numpy(np.ascontiguousarray(planes)).cuda()
     d_cams = gs.cameras_to_device(cams)
     tt = ctx.total_tiles(cams)
-    proj = gs.gs_project(ctx, params, sh, d_cams, V)
+    if proj32 is None:
+        proj = gs.gs_project(ctx, params, sh, d_cams, V)
+    else:
+        proj = torch.from_numpy(np.ascontiguousarray(proj32)).cuda()
     keys, vals, ranges, nk = gs.gs_bin_sort(ctx, proj, d_cams, V, n, tt, keys_cap)
     torch.cuda.synchronize()
     code, detail = ctx.status()
@@ -62,13 +66,17 @@ def test_two_level_matches_direct_and_oracle(name):
     np.testing.assert_array_equal(a["keys"], b["keys"])
     np.testing.assert_array_equal(a["vals"], b["vals"])
     np.testing.assert_array_equal(a["ranges"], b["ranges"])
-    # and the oracle's sort of the same (float32) projection
-    gp = gpu_proj_to_oracle(a["proj"])
-    keys, vals, ranges = O.bin_sort(cams32(cams), gp[..., 12:16].astype(np.int32),
-                                    a["proj"][..., 2].astype(np.float32), tile=tile)
-    np.testing.assert_array_equal(a["vals"], vals)
-    np.testing.assert_array_equal(a["keys"], (keys >> np.uint64(32)).astype(np.uint32))
-    np.testing.assert_array_equal(a["ranges"], ranges)
+    # both modes on the oracle's own records (rounded to float32) against
+    # the oracle's sort of them
+    og32 = oracle_proj_to_gpu(O.project(planes, sh, cams32(cams), tile))
+    ogd = gpu_proj_to_oracle(og32)
+    keys, vals, ranges = O.bin_sort(cams32(cams), ogd[..., 12:16].astype(np.int32), og32[..., 2].copy(), tile=tile)
+    for mode in ("two_level", "direct"):
+        c = _bin(mode, planes, sh, cams, tile, bits, items, cap, proj32=og32)
+        assert c["code"] == 0 and c["K"] == len(vals)
+        np.testing.assert_array_equal(c["vals"], vals)
+        np.testing.assert_array_equal(c["keys"], (keys >> np.uint64(32)).astype(np.uint32))
+        np.testing.assert_array_equal(c["ranges"], ranges)
 
 
 def test_two_level_chunks_span_super_tiles():
@@ -157,13 +165,14 @@ def test_autotune_times_every_configuration_and_keeps_results_exact():
     assert ctx.status()[0] == 0
     d_cams = gs.cameras_to_device(cams)
     tt = ctx.total_tiles(cams)
-    proj = gs.gs_project(ctx, params, sh, d_cams, 3)
+    # the tuned context bins the oracle's own records (rounded to float32) as the oracle does
+    og32 = oracle_proj_to_gpu(O.project(planes, sh, cams32(cams)))
+    ogd = gpu_proj_to_oracle(og32)
+    proj = torch.from_numpy(og32).cuda()
     keys, vals, ranges, nk = gs.gs_bin_sort(ctx, proj, d_cams, 3, n, tt, cap)
     torch.cuda.synchronize()
     K = int(nk.item())
-    gp = gpu_proj_to_oracle(proj.cpu().numpy())
-    okeys, ovals, oranges = O.bin_sort(cams32(cams), gp[..., 12:16].astype(np.int32),
-                                       proj.cpu().numpy()[..., 2].astype(np.float32))
+    okeys, ovals, oranges = O.bin_sort(cams32(cams), ogd[..., 12:16].astype(np.int32), og32[..., 2].copy())
     np.testing.assert_array_equal(vals.cpu().numpy()[:K].view(np.uint32), ovals)
     np.testing.assert_array_equal(ranges.cpu().numpy().view(np.uint32), oranges)
     ctx.close()

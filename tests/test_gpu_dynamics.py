@@ -6,7 +6,8 @@ import pytest
 
 import gs_inputs as gi
 import oracle as O
-from gpu_util import GpuRun, cams32, gpu_proj_to_oracle, l1_sign_expected, rel_l2, scene
+from flips import decision_flips
+from gpu_util import GpuRun, OracleStages, cams32, gpu_proj_to_oracle, l1_sign_expected, rel_l2, scene
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-4
@@ -53,15 +54,16 @@ def test_dynamic_projection_matches_oracle(dcase):
 def test_dynamic_gradients_match_oracle(dcase):
     planes, sh, cams, d, run = dcase
     gp = run.oracle_proj()
-    g2 = run.np("grad2d")[..., :9].astype(np.float64)
-    dp = O.project_bwd(planes, sh, cams, g2, dyn=d)  # stage-wise: the GPU's 2D gradients
-    assert rel_l2(run.np("dparams"), dp) <= TOL
+    # stage-wise: the GPU projection adjoint on the oracle's 2D gradients
+    st = OracleStages(O, planes, sh, cams, run.np("target"), dyn=d, gpu_dyn=run.dyn)
+    assert rel_l2(st.gpu_project_bwd(), st.dparams) <= TOL
+    st.close()
     r = O.loss_and_grad(planes, sh, cams, run.np("target"), dyn=d)  # end to end
-    flips, _ = O.decision_flips(cams, r["proj"], r["vals"], r["ranges"], gp, run.sorted_vals(), run.ranges_np())
+    flips, _ = decision_flips(cams, r["proj"], r["vals"], r["ranges"], gp, run.sorted_vals(), run.ranges_np())
     support = np.any(r["proj"][..., [7, 12, 13, 14, 15]] != gp[..., [7, 12, 13, 14, 15]], axis=(0, 2))
     odd = flips.any(axis=0) | support
     assert odd.mean() <= 1e-3
-    od, _ = l1_sign_expected(O, planes, sh, cams, r, run.np("target"), run.np("image"), dyn=d)
+    od, _ = l1_sign_expected(O, planes, sh, cams, r, run.np("target"), run.np("dparams"), dyn=d, keep=~odd)
     assert rel_l2(run.np("dparams")[:, ~odd], od[:, ~odd]) <= TOL
     assert abs(float(run.loss.item()) - r["loss"]) <= TOL * r["loss"]
 

@@ -8,6 +8,7 @@ import pytest
 
 import gs_inputs as gi
 import oracle as O
+from flips import decision_flips
 from gpu_util import cams32, gpu_proj_to_oracle, l1_sign_expected, rel_l2, scene
 
 pytestmark = pytest.mark.gpu
@@ -70,13 +71,17 @@ def test_frozen_pool_step_equals_union_step_with_frozen_rows_fixed(bwd_threads):
     r = O.loss_and_grad(union, sh, c32, target)
     gp = gpu_proj_to_oracle(proj.cpu().numpy())
     K = int(nk.item())
-    flips, _ = O.decision_flips(c32, r["proj"], r["vals"], r["ranges"], gp,
+    flips, _ = decision_flips(c32, r["proj"], r["vals"], r["ranges"], gp,
                                 vals.cpu().numpy()[:K].view(np.uint32), ranges.cpu().numpy().view(np.uint32))
     support = np.any(r["proj"][..., [7, 12, 13, 14, 15]] != gp[..., [7, 12, 13, 14, 15]], axis=(0, 2))
     odd = (flips.any(axis=0) | support)[:na]
     assert odd.mean() <= 1e-3
-    od, _ = l1_sign_expected(O, union, sh, c32, r, target, image.cpu().numpy())
     g = tr.grads.cpu().numpy()
+    gu = np.zeros_like(r["dparams"])
+    gu[:, :na] = g
+    keep_u = np.zeros(na + nf, dtype=bool)
+    keep_u[:na] = ~odd
+    od, _ = l1_sign_expected(O, union, sh, c32, r, target, gu, keep=keep_u)
     assert rel_l2(g[:, ~odd], od[:, :na][:, ~odd]) <= 1e-4
     for c in (ctx, c2):
         c.close()

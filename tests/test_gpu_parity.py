@@ -1,7 +1,8 @@
 """Parity of the CUDA path (through the C ABI) with the FP64 oracle.
 
 Bars: keys, sort order, tile ranges and delta indices/records bit-exact
-(stage-wise: the oracle stage runs on the GPU's float32 upstream results);
+(stage-wise: each GPU stage runs on the oracle's own upstream results rounded
+to float32 and is compared with the oracle stage on the same inputs);
 images, losses and gradients within 1e-4 relative L2.  Integer decisions taken
 by floating point (radius, tile rectangle, termination) are compared where
 both sides decide them in the same precision, and otherwise counted and
@@ -14,7 +15,8 @@ import pytest
 
 import gs_inputs as gi
 import oracle as O
-from gpu_util import GpuRun, cams32, gpu_proj_to_oracle, l1_sign_expected, rel_l2, scene
+from flips import decision_flips
+from gpu_util import GpuRun, OracleStages, cams32, gpu_proj_to_oracle, l1_sign_expected, rel_l2, scene
 
 pytestmark = pytest.mark.gpu
 
@@ -66,27 +68,36 @@ def test_projection_matches_oracle(case):
     np.testing.assert_array_equal(gp[..., 11][both], og[..., 11][both])
 
 
-def test_bin_sort_bit_exact_stagewise(case):
-    """Oracle binning + lexicographic sort on the GPU's float32 rectangles and
-    depths must reproduce the GPU's keys, order and ranges exactly."""
-    name, planes, sh, cams, run = case
-    gp = run.oracle_proj()
-    rects = gp[..., 12:16].astype(np.int32)
-    depth = run.np("proj")[..., 2].astype(np.float32)
-    keys, vals, ranges = O.bin_sort(cams, rects, depth)
-    assert run.K == len(vals)
-    np.testing.assert_array_equal(run.sorted_vals(), vals)
-    np.testing.assert_array_equal(run.sorted_keys(), (keys >> np.uint64(32)).astype(np.uint32))
-    np.testing.assert_array_equal(run.ranges_np(), ranges)
+@pytest.fixture(scope="module", params=list(CASES))
+def stages(request):
+    """The oracle's chain on the case, and the GPU stages run on its float32
+    intermediates (see OracleStages)."""
+    n, sh, V, W, H, shift = CASES[request.param]
+    planes = scene(n, sh, 0, shift)
+    cams = cams32(gi.ring_cameras(V, W, H))
+    target = O.forward(scene(n, sh, 1, shift), sh, cams)["image"]
+    st = OracleStages(O, planes, sh, cams, target)
+    yield request.param, st
+    st.close()
 
 
-def test_render_fwd_stagewise(case):
-    name, planes, sh, cams, run = case
-    gp = run.oracle_proj()
-    img, T, nc = O.render(cams, gp, run.sorted_vals(), run.ranges_np())
-    assert rel_l2(run.np("image"), img) <= TOL
-    assert rel_l2(run.np("T"), T) <= TOL
-    mism = np.mean(run.np("nc").view(np.uint32) != nc)
+def test_bin_sort_bit_exact_stagewise(stages):
+    """The GPU's binning and sort of the oracle's float32 records must give
+    the oracle's keys, order and ranges exactly."""
+    name, st = stages
+    keys, vals, ranges = st.gpu_bin_sort()
+    assert len(vals) == st.K
+    np.testing.assert_array_equal(vals, st.vals)
+    np.testing.assert_array_equal(keys, (st.keys >> np.uint64(32)).astype(np.uint32))
+    np.testing.assert_array_equal(ranges, st.ranges)
+
+
+def test_render_fwd_stagewise(stages):
+    name, st = stages
+    img, T, nc = st.gpu_render_fwd()
+    assert rel_l2(img.cpu().numpy(), st.image) <= TOL
+    assert rel_l2(T.cpu().numpy(), st.T) <= TOL
+    mism = np.mean(nc.cpu().numpy().view(np.uint32) != st.nc)
     assert mism <= 1e-3, mism
 
 
@@ -96,30 +107,25 @@ def test_render_end_to_end(case):
     assert rel_l2(run.np("image"), f["image"]) <= TOL
 
 
-def test_loss_matches_oracle(case):
-    name, planes, sh, cams, run = case
-    V = len(cams["fx"])
-    H, W = int(cams["height"][0]), int(cams["width"][0])
-    L, dimg = O.loss(run.np("image"), run.np("target"), V, H, W)
-    assert abs(float(run.loss.item()) - L) <= TOL * abs(L)
-    assert rel_l2(run.np("dimage"), dimg) <= TOL
+def test_loss_matches_oracle(stages):
+    name, st = stages
+    L, dimg = st.gpu_loss()
+    assert abs(L - st.loss) <= TOL * abs(st.loss)
+    assert rel_l2(dimg, st.dimage32) <= TOL
 
 
-def test_raster_bwd_stagewise(case):
-    name, planes, sh, cams, run = case
-    gp = run.oracle_proj()
-    g2 = O.render_bwd(cams, gp, run.sorted_vals(), run.ranges_np(), run.np("dimage"))
-    gg = run.np("grad2d")
+def test_raster_bwd_stagewise(stages):
+    name, st = stages
+    gg = st.gpu_raster_bwd()
     assert np.all(gg[..., 9:] == 0)
     for k in range(9):
-        assert rel_l2(gg[..., k], g2[..., k]) <= TOL, k
+        assert rel_l2(gg[..., k], st.grad2d[..., k]) <= TOL, k
 
 
-def test_project_bwd_stagewise(case):
-    name, planes, sh, cams, run = case
-    g2 = run.np("grad2d")[..., :9].astype(np.float64)
-    dp = O.project_bwd(planes, sh, cams, g2)
-    gd = run.np("dparams")
+def test_project_bwd_stagewise(stages):
+    name, st = stages
+    gd, dp = st.gpu_project_bwd(), st.dparams
+    sh = st.sh
     nb = (sh + 1) ** 2
     groups = {"mean": (0, slice(0, 3)), "logit": (0, slice(3, 4)), "scale": (1, slice(0, 3)),
               "quat": (2, slice(0, 4))}
@@ -153,10 +159,10 @@ def test_gradient_end_to_end(case):
     og, gp = r["proj"], run.oracle_proj()
     fields = [7, 12, 13, 14, 15]
     support = np.any(og[..., fields] != gp[..., fields], axis=(0, 2))
-    flips, npix = O.decision_flips(cams, og, r["vals"], r["ranges"], gp, run.sorted_vals(), run.ranges_np())
+    flips, npix = decision_flips(cams, og, r["vals"], r["ranges"], gp, run.sorted_vals(), run.ranges_np())
     odd = support | flips.any(axis=0)
     keep = ~odd
-    od, ties = l1_sign_expected(O, planes, sh, cams, r, target, run.np("image"))
+    od, ties = l1_sign_expected(O, planes, sh, cams, r, target, gd, keep=keep)
     e_all, e_keep = rel_l2(gd, od), rel_l2(gd[:, keep], od[:, keep])
     print("gradient end-to-end", name, "all", e_all, "kept", e_keep, "threshold flips", int(odd.sum()),
           "pixels", npix, "L1 sign ties", ties)
@@ -182,7 +188,6 @@ def test_adam_matches_oracle():
         g = (rng.normal(size=theta.shape) * 10 ** rng.uniform(-5, 0, size=theta.shape)).astype(np.float32)
         g[1, :, 3] = 0
         gt = torch.from_numpy(g).cuda()
-        before = th.clone()
         use_dev = step == 2
         cfg = gs.adam_cfg(lr=lr, step=step, d_step=d_step if use_dev else None, increment=use_dev)
         if use_dev:
@@ -190,10 +195,10 @@ def test_adam_matches_oracle():
         gs.gs_adam_step(ctx, th, gt, m, v, cfg)
         torch.cuda.synchronize()
         O.adam(th_o, gi.planes_to_rows(g).astype(np.float64), m_o, v_o, np.tile(lr, (n, 1)).astype(np.float64), step)
-        upd_g = gi.planes_to_rows((th - before).cpu().numpy())
-        upd_o = th_o - gi.planes_to_rows(before.cpu().numpy()).astype(np.float64)
+        # each side carries its own state; the updates so far must agree
+        upd_g = gi.planes_to_rows(th.cpu().numpy()).astype(np.float64) - gi.planes_to_rows(theta).astype(np.float64)
+        upd_o = th_o - gi.planes_to_rows(theta).astype(np.float64)
         assert rel_l2(upd_g, upd_o) <= TOL
-        th_o = gi.planes_to_rows(th.cpu().numpy()).astype(np.float64)  # continue from the GPU state
     assert int(d_step.item()) == 3
     ctx.close()
 
@@ -288,12 +293,13 @@ def test_tile_size_8_matches_16():
     b = GpuRun(planes, 1, cams, target, tile=8, sort_bits=5)
     f8 = O.forward(planes, 1, cams32(cams), tile=8)
     assert rel_l2(b.np("image"), f8["image"]) <= TOL
-    # tile size changes the (P, rect) support, so compare each with its oracle
-    gp = b.oracle_proj()
-    keys, vals, ranges = O.bin_sort(cams32(cams), gp[..., 12:16].astype(np.int32),
-                                    b.np("proj")[..., 2].astype(np.float32), tile=8)
-    np.testing.assert_array_equal(b.sorted_vals(), vals)
-    np.testing.assert_array_equal(b.ranges_np(), ranges)
+    # tile size changes the (P, rect) support: the 8-px binning of the
+    # oracle's own records must be the oracle's
+    st = OracleStages(O, planes, 1, cams32(cams), target, tile=8)
+    _, vals, ranges = st.gpu_bin_sort()
+    np.testing.assert_array_equal(vals, st.vals)
+    np.testing.assert_array_equal(ranges, st.ranges)
+    st.close()
     a.close(); b.close()
 
 

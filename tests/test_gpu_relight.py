@@ -7,7 +7,8 @@ import pytest
 
 import gs_inputs as gi
 import oracle as O
-from gpu_util import GpuRun, cams32, l1_sign_expected, rel_l2, scene
+from flips import decision_flips
+from gpu_util import GpuRun, OracleStages, cams32, l1_sign_expected, rel_l2, scene
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-4
@@ -88,16 +89,18 @@ def test_relit_projection_matches_oracle(rcase):
 def test_relit_gradients_match_oracle(rcase):
     planes, sh, cams, d, run = rcase
     gp = run.oracle_proj()
-    g2 = run.np("grad2d")[..., :9].astype(np.float64)
-    dp = O.project_bwd(planes, sh, cams, g2, dyn=d)  # stage-wise: the GPU's 2D gradients
-    assert rel_l2(run.np("dparams"), dp) <= TOL
-    assert rel_l2(run.np("dparams")[3:], dp[3:]) <= TOL  # the SH (transfer) part alone
+    # stage-wise: the GPU projection adjoint on the oracle's 2D gradients
+    st = OracleStages(O, planes, sh, cams, run.np("target"), dyn=d, gpu_dyn=run.dyn, gpu_lighting=run.lighting)
+    gd = st.gpu_project_bwd()
+    assert rel_l2(gd, st.dparams) <= TOL
+    assert rel_l2(gd[3:], st.dparams[3:]) <= TOL  # the SH (transfer) part alone
+    st.close()
     r = O.loss_and_grad(planes, sh, cams, run.np("target"), dyn=d)  # end to end
-    flips, _ = O.decision_flips(cams, r["proj"], r["vals"], r["ranges"], gp, run.sorted_vals(), run.ranges_np())
+    flips, _ = decision_flips(cams, r["proj"], r["vals"], r["ranges"], gp, run.sorted_vals(), run.ranges_np())
     support = np.any(r["proj"][..., [7, 12, 13, 14, 15]] != gp[..., [7, 12, 13, 14, 15]], axis=(0, 2))
     odd = flips.any(axis=0) | support
     assert odd.mean() <= 1e-3
-    od, _ = l1_sign_expected(O, planes, sh, cams, r, run.np("target"), run.np("image"), dyn=d)
+    od, _ = l1_sign_expected(O, planes, sh, cams, r, run.np("target"), run.np("dparams"), dyn=d, keep=~odd)
     assert rel_l2(run.np("dparams")[:, ~odd], od[:, ~odd]) <= TOL
     assert abs(float(run.loss.item()) - r["loss"]) <= TOL * r["loss"]
 

@@ -58,12 +58,19 @@ def test_full_record_replay_bit_exact():
     ctx = gs.Context(0, 1 << 24)
     t_base = torch.from_numpy(base).cuda()
     idx, rec, cnt = gs.gs_extract_delta(ctx, torch.from_numpy(th).cuda(), t_base, 1e-3)
-    client = torch.from_numpy(base).cuda()
-    gs.gs_apply_delta(ctx, client, rec, cnt)
     torch.cuda.synchronize()
     m = int(cnt.item())
-    assert ctx.status()[0] == 0 and m > 0
-    np.testing.assert_array_equal(client.cpu().numpy(), O.apply_delta(base, rec.cpu().numpy()[:m]))
+    oi, orec, _ = O.delta(th, base, 1e-3)
+    assert m == len(oi) > 0
+    np.testing.assert_array_equal(rec.cpu().numpy()[:m], orec)
+    # the client replays the oracle's records; the oracle replays the same
+    client = torch.from_numpy(base).cuda()
+    d_rec = torch.from_numpy(np.ascontiguousarray(orec)).cuda()
+    d_cnt = torch.tensor([len(oi)], dtype=torch.int32, device="cuda")
+    gs.gs_apply_delta(ctx, client, d_rec, d_cnt)
+    torch.cuda.synchronize()
+    assert ctx.status()[0] == 0
+    np.testing.assert_array_equal(client.cpu().numpy(), O.apply_delta(base, orec))
     ctx.close()
 
 
