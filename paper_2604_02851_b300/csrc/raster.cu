@@ -307,7 +307,7 @@ k_raster_bwd(const float4* __restrict__ proj, const ViewInfo* __restrict__ vt, i
     __shared__ float4 s_c[BATCH];   // r, g, b
     __shared__ uint32_t s_g[BATCH];
     __shared__ uint32_t s_pos[BATCH];  // position in the tile's list
-    __shared__ float s_acc[9][BATCH];
+    __shared__ float s_acc[9][BATCH + 1];  // padded: the 9 slots of one fragment sit in different banks
     __shared__ uint32_t s_max;
     __shared__ int s_wcnt[NT / 32];
     const int64_t gt = blockIdx.x;
