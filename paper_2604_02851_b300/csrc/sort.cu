@@ -154,7 +154,7 @@ __global__ void k_hist_scan(uint32_t* hist, int passes) {
 // pass of the tile-key sort, vout (values), kout (keys, may be null) and the
 // per-key [start, end) ranges.
 template <int BITS, int ITEMS>
-__global__ void __launch_bounds__(kThreads, 2)
+__global__ void __launch_bounds__(kThreads, 3)
 k_onesweep(const uint64_t* __restrict__ in, uint64_t* __restrict__ out, uint32_t* __restrict__ kout,
            uint32_t* __restrict__ vout, const uint32_t* d_count, int64_t cap, int shift, uint32_t kmask,
            const uint32_t* __restrict__ digit_off, unsigned long long* __restrict__ lookback,
@@ -902,7 +902,7 @@ void onesweep_passes(uint64_t* const buf[2], uint64_t* last_out, uint32_t* kout,
         const bool last = p == passes - 1;
         const uint64_t* src = buf[p % 2];
         uint64_t* dst = last ? last_out : buf[(p + 1) % 2];
-        k_onesweep<BITS, ITEMS><<<sm_count * 2, kThreads, 0, st>>>(
+        k_onesweep<BITS, ITEMS><<<sm_count * 3, kThreads, 0, st>>>(
             src, dst, last ? kout : nullptr, last ? vout : nullptr, d_count, cap, p * BITS, kmask, s.hist + p * 256,
             s.lookback + (int64_t)p * s.max_sort_tiles * R, s.counters + p, last ? ranges : nullptr, status);
     }
