@@ -770,11 +770,10 @@ k_fine_write(const uint64_t* __restrict__ citems, const uint2* __restrict__ cran
              const uint2* __restrict__ ranges, int64_t cap, uint32_t* __restrict__ vout,
              uint32_t* __restrict__ kout) {
     __shared__ uint32_t s_col[kFineGroups][64];
-    __shared__ uint32_t s_gv[kFineGroups][32];
+    __shared__ uint32_t s_gv[kFineGroups][33];
     __shared__ uint32_t s_base[64], s_tile[64];
-    __shared__ uint32_t s_stage[kFineWarps][kFineStage];
+    __shared__ uint32_t s_stage[kFineWarps][4 * kFineStage];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const uint32_t lt = lanemask_lt();
     uint32_t* stage = s_stage[warp];
     const uint32_t nchunks = *d_n_chunks;
     for (uint32_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
@@ -791,24 +790,43 @@ k_fine_write(const uint64_t* __restrict__ citems, const uint2* __restrict__ cran
         s_col[warp][lane + 32] = c1;
         s_gv[warp][lane] = gval;
         __syncthreads();
-        uint32_t gv[kFineGroups];  // this lane's entry of every group
+        // Each warp writes 8 of the 64 tiles, 4 per round.  Lane (q, g) owns
+        // the column word of tile q and group g: the 8 lanes of a tile scan
+        // their counts for offsets, then each lane stages the entries of its
+        // set bits in order, and the warp stores the 4 runs contiguously.
+        const int q = lane >> 3, g = lane & 7;
 #pragma unroll
-        for (int g = 0; g < kFineGroups; ++g) gv[g] = s_gv[g][lane];
-        for (int k = warp; k < 64; k += kFineWarps) {
-            uint32_t cnt = 0;
+        for (int rho = 0; rho < 2; ++rho) {
+            const int k = warp * 8 + rho * 4 + q;
+            uint32_t w = s_col[g][k];
+            const uint32_t cw = __popc(w);
+            uint32_t incl = cw;
 #pragma unroll
-            for (int g = 0; g < kFineGroups; ++g) {
-                const uint32_t word = s_col[g][k];
-                if ((word >> lane) & 1u) stage[cnt + __popc(word & lt)] = gv[g];
-                cnt += __popc(word);
+            for (int o = 1; o < 8; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+                if (g >= o) incl += y;
+            }
+            uint32_t off = incl - cw;
+            const uint32_t tot = __shfl_sync(0xFFFFFFFFu, incl, lane | 7);
+            uint32_t* st = stage + q * kFineStage;
+            while (w) {
+                const int b = __ffs(w) - 1;
+                w &= w - 1u;
+                st[off++] = s_gv[g][b];
             }
             __syncwarp();
-            const uint32_t base = s_base[k], t = s_tile[k];
-            for (uint32_t i = (uint32_t)lane; i < cnt; i += 32) {
-                const uint32_t o = base + i;
-                if ((int64_t)o < cap) {
-                    vout[o] = stage[i];
-                    if (kout) kout[o] = t;
+#pragma unroll
+            for (int qq = 0; qq < 4; ++qq) {
+                const int kk = warp * 8 + rho * 4 + qq;
+                const uint32_t cnt = __shfl_sync(0xFFFFFFFFu, tot, qq * 8);
+                const uint32_t base = s_base[kk], t = s_tile[kk];
+                const uint32_t* sq = stage + qq * kFineStage;
+                for (uint32_t i = (uint32_t)lane; i < cnt; i += 32) {
+                    const uint32_t o = base + i;
+                    if ((int64_t)o < cap) {
+                        vout[o] = sq[i];
+                        if (kout) kout[o] = t;
+                    }
                 }
             }
             __syncwarp();
