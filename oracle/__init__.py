@@ -41,6 +41,8 @@ def lib():
         L.or_sh_basis.argtypes = [_D, _D]
         L.or_sh_basis_grad.argtypes = [_D, _D]
         L.or_rect.argtypes = [C.c_double, C.c_double, C.c_double, C.c_int, C.c_int, C.c_int, _I32]
+        L.or_splat_rect.argtypes = [C.c_double, C.c_double, C.c_double, C.c_double, C.c_double, C.c_double,
+                                    C.c_int, C.c_int, C.c_int, _I32]
         L.or_project.argtypes = [C.c_int64, C.c_int, _D, C.c_int, _D, C.c_int, _D]
         L.or_project_dyn.argtypes = [C.c_int64, C.c_int, _D, C.c_int, _D, C.c_int, _I32, _D, C.c_void_p, _D,
                                      C.c_double, C.c_double, _D]
@@ -135,8 +137,17 @@ def sh_basis_grad(d) -> np.ndarray:
 
 
 def rect(u, v, r, width, height, tile=TILE):
+    """Tile rectangle of the square of half-side r around (u, v)."""
     out = np.zeros(4, dtype=np.int32)
     lib().or_rect(float(u), float(v), float(r), int(width), int(height), int(tile), out)
+    return out
+
+
+def splat_rect(u, v, r, a, c, opacity, width, height, tile=TILE):
+    """Tile rectangle of a splat (the square cut to its alpha >= 1/255 box)."""
+    out = np.zeros(4, dtype=np.int32)
+    lib().or_splat_rect(float(u), float(v), float(r), float(a), float(c), float(opacity), int(width),
+                        int(height), int(tile), out)
     return out
 
 

@@ -129,6 +129,35 @@ void or_rect(double u, double v, double r, int W, int H, int tile, int32_t* rect
     rect[3] = (int32_t)clampd(floor((v + r + tile - 1) / tile), 0.0, (double)TY);
 }
 
+/* Tile rectangle of a splat.  READING (the cited method bins by the 3-sigma
+ * square; the paper is silent): the square of half-side r, cut down on each
+ * axis to the bounding box of the ellipse where the splat's alpha reaches
+ * 1/255, q = d^T Sigma2^-1 d <= tau = 2 ln(255 o), whose half-widths are
+ * sqrt(tau a) and sqrt(tau c) for the 2D covariance (a, b; b, c), widened by
+ * 0.1 % + 0.01 px against rounding: the tiles holding a pixel centre within
+ * that box, intersected with the square's tiles.  Every pixel that
+ * compositing takes the splat at (inside the square, alpha >= 1/255) lies
+ * inside this rectangle, so the rendered image is the square's; a splat whose
+ * opacity is below 1/255 gets no tile. */
+void or_splat_rect(double u, double v, double r, double a, double c, double o, int W, int H, int tile,
+                   int32_t* rect) {
+    int32_t sq[4];
+    or_rect(u, v, r, W, H, tile, sq);
+    double tau = 2.0 * log(255.0 * o);
+    rect[0] = rect[1] = rect[2] = rect[3] = 0;
+    if (!(tau >= 0.0)) return;
+    double rx = sqrt(tau * a) * 1.001 + 0.01, ry = sqrt(tau * c) * 1.001 + 0.01;
+    /* tiles of the pixel centres p + 0.5 within [u - rx, u + rx] (and likewise in y) */
+    int32_t x0 = (int32_t)clampd(floor(ceil(u - rx - 0.5) / tile), 0.0, (double)W);
+    int32_t x1 = (int32_t)clampd(floor((u + rx - 0.5) / tile) + 1.0, 0.0, (double)W);
+    int32_t y0 = (int32_t)clampd(floor(ceil(v - ry - 0.5) / tile), 0.0, (double)H);
+    int32_t y1 = (int32_t)clampd(floor((v + ry - 0.5) / tile) + 1.0, 0.0, (double)H);
+    x0 = x0 > sq[0] ? x0 : sq[0]; x1 = x1 < sq[2] ? x1 : sq[2];
+    y0 = y0 > sq[1] ? y0 : sq[1]; y1 = y1 < sq[3] ? y1 : sq[3];
+    if (x1 <= x0 || y1 <= y0) return;
+    rect[0] = x0; rect[1] = y0; rect[2] = x1; rect[3] = y1;
+}
+
 /* ------------------------------------------------------------------------
  * Projection + SH colour (Sec. 3.2.3: the 3DGS parameters rendered by
  * differentiable splatting; Sec. 3.2.2: SH appearance).
@@ -382,7 +411,7 @@ static void project_impl(int64_t n, int sh_degree, const double* rows, int V, co
             double u = cam[12] * G.t[0] / G.t[2] + cam[14];
             double vv = cam[13] * G.t[1] / G.t[2] + cam[15];
             int32_t rect[4];
-            or_rect(u, vv, r, (int)cam[16], (int)cam[17], tile, rect);
+            or_splat_rect(u, vv, r, G.a, G.c, opac, (int)cam[16], (int)cam[17], tile, rect);
             if ((rect[2] - rect[0]) * (rect[3] - rect[1]) == 0) continue;
             double rgb[3], raw[3];
             int mask = 0;
@@ -670,7 +699,7 @@ static void project_bwd_impl(int64_t n, int sh_degree, const double* rows, int V
             double r = ceil(3.0 * sqrt(mid + sqrt(fmax(0.1, mid * mid - G.det))));
             double u = fx * G.t[0] / G.t[2] + cam[14], vv = fy * G.t[1] / G.t[2] + cam[15];
             int32_t rect[4];
-            or_rect(u, vv, r, (int)cam[16], (int)cam[17], tile, rect);
+            or_splat_rect(u, vv, r, G.a, G.c, opac, (int)cam[16], (int)cam[17], tile, rect);
             if ((rect[2] - rect[0]) * (rect[3] - rect[1]) == 0) continue;
             const double* gr = grad2d + ((int64_t)v * n + g) * G2D_STRIDE;
             double gu = gr[0], gv = gr[1], gA = gr[2], gB = gr[3], gC = gr[4], go = gr[5];

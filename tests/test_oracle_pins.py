@@ -1092,3 +1092,63 @@ def test_light_visibility_occluder_scene():
     # an empty map (+inf) lights everything
     v2, _ = O.light_visibility(sc, lc, np.full((64, 64), np.inf))
     assert np.all(v2 == 255)
+
+
+# ---------------------------------------------------------------- splat rectangle
+def _rect_case():
+    sc = gi.make_scene(400, 1, 50)
+    sc[1, :, :3] += 0.6
+    sc[1, :, 0] += np.random.default_rng(50).normal(0, 0.7, 400)  # anisotropic splats
+    sc[0, :30, 3] = -7.0  # opacity below 1/255
+    cams = gi.ring_cameras(2, 96, 80)
+    return sc, cams
+
+
+def test_splat_rect_is_inside_the_square_and_covers_every_pixel_alpha_reaches():
+    sc, cams = _rect_case()
+    pr = O.project(sc, 1, cams)
+    checked = 0
+    for v in range(2):
+        W, H = int(cams["width"][v]), int(cams["height"][v])
+        ys, xs = np.mgrid[0:H, 0:W] + 0.5
+        for g in range(pr.shape[1]):
+            p = pr[v, g]
+            if p[14] <= p[12]:
+                continue
+            u, vv, o, A, B, C, r = p[0], p[1], p[3], p[4], p[5], p[6], p[7]
+            sq = O.rect(u, vv, r, W, H)
+            assert sq[0] <= p[12] and sq[1] <= p[13] and p[14] <= sq[2] and p[15] <= sq[3]
+            # pixels of the square where alpha >= 1/255 (brute force, FP64)
+            dx, dy = xs - u, ys - vv
+            alpha = o * np.exp(-0.5 * (A * dx * dx + 2 * B * dx * dy + C * dy * dy))
+            tx, ty = (xs // 16).astype(int), (ys // 16).astype(int)
+            in_sq = (tx >= sq[0]) & (tx < sq[2]) & (ty >= sq[1]) & (ty < sq[3])
+            hit = in_sq & (alpha >= 1.0 / 255.0)
+            in_rect = (tx >= p[12]) & (tx < p[14]) & (ty >= p[13]) & (ty < p[15])
+            assert np.all(in_rect[hit])
+            checked += 1
+    assert checked > 300
+    # faint splats get no tile
+    assert np.all(pr[:, :30, 14] == 0)
+
+
+def test_splat_rect_leaves_the_image_of_the_square_unchanged():
+    """Binning by the 3-sigma squares and by the cut-down rectangles renders
+    the same image, transmittance and contributor counts: the tiles dropped
+    hold no pixel where the splat's alpha reaches 1/255."""
+    sc, cams = _rect_case()
+    f = O.forward(sc, 1, cams)
+    pr = f["proj"]
+    sq = np.zeros(pr.shape[:2] + (4,), dtype=np.int32)
+    for v in range(2):
+        W, H = int(cams["width"][v]), int(cams["height"][v])
+        for g in range(pr.shape[1]):
+            if pr[v, g, 7] > 0:
+                sq[v, g] = O.rect(pr[v, g, 0], pr[v, g, 1], pr[v, g, 7], W, H)
+    keys, vals, ranges = O.bin_sort(cams, sq, pr[..., 2].astype(np.float32))
+    assert len(vals) > len(f["vals"])
+    img, T, nc = O.render(cams, pr, vals, ranges)
+    np.testing.assert_array_equal(img, f["image"])
+    np.testing.assert_array_equal(T, f["T_final"])
+    # contributor counts are list positions: compare the contributing sets instead
+    assert np.array_equal(nc > 0, f["n_contrib"] > 0)
