@@ -267,7 +267,23 @@ k_project(const float4* __restrict__ P, int64_t n, int64_t g_off, int64_t n_out,
             vv = C.fy * Vg.ty / Vg.tz + C.cy;
             const ViewInfo vi = vt[v];
             tile_rect(u, vv, r, vi.tx, vi.ty, tile, x0, y0, x1, y1);
-            ok = (x1 - x0) * (y1 - y0) > 0;
+            // cut the square down to the tiles of pixel centres inside the
+            // box of the ellipse where alpha reaches 1/255 (q <= tau =
+            // 2 ln(255 o), half-widths sqrt(tau a), sqrt(tau c)): compositing
+            // takes the splat nowhere else, so the image is the square's
+            const float tau = 2.f * (logf(G.opac) + 5.5412635f);  // ln 255
+            if (tau >= 0.f) {
+                const float rx = sqrtf(tau * Vg.a) * 1.001f + 0.01f, ry = sqrtf(tau * Vg.c) * 1.001f + 0.01f;
+                const float ft = (float)tile;
+                const int ex0 = (int)fminf(fmaxf(floorf(ceilf(u - rx - 0.5f) / ft), 0.f), (float)vi.tx);
+                const int ex1 = (int)fminf(fmaxf(floorf((u + rx - 0.5f) / ft) + 1.f, 0.f), (float)vi.tx);
+                const int ey0 = (int)fminf(fmaxf(floorf(ceilf(vv - ry - 0.5f) / ft), 0.f), (float)vi.ty);
+                const int ey1 = (int)fminf(fmaxf(floorf((vv + ry - 0.5f) / ft) + 1.f, 0.f), (float)vi.ty);
+                x0 = max(x0, ex0); x1 = min(x1, ex1); y0 = max(y0, ey0); y1 = min(y1, ey1);
+            } else {
+                x1 = x0;  // a splat fainter than 1/255 takes no pixel
+            }
+            ok = x1 > x0 && y1 > y0;
         }
         if (!ok) {
             const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
