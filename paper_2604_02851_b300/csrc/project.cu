@@ -247,6 +247,7 @@ k_project(const float4* __restrict__ P, int64_t n, int64_t g_off, int64_t n_out,
     sh[0] *= G.L; sh[1] *= G.L; sh[2] *= G.L;
     float lrgb[3] = {0.f, 0.f, 0.f};
     uint32_t lmask = 0;
+    const float tau = 2.f * (logf(G.opac) + 5.5412635f);  // 2 ln(255 o): the alpha >= 1/255 ellipse
     if (LIT) {
         const float* lt = staged ? s_lt + lit_group(dyn, g_off + g) * kStageStride : lit_row(dyn, g_off + g);
         relit_rgb<NB>(sh, lt, lit_vis(dyn, g_off + g), lrgb, lmask);
@@ -271,7 +272,6 @@ k_project(const float4* __restrict__ P, int64_t n, int64_t g_off, int64_t n_out,
             // box of the ellipse where alpha reaches 1/255 (q <= tau =
             // 2 ln(255 o), half-widths sqrt(tau a), sqrt(tau c)): compositing
             // takes the splat nowhere else, so the image is the square's
-            const float tau = 2.f * (logf(G.opac) + 5.5412635f);  // ln 255
             if (tau >= 0.f) {
                 const float rx = sqrtf(tau * Vg.a) * 1.001f + 0.01f, ry = sqrtf(tau * Vg.c) * 1.001f + 0.01f;
                 const float ft = (float)tile;
