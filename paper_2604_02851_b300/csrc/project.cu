@@ -320,7 +320,7 @@ k_project(const float4* __restrict__ P, int64_t n, int64_t g_off, int64_t n_out,
 
 // ------------------------------------------------------------------ adjoint
 template <int D, bool LIT>
-__global__ void __launch_bounds__(128, 4)
+__global__ void __launch_bounds__(128, 3)
 k_project_bwd(const float4* __restrict__ P, int64_t n, int64_t n_out, Dyn dyn, const gs_camera* __restrict__ cams,
               int V,
               const float4* __restrict__ proj, const float4* __restrict__ g2d,
