@@ -307,7 +307,7 @@ k_raster_bwd(const float4* __restrict__ proj, const ViewInfo* __restrict__ vt, i
     __shared__ float4 s_c[BATCH];   // r, g, b
     __shared__ uint32_t s_g[BATCH];
     __shared__ uint32_t s_pos[BATCH];  // position in the tile's list
-    __shared__ float s_acc[9][BATCH + 1];  // padded: the 9 slots of one fragment sit in different banks
+    __shared__ float s_acc[9][BATCH + 1];  // raw sums per fragment, padded: the 9 sit in different banks
     __shared__ uint32_t s_max;
     __shared__ int s_wcnt[NT / 32];
     const int64_t gt = blockIdx.x;
@@ -450,42 +450,37 @@ k_raster_bwd(const float4* __restrict__ proj, const ViewInfo* __restrict__ vt, i
             // frozen Gaussians (index >= n_active) take part in the
             // recursion but need no gradient
             if (s_g[j] < n_active && __any_sync(0xFFFFFFFFu, contrib)) {
-                // lane 4q ends with sum q of (S1, S2, S3, S4, S5, S0, g6, g7)
+                // nine sums per fragment: S1 = sum dP dx, S2 = sum dP dy,
+                // S3 = sum dP dx^2, S4 = sum dP dx dy, S5 = sum dP dy^2,
+                // S0 = sum dP and the three colour sums; lane 4q ends with
+                // the warp's sum q of the first eight
                 const float f0 = s0.x + s0.y, f1 = s1.x + s1.y;
                 const float vals8[8] = {f1, f0 * dy, s2.x + s2.y, f1 * dy, f0 * dy * dy, f0, g6.x + g6.y,
                                         g7.x + g7.y};
                 const float mine = warp_sum8(vals8, lane);
-                const float S1 = __shfl_sync(0xFFFFFFFFu, mine, 0), S2 = __shfl_sync(0xFFFFFFFFu, mine, 4);
                 const float gb = warp_sum(g8.x + g8.y);
-                const int q = lane >> 2;
-                if ((lane & 3) == 0 || lane == 1) {
-                    // the conic and mean gradients from the five sums:
-                    // dL/du = -A S1 - B S2, dL/dv = -C S2 - B S1,
-                    // dL/dA = -S3 / 2, dL/dB = -S4, dL/dC = -S5 / 2
-                    const float4 co = s_b[j];
-                    float val;
-                    int slot;
-                    if (lane == 1) { val = gb; slot = 8; }
-                    else {
-                        // opacity: sum dL/dalpha * G = S0 / o (G = alpha / o unclamped)
-                        slot = q;
-                        val = q == 0 ? -co.x * S1 - co.y * S2
-                            : q == 1 ? -co.z * S2 - co.y * S1
-                            : q == 2 ? -0.5f * mine
-                            : q == 3 ? -mine
-                            : q == 4 ? -0.5f * mine
-                            : q == 5 ? mine / a.z : mine;
-                    }
-                    if (NT == 32) s_acc[slot][j] += val;
-                    else atomicAdd(&s_acc[slot][j], val);
+                if ((lane & 3) == 0) {
+                    if (NT == 32) s_acc[lane >> 2][j] += mine;
+                    else atomicAdd(&s_acc[lane >> 2][j], mine);
+                }
+                if (lane == 1) {
+                    if (NT == 32) s_acc[8][j] += gb;
+                    else atomicAdd(&s_acc[8][j], gb);
                 }
             }
         }
         __syncthreads();
         if ((int)threadIdx.x < cnt) {
+            // the conic, mean and opacity gradients from the sums:
+            // dL/du = -A S1 - B S2, dL/dv = -C S2 - B S1, dL/dA = -S3 / 2,
+            // dL/dB = -S4, dL/dC = -S5 / 2, dL/do = S0 / o (G = alpha / o
+            // where alpha is not clamped)
             const int t = threadIdx.x;
-            const float4 A = make_float4(s_acc[0][t], s_acc[1][t], s_acc[2][t], s_acc[3][t]);
-            const float4 Bv = make_float4(s_acc[4][t], s_acc[5][t], s_acc[6][t], s_acc[7][t]);
+            const float S1 = s_acc[0][t], S2 = s_acc[1][t], S3 = s_acc[2][t], S4 = s_acc[3][t];
+            const float S5 = s_acc[4][t], S0 = s_acc[5][t];
+            const float4 co = s_b[t];
+            const float4 A = make_float4(-co.x * S1 - co.y * S2, -co.z * S2 - co.y * S1, -0.5f * S3, -S4);
+            const float4 Bv = make_float4(-0.5f * S5, S0 / s_a[t].z, s_acc[6][t], s_acc[7][t]);
             const float Cv = s_acc[8][t];
             float* dst = grad2d + (rbase + s_g[t]) * kGradStride;
             if (A.x != 0.f || A.y != 0.f || A.z != 0.f || A.w != 0.f)
