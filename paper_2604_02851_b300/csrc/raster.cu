@@ -72,7 +72,7 @@ constexpr float kCullMargin = 0.01f;
 
 __device__ __forceinline__ float box_max_exponent(float4 q, float dxl, float dxh, float dyl, float dyh) {
     if (dxl <= 0.f && dxh >= 0.f && dyl <= 0.f && dyh >= 0.f) return 0.f;
-    const float ia = 0.5f / q.x, ic = 0.5f / q.z;
+    const float ia = __fdividef(0.5f, q.x), ic = __fdividef(0.5f, q.z);  // the margin covers the approximation
     float best = __int_as_float(0xff800000);
     const float ex[2] = {dxl, dxh}, ey[2] = {dyl, dyh};
 #pragma unroll
