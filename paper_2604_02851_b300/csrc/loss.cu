@@ -52,12 +52,27 @@ k_ssim_fwd(const float* __restrict__ x, const float* __restrict__ y, int H, int 
     const float* xp = x + plane * HW;
     const float* yp = y + plane * HW;
     const int ox = blockIdx.x * TW, oy = blockIdx.y * TW;
-    for (int i = threadIdx.x; i < SW * SW; i += 256) {
-        const int r = i / SW, c = i % SW;
-        const int gy = oy + r - HALO, gx = ox + c - HALO;
-        const bool in = gy >= 0 && gy < H && gx >= 0 && gx < W;
-        sx[r][c] = in ? xp[(int64_t)gy * W + gx] : 0.f;
-        sy[r][c] = in ? yp[(int64_t)gy * W + gx] : 0.f;
+    {
+        // all of this thread's loads in flight before the first store
+        constexpr int NL = (SW * SW + 255) / 256;
+        float lx[NL], ly[NL];
+#pragma unroll
+        for (int k = 0; k < NL; ++k) {
+            const int i = threadIdx.x + k * 256;
+            const int r = i / SW, c = i % SW;
+            const int gy = oy + r - HALO, gx = ox + c - HALO;
+            const bool in = i < SW * SW && gy >= 0 && gy < H && gx >= 0 && gx < W;
+            lx[k] = in ? __ldg(&xp[(int64_t)gy * W + gx]) : 0.f;
+            ly[k] = in ? __ldg(&yp[(int64_t)gy * W + gx]) : 0.f;
+        }
+#pragma unroll
+        for (int k = 0; k < NL; ++k) {
+            const int i = threadIdx.x + k * 256;
+            if (i < SW * SW) {
+                sx[i / SW][i % SW] = lx[k];
+                sy[i / SW][i % SW] = ly[k];
+            }
+        }
     }
     __syncthreads();
     // horizontal: task = (row r of 42, column group of RB)
@@ -155,14 +170,30 @@ k_ssim_bwd(const float* __restrict__ x, const float* __restrict__ y, int H, int 
     const int plane = blockIdx.z;
     const int64_t HW = (int64_t)H * W;
     const int ox = blockIdx.x * TW, oy = blockIdx.y * TW;
-    for (int i = threadIdx.x; i < SW * SW; i += 256) {
-        const int r = i / SW, c = i % SW;
-        const int gy = oy + r - HALO, gx = ox + c - HALO;
-        const bool in = gy >= 0 && gy < H && gx >= 0 && gx < W;
-        const int64_t p = plane * HW + (int64_t)gy * W + gx;
-        sm[0][r][c] = in ? dm0[p] : 0.f;
-        sm[1][r][c] = in ? dm1[p] : 0.f;
-        sm[2][r][c] = in ? dm2[p] : 0.f;
+    {
+        // all of this thread's loads in flight before the first store
+        constexpr int NL = (SW * SW + 255) / 256;
+        float l0[NL], l1[NL], l2[NL];
+#pragma unroll
+        for (int k = 0; k < NL; ++k) {
+            const int i = threadIdx.x + k * 256;
+            const int r = i / SW, c = i % SW;
+            const int gy = oy + r - HALO, gx = ox + c - HALO;
+            const bool in = i < SW * SW && gy >= 0 && gy < H && gx >= 0 && gx < W;
+            const int64_t p = plane * HW + (int64_t)gy * W + gx;
+            l0[k] = in ? __ldg(&dm0[p]) : 0.f;
+            l1[k] = in ? __ldg(&dm1[p]) : 0.f;
+            l2[k] = in ? __ldg(&dm2[p]) : 0.f;
+        }
+#pragma unroll
+        for (int k = 0; k < NL; ++k) {
+            const int i = threadIdx.x + k * 256;
+            if (i < SW * SW) {
+                sm[0][i / SW][i % SW] = l0[k];
+                sm[1][i / SW][i % SW] = l1[k];
+                sm[2][i / SW][i % SW] = l2[k];
+            }
+        }
     }
     __syncthreads();
     for (int t = threadIdx.x; t < SW * (TW / RB); t += 256) {
