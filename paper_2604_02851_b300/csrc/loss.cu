@@ -170,6 +170,19 @@ k_ssim_bwd(const float* __restrict__ x, const float* __restrict__ y, int H, int 
     const int plane = blockIdx.z;
     const int64_t HW = (int64_t)H * W;
     const int ox = blockIdx.x * TW, oy = blockIdx.y * TW;
+    // the image and target at this thread's outputs, fetched early
+    float xo[RB], yo[RB];
+    {
+        const int c = threadIdx.x % TW, r0 = (threadIdx.x / TW) * RB, gx = ox + c;
+#pragma unroll
+        for (int i = 0; i < RB; ++i) {
+            const int gy = oy + r0 + i;
+            const bool in = gy < H && gx < W;
+            const int64_t p = plane * HW + (int64_t)gy * W + gx;
+            xo[i] = in ? __ldg(&x[p]) : 0.f;
+            yo[i] = in ? __ldg(&y[p]) : 0.f;
+        }
+    }
     {
         // all of this thread's loads in flight before the first store
         constexpr int NL = (SW * SW + 255) / 256;
@@ -242,7 +255,7 @@ k_ssim_bwd(const float* __restrict__ x, const float* __restrict__ y, int H, int 
             const int gy = oy + r0 + i;
             if (gy >= H || gx >= W) continue;
             const int64_t p = plane * HW + (int64_t)gy * W + gx;
-            const float xv = x[p], yv = y[p];
+            const float xv = xo[i], yv = yo[i];
             const float d = xv - yv;
             const float sgn = d > 0.f ? 1.f : (d < 0.f ? -1.f : 0.f);
             dx[p] = (w_l1 * sgn - w_ssim * (a01[i].x + 2.f * xv * a01[i].y + yv * a2[i])) * inv_m;
