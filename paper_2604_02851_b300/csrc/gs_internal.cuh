@@ -112,7 +112,28 @@ inline Dyn make_dyn(const gs_dynamics* d, const gs_precull* pc = nullptr, uint8_
 // array; dynamics arrays are indexed by g_off + g.
 void launch_project(const float* params, int64_t n, int sh_degree, const Dyn& dyn, const gs_camera* d_cams,
                     const ViewInfo* vt, int V, int tile, float* proj, uint64_t* depth_kv, cudaStream_t st,
-                    int64_t g_off = 0, int64_t n_out = -1);
+                    int64_t g_off = 0, int64_t n_out = -1, uint2* rects = nullptr);
+
+// L2 eviction-priority policies for cache-hinted loads and stores.
+__device__ __forceinline__ uint64_t l2_policy_evict_last() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ uint64_t l2_policy_evict_first() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ void st_hint(uint2* p, uint2 v, uint64_t pol) {
+    asm volatile("st.global.L2::cache_hint.v2.u32 [%0], {%1, %2}, %3;" ::"l"(p), "r"(v.x), "r"(v.y), "l"(pol)
+                 : "memory");
+}
+__device__ __forceinline__ uint2 ld_hint(const uint2* p, uint64_t pol) {
+    uint2 v;
+    asm volatile("ld.global.L2::cache_hint.v2.u32 {%0, %1}, [%2], %3;" : "=r"(v.x), "=r"(v.y) : "l"(p), "l"(pol));
+    return v;
+}
 
 // Adjoint of the first n records of each view (record stride n_out).
 void launch_project_bwd(const float* params, int64_t n, int sh_degree, const Dyn& dyn, const gs_camera* d_cams,
@@ -141,6 +162,8 @@ struct SortScratch {
     unsigned long long* lookback;  // [4][max_tiles][256]
     int64_t max_sort_tiles;    // per pass
     uint32_t* d_count_depth;   // depth-sort items (V*n, or those kept by the compaction)
+    uint2* rects;              // [V*n] tile rectangle of each record: (x0 | y0 << 16, x1 | y1 << 16),
+                               // kept in L2 (evict-last) from the projection to the emission
     uint32_t* keep_sums;       // block sums of the depth-item compaction
     // two-level binning (super-tile lists, then per-tile lists)
     uint2* cranges;            // [total_tiles] bound on super-tiles: coarse [start, end)

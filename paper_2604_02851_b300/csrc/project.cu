@@ -203,7 +203,7 @@ template <int D, bool LIT>
 __global__ void __launch_bounds__(256)
 k_project(const float4* __restrict__ P, int64_t n, int64_t g_off, int64_t n_out, Dyn dyn,
           const gs_camera* __restrict__ cams, const ViewInfo* __restrict__ vt, int V, int tile,
-          float4* __restrict__ proj, uint64_t* __restrict__ dkv) {
+          float4* __restrict__ proj, uint64_t* __restrict__ dkv, uint2* __restrict__ rects) {
     const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     extern __shared__ float s_lt[];
     bool staged = false;
@@ -289,6 +289,7 @@ k_project(const float4* __restrict__ P, int64_t n, int64_t g_off, int64_t n_out,
             const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
             out[0] = z; out[1] = z; out[2] = z; out[3] = z;
             if (dkv) dkv[rec] = (0xFFFFFFFFull << 32) | (uint32_t)rec;
+            if (rects) st_hint(rects + rec, make_uint2(0u, 0u), l2_policy_evict_last());
             continue;
         }
         float rgb[3] = {lrgb[0], lrgb[1], lrgb[2]};
@@ -315,6 +316,8 @@ k_project(const float4* __restrict__ P, int64_t n, int64_t g_off, int64_t n_out,
         out[3] = make_float4(__uint_as_float(lo), __uint_as_float(hi),
                              __uint_as_float((uint32_t)((x1 - x0) * (y1 - y0))), 0.f);
         if (dkv) dkv[rec] = ((uint64_t)__float_as_uint(Vg.tz) << 32) | (uint32_t)rec;
+        // the emission gathers the rectangle in depth order: kept in L2
+        if (rects) st_hint(rects + rec, make_uint2(lo, hi), l2_policy_evict_last());
     }
 }
 
@@ -565,7 +568,7 @@ void launch_view_table(const gs_camera* d_cams, int V, int tile, ViewInfo* vt, l
 
 void launch_project(const float* params, int64_t n, int sh_degree, const Dyn& dyn, const gs_camera* d_cams,
                     const ViewInfo* vt, int V, int tile, float* proj, uint64_t* depth_kv, cudaStream_t st,
-                    int64_t g_off, int64_t n_out) {
+                    int64_t g_off, int64_t n_out, uint2* rects) {
     if (n <= 0) return;
     if (n_out < 0) n_out = n;
     const int threads = 256;
@@ -575,8 +578,8 @@ void launch_project(const float* params, int64_t n, int sh_degree, const Dyn& dy
     const bool lit = dyn.lit_tab != nullptr;
     const size_t smem = lit && lit_groups(dyn) <= kStageGroups ? sizeof(float) * lit_groups(dyn) * kStageStride : 0;
 #define GS_PROJ(DD)                                                                                              \
-    (lit ? k_project<DD, true><<<blocks, threads, smem, st>>>(P, n, g_off, n_out, dyn, d_cams, vt, V, tile, out, depth_kv) \
-         : k_project<DD, false><<<blocks, threads, 0, st>>>(P, n, g_off, n_out, dyn, d_cams, vt, V, tile, out, depth_kv))
+    (lit ? k_project<DD, true><<<blocks, threads, smem, st>>>(P, n, g_off, n_out, dyn, d_cams, vt, V, tile, out, depth_kv, rects) \
+         : k_project<DD, false><<<blocks, threads, 0, st>>>(P, n, g_off, n_out, dyn, d_cams, vt, V, tile, out, depth_kv, rects))
     switch (sh_degree) {
         case 0: GS_PROJ(0); break;
         case 1: GS_PROJ(1); break;

@@ -329,12 +329,14 @@ __global__ void k_clear_u32(uint32_t* p, int64_t n) {
 
 // Depth-sort input from projection records: key = float32 depth bits of a
 // visible (view, Gaussian), all-ones when culled; value = record index.
-__global__ void k_depth_keys(const uint4* __restrict__ proj, int64_t items, uint64_t* __restrict__ kv) {
+__global__ void k_depth_keys(const uint4* __restrict__ proj, int64_t items, uint64_t* __restrict__ kv,
+                             uint2* __restrict__ rects) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= items) return;
-    const uint32_t tiles = proj[i * 4 + 3].z;
-    const uint32_t key = tiles ? proj[i * 4].z : 0xFFFFFFFFu;
+    const uint4 r3 = proj[i * 4 + 3];
+    const uint32_t key = r3.z ? proj[i * 4].z : 0xFFFFFFFFu;
     kv[i] = ((uint64_t)key << 32) | (uint32_t)i;
+    st_hint(rects + i, make_uint2(r3.x, r3.y), l2_policy_evict_last());
 }
 
 // Compaction of depth-sort items: the items with a key other than all ones
@@ -419,7 +421,7 @@ __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t x, int lane) {
 // one contiguous range.
 template <int BITS>
 __global__ void __launch_bounds__(kEmitThreads)
-k_emit(const uint64_t* __restrict__ dsorted, int64_t total, int64_t n, const uint4* __restrict__ proj,
+k_emit(const uint64_t* __restrict__ dsorted, int64_t total, int64_t n, const uint2* __restrict__ rects,
        const ViewInfo* __restrict__ vt, int64_t cap, uint64_t* __restrict__ kv,
        unsigned long long* __restrict__ lookback, uint32_t* block_counter, uint32_t* d_num_keys,
        int passes, uint32_t* __restrict__ hist, int sshift, unsigned long long* fine_total, uint32_t key_bound,
@@ -451,7 +453,11 @@ k_emit(const uint64_t* __restrict__ dsorted, int64_t total, int64_t n, const uin
         tx[r] = 1;
         if (idx < total) {
             const uint32_t rr = (uint32_t)dsorted[idx];
-            const uint4 p3 = proj[(size_t)rr * 4 + 3];
+            // the record's tile rectangle, left in L2 by the projection (its
+            // last use: demoted for eviction)
+            const uint2 rc = ld_hint(rects + rr, l2_policy_evict_first());
+            const uint32_t rw = (rc.y & 0xFFFFu) - (rc.x & 0xFFFFu), rh = (rc.y >> 16) - (rc.x >> 16);
+            const uint4 p3 = make_uint4(rc.x, rc.y, rw * rh, 0u);
             const uint32_t v = (uint32_t)(rr / (uint64_t)n);
             cnt[r] = p3.z;
             lo[r] = p3.x;
@@ -939,7 +945,7 @@ void emit_and_sort(const uint64_t* dsorted, int64_t items, const uint32_t* d_ite
     cudaMemsetAsync(s.hist, 0, sizeof(uint32_t) * kMaxPasses * 256, st);
     cudaMemsetAsync(s.counters, 0, sizeof(uint32_t) * 8, st);
     cudaMemsetAsync(s.emit_lookback, 0, sizeof(unsigned long long) * (size_t)nblk, st);
-    k_emit<BITS><<<(unsigned)nblk, kEmitThreads, 0, st>>>(dsorted, items, n, pr, vt, keys_cap, s.tkv[0],
+    k_emit<BITS><<<(unsigned)nblk, kEmitThreads, 0, st>>>(dsorted, items, n, s.rects, vt, keys_cap, s.tkv[0],
                                                           s.emit_lookback, s.counters + 7, d_num_keys, passes,
                                                           s.hist, 0, nullptr, (uint32_t)total_tiles, d_items,
                                                           status);
@@ -971,7 +977,7 @@ void emit_two_level(const uint64_t* dsorted, int64_t items, const uint32_t* d_it
     cudaMemsetAsync(s.counters, 0, sizeof(uint32_t) * 8, st);
     cudaMemsetAsync(s.emit_lookback, 0, sizeof(unsigned long long) * (size_t)nblk, st);
     cudaMemsetAsync(s.d_fine_total, 0, sizeof(unsigned long long), st);
-    k_emit<BITS><<<(unsigned)nblk, kEmitThreads, 0, st>>>(dsorted, items, n, pr, vt, keys_cap, s.tkv[0],
+    k_emit<BITS><<<(unsigned)nblk, kEmitThreads, 0, st>>>(dsorted, items, n, s.rects, vt, keys_cap, s.tkv[0],
                                                           s.emit_lookback, s.counters + 7, s.d_count_coarse,
                                                           passes, s.hist, kSuperShift, s.d_fine_total,
                                                           (uint32_t)n_super, d_items, status);
@@ -1022,6 +1028,7 @@ void carve_sort_scratch(char* base, int V, int64_t n, int64_t keys_cap, int64_t 
     s->max_sort_tiles = (std::max(items, keys_cap) + kMinTileKeys - 1) / kMinTileKeys + 1;
     s->lookback = c.take<unsigned long long>((size_t)kMaxPasses * s->max_sort_tiles * 256);
     s->d_count_depth = c.take<uint32_t>(1);
+    s->rects = c.take<uint2>(items);
     s->keep_sums = c.take<uint32_t>((items + kKeepBlock - 1) / kKeepBlock + 1);
     // super-tiles never outnumber tiles
     const int64_t ns = total_tiles > 0 ? total_tiles : 1;
@@ -1054,7 +1061,7 @@ void launch_bin_sort(const float* proj, const ViewInfo* vt, int V, int64_t n, in
     // 1. depth sort of all (view, Gaussian) pairs: 32-bit keys, 4 passes of
     //    8-bit digits ending back in dkv[0]
     if (!depth_ready)
-        k_depth_keys<<<(unsigned)((items + 255) / 256), 256, 0, st>>>(pr, items, s.dkv[0]);
+        k_depth_keys<<<(unsigned)((items + 255) / 256), 256, 0, st>>>(pr, items, s.dkv[0], s.rects);
     // with compaction the kept items move to dkv[1] and the sort ends there
     const uint64_t* dsorted = s.dkv[0];
     const uint32_t* d_items = nullptr;
