@@ -37,8 +37,6 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
-constexpr int kItems = 16;                       // keys per thread per tile
-constexpr int kTileKeys = kThreads * kItems;     // 4096
 constexpr int kMinTileKeys = kThreads * 8;       // smallest onesweep tile (look-back sizing)
 constexpr int kMaxPasses = 4;
 constexpr unsigned long long kFlagAgg = 1ULL << 62;
@@ -768,6 +766,7 @@ constexpr int kFineWarps = kFineThreads / 32;
 constexpr int kFineStage = kFineChunk;
 static_assert(kFineWarps == kFineGroups, "one warp per group of the chunk");
 
+template <bool KOUT>
 __global__ void __launch_bounds__(kFineThreads)
 k_fine_write(const uint64_t* __restrict__ citems, const uint2* __restrict__ cranges,
              const uint32_t* __restrict__ chunk_first, const uint32_t* __restrict__ chunk_s,
@@ -782,6 +781,7 @@ k_fine_write(const uint64_t* __restrict__ citems, const uint2* __restrict__ cran
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint32_t* stage = s_stage[warp];
     const uint32_t nchunks = *d_n_chunks;
+    const uint32_t cap32 = cap < 0xFFFFFFFFll ? (uint32_t)cap : 0xFFFFFFFFu;  // keys_cap < 2^32
     for (uint32_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
         const FineChunk f = fine_chunk(c, cranges, chunk_first, chunk_s, vt, V, total_tiles, lane);
         if (warp == 0) {
@@ -821,24 +821,36 @@ k_fine_write(const uint64_t* __restrict__ citems, const uint2* __restrict__ cran
                 st[off++] = s_gv[g][b];
             }
             __syncwarp();
-#pragma unroll
-            for (int qq = 0; qq < 4; ++qq) {
-                const int kk = warp * 8 + rho * 4 + qq;
-                const uint32_t cnt = __shfl_sync(0xFFFFFFFFu, tot, qq * 8);
-                const uint32_t base = s_base[kk], t = s_tile[kk];
-                const uint32_t* sq = stage + qq * kFineStage;
-                for (uint32_t i = (uint32_t)lane; i < cnt; i += 32) {
-                    const uint32_t o = base + i;
-                    if ((int64_t)o < cap) {
-                        vout[o] = sq[i];
-                        if (kout) kout[o] = t;
-                    }
+            // the four runs as one sequence: item i of it is entry i - e_qq
+            // of run qq, e_qq the runs' exclusive prefix
+            const uint32_t e1 = __shfl_sync(0xFFFFFFFFu, tot, 0);
+            const uint32_t e2 = e1 + __shfl_sync(0xFFFFFFFFu, tot, 8);
+            const uint32_t e3 = e2 + __shfl_sync(0xFFFFFFFFu, tot, 16);
+            const uint32_t all = e3 + __shfl_sync(0xFFFFFFFFu, tot, 24);
+            const int k0 = warp * 8 + rho * 4;
+            for (uint32_t i = (uint32_t)lane; i < all; i += 32) {
+                const int qq = (int)(i >= e1) + (int)(i >= e2) + (int)(i >= e3);
+                const uint32_t idx = i - (qq == 0 ? 0u : qq == 1 ? e1 : qq == 2 ? e2 : e3);
+                const uint32_t o = s_base[k0 + qq] + idx;
+                if (o < cap32) {
+                    vout[o] = stage[qq * kFineStage + idx];
+                    if (KOUT) kout[o] = s_tile[k0 + qq];
                 }
             }
             __syncwarp();
         }
         __syncthreads();
     }
+}
+
+template <bool KOUT>
+unsigned fine_write_grid(int sm_count) {
+    static int per_sm = 0;
+    if (per_sm == 0 &&
+        (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fine_write<KOUT>, kFineThreads, 0) != cudaSuccess ||
+         per_sm < 1))
+        per_sm = 1;
+    return (unsigned)(sm_count * per_sm);
 }
 
 // Per (super-tile, tile): exclusive prefix of the chunk counts in place, and
@@ -1001,10 +1013,16 @@ void emit_two_level(const uint64_t* dsorted, int64_t items, const uint32_t* d_it
     k_fine_prefix<<<(unsigned)((n_super * 64 + 255) / 256), 256, 0, st>>>(s.chunk_first, s.d_n_chunks, vt, V,
                                                                          total_tiles, s.chunk_off, s.tile_count);
     k_tile_scan<<<1, 1024, 0, st>>>(s.tile_count, total_tiles, keys_cap, reinterpret_cast<uint2*>(ranges));
-    k_fine_write<<<(unsigned)(sm_count * 8), kFineThreads, 0, st>>>(citems, s.cranges, s.chunk_first, s.chunk_s, s.d_n_chunks, vt, V,
-                                                 total_tiles, s.chunk_off,
-                                                 reinterpret_cast<const uint2*>(ranges), keys_cap, sorted_vals,
-                                                 sorted_keys);
+    // one wave: a grid-stride loop over the chunks with as many blocks as are
+    // resident (the staging buffers limit residency below 8 blocks an SM)
+    if (sorted_keys)
+        k_fine_write<true><<<fine_write_grid<true>(sm_count), kFineThreads, 0, st>>>(
+            citems, s.cranges, s.chunk_first, s.chunk_s, s.d_n_chunks, vt, V, total_tiles, s.chunk_off,
+            reinterpret_cast<const uint2*>(ranges), keys_cap, sorted_vals, sorted_keys);
+    else
+        k_fine_write<false><<<fine_write_grid<false>(sm_count), kFineThreads, 0, st>>>(
+            citems, s.cranges, s.chunk_first, s.chunk_s, s.d_n_chunks, vt, V, total_tiles, s.chunk_off,
+            reinterpret_cast<const uint2*>(ranges), keys_cap, sorted_vals, nullptr);
 }
 
 }  // namespace
