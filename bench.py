@@ -86,8 +86,10 @@ def phase_model(n, V, K, total_tiles, npix, sum_nc, n_changed, binning, passes, 
         "loss": ("hbm", 3 * npix * 44),
         "raster_bwd": ("alu", sum_nc * RASTER_BWD_FLOP_PER_FRAGMENT),
         "project_bwd": ("hbm", nt * 480 + V * nt * (48 + 32)),
-        "adam": ("hbm", 60 * nt * 4 * 7),
-        "delta": ("hbm", nt * (480 + 2) + n_changed * (240 + 240 + 128 + 4)),
+        # Adam fused with the delta's changed test: theta, grad, m, v, baseline
+        # read, theta, m, v written, one flag byte out
+        "adam": ("hbm", 60 * nt * 4 * 8 + nt),
+        "delta": ("hbm", nt + n_changed * (240 + 240 + 128 + 4)),
     }
 
 
@@ -116,7 +118,7 @@ def measured_traffic(workload, kernel):
 
 # phases that are one kernel (plus negligible set-up launches), by kernel name
 SINGLE_KERNEL_PHASES = {"project": "k_project", "emit": "k_emit", "render_fwd": "k_render_fwd",
-                        "raster_bwd": "k_raster_bwd", "project_bwd": "k_project_bwd", "adam": "k_adam"}
+                        "raster_bwd": "k_raster_bwd", "project_bwd": "k_project_bwd", "adam": "k_adam_flags"}
 
 
 def gpu_launches_per_step(binning, passes):
@@ -125,11 +127,12 @@ def gpu_launches_per_step(binning, passes):
     4 passes), emission and sort (two-level: emission, fine total, ranges
     init, look-back clear, scan, passes, ranges fix, chunk table, count,
     prefix, tile scan, write; direct: emission, ranges init, look-back clear,
-    scan, passes, ranges fix), compositing, loss (2), adjoints (2), Adam (2),
-    delta (3)."""
+    scan, passes, ranges fix), compositing, loss (2), adjoints (2), Adam
+    with the delta's changed test and the step counter (2), delta scan and
+    records (2)."""
     depth = 8
     sort = (11 + passes) if binning == "two_level" else (5 + passes)
-    return 1 + 1 + depth + sort + 1 + 2 + 1 + 1 + 2 + 3
+    return 1 + 1 + depth + sort + 1 + 2 + 1 + 1 + 2 + 2
 
 
 def replica_seeds(rank: int):

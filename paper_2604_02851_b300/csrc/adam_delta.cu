@@ -21,6 +21,21 @@ namespace {
 
 struct LrTable { float lr[60]; };
 
+// One bias-corrected Adam update of a float4 of parameters (learning rates
+// l[0..3]); bc1 = 1 - b1^t, sbc2 = sqrt(1 - b2^t).
+__device__ __forceinline__ void adam4(float4& th, float4& mm, float4& vv, const float4 g, const float* l, float b1,
+                                      float b2, float eps, float bc1, float sbc2) {
+#define ADAM_LANE(c, k)                                                   \
+    mm.c = b1 * mm.c + (1.f - b1) * g.c;                                  \
+    vv.c = b2 * vv.c + (1.f - b2) * g.c * g.c;                            \
+    th.c -= (l[k] / bc1) * mm.c / (sqrtf(vv.c) / sbc2 + eps);
+    ADAM_LANE(x, 0)
+    ADAM_LANE(y, 1)
+    ADAM_LANE(z, 2)
+    ADAM_LANE(w, 3)
+#undef ADAM_LANE
+}
+
 __global__ void __launch_bounds__(256)
 k_adam(float4* __restrict__ theta, const float4* __restrict__ grad, float4* __restrict__ m,
        float4* __restrict__ v, int64_t n, LrTable lr, float b1, float b2, float eps, int host_step,
@@ -36,16 +51,7 @@ k_adam(float4* __restrict__ theta, const float4* __restrict__ grad, float4* __re
         if (fwd && !fwd[i - (int64_t)plane * n]) continue;  // preculled: no update
         const float4 g = grad[i];
         float4 mm = m[i], vv = v[i], th = theta[i];
-        const float* l = lr.lr + 4 * plane;
-#define ADAM_LANE(c, k)                                                   \
-        mm.c = b1 * mm.c + (1.f - b1) * g.c;                              \
-        vv.c = b2 * vv.c + (1.f - b2) * g.c * g.c;                        \
-        th.c -= (l[k] / bc1) * mm.c / (sqrtf(vv.c) / sbc2 + eps);
-        ADAM_LANE(x, 0)
-        ADAM_LANE(y, 1)
-        ADAM_LANE(z, 2)
-        ADAM_LANE(w, 3)
-#undef ADAM_LANE
+        adam4(th, mm, vv, g, lr.lr + 4 * plane, b1, b2, eps, bc1, sbc2);
         m[i] = mm;
         v[i] = vv;
         theta[i] = th;
@@ -68,6 +74,49 @@ k_delta_flags(const float4* __restrict__ theta, const float4* __restrict__ base,
             const float4 a = theta[p * n + g], b = base[p * n + g];
             const float m = fmaxf(fmaxf(fabsf(a.x - b.x), fabsf(a.y - b.y)), fmaxf(fabsf(a.z - b.z), fabsf(a.w - b.w)));
             changed |= (m > thr) ? 1u : 0u;
+        }
+        flags[g] = (uint8_t)changed;
+    }
+    const uint32_t cnt = __syncthreads_count(changed);
+    if (threadIdx.x == 0) block_sums[blockIdx.x] = cnt;
+}
+
+// The training step's Adam update fused with the changed test of the delta
+// extraction: one thread per Gaussian walks its 15 planes, updates them and
+// compares the new values with the baseline, so that the parameters are read
+// once.  Same arithmetic as k_adam and k_delta_flags.  Six blocks an SM (40
+// registers, the learning rates in shared memory) keep enough loads in
+// flight; unrolling the plane loop, or 5 and 8 blocks, measured slower.
+__global__ void __launch_bounds__(kDeltaThreads, 6)
+k_adam_flags(float4* __restrict__ theta, const float4* __restrict__ grad, float4* __restrict__ m,
+             float4* __restrict__ v, const float4* __restrict__ base, int64_t n, LrTable lr, float b1, float b2,
+             float eps, int host_step, const int32_t* __restrict__ d_step, const uint8_t* __restrict__ fwd,
+             float thr, uint8_t* __restrict__ flags, uint32_t* __restrict__ block_sums) {
+    __shared__ float s_lr[60];
+    if (threadIdx.x < 60) s_lr[threadIdx.x] = lr.lr[threadIdx.x];
+    __syncthreads();
+    const int step = d_step ? *d_step : host_step;
+    const float bc1 = 1.f - powf(b1, (float)step);
+    const float sbc2 = sqrtf(1.f - powf(b2, (float)step));
+    const int64_t g = (int64_t)blockIdx.x * kDeltaThreads + threadIdx.x;
+    uint32_t changed = 0;
+    if (g < n) {
+        const bool upd = !fwd || fwd[g];  // preculled: no update
+#pragma unroll 1
+        for (int p = 0; p < 15; ++p) {
+            const int64_t i = p * n + g;
+            float4 th = theta[i];
+            const float4 b = base[i];
+            if (upd) {
+                const float4 gr = grad[i];
+                float4 mm = m[i], vv = v[i];
+                adam4(th, mm, vv, gr, s_lr + 4 * p, b1, b2, eps, bc1, sbc2);
+                m[i] = mm;
+                v[i] = vv;
+                theta[i] = th;
+            }
+            const float d = fmaxf(fmaxf(fabsf(th.x - b.x), fabsf(th.y - b.y)), fmaxf(fabsf(th.z - b.z), fabsf(th.w - b.w)));
+            changed |= (d > thr) ? 1u : 0u;
         }
         flags[g] = (uint8_t)changed;
     }
@@ -335,6 +384,34 @@ void launch_delta(const float* theta, float* baseline, int64_t n, float thr, uin
     k_delta_flags<<<(unsigned)nblk, kDeltaThreads, 0, st>>>(th, b, n, thr, flags, sums);
     k_scan_sums<<<1, 1024, 0, st>>>(sums, nblk, d_count, -1, nullptr);
     k_delta_emit<<<(unsigned)nblk, kDeltaThreads, 0, st>>>(th, b, n, flags, sums, d_idx, d_records);
+}
+
+void launch_adam_delta(float* theta, const float* grad, float* m, float* v, int64_t n, const gs_adam_cfg& cfg,
+                       const uint8_t* fwd, float* baseline, float thr, uint32_t* d_idx, uint8_t* d_records,
+                       uint32_t* d_count, char* scratch, cudaStream_t st, void (*mark)(void* const*, int, cudaStream_t),
+                       void* const* events, int event) {
+    Carver c(scratch);
+    uint8_t* flags = c.take<uint8_t>(n > 0 ? n : 1);
+    const int64_t nblk = (n + kDeltaThreads - 1) / kDeltaThreads;
+    uint32_t* sums = c.take<uint32_t>(nblk + 1);
+    if (n > 0) {
+        LrTable lr;
+        for (int i = 0; i < 60; ++i) lr.lr[i] = cfg.lr[i];
+        k_adam_flags<<<(unsigned)nblk, kDeltaThreads, 0, st>>>(
+            reinterpret_cast<float4*>(theta), reinterpret_cast<const float4*>(grad), reinterpret_cast<float4*>(m),
+            reinterpret_cast<float4*>(v), reinterpret_cast<const float4*>(baseline), n, lr, cfg.beta1, cfg.beta2,
+            cfg.eps, cfg.step, cfg.d_step, fwd, thr, flags, sums);
+    }
+    if (cfg.d_step && cfg.increment) k_inc_step<<<1, 1, 0, st>>>(const_cast<int32_t*>(cfg.d_step));
+    if (mark) mark(events, event, st);
+    if (n <= 0) {
+        cudaMemsetAsync(d_count, 0, sizeof(uint32_t), st);
+        return;
+    }
+    k_scan_sums<<<1, 1024, 0, st>>>(sums, nblk, d_count, -1, nullptr);
+    k_delta_emit<<<(unsigned)nblk, kDeltaThreads, 0, st>>>(reinterpret_cast<const float4*>(theta),
+                                                          reinterpret_cast<float4*>(baseline), n, flags, sums, d_idx,
+                                                          d_records);
 }
 
 bool attr_group(int attr, int* lo, int* hi, int* f32) {

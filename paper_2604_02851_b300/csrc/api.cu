@@ -537,10 +537,11 @@ gs_status_t gs_train_step_events(gs_ctx* ctx, const gs_camera* d_cams, const gs_
     gs_adam_cfg ac = cfg->adam;
     ac.d_step = io->d_step;
     ac.increment = 1;
-    launch_adam(io->params, io->grads, io->adam_m, io->adam_v, na, ac, st, cfg->precull ? p.fwd : nullptr);
-    mark(ev, 9, st);
-    launch_delta(io->params, io->baseline, na, cfg->delta_thr, io->d_delta_idx, io->d_delta_records,
-                 io->d_delta_count, p.delta, st);
+    // Adam with the delta's changed test (phase 9 ends after it), then the
+    // delta's scan and records
+    launch_adam_delta(io->params, io->grads, io->adam_m, io->adam_v, na, ac, cfg->precull ? p.fwd : nullptr,
+                      io->baseline, cfg->delta_thr, io->d_delta_idx, io->d_delta_records, io->d_delta_count,
+                      p.delta, st, ev ? mark : nullptr, ev, 9);
     mark(ev, 10, st);
     return launch_check();
 }

@@ -224,6 +224,13 @@ void launch_cell_visibility(const gs_camera* d_cams, const gs_camera* host_cams,
 size_t delta_scratch_bytes(int64_t n);
 void launch_delta(const float* theta, float* baseline, int64_t n, float thr, uint32_t* d_idx,
                   uint8_t* d_records, uint32_t* d_count, char* scratch, cudaStream_t st);
+// The training step's Adam update and delta extraction: Adam fused with the
+// changed test (k_adam_flags), the step counter increment, then (after the
+// optional phase mark) the scan and the record emission.
+void launch_adam_delta(float* theta, const float* grad, float* m, float* v, int64_t n, const gs_adam_cfg& cfg,
+                       const uint8_t* fwd, float* baseline, float thr, uint32_t* d_idx, uint8_t* d_records,
+                       uint32_t* d_count, char* scratch, cudaStream_t st, void (*mark)(void* const*, int, cudaStream_t),
+                       void* const* events, int event);
 
 // Tensor deltas of one attribute group (GS_ATTR_*) and client-side replay.
 bool attr_group(int attr, int* lo, int* hi, int* f32);
