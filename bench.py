@@ -72,10 +72,10 @@ def phase_model(n, V, K, total_tiles, npix, sum_nc, n_changed, binning, passes, 
     vn = V * n
     nt = n if n_train is None else n_train  # Gaussians that are trained (the active pool)
     if binning == "two_level":
-        emit = vn * (8 + 16) + Kc * 8
+        emit = vn * (8 + 8) + Kc * 8
         sort = Kc * 16 * passes + 2 * Kc * 8 + K * 4 + total_tiles * 8 + chunks * 64 * 4 * 3
     else:
-        emit = vn * (8 + 16) + K * 8
+        emit = vn * (8 + 8) + K * 8
         sort = K * (16 * (passes - 1) + 12) + total_tiles * 16
     return {
         "project": ("hbm", n * 240 + vn * (64 + 8)),
@@ -97,7 +97,7 @@ def phase_model(n, V, K, total_tiles, npix, sum_nc, n_changed, binning, passes, 
 # capture at full size; profiles/train_step_1M_8x720p_traffic.md), valid while
 # the kernel's source file is unchanged (first 12 hex digits of its SHA-1).
 MEASURED_TRAFFIC = {
-    ("c3_1M_8x720p", "k_raster_bwd"): (265.7e6, "csrc/raster.cu", "4048faea60c2"),
+    ("c3_1M_8x720p", "k_raster_bwd"): (265.0e6, "csrc/raster.cu", "f8476020b95c"),
 }
 
 
