@@ -463,11 +463,13 @@ gs_status_t gs_render_batch(gs_ctx* ctx, const gs_scene* scene, const gs_camera*
     const Dyn dyn = scene_dyn(ctx, scene->dyn, scene->precull, nullptr, scene->lighting, st);
     launch_project(scene->params, scene->n, scene->sh_degree, dyn, d_cams, p.vt, n_requests, ctx->tile, p.proj,
                    s.dkv[0], st, 0, -1, s.rects);
+    // two-level binning leaves the per-tile lists in chunk-bitmap form
+    CoarseLists cl;
     launch_bin_sort(p.proj, p.vt, n_requests, scene->n, keys_cap, total_tiles, ctx->binning, ctx->sort_bits, ctx->sort_items, s, true, nullptr,
                     p.vals, p.ranges, p.n_keys, ctx->d_status, ctx->sm_count, st, nullptr, nullptr, 0,
-                    scene->precull != nullptr);
+                    scene->precull != nullptr, &cl);
     launch_render_fwd(p.proj, p.vt, n_requests, scene->n, ctx->tile, ctx->raster_tpr, p.vals, p.ranges, b, image, nullptr,
-                      nullptr, total_tiles, st);
+                      nullptr, total_tiles, st, &cl);
     return launch_check();
 }
 
@@ -520,17 +522,21 @@ gs_status_t gs_train_step_events(gs_ctx* ctx, const gs_camera* d_cams, const gs_
         launch_project(io->frozen, cfg->n_frozen, cfg->sh_degree, dyn, d_cams, p.vt, V, B, p.proj, s.dkv[0], st,
                        na, n, s.rects);
     mark(ev, 1, st);
+    // two-level binning leaves the per-tile lists in chunk-bitmap form, which
+    // both raster kernels walk
+    CoarseLists cl;
     launch_bin_sort(p.proj, p.vt, V, n, cfg->keys_cap, tt, ctx->binning, ctx->sort_bits, ctx->sort_items, s, true, nullptr,
                     p.vals, p.ranges, p.n_keys, ctx->d_status, ctx->sm_count, st, ev ? mark : nullptr, ev, 2,
-                    cfg->precull != nullptr);
+                    cfg->precull != nullptr, &cl);
     mark(ev, 4, st);
-    launch_render_fwd(p.proj, p.vt, V, n, B, ctx->raster_tpr, p.vals, p.ranges, b, io->image, p.T_final, p.n_contrib, tt, st);
+    launch_render_fwd(p.proj, p.vt, V, n, B, ctx->raster_tpr, p.vals, p.ranges, b, io->image, p.T_final, p.n_contrib, tt,
+                      st, &cl);
     mark(ev, 5, st);
     launch_loss(io->image, io->targets, V, cfg->height, cfg->width, cfg->w_l1, cfg->w_ssim, io->d_loss, p.dimage,
                 p.loss, st);
     mark(ev, 6, st);
     launch_raster_bwd(p.proj, p.vt, V, n, B, ctx->raster_bwd_tpr, p.vals, p.ranges, b, p.T_final, p.n_contrib, p.dimage, p.grad2d, tt,
-                      st, na);
+                      st, na, &cl);
     mark(ev, 7, st);
     launch_project_bwd(io->params, na, cfg->sh_degree, dyn, d_cams, V, p.proj, p.grad2d, io->grads, 0, st, n);
     mark(ev, 8, st);
@@ -578,15 +584,16 @@ gs_status_t gs_autotune(gs_ctx* ctx, const gs_scene* scene, const gs_camera* d_c
     auto run = [&](cudaEvent_t* ev) {
         launch_view_table(d_cams, V, B, p.vt, tt, ctx->d_status, st);
         launch_project(scene->params, n, scene->sh_degree, dyn, d_cams, p.vt, V, B, p.proj, s.dkv[0], st, 0, -1, s.rects);
+        CoarseLists cl;
         launch_bin_sort(p.proj, p.vt, V, n, keys_cap, tt, ctx->binning, ctx->sort_bits, ctx->sort_items, s, true,
                         nullptr, p.vals, p.ranges, p.n_keys, ctx->d_status, ctx->sm_count, st, nullptr, nullptr, 0,
-                        scene->precull != nullptr);
+                        scene->precull != nullptr, &cl);
         if (ev) cudaEventRecord(ev[0], st);
         launch_render_fwd(p.proj, p.vt, V, n, B, ctx->raster_tpr, p.vals, p.ranges, bg, image, p.T_final,
-                          p.n_contrib, tt, st);
+                          p.n_contrib, tt, st, &cl);
         if (ev) cudaEventRecord(ev[1], st);
         launch_raster_bwd(p.proj, p.vt, V, n, B, ctx->raster_bwd_tpr, p.vals, p.ranges, bg, p.T_final, p.n_contrib,
-                          p.dimage, p.grad2d, tt, st);
+                          p.dimage, p.grad2d, tt, st, -1, &cl);
         if (ev) cudaEventRecord(ev[2], st);
     };
     constexpr int kMaxReps = 16;
@@ -609,10 +616,12 @@ gs_status_t gs_autotune(gs_ctx* ctx, const gs_scene* scene, const gs_camera* d_c
     const int bitss[3] = {8, 7, 6};
     const int itemss[3] = {16, 12, 8};
     const int tprs[2] = {4, 2};
-    // per configuration: time outside compositing; per layout: the best
-    // compositing and adjoint times seen
-    float best_pre = -1.f, best_fwd[2] = {-1.f, -1.f}, best_bwd[2] = {-1.f, -1.f};
-    int bb = keep_bin, bbits = keep_bits, bitems = keep_items;
+    // per binning mode (its raster kernels read different list forms): the
+    // sort settings with the least time outside compositing, and per layout
+    // the best compositing and adjoint times seen
+    float best_pre[2] = {-1.f, -1.f}, best_fwd[2][2] = {{-1.f, -1.f}, {-1.f, -1.f}},
+          best_bwd[2][2] = {{-1.f, -1.f}, {-1.f, -1.f}};
+    int bbits[2] = {keep_bits, keep_bits}, bitems[2] = {keep_items, keep_items};
     int32_t count = 0;
     gs_status_t rc = GS_OK;
     for (int ib = 0; ib < 2 && rc == GS_OK; ++ib)
@@ -660,12 +669,12 @@ gs_status_t gs_autotune(gs_ctx* ctx, const gs_scene* scene, const gs_camera* d_c
                     }
                     ++count;
                     const float pre = ms - fwd - bwd;
-                    if (best_pre < 0.f || pre < best_pre) {
-                        best_pre = pre;
-                        bb = bins[ib]; bbits = bitss[ibits]; bitems = itemss[iit];
+                    if (best_pre[ib] < 0.f || pre < best_pre[ib]) {
+                        best_pre[ib] = pre;
+                        bbits[ib] = bitss[ibits]; bitems[ib] = itemss[iit];
                     }
-                    if (best_fwd[itp] < 0.f || fwd < best_fwd[itp]) best_fwd[itp] = fwd;
-                    if (best_bwd[itp] < 0.f || bwd < best_bwd[itp]) best_bwd[itp] = bwd;
+                    if (best_fwd[ib][itp] < 0.f || fwd < best_fwd[ib][itp]) best_fwd[ib][itp] = fwd;
+                    if (best_bwd[ib][itp] < 0.f || bwd < best_bwd[ib][itp]) best_bwd[ib][itp] = bwd;
                 }
     destroy_events();
     if (n_results) *n_results = count < max_results ? count : max_results;
@@ -674,10 +683,15 @@ gs_status_t gs_autotune(gs_ctx* ctx, const gs_scene* scene, const gs_camera* d_c
         ctx->raster_tpr = keep_tpr; ctx->raster_bwd_tpr = keep_btpr;
         return rc;
     }
-    ctx->binning = bb; ctx->sort_bits = bbits; ctx->sort_items = bitems;
     // a layout never timed (8-px tiles) keeps -1 and loses
-    ctx->raster_tpr = (best_fwd[1] >= 0.f && best_fwd[1] < best_fwd[0]) ? tprs[1] : tprs[0];
-    ctx->raster_bwd_tpr = (best_bwd[1] >= 0.f && best_bwd[1] < best_bwd[0]) ? tprs[1] : tprs[0];
+    auto best_of = [](const float (&t)[2]) { return (t[1] >= 0.f && t[1] < t[0]) ? 1 : 0; };
+    float total[2];
+    for (int ib = 0; ib < 2; ++ib)
+        total[ib] = best_pre[ib] + best_fwd[ib][best_of(best_fwd[ib])] + best_bwd[ib][best_of(best_bwd[ib])];
+    const int b = total[1] < total[0] ? 1 : 0;
+    ctx->binning = bins[b]; ctx->sort_bits = bbits[b]; ctx->sort_items = bitems[b];
+    ctx->raster_tpr = tprs[best_of(best_fwd[b])];
+    ctx->raster_bwd_tpr = tprs[best_of(best_bwd[b])];
     return launch_check();
 }
 

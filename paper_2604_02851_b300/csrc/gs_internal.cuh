@@ -186,26 +186,49 @@ constexpr int kBinTwoLevel = 0;
 constexpr int kBinDirect = 1;
 
 // Full bin + sort: depth sort, key emission, tile-key sort, ranges.
+// Per-tile lists in chunk-bitmap form: two-level binning without the
+// expansion into per-tile arrays.  Super-tile s's depth-ordered coarse items
+// citems[cranges[s].x, cranges[s].y) are cut into chunks of kChunkItems
+// (chunk_first[s] .. chunk_first[s + 1], clamped to *d_n_chunks); the 8
+// words bitmap[c][k][0..7] of chunk c and local tile k (8 y + x within the
+// super-tile) mark, bit j of word w, whether item 32 w + j of the chunk is an
+// entry of that tile.  A tile's list is its marked items in chunk order, the
+// order of the expanded list.
+constexpr int kChunkItems = 256;
+struct CoarseLists {
+    const uint64_t* citems = nullptr;  // null: the call produced expanded lists
+    const uint2* cranges = nullptr;
+    const uint32_t* chunk_first = nullptr;
+    const uint32_t* d_n_chunks = nullptr;
+    const uint32_t* bitmap = nullptr;
+};
+
+// coarse: when non-null and the two-level path is taken, the per-tile lists
+// are left in chunk-bitmap form (*coarse filled; sorted_keys, sorted_vals and
+// ranges untouched); otherwise coarse->citems stays null.
 void launch_bin_sort(const float* proj, const ViewInfo* vt, int V, int64_t n, int64_t keys_cap,
                      int64_t total_tiles, int binning, int sort_bits, int sort_items, const SortScratch& s,
                      bool depth_ready,
                      uint32_t* sorted_keys, uint32_t* sorted_vals, uint32_t* ranges,
                      uint32_t* d_num_keys, DevStatus* status, int sm_count, cudaStream_t st,
                      void (*mark)(void* const*, int, cudaStream_t) = nullptr, void* const* events = nullptr,
-                     int first_event = 0, bool compact = false);
+                     int first_event = 0, bool compact = false, CoarseLists* coarse = nullptr);
 
 // tpr: threads per pixel row of a 16 x 16 tile (2 or 4); 8 x 8 tiles use 4.
 // Adjoint: Gaussians with index >= n_active (a frozen pool appended after the
 // active one) get no 2D gradient (n_active < 0: all of them do).
+// coarse: lists in chunk-bitmap form (then vals and ranges are not read, and
+// n_contrib holds citems positions + 1), or null for expanded lists.
 void launch_render_fwd(const float* proj, const ViewInfo* vt, int V, int64_t n, int tile, int tpr,
                        const uint32_t* vals, const uint32_t* ranges, float3 bg, float* image,
                        float* T_final, uint32_t* n_contrib, int64_t total_tiles,
-                       cudaStream_t st);
+                       cudaStream_t st, const CoarseLists* coarse = nullptr);
 
 void launch_raster_bwd(const float* proj, const ViewInfo* vt, int V, int64_t n, int tile, int tpr,
                        const uint32_t* vals, const uint32_t* ranges, float3 bg,
                        const float* T_final, const uint32_t* n_contrib, const float* dimage,
-                       float* grad2d, int64_t total_tiles, cudaStream_t st, int64_t n_active = -1);
+                       float* grad2d, int64_t total_tiles, cudaStream_t st, int64_t n_active = -1,
+                       const CoarseLists* coarse = nullptr);
 
 size_t loss_scratch_bytes(int V, int H, int W);
 void launch_loss(const float* image, const float* target, int V, int H, int W, float w_l1,

@@ -99,10 +99,73 @@ __device__ __forceinline__ bool reaches_tile(float4 a, float4 q, float x0, float
 template <int B, int TPR>
 constexpr int fwd_min_blocks() { return B * TPR == 32 ? 24 : 1024 / (B * TPR); }
 
-template <int B, int TPR>
+// Tile gt's place in the chunk-bitmap lists: its super-tile s, its local
+// index k (8 y + x) there, the super-tile's chunks [c0, c1) and first item.
+struct TileChunks {
+    uint32_t c0, c1, k, item0;
+};
+
+__device__ __forceinline__ TileChunks tile_chunks(const CoarseLists& cl, const ViewInfo& vi, int lt) {
+    const int tx = lt % vi.tx, ty = lt / vi.tx;
+    const int64_t sidx = vi.stile_off + (int64_t)(ty >> kSuperShift) * vi.stx + (tx >> kSuperShift);
+    TileChunks t;
+    const uint32_t nch = *cl.d_n_chunks;
+    t.c0 = min(cl.chunk_first[sidx], nch);
+    t.c1 = min(cl.chunk_first[sidx + 1], nch);
+    t.k = (uint32_t)(((ty & (kSuper - 1)) << kSuperShift) | (tx & (kSuper - 1)));
+    t.item0 = cl.cranges[sidx].x;
+    return t;
+}
+
+// The marked items of chunk c for this tile, in list order, into s_cand
+// (positions: indices into citems); returns their count.  NT threads, each
+// owning 256 / NT consecutive bits of the chunk's 256-bit mask `word`
+// (this thread's 32-bit word of it); positions at or past `limit` are
+// dropped.  Ends with a barrier.
+template <int NT>
+__device__ __forceinline__ int chunk_candidates(uint32_t word, uint32_t item_base, uint32_t limit,
+                                                uint32_t* s_cand, int* s_ctot) {
+    constexpr int BPT = kChunkItems / NT;
+    static_assert(BPT == 4 || BPT == 8, "4 or 8 bits a thread");
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t my = (word >> ((threadIdx.x * BPT) & 31)) & ((1u << BPT) - 1u);
+    const uint32_t a = item_base + threadIdx.x * BPT;
+    if (a >= limit) my = 0u;
+    else if (limit - a < (uint32_t)BPT) my &= (1u << (limit - a)) - 1u;
+    const uint32_t pc = __popc(my);
+    uint32_t incl = pc;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    int total;
+    uint32_t off = incl - pc;
+    if (NT > 32) {
+        if (lane == 31) s_ctot[warp] = (int)incl;
+        __syncthreads();
+        total = 0;
+#pragma unroll
+        for (int w = 0; w < NT / 32; ++w) {
+            if (w < warp) off += (uint32_t)s_ctot[w];
+            total += s_ctot[w];
+        }
+    } else {
+        total = (int)__shfl_sync(0xFFFFFFFFu, incl, 31);
+    }
+    while (my) {
+        const int b = __ffs(my) - 1;
+        my &= my - 1u;
+        s_cand[off++] = a + (uint32_t)b;
+    }
+    __syncthreads();
+    return total;
+}
+
+template <int B, int TPR, bool COARSE>
 __global__ void __launch_bounds__(B * TPR, fwd_min_blocks<B, TPR>())
 k_render_fwd(const float4* __restrict__ proj, const ViewInfo* __restrict__ vt, int V, int64_t n,
-             const uint32_t* __restrict__ vals, const uint2* __restrict__ ranges, float3 bg,
+             const uint32_t* __restrict__ vals, const uint2* __restrict__ ranges, CoarseLists cl, float3 bg,
              float* __restrict__ image, float* __restrict__ T_final, uint32_t* __restrict__ n_contrib) {
     constexpr int NT = B * TPR;        // threads per block
     constexpr int PX = B / TPR;        // pixels per thread
@@ -127,8 +190,9 @@ k_render_fwd(const float4* __restrict__ proj, const ViewInfo* __restrict__ vt, i
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const float fy = (float)py + 0.5f;
     const float fx0 = (float)px0 + 0.5f;
-    const uint2 rg = ranges[gt];
     const int64_t rbase = (int64_t)v * n;
+    __shared__ uint32_t s_cand[COARSE ? kChunkItems : 1];
+    __shared__ int s_ctot[NW];
 
     // pixel pairs (2p, 2p + 1) in packed float2 registers.  pen is added to
     // a pixel's exponent: 0 while it composites, -inf once it has stopped (or
@@ -148,17 +212,22 @@ k_render_fwd(const float4* __restrict__ proj, const ViewInfo* __restrict__ vt, i
     }
 #pragma unroll
     for (int k = 0; k < PX; ++k) last[k] = 0;
-    for (uint32_t start = rg.x; start < rg.y; start += BATCH) {
-        if (__syncthreads_count(nlive != 0) == 0) break;
+    // One round: list items [0, nslot) of a window, item(i, pos, g) giving
+    // item i's list position and Gaussian.  The fragments that reach the
+    // tile are staged in list order, then composited.
+    auto round = [&](int nslot, auto item) {
         // stage the fragments of this round that reach the tile, in list order
         float4 ra[2], rq[2], rc[2];
         bool keep[2];
+        uint32_t ipos[2];
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-            const uint32_t idx = start + threadIdx.x + h * NT;
+            const int slot = (int)threadIdx.x + h * NT;
             keep[h] = false;
-            if (idx < rg.y) {
-                const int64_t r = (rbase + vals[idx]) * 4;
+            if (slot < nslot) {
+                uint32_t g;
+                item(slot, ipos[h], g);
+                const int64_t r = (rbase + g) * 4;
                 const float4 a = proj[r], b = proj[r + 1];
                 rc[h] = proj[r + 2];
                 ra[h] = make_float4(a.x, a.y, a.w, cutoff_log2(a.w));
@@ -179,11 +248,11 @@ k_render_fwd(const float4* __restrict__ proj, const ViewInfo* __restrict__ vt, i
         const uint32_t ltm = (1u << lane) - 1u;
         if (keep[0]) {
             const int d = off0 + __popc(m0 & ltm);
-            s_a[d] = ra[0]; s_q[d] = rq[0]; s_c[d] = rc[0]; s_pos[d] = start + threadIdx.x - rg.x;
+            s_a[d] = ra[0]; s_q[d] = rq[0]; s_c[d] = rc[0]; s_pos[d] = ipos[0];
         }
         if (keep[1]) {
             const int d = off1 + __popc(m1 & ltm);
-            s_a[d] = ra[1]; s_q[d] = rq[1]; s_c[d] = rc[1]; s_pos[d] = start + threadIdx.x + NT - rg.x;
+            s_a[d] = ra[1]; s_q[d] = rq[1]; s_c[d] = rc[1]; s_pos[d] = ipos[1];
         }
         __syncthreads();
         for (int j = 0; j < cnt && nlive; ++j) {
@@ -224,6 +293,39 @@ k_render_fwd(const float4* __restrict__ proj, const ViewInfo* __restrict__ vt, i
                 if (v0) last[k0] = pos1;
                 if (v1) last[k1] = pos1;
             }
+        }
+    };
+    if (!COARSE) {
+        const uint2 rg = ranges[gt];
+        for (uint32_t start = rg.x; start < rg.y; start += BATCH) {
+            if (__syncthreads_count(nlive != 0) == 0) break;
+            round((int)min((uint32_t)BATCH, rg.y - start), [&](int i, uint32_t& pos, uint32_t& g) {
+                pos = start + (uint32_t)i - rg.x;
+                g = vals[start + (uint32_t)i];
+            });
+        }
+    } else {
+        // chunk by chunk: this thread's bitmap word of the next chunk is
+        // requested while the current one is composited
+        const TileChunks tc = tile_chunks(cl, vi, lt);
+        const uint32_t wsel = (threadIdx.x * (kChunkItems / NT)) >> 5;
+        const uint32_t* bm = cl.bitmap + (size_t)tc.k * 8 + wsel;
+        uint32_t wnext = tc.c0 < tc.c1 ? bm[(size_t)tc.c0 * 512] : 0u;
+        for (uint32_t c = tc.c0; c < tc.c1; ++c) {
+            if (__syncthreads_count(nlive != 0) == 0) break;
+            const uint32_t word = wnext;
+            if (c + 1 < tc.c1) wnext = bm[(size_t)(c + 1) * 512];
+            const int cnt = chunk_candidates<NT>(word, tc.item0 + (c - tc.c0) * kChunkItems, 0xFFFFFFFFu, s_cand,
+                                                 s_ctot);
+            bool stop = false;
+            for (int w0 = 0; w0 < cnt; w0 += BATCH) {
+                if (w0 > 0 && __syncthreads_count(nlive != 0) == 0) { stop = true; break; }
+                round(min(BATCH, cnt - w0), [&](int i, uint32_t& pos, uint32_t& g) {
+                    pos = s_cand[w0 + i];
+                    g = (uint32_t)cl.citems[pos];
+                });
+            }
+            if (stop) break;
         }
     }
     const int64_t HW = (int64_t)vi.width * vi.height;
@@ -296,10 +398,10 @@ __device__ __forceinline__ float rcp_approx(float x) {
 template <int B, int TPR>
 constexpr int bwd_min_blocks() { return B * TPR == 32 ? 24 : 1024 / (B * TPR); }
 
-template <int B, int TPR>
+template <int B, int TPR, bool COARSE>
 __global__ void __launch_bounds__(B * TPR, bwd_min_blocks<B, TPR>())
 k_raster_bwd(const float4* __restrict__ proj, const ViewInfo* __restrict__ vt, int V, int64_t n,
-             const uint32_t* __restrict__ vals, const uint2* __restrict__ ranges, float3 bg,
+             const uint32_t* __restrict__ vals, const uint2* __restrict__ ranges, CoarseLists cl, float3 bg,
              const float* __restrict__ T_final, const uint32_t* __restrict__ n_contrib,
              const float* __restrict__ dimage, float* __restrict__ grad2d, int64_t n_active) {
     constexpr int NT = B * TPR;
@@ -316,6 +418,8 @@ k_raster_bwd(const float4* __restrict__ proj, const ViewInfo* __restrict__ vt, i
     __shared__ float s_acc[9][BATCH + 1];  // raw sums per fragment, padded: the 9 sit in different banks
     __shared__ uint32_t s_max;
     __shared__ int s_wcnt[NT / 32];
+    __shared__ uint32_t s_cand[COARSE ? kChunkItems : 1];
+    __shared__ int s_ctot[NT / 32];
     const int64_t gt = blockIdx.x;
     if (gt >= vt[V].tile_off) return;
     const int v = find_view(vt, V, gt);
@@ -327,7 +431,6 @@ k_raster_bwd(const float4* __restrict__ proj, const ViewInfo* __restrict__ vt, i
     const float fy = (float)py + 0.5f;
     const float fx0 = (float)px0 + 0.5f;
     const float tx0 = (float)((lt % vi.tx) * B) + 0.5f, ty0 = (float)((lt / vi.tx) * B) + 0.5f;
-    const uint2 rg = ranges[gt];
     const int64_t rbase = (int64_t)v * n;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
@@ -366,16 +469,16 @@ k_raster_bwd(const float4* __restrict__ proj, const ViewInfo* __restrict__ vt, i
     __syncthreads();
     const uint32_t maxl = s_max;
 
-    for (int64_t bend = maxl; bend > 0; bend -= BATCH) {
-        const uint32_t bstart = bend > BATCH ? (uint32_t)(bend - BATCH) : 0u;
-        const int nslot = (int)(bend - bstart);
+    // One round: list items [0, nslot) of a window (item(i, pos, g): list
+    // position and Gaussian), staged in list order and walked back to front.
+    auto round = [&](int nslot, auto item) {
         __syncthreads();  // the previous batch's flush is complete
         // stage the fragments of this round that reach the tile, in list order
         bool keep = false;
-        uint32_t g = 0;
+        uint32_t g = 0, ipos = 0;
         float4 a, b, c, aq, qq;
         if ((int)threadIdx.x < nslot) {
-            g = vals[rg.x + bstart + threadIdx.x];
+            item((int)threadIdx.x, ipos, g);
             const int64_t r = (rbase + g) * 4;
             a = proj[r]; b = proj[r + 1]; c = proj[r + 2];
             aq = make_float4(a.x, a.y, a.w, cutoff_log2(a.w));
@@ -401,7 +504,7 @@ k_raster_bwd(const float4* __restrict__ proj, const ViewInfo* __restrict__ vt, i
             s_b[d] = b;
             s_c[d] = c;
             s_g[d] = g;
-            s_pos[d] = bstart + threadIdx.x;
+            s_pos[d] = ipos;
 #pragma unroll
             for (int q = 0; q < 9; ++q) s_acc[q][d] = 0.f;
         }
@@ -495,6 +598,42 @@ k_raster_bwd(const float4* __restrict__ proj, const ViewInfo* __restrict__ vt, i
                 atomicAdd(reinterpret_cast<float4*>(dst + 4), Bv);
             if (Cv != 0.f) atomicAdd(dst + 8, Cv);
         }
+    };
+    if (!COARSE) {
+        const uint2 rg = ranges[gt];
+        for (int64_t bend = maxl; bend > 0; bend -= BATCH) {
+            const uint32_t bstart = bend > BATCH ? (uint32_t)(bend - BATCH) : 0u;
+            round((int)(bend - bstart), [&](int i, uint32_t& pos, uint32_t& g) {
+                pos = bstart + (uint32_t)i;
+                g = vals[rg.x + bstart + (uint32_t)i];
+            });
+        }
+    } else if (maxl > 0) {
+        // chunks back to front from the one holding position maxl - 1 (the
+        // last contributor of any pixel); the previous chunk's bitmap word is
+        // requested while the current one is processed
+        const TileChunks tc = tile_chunks(cl, vi, lt);
+        const uint32_t wsel = (threadIdx.x * (kChunkItems / NT)) >> 5;
+        const uint32_t* bm = cl.bitmap + (size_t)tc.k * 8 + wsel;
+        if (tc.c1 > tc.c0 && maxl - 1 >= tc.item0) {
+            uint32_t chi = tc.c0 + (maxl - 1 - tc.item0) / kChunkItems;
+            if (chi > tc.c1 - 1) chi = tc.c1 - 1;
+            uint32_t wprev = bm[(size_t)chi * 512];
+            for (int64_t c = chi; c >= (int64_t)tc.c0; --c) {
+                const uint32_t word = wprev;
+                if (c > (int64_t)tc.c0) wprev = bm[(size_t)(c - 1) * 512];
+                __syncthreads();  // s_cand of the previous chunk is no longer read
+                const int cnt = chunk_candidates<NT>(word, tc.item0 + ((uint32_t)c - tc.c0) * kChunkItems, maxl,
+                                                     s_cand, s_ctot);
+                for (int wend = cnt; wend > 0; wend -= BATCH) {
+                    const int wstart = wend > BATCH ? wend - BATCH : 0;
+                    round(wend - wstart, [&](int i, uint32_t& pos, uint32_t& g) {
+                        pos = s_cand[wstart + i];
+                        g = (uint32_t)cl.citems[pos];
+                    });
+                }
+            }
+        }
     }
 }
 
@@ -502,35 +641,50 @@ k_raster_bwd(const float4* __restrict__ proj, const ViewInfo* __restrict__ vt, i
 
 void launch_render_fwd(const float* proj, const ViewInfo* vt, int V, int64_t n, int tile, int tpr,
                        const uint32_t* vals, const uint32_t* ranges, float3 bg, float* image,
-                       float* T_final, uint32_t* n_contrib, int64_t total_tiles, cudaStream_t st) {
+                       float* T_final, uint32_t* n_contrib, int64_t total_tiles, cudaStream_t st,
+                       const CoarseLists* coarse) {
     if (total_tiles <= 0) return;
     const float4* p = reinterpret_cast<const float4*>(proj);
     const uint2* r = reinterpret_cast<const uint2*>(ranges);
     const unsigned nb = (unsigned)total_tiles;
+    const CoarseLists cl = coarse ? *coarse : CoarseLists{};
+#define GS_FWD(BB, TT, NTH)                                                                                        \
+    (cl.citems ? k_render_fwd<BB, TT, true><<<nb, NTH, 0, st>>>(p, vt, V, n, vals, r, cl, bg, image, T_final,      \
+                                                                n_contrib)                                         \
+               : k_render_fwd<BB, TT, false><<<nb, NTH, 0, st>>>(p, vt, V, n, vals, r, cl, bg, image, T_final,     \
+                                                                 n_contrib))
     if (tile == 8)
-        k_render_fwd<8, 4><<<nb, 32, 0, st>>>(p, vt, V, n, vals, r, bg, image, T_final, n_contrib);
+        GS_FWD(8, 4, 32);
     else if (tpr == 2)
-        k_render_fwd<16, 2><<<nb, 32, 0, st>>>(p, vt, V, n, vals, r, bg, image, T_final, n_contrib);
+        GS_FWD(16, 2, 32);
     else
-        k_render_fwd<16, 4><<<nb, 64, 0, st>>>(p, vt, V, n, vals, r, bg, image, T_final, n_contrib);
+        GS_FWD(16, 4, 64);
+#undef GS_FWD
 }
 
 void launch_raster_bwd(const float* proj, const ViewInfo* vt, int V, int64_t n, int tile, int tpr,
                        const uint32_t* vals, const uint32_t* ranges, float3 bg, const float* T_final,
                        const uint32_t* n_contrib, const float* dimage, float* grad2d,
-                       int64_t total_tiles, cudaStream_t st, int64_t n_active) {
+                       int64_t total_tiles, cudaStream_t st, int64_t n_active, const CoarseLists* coarse) {
     if (n_active < 0) n_active = n;
     cudaMemsetAsync(grad2d, 0, sizeof(float) * kGradStride * (size_t)V * (size_t)n, st);
     if (total_tiles <= 0) return;
     const float4* p = reinterpret_cast<const float4*>(proj);
     const uint2* r = reinterpret_cast<const uint2*>(ranges);
     const unsigned nb = (unsigned)total_tiles;
+    const CoarseLists cl = coarse ? *coarse : CoarseLists{};
+#define GS_BWD(BB, TT, NTH)                                                                                        \
+    (cl.citems ? k_raster_bwd<BB, TT, true><<<nb, NTH, 0, st>>>(p, vt, V, n, vals, r, cl, bg, T_final, n_contrib,  \
+                                                                dimage, grad2d, n_active)                          \
+               : k_raster_bwd<BB, TT, false><<<nb, NTH, 0, st>>>(p, vt, V, n, vals, r, cl, bg, T_final, n_contrib, \
+                                                                 dimage, grad2d, n_active))
     if (tile == 8)
-        k_raster_bwd<8, 4><<<nb, 32, 0, st>>>(p, vt, V, n, vals, r, bg, T_final, n_contrib, dimage, grad2d, n_active);
+        GS_BWD(8, 4, 32);
     else if (tpr == 2)
-        k_raster_bwd<16, 2><<<nb, 32, 0, st>>>(p, vt, V, n, vals, r, bg, T_final, n_contrib, dimage, grad2d, n_active);
+        GS_BWD(16, 2, 32);
     else
-        k_raster_bwd<16, 4><<<nb, 64, 0, st>>>(p, vt, V, n, vals, r, bg, T_final, n_contrib, dimage, grad2d, n_active);
+        GS_BWD(16, 4, 64);
+#undef GS_BWD
 }
 
 }  // namespace gs

@@ -598,7 +598,7 @@ k_emit(const uint64_t* __restrict__ dsorted, int64_t total, int64_t n, const uin
 // writes each chunk's entries at its offsets, in chunk order and, within a
 // chunk, in list order -- the stable (tile, depth, index) order.
 constexpr int kFineThreads = 256;
-constexpr int kFineChunk = 256;
+constexpr int kFineChunk = kChunkItems;
 
 // Fine total from the rectangles: number of stored entries, capacity check.
 __global__ void k_fine_total(const unsigned long long* fine_total, int64_t cap, uint32_t* d_num_keys,
@@ -622,7 +622,7 @@ __device__ __forceinline__ int find_super_view(const ViewInfo* __restrict__ vt, 
 __global__ void __launch_bounds__(1024)
 k_fine_chunks(const uint2* __restrict__ cranges, const ViewInfo* __restrict__ vt, int V, int64_t ns_bound,
               uint32_t* __restrict__ chunk_first, uint32_t* __restrict__ chunk_s, uint32_t* d_n_chunks,
-              int64_t max_chunks) {
+              int64_t max_chunks, DevStatus* status) {
     __shared__ uint32_t s_part[1024];
     const int64_t ns = vt[V].stile_off < ns_bound ? vt[V].stile_off : ns_bound;
     const int64_t per = (ns + blockDim.x - 1) / blockDim.x;
@@ -654,6 +654,9 @@ k_fine_chunks(const uint2* __restrict__ cranges, const ViewInfo* __restrict__ vt
         chunk_first[ns] = s_part[threadIdx.x];
         const uint32_t tot = s_part[threadIdx.x];
         *d_n_chunks = (int64_t)tot < max_chunks ? tot : (uint32_t)max_chunks;
+        // more chunks than their tables hold: the caller's key capacity
+        // (keys_cap / 256 chunks) is too small for them
+        if ((int64_t)tot > max_chunks) record_status(status, GS_ERR_CAPACITY, (long long)tot * kFineChunk);
     }
 }
 
@@ -751,6 +754,34 @@ k_fine_count(const uint64_t* __restrict__ citems, const uint2* __restrict__ cran
         }
         chunk_off[(size_t)c * 64 + lane] = n0;
         chunk_off[(size_t)c * 64 + 32 + lane] = n1;
+    }
+}
+
+// Bitmap pass, one warp per chunk: the transposed column words of the
+// chunk's groups, stored as bitmap[c][k][group] (two 32-byte rows a lane).
+__global__ void __launch_bounds__(kFineThreads)
+k_fine_mask(const uint64_t* __restrict__ citems, const uint2* __restrict__ cranges,
+            const uint32_t* __restrict__ chunk_first, const uint32_t* __restrict__ chunk_s,
+            const uint32_t* __restrict__ d_n_chunks, const ViewInfo* __restrict__ vt, int V,
+            int64_t total_tiles, uint32_t* __restrict__ bitmap) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t nchunks = *d_n_chunks;
+    const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < nchunks; c += nw) {
+        const FineChunk f = fine_chunk(c, cranges, chunk_first, chunk_s, vt, V, total_tiles, lane);
+        uint32_t w0[8], w1[8];
+#pragma unroll
+        for (int grp = 0; grp < 8; ++grp) {
+            uint32_t gval = 0, c0 = 0, c1 = 0;
+            if (f.a + (uint32_t)grp * 32u < f.e) fine_group(f, (uint32_t)grp, citems, lane, gval, c0, c1);
+            w0[grp] = c0;
+            w1[grp] = c1;
+        }
+        uint4* out = reinterpret_cast<uint4*>(bitmap) + (size_t)c * 128;
+        out[2 * lane] = make_uint4(w0[0], w0[1], w0[2], w0[3]);
+        out[2 * lane + 1] = make_uint4(w0[4], w0[5], w0[6], w0[7]);
+        out[64 + 2 * lane] = make_uint4(w1[0], w1[1], w1[2], w1[3]);
+        out[64 + 2 * lane + 1] = make_uint4(w1[4], w1[5], w1[6], w1[7]);
     }
 }
 
@@ -977,7 +1008,8 @@ void emit_two_level(const uint64_t* dsorted, int64_t items, const uint32_t* d_it
                     int64_t keys_cap, const SortScratch& s, uint32_t* sorted_keys,
                     uint32_t* sorted_vals, uint32_t* ranges, int64_t total_tiles, uint32_t* d_num_keys,
                     DevStatus* status, int sm_count, cudaStream_t st,
-                    void (*mark)(void* const*, int, cudaStream_t), void* const* events, int ev) {
+                    void (*mark)(void* const*, int, cudaStream_t), void* const* events, int ev,
+                    CoarseLists* coarse) {
     // the host knows the tile count only: super-tiles never outnumber tiles,
     // so it bounds their count (the kernels read the exact one from vt[V])
     const int64_t n_super = total_tiles;
@@ -1004,10 +1036,26 @@ void emit_two_level(const uint64_t* dsorted, int64_t items, const uint32_t* d_it
                                  reinterpret_cast<uint32_t*>(s.cranges), status, sm_count, st,
                                  (uint32_t)((1ull << bits) - 1ull));
     k_ranges_fix<<<sm_count, 256, 0, st>>>(s.cranges, n_super);
+    const unsigned fgrid = (unsigned)(sm_count * 8);
+    if (coarse) {
+        // chunk-bitmap lists: the bitmaps go to the ping-pong buffer the last
+        // pass read (keys_cap 8-byte items: room for keys_cap / 256 chunks)
+        uint32_t* bitmap = reinterpret_cast<uint32_t*>(buf[1 - passes % 2]);
+        const int64_t bm_chunks = keys_cap / kFineChunk;
+        k_fine_chunks<<<1, 1024, 0, st>>>(s.cranges, vt, V, n_super, s.chunk_first, s.chunk_s, s.d_n_chunks,
+                                          std::min<int64_t>(s.max_chunks, bm_chunks), status);
+        k_fine_mask<<<fgrid, kFineThreads, 0, st>>>(citems, s.cranges, s.chunk_first, s.chunk_s, s.d_n_chunks, vt,
+                                                    V, total_tiles, bitmap);
+        coarse->citems = citems;
+        coarse->cranges = s.cranges;
+        coarse->chunk_first = s.chunk_first;
+        coarse->d_n_chunks = s.d_n_chunks;
+        coarse->bitmap = bitmap;
+        return;
+    }
     // fine expansion
     k_fine_chunks<<<1, 1024, 0, st>>>(s.cranges, vt, V, n_super, s.chunk_first, s.chunk_s, s.d_n_chunks,
-                                      s.max_chunks);
-    const unsigned fgrid = (unsigned)(sm_count * 8);
+                                      s.max_chunks, status);
     k_fine_count<<<fgrid, kFineThreads, 0, st>>>(citems, s.cranges, s.chunk_first, s.chunk_s, s.d_n_chunks, vt, V,
                                                  total_tiles, s.chunk_off);
     k_fine_prefix<<<(unsigned)((n_super * 64 + 255) / 256), 256, 0, st>>>(s.chunk_first, s.d_n_chunks, vt, V,
@@ -1068,7 +1116,8 @@ void launch_bin_sort(const float* proj, const ViewInfo* vt, int V, int64_t n, in
                      uint32_t* sorted_keys, uint32_t* sorted_vals, uint32_t* ranges,
                      uint32_t* d_num_keys, DevStatus* status, int sm_count, cudaStream_t st,
                      void (*mark)(void* const*, int, cudaStream_t), void* const* events, int first_event,
-                     bool compact) {
+                     bool compact, CoarseLists* coarse) {
+    if (coarse) *coarse = CoarseLists{};
     const int64_t items = (int64_t)V * n;
     const uint4* pr = reinterpret_cast<const uint4*>(proj);
     if (items == 0) {
@@ -1118,7 +1167,8 @@ void launch_bin_sort(const float* proj, const ViewInfo* vt, int V, int64_t n, in
         else                                                                                                    \
             emit_two_level<B, I>(dsorted, items, d_items, n, pr, vt, V, keys_cap, s, sorted_keys, sorted_vals,  \
                                  ranges,                                                                        \
-                                 total_tiles, d_num_keys, status, sm_count, st, mark, events, first_event + 1); \
+                                 total_tiles, d_num_keys, status, sm_count, st, mark, events, first_event + 1,  \
+                                 coarse);                                                                       \
     } while (0)
     const int it = sort_items == 8 ? 8 : (sort_items == 16 ? 16 : 12);
     switch (sort_bits * 100 + it) {

@@ -135,9 +135,10 @@ def test_render_after_overflow_reads_stored_entries_only(mode):
 
 def test_autotune_times_every_configuration_and_keeps_results_exact():
     """gs_autotune tries 2 binnings x 3 digit widths x 3 item counts x 2 raster
-    layouts, leaves the context on the fastest binning/sort (time outside
-    compositing) and the fastest compositing and adjoint layouts, and the sort
-    it then produces is still the oracle's."""
+    layouts.  Per binning (whose raster kernels read different list forms) it
+    takes the sort settings with the least time outside compositing and the
+    fastest compositing and adjoint layouts; it keeps the binning whose sum of
+    the three is smaller.  The sort it then produces is still the oracle's."""
     import torch
     import paper_2604_02851_b300 as gs
     n, sh = 30_000, 1
@@ -153,15 +154,22 @@ def test_autotune_times_every_configuration_and_keeps_results_exact():
         (b, bits, it, t) for b in ("two_level", "direct") for bits in (8, 7, 6) for it in (16, 12, 8) for t in (4, 2)}
     assert all(e["ms"] > 0 and 0 < e["ms_render_fwd"] and 0 < e["ms_render_bwd"] for e in entries)
     assert all(e["ms_render_fwd"] + e["ms_render_bwd"] < e["ms"] for e in entries)
-    pre = {(e["binning"], e["sort_bits"], e["sort_items"]): [] for e in entries}
-    for e in entries:
-        pre[(e["binning"], e["sort_bits"], e["sort_items"])].append(e["ms"] - e["ms_render_fwd"] - e["ms_render_bwd"])
-    low = min(min(v) for v in pre.values())
-    assert min(pre[(best["binning"], best["sort_bits"], best["sort_items"])]) <= low * (1 + 1e-5) + 1e-6
-    fwd = {t: min(e["ms_render_fwd"] for e in entries if e["raster_threads"] == t) for t in (4, 2)}
-    bwd = {t: min(e["ms_render_bwd"] for e in entries if e["raster_threads"] == t) for t in (4, 2)}
-    assert fwd[best["raster_threads"]] <= min(fwd.values()) * (1 + 1e-5)
-    assert bwd[best["raster_bwd_threads"]] <= min(bwd.values()) * (1 + 1e-5)
+    def pre(e):
+        return e["ms"] - e["ms_render_fwd"] - e["ms_render_bwd"]
+
+    total = {}
+    for b in ("two_level", "direct"):
+        es = [e for e in entries if e["binning"] == b]
+        fwd = {t: min(e["ms_render_fwd"] for e in es if e["raster_threads"] == t) for t in (4, 2)}
+        bwd = {t: min(e["ms_render_bwd"] for e in es if e["raster_threads"] == t) for t in (4, 2)}
+        total[b] = min(pre(e) for e in es) + min(fwd.values()) + min(bwd.values())
+        if b == best["binning"]:
+            low = min(pre(e) for e in es)
+            chosen = [pre(e) for e in es if (e["sort_bits"], e["sort_items"]) == (best["sort_bits"], best["sort_items"])]
+            assert min(chosen) <= low * (1 + 1e-5) + 1e-6
+            assert fwd[best["raster_threads"]] <= min(fwd.values()) * (1 + 1e-5)
+            assert bwd[best["raster_bwd_threads"]] <= min(bwd.values()) * (1 + 1e-5)
+    assert total[best["binning"]] <= min(total.values()) * (1 + 1e-5) + 1e-6
     assert ctx.status()[0] == 0
     d_cams = gs.cameras_to_device(cams)
     tt = ctx.total_tiles(cams)

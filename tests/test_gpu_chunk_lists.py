@@ -1,0 +1,99 @@
+"""Per-tile lists in chunk-bitmap form against the expanded lists.
+
+With two-level binning, gs_train_step and gs_render_batch do not expand the
+super-tile lists into per-tile arrays: both raster kernels walk each tile's
+entries through the bitmaps of its super-tile's 256-item chunks (forward in
+list order, the adjoint back to front from the chunk of the last
+contributor).  With direct binning they read the expanded lists.  Both forms
+visit the same fragments in the same order, so the first step's rendered
+image and loss are bit-identical; the gradients differ only in the order of
+the float atomics, and so do the parameters (and the next step's image) by
+rounding.  Cases: one super-tile holding many chunks, ragged image edges, big
+splats spanning many super-tiles, both raster layouts, 8-pixel tiles, and an
+opaque scene whose pixels stop early.
+"""
+import numpy as np
+import pytest
+
+import gs_inputs as gi
+import oracle as O
+from gpu_util import cams32, rel_l2, scene
+
+pytestmark = pytest.mark.gpu
+
+CASES = {
+    # name: (n, sh, views, width, height, log-scale shift, logit shift, tile, fwd layout, bwd layout)
+    "one_supertile_chunks": (60_000, 1, 1, 128, 128, 0.5, 0.0, 16, 4, 2),
+    "ragged_edges": (20_000, 2, 3, 200, 136, 0.0, 0.0, 16, 2, 4),
+    "big_splats": (3_000, 0, 2, 333, 250, 1.5, 0.0, 16, 4, 4),
+    "opaque_early_stop": (30_000, 1, 2, 176, 112, 0.8, 4.0, 16, 4, 2),
+    "tile8": (8_000, 0, 2, 150, 90, 0.5, 0.0, 8, 4, 4),
+}
+
+
+def _trainer(mode, planes, sh, cams, target, tile, tpr, btpr):
+    import torch
+    import paper_2604_02851_b300 as gs
+    from paper_2604_02851_b300.train import OnlineTrainer, estimate_keys
+    ctx = gs.Context(0, 0, tile=tile, binning=mode, raster_threads=tpr, raster_bwd_threads=btpr)
+    params = torch.from_numpy(np.ascontiguousarray(planes)).cuda()
+    cap = estimate_keys(ctx, params, sh, cams, slack=1.5)
+    tr = OnlineTrainer(params, sh, cams, cap, ctx=ctx)
+    tr.targets.copy_(target)
+    return tr
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_train_step_chunk_lists_match_expanded_lists(name):
+    import torch
+    n, sh, V, W, H, sshift, lshift, tile, tpr, btpr = CASES[name]
+    planes = scene(n, sh, 21, sshift)
+    planes[0, :, 3] += lshift
+    cams = gi.ring_cameras(V, W, H)
+    tgt = O.forward(scene(n, sh, 22, sshift), sh, cams32(cams))["image"].astype(np.float32)
+    target = torch.from_numpy(np.ascontiguousarray(tgt.reshape(-1))).cuda()
+    a = _trainer("two_level", planes, sh, cams, target, tile, tpr, btpr)
+    b = _trainer("direct", planes, sh, cams, target, tile, tpr, btpr)
+    for step in (1, 2):
+        a.step()
+        b.step()
+        torch.cuda.synchronize()
+        assert a.ctx.status()[0] == 0 and b.ctx.status()[0] == 0
+        if step == 1:  # same parameters: same image and loss, bit for bit
+            np.testing.assert_array_equal(a.image.cpu().numpy(), b.image.cpu().numpy())
+            assert a.loss() == b.loss()
+        else:
+            assert rel_l2(a.image.cpu().numpy(), b.image.cpu().numpy()) <= 1e-6
+            assert abs(a.loss() - b.loss()) <= 1e-6 * b.loss()
+        assert rel_l2(a.grads.cpu().numpy(), b.grads.cpu().numpy()) <= 1e-5
+        upd = np.linalg.norm(b.params.cpu().numpy() - planes)
+        assert np.linalg.norm(a.params.cpu().numpy() - b.params.cpu().numpy()) <= 1e-3 * upd
+    if name == "one_supertile_chunks":
+        # the super-tile's list spans many 256-item chunks
+        K = int(np.count_nonzero(O.project(planes, sh, cams32(cams))[..., 14] > 0))
+        assert K > 20 * 256
+    a.ctx.close()
+    b.ctx.close()
+
+
+@pytest.mark.parametrize("name", ["one_supertile_chunks", "ragged_edges", "opaque_early_stop", "tile8"])
+def test_render_batch_chunk_lists_match_expanded_lists(name):
+    import torch
+    import paper_2604_02851_b300 as gs
+    n, sh, V, W, H, sshift, lshift, tile, tpr, _ = CASES[name]
+    planes = scene(n, sh, 23, sshift)
+    planes[0, :, 3] += lshift
+    cams = gi.ring_cameras(V, W, H)
+    params = torch.from_numpy(np.ascontiguousarray(planes)).cuda()
+    imgs = []
+    for mode in ("two_level", "direct"):
+        ctx = gs.Context(0, 0, tile=tile, binning=mode, raster_threads=tpr)
+        cap = 1 << 22
+        ctx.reserve(ctx.workspace_size(cams, n, cap))
+        d_cams = gs.cameras_to_device(cams)
+        img = gs.gs_render_batch(ctx, params, sh, d_cams, V, ctx.total_tiles(cams), cap, gs.total_pixels(cams))
+        torch.cuda.synchronize()
+        assert ctx.status()[0] == 0
+        imgs.append(img.cpu().numpy())
+        ctx.close()
+    np.testing.assert_array_equal(imgs[0], imgs[1])
