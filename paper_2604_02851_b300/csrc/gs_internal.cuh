@@ -34,7 +34,22 @@ struct ViewInfo {
     int64_t pix_off;      // first pixel (per channel) of this view
     int32_t stx, sty;     // super-tiles along x / y
     int64_t stile_off;    // first global super-tile index of this view
+    int32_t rect32;       // totals entry vt[V] only: 1 when every view has at most 256 tiles
+                          // along x and y, so the tile rectangles take their 4-byte form
+    int32_t pad;
 };
+
+// Tile rectangle [x0, x1) x [y0, y1) in 4 bytes (x0, x1 - 1, y0, y1 - 1, a
+// byte each; the empty rectangle is x0 = 1, x1 = 1, y0 = 0, y1 = 1).
+__device__ __forceinline__ uint32_t rect32_pack(uint32_t lo, uint32_t hi) {
+    const uint32_t x0 = lo & 0xFFFFu, y0 = lo >> 16, x1 = hi & 0xFFFFu, y1 = hi >> 16;
+    if (x1 <= x0 || y1 <= y0) return 1u;
+    return x0 | ((x1 - 1u) << 8) | (y0 << 16) | ((y1 - 1u) << 24);
+}
+__device__ __forceinline__ uint2 rect32_unpack(uint32_t r) {
+    return make_uint2((r & 0xFFu) | (((r >> 16) & 0xFFu) << 16),
+                      (((r >> 8) & 0xFFu) + 1u) | (((r >> 24) + 1u) << 16));
+}
 
 struct DevStatus {
     int32_t code;
@@ -129,6 +144,14 @@ __device__ __forceinline__ void st_hint(uint2* p, uint2 v, uint64_t pol) {
     asm volatile("st.global.L2::cache_hint.v2.u32 [%0], {%1, %2}, %3;" ::"l"(p), "r"(v.x), "r"(v.y), "l"(pol)
                  : "memory");
 }
+__device__ __forceinline__ void st_hint(uint32_t* p, uint32_t v, uint64_t pol) {
+    asm volatile("st.global.L2::cache_hint.u32 [%0], %1, %2;" ::"l"(p), "r"(v), "l"(pol) : "memory");
+}
+__device__ __forceinline__ uint32_t ld_hint(const uint32_t* p, uint64_t pol) {
+    uint32_t v;
+    asm volatile("ld.global.L2::cache_hint.u32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol));
+    return v;
+}
 __device__ __forceinline__ uint2 ld_hint(const uint2* p, uint64_t pol) {
     uint2 v;
     asm volatile("ld.global.L2::cache_hint.v2.u32 {%0, %1}, [%2], %3;" : "=r"(v.x), "=r"(v.y) : "l"(p), "l"(pol));
@@ -163,7 +186,8 @@ struct SortScratch {
     int64_t max_sort_tiles;    // per pass
     uint32_t* d_count_depth;   // depth-sort items (V*n, or those kept by the compaction)
     uint2* rects;              // [V*n] tile rectangle of each record: (x0 | y0 << 16, x1 | y1 << 16),
-                               // kept in L2 (evict-last) from the projection to the emission
+                               // or as uint32 [V*n] in the 4-byte form when vt[V].rect32; kept in
+                               // L2 (evict-last) from the projection to the emission
     uint32_t* keep_sums;       // block sums of the depth-item compaction
     // two-level binning (super-tile lists, then per-tile lists)
     uint2* cranges;            // [total_tiles] bound on super-tiles: coarse [start, end)

@@ -221,6 +221,7 @@ k_project(const float4* __restrict__ P, int64_t n, int64_t g_off, int64_t n_out,
     if (g >= n) return;
     constexpr int NB = (D + 1) * (D + 1);
     constexpr int NPL = (3 * NB + 3) / 4;
+    const bool rect32 = rects && vt[V].rect32;
     Gauss G;
     load_gauss(P, n, g, G);
     apply_dyn(dyn, g_off + g, G);
@@ -291,7 +292,10 @@ k_project(const float4* __restrict__ P, int64_t n, int64_t g_off, int64_t n_out,
             const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
             out[0] = z; out[1] = z; out[2] = z; out[3] = z;
             if (dkv) dkv[rec] = (0xFFFFFFFFull << 32) | (uint32_t)rec;
-            if (rects) st_hint(rects + rec, make_uint2(0u, 0u), l2_policy_evict_last());
+            if (rects) {
+                if (rect32) st_hint(reinterpret_cast<uint32_t*>(rects) + rec, 1u, l2_policy_evict_last());
+                else st_hint(rects + rec, make_uint2(0u, 0u), l2_policy_evict_last());
+            }
             continue;
         }
         float rgb[3] = {lrgb[0], lrgb[1], lrgb[2]};
@@ -319,7 +323,10 @@ k_project(const float4* __restrict__ P, int64_t n, int64_t g_off, int64_t n_out,
                              __uint_as_float((uint32_t)((x1 - x0) * (y1 - y0))), 0.f);
         if (dkv) dkv[rec] = ((uint64_t)__float_as_uint(Vg.tz) << 32) | (uint32_t)rec;
         // the emission gathers the rectangle in depth order: kept in L2
-        if (rects) st_hint(rects + rec, make_uint2(lo, hi), l2_policy_evict_last());
+        if (rects) {
+            if (rect32) st_hint(reinterpret_cast<uint32_t*>(rects) + rec, rect32_pack(lo, hi), l2_policy_evict_last());
+            else st_hint(rects + rec, make_uint2(lo, hi), l2_policy_evict_last());
+        }
     }
 }
 
@@ -538,6 +545,7 @@ __global__ void k_view_table(const gs_camera* __restrict__ cams, int V, int tile
     int64_t toff = 0, poff = 0, soff = 0;
     for (int v = 0; v < V; ++v) {
         ViewInfo vi;
+        vi.rect32 = vi.pad = 0;
         vi.width = cams[v].width;
         vi.height = cams[v].height;
         vi.tx = (vi.width + tile - 1) / tile;
@@ -557,6 +565,10 @@ __global__ void k_view_table(const gs_camera* __restrict__ cams, int V, int tile
     tot.tile_off = toff;
     tot.pix_off = poff;
     tot.stile_off = soff;
+    tot.rect32 = 1;
+    tot.pad = 0;
+    for (int v = 0; v < V; ++v)
+        if (vt[v].tx > 256 || vt[v].ty > 256) tot.rect32 = 0;
     vt[V] = tot;
     if (expect_tiles >= 0 && toff != expect_tiles) record_status(status, GS_ERR_ARG, toff);
 }

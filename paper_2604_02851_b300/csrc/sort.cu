@@ -327,14 +327,17 @@ __global__ void k_clear_u32(uint32_t* p, int64_t n) {
 
 // Depth-sort input from projection records: key = float32 depth bits of a
 // visible (view, Gaussian), all-ones when culled; value = record index.
-__global__ void k_depth_keys(const uint4* __restrict__ proj, int64_t items, uint64_t* __restrict__ kv,
-                             uint2* __restrict__ rects) {
+__global__ void k_depth_keys(const uint4* __restrict__ proj, int64_t items, const ViewInfo* __restrict__ vt, int V,
+                             uint64_t* __restrict__ kv, uint2* __restrict__ rects) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= items) return;
     const uint4 r3 = proj[i * 4 + 3];
     const uint32_t key = r3.z ? proj[i * 4].z : 0xFFFFFFFFu;
     kv[i] = ((uint64_t)key << 32) | (uint32_t)i;
-    st_hint(rects + i, make_uint2(r3.x, r3.y), l2_policy_evict_last());
+    if (vt[V].rect32)
+        st_hint(reinterpret_cast<uint32_t*>(rects) + i, r3.z ? rect32_pack(r3.x, r3.y) : 1u, l2_policy_evict_last());
+    else
+        st_hint(rects + i, make_uint2(r3.x, r3.y), l2_policy_evict_last());
 }
 
 // Compaction of depth-sort items: the items with a key other than all ones
@@ -423,7 +426,7 @@ k_emit(const uint64_t* __restrict__ dsorted, int64_t total, int64_t n, const uin
        const ViewInfo* __restrict__ vt, int64_t cap, uint64_t* __restrict__ kv,
        unsigned long long* __restrict__ lookback, uint32_t* block_counter, uint32_t* d_num_keys,
        int passes, uint32_t* __restrict__ hist, int sshift, unsigned long long* fine_total, uint32_t key_bound,
-       const uint32_t* d_total, DevStatus* status) {
+       const uint32_t* d_total, DevStatus* status, int V) {
     constexpr int R = 1 << BITS;
     __shared__ uint32_t s_hist[kMaxPasses][R];
     __shared__ int s_mark[kEmitWarps][32];
@@ -431,6 +434,7 @@ k_emit(const uint64_t* __restrict__ dsorted, int64_t total, int64_t n, const uin
     __shared__ uint32_t s_blk;
     __shared__ unsigned long long s_excl;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const bool rect32 = vt[V].rect32 != 0;
     for (int i = threadIdx.x; i < kMaxPasses * R; i += kEmitThreads) (&s_hist[0][0])[i] = 0;
     if (threadIdx.x == 0) s_blk = atomicAdd(block_counter, 1u);
     __syncthreads();
@@ -453,7 +457,9 @@ k_emit(const uint64_t* __restrict__ dsorted, int64_t total, int64_t n, const uin
             const uint32_t rr = (uint32_t)dsorted[idx];
             // the record's tile rectangle, left in L2 by the projection (its
             // last use: demoted for eviction)
-            const uint2 rc = ld_hint(rects + rr, l2_policy_evict_first());
+            const uint2 rc = rect32 ? rect32_unpack(ld_hint(reinterpret_cast<const uint32_t*>(rects) + rr,
+                                                            l2_policy_evict_first()))
+                                    : ld_hint(rects + rr, l2_policy_evict_first());
             const uint32_t rw = (rc.y & 0xFFFFu) - (rc.x & 0xFFFFu), rh = (rc.y >> 16) - (rc.x >> 16);
             const uint4 p3 = make_uint4(rc.x, rc.y, rw * rh, 0u);
             const uint32_t v = (uint32_t)(rr / (uint64_t)n);
@@ -978,7 +984,7 @@ void onesweep_passes(uint64_t* const buf[2], uint64_t* last_out, uint32_t* kout,
 // Emission + tile-key sort + ranges, for one digit width.
 template <int BITS, int ITEMS>
 void emit_and_sort(const uint64_t* dsorted, int64_t items, const uint32_t* d_items, int64_t n, const uint4* pr,
-                   const ViewInfo* vt,
+                   const ViewInfo* vt, int V,
                    int64_t keys_cap, int key_bits, const SortScratch& s, uint32_t* sorted_keys,
                    uint32_t* sorted_vals, uint32_t* ranges, int64_t total_tiles, uint32_t* d_num_keys,
                    DevStatus* status, int sm_count, cudaStream_t st,
@@ -991,7 +997,7 @@ void emit_and_sort(const uint64_t* dsorted, int64_t items, const uint32_t* d_ite
     k_emit<BITS><<<(unsigned)nblk, kEmitThreads, 0, st>>>(dsorted, items, n, s.rects, vt, keys_cap, s.tkv[0],
                                                           s.emit_lookback, s.counters + 7, d_num_keys, passes,
                                                           s.hist, 0, nullptr, (uint32_t)total_tiles, d_items,
-                                                          status);
+                                                          status, V);
     if (mark) mark(events, ev, st);
     k_ranges_init<<<sm_count * 2, 256, 0, st>>>(reinterpret_cast<uint2*>(ranges), total_tiles);
     uint64_t* const buf[2] = {s.tkv[0], s.tkv[1]};
@@ -1024,7 +1030,7 @@ void emit_two_level(const uint64_t* dsorted, int64_t items, const uint32_t* d_it
     k_emit<BITS><<<(unsigned)nblk, kEmitThreads, 0, st>>>(dsorted, items, n, s.rects, vt, keys_cap, s.tkv[0],
                                                           s.emit_lookback, s.counters + 7, s.d_count_coarse,
                                                           passes, s.hist, kSuperShift, s.d_fine_total,
-                                                          (uint32_t)n_super, d_items, status);
+                                                          (uint32_t)n_super, d_items, status, V);
     k_fine_total<<<1, 1, 0, st>>>(s.d_fine_total, keys_cap, d_num_keys, status);
     if (mark) mark(events, ev, st);
     // stable sort by super-tile; the values land in the ping-pong buffer the
@@ -1128,7 +1134,7 @@ void launch_bin_sort(const float* proj, const ViewInfo* vt, int V, int64_t n, in
     // 1. depth sort of all (view, Gaussian) pairs: 32-bit keys, 4 passes of
     //    8-bit digits ending back in dkv[0]
     if (!depth_ready)
-        k_depth_keys<<<(unsigned)((items + 255) / 256), 256, 0, st>>>(pr, items, s.dkv[0], s.rects);
+        k_depth_keys<<<(unsigned)((items + 255) / 256), 256, 0, st>>>(pr, items, vt, V, s.dkv[0], s.rects);
     // with compaction the kept items move to dkv[1] and the sort ends there
     const uint64_t* dsorted = s.dkv[0];
     const uint32_t* d_items = nullptr;
@@ -1161,7 +1167,7 @@ void launch_bin_sort(const float* proj, const ViewInfo* vt, int V, int64_t n, in
 #define GS_EMIT_SORT(B, I)                                                                                      \
     do {                                                                                                        \
         if (binning == kBinDirect || bits > kMaxCoarseKeyBits)                                                  \
-            emit_and_sort<B, I>(dsorted, items, d_items, n, pr, vt, keys_cap, bits, s, sorted_keys, sorted_vals,  \
+            emit_and_sort<B, I>(dsorted, items, d_items, n, pr, vt, V, keys_cap, bits, s, sorted_keys, sorted_vals, \
                                 ranges,                                                                         \
                                 total_tiles, d_num_keys, status, sm_count, st, mark, events, first_event + 1);  \
         else                                                                                                    \
