@@ -199,10 +199,11 @@ __device__ __forceinline__ float lit_vis(const Dyn& d, int64_t g) {
     return d.vis ? (float)d.vis[g] * (1.f / 255.f) : 1.f;
 }
 
-// Three blocks an SM (at most 85 registers a thread, a few spills at SH
-// degree 3) measured faster than two at 116 registers.
+// View-dependent colour: four blocks an SM (64 registers; the coefficients
+// wait in shared memory); relit colour: three (85 registers).  Both measured
+// faster than two blocks with the coefficients in 116 registers.
 template <int D, bool LIT>
-__global__ void __launch_bounds__(256, 3)
+__global__ void __launch_bounds__(256, LIT ? 3 : 4)
 k_project(const float4* __restrict__ P, int64_t n, int64_t g_off, int64_t n_out, Dyn dyn,
           const gs_camera* __restrict__ cams, const ViewInfo* __restrict__ vt, int V, int tile,
           float4* __restrict__ proj, uint64_t* __restrict__ dkv, uint2* __restrict__ rects) {
@@ -241,17 +242,28 @@ k_project(const float4* __restrict__ P, int64_t n, int64_t g_off, int64_t n_out,
         kept = dyn.cell_vis[cell] != 0;
         if (dyn.fwd && g_off == 0) dyn.fwd[g] = kept ? 1 : 0;
     }
-    float sh[NPL * 4];
-#pragma unroll
-    for (int pl = 0; pl < NPL; ++pl) {
-        const float4 c = P[(3 + pl) * n + g];
-        sh[4 * pl] = c.x; sh[4 * pl + 1] = c.y; sh[4 * pl + 2] = c.z; sh[4 * pl + 3] = c.w;
-    }
-    sh[0] *= G.L; sh[1] *= G.L; sh[2] *= G.L;
+    // relit colour: the coefficients in registers, used once; view-dependent
+    // colour: in shared memory (this thread's column, the DC term scaled),
+    // read per view
     float lrgb[3] = {0.f, 0.f, 0.f};
     uint32_t lmask = 0;
     const float tau = 2.f * (logf(G.opac) + 5.5412635f);  // 2 ln(255 o): the alpha >= 1/255 ellipse
-    if (LIT) {
+    float4* s_sh = reinterpret_cast<float4*>(s_lt);
+    if constexpr (!LIT) {
+#pragma unroll
+        for (int pl = 0; pl < NPL; ++pl) {
+            float4 c = P[(3 + pl) * n + g];
+            if (pl == 0) { c.x *= G.L; c.y *= G.L; c.z *= G.L; }
+            s_sh[pl * blockDim.x + threadIdx.x] = c;
+        }
+    } else {
+        float sh[NPL * 4];
+#pragma unroll
+        for (int pl = 0; pl < NPL; ++pl) {
+            const float4 c = P[(3 + pl) * n + g];
+            sh[4 * pl] = c.x; sh[4 * pl + 1] = c.y; sh[4 * pl + 2] = c.z; sh[4 * pl + 3] = c.w;
+        }
+        sh[0] *= G.L; sh[1] *= G.L; sh[2] *= G.L;
         const float* lt = staged ? s_lt + lit_group(dyn, g_off + g) * kStageStride : lit_row(dyn, g_off + g);
         relit_rgb<NB>(sh, lt, lit_vis(dyn, g_off + g), lrgb, lmask);
     }
@@ -304,14 +316,22 @@ k_project(const float4* __restrict__ P, int64_t n, int64_t g_off, int64_t n_out,
             float Y[16];
             const float3 ds = sh_dir(G, Vg.dir);
             sh_basis<D>(ds.x, ds.y, ds.z, Y);
+            float acc[3] = {0.f, 0.f, 0.f};  // each channel summed over k in order
+#pragma unroll
+            for (int pl = 0; pl < NPL; ++pl) {
+                const float4 c4 = s_sh[pl * blockDim.x + threadIdx.x];
+                const float cv[4] = {c4.x, c4.y, c4.z, c4.w};
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int j = 4 * pl + e;
+                    if (j < 3 * NB) acc[j % 3] += cv[e] * Y[j / 3];
+                }
+            }
 #pragma unroll
             for (int ch = 0; ch < 3; ++ch) {
-                float acc = 0.f;
-#pragma unroll
-                for (int k = 0; k < NB; ++k) acc += sh[3 * k + ch] * Y[k];
-                acc += 0.5f;
-                if (acc < 0.f) { acc = 0.f; mask |= 1u << ch; }
-                rgb[ch] = acc;
+                float a = acc[ch] + 0.5f;
+                if (a < 0.f) { a = 0.f; mask |= 1u << ch; }
+                rgb[ch] = a;
             }
         }
         const float idet = 1.f / Vg.det;
@@ -341,11 +361,16 @@ k_project_bwd(const float4* __restrict__ P, int64_t n, int64_t n_out, Dyn dyn, c
     if (g >= n) return;
     constexpr int NB = (D + 1) * (D + 1);
     constexpr int NPL = (3 * NB + 3) / 4;
+    // the SH coefficients are staged in shared memory once and re-read per
+    // view from there, rather than held in registers next to their gradient
+    __shared__ float4 s_sh[LIT ? 1 : NPL][128];
+    if (!LIT) {
+#pragma unroll
+        for (int pl = 0; pl < NPL; ++pl) s_sh[pl][threadIdx.x] = __ldg(&P[(3 + pl) * n + g]);
+    }
     Gauss G;
     load_gauss(P, n, g, G);
     apply_dyn(dyn, g, G);
-    // the SH coefficients are re-read per view (L1 hits) rather than held in
-    // registers next to their gradient, to keep the thread's footprint small
     float dsh[NPL * 4];
 #pragma unroll
     for (int pl = 0; pl < NPL; ++pl) dsh[4 * pl] = dsh[4 * pl + 1] = dsh[4 * pl + 2] = dsh[4 * pl + 3] = 0.f;
@@ -382,7 +407,7 @@ k_project_bwd(const float4* __restrict__ P, int64_t n, int64_t n_out, Dyn dyn, c
         for (int k = 0; k < 16; ++k) wsum[k] = 0.f;
 #pragma unroll
         for (int pl = 0; pl < NPL; ++pl) {
-            const float4 c4 = __ldg(&P[(3 + pl) * n + g]);
+            const float4 c4 = s_sh[LIT ? 0 : pl][threadIdx.x];
             const float cv[4] = {c4.x, c4.y, c4.z, c4.w};
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
@@ -593,7 +618,8 @@ void launch_project(const float* params, int64_t n, int sh_degree, const Dyn& dy
     const size_t smem = lit && lit_groups(dyn) <= kStageGroups ? sizeof(float) * lit_groups(dyn) * kStageStride : 0;
 #define GS_PROJ(DD)                                                                                              \
     (lit ? k_project<DD, true><<<blocks, threads, smem, st>>>(P, n, g_off, n_out, dyn, d_cams, vt, V, tile, out, depth_kv, rects) \
-         : k_project<DD, false><<<blocks, threads, 0, st>>>(P, n, g_off, n_out, dyn, d_cams, vt, V, tile, out, depth_kv, rects))
+         : k_project<DD, false><<<blocks, threads, sizeof(float4) * threads * ((3 * (DD + 1) * (DD + 1) + 3) / 4), st>>>( \
+               P, n, g_off, n_out, dyn, d_cams, vt, V, tile, out, depth_kv, rects))
     switch (sh_degree) {
         case 0: GS_PROJ(0); break;
         case 1: GS_PROJ(1); break;
