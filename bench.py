@@ -65,20 +65,21 @@ FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12  # SMs x FP32 lanes x FMA x ma
 def phase_model(n, V, K, total_tiles, npix, sum_nc, n_changed, binning, passes, Kc, chunks, n_train=None):
     """Algorithmic bytes (HBM) or FLOPs per launch of each phase.
 
-    K fine (tile, Gaussian) entries; two-level binning also moves Kc coarse
+    K fine (tile, Gaussian) entries; two-level binning moves Kc coarse
     (super-tile, Gaussian) entries through `passes` radix passes and writes
-    per-chunk tile counts (chunks x 64); direct binning moves the K entries
+    the chunk bitmaps (2 KB per chunk); direct binning moves the K entries
     through `passes` passes."""
     vn = V * n
     nt = n if n_train is None else n_train  # Gaussians that are trained (the active pool)
     if binning == "two_level":
-        emit = vn * (8 + 8) + Kc * 8
-        sort = Kc * 16 * passes + 2 * Kc * 8 + K * 4 + total_tiles * 8 + chunks * 64 * 4 * 3
+        # the training step stops at the chunk bitmaps (2 KB per chunk)
+        emit = vn * (8 + 4) + Kc * 8
+        sort = Kc * 16 * passes + Kc * 8 + chunks * 2048
     else:
-        emit = vn * (8 + 8) + K * 8
+        emit = vn * (8 + 4) + K * 8
         sort = K * (16 * (passes - 1) + 12) + total_tiles * 16
     return {
-        "project": ("hbm", n * 240 + vn * (64 + 8)),
+        "project": ("hbm", n * 240 + vn * (64 + 4)),
         "depth_sort": ("hbm", vn * (4 * 16 + 4)),
         "emit": ("hbm", emit),
         "tile_sort": ("hbm", sort),
@@ -97,7 +98,7 @@ def phase_model(n, V, K, total_tiles, npix, sum_nc, n_changed, binning, passes, 
 # capture at full size; profiles/train_step_1M_8x720p_traffic.md), valid while
 # the kernel's source file is unchanged (first 12 hex digits of its SHA-1).
 MEASURED_TRAFFIC = {
-    ("c3_1M_8x720p", "k_raster_bwd"): (265.0e6, "csrc/raster.cu", "f8476020b95c"),
+    ("c3_1M_8x720p", "k_raster_bwd"): (257.9e6, "csrc/raster.cu", "81a96c65e834"),
 }
 
 
@@ -125,13 +126,12 @@ def gpu_launches_per_step(binning, passes):
     """Kernels of one train step, counted from the launch sequence: view
     table, projection, depth sort (count, histogram, look-back clear, scan,
     4 passes), emission and sort (two-level: emission, fine total, ranges
-    init, look-back clear, scan, passes, ranges fix, chunk table, count,
-    prefix, tile scan, write; direct: emission, ranges init, look-back clear,
-    scan, passes, ranges fix), compositing, loss (2), adjoints (2), Adam
-    with the delta's changed test and the step counter (2), delta scan and
-    records (2)."""
+    init, look-back clear, scan, passes, ranges fix, chunk table, bitmaps;
+    direct: emission, ranges init, look-back clear, scan, passes, ranges
+    fix), compositing, loss (2), adjoints (2), Adam with the delta's changed
+    test and the step counter (2), delta scan and records (2)."""
     depth = 8
-    sort = (11 + passes) if binning == "two_level" else (5 + passes)
+    sort = (8 + passes) if binning == "two_level" else (5 + passes)
     return 1 + 1 + depth + sort + 1 + 2 + 1 + 1 + 2 + 2
 
 
