@@ -132,16 +132,21 @@ k_hist(const uint64_t* __restrict__ items, const uint32_t* d_count, int64_t cap,
 template <int BITS>
 __global__ void k_hist_scan(uint32_t* hist, int passes) {
     constexpr int R = 1 << BITS;
-    __shared__ uint32_t s[256];
-    for (int p = 0; p < passes; ++p) {
-        if (threadIdx.x < R) s[threadIdx.x] = hist[p * 256 + threadIdx.x];
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            uint32_t acc = 0;
-            for (int d = 0; d < R; ++d) { const uint32_t c = s[d]; s[d] = acc; acc += c; }
+    __shared__ uint32_t s_w[8];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int p = 0; p < passes; ++p) {  // 256 threads, one digit each: exclusive block scan
+        const uint32_t x = threadIdx.x < R ? hist[p * 256 + threadIdx.x] : 0u;
+        uint32_t incl = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+            if (lane >= o) incl += y;
         }
+        if (lane == 31) s_w[warp] = incl;
         __syncthreads();
-        if (threadIdx.x < R) hist[p * 256 + threadIdx.x] = s[threadIdx.x];
+        uint32_t off = 0;
+        for (int w = 0; w < warp; ++w) off += s_w[w];
+        if (threadIdx.x < R) hist[p * 256 + threadIdx.x] = off + incl - x;
         __syncthreads();
     }
 }
@@ -652,8 +657,6 @@ k_fine_chunks(const uint2* __restrict__ cranges, const ViewInfo* __restrict__ vt
         const uint2 r = cranges[s];
         const uint32_t nc = (r.y > r.x ? r.y - r.x + kFineChunk - 1 : 0u) / kFineChunk;
         chunk_first[s] = run;
-        for (uint32_t c = 0; c < nc; ++c)
-            if ((int64_t)run + c < max_chunks) chunk_s[run + c] = (uint32_t)s;
         run += nc;
     }
     if (threadIdx.x == blockDim.x - 1) {
@@ -664,6 +667,19 @@ k_fine_chunks(const uint2* __restrict__ cranges, const ViewInfo* __restrict__ vt
         // (keys_cap / 256 chunks) is too small for them
         if ((int64_t)tot > max_chunks) record_status(status, GS_ERR_CAPACITY, (long long)tot * kFineChunk);
     }
+}
+
+// chunk_s[c] := super-tile of chunk c, one warp per super-tile (coalesced
+// runs; chunks past the table are dropped, as k_fine_chunks reports).
+__global__ void __launch_bounds__(256)
+k_chunk_owner(const uint32_t* __restrict__ chunk_first, const ViewInfo* __restrict__ vt, int V, int64_t ns_bound,
+              uint32_t* __restrict__ chunk_s, int64_t max_chunks) {
+    const int64_t ns = vt[V].stile_off < ns_bound ? vt[V].stile_off : ns_bound;
+    const int64_t s = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (s >= ns) return;
+    const int64_t c0 = chunk_first[s];
+    const int64_t c1 = min((int64_t)chunk_first[s + 1], max_chunks);
+    for (int64_t c = c0 + (threadIdx.x & 31); c < c1; c += 32) chunk_s[c] = (uint32_t)s;
 }
 
 // 32 x 32 bit-matrix transpose across a warp: on return bit j of lane k's
@@ -1050,6 +1066,8 @@ void emit_two_level(const uint64_t* dsorted, int64_t items, const uint32_t* d_it
         const int64_t bm_chunks = keys_cap / kFineChunk;
         k_fine_chunks<<<1, 1024, 0, st>>>(s.cranges, vt, V, n_super, s.chunk_first, s.chunk_s, s.d_n_chunks,
                                           std::min<int64_t>(s.max_chunks, bm_chunks), status);
+        k_chunk_owner<<<(unsigned)((n_super + 7) / 8), 256, 0, st>>>(s.chunk_first, vt, V, n_super, s.chunk_s,
+                                                                   std::min<int64_t>(s.max_chunks, bm_chunks));
         k_fine_mask<<<fgrid, kFineThreads, 0, st>>>(citems, s.cranges, s.chunk_first, s.chunk_s, s.d_n_chunks, vt,
                                                     V, total_tiles, bitmap);
         coarse->citems = citems;
@@ -1062,6 +1080,8 @@ void emit_two_level(const uint64_t* dsorted, int64_t items, const uint32_t* d_it
     // fine expansion
     k_fine_chunks<<<1, 1024, 0, st>>>(s.cranges, vt, V, n_super, s.chunk_first, s.chunk_s, s.d_n_chunks,
                                       s.max_chunks, status);
+    k_chunk_owner<<<(unsigned)((n_super + 7) / 8), 256, 0, st>>>(s.chunk_first, vt, V, n_super, s.chunk_s,
+                                                               s.max_chunks);
     k_fine_count<<<fgrid, kFineThreads, 0, st>>>(citems, s.cranges, s.chunk_first, s.chunk_s, s.d_n_chunks, vt, V,
                                                  total_tiles, s.chunk_off);
     k_fine_prefix<<<(unsigned)((n_super * 64 + 255) / 256), 256, 0, st>>>(s.chunk_first, s.d_n_chunks, vt, V,
