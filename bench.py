@@ -56,9 +56,19 @@ def _peaks():
         return 6400.0, "fallback"
 
 
-# FP32 operations per unit of work, counted from the kernels' source (FMA = 2).
-RASTER_FWD_FLOP_PER_FRAGMENT = 20     # one (pixel, fragment) evaluation up to the last kept fragment
-RASTER_BWD_FLOP_PER_FRAGMENT = 60     # one (pixel, fragment) adjoint evaluation
+# FP32 operations per unit of work, counted from the kernels' source (FMA = 2;
+# an ex2 / rcp, a min and a compare count 1 each).  Unit: one (pixel,
+# fragment) evaluation up to the pixel's last contributor, counted as a full
+# evaluation (pairs below the alpha cut-off stop after the exponent, so this
+# is an upper bound on the work done).
+#   compositing: offset 1, exponent 2 FMA + penalty 1, test 1, ex2 + scale 2,
+#     min 1, 1 - alpha and T update 3, weight 1, three colour FMAs 6 = 20
+#   adjoint: offset 1, exponent 2 FMA, test 1, ex2 + scale 2, min 1,
+#     1 - alpha 2, rcp + T 2, weight 1, three colour-gradient FMAs 6,
+#     dL/dC . (c - R) 7, dL/dalpha 1, X update 2, clamp select + dL/dP 2,
+#     dL/dP dx 1 and the sums of dL/dP, dL/dP dx, dL/dP dx^2 4 = 37
+RASTER_FWD_FLOP_PER_FRAGMENT = 20
+RASTER_BWD_FLOP_PER_FRAGMENT = 37
 FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12  # SMs x FP32 lanes x FMA x max SM clock
 
 
