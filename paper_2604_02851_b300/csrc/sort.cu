@@ -791,13 +791,19 @@ k_fine_mask(const uint64_t* __restrict__ citems, const uint2* __restrict__ crang
     const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
     for (uint32_t c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < nchunks; c += nw) {
         const FineChunk f = fine_chunk(c, cranges, chunk_first, chunk_s, vt, V, total_tiles, lane);
+        // the chunk's 8 items of this lane requested together, then decoded
+        uint32_t rect[8];
+#pragma unroll
+        for (int grp = 0; grp < 8; ++grp) {
+            const uint32_t i = f.a + (uint32_t)grp * 32u + (uint32_t)lane;
+            rect[grp] = i < f.e ? (uint32_t)(citems[i] >> kRectShift) : 0xFFFFFFFFu;
+        }
         uint32_t w0[8], w1[8];
 #pragma unroll
         for (int grp = 0; grp < 8; ++grp) {
-            uint32_t gval = 0, c0 = 0, c1 = 0;
-            if (f.a + (uint32_t)grp * 32u < f.e) fine_group(f, (uint32_t)grp, citems, lane, gval, c0, c1);
-            w0[grp] = c0;
-            w1[grp] = c1;
+            const uint64_t m = rect[grp] == 0xFFFFFFFFu ? 0ull : rect12_mask(rect[grp]) & f.valid;
+            w0[grp] = transpose32((uint32_t)m, lane);
+            w1[grp] = transpose32((uint32_t)(m >> 32), lane);
         }
         uint4* out = reinterpret_cast<uint4*>(bitmap) + (size_t)c * 128;
         out[2 * lane] = make_uint4(w0[0], w0[1], w0[2], w0[3]);
