@@ -379,9 +379,14 @@ k_project_bwd(const float4* __restrict__ P, int64_t n, int64_t n_out, Dyn dyn, c
     float D00 = 0.f, D01 = 0.f, D02 = 0.f, D11 = 0.f, D12 = 0.f, D22 = 0.f;  // dSigma + dSigma^T
     for (int v = 0; v < V; ++v) {
         const int64_t rec = (int64_t)v * n_out + g;
-        const float4 pr3 = proj[rec * 4 + 3];
-        if (__float_as_uint(pr3.z) == 0u) continue;  // culled in this view
+        // every term of a view's contribution is a multiple of its 2D
+        // gradient: views without one (culled, or reaching no pixel's
+        // compositing) are skipped before their projection record is read
         const float4 ga = g2d[rec * 3], gb = g2d[rec * 3 + 1], gc = g2d[rec * 3 + 2];
+        if (ga.x == 0.f && ga.y == 0.f && ga.z == 0.f && ga.w == 0.f && gb.x == 0.f && gb.y == 0.f &&
+            gb.z == 0.f && gb.w == 0.f && gc.x == 0.f)
+            continue;
+        if (__float_as_uint(proj[rec * 4 + 3].z) == 0u) continue;  // culled in this view
         const uint32_t mask = __float_as_uint(proj[rec * 4 + 2].w);
         const Cam C = load_cam(cams + v);
         ViewGeom Vg;
