@@ -136,12 +136,13 @@ def gpu_launches_per_step(binning, passes):
     """Kernels of one train step, counted from the launch sequence: view
     table, projection, depth sort (count, histogram, look-back clear, scan,
     4 passes), emission and sort (two-level: emission, fine total, ranges
-    init, look-back clear, scan, passes, ranges fix, chunk table, bitmaps;
+    init, look-back clear, scan, passes, ranges fix, chunk table, chunk
+    owners, bitmaps;
     direct: emission, ranges init, look-back clear, scan, passes, ranges
     fix), compositing, loss (2), adjoints (2), Adam with the delta's changed
     test and the step counter (2), delta scan and records (2)."""
     depth = 8
-    sort = (8 + passes) if binning == "two_level" else (5 + passes)
+    sort = (9 + passes) if binning == "two_level" else (5 + passes)
     return 1 + 1 + depth + sort + 1 + 2 + 1 + 1 + 2 + 2
 
 
