@@ -1067,13 +1067,12 @@ void emit_two_level(const uint64_t* dsorted, int64_t items, const uint32_t* d_it
     const unsigned fgrid = (unsigned)(sm_count * 8);
     if (coarse) {
         // chunk-bitmap lists: the bitmaps go to the ping-pong buffer the last
-        // pass read (keys_cap 8-byte items: room for keys_cap / 256 chunks)
+        // pass read and the room after it (2 KB for each of max_chunks)
         uint32_t* bitmap = reinterpret_cast<uint32_t*>(buf[1 - passes % 2]);
-        const int64_t bm_chunks = keys_cap / kFineChunk;
         k_fine_chunks<<<1, 1024, 0, st>>>(s.cranges, vt, V, n_super, s.chunk_first, s.chunk_s, s.d_n_chunks,
-                                          std::min<int64_t>(s.max_chunks, bm_chunks), status);
+                                          s.max_chunks, status);
         k_chunk_owner<<<(unsigned)((n_super + 7) / 8), 256, 0, st>>>(s.chunk_first, vt, V, n_super, s.chunk_s,
-                                                                   std::min<int64_t>(s.max_chunks, bm_chunks));
+                                                                   s.max_chunks);
         k_fine_mask<<<fgrid, kFineThreads, 0, st>>>(citems, s.cranges, s.chunk_first, s.chunk_s, s.d_n_chunks, vt,
                                                     V, total_tiles, bitmap);
         coarse->citems = citems;
@@ -1119,8 +1118,16 @@ void carve_sort_scratch(char* base, int V, int64_t n, int64_t keys_cap, int64_t 
     s->dkv[0] = c.take<uint64_t>(items);
     s->dkv[1] = c.take<uint64_t>(items);
     s->emit_lookback = c.take<unsigned long long>((items + kEmitBlock - 1) / kEmitBlock + 1);
+    // super-tiles never outnumber tiles
+    const int64_t ns = total_tiles > 0 ? total_tiles : 1;
+    // each ping-pong buffer is followed by room for ns + 1 chunk bitmaps, so
+    // that the one the super-tile sort leaves free holds the bitmaps of all
+    // keys_cap / 256 + ns + 1 chunks the chunk table allows
+    const size_t bm_room = (size_t)(ns + 1) * kChunkItems * 8;
     s->tkv[0] = c.take<uint64_t>(keys_cap);
+    c.take<char>(bm_room);
     s->tkv[1] = c.take<uint64_t>(keys_cap);
+    c.take<char>(bm_room);
     s->hist = c.take<uint32_t>(kMaxPasses * 256);
     s->counters = c.take<uint32_t>(8);
     s->max_sort_tiles = (std::max(items, keys_cap) + kMinTileKeys - 1) / kMinTileKeys + 1;
@@ -1128,8 +1135,6 @@ void carve_sort_scratch(char* base, int V, int64_t n, int64_t keys_cap, int64_t 
     s->d_count_depth = c.take<uint32_t>(1);
     s->rects = c.take<uint2>(items);
     s->keep_sums = c.take<uint32_t>((items + kKeepBlock - 1) / kKeepBlock + 1);
-    // super-tiles never outnumber tiles
-    const int64_t ns = total_tiles > 0 ? total_tiles : 1;
     s->max_chunks = keys_cap / kFineChunk + ns + 1;
     s->cranges = c.take<uint2>(ns);
     s->chunk_first = c.take<uint32_t>(ns + 1);

@@ -9,8 +9,9 @@ visit the same fragments in the same order, so the first step's rendered
 image and loss are bit-identical; the gradients differ only in the order of
 the float atomics, and so do the parameters (and the next step's image) by
 rounding.  Cases: one super-tile holding many chunks, ragged image edges, big
-splats spanning many super-tiles, both raster layouts, 8-pixel tiles, and an
-opaque scene whose pixels stop early.
+splats spanning many super-tiles, both raster layouts, 8-pixel tiles, an
+opaque scene whose pixels stop early, and a tiny scene over many views (more
+chunks than keys_cap / 256).
 """
 import numpy as np
 import pytest
@@ -28,6 +29,9 @@ CASES = {
     "big_splats": (3_000, 0, 2, 333, 250, 1.5, 0.0, 16, 4, 4),
     "opaque_early_stop": (30_000, 1, 2, 176, 112, 0.8, 4.0, 16, 4, 2),
     "tile8": (8_000, 0, 2, 150, 90, 0.5, 0.0, 8, 4, 4),
+    # a handful of Gaussians over many views: more chunks (one per non-empty
+    # super-tile) than keys_cap / 256, the bitmaps still fit
+    "tiny_many_views": (12, 0, 16, 256, 160, 1.0, 2.0, 16, 4, 2),
 }
 
 
@@ -72,6 +76,13 @@ def test_train_step_chunk_lists_match_expanded_lists(name):
         # the super-tile's list spans many 256-item chunks
         K = int(np.count_nonzero(O.project(planes, sh, cams32(cams))[..., 14] > 0))
         assert K > 20 * 256
+    if name == "tiny_many_views":
+        # every non-empty super-tile takes a chunk: more than keys_cap / 256
+        rect = O.project(planes, sh, cams32(cams))[..., 12:16].astype(np.int64)
+        sup = {(v, sy, sx) for v in range(V) for g in range(n)
+               for x0, x1, y0, y1 in [rect[v, g]] if x1 > x0 and y1 > y0
+               for sy in range(y0 >> 3, ((y1 - 1) >> 3) + 1) for sx in range(x0 >> 3, ((x1 - 1) >> 3) + 1)}
+        assert len(sup) > a.keys_cap // 256
     a.ctx.close()
     b.ctx.close()
 
