@@ -90,6 +90,10 @@ __device__ __forceinline__ bool look_back(unsigned long long* lb, int64_t slot, 
             }
             if (done) break;
             p -= used;
+            // nothing ready: back off so that the polling does not take the
+            // issue slots of the SM's other tiles (250 ns measured best of
+            // 32-500 ns)
+            if (used == 0) __nanosleep(250);
             if (used == 0 && clock64() - t0 > kSpinCycles) {
                 record_status(status, GS_ERR_TIMEOUT, slot);
                 ok = false;
