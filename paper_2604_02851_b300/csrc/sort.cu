@@ -633,11 +633,10 @@ __device__ __forceinline__ int find_super_view(const ViewInfo* __restrict__ vt, 
 }
 
 // Chunk table (one block): chunk_first[s] = first chunk of super-tile s,
-// chunk_s[c] = super-tile of chunk c, *d_n_chunks = total (clamped).
+// *d_n_chunks = total (clamped); k_chunk_owner then fills chunk_s.
 __global__ void __launch_bounds__(1024)
 k_fine_chunks(const uint2* __restrict__ cranges, const ViewInfo* __restrict__ vt, int V, int64_t ns_bound,
-              uint32_t* __restrict__ chunk_first, uint32_t* __restrict__ chunk_s, uint32_t* d_n_chunks,
-              int64_t max_chunks, DevStatus* status) {
+              uint32_t* __restrict__ chunk_first, uint32_t* d_n_chunks, int64_t max_chunks, DevStatus* status) {
     __shared__ uint32_t s_part[1024];
     const int64_t ns = vt[V].stile_off < ns_bound ? vt[V].stile_off : ns_bound;
     const int64_t per = (ns + blockDim.x - 1) / blockDim.x;
@@ -1073,7 +1072,7 @@ void emit_two_level(const uint64_t* dsorted, int64_t items, const uint32_t* d_it
         // chunk-bitmap lists: the bitmaps go to the ping-pong buffer the last
         // pass read and the room after it (2 KB for each of max_chunks)
         uint32_t* bitmap = reinterpret_cast<uint32_t*>(buf[1 - passes % 2]);
-        k_fine_chunks<<<1, 1024, 0, st>>>(s.cranges, vt, V, n_super, s.chunk_first, s.chunk_s, s.d_n_chunks,
+        k_fine_chunks<<<1, 1024, 0, st>>>(s.cranges, vt, V, n_super, s.chunk_first, s.d_n_chunks,
                                           s.max_chunks, status);
         k_chunk_owner<<<(unsigned)((n_super + 7) / 8), 256, 0, st>>>(s.chunk_first, vt, V, n_super, s.chunk_s,
                                                                    s.max_chunks);
@@ -1087,7 +1086,7 @@ void emit_two_level(const uint64_t* dsorted, int64_t items, const uint32_t* d_it
         return;
     }
     // fine expansion
-    k_fine_chunks<<<1, 1024, 0, st>>>(s.cranges, vt, V, n_super, s.chunk_first, s.chunk_s, s.d_n_chunks,
+    k_fine_chunks<<<1, 1024, 0, st>>>(s.cranges, vt, V, n_super, s.chunk_first, s.d_n_chunks,
                                       s.max_chunks, status);
     k_chunk_owner<<<(unsigned)((n_super + 7) / 8), 256, 0, st>>>(s.chunk_first, vt, V, n_super, s.chunk_s,
                                                                s.max_chunks);
