@@ -108,3 +108,35 @@ def test_render_batch_chunk_lists_match_expanded_lists(name):
         imgs.append(img.cpu().numpy())
         ctx.close()
     np.testing.assert_array_equal(imgs[0], imgs[1])
+
+
+@pytest.mark.parametrize("case", ["all_culled", "one_gaussian"])
+def test_train_step_chunk_lists_degenerate(case):
+    """Degenerate scenes through the fused step with chunk-bitmap lists: every
+    Gaussian outside every view (no list entry at all: the image is the
+    background, no gradient, Adam leaves the parameters), and a single
+    Gaussian; both as with the expanded lists."""
+    import torch
+    n, sh, V, W, H = (64, 0, 2, 96, 80) if case == "all_culled" else (1, 1, 3, 96, 80)
+    planes = scene(n, sh, 31, 2.0)
+    if case == "all_culled":
+        planes[0, :, 0:3] = np.array([0.0, 40.0, 0.0], dtype=np.float32)  # far above every ring camera's view
+    cams = gi.ring_cameras(V, W, H)
+    target = torch.full((3 * V * W * H,), 0.25, dtype=torch.float32, device="cuda")
+    a = _trainer("two_level", planes, sh, cams, target, 16, 4, 2)
+    b = _trainer("direct", planes, sh, cams, target, 16, 4, 2)
+    for tr in (a, b):
+        tr.step()
+    torch.cuda.synchronize()
+    assert a.ctx.status()[0] == 0 and b.ctx.status()[0] == 0
+    np.testing.assert_array_equal(a.image.cpu().numpy(), b.image.cpu().numpy())
+    assert a.loss() == b.loss()
+    if case == "all_culled":
+        np.testing.assert_array_equal(a.image.cpu().numpy(), np.zeros(3 * V * W * H, np.float32))
+        assert not np.any(a.grads.cpu().numpy())
+        np.testing.assert_array_equal(a.params.cpu().numpy(), planes)
+    else:
+        assert np.any(a.image.cpu().numpy() > 0)
+        assert rel_l2(a.grads.cpu().numpy(), b.grads.cpu().numpy()) <= 1e-5
+    a.ctx.close()
+    b.ctx.close()
