@@ -221,6 +221,7 @@ constexpr int kBinDirect = 1;
 constexpr int kChunkItems = 256;
 struct CoarseLists {
     const uint64_t* citems = nullptr;  // null: the call produced expanded lists
+    const uint32_t* cvals = nullptr;   // the items' Gaussian indices (low words), compact
     const uint2* cranges = nullptr;
     const uint32_t* chunk_first = nullptr;
     const uint32_t* d_n_chunks = nullptr;

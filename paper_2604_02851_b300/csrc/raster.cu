@@ -322,7 +322,7 @@ k_render_fwd(const float4* __restrict__ proj, const ViewInfo* __restrict__ vt, i
                 if (w0 > 0 && __syncthreads_count(nlive != 0) == 0) { stop = true; break; }
                 round(min(BATCH, cnt - w0), [&](int i, uint32_t& pos, uint32_t& g) {
                     pos = s_cand[w0 + i];
-                    g = (uint32_t)cl.citems[pos];
+                    g = cl.cvals[pos];
                 });
             }
             if (stop) break;
@@ -629,7 +629,7 @@ k_raster_bwd(const float4* __restrict__ proj, const ViewInfo* __restrict__ vt, i
                     const int wstart = wend > BATCH ? wend - BATCH : 0;
                     round(wend - wstart, [&](int i, uint32_t& pos, uint32_t& g) {
                         pos = s_cand[wstart + i];
-                        g = (uint32_t)cl.citems[pos];
+                        g = cl.cvals[pos];
                     });
                 }
             }

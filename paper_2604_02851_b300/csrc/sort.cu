@@ -1063,7 +1063,10 @@ void emit_two_level(const uint64_t* dsorted, int64_t items, const uint32_t* d_it
     k_ranges_init<<<sm_count, 256, 0, st>>>(s.cranges, n_super);
     uint64_t* const buf[2] = {s.tkv[0], s.tkv[1]};
     const uint64_t* citems = buf[passes % 2];
-    onesweep_passes<BITS, ITEMS>(buf, buf[passes % 2], nullptr, nullptr, s.d_count_coarse, keys_cap, passes, s,
+    // chunk-bitmap lists: the last pass also writes the items' Gaussian
+    // indices compactly (into the caller's value array, unused otherwise)
+    onesweep_passes<BITS, ITEMS>(buf, buf[passes % 2], nullptr, coarse ? sorted_vals : nullptr, s.d_count_coarse,
+                                 keys_cap, passes, s,
                                  reinterpret_cast<uint32_t*>(s.cranges), status, sm_count, st,
                                  (uint32_t)((1ull << bits) - 1ull));
     k_ranges_fix<<<sm_count, 256, 0, st>>>(s.cranges, n_super);
@@ -1079,6 +1082,7 @@ void emit_two_level(const uint64_t* dsorted, int64_t items, const uint32_t* d_it
         k_fine_mask<<<fgrid, kFineThreads, 0, st>>>(citems, s.cranges, s.chunk_first, s.chunk_s, s.d_n_chunks, vt,
                                                     V, total_tiles, bitmap);
         coarse->citems = citems;
+        coarse->cvals = sorted_vals;
         coarse->cranges = s.cranges;
         coarse->chunk_first = s.chunk_first;
         coarse->d_n_chunks = s.d_n_chunks;
