@@ -351,8 +351,10 @@ k_project(const float4* __restrict__ P, int64_t n, int64_t g_off, int64_t n_out,
 }
 
 // ------------------------------------------------------------------ adjoint
+// View-dependent colour: 4 blocks an SM (128 registers; the SH coefficients
+// and their gradient accumulators in shared memory, 48 KB a block); relit: 3.
 template <int D, bool LIT>
-__global__ void __launch_bounds__(128, 3)
+__global__ void __launch_bounds__(128, LIT ? 3 : 4)
 k_project_bwd(const float4* __restrict__ P, int64_t n, int64_t n_out, Dyn dyn, const gs_camera* __restrict__ cams,
               int V,
               const float4* __restrict__ proj, const float4* __restrict__ g2d,
@@ -371,9 +373,15 @@ k_project_bwd(const float4* __restrict__ P, int64_t n, int64_t n_out, Dyn dyn, c
     Gauss G;
     load_gauss(P, n, g, G);
     apply_dyn(dyn, g, G);
+    // view-dependent colour: the SH gradient accumulates in shared memory
+    // (this thread's column), next to the coefficients
+    __shared__ float4 s_dsh[LIT ? 1 : NPL][128];
     float dsh[NPL * 4];
 #pragma unroll
-    for (int pl = 0; pl < NPL; ++pl) dsh[4 * pl] = dsh[4 * pl + 1] = dsh[4 * pl + 2] = dsh[4 * pl + 3] = 0.f;
+    for (int pl = 0; pl < NPL; ++pl) {
+        if (!LIT) s_dsh[pl][threadIdx.x] = make_float4(0.f, 0.f, 0.f, 0.f);
+        dsh[4 * pl] = dsh[4 * pl + 1] = dsh[4 * pl + 2] = dsh[4 * pl + 3] = 0.f;
+    }
     float dmx = 0.f, dmy = 0.f, dmz = 0.f, dlogit = 0.f;
     float gsum[3] = {0.f, 0.f, 0.f};  // relit: colour gradient summed over the views
     float D00 = 0.f, D01 = 0.f, D02 = 0.f, D11 = 0.f, D12 = 0.f, D22 = 0.f;  // dSigma + dSigma^T
@@ -414,14 +422,17 @@ k_project_bwd(const float4* __restrict__ P, int64_t n, int64_t n_out, Dyn dyn, c
         for (int pl = 0; pl < NPL; ++pl) {
             const float4 c4 = s_sh[LIT ? 0 : pl][threadIdx.x];
             const float cv[4] = {c4.x, c4.y, c4.z, c4.w};
+            float4 d4 = s_dsh[LIT ? 0 : pl][threadIdx.x];
+            float dv[4] = {d4.x, d4.y, d4.z, d4.w};
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
                 const int j = 4 * pl + e;
                 if (j >= 3 * NB) break;
                 const int k = j / 3, ch = j % 3;
-                dsh[j] += gm[ch] * Y[k] * (k == 0 ? G.L : 1.f);
+                dv[e] += gm[ch] * Y[k] * (k == 0 ? G.L : 1.f);
                 wsum[k] += gm[ch] * cv[e];
             }
+            s_dsh[LIT ? 0 : pl][threadIdx.x] = make_float4(dv[0], dv[1], dv[2], dv[3]);
         }
         float3 ddir = sh_basis_vjp<D>(dsd.x, dsd.y, dsd.z, wsum);
         if (G.moved) {  // the SH direction is R_g^T dir
@@ -554,7 +565,8 @@ k_project_bwd(const float4* __restrict__ P, int64_t n, int64_t n_out, Dyn dyn, c
     for (int pl = 0; pl < 12; ++pl) {
         float4 o = make_float4(0.f, 0.f, 0.f, 0.f);
         if (pl < NPL) {
-            o = make_float4(dsh[4 * pl], dsh[4 * pl + 1], dsh[4 * pl + 2], dsh[4 * pl + 3]);
+            o = LIT ? make_float4(dsh[4 * pl], dsh[4 * pl + 1], dsh[4 * pl + 2], dsh[4 * pl + 3])
+                    : s_dsh[LIT ? 0 : pl][threadIdx.x];
             // lanes beyond the 3*NB used coefficients carry no gradient
             if (4 * pl + 0 >= 3 * NB) o.x = 0.f;
             if (4 * pl + 1 >= 3 * NB) o.y = 0.f;
