@@ -438,7 +438,10 @@ k_raster_bwd(const float4* __restrict__ proj, const ViewInfo* __restrict__ vt, i
     // a fragment, R, enters the gradient only as dL/dC . R (dL/dC is fixed per
     // pixel), so the walk keeps that scalar X instead of R:
     //   dL/dalpha_j = T_j (dL/dC . c_j - X_j),  X_{j-1} = X_j + alpha_j (dL/dC . c_j - X_j).
-    float2 T[NP], dCr[NP], dCg[NP], dCb[NP], X[NP];
+    float2 T[NP], X[NP];
+    // dL/dC per pixel pair: read-only in the walk, kept in this thread's
+    // column of shared memory instead of 3 NP register pairs
+    __shared__ float2 s_dC[3][NP][NT];
     uint32_t last[PX];
     uint32_t mylast = 0;
     const int64_t HW = (int64_t)vi.width * vi.height;
@@ -460,7 +463,9 @@ k_raster_bwd(const float4* __restrict__ proj, const ViewInfo* __restrict__ vt, i
             }
         }
         T[p] = make_float2(t[0], t[1]);
-        dCr[p] = make_float2(r[0], r[1]); dCg[p] = make_float2(g[0], g[1]); dCb[p] = make_float2(b[0], b[1]);
+        s_dC[0][p][threadIdx.x] = make_float2(r[0], r[1]);
+        s_dC[1][p][threadIdx.x] = make_float2(g[0], g[1]);
+        s_dC[2][p][threadIdx.x] = make_float2(b[0], b[1]);
         X[p] = make_float2(r[0] * bg.x + g[0] * bg.y + b[0] * bg.z, r[1] * bg.x + g[1] * bg.y + b[1] * bg.z);
     }
     if (threadIdx.x == 0) s_max = 0;
@@ -541,11 +546,13 @@ k_raster_bwd(const float4* __restrict__ proj, const ViewInfo* __restrict__ vt, i
                                               v1 ? T[p].y * rcp_approx(om.y) : T[p].y);
                 T[p] = Tj;
                 const float2 w = __fmul2_rn(al, Tj);
-                g6 = __ffma2_rn(w, dCr[p], g6);
-                g7 = __ffma2_rn(w, dCg[p], g7);
-                g8 = __ffma2_rn(w, dCb[p], g8);
+                const float2 dCr = s_dC[0][p][threadIdx.x], dCg = s_dC[1][p][threadIdx.x],
+                             dCb = s_dC[2][p][threadIdx.x];
+                g6 = __ffma2_rn(w, dCr, g6);
+                g7 = __ffma2_rn(w, dCg, g7);
+                g8 = __ffma2_rn(w, dCb, g8);
                 // e = dL/dC . (c - R)
-                const float2 e = __ffma2_rn(dCb[p], cb, __ffma2_rn(dCg[p], cg, __ffma2_rn(dCr[p], cr, __fmul2_rn(X[p], m1))));
+                const float2 e = __ffma2_rn(dCb, cb, __ffma2_rn(dCg, cg, __ffma2_rn(dCr, cr, __fmul2_rn(X[p], m1))));
                 const float2 dal = __fmul2_rn(Tj, e);
                 X[p] = __ffma2_rn(al, e, X[p]);
                 // dL/dP = dL/dalpha * alpha where alpha is not clamped
