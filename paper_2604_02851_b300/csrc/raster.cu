@@ -393,10 +393,11 @@ __device__ __forceinline__ float rcp_approx(float x) {
 // A thread's pixels share one row (one dy): it keeps sum dP, sum dP dx and
 // sum dP dx^2 per pixel and forms S2, S4, S5 with its dy once per fragment.
 // Blocks per SM the adjoint is compiled for: with 8-pixel strips (one warp
-// per tile) the register budget is set so that 24 tiles fit on an SM, with
+// per tile) the register budget is set so that 26 tiles fit on an SM (78
+// registers; 24, 28 and 30 measured: 30 falls off a spill cliff), with
 // 4-pixel strips 1024 threads.
 template <int B, int TPR>
-constexpr int bwd_min_blocks() { return B * TPR == 32 ? 24 : 1024 / (B * TPR); }
+constexpr int bwd_min_blocks() { return B * TPR == 32 ? 26 : 1024 / (B * TPR); }
 
 template <int B, int TPR, bool COARSE>
 __global__ void __launch_bounds__(B * TPR, bwd_min_blocks<B, TPR>())
