@@ -376,11 +376,9 @@ k_project_bwd(const float4* __restrict__ P, int64_t n, int64_t n_out, Dyn dyn, c
     // view-dependent colour: the SH gradient accumulates in shared memory
     // (this thread's column), next to the coefficients
     __shared__ float4 s_dsh[LIT ? 1 : NPL][128];
-    float dsh[NPL * 4];
+    if (!LIT) {
 #pragma unroll
-    for (int pl = 0; pl < NPL; ++pl) {
-        if (!LIT) s_dsh[pl][threadIdx.x] = make_float4(0.f, 0.f, 0.f, 0.f);
-        dsh[4 * pl] = dsh[4 * pl + 1] = dsh[4 * pl + 2] = dsh[4 * pl + 3] = 0.f;
+        for (int pl = 0; pl < NPL; ++pl) s_dsh[pl][threadIdx.x] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
     float dmx = 0.f, dmy = 0.f, dmz = 0.f, dlogit = 0.f;
     float gsum[3] = {0.f, 0.f, 0.f};  // relit: colour gradient summed over the views
@@ -495,12 +493,6 @@ k_project_bwd(const float4* __restrict__ P, int64_t n, int64_t n_out, Dyn dyn, c
         dmy += W[1] * dtx + W[4] * dty + W[7] * dtz;
         dmz += W[2] * dtx + W[5] * dty + W[8] * dtz;
     }
-    if (LIT) {
-        const float* lt = lit_row(dyn, g);
-        const float lv = lit_vis(dyn, g);
-#pragma unroll
-        for (int j = 0; j < 3 * NB; ++j) dsh[j] = gsum[j % 3] * (__ldg(&lt[j]) + lv * __ldg(&lt[48 + j]));
-    }
     if (G.moved) {  // back to the object frame: mean_w = R_g mean + t_g, Sigma_w = R_g Sigma R_g^T
         const float* Rg = G.Rg;
         const float m0 = dmx, m1 = dmy, m2 = dmz;
@@ -561,12 +553,25 @@ k_project_bwd(const float4* __restrict__ P, int64_t n, int64_t n_out, Dyn dyn, c
     dP[g] = o0;
     dP[n + g] = o1;
     dP[2 * n + g] = o2;
+    // relit: coefficient j's gradient is the summed colour gradient times
+    // its transfer weight (environment + visible direct light), formed here
+    const float* lt = LIT ? lit_row(dyn, g) : nullptr;
+    const float lv = LIT ? lit_vis(dyn, g) : 0.f;
 #pragma unroll
     for (int pl = 0; pl < 12; ++pl) {
         float4 o = make_float4(0.f, 0.f, 0.f, 0.f);
         if (pl < NPL) {
-            o = LIT ? make_float4(dsh[4 * pl], dsh[4 * pl + 1], dsh[4 * pl + 2], dsh[4 * pl + 3])
-                    : s_dsh[LIT ? 0 : pl][threadIdx.x];
+            if (LIT) {
+                float ov[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int j = 4 * pl + e;
+                    ov[e] = j < 3 * NB ? gsum[j % 3] * (__ldg(&lt[j]) + lv * __ldg(&lt[48 + j])) : 0.f;
+                }
+                o = make_float4(ov[0], ov[1], ov[2], ov[3]);
+            } else {
+                o = s_dsh[LIT ? 0 : pl][threadIdx.x];
+            }
             // lanes beyond the 3*NB used coefficients carry no gradient
             if (4 * pl + 0 >= 3 * NB) o.x = 0.f;
             if (4 * pl + 1 >= 3 * NB) o.y = 0.f;
