@@ -6,9 +6,10 @@
 // it is rendered from the Gaussians: texel (i, j) keeps the smallest light
 // depth of the Gaussians whose splat alpha o exp(-q/2) at the texel centre
 // reaches alpha_min.  Each lane sets up one Gaussian's footprint, then the
-// warp splats its 32 Gaussians in turn, the lanes striding over the texels of
-// each bounding box and merging depths with a float atomic min, so the map
-// does not depend on the order of the Gaussians.
+// warp splats its 32 Gaussians in turn, each lane walking columns of the
+// bounding box with the quadratic stepped row by row, and merging depths with
+// a float atomic min, so the map does not depend on the order of the
+// Gaussians.
 #include "gauss.cuh"
 
 namespace gs {
@@ -87,7 +88,7 @@ __device__ __forceinline__ bool light_splat(const float4* __restrict__ P, int64_
 }
 
 // Each lane sets up one Gaussian's footprint; the warp then walks the
-// footprints one after another, its lanes striding over the texels of each.
+// footprints one after another, its lanes taking the footprint's columns.
 __global__ void __launch_bounds__(256)
 k_light_depth(const float4* __restrict__ P, int64_t n, Dyn dyn, gs_light_camera lc, float* __restrict__ depth) {
     const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -104,18 +105,22 @@ k_light_depth(const float4* __restrict__ P, int64_t n, Dyn dyn, gs_light_camera 
         const float C = __shfl_sync(0xffffffffu, mine.C, src);
         const int i0 = __shfl_sync(0xffffffffu, mine.i0, src), j0 = __shfl_sync(0xffffffffu, mine.j0, src);
         const int nw = __shfl_sync(0xffffffffu, mine.nw, src), nh = __shfl_sync(0xffffffffu, mine.nh, src);
-        const int total = nw * nh;  // <= 16384^2
-        // texel t = lane + 32 k of the box, row-major; (i, j) advance by 32
-        // texels without a division per step
-        int j = lane / nw, i = lane - j * nw;
-        const int dj = 32 / nw, di = 32 - dj * nw;
-        for (int t = lane; t < total; t += 32) {
-            const float dx = (float)(i0 + i) + 0.5f - u, dy = (float)(j0 + j) + 0.5f - v;
-            const float q = A * dx * dx + 2.f * B * dx * dy + C * dy * dy;
-            if (q <= tau) atomic_min_float(depth + (int64_t)(j0 + j) * lc.width + (i0 + i), z);
-            i += di;
-            j += dj;
-            if (i >= nw) { i -= nw; ++j; }
+        // lane l walks the columns l, l + 32, ... of the box top to bottom,
+        // stepping the quadratic by rows: q(dy + 1) = q + 2 B dx + C (2 dy + 1)
+        // (rounding differences at q ~ tau decide a boundary texel either way)
+        const float twoB = 2.f * B;
+        for (int ci = lane; ci < nw; ci += 32) {
+            const float dx = (float)(i0 + ci) + 0.5f - u;
+            float dy = (float)j0 + 0.5f - v;
+            float q = (A * dx + twoB * dy) * dx + C * dy * dy;
+            const float qx = twoB * dx + C;  // row step is qx + 2 C dy
+            float* texel = depth + (int64_t)j0 * lc.width + (i0 + ci);
+            for (int r = 0; r < nh; ++r) {
+                if (q <= tau) atomic_min_float(texel, z);
+                q += qx + 2.f * C * dy;
+                dy += 1.f;
+                texel += lc.width;
+            }
         }
     }
 }
