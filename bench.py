@@ -108,7 +108,7 @@ def phase_model(n, V, K, total_tiles, npix, sum_nc, n_changed, binning, passes, 
 # capture at full size; profiles/train_step_1M_8x720p_traffic.md), valid while
 # the kernel's source file is unchanged (first 12 hex digits of its SHA-1).
 MEASURED_TRAFFIC = {
-    ("c3_1M_8x720p", "k_raster_bwd"): (253.6e6, "csrc/raster.cu", "271092883bd6"),
+    ("c3_1M_8x720p", "k_raster_bwd"): (252.9e6, "csrc/raster.cu", "a344e179321a"),
 }
 
 

@@ -171,7 +171,10 @@ k_render_fwd(const float4* __restrict__ proj, const ViewInfo* __restrict__ vt, i
     constexpr int PX = B / TPR;        // pixels per thread
     constexpr int NP = PX / 2;         // pixel pairs per thread
     static_assert(NT % 32 == 0 && PX % 2 == 0, "whole warps, pixel pairs");
-    constexpr int BATCH = 2 * NT;      // fragments staged per round
+    // fragments staged per round: two slots a thread for expanded lists,
+    // one for chunk bitmaps (a chunk holds ~37 of a tile's candidates)
+    constexpr int SLOTS = COARSE ? 1 : 2;
+    constexpr int BATCH = SLOTS * NT;
     constexpr int NW = NT / 32;
     __shared__ float4 s_a[BATCH];      // u, v, opacity, log2 cut-off
     __shared__ float4 s_q[BATCH];      // base-2 conic coefficients
@@ -217,11 +220,11 @@ k_render_fwd(const float4* __restrict__ proj, const ViewInfo* __restrict__ vt, i
     // tile are staged in list order, then composited.
     auto round = [&](int nslot, auto item) {
         // stage the fragments of this round that reach the tile, in list order
-        float4 ra[2], rq[2], rc[2];
-        bool keep[2];
-        uint32_t ipos[2];
+        float4 ra[SLOTS], rq[SLOTS], rc[SLOTS];
+        bool keep[SLOTS];
+        uint32_t ipos[SLOTS];
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
+        for (int h = 0; h < SLOTS; ++h) {
             const int slot = (int)threadIdx.x + h * NT;
             keep[h] = false;
             if (slot < nslot) {
@@ -235,24 +238,29 @@ k_render_fwd(const float4* __restrict__ proj, const ViewInfo* __restrict__ vt, i
                 keep[h] = reaches_tile(ra[h], rq[h], tx0, tx0 + (float)(B - 1), ty0, ty0 + (float)(B - 1));
             }
         }
-        const uint32_t m0 = __ballot_sync(0xFFFFFFFFu, keep[0]), m1 = __ballot_sync(0xFFFFFFFFu, keep[1]);
-        if (lane == 0) { s_wcnt[warp] = __popc(m0); s_wcnt[NW + warp] = __popc(m1); }
-        __syncthreads();
-        int cnt = 0, off0 = 0, off1 = 0;
+        uint32_t m[SLOTS];
 #pragma unroll
-        for (int w = 0; w < 2 * NW; ++w) {
-            if (w < warp) off0 += s_wcnt[w];
-            if (w < NW + warp) off1 += s_wcnt[w];
+        for (int h = 0; h < SLOTS; ++h) {
+            m[h] = __ballot_sync(0xFFFFFFFFu, keep[h]);
+            if (lane == 0) s_wcnt[h * NW + warp] = __popc(m[h]);
+        }
+        __syncthreads();
+        int cnt = 0, off[SLOTS];
+#pragma unroll
+        for (int h = 0; h < SLOTS; ++h) off[h] = 0;
+#pragma unroll
+        for (int w = 0; w < SLOTS * NW; ++w) {
+#pragma unroll
+            for (int h = 0; h < SLOTS; ++h)
+                if (w < h * NW + warp) off[h] += s_wcnt[w];
             cnt += s_wcnt[w];
         }
         const uint32_t ltm = (1u << lane) - 1u;
-        if (keep[0]) {
-            const int d = off0 + __popc(m0 & ltm);
-            s_a[d] = ra[0]; s_q[d] = rq[0]; s_c[d] = rc[0]; s_pos[d] = ipos[0];
-        }
-        if (keep[1]) {
-            const int d = off1 + __popc(m1 & ltm);
-            s_a[d] = ra[1]; s_q[d] = rq[1]; s_c[d] = rc[1]; s_pos[d] = ipos[1];
+#pragma unroll
+        for (int h = 0; h < SLOTS; ++h) {
+            if (!keep[h]) continue;
+            const int d = off[h] + __popc(m[h] & ltm);
+            s_a[d] = ra[h]; s_q[d] = rq[h]; s_c[d] = rc[h]; s_pos[d] = ipos[h];
         }
         __syncthreads();
         for (int j = 0; j < cnt && nlive; ++j) {
