@@ -267,6 +267,25 @@ gs_status_t gs_light_depth_map(gs_ctx* ctx, const gs_scene* scene, const gs_ligh
  * is at most depth[floor(v)][floor(u)] + bias, else 0.  No workspace. */
 gs_status_t gs_light_visibility(gs_ctx* ctx, const gs_scene* scene, const gs_light_camera* lcam,
                                 const float* depth, uint8_t* visibility, void* stream);
+/* Bound of every wait of one block on another in the context's kernels
+ * (the look-backs of the onesweep sort passes and of the key emission), in
+ * SM clock cycles counted from the start of the wait; 0 restores the default
+ * of 2e9 cycles (about one second at 2 GHz).  A wait that runs out records
+ * GS_ERR_TIMEOUT in the status word, its block publishes what it has and
+ * skips its scatter, and the kernel returns: results of that call are then
+ * incomplete, never out of bounds.  Read by calls enqueued later; a graph
+ * keeps the value it was captured with.  GS_ERR_ARG for cycles < 0. */
+gs_status_t gs_ctx_set_wait_limit(gs_ctx* ctx, int64_t cycles);
+/* Test hook of the bounded waits (failure detection without a GPU fault):
+ * with tile >= 0, the next gs_bin_sort calls of this context with direct
+ * binning (GS_BINNING_DIRECT) run the last pass of their tile-key sort with
+ * onesweep tile `tile` withholding its digit counts, a flag that nothing
+ * else sets, so that the waits of the tiles after it run out
+ * (GS_ERR_TIMEOUT).  Only that pass is affected: its output goes to the
+ * caller's arrays, which no later kernel of the call reads, and those arrays
+ * are then incomplete.  Two-level binning and the fused calls ignore the
+ * hook.  -1 (the default) turns it off; GS_ERR_ARG below -1. */
+gs_status_t gs_ctx_set_wait_test(gs_ctx* ctx, int64_t tile);
 /* Reads and clears the device status word (synchronises `stream`).
  * *status receives the first error a kernel recorded since the last read
  * (GS_OK if none); *detail receives the required size for GS_ERR_CAPACITY. */
@@ -286,13 +305,22 @@ int64_t gs_total_tiles(const gs_ctx* ctx, const gs_camera* host_cams, int32_t n_
  * Jacobian J of the pinhole map at t (x/z, y/z clamped to 1.3 tan(fov/2));
  * Sigma2D = J R Sigma R^T J^T + 0.3 I; conic = Sigma2D^-1; radius =
  * ceil(3 sqrt(lambda_max)), lambda_max = mid + sqrt(max(0.1, mid^2 - det));
- * tile rectangle of that square; rgb = SH(dir) + 0.5 clamped at 0;
- * opacity = sigmoid(logit).  Culled: z <= near, det <= 0, or empty rect.
+ * tile rectangle: the tiles [floor((u - r) / B), floor((u + r + B - 1) / B))
+ * (likewise in v) of the square of half-side r, cut to the tiles that hold
+ * a pixel centre inside the bounding box of the ellipse where alpha reaches
+ * 1/255 (half-widths sqrt(tau a), sqrt(tau c), tau = 2 ln(255 o), for the
+ * 2D covariance (a, b; b, c), widened by 0.1 % + 0.01 px; none when
+ * o < 1/255): every pixel the square's compositing takes the splat at lies
+ * inside, so images and gradients are those of the square;
+ * rgb = SH(dir) + 0.5 clamped at 0; opacity = sigmoid(logit).  Culled:
+ * z <= near, det <= 0, or empty rect.
  * d_cams: device gs_camera[V].  Writes proj [V][n][16]. */
 gs_status_t gs_project(gs_ctx* ctx, const gs_scene* scene, const gs_camera* d_cams,
                        int32_t n_views, float* proj, void* stream);
 
-/* Tile binning + radix sort: every (view, Gaussian, touched tile) becomes one
+/* Tile binning + radix sort (Sec. 3.2.3: the model is refit by the
+ * differentiable tile rasterisation of the cited 3DGS method, whose per-tile
+ * lists are depth-sorted): every (view, Gaussian, touched tile) becomes one
  * (tile key, Gaussian index) entry, ordered by (view, tile, float32 depth,
  * Gaussian index); then per-tile [start, end) ranges.  Implemented as a
  * stable depth sort of the V*n projected Gaussians followed by a stable
@@ -308,8 +336,10 @@ gs_status_t gs_bin_sort(gs_ctx* ctx, const float* proj, const gs_camera* d_cams,
                         uint32_t* sorted_keys, uint32_t* sorted_vals, uint32_t* ranges,
                         uint32_t* d_num_keys, void* stream);
 
-/* Front-to-back alpha compositing per pixel over its tile's sorted list:
- * alpha = min(0.99, o exp(P)), P = -(A dx^2 + C dy^2)/2 - B dx dy, skipped
+/* Front-to-back alpha compositing per pixel over its tile's sorted list
+ * (Sec. 3.1: the optimiser "renders the present Gaussian model from those
+ * viewpoints"; Sec. 3.2.3: the cited 3DGS method's differentiable
+ * rasteriser): alpha = min(0.99, o exp(P)), P = -(A dx^2 + C dy^2)/2 - B dx dy, skipped
  * when P > 0 or alpha < 1/255; stops before the fragment that would take
  * T below 1e-4.  image = sum c alpha T + T_final * bg.  n_contrib = 1-based
  * list position of the last fragment added (0 if none).
@@ -333,9 +363,11 @@ gs_status_t gs_loss(gs_ctx* ctx, const float* image, const float* target, int32_
 
 /* --------------------------------------------------------------- backward */
 
-/* Reverse-order adjoint of gs_render_fwd: per pixel, walks its list back from
- * n_contrib, recovering each T_j from T_final (no per-fragment state is
- * stored), and accumulates dL/d(u, v, A, B, C, opacity, rgb) per (view,
+/* Reverse-order adjoint of gs_render_fwd (Sec. 3.2.3: the parameters are
+ * refit by gradient descent through the differentiable rasteriser; Sec. 3.1:
+ * "compares the result ... and updates the trainable Gaussian parameters"):
+ * per pixel, walks its list back from n_contrib, recovering each T_j from
+ * T_final (no per-fragment state is stored), and accumulates dL/d(u, v, A, B, C, opacity, rgb) per (view,
  * Gaussian) into grad2d (which it first zeroes). */
 gs_status_t gs_raster_bwd(gs_ctx* ctx, const float* proj, const gs_camera* d_cams,
                           int32_t n_views, int64_t n, int64_t total_tiles,
@@ -344,14 +376,18 @@ gs_status_t gs_raster_bwd(gs_ctx* ctx, const float* proj, const gs_camera* d_cam
                           const uint32_t* n_contrib, const float* dimage, float* grad2d,
                           void* stream);
 
-/* Adjoint of gs_project: grad2d of every view -> parameter gradients
- * dparams [15][n][4], summed over views (accumulate != 0 adds to dparams,
+/* Adjoint of gs_project (Sec. 3.2.3: gradients of the 3DGS parameters --
+ * mean, scale, rotation, opacity, SH coefficients -- through the EWA
+ * projection and the SH colour of Sec. 3.2.2 / 3.4.1): grad2d of every view
+ * -> parameter gradients dparams [15][n][4], summed over views (accumulate != 0 adds to dparams,
  * else overwrites).  Zero through clamps, culls and rounding steps. */
 gs_status_t gs_project_bwd(gs_ctx* ctx, const gs_scene* scene, const gs_camera* d_cams,
                            int32_t n_views, const float* proj, const float* grad2d,
                            float* dparams, int32_t accumulate, void* stream);
 
-/* gs_raster_bwd followed by gs_project_bwd (overwriting dparams). */
+/* gs_raster_bwd followed by gs_project_bwd (overwriting dparams): the
+ * gradient of the loss with respect to every trainable parameter of the
+ * current model (Sec. 3.1, 3.2.3). */
 gs_status_t gs_render_bwd(gs_ctx* ctx, const gs_scene* scene, const gs_camera* d_cams,
                           int32_t n_views, int64_t total_tiles, const float* proj,
                           const uint32_t* sorted_vals,
@@ -442,7 +478,10 @@ gs_status_t gs_apply_delta(gs_ctx* ctx, float* params, int64_t n, const uint8_t*
  * All calls on a device share the array (its old contents never matter, so
  * nothing is cleared); calls that overlap on the GPU race and must not be
  * issued.  The first call on a device looks the array's address up with that
- * device current; make it outside any stream capture. */
+ * device current and keeps it for the life of the process; make that call
+ * outside any stream capture.  The kept address belongs to the device's
+ * primary context: after that context is reset (cudaDeviceReset) or torn
+ * down and created again, it is stale and the call must not be used. */
 gs_status_t gs_extract_delta_noalloc(const float* theta, float* baseline, int64_t n, float thr,
                                      uint32_t* d_idx, uint8_t* d_records, uint32_t* d_count,
                                      void* stream);

@@ -27,6 +27,7 @@ _I32 = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
 _U32 = np.ctypeslib.ndpointer(dtype=np.uint32, flags="C_CONTIGUOUS")
 _U64 = np.ctypeslib.ndpointer(dtype=np.uint64, flags="C_CONTIGUOUS")
 _U8 = np.ctypeslib.ndpointer(dtype=np.uint8, flags="C_CONTIGUOUS")
+_I64 = np.ctypeslib.ndpointer(dtype=np.int64, flags="C_CONTIGUOUS")
 
 TILE = 16
 PROJ_FIELDS = ("u", "v", "depth", "opacity", "A", "B", "C", "radius", "r", "g", "b",
@@ -58,6 +59,10 @@ def lib():
         L.or_bin_count.restype = C.c_int64
         L.or_bin_sort.argtypes = [C.c_int, C.c_int64, _D, C.c_int, _I32, _F, _U64, _U32, _U32]
         L.or_bin_sort.restype = C.c_int64
+        L.or_bin_ranges.argtypes = [C.c_int, C.c_int64, _D, C.c_int, _I32, _U32]
+        L.or_bin_ranges.restype = C.c_int64
+        L.or_bin_tiles.argtypes = [C.c_int, C.c_int64, _D, C.c_int, _I32, _F, C.c_int64, _I64, C.c_void_p, _I64]
+        L.or_bin_tiles.restype = C.c_int64
         L.or_render.argtypes = [C.c_int, C.c_int64, _D, C.c_int, _D, _U32, _U32, _D, _D, _D, _I32]
         L.or_render_bwd.argtypes = [C.c_int, C.c_int64, _D, C.c_int, _D, _U32, _U32, _D, _D, _D]
         L.or_project_bwd.argtypes = [C.c_int64, C.c_int, _D, C.c_int, _D, C.c_int, _D, _D]
@@ -266,6 +271,31 @@ def bin_sort(cams: dict, rects, depth32, tile: int = TILE):
     ranges = np.zeros((n_tiles(cams, tile), 2), dtype=np.uint32)
     lib().or_bin_sort(V, n, cams_array(cams), tile, rects, depth32, keys, vals, ranges)
     return keys[:K], vals[:K], ranges
+
+
+def bin_ranges(cams: dict, rects, tile: int = TILE):
+    """rects [V][n][4] int32 -> (ranges [T][2] uint32 as bin_sort gives them, entry count),
+    without forming the entries."""
+    rects = np.ascontiguousarray(rects, dtype=np.int32)
+    V, n = rects.shape[:2]
+    ranges = np.zeros((n_tiles(cams, tile), 2), dtype=np.uint32)
+    K = int(lib().or_bin_ranges(V, n, cams_array(cams), tile, rects, ranges))
+    return ranges, K
+
+
+def bin_tiles(cams: dict, rects, depth32, tiles, tile: int = TILE):
+    """The sorted lists of the given global tiles only -> (vals u32, start int64 [len(tiles) + 1]):
+    tile i's Gaussians, in bin_sort's order, are vals[start[i]:start[i + 1]]."""
+    rects = np.ascontiguousarray(rects, dtype=np.int32)
+    depth32 = np.ascontiguousarray(depth32, dtype=np.float32)
+    req = np.ascontiguousarray(tiles, dtype=np.int64)
+    V, n = depth32.shape
+    start = np.zeros(len(req) + 1, dtype=np.int64)
+    cams_a = cams_array(cams)
+    total = int(lib().or_bin_tiles(V, n, cams_a, tile, rects, depth32, len(req), req, None, start))
+    vals = np.zeros(max(total, 1), dtype=np.uint32)
+    lib().or_bin_tiles(V, n, cams_a, tile, rects, depth32, len(req), req, vals.ctypes.data_as(C.c_void_p), start)
+    return vals[:total], start
 
 
 def render(cams: dict, proj, vals, ranges, bg=(0.0, 0.0, 0.0), tile: int = TILE):

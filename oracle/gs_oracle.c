@@ -517,6 +517,110 @@ int64_t or_bin_sort(int V, int64_t n, const double* cams, int tile, const int32_
     return K;
 }
 
+/* The [start, end) range of every tile in the order above, without forming
+ * the entries: a tile's run length is the number of (view, Gaussian) whose
+ * rectangle holds it, and runs follow each other in tile order (empty tiles
+ * (0, 0)), exactly as or_bin_sort writes them.  Returns the entry count. */
+int64_t or_bin_ranges(int V, int64_t n, const double* cams, int tile, const int32_t* rects, uint32_t* ranges) {
+    int64_t T = 0;
+    for (int v = 0; v < V; ++v) {
+        const double* cam = cams + (int64_t)v * CAM_STRIDE;
+        T += (int64_t)tiles_along((int)cam[16], tile) * tiles_along((int)cam[17], tile);
+    }
+    int64_t* count = (int64_t*)calloc((size_t)(T > 0 ? T : 1), sizeof(int64_t));
+    int64_t toff = 0;
+    for (int v = 0; v < V; ++v) {
+        const double* cam = cams + (int64_t)v * CAM_STRIDE;
+        int TX = tiles_along((int)cam[16], tile), TY = tiles_along((int)cam[17], tile);
+        for (int64_t g = 0; g < n; ++g) {
+            const int32_t* r = rects + ((int64_t)v * n + g) * 4;
+            for (int ty = r[1]; ty < r[3]; ++ty)
+                for (int tx = r[0]; tx < r[2]; ++tx) count[toff + (int64_t)ty * TX + tx] += 1;
+        }
+        toff += (int64_t)TX * TY;
+    }
+    int64_t run = 0;
+    for (int64_t t = 0; t < T; ++t) {
+        ranges[2 * t] = count[t] ? (uint32_t)run : 0u;
+        ranges[2 * t + 1] = count[t] ? (uint32_t)(run + count[t]) : 0u;
+        run += count[t];
+    }
+    free(count);
+    return run;
+}
+
+/* The sorted entries of some tiles only: for each global tile index req[i],
+ * the Gaussians whose rectangle holds that tile, ordered as in or_bin_sort
+ * (float32 depth bits, then Gaussian index), appended to vals; tile i's run
+ * is vals[start[i], start[i + 1]).  With vals == NULL only start is filled.
+ * Returns the total. */
+typedef struct { uint32_t d; uint32_t g; } tile_entry;
+
+static int cmp_tile_entry(const void* A, const void* B) {
+    const tile_entry* a = (const tile_entry*)A;
+    const tile_entry* b = (const tile_entry*)B;
+    if (a->d != b->d) return a->d < b->d ? -1 : 1;
+    return a->g < b->g ? -1 : (a->g > b->g ? 1 : 0);
+}
+
+/* view, column and row of global tile t (-1 view when t is out of range) */
+static int tile_place(int V, const double* cams, int tile, int64_t t, int* tx, int* ty) {
+    int64_t toff = 0;
+    for (int v = 0; v < V; ++v) {
+        const double* cam = cams + (int64_t)v * CAM_STRIDE;
+        int TX = tiles_along((int)cam[16], tile), TY = tiles_along((int)cam[17], tile);
+        if (t < toff + (int64_t)TX * TY) {
+            *tx = (int)((t - toff) % TX);
+            *ty = (int)((t - toff) / TX);
+            return v;
+        }
+        toff += (int64_t)TX * TY;
+    }
+    return -1;
+}
+
+int64_t or_bin_tiles(int V, int64_t n, const double* cams, int tile, const int32_t* rects, const float* depth,
+                     int64_t n_req, const int64_t* req, uint32_t* vals, int64_t* start) {
+    int64_t* cnt = (int64_t*)calloc((size_t)(n_req > 0 ? n_req : 1), sizeof(int64_t));
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t i = 0; i < n_req; ++i) {
+        int tx = 0, ty = 0;
+        int v = tile_place(V, cams, tile, req[i], &tx, &ty);
+        if (v < 0) continue;
+        int64_t c = 0;
+        for (int64_t g = 0; g < n; ++g) {
+            const int32_t* r = rects + ((int64_t)v * n + g) * 4;
+            if (tx >= r[0] && tx < r[2] && ty >= r[1] && ty < r[3]) ++c;
+        }
+        cnt[i] = c;
+    }
+    start[0] = 0;
+    for (int64_t i = 0; i < n_req; ++i) start[i + 1] = start[i] + cnt[i];
+    if (vals) {
+#pragma omp parallel for schedule(dynamic, 1)
+        for (int64_t i = 0; i < n_req; ++i) {
+            int tx = 0, ty = 0;
+            int v = tile_place(V, cams, tile, req[i], &tx, &ty);
+            if (v < 0 || cnt[i] == 0) continue;
+            tile_entry* E = (tile_entry*)malloc(sizeof(tile_entry) * (size_t)cnt[i]);
+            int64_t k = 0;
+            for (int64_t g = 0; g < n; ++g) {
+                const int32_t* r = rects + ((int64_t)v * n + g) * 4;
+                if (tx >= r[0] && tx < r[2] && ty >= r[1] && ty < r[3]) {
+                    memcpy(&E[k].d, &depth[(int64_t)v * n + g], 4);
+                    E[k].g = (uint32_t)g;
+                    ++k;
+                }
+            }
+            qsort(E, (size_t)k, sizeof(tile_entry), cmp_tile_entry);
+            for (int64_t j = 0; j < k; ++j) vals[start[i] + j] = E[j].g;
+            free(E);
+        }
+    }
+    free(cnt);
+    return start[n_req];
+}
+
 /* ------------------------------------------------------------------------
  * Front-to-back alpha compositing (Sec. 3.2.3 differentiable rendering, as in
  * the cited method).  Per pixel, in sorted order, from T = 1:

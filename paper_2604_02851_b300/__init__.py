@@ -113,6 +113,14 @@ class Context:
         return {"binning": names[v[0].value], "sort_bits": v[1].value, "sort_items": v[2].value,
                 "raster_threads": v[3].value, "raster_bwd_threads": v[4].value}
 
+    def set_wait_limit(self, cycles: int) -> None:
+        """Bound of every inter-block wait in clock cycles (0: the default)."""
+        check("gs_ctx_set_wait_limit", _lib.lib().gs_ctx_set_wait_limit(self.ptr, int(cycles)))
+
+    def set_wait_test(self, tile: int) -> None:
+        """Test hook of the bounded waits (gs_ctx_set_wait_test); -1 turns it off."""
+        check("gs_ctx_set_wait_test", _lib.lib().gs_ctx_set_wait_test(self.ptr, int(tile)))
+
     def reserve(self, nbytes: int) -> None:
         check("gs_ctx_reserve", _lib.lib().gs_ctx_reserve(self.ptr, int(nbytes)))
 

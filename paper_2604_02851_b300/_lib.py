@@ -19,7 +19,7 @@ STATUS_NAMES = {0: "GS_OK", 1: "GS_ERR_ARG", 2: "GS_ERR_CAPACITY", 3: "GS_ERR_CU
 # every symbol include/gs.h declares
 EXPORTS = (
     "gs_ctx_create", "gs_ctx_destroy", "gs_ctx_reserve", "gs_ctx_set_tile", "gs_ctx_set_sort_bits", "gs_ctx_set_sort_items", "gs_ctx_set_binning", "gs_ctx_set_raster_threads",
-    "gs_ctx_set_raster_bwd_threads", "gs_ctx_get_tuning",
+    "gs_ctx_set_raster_bwd_threads", "gs_ctx_get_tuning", "gs_ctx_set_wait_limit", "gs_ctx_set_wait_test",
     "gs_get_status", "gs_workspace_size", "gs_total_tiles", "gs_project", "gs_bin_sort",
     "gs_render_fwd", "gs_loss", "gs_raster_bwd", "gs_project_bwd", "gs_render_bwd",
     "gs_adam_step", "gs_extract_delta", "gs_render_batch", "gs_train_step",
@@ -112,6 +112,8 @@ _SIGS = {
     "gs_ctx_set_binning": [_P, _I32],
     "gs_ctx_set_raster_threads": [_P, _I32],
     "gs_ctx_set_raster_bwd_threads": [_P, _I32],
+    "gs_ctx_set_wait_limit": [_P, _I64],
+    "gs_ctx_set_wait_test": [_P, _I64],
     "gs_ctx_get_tuning": [_P, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32),
                           C.POINTER(C.c_int32), C.POINTER(C.c_int32)],
     "gs_get_status": [_P, _P, C.POINTER(_I32), C.POINTER(_I64)],

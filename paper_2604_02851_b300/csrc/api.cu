@@ -117,6 +117,14 @@ gs_status_t check_ws(const gs_ctx* ctx, size_t need) {
     return need <= ctx->ws_bytes ? GS_OK : GS_ERR_CAPACITY;
 }
 
+// The context's wait bound without the test hook (fused calls read their
+// sorts' outputs).
+WaitCfg spin_only(const gs_ctx* ctx) {
+    WaitCfg w;
+    w.spin = ctx->wait_cycles;
+    return w;
+}
+
 }  // namespace
 
 extern "C" {
@@ -227,6 +235,18 @@ gs_status_t gs_ctx_set_raster_bwd_threads(gs_ctx* ctx, int32_t threads_per_row) 
     return GS_OK;
 }
 
+gs_status_t gs_ctx_set_wait_limit(gs_ctx* ctx, int64_t cycles) {
+    if (!ctx || cycles < 0) return GS_ERR_ARG;
+    ctx->wait_cycles = cycles == 0 ? kSpinCycles : (long long)cycles;
+    return GS_OK;
+}
+
+gs_status_t gs_ctx_set_wait_test(gs_ctx* ctx, int64_t tile) {
+    if (!ctx || tile < -1) return GS_ERR_ARG;
+    ctx->wait_test_tile = tile;
+    return GS_OK;
+}
+
 gs_status_t gs_ctx_get_tuning(const gs_ctx* ctx, int32_t* binning, int32_t* sort_bits, int32_t* sort_items,
                               int32_t* raster_threads, int32_t* raster_bwd_threads) {
     if (!ctx) return GS_ERR_ARG;
@@ -301,8 +321,12 @@ gs_status_t gs_bin_sort(gs_ctx* ctx, const float* proj, const gs_camera* d_cams,
     SortScratch s;
     carve_sort_scratch(ss, n_views, n, keys_cap, total_tiles, &s);
     launch_view_table(d_cams, n_views, ctx->tile, vt, total_tiles, ctx->d_status, S(stream));
+    WaitCfg wait;
+    wait.spin = ctx->wait_cycles;
+    wait.withhold = ctx->wait_test_tile;  // the test hook applies to this call only
     launch_bin_sort(proj, vt, n_views, n, keys_cap, total_tiles, ctx->binning, ctx->sort_bits, ctx->sort_items, s, false, sorted_keys,
-                    sorted_vals, ranges, d_num_keys, ctx->d_status, ctx->sm_count, S(stream));
+                    sorted_vals, ranges, d_num_keys, ctx->d_status, ctx->sm_count, S(stream), nullptr, nullptr, 0,
+                    false, nullptr, wait);
     return launch_check();
 }
 
@@ -467,7 +491,7 @@ gs_status_t gs_render_batch(gs_ctx* ctx, const gs_scene* scene, const gs_camera*
     CoarseLists cl;
     launch_bin_sort(p.proj, p.vt, n_requests, scene->n, keys_cap, total_tiles, ctx->binning, ctx->sort_bits, ctx->sort_items, s, true, nullptr,
                     p.vals, p.ranges, p.n_keys, ctx->d_status, ctx->sm_count, st, nullptr, nullptr, 0,
-                    scene->precull != nullptr, &cl);
+                    scene->precull != nullptr, &cl, spin_only(ctx));
     launch_render_fwd(p.proj, p.vt, n_requests, scene->n, ctx->tile, ctx->raster_tpr, p.vals, p.ranges, b, image, nullptr,
                       nullptr, total_tiles, st, &cl);
     return launch_check();
@@ -527,7 +551,7 @@ gs_status_t gs_train_step_events(gs_ctx* ctx, const gs_camera* d_cams, const gs_
     CoarseLists cl;
     launch_bin_sort(p.proj, p.vt, V, n, cfg->keys_cap, tt, ctx->binning, ctx->sort_bits, ctx->sort_items, s, true, nullptr,
                     p.vals, p.ranges, p.n_keys, ctx->d_status, ctx->sm_count, st, ev ? mark : nullptr, ev, 2,
-                    cfg->precull != nullptr, &cl);
+                    cfg->precull != nullptr, &cl, spin_only(ctx));
     mark(ev, 4, st);
     launch_render_fwd(p.proj, p.vt, V, n, B, ctx->raster_tpr, p.vals, p.ranges, b, io->image, p.T_final, p.n_contrib, tt,
                       st, &cl);
@@ -587,7 +611,7 @@ gs_status_t gs_autotune(gs_ctx* ctx, const gs_scene* scene, const gs_camera* d_c
         CoarseLists cl;
         launch_bin_sort(p.proj, p.vt, V, n, keys_cap, tt, ctx->binning, ctx->sort_bits, ctx->sort_items, s, true,
                         nullptr, p.vals, p.ranges, p.n_keys, ctx->d_status, ctx->sm_count, st, nullptr, nullptr, 0,
-                        scene->precull != nullptr, &cl);
+                        scene->precull != nullptr, &cl, spin_only(ctx));
         if (ev) cudaEventRecord(ev[0], st);
         launch_render_fwd(p.proj, p.vt, V, n, B, ctx->raster_tpr, p.vals, p.ranges, bg, image, p.T_final,
                           p.n_contrib, tt, st, &cl);

@@ -19,8 +19,11 @@
 //  - calls whose work overlaps on the GPU (different streams without an
 //    ordering between them) race on the shared array and must not be issued;
 //  - the first call on a device looks up the array's device address
-//    (cudaGetSymbolAddress, with that device current); make that first call
-//    outside any stream capture.
+//    (cudaGetSymbolAddress, with that device current) and keeps it for the
+//    life of the process; make that first call outside any stream capture;
+//  - the kept address belongs to the device's primary context: after a
+//    reset of that context (cudaDeviceReset) it is stale, and the call must
+//    not be used again in that process.
 #include <mutex>
 
 #include "gs_internal.cuh"

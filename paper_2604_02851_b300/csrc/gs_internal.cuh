@@ -61,8 +61,19 @@ __device__ __forceinline__ void record_status(DevStatus* s, int code, long long 
     if (atomicCAS(&s->code, 0, code) == 0) s->detail = detail;
 }
 
-// Spin bound for inter-block waits: about one second at 2 GHz.
+// Spin bound for inter-block waits: about one second at 2 GHz (the
+// context's default; gs_ctx_set_wait_limit changes it).
 constexpr long long kSpinCycles = 2000000000LL;
+
+// Bounded-wait settings passed to the kernels that wait on other blocks:
+// spin, the bound in clock cycles; withhold >= 0 (a test hook, honoured by
+// gs_bin_sort alone): onesweep tile `withhold` of the last pass of the direct
+// binning's tile-key sort publishes no digit counts, so that the waits of the
+// tiles after it run out.
+struct WaitCfg {
+    long long spin = kSpinCycles;
+    int64_t withhold = -1;
+};
 
 // ------------------------------------------------------------ launchers
 // Every launcher enqueues on `st`; none synchronises or allocates.
@@ -237,7 +248,8 @@ void launch_bin_sort(const float* proj, const ViewInfo* vt, int V, int64_t n, in
                      uint32_t* sorted_keys, uint32_t* sorted_vals, uint32_t* ranges,
                      uint32_t* d_num_keys, DevStatus* status, int sm_count, cudaStream_t st,
                      void (*mark)(void* const*, int, cudaStream_t) = nullptr, void* const* events = nullptr,
-                     int first_event = 0, bool compact = false, CoarseLists* coarse = nullptr);
+                     int first_event = 0, bool compact = false, CoarseLists* coarse = nullptr,
+                     WaitCfg wait = WaitCfg{});
 
 // tpr: threads per pixel row of a 16 x 16 tile (2 or 4); 8 x 8 tiles use 4.
 // Adjoint: Gaussians with index >= n_active (a frozen pool appended after the
@@ -325,6 +337,8 @@ struct gs_ctx {
     size_t ws_bytes = 0;
     gs::DevStatus* d_status = nullptr;
     float* d_light_tab = nullptr;   // [kMaxGroups][kLitTab] relighting table
+    long long wait_cycles = gs::kSpinCycles;  // bound of every inter-block wait
+    int64_t wait_test_tile = -1;              // gs_ctx_set_wait_test (test hook; -1: off)
     cudaStream_t capture_stream = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t graph_exec = nullptr;

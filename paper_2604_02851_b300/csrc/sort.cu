@@ -26,8 +26,8 @@
 // tile-key sort writes the values (and the keys only if asked) and records
 // each tile's [start, end) range with min/max atomics at run boundaries.
 // Blocks take work from atomic counters in launch order, so a waited-on tile
-// always belongs to a running block; every wait is bounded (about 1 s) and
-// reports GS_ERR_TIMEOUT.
+// always belongs to a running block; every wait is bounded (about 1 s by
+// default, the context's wait limit) and reports GS_ERR_TIMEOUT.
 #include <algorithm>
 
 #include "gs_internal.cuh"
@@ -64,11 +64,13 @@ __device__ __forceinline__ int64_t clamp_count(const uint32_t* d_count, int64_t 
 
 // Exclusive prefix of `mine` over the slots 0..slot-1 of a look-back array
 // whose slots hold (flag | count); publishes this slot's inclusive value.
-// Four predecessors are read per round trip.  Bounded: on time-out records
-// GS_ERR_TIMEOUT and returns false.
+// Four predecessors are read per round trip.  Bounded: when a round finds
+// no predecessor ready more than `spin` clock cycles after the wait began, it
+// records GS_ERR_TIMEOUT, publishes the partial inclusive value (so that
+// later slots need not wait as long) and returns false.
 __device__ __forceinline__ bool look_back(unsigned long long* lb, int64_t slot, int stride,
                                           unsigned long long mine, unsigned long long* excl_out,
-                                          DevStatus* status) {
+                                          DevStatus* status, long long spin) {
     unsigned long long excl = 0;
     bool ok = true;
     if (slot > 0) {
@@ -94,7 +96,7 @@ __device__ __forceinline__ bool look_back(unsigned long long* lb, int64_t slot, 
             // issue slots of the SM's other tiles (250 ns measured best of
             // 32-500 ns)
             if (used == 0) __nanosleep(250);
-            if (used == 0 && clock64() - t0 > kSpinCycles) {
+            if (used == 0 && clock64() - t0 > spin) {
                 record_status(status, GS_ERR_TIMEOUT, slot);
                 ok = false;
                 break;
@@ -165,7 +167,8 @@ __global__ void __launch_bounds__(kThreads, 3)
 k_onesweep(const uint64_t* __restrict__ in, uint64_t* __restrict__ out, uint32_t* __restrict__ kout,
            uint32_t* __restrict__ vout, const uint32_t* d_count, int64_t cap, int shift, uint32_t kmask,
            const uint32_t* __restrict__ digit_off, unsigned long long* __restrict__ lookback,
-           uint32_t* tile_counter, uint32_t* __restrict__ ranges, DevStatus* status) {
+           uint32_t* tile_counter, uint32_t* __restrict__ ranges, DevStatus* status, long long spin,
+           int64_t withhold) {
     constexpr int R = 1 << BITS;
     constexpr uint32_t MASK = R - 1;
     constexpr int TILE = kThreads * ITEMS;
@@ -187,6 +190,9 @@ k_onesweep(const uint64_t* __restrict__ in, uint64_t* __restrict__ out, uint32_t
         __syncthreads();
         const int64_t tile = s_tile;
         if (tile >= n_tiles) break;
+        // test hook (gs_ctx_set_wait_test): this tile publishes nothing and
+        // scatters nothing, so the look-backs of the tiles after it run out
+        const bool withheld = tile == withhold;
 
         // ---- load (warp-striped: warp w owns a contiguous run of 32*ITEMS);
         //      missing tail items get the all-ones key
@@ -230,7 +236,8 @@ k_onesweep(const uint64_t* __restrict__ in, uint64_t* __restrict__ out, uint32_t
             uint32_t acc = 0;
             for (int w = 0; w < kWarps; ++w) { const uint32_t c = s_whist[w][d]; s_whist[w][d] = acc; acc += c; }
             tile_cnt = acc;
-            st_volatile(lookback + tile * R + d, (tile == 0 ? kFlagInc : kFlagAgg) | (unsigned long long)tile_cnt);
+            if (!withheld)
+                st_volatile(lookback + tile * R + d, (tile == 0 ? kFlagInc : kFlagAgg) | (unsigned long long)tile_cnt);
             s_local[d] = tile_cnt;
         }
         __syncthreads();
@@ -261,7 +268,8 @@ k_onesweep(const uint64_t* __restrict__ in, uint64_t* __restrict__ out, uint32_t
         // ---- look back over preceding tiles, one thread per digit
         if (threadIdx.x < R) {
             unsigned long long excl = 0;
-            if (!look_back(lookback + threadIdx.x, tile, R, tile_cnt, &excl, status)) s_abort = 1;
+            if (withheld) s_abort = 1;
+            else if (!look_back(lookback + threadIdx.x, tile, R, tile_cnt, &excl, status, spin)) s_abort = 1;
             s_gbase[threadIdx.x] = digit_off[threadIdx.x] + (uint32_t)excl;
         }
         __syncthreads();
@@ -438,7 +446,7 @@ k_emit(const uint64_t* __restrict__ dsorted, int64_t total, int64_t n, const uin
        const ViewInfo* __restrict__ vt, int64_t cap, uint64_t* __restrict__ kv,
        unsigned long long* __restrict__ lookback, uint32_t* block_counter, uint32_t* d_num_keys,
        int passes, uint32_t* __restrict__ hist, int sshift, unsigned long long* fine_total, uint32_t key_bound,
-       const uint32_t* d_total, DevStatus* status, int V) {
+       const uint32_t* d_total, DevStatus* status, int V, long long spin) {
     constexpr int R = 1 << BITS;
     __shared__ uint32_t s_hist[kMaxPasses][R];
     __shared__ int s_mark[kEmitWarps][32];
@@ -515,7 +523,7 @@ k_emit(const uint64_t* __restrict__ dsorted, int64_t total, int64_t n, const uin
     if (threadIdx.x == 0) {
         st_volatile(lookback + b, (b == 0 ? kFlagInc : kFlagAgg) | (unsigned long long)btot);
         unsigned long long excl = 0;
-        look_back(lookback, b, 1, btot, &excl, status);
+        look_back(lookback, b, 1, btot, &excl, status, spin);
         s_excl = excl;
         if (b == nblk - 1) {
             const unsigned long long K = excl + btot;
@@ -990,11 +998,13 @@ k_tile_scan(const uint32_t* __restrict__ tile_count, int64_t total_tiles, int64_
 // ------------------------------------------------------------ drivers
 // Passes over packed items: non-last passes ping-pong between buf[0] and
 // buf[1] (input in buf[0]); the last pass writes `last_out` (packed) or the
-// caller's value / key arrays and ranges.
+// caller's value / key arrays and ranges.  wait.withhold applies to the last
+// pass only.
 template <int BITS, int ITEMS>
 void onesweep_passes(uint64_t* const buf[2], uint64_t* last_out, uint32_t* kout, uint32_t* vout,
                      const uint32_t* d_count, int64_t cap, int passes, const SortScratch& s, uint32_t* ranges,
-                     DevStatus* status, int sm_count, cudaStream_t st, uint32_t kmask = 0xFFFFFFFFu) {
+                     DevStatus* status, int sm_count, cudaStream_t st, WaitCfg wait,
+                     uint32_t kmask = 0xFFFFFFFFu) {
     constexpr int R = 1 << BITS;
     k_clear_lookback<<<sm_count * 4, 256, 0, st>>>(s.lookback, d_count, cap, R, passes, s.max_sort_tiles,
                                                    kThreads * ITEMS);
@@ -1005,7 +1015,8 @@ void onesweep_passes(uint64_t* const buf[2], uint64_t* last_out, uint32_t* kout,
         uint64_t* dst = last ? last_out : buf[(p + 1) % 2];
         k_onesweep<BITS, ITEMS><<<sm_count * 3, kThreads, 0, st>>>(
             src, dst, last ? kout : nullptr, last ? vout : nullptr, d_count, cap, p * BITS, kmask, s.hist + p * 256,
-            s.lookback + (int64_t)p * s.max_sort_tiles * R, s.counters + p, last ? ranges : nullptr, status);
+            s.lookback + (int64_t)p * s.max_sort_tiles * R, s.counters + p, last ? ranges : nullptr, status,
+            wait.spin, last ? wait.withhold : -1);
     }
 }
 
@@ -1016,7 +1027,7 @@ void emit_and_sort(const uint64_t* dsorted, int64_t items, const uint32_t* d_ite
                    int64_t keys_cap, int key_bits, const SortScratch& s, uint32_t* sorted_keys,
                    uint32_t* sorted_vals, uint32_t* ranges, int64_t total_tiles, uint32_t* d_num_keys,
                    DevStatus* status, int sm_count, cudaStream_t st,
-                   void (*mark)(void* const*, int, cudaStream_t), void* const* events, int ev) {
+                   void (*mark)(void* const*, int, cudaStream_t), void* const* events, int ev, WaitCfg wait) {
     const int passes = (key_bits + BITS - 1) / BITS;
     const int64_t nblk = (items + kEmitBlock - 1) / kEmitBlock;
     cudaMemsetAsync(s.hist, 0, sizeof(uint32_t) * kMaxPasses * 256, st);
@@ -1025,12 +1036,14 @@ void emit_and_sort(const uint64_t* dsorted, int64_t items, const uint32_t* d_ite
     k_emit<BITS><<<(unsigned)nblk, kEmitThreads, 0, st>>>(dsorted, items, n, s.rects, vt, keys_cap, s.tkv[0],
                                                           s.emit_lookback, s.counters + 7, d_num_keys, passes,
                                                           s.hist, 0, nullptr, (uint32_t)total_tiles, d_items,
-                                                          status, V);
+                                                          status, V, wait.spin);
     if (mark) mark(events, ev, st);
     k_ranges_init<<<sm_count * 2, 256, 0, st>>>(reinterpret_cast<uint2*>(ranges), total_tiles);
     uint64_t* const buf[2] = {s.tkv[0], s.tkv[1]};
+    // the last pass writes the caller's arrays, which no later kernel of the
+    // call reads: the one pass where the wait test hook applies
     onesweep_passes<BITS, ITEMS>(buf, nullptr, sorted_keys, sorted_vals, d_num_keys, keys_cap, passes, s, ranges,
-                                 status, sm_count, st);
+                                 status, sm_count, st, wait);
     k_ranges_fix<<<sm_count * 2, 256, 0, st>>>(reinterpret_cast<uint2*>(ranges), total_tiles);
 }
 
@@ -1043,7 +1056,8 @@ void emit_two_level(const uint64_t* dsorted, int64_t items, const uint32_t* d_it
                     uint32_t* sorted_vals, uint32_t* ranges, int64_t total_tiles, uint32_t* d_num_keys,
                     DevStatus* status, int sm_count, cudaStream_t st,
                     void (*mark)(void* const*, int, cudaStream_t), void* const* events, int ev,
-                    CoarseLists* coarse) {
+                    CoarseLists* coarse, WaitCfg wait) {
+    wait.withhold = -1;  // later kernels read this sort's output
     // the host knows the tile count only: super-tiles never outnumber tiles,
     // so it bounds their count (the kernels read the exact one from vt[V])
     const int64_t n_super = total_tiles;
@@ -1058,7 +1072,7 @@ void emit_two_level(const uint64_t* dsorted, int64_t items, const uint32_t* d_it
     k_emit<BITS><<<(unsigned)nblk, kEmitThreads, 0, st>>>(dsorted, items, n, s.rects, vt, keys_cap, s.tkv[0],
                                                           s.emit_lookback, s.counters + 7, s.d_count_coarse,
                                                           passes, s.hist, kSuperShift, s.d_fine_total,
-                                                          (uint32_t)n_super, d_items, status, V);
+                                                          (uint32_t)n_super, d_items, status, V, wait.spin);
     k_fine_total<<<1, 1, 0, st>>>(s.d_fine_total, keys_cap, d_num_keys, status);
     if (mark) mark(events, ev, st);
     // stable sort by super-tile; the values land in the ping-pong buffer the
@@ -1070,7 +1084,7 @@ void emit_two_level(const uint64_t* dsorted, int64_t items, const uint32_t* d_it
     // indices compactly (into the caller's value array, unused otherwise)
     onesweep_passes<BITS, ITEMS>(buf, buf[passes % 2], nullptr, coarse ? sorted_vals : nullptr, s.d_count_coarse,
                                  keys_cap, passes, s,
-                                 reinterpret_cast<uint32_t*>(s.cranges), status, sm_count, st,
+                                 reinterpret_cast<uint32_t*>(s.cranges), status, sm_count, st, wait,
                                  (uint32_t)((1ull << bits) - 1ull));
     k_ranges_fix<<<sm_count, 256, 0, st>>>(s.cranges, n_super);
     const unsigned fgrid = (unsigned)(sm_count * 8);
@@ -1163,8 +1177,10 @@ void launch_bin_sort(const float* proj, const ViewInfo* vt, int V, int64_t n, in
                      uint32_t* sorted_keys, uint32_t* sorted_vals, uint32_t* ranges,
                      uint32_t* d_num_keys, DevStatus* status, int sm_count, cudaStream_t st,
                      void (*mark)(void* const*, int, cudaStream_t), void* const* events, int first_event,
-                     bool compact, CoarseLists* coarse) {
+                     bool compact, CoarseLists* coarse, WaitCfg wait) {
     if (coarse) *coarse = CoarseLists{};
+    WaitCfg dwait = wait;
+    dwait.withhold = -1;  // the depth sort's output feeds the emission
     const int64_t items = (int64_t)V * n;
     const uint4* pr = reinterpret_cast<const uint4*>(proj);
     if (items == 0) {
@@ -1189,7 +1205,7 @@ void launch_bin_sort(const float* proj, const ViewInfo* vt, int V, int64_t n, in
         k_hist<8><<<sm_count * 4, kThreads, 0, st>>>(s.dkv[1], s.d_count_depth, items, 4, s.hist);
         uint64_t* const dbuf[2] = {s.dkv[1], s.dkv[0]};
         onesweep_passes<8, 16>(dbuf, s.dkv[1], nullptr, nullptr, s.d_count_depth, items, 4, s, nullptr, status,
-                               sm_count, st);
+                               sm_count, st, dwait);
         dsorted = s.dkv[1];
         d_items = s.d_count_depth;
     } else {
@@ -1197,7 +1213,7 @@ void launch_bin_sort(const float* proj, const ViewInfo* vt, int V, int64_t n, in
         k_hist<8><<<sm_count * 4, kThreads, 0, st>>>(s.dkv[0], s.d_count_depth, items, 4, s.hist);
         uint64_t* const dbuf[2] = {s.dkv[0], s.dkv[1]};
         onesweep_passes<8, 16>(dbuf, s.dkv[0], nullptr, nullptr, s.d_count_depth, items, 4, s, nullptr, status,
-                               sm_count, st);
+                               sm_count, st, dwait);
     }
     if (mark) mark(events, first_event, st);
     // 2. emission in depth order with the key histograms, 3. stable sort by
@@ -1210,12 +1226,13 @@ void launch_bin_sort(const float* proj, const ViewInfo* vt, int V, int64_t n, in
         if (binning == kBinDirect || bits > kMaxCoarseKeyBits)                                                  \
             emit_and_sort<B, I>(dsorted, items, d_items, n, pr, vt, V, keys_cap, bits, s, sorted_keys, sorted_vals, \
                                 ranges,                                                                         \
-                                total_tiles, d_num_keys, status, sm_count, st, mark, events, first_event + 1);  \
+                                total_tiles, d_num_keys, status, sm_count, st, mark, events, first_event + 1,   \
+                                wait);                                                                          \
         else                                                                                                    \
             emit_two_level<B, I>(dsorted, items, d_items, n, pr, vt, V, keys_cap, s, sorted_keys, sorted_vals,  \
                                  ranges,                                                                        \
                                  total_tiles, d_num_keys, status, sm_count, st, mark, events, first_event + 1,  \
-                                 coarse);                                                                       \
+                                 coarse, wait);                                                                 \
     } while (0)
     const int it = sort_items == 8 ? 8 : (sort_items == 16 ? 16 : 12);
     switch (sort_bits * 100 + it) {

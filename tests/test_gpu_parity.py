@@ -15,12 +15,16 @@ import pytest
 
 import gs_inputs as gi
 import oracle as O
-from flips import decision_flips
+from flips import decision_flips, decision_margins
 from gpu_util import GpuRun, OracleStages, cams32, gpu_proj_to_oracle, l1_sign_expected, rel_l2, scene
 
 pytestmark = pytest.mark.gpu
 
 TOL = 1e-4
+# relative distance from a threshold within which float32 and float64 walks
+# of the same records may take a compositing decision differently (float32
+# transmittance over a few hundred fragments drifts by ~1e-5 relative)
+NEAR_DECISION = 1e-4
 
 CASES = {
     # name: (n, sh_degree, views, width, height, scale shift)
@@ -93,12 +97,18 @@ def test_bin_sort_bit_exact_stagewise(stages):
 
 
 def test_render_fwd_stagewise(stages):
+    """Both sides composite the same float32 records and lists, so a
+    contributor count may differ only at a pixel where a decision of the walk
+    (the alpha cut-off, the termination test, the sign of P) lies within
+    rounding of its threshold: every mismatch must be such a pixel."""
     name, st = stages
     img, T, nc = st.gpu_render_fwd()
     assert rel_l2(img.cpu().numpy(), st.image) <= TOL
     assert rel_l2(T.cpu().numpy(), st.T) <= TOL
-    mism = np.mean(nc.cpu().numpy().view(np.uint32) != st.nc)
-    assert mism <= 1e-3, mism
+    mism = nc.cpu().numpy().view(np.uint32) != st.nc
+    near = decision_margins(st.cams, st.projd, st.vals, st.ranges) <= NEAR_DECISION
+    print("render stage-wise", name, "count mismatches", int(mism.sum()), "near-threshold pixels", int(near.sum()))
+    assert not np.any(mism & ~near), np.nonzero(mism & ~near)[0][:10]
 
 
 def test_render_end_to_end(case):
@@ -167,6 +177,8 @@ def test_gradient_end_to_end(case):
     print("gradient end-to-end", name, "all", e_all, "kept", e_keep, "threshold flips", int(odd.sum()),
           "pixels", npix, "L1 sign ties", ties)
     assert odd.mean() <= 1e-3, int(odd.sum())
+    # the L1 tie family must stay small, or its fit could absorb a real error
+    assert ties <= 1e-4 * target.size, ties
     assert e_keep <= TOL, (e_all, e_keep)
 
 

@@ -292,6 +292,49 @@ def test_bin_sort_matches_lexsort():
             assert ranges[t, 0] == ranges[t, 1]
 
 
+def test_bin_ranges_and_tile_lists_match_numpy():
+    """The ranges of every tile (without forming the entries) and the
+    sorted lists of chosen tiles, against a numpy count per tile and a
+    lexsort of each chosen tile's (depth bits, index) pairs, on ragged views
+    of different sizes with equal depths."""
+    cams = gi.cameras_from_eyes([(0, 0, 3), (3, 0, 0), (0, 0, -3)], [70, 33, 48], [50, 47, 16])
+    TX = [(int(w) + 15) // 16 for w in cams["width"]]
+    TY = [(int(h) + 15) // 16 for h in cams["height"]]
+    V, n = 3, 500
+    rects = np.zeros((V, n, 4), dtype=np.int32)
+    for v in range(V):
+        x0 = RNG.integers(0, TX[v], n); y0 = RNG.integers(0, TY[v], n)
+        rects[v, :, 0] = x0; rects[v, :, 1] = y0
+        rects[v, :, 2] = np.minimum(TX[v], x0 + RNG.integers(0, 3, n))
+        rects[v, :, 3] = np.minimum(TY[v], y0 + RNG.integers(0, 3, n))
+    depth = RNG.uniform(0.5, 5, (V, n)).astype(np.float32)
+    depth[1, :80] = depth[1, 80:160]  # equal depths: ties broken by index
+    off = np.concatenate([[0], np.cumsum([a * b for a, b in zip(TX, TY)])])
+    count = np.zeros(off[-1], dtype=np.int64)
+    members = [[] for _ in range(off[-1])]
+    for v in range(V):
+        for g in range(n):
+            r = rects[v, g]
+            for ty in range(r[1], r[3]):
+                for tx in range(r[0], r[2]):
+                    t = off[v] + ty * TX[v] + tx
+                    count[t] += 1
+                    members[t].append(g)
+    ranges, K = O.bin_ranges(cams, rects)
+    assert K == count.sum()
+    start = np.concatenate([[0], np.cumsum(count)])[:-1]
+    np.testing.assert_array_equal(ranges[:, 0], np.where(count > 0, start, 0))
+    np.testing.assert_array_equal(ranges[:, 1], np.where(count > 0, start + count, 0))
+    pick = np.array([0, 5, off[1], off[1] + 3, off[2] - 1, off[2], off[3] - 1, 7], dtype=np.int64)
+    vals, st = O.bin_tiles(cams, rects, depth, pick)
+    for i, t in enumerate(pick):
+        v = int(np.searchsorted(off, t, side="right") - 1)
+        g = np.array(members[t], dtype=np.int64)
+        order = np.lexsort((g, depth[v, g].view(np.uint32))) if g.size else g
+        np.testing.assert_array_equal(vals[st[i]:st[i + 1]], g[order])
+    assert st[-1] == sum(len(members[t]) for t in pick)
+
+
 def test_render_invariants():
     sc = gi.make_scene(3000, 2, 5)
     cams = gi.ring_cameras(2, 48, 40)
