@@ -69,7 +69,12 @@ def _peaks():
 #     dL/dP dx 1 and the sums of dL/dP, dL/dP dx, dL/dP dx^2 4 = 37
 RASTER_FWD_FLOP_PER_FRAGMENT = 20
 RASTER_BWD_FLOP_PER_FRAGMENT = 37
-FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12  # SMs x FP32 lanes x FMA x max SM clock
+FP32_LANES_PER_SM = 128
+
+
+def fp32_peak_tflops(sm_count: int, sm_mhz: float) -> float:
+    """FP32 peak of the device at a clock: SMs x 128 FP32 lanes x 2 (FMA) x clock."""
+    return sm_count * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
 
 
 def phase_model(n, V, K, total_tiles, npix, sum_nc, n_changed, binning, passes, Kc, chunks, n_train=None):
@@ -97,16 +102,23 @@ def phase_model(n, V, K, total_tiles, npix, sum_nc, n_changed, binning, passes, 
         "loss": ("hbm", 3 * npix * 44),
         "raster_bwd": ("alu", sum_nc * RASTER_BWD_FLOP_PER_FRAGMENT),
         "project_bwd": ("hbm", nt * 480 + V * nt * (48 + 32)),
-        # Adam fused with the delta's changed test: theta, grad, m, v, baseline
-        # read, theta, m, v written, one flag byte out
-        "adam": ("hbm", 60 * nt * 4 * 8 + nt),
-        "delta": ("hbm", nt + n_changed * (240 + 240 + 128 + 4)),
+        # Adam fused with the whole delta extraction (one kernel): theta, grad,
+        # m, v, baseline read, theta, m, v written; per changed Gaussian its
+        # index and record written, its baseline rewritten
+        "adam": ("hbm", 60 * nt * 4 * 8 + n_changed * (4 + 128 + 240)),
     }
 
 
-# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum, one ncu
-# capture at full size; profiles/train_step_1M_8x720p_traffic.md), valid while
-# the kernel's source file is unchanged (first 12 hex digits of its SHA-1).
+def delta_bytes(n, n_changed):
+    """Algorithmic bytes of one gs_extract_delta: theta and baseline read
+    (2 x 240 B per Gaussian), per changed Gaussian the index, the 128-byte
+    record and the rewritten baseline (240 B)."""
+    return n * 480 + n_changed * (4 + 128 + 240)
+
+
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum of the
+# kernel in one ncu capture), valid while the kernel's source file is
+# unchanged (first 12 hex digits of its SHA-1).
 MEASURED_TRAFFIC = {
     ("c3_1M_8x720p", "k_raster_bwd"): (252.9e6, "csrc/raster.cu", "a344e179321a"),
 }
@@ -129,7 +141,7 @@ def measured_traffic(workload, kernel):
 
 # phases that are one kernel (plus negligible set-up launches), by kernel name
 SINGLE_KERNEL_PHASES = {"project": "k_project", "emit": "k_emit", "render_fwd": "k_render_fwd",
-                        "raster_bwd": "k_raster_bwd", "project_bwd": "k_project_bwd", "adam": "k_adam_flags"}
+                        "raster_bwd": "k_raster_bwd", "project_bwd": "k_project_bwd", "adam": "k_adam_delta"}
 
 
 def gpu_launches_per_step(binning, passes):
@@ -139,11 +151,11 @@ def gpu_launches_per_step(binning, passes):
     init, look-back clear, scan, passes, ranges fix, chunk table, chunk
     owners, bitmaps;
     direct: emission, ranges init, look-back clear, scan, passes, ranges
-    fix), compositing, loss (2), adjoints (2), Adam with the delta's changed
-    test and the step counter (2), delta scan and records (2)."""
+    fix), compositing, loss (2), adjoints (2), Adam fused with the delta
+    extraction and the step counter (2)."""
     depth = 8
     sort = (9 + passes) if binning == "two_level" else (5 + passes)
-    return 1 + 1 + depth + sort + 1 + 2 + 1 + 1 + 2 + 2
+    return 1 + 1 + depth + sort + 1 + 2 + 1 + 1 + 2
 
 
 def replica_seeds(rank: int):
@@ -207,7 +219,7 @@ class ClockSampler:
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
         try:
             self.p = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={q}", "--format=csv,noheader,nounits",
-                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+                                       "-lms", "50"], stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.p = None
 
@@ -303,9 +315,9 @@ class OracleSampler:
 
     def describe(self, samples) -> str:
         self.adam_seconds()
-        return (f"{samples} samples of one 16-row band of one view (all {self.n} Gaussians projected, binned, "
-                f"composited, loss + both adjoints, FP64), scaled x{self.bands} bands x{self.V} views; "
-                f"Adam on {self.adam_floats} floats scaled to {self.n * 60}")
+        return (f"estimated from band samples: {samples} samples of one 16-row band of one view (all {self.n} "
+                f"Gaussians projected, binned, composited, loss + both adjoints, FP64), scaled x{self.bands} bands "
+                f"x{self.V} views; Adam on {self.adam_floats} floats scaled to {self.n * 60}")
 
 
 RELIGHT_RADIANCE = (1.0, 0.95, 0.9)
@@ -357,7 +369,7 @@ def run_reference(args, rank, world):
             "config": {"workload": args.workload, "gaussians": n, "sh_degree": sh, "views": V,
                        "resolution": [W, H]},
             "cpu_baseline": {"value": value, "unit": "steps/s", "cores": omp_cores(), "kind": "oracle",
-                             "sample": smp.describe(len(times)), "wall_s": wall},
+                             "sample": smp.describe(len(times)), "estimated": True, "wall_s": wall},
             "e2e": {"value": value, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -554,8 +566,17 @@ def run_ours(args, rank, world, local_rank):
     model = phase_model(n, V, K, tr.total_tiles, tr.npix, sum_nc, changed, args.binning, tile_passes, Kc, chunks,
                         n_train=params.shape[1])
     hbm_peak, peak_src = _peaks()
+    # FP32 peak from the queried SM count at the median SM clock sampled in the timed region
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    sm_mhz = clk.get("sm_mhz") or clk.get("sm_max_mhz") or 2032.0
+    fp32_peak = fp32_peak_tflops(sm_count, sm_mhz)
+    fp32_src = f"derived: {sm_count} SMs (queried) x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_mhz:.0f} MHz (median sampled)"
     kernels = {}
     for name, ms in phase_avg.items():
+        if name not in model:
+            # the delta extraction runs inside the Adam kernel: its phase is empty
+            kernels[name] = {"ms": ms, "fused_into": "adam"}
+            continue
         bound, work = model[name]
         if bound == "hbm":
             ach = work / (ms / 1e3) / 1e9
@@ -564,18 +585,20 @@ def run_ours(args, rank, world, local_rank):
         else:
             ach = work / (ms / 1e3) / 1e12
             kernels[name] = {"ms": ms, "bound": "alu", "achieved": ach, "unit": "TFLOP/s",
-                             "peak": FP32_PEAK_TFLOPS, "frac": ach / FP32_PEAK_TFLOPS, "algorithmic_flop": work}
+                             "peak": fp32_peak, "frac": ach / fp32_peak, "algorithmic_flop": work}
     dom = max(SINGLE_KERNEL_PHASES, key=lambda p: phase_avg[p])
     dk = kernels[dom]
     roofline = {"kernel": SINGLE_KERNEL_PHASES[dom], "bound": dk["bound"], "achieved": dk["achieved"],
                 "peak": dk["peak"],
                 "unit": dk["unit"], "frac": dk["frac"],
                 "traffic": measured_traffic(args.workload, SINGLE_KERNEL_PHASES[dom]),
-                "peak_source": peak_src if dk["bound"] == "hbm" else "derived: 148 SMs x 128 FP32 lanes x 2 x 2032 MHz"}
+                "peak_source": peak_src if dk["bound"] == "hbm" else fp32_src}
 
     # ---- tensor deltas per attribute group since the start of the timed steps
     tensor_deltas = measure_tensor_deltas(gs, torch, params, snapshot, _peaks()[0]) if args.tensor_deltas else None
     del snapshot
+    # ---- the standalone gs_extract_delta on the changed set of one step
+    delta_standalone = measure_delta_standalone(gs, torch, tr, next_targets, hbm_peak) if args.delta_reps else None
 
     # ---- end to end through the public API: host targets in, loss + delta out
     host_targets = None
@@ -660,7 +683,7 @@ def run_ours(args, rank, world, local_rank):
                "gpu_launches": (gpu_launches_per_step(args.binning, tile_passes)
                                 + (1 + 3 + (2 if frozen is not None else 0) if args.relight else 0)
                                 + (1 if frozen is not None else 0)) * args.steps,
-               "tensor_deltas": tensor_deltas,
+               "tensor_deltas": tensor_deltas, "delta_standalone": delta_standalone,
                "phases_ms": phase_avg, "kernels": kernels, "loss_last": loss_last, "delta_changed_last": changed,
                "wall_s_timed_loop": wall}
         print(json.dumps(out), flush=True)
@@ -715,6 +738,44 @@ def run_serving(args, local_rank, rank):
     del srv, params
     torch.cuda.empty_cache()
     return res
+
+
+def measure_delta_standalone(gs, torch, tr, next_targets, hbm_peak, reps=10):
+    """gs_extract_delta on the inputs of one training step's delta: the
+    parameters after one more step and the transmitted baseline before it
+    (so the same changed set as the step's fused extraction).  Timed with
+    CUDA events per call; the baseline is restored between calls outside
+    the events."""
+    b0 = tr.baseline.clone()
+    next_targets()
+    tr.step()
+    torch.cuda.synchronize()
+    fused_m = tr.delta_count()
+    n = tr.params.shape[1]
+    ctx = gs.Context(tr.params.device.index or 0, 1 << 26)
+    base = b0.clone()
+    idx = torch.empty(max(n, 1), dtype=torch.int32, device=tr.params.device)
+    rec = torch.empty((max(n, 1), 128), dtype=torch.uint8, device=tr.params.device)
+    cnt = torch.zeros(1, dtype=torch.int32, device=tr.params.device)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    times = []
+    for r in range(reps + 2):
+        base.copy_(b0)
+        e0.record()
+        gs.gs_extract_delta(ctx, tr.params, base, tr.delta_thr, d_idx=idx, d_records=rec, d_count=cnt)
+        e1.record()
+        e1.synchronize()
+        if r >= 2:
+            times.append(e0.elapsed_time(e1))
+    ctx.raise_status()
+    m = int(cnt.item())
+    ctx.close()
+    ms = float(np.median(times))
+    work = delta_bytes(n, m)
+    ach = work / (ms / 1e3) / 1e9
+    return {"ms": ms, "changed": m, "changed_by_fused_step": fused_m, "bound": "hbm", "achieved": ach,
+            "unit": "GB/s", "peak": hbm_peak, "frac": ach / hbm_peak, "algorithmic_bytes": work,
+            "kernel": "k_delta_onepass", "reps": reps}
 
 
 TENSOR_GROUPS = (("mean", 0, 3, 4), ("opacity", 3, 4, 2), ("scale", 4, 7, 2), ("rotation", 8, 12, 2),
@@ -819,6 +880,8 @@ def main():
                     help="fraction of the model held in the inference-only (frozen) pool")
     ap.add_argument("--relight", action="store_true",
                     help="SH-lighting product and per-frame light visibility (Sec. 3.4.1) in every step")
+    ap.add_argument("--delta-reps", type=int, default=10,
+                    help="time the standalone gs_extract_delta on one step's changed set (0: skip)")
     ap.add_argument("--tensor-deltas", action=argparse.BooleanOptionalAction, default=True,
                     help="time per-attribute tensor-delta extraction and replay after the timed steps")
     args = ap.parse_args()

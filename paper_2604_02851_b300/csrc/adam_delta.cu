@@ -9,8 +9,12 @@
 // with residuals against the previously transmitted state and fresh baselines
 // after a snapshot.  A Gaussian is sent when any of its 60 floats moved by
 // more than thr from its last transmitted value; the sent set is compacted in
-// index order (block sums, one-block scan, ordered emit) and packed as
-// 128-byte records: uint32 index, float32 mean, 56 float16 (RNE) attributes.
+// index order and packed as 128-byte records: uint32 index, float32 mean, 56
+// float16 (RNE) attributes.  gs_extract_delta and the training step compact
+// in one pass (each block finds its output offset by decoupled look-back over
+// the blocks before it); the allocation-free entry point keeps a three-kernel
+// form (flags and block sums, a one-block scan, an ordered emit) whose
+// scratch needs no clearing.
 #include <cuda_fp16.h>
 #include <math.h>
 
@@ -20,6 +24,8 @@ namespace gs {
 namespace {
 
 struct LrTable { float lr[60]; };
+
+constexpr int kDeltaThreads = 256;  // Gaussians per delta block
 
 // One bias-corrected Adam update of a float4 of parameters (learning rates
 // l[0..3]); bc1 = 1 - b1^t, sbc2 = sqrt(1 - b2^t).
@@ -60,8 +66,92 @@ k_adam(float4* __restrict__ theta, const float4* __restrict__ grad, float4* __re
 
 __global__ void k_inc_step(int32_t* d_step) { *d_step += 1; }
 
+// One 128-byte record of Gaussian g at output slot `off`, read plane by plane
+// from theta (so that few registers are live), and its baseline planes set to
+// theta: word 0 index, words 1-3 mean (float32), then float16 RNE pairs of
+// log-scale xyz, quaternion wxyz, opacity logit (words 4-7) and the 48 SH
+// coefficients in flat order (two words per plane 3..14).
+__device__ __forceinline__ uint32_t half2_bits(float a, float b) {
+    return (uint32_t)__half_as_ushort(__float2half_rn(a)) | ((uint32_t)__half_as_ushort(__float2half_rn(b)) << 16);
+}
+
+__device__ __forceinline__ void emit_record(const float4* __restrict__ theta, float4* __restrict__ base, int64_t n,
+                                            int64_t g, uint32_t off, uint32_t* __restrict__ d_idx,
+                                            uint8_t* __restrict__ d_records) {
+    d_idx[off] = (uint32_t)g;
+    const float4 p0 = theta[g], p1 = theta[n + g], p2 = theta[2 * n + g];
+    base[g] = p0;
+    base[n + g] = p1;
+    base[2 * n + g] = p2;
+    uint4* rec = reinterpret_cast<uint4*>(d_records + (size_t)off * 128);
+    rec[0] = make_uint4((uint32_t)g, __float_as_uint(p0.x), __float_as_uint(p0.y), __float_as_uint(p0.z));
+    rec[1] = make_uint4(half2_bits(p1.x, p1.y), half2_bits(p1.z, p2.x), half2_bits(p2.y, p2.z),
+                        half2_bits(p2.w, p0.w));
+    uint2* sh = reinterpret_cast<uint2*>(rec + 2);
+#pragma unroll 4
+    for (int p = 3; p < 15; ++p) {
+        const float4 a = theta[p * n + g];
+        base[p * n + g] = a;
+        sh[p - 3] = make_uint2(half2_bits(a.x, a.y), half2_bits(a.z, a.w));
+    }
+}
+
+// Block part of the one-pass compaction: the block's changed count, its
+// output offset by look-back (block ticket b of nblk), and each changed
+// thread's slot.  The last block writes the total to *d_count.
+__device__ __forceinline__ uint32_t delta_slot(bool changed, int64_t b, int64_t nblk, unsigned long long* lookback,
+                                               uint32_t* d_count, DevStatus* status, long long spin) {
+    __shared__ uint32_t s_w[kDeltaThreads / 32];
+    __shared__ unsigned long long s_excl;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t bal = __ballot_sync(0xFFFFFFFFu, changed);
+    if (lane == 0) s_w[warp] = __popc(bal);
+    __syncthreads();
+    uint32_t woff = 0, tot = 0;
+#pragma unroll
+    for (int w = 0; w < kDeltaThreads / 32; ++w) {
+        if (w < warp) woff += s_w[w];
+        tot += s_w[w];
+    }
+    if (threadIdx.x == 0) {
+        st_volatile(lookback + b, (b == 0 ? kFlagInc : kFlagAgg) | (unsigned long long)tot);
+        unsigned long long excl = 0;
+        look_back(lookback, b, 1, tot, &excl, status, spin);
+        s_excl = excl;
+        if (b == nblk - 1) *d_count = (uint32_t)(excl + tot);
+    }
+    __syncthreads();
+    return (uint32_t)s_excl + woff + __popc(bal & ((1u << lane) - 1u));
+}
+
+// gs_extract_delta in one pass: block ticket b tests Gaussians b*256 ..
+// b*256 + 255 (theta and baseline streamed once), finds its offset and
+// writes the records of its changed Gaussians.  lookback [nblk] and the
+// ticket counter start at zero.
+__global__ void __launch_bounds__(kDeltaThreads)
+k_delta_onepass(const float4* __restrict__ theta, float4* __restrict__ base, int64_t n, float thr,
+                uint32_t* __restrict__ d_idx, uint8_t* __restrict__ d_records, uint32_t* d_count,
+                unsigned long long* lookback, uint32_t* ticket, int64_t nblk, DevStatus* status, long long spin) {
+    __shared__ uint32_t s_blk;
+    if (threadIdx.x == 0) s_blk = atomicAdd(ticket, 1u);
+    __syncthreads();
+    const int64_t b = s_blk;
+    const int64_t g = b * kDeltaThreads + threadIdx.x;
+    bool changed = false;
+    if (g < n) {
+        float d = 0.f;
+#pragma unroll
+        for (int p = 0; p < 15; ++p) {
+            const float4 a = theta[p * n + g], c = base[p * n + g];
+            d = fmaxf(d, fmaxf(fmaxf(fabsf(a.x - c.x), fabsf(a.y - c.y)), fmaxf(fabsf(a.z - c.z), fabsf(a.w - c.w))));
+        }
+        changed = d > thr;
+    }
+    const uint32_t off = delta_slot(changed, b, nblk, lookback, d_count, status, spin);
+    if (changed) emit_record(theta, base, n, g, off, d_idx, d_records);
+}
+
 // ---------------------------------------------------------------- delta
-constexpr int kDeltaThreads = 256;
 
 __global__ void __launch_bounds__(kDeltaThreads)
 k_delta_flags(const float4* __restrict__ theta, const float4* __restrict__ base, int64_t n, float thr,
@@ -81,32 +171,38 @@ k_delta_flags(const float4* __restrict__ theta, const float4* __restrict__ base,
     if (threadIdx.x == 0) block_sums[blockIdx.x] = cnt;
 }
 
-// The training step's Adam update fused with the changed test of the delta
-// extraction: one thread per Gaussian walks its 15 planes, updates them and
-// compares the new values with the baseline, so that the parameters are read
-// once.  Same arithmetic as k_adam and k_delta_flags.  Six blocks an SM (40
-// registers, the learning rates in shared memory) keep enough loads in
-// flight; unrolling the plane loop, or 5 and 8 blocks, measured slower.
+// The training step's Adam update fused with the whole delta extraction: one
+// thread per Gaussian (block ticket order) walks its 15 planes, updates them
+// and compares the new values with the baseline, so that the parameters are
+// read once; the block then finds its output offset by look-back and its
+// changed threads write their records (re-reading the planes they just
+// wrote).  Same arithmetic as k_adam and k_delta_onepass.  Six blocks an SM
+// (the learning rates in shared memory) keep enough loads in flight;
+// unrolling the plane loop, or 5 and 8 blocks, measured slower.
 __global__ void __launch_bounds__(kDeltaThreads, 6)
-k_adam_flags(float4* __restrict__ theta, const float4* __restrict__ grad, float4* __restrict__ m,
-             float4* __restrict__ v, const float4* __restrict__ base, int64_t n, LrTable lr, float b1, float b2,
+k_adam_delta(float4* __restrict__ theta, const float4* __restrict__ grad, float4* __restrict__ m,
+             float4* __restrict__ v, float4* __restrict__ base, int64_t n, LrTable lr, float b1, float b2,
              float eps, int host_step, const int32_t* __restrict__ d_step, const uint8_t* __restrict__ fwd,
-             float thr, uint8_t* __restrict__ flags, uint32_t* __restrict__ block_sums) {
+             float thr, uint32_t* __restrict__ d_idx, uint8_t* __restrict__ d_records, uint32_t* d_count,
+             unsigned long long* lookback, uint32_t* ticket, int64_t nblk, DevStatus* status, long long spin) {
     __shared__ float s_lr[60];
+    __shared__ uint32_t s_blk;
     if (threadIdx.x < 60) s_lr[threadIdx.x] = lr.lr[threadIdx.x];
+    if (threadIdx.x == 0) s_blk = atomicAdd(ticket, 1u);
     __syncthreads();
     const int step = d_step ? *d_step : host_step;
     const float bc1 = 1.f - powf(b1, (float)step);
     const float sbc2 = sqrtf(1.f - powf(b2, (float)step));
-    const int64_t g = (int64_t)blockIdx.x * kDeltaThreads + threadIdx.x;
-    uint32_t changed = 0;
+    const int64_t b = s_blk;
+    const int64_t g = b * kDeltaThreads + threadIdx.x;
+    bool changed = false;
     if (g < n) {
         const bool upd = !fwd || fwd[g];  // preculled: no update
 #pragma unroll 1
         for (int p = 0; p < 15; ++p) {
             const int64_t i = p * n + g;
             float4 th = theta[i];
-            const float4 b = base[i];
+            const float4 bb = base[i];
             if (upd) {
                 const float4 gr = grad[i];
                 float4 mm = m[i], vv = v[i];
@@ -115,13 +211,12 @@ k_adam_flags(float4* __restrict__ theta, const float4* __restrict__ grad, float4
                 v[i] = vv;
                 theta[i] = th;
             }
-            const float d = fmaxf(fmaxf(fabsf(th.x - b.x), fabsf(th.y - b.y)), fmaxf(fabsf(th.z - b.z), fabsf(th.w - b.w)));
-            changed |= (d > thr) ? 1u : 0u;
+            const float d = fmaxf(fmaxf(fabsf(th.x - bb.x), fabsf(th.y - bb.y)), fmaxf(fabsf(th.z - bb.z), fabsf(th.w - bb.w)));
+            changed |= d > thr;
         }
-        flags[g] = (uint8_t)changed;
     }
-    const uint32_t cnt = __syncthreads_count(changed);
-    if (threadIdx.x == 0) block_sums[blockIdx.x] = cnt;
+    const uint32_t off = delta_slot(changed, b, nblk, lookback, d_count, status, spin);
+    if (changed) emit_record(theta, base, n, g, off, d_idx, d_records);
 }
 
 __global__ void __launch_bounds__(kDeltaThreads)
@@ -184,47 +279,38 @@ __device__ __forceinline__ void set_lane(float4& a, int l, float v) {
     if (l == 0) a.x = v; else if (l == 1) a.y = v; else if (l == 2) a.z = v; else a.w = v;
 }
 
+// Tensor delta of one group in one pass (as k_delta_onepass): block ticket
+// b tests its Gaussians' group floats, finds its offset by look-back and
+// writes each changed Gaussian's index, its group record (float32 or float16
+// RNE, densely packed) and the group's baseline floats.
 __global__ void __launch_bounds__(kDeltaThreads)
-k_tdelta_flags(const float4* __restrict__ theta, const float4* __restrict__ base, int64_t n, Group gr, float thr,
-               uint8_t* __restrict__ flags, uint32_t* __restrict__ block_sums) {
-    const int64_t g = (int64_t)blockIdx.x * kDeltaThreads + threadIdx.x;
-    uint32_t changed = 0;
+k_tdelta_onepass(const float4* __restrict__ theta, float4* __restrict__ base, int64_t n, Group gr, float thr,
+                 uint32_t* __restrict__ d_idx, uint8_t* __restrict__ d_vals, uint32_t* d_count,
+                 unsigned long long* lookback, uint32_t* ticket, int64_t nblk, DevStatus* status, long long spin) {
+    __shared__ uint32_t s_blk;
+    if (threadIdx.x == 0) s_blk = atomicAdd(ticket, 1u);
+    __syncthreads();
+    const int64_t b = s_blk;
+    const int64_t g = b * kDeltaThreads + threadIdx.x;
+    bool changed = false;
     if (g < n) {
         for (int p = gr.lo >> 2; p <= (gr.hi - 1) >> 2; ++p) {
-            const float4 a = theta[p * n + g], b = base[p * n + g];
+            const float4 a = theta[p * n + g], c = base[p * n + g];
 #pragma unroll
             for (int l = 0; l < 4; ++l) {
                 const int f = 4 * p + l;
-                if (f >= gr.lo && f < gr.hi && fabsf(lane_of(a, l) - lane_of(b, l)) > thr) changed = 1u;
+                if (f >= gr.lo && f < gr.hi && fabsf(lane_of(a, l) - lane_of(c, l)) > thr) changed = true;
             }
         }
-        flags[g] = (uint8_t)changed;
     }
-    const uint32_t cnt = __syncthreads_count(changed);
-    if (threadIdx.x == 0) block_sums[blockIdx.x] = cnt;
-}
-
-__global__ void __launch_bounds__(kDeltaThreads)
-k_tdelta_emit(const float4* __restrict__ theta, float4* __restrict__ base, int64_t n, Group gr,
-              const uint8_t* __restrict__ flags, const uint32_t* __restrict__ block_off,
-              uint32_t* __restrict__ d_idx, uint8_t* __restrict__ d_vals) {
-    const int64_t g = (int64_t)blockIdx.x * kDeltaThreads + threadIdx.x;
-    const bool ch = g < n && flags[g];
-    const uint32_t ballot = __ballot_sync(0xFFFFFFFFu, ch);
-    __shared__ uint32_t s_w[kDeltaThreads / 32];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (lane == 0) s_w[warp] = __popc(ballot);
-    __syncthreads();
-    uint32_t off = block_off[blockIdx.x];
-    for (int w = 0; w < warp; ++w) off += s_w[w];
-    off += __popc(ballot & ((1u << lane) - 1u));
-    if (!ch) return;
+    const uint32_t off = delta_slot(changed, b, nblk, lookback, d_count, status, spin);
+    if (!changed) return;
     d_idx[off] = (uint32_t)g;
     const int rb = (gr.hi - gr.lo) * (gr.f32 ? 4 : 2);
     uint8_t* rec = d_vals + (size_t)off * rb;
     for (int p = gr.lo >> 2; p <= (gr.hi - 1) >> 2; ++p) {
         const float4 a = theta[p * n + g];
-        float4 b = base[p * n + g];
+        float4 c = base[p * n + g];
 #pragma unroll
         for (int l = 0; l < 4; ++l) {
             const int f = 4 * p + l;
@@ -232,9 +318,9 @@ k_tdelta_emit(const float4* __restrict__ theta, float4* __restrict__ base, int64
             const float v = lane_of(a, l);
             if (gr.f32) reinterpret_cast<float*>(rec)[f - gr.lo] = v;
             else reinterpret_cast<__half*>(rec)[f - gr.lo] = __float2half_rn(v);
-            set_lane(b, l, v);
+            set_lane(c, l, v);
         }
-        base[p * n + g] = b;
+        base[p * n + g] = c;
     }
 }
 
@@ -386,32 +472,55 @@ void launch_delta(const float* theta, float* baseline, int64_t n, float thr, uin
     k_delta_emit<<<(unsigned)nblk, kDeltaThreads, 0, st>>>(th, b, n, flags, sums, d_idx, d_records);
 }
 
-void launch_adam_delta(float* theta, const float* grad, float* m, float* v, int64_t n, const gs_adam_cfg& cfg,
-                       const uint8_t* fwd, float* baseline, float thr, uint32_t* d_idx, uint8_t* d_records,
-                       uint32_t* d_count, char* scratch, cudaStream_t st, void (*mark)(void* const*, int, cudaStream_t),
-                       void* const* events, int event) {
-    Carver c(scratch);
-    uint8_t* flags = c.take<uint8_t>(n > 0 ? n : 1);
-    const int64_t nblk = (n + kDeltaThreads - 1) / kDeltaThreads;
-    uint32_t* sums = c.take<uint32_t>(nblk + 1);
-    if (n > 0) {
-        LrTable lr;
-        for (int i = 0; i < 60; ++i) lr.lr[i] = cfg.lr[i];
-        k_adam_flags<<<(unsigned)nblk, kDeltaThreads, 0, st>>>(
-            reinterpret_cast<float4*>(theta), reinterpret_cast<const float4*>(grad), reinterpret_cast<float4*>(m),
-            reinterpret_cast<float4*>(v), reinterpret_cast<const float4*>(baseline), n, lr, cfg.beta1, cfg.beta2,
-            cfg.eps, cfg.step, cfg.d_step, fwd, thr, flags, sums);
-    }
-    if (cfg.d_step && cfg.increment) k_inc_step<<<1, 1, 0, st>>>(const_cast<int32_t*>(cfg.d_step));
-    if (mark) mark(events, event, st);
+size_t delta_onepass_scratch_bytes(int64_t n) {
+    Carver c(nullptr);
+    c.take<unsigned long long>((n + kDeltaThreads - 1) / kDeltaThreads + 1);
+    c.take<uint32_t>(1);
+    return c.off;
+}
+
+void launch_delta_onepass(const float* theta, float* baseline, int64_t n, float thr, uint32_t* d_idx,
+                          uint8_t* d_records, uint32_t* d_count, char* scratch, DevStatus* status, long long spin,
+                          cudaStream_t st) {
     if (n <= 0) {
         cudaMemsetAsync(d_count, 0, sizeof(uint32_t), st);
         return;
     }
-    k_scan_sums<<<1, 1024, 0, st>>>(sums, nblk, d_count, -1, nullptr);
-    k_delta_emit<<<(unsigned)nblk, kDeltaThreads, 0, st>>>(reinterpret_cast<const float4*>(theta),
-                                                          reinterpret_cast<float4*>(baseline), n, flags, sums, d_idx,
-                                                          d_records);
+    const int64_t nblk = (n + kDeltaThreads - 1) / kDeltaThreads;
+    Carver c(scratch);
+    unsigned long long* lb = c.take<unsigned long long>(nblk + 1);
+    uint32_t* ticket = c.take<uint32_t>(1);
+    cudaMemsetAsync(scratch, 0, c.off, st);
+    k_delta_onepass<<<(unsigned)nblk, kDeltaThreads, 0, st>>>(reinterpret_cast<const float4*>(theta),
+                                                             reinterpret_cast<float4*>(baseline), n, thr, d_idx,
+                                                             d_records, d_count, lb, ticket, nblk, status, spin);
+}
+
+void launch_adam_delta(float* theta, const float* grad, float* m, float* v, int64_t n, const gs_adam_cfg& cfg,
+                       const uint8_t* fwd, float* baseline, float thr, uint32_t* d_idx, uint8_t* d_records,
+                       uint32_t* d_count, char* scratch, DevStatus* status, long long spin, cudaStream_t st,
+                       void (*mark)(void* const*, int, cudaStream_t), void* const* events, int event) {
+    if (n > 0) {
+        const int64_t nblk = (n + kDeltaThreads - 1) / kDeltaThreads;
+        Carver c(scratch);
+        unsigned long long* lb = c.take<unsigned long long>(nblk + 1);
+        uint32_t* ticket = c.take<uint32_t>(1);
+        cudaMemsetAsync(scratch, 0, c.off, st);
+        LrTable lr;
+        for (int i = 0; i < 60; ++i) lr.lr[i] = cfg.lr[i];
+        k_adam_delta<<<(unsigned)nblk, kDeltaThreads, 0, st>>>(
+            reinterpret_cast<float4*>(theta), reinterpret_cast<const float4*>(grad), reinterpret_cast<float4*>(m),
+            reinterpret_cast<float4*>(v), reinterpret_cast<float4*>(baseline), n, lr, cfg.beta1, cfg.beta2,
+            cfg.eps, cfg.step, cfg.d_step, fwd, thr, d_idx, d_records, d_count, lb, ticket, nblk, status, spin);
+    } else {
+        cudaMemsetAsync(d_count, 0, sizeof(uint32_t), st);
+    }
+    if (cfg.d_step && cfg.increment) k_inc_step<<<1, 1, 0, st>>>(const_cast<int32_t*>(cfg.d_step));
+    // Adam and the delta are one kernel: both phase marks follow it
+    if (mark) {
+        mark(events, event, st);
+        mark(events, event + 1, st);
+    }
 }
 
 bool attr_group(int attr, int* lo, int* hi, int* f32) {
@@ -427,22 +536,22 @@ bool attr_group(int attr, int* lo, int* hi, int* f32) {
 }
 
 void launch_tensor_delta(const float* theta, float* baseline, int64_t n, int attr, float thr, uint32_t* d_idx,
-                         uint8_t* d_vals, uint32_t* d_count, char* scratch, cudaStream_t st) {
+                         uint8_t* d_vals, uint32_t* d_count, char* scratch, DevStatus* status, long long spin,
+                         cudaStream_t st) {
     Group gr;
     attr_group(attr, &gr.lo, &gr.hi, &gr.f32);
-    Carver c(scratch);
-    uint8_t* flags = c.take<uint8_t>(n > 0 ? n : 1);
-    const int64_t nblk = (n + kDeltaThreads - 1) / kDeltaThreads;
-    uint32_t* sums = c.take<uint32_t>(nblk + 1);
     if (n <= 0) {
         cudaMemsetAsync(d_count, 0, sizeof(uint32_t), st);
         return;
     }
-    const float4* th = reinterpret_cast<const float4*>(theta);
-    float4* b = reinterpret_cast<float4*>(baseline);
-    k_tdelta_flags<<<(unsigned)nblk, kDeltaThreads, 0, st>>>(th, b, n, gr, thr, flags, sums);
-    k_scan_sums<<<1, 1024, 0, st>>>(sums, nblk, d_count, -1, nullptr);
-    k_tdelta_emit<<<(unsigned)nblk, kDeltaThreads, 0, st>>>(th, b, n, gr, flags, sums, d_idx, d_vals);
+    const int64_t nblk = (n + kDeltaThreads - 1) / kDeltaThreads;
+    Carver c(scratch);
+    unsigned long long* lb = c.take<unsigned long long>(nblk + 1);
+    uint32_t* ticket = c.take<uint32_t>(1);
+    cudaMemsetAsync(scratch, 0, c.off, st);
+    k_tdelta_onepass<<<(unsigned)nblk, kDeltaThreads, 0, st>>>(reinterpret_cast<const float4*>(theta),
+                                                              reinterpret_cast<float4*>(baseline), n, gr, thr, d_idx,
+                                                              d_vals, d_count, lb, ticket, nblk, status, spin);
 }
 
 void launch_apply_tensor_delta(float* params, int64_t n, int attr, const uint32_t* d_idx, const uint8_t* d_vals,

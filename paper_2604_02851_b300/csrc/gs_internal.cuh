@@ -75,6 +75,68 @@ struct WaitCfg {
     int64_t withhold = -1;
 };
 
+// ------------------------------------------------------------ decoupled look-back
+// Slots of a look-back array hold (flag | count): kFlagAgg when a block has
+// published its own count, kFlagInc when it has published the inclusive
+// prefix through itself.
+constexpr unsigned long long kFlagAgg = 1ULL << 62;
+constexpr unsigned long long kFlagInc = 2ULL << 62;
+constexpr unsigned long long kValMask = (1ULL << 62) - 1;
+
+__device__ __forceinline__ unsigned long long ld_volatile(const unsigned long long* p) {
+    return *reinterpret_cast<const volatile unsigned long long*>(p);
+}
+
+__device__ __forceinline__ void st_volatile(unsigned long long* p, unsigned long long v) {
+    *reinterpret_cast<volatile unsigned long long*>(p) = v;
+}
+
+// Exclusive prefix of `mine` over the slots 0..slot-1 of a look-back array
+// whose slots hold (flag | count); publishes this slot's inclusive value.
+// Four predecessors are read per round trip.  Bounded: when a round finds
+// no predecessor ready more than `spin` clock cycles after the wait began, it
+// records GS_ERR_TIMEOUT, publishes the partial inclusive value (so that
+// later slots need not wait as long) and returns false.
+__device__ __forceinline__ bool look_back(unsigned long long* lb, int64_t slot, int stride,
+                                          unsigned long long mine, unsigned long long* excl_out,
+                                          DevStatus* status, long long spin) {
+    unsigned long long excl = 0;
+    bool ok = true;
+    if (slot > 0) {
+        int64_t p = slot - 1;
+        const long long t0 = clock64();
+        for (;;) {
+            unsigned long long x[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) x[k] = (p - k >= 0) ? ld_volatile(lb + (p - k) * stride) : 0ULL;
+            bool done = false;
+            int used = 0;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                if (done || used < k) break;  // stop at the first slot that is not ready
+                if (!(x[k] & (kFlagAgg | kFlagInc))) break;
+                excl += x[k] & kValMask;
+                used = k + 1;
+                if (x[k] & kFlagInc) done = true;
+            }
+            if (done) break;
+            p -= used;
+            // nothing ready: back off so that the polling does not take the
+            // issue slots of the SM's other tiles (250 ns measured best of
+            // 32-500 ns)
+            if (used == 0) __nanosleep(250);
+            if (used == 0 && clock64() - t0 > spin) {
+                record_status(status, GS_ERR_TIMEOUT, slot);
+                ok = false;
+                break;
+            }
+        }
+        st_volatile(lb + slot * stride, kFlagInc | (excl + mine));
+    }
+    *excl_out = excl;
+    return ok;
+}
+
 // ------------------------------------------------------------ launchers
 // Every launcher enqueues on `st`; none synchronises or allocates.
 
@@ -281,21 +343,33 @@ size_t precull_scratch_bytes(const gs_camera* host_cams, int V);
 void launch_cell_visibility(const gs_camera* d_cams, const gs_camera* host_cams, int V, const float* depth,
                             const gs_precull& grid, uint8_t* vis, char* scratch, cudaStream_t st);
 
+// Delta extraction in three kernels (flags and block sums, one-block scan,
+// ordered emit) over scratch that needs no clearing: the allocation-free
+// entry point.
 size_t delta_scratch_bytes(int64_t n);
 void launch_delta(const float* theta, float* baseline, int64_t n, float thr, uint32_t* d_idx,
                   uint8_t* d_records, uint32_t* d_count, char* scratch, cudaStream_t st);
-// The training step's Adam update and delta extraction: Adam fused with the
-// changed test (k_adam_flags), the step counter increment, then (after the
-// optional phase mark) the scan and the record emission.
+// Delta extraction in one pass (decoupled look-back over block tickets; the
+// scratch is cleared by the launch): gs_extract_delta.
+size_t delta_onepass_scratch_bytes(int64_t n);
+void launch_delta_onepass(const float* theta, float* baseline, int64_t n, float thr, uint32_t* d_idx,
+                          uint8_t* d_records, uint32_t* d_count, char* scratch, DevStatus* status, long long spin,
+                          cudaStream_t st);
+// The training step's Adam update and delta extraction in one kernel
+// (k_adam_delta, scratch as the one-pass delta), then the step counter
+// increment and the phase marks `event` (after Adam) and `event` + 1 (after
+// the delta), both after the kernel.
 void launch_adam_delta(float* theta, const float* grad, float* m, float* v, int64_t n, const gs_adam_cfg& cfg,
                        const uint8_t* fwd, float* baseline, float thr, uint32_t* d_idx, uint8_t* d_records,
-                       uint32_t* d_count, char* scratch, cudaStream_t st, void (*mark)(void* const*, int, cudaStream_t),
-                       void* const* events, int event);
+                       uint32_t* d_count, char* scratch, DevStatus* status, long long spin, cudaStream_t st,
+                       void (*mark)(void* const*, int, cudaStream_t), void* const* events, int event);
 
 // Tensor deltas of one attribute group (GS_ATTR_*) and client-side replay.
 bool attr_group(int attr, int* lo, int* hi, int* f32);
+// (one pass, scratch as launch_delta_onepass)
 void launch_tensor_delta(const float* theta, float* baseline, int64_t n, int attr, float thr, uint32_t* d_idx,
-                         uint8_t* d_vals, uint32_t* d_count, char* scratch, cudaStream_t st);
+                         uint8_t* d_vals, uint32_t* d_count, char* scratch, DevStatus* status, long long spin,
+                         cudaStream_t st);
 void launch_apply_tensor_delta(float* params, int64_t n, int attr, const uint32_t* d_idx, const uint8_t* d_vals,
                                const uint32_t* d_count, DevStatus* status, int sm_count, cudaStream_t st);
 void launch_apply_delta(float* params, int64_t n, const uint8_t* d_records, const uint32_t* d_count,

@@ -39,73 +39,15 @@ constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 constexpr int kMinTileKeys = kThreads * 8;       // smallest onesweep tile (look-back sizing)
 constexpr int kMaxPasses = 4;
-constexpr unsigned long long kFlagAgg = 1ULL << 62;
-constexpr unsigned long long kFlagInc = 2ULL << 62;
-constexpr unsigned long long kValMask = (1ULL << 62) - 1;
-
 __device__ __forceinline__ uint32_t lanemask_lt() {
     uint32_t m;
     asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
     return m;
 }
 
-__device__ __forceinline__ unsigned long long ld_volatile(const unsigned long long* p) {
-    return *reinterpret_cast<const volatile unsigned long long*>(p);
-}
-
-__device__ __forceinline__ void st_volatile(unsigned long long* p, unsigned long long v) {
-    *reinterpret_cast<volatile unsigned long long*>(p) = v;
-}
-
 __device__ __forceinline__ int64_t clamp_count(const uint32_t* d_count, int64_t cap) {
     const int64_t k = (int64_t)*d_count;
     return k < cap ? k : cap;
-}
-
-// Exclusive prefix of `mine` over the slots 0..slot-1 of a look-back array
-// whose slots hold (flag | count); publishes this slot's inclusive value.
-// Four predecessors are read per round trip.  Bounded: when a round finds
-// no predecessor ready more than `spin` clock cycles after the wait began, it
-// records GS_ERR_TIMEOUT, publishes the partial inclusive value (so that
-// later slots need not wait as long) and returns false.
-__device__ __forceinline__ bool look_back(unsigned long long* lb, int64_t slot, int stride,
-                                          unsigned long long mine, unsigned long long* excl_out,
-                                          DevStatus* status, long long spin) {
-    unsigned long long excl = 0;
-    bool ok = true;
-    if (slot > 0) {
-        int64_t p = slot - 1;
-        const long long t0 = clock64();
-        for (;;) {
-            unsigned long long x[4];
-#pragma unroll
-            for (int k = 0; k < 4; ++k) x[k] = (p - k >= 0) ? ld_volatile(lb + (p - k) * stride) : 0ULL;
-            bool done = false;
-            int used = 0;
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                if (done || used < k) break;  // stop at the first slot that is not ready
-                if (!(x[k] & (kFlagAgg | kFlagInc))) break;
-                excl += x[k] & kValMask;
-                used = k + 1;
-                if (x[k] & kFlagInc) done = true;
-            }
-            if (done) break;
-            p -= used;
-            // nothing ready: back off so that the polling does not take the
-            // issue slots of the SM's other tiles (250 ns measured best of
-            // 32-500 ns)
-            if (used == 0) __nanosleep(250);
-            if (used == 0 && clock64() - t0 > spin) {
-                record_status(status, GS_ERR_TIMEOUT, slot);
-                ok = false;
-                break;
-            }
-        }
-        st_volatile(lb + slot * stride, kFlagInc | (excl + mine));
-    }
-    *excl_out = excl;
-    return ok;
 }
 
 // ------------------------------------------------------------ histograms
