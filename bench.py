@@ -7,9 +7,12 @@ parameter per step.  One step = one graph launch of the whole batched step.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-Prints one JSON line (rank 0).  Multi-GPU runs are independent replicas
-(one model per GPU, no collective on the data path); the timing is the max
-over ranks.
+Prints one JSON line (rank 0).  With N > 1 GPUs the views of each step are
+split over the ranks (rank r renders views r, r + N, ...) and their
+gradients are summed by an NCCL all-reduce before every rank runs the same
+update (paper_2604_02851_b300.parallel); the throughput is steps of the whole
+job over the slowest rank's time.  --parallelism replicas instead runs one
+independent model per GPU.
 """
 from __future__ import annotations
 
@@ -102,10 +105,12 @@ def phase_model(n, V, K, total_tiles, npix, sum_nc, n_changed, binning, passes, 
         "loss": ("hbm", 3 * npix * 44),
         "raster_bwd": ("alu", sum_nc * RASTER_BWD_FLOP_PER_FRAGMENT),
         "project_bwd": ("hbm", nt * 480 + V * nt * (48 + 32)),
-        # Adam fused with the whole delta extraction (one kernel): theta, grad,
-        # m, v, baseline read, theta, m, v written; per changed Gaussian its
-        # index and record written, its baseline rewritten
-        "adam": ("hbm", 60 * nt * 4 * 8 + n_changed * (4 + 128 + 240)),
+        # Adam fused with the delta's changed test: theta, grad, m, v, baseline
+        # read, theta, m, v written, one flag byte out
+        "adam": ("hbm", 60 * nt * 4 * 8 + nt),
+        # the records: flags read, per changed Gaussian theta re-read, index,
+        # record and baseline written
+        "delta": ("hbm", nt + n_changed * (240 + 4 + 128 + 240)),
     }
 
 
@@ -141,7 +146,8 @@ def measured_traffic(workload, kernel):
 
 # phases that are one kernel (plus negligible set-up launches), by kernel name
 SINGLE_KERNEL_PHASES = {"project": "k_project", "emit": "k_emit", "render_fwd": "k_render_fwd",
-                        "raster_bwd": "k_raster_bwd", "project_bwd": "k_project_bwd", "adam": "k_adam_delta"}
+                        "raster_bwd": "k_raster_bwd", "project_bwd": "k_project_bwd", "adam": "k_adam_flags",
+                        "delta": "k_delta_emit_lb"}
 
 
 def gpu_launches_per_step(binning, passes):
@@ -151,11 +157,11 @@ def gpu_launches_per_step(binning, passes):
     init, look-back clear, scan, passes, ranges fix, chunk table, chunk
     owners, bitmaps;
     direct: emission, ranges init, look-back clear, scan, passes, ranges
-    fix), compositing, loss (2), adjoints (2), Adam fused with the delta
-    extraction and the step counter (2)."""
+    fix), compositing, loss (2), adjoints (2), Adam with the delta's changed
+    test and the step counter (2), the delta records (1)."""
     depth = 8
     sort = (9 + passes) if binning == "two_level" else (5 + passes)
-    return 1 + 1 + depth + sort + 1 + 2 + 1 + 1 + 2
+    return 1 + 1 + depth + sort + 1 + 2 + 1 + 1 + 2 + 1
 
 
 def replica_seeds(rank: int):
@@ -375,6 +381,174 @@ def run_reference(args, rank, world):
 
 
 # ---------------------------------------------------------------- GPU leg
+def run_sharded(args, rank, world, local_rank):
+    """The training step with its views split over the ranks: per step, each
+    rank's gradient part (one graph launch over its views), the all-reduce of
+    the gradient, the update (the same on every rank).  Strong scaling: every
+    step covers all views of the workload whatever the number of ranks."""
+    import torch
+    import paper_2604_02851_b300 as gs
+    from paper_2604_02851_b300 import parallel
+    from paper_2604_02851_b300.train import estimate_keys
+
+    if args.frozen_frac > 0 or args.precull or args.relight or args.workload in FAR_WORKLOADS:
+        raise SystemExit("view sharding runs the plain or dynamic workloads (no freezing, preculling or relighting)")
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    n, sh, V, W, H = WORKLOADS[args.workload]
+    views = parallel.shard_views(V, world, rank)
+    cams = gi.ring_cameras(V, W, H)
+    sub = parallel.subset_cameras(cams, views)
+    # one model, replicated on every rank
+    params = torch.from_numpy(gi.make_scene(n, sh, gi.SEED_MODEL)).to(dev)
+    tparams = torch.from_numpy(gi.make_scene(n, sh, gi.SEED_TARGET)).to(dev)
+    dynamic = args.workload in DYNAMIC_WORKLOADS
+    drift = None if dynamic else torch.from_numpy(gi.drift_signs(n)).to(dev) * 1e-3
+    frames = max(args.steps, 1) + args.warmup + args.e2e_steps + 16
+    dyn = None
+    if dynamic:
+        poses = gi.frame_poses(frames, 16)
+        lights = gi.light_directions(frames)
+        dyn = gs.Dynamics(gi.rigid_groups(n, 16), poses[0], gi.unit_normals(n), lights[0], 0.3, 0.7, device=dev)
+    frame = [0]
+
+    def make_ctx():
+        return gs.Context(local_rank, 0, tile=args.tile, sort_bits=args.sort_bits, sort_items=args.sort_items,
+                          binning=args.binning, raster_threads=args.raster_threads,
+                          raster_bwd_threads=args.raster_bwd_threads)
+    ctx = make_ctx()
+    keys_cap = estimate_keys(ctx, params, sh, sub, slack=1.3, dyn=dyn)
+    if args.autotune:
+        ctx.reserve(ctx.workspace_size(sub, n, keys_cap))
+        best, _ = gs.gs_autotune(ctx, params, sh, sub, keys_cap, reps=2, dyn=dyn)
+        args.binning, args.sort_bits = best["binning"], best["sort_bits"]
+        args.sort_items, args.raster_threads = best["sort_items"], best["raster_threads"]
+        args.raster_bwd_threads = best["raster_bwd_threads"]
+    st = parallel.ViewShardedTrainer(params, sh, cams, keys_cap, rank, world, ctx=ctx, dyn=dyn)
+    tr = st.trainer
+    tctx = make_ctx()
+    tctx.reserve(tctx.workspace_size(sub, n, keys_cap))
+
+    def next_targets():
+        if dynamic:
+            frame[0] = (frame[0] + 1) % frames
+            dyn.set_frame(poses[frame[0]], lights[frame[0]])
+        else:
+            tparams.add_(drift)
+        gs.gs_render_batch(tctx, tparams, sh, tr.d_cams, len(views), tr.total_tiles, keys_cap, tr.npix,
+                           image=st.targets, dyn=dyn)
+
+    phase_ev = [torch.cuda.Event(enable_timing=True) for _ in range(gs._lib.TRAIN_PHASE_EVENTS)]
+    next_targets()
+    tr.capture(phase_events=phase_ev)
+    for _ in range(args.warmup):
+        next_targets()
+        st.step()
+    torch.cuda.synchronize()
+    st.raise_status()
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    phase_ms = np.zeros(len(phase_ev) - 1)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local_rank)
+    for k in range(args.steps):
+        next_targets()
+        ev0[k].record()
+        st.step()
+        ev1[k].record()
+        ev1[k].synchronize()
+        for i in range(8):  # the gradient part's phases (the update runs outside the graph)
+            phase_ms[i] += event_ms(phase_ev[i], phase_ev[i + 1])
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    if world > 1:
+        torch.distributed.barrier()
+    step_ms = np.array([a.elapsed_time(b) for a, b in zip(ev0, ev1)])
+    st.raise_status()
+    t = torch.tensor([float(step_ms.sum())], dtype=torch.float64, device=dev)
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    total_ms = float(t.item())
+    value = args.steps / (total_ms / 1e3)
+    loss = st.loss()
+    phase_avg = {name: float(ms / args.steps) for name, ms in zip(gs._lib.TRAIN_PHASES[:8], phase_ms[:8])}
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    sm_mhz = clk.get("sm_mhz") or clk.get("sm_max_mhz") or 2032.0
+    fp32_peak = fp32_peak_tflops(sm_count, sm_mhz)
+    # work counts of this rank's views, for the dominant kernel's roofline
+    proj = gs.gs_project(ctx, params, sh, tr.d_cams, len(views), dyn=dyn)
+    _, vals, ranges, nk = gs.gs_bin_sort(ctx, proj, tr.d_cams, len(views), n, tr.total_tiles, keys_cap,
+                                         want_keys=False)
+    _, T, nc = gs.gs_render_fwd(ctx, proj, tr.d_cams, len(views), n, tr.total_tiles, vals, ranges, tr.npix)
+    torch.cuda.synchronize()
+    sum_nc = int(nc.to(torch.int64).sum().item())
+    del proj, vals, ranges, T, nc
+    ach = sum_nc * RASTER_BWD_FLOP_PER_FRAGMENT / (phase_avg["raster_bwd"] / 1e3) / 1e12
+    roofline = {"kernel": "k_raster_bwd", "bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": ach / fp32_peak, "traffic": None,
+                "peak_source": f"derived: {sm_count} SMs (queried) x {FP32_LANES_PER_SM} FP32 lanes x 2 x "
+                               f"{sm_mhz:.0f} MHz (median sampled)"}
+    # end to end: this rank's targets up from pinned host memory, the step,
+    # rank 0 reads the loss, the delta count and the records back
+    e2e = None
+    if args.e2e_steps > 0:
+        host = torch.empty(st.targets.numel(), dtype=torch.float32).pin_memory()
+        next_targets()
+        host.copy_(st.targets)
+        h_loss = torch.empty(1, dtype=torch.float32).pin_memory()
+        h_cnt = torch.empty(1, dtype=torch.int32).pin_memory()
+        h_rec = torch.empty((n, gs.RECORD_BYTES), dtype=torch.uint8).pin_memory()
+        h2d = d2h = 0
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.e2e_steps):
+            st.targets.copy_(host, non_blocking=True)
+            h2d += host.numel() * 4
+            st.step()
+            lt = tr.d_loss.clone()
+            parallel.reduce_gradients(lt)  # the loss of all views: the sum of the ranks' shares
+            if rank == 0:
+                h_loss.copy_(lt, non_blocking=True)
+                h_cnt.copy_(tr.d_count, non_blocking=True)
+                torch.cuda.current_stream().synchronize()
+                m = int(h_cnt.item())
+                if m:
+                    h_rec[:m].copy_(tr.d_records[:m], non_blocking=True)
+                d2h += 8 + m * gs.RECORD_BYTES
+        e1.record()
+        torch.cuda.synchronize()
+        t = torch.tensor([e0.elapsed_time(e1)], dtype=torch.float64, device=dev)
+        if world > 1:
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e = {"value": args.e2e_steps / (float(t.item()) / 1e3), "unit": "steps/s",
+               "h2d_bytes_per_step": h2d // args.e2e_steps, "d2h_bytes_per_step": d2h // args.e2e_steps,
+               "steps": args.e2e_steps,
+               "pipeline": "per step: each rank uploads its views' targets, the sharded step, rank 0 reads back "
+                           "the loss and the delta records"}
+    tctx.close()
+    if rank == 0:
+        out = {"metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+               "scaling": "strong", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+               "config": {"workload": args.workload, "gaussians": n, "sh_degree": sh, "views": V,
+                          "views_per_rank": len(views), "resolution": [W, H], "keys_cap": keys_cap,
+                          "binning": args.binning, "sort_digit_bits": args.sort_bits, "sort_items": args.sort_items,
+                          "raster_threads_per_row": args.raster_threads,
+                          "raster_bwd_threads_per_row": args.raster_bwd_threads,
+                          "l2": "inputs larger than L2 (params 240 MB, keys > 1 GB per step)",
+                          "parallelism": f"views over {world} ranks, NCCL all-reduce of the gradient"},
+               "roofline": roofline, "cpu_baseline": None, "clocks": clk, "e2e": e2e,
+               "gpu_launches": gpu_launches_per_step(
+                   args.binning, math.ceil(math.ceil(math.log2(max(tr.total_tiles, 2))) / args.sort_bits)) * args.steps,
+               "phases_ms_rank0_gradient_part": phase_avg, "loss_last": loss}
+        print(json.dumps(out), flush=True)
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     import paper_2604_02851_b300 as gs
@@ -775,7 +949,7 @@ def measure_delta_standalone(gs, torch, tr, next_targets, hbm_peak, reps=10):
     ach = work / (ms / 1e3) / 1e9
     return {"ms": ms, "changed": m, "changed_by_fused_step": fused_m, "bound": "hbm", "achieved": ach,
             "unit": "GB/s", "peak": hbm_peak, "frac": ach / hbm_peak, "algorithmic_bytes": work,
-            "kernel": "k_delta_onepass", "reps": reps}
+            "kernels": "k_delta_flags + k_delta_emit_lb", "reps": reps}
 
 
 TENSOR_GROUPS = (("mean", 0, 3, 4), ("opacity", 3, 4, 2), ("scale", 4, 7, 2), ("rotation", 8, 12, 2),
@@ -880,6 +1054,9 @@ def main():
                     help="fraction of the model held in the inference-only (frozen) pool")
     ap.add_argument("--relight", action="store_true",
                     help="SH-lighting product and per-frame light visibility (Sec. 3.4.1) in every step")
+    ap.add_argument("--parallelism", choices=("auto", "views", "replicas"), default="auto",
+                    help="N > 1 GPUs: split each step's views over the ranks (auto, views) or run one model per "
+                         "GPU (replicas); views also forces the split path on one GPU")
     ap.add_argument("--delta-reps", type=int, default=10,
                     help="time the standalone gs_extract_delta on one step's changed set (0: skip)")
     ap.add_argument("--tensor-deltas", action=argparse.BooleanOptionalAction, default=True,
@@ -895,10 +1072,13 @@ def main():
     if args.impl == "reference":
         run_reference(args, rank, world)
         return
-    if world > 1:
+    if world > 1 or args.parallelism == "views":
         import torch
         torch.distributed.init_process_group("nccl")
-    run_ours(args, rank, world, local_rank)
+    if args.parallelism == "views" or (world > 1 and args.parallelism == "auto"):
+        run_sharded(args, rank, world, local_rank)
+    else:
+        run_ours(args, rank, world, local_rank)
     if world > 1:
         import torch
         torch.distributed.destroy_process_group()

@@ -533,11 +533,28 @@ typedef struct gs_train_cfg {
                                culled cells are not rendered and get no Adam
                                update (their parameters and moments stay) */
     const gs_lighting* lighting; /* host pointer; NULL: view-dependent SH colour */
+    int32_t phases;       /* GS_TRAIN_* parts to run; 0 = GS_TRAIN_ALL */
+    int32_t _pad2;
 } gs_train_cfg;
+
+/* Parts of the training step (gs_train_cfg.phases).  GS_TRAIN_GRADIENT runs
+ * projection, binning, compositing, the loss and both adjoints and leaves
+ * dL/dparams of this call's views in io->grads (parameters, Adam moments,
+ * baseline and step counter untouched); GS_TRAIN_UPDATE runs Adam on
+ * io->grads, the delta extraction and the step counter increment.  Splitting
+ * the step lets a caller combine the gradients of several calls in between:
+ * the views of one step spread over GPUs (Sec. 3.1 renders the model from
+ * all ready reference cameras; each GPU takes some of them, with w_l1 and
+ * w_ssim scaled by its share of the views, and the rank gradients are summed
+ * before the update), or mini-batches of views accumulated on one GPU. */
+#define GS_TRAIN_GRADIENT 1
+#define GS_TRAIN_UPDATE 2
+#define GS_TRAIN_ALL 3
 
 /* One whole optimisation step over all V reference views (Sec. 3.1: "iterates
  * over ready reference cameras, optionally grouping them as mini batches"):
- * project, bin/sort, composite, loss, backward, Adam, delta extraction.
+ * project, bin/sort, composite, loss, backward, Adam, delta extraction (or
+ * the part of it cfg->phases selects).
  * Enqueue-only, no host synchronisation and no allocation: safe to capture
  * into a CUDA graph.
  * Gaussian freezing (Sec. 3.3): the n_frozen Gaussians of io.frozen are

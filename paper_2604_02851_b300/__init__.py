@@ -570,9 +570,12 @@ def train_io(params, grads, m, v, baseline, targets, image, d_loss, d_idx, d_rec
 
 def train_cfg(n, sh_degree, n_views, width, height, keys_cap, w_l1=0.8, w_ssim=0.2, bg=(0.0, 0.0, 0.0),
               delta_thr=1e-3, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, dyn: "Dynamics | None" = None,
-              n_frozen: int = 0, precull: "Precull | None" = None, lighting: "Lighting | None" = None):
+              n_frozen: int = 0, precull: "Precull | None" = None, lighting: "Lighting | None" = None,
+              phases: int = 0):
+    """gs_train_cfg; phases: _lib.TRAIN_GRADIENT, TRAIN_UPDATE or TRAIN_ALL (0 = all)."""
     cfg = _lib.gs_train_cfg()
     cfg.n_frozen = int(n_frozen)
+    cfg.phases = int(phases)
     if lighting is not None:
         cfg.lighting = C.pointer(lighting.struct)
     if precull is not None:

@@ -92,7 +92,8 @@ class gs_train_cfg(C.Structure):
                 ("width", C.c_int32), ("height", C.c_int32), ("keys_cap", C.c_int64),
                 ("w_l1", C.c_float), ("w_ssim", C.c_float), ("bg", C.c_float * 3),
                 ("delta_thr", C.c_float), ("adam", gs_adam_cfg), ("n_frozen", C.c_int64),
-                ("precull", C.POINTER(gs_precull)), ("lighting", C.POINTER(gs_lighting))]
+                ("precull", C.POINTER(gs_precull)), ("lighting", C.POINTER(gs_lighting)),
+                ("phases", C.c_int32), ("_pad2", C.c_int32)]
 
 
 assert C.sizeof(gs_camera) == 80
@@ -145,6 +146,7 @@ _SIGS = {
     "gs_light_visibility": [_P, C.POINTER(gs_scene), C.POINTER(gs_light_camera), _P, _P, _P],
 }
 TRAIN_PHASE_EVENTS = 11
+TRAIN_GRADIENT, TRAIN_UPDATE, TRAIN_ALL = 1, 2, 3  # GS_TRAIN_* in include/gs.h
 TRAIN_PHASES = ("project", "depth_sort", "emit", "tile_sort", "render_fwd", "loss", "raster_bwd", "project_bwd",
                 "adam", "delta")
 _RESTYPES = {"gs_workspace_size": C.c_size_t, "gs_total_tiles": C.c_int64, "gs_tensor_record_bytes": C.c_int32,

@@ -10,9 +10,10 @@
 // after a snapshot.  A Gaussian is sent when any of its 60 floats moved by
 // more than thr from its last transmitted value; the sent set is compacted in
 // index order and packed as 128-byte records: uint32 index, float32 mean, 56
-// float16 (RNE) attributes.  gs_extract_delta and the training step compact
-// in one pass (each block finds its output offset by decoupled look-back over
-// the blocks before it); the allocation-free entry point keeps a three-kernel
+// float16 (RNE) attributes.  A flag pass (fused with Adam in the training
+// step) marks the changed Gaussians; gs_extract_delta and the training step
+// then emit in one kernel whose blocks find their output offsets by
+// decoupled look-back; the allocation-free entry point keeps a three-kernel
 // form (flags and block sums, a one-block scan, an ordered emit) whose
 // scratch needs no clearing.
 #include <cuda_fp16.h>
@@ -124,35 +125,29 @@ __device__ __forceinline__ uint32_t delta_slot(bool changed, int64_t b, int64_t 
     return (uint32_t)s_excl + woff + __popc(bal & ((1u << lane) - 1u));
 }
 
-// gs_extract_delta in one pass: block ticket b tests Gaussians b*256 ..
-// b*256 + 255 (theta and baseline streamed once), finds its offset and
-// writes the records of its changed Gaussians.  lookback [nblk] and the
-// ticket counter start at zero.
+// The changed Gaussians' records in index order, from the flags of
+// k_delta_flags or k_adam_flags: block ticket b takes the flags of Gaussians
+// b*256 .. b*256 + 255, finds its output offset by decoupled look-back over
+// the blocks before it (short blocks: a predecessor is never long in
+// coming) and its changed threads write their records.  One kernel instead
+// of a one-block scan of the block sums followed by the emit.  lookback
+// [nblk] and the ticket counter start at zero.
 __global__ void __launch_bounds__(kDeltaThreads)
-k_delta_onepass(const float4* __restrict__ theta, float4* __restrict__ base, int64_t n, float thr,
-                uint32_t* __restrict__ d_idx, uint8_t* __restrict__ d_records, uint32_t* d_count,
-                unsigned long long* lookback, uint32_t* ticket, int64_t nblk, DevStatus* status, long long spin) {
+k_delta_emit_lb(const float4* __restrict__ theta, float4* __restrict__ base, int64_t n,
+                const uint8_t* __restrict__ flags, uint32_t* __restrict__ d_idx, uint8_t* __restrict__ d_records,
+                uint32_t* d_count, unsigned long long* lookback, uint32_t* ticket, int64_t nblk, DevStatus* status,
+                long long spin) {
     __shared__ uint32_t s_blk;
     if (threadIdx.x == 0) s_blk = atomicAdd(ticket, 1u);
     __syncthreads();
     const int64_t b = s_blk;
     const int64_t g = b * kDeltaThreads + threadIdx.x;
-    bool changed = false;
-    if (g < n) {
-        float d = 0.f;
-#pragma unroll
-        for (int p = 0; p < 15; ++p) {
-            const float4 a = theta[p * n + g], c = base[p * n + g];
-            d = fmaxf(d, fmaxf(fmaxf(fabsf(a.x - c.x), fabsf(a.y - c.y)), fmaxf(fabsf(a.z - c.z), fabsf(a.w - c.w))));
-        }
-        changed = d > thr;
-    }
+    const bool changed = g < n && flags[g];
     const uint32_t off = delta_slot(changed, b, nblk, lookback, d_count, status, spin);
     if (changed) emit_record(theta, base, n, g, off, d_idx, d_records);
 }
 
-// ---------------------------------------------------------------- delta
-
+// ---------------------------------------------------------------- delta flags
 __global__ void __launch_bounds__(kDeltaThreads)
 k_delta_flags(const float4* __restrict__ theta, const float4* __restrict__ base, int64_t n, float thr,
               uint8_t* __restrict__ flags, uint32_t* __restrict__ block_sums) {
@@ -171,38 +166,32 @@ k_delta_flags(const float4* __restrict__ theta, const float4* __restrict__ base,
     if (threadIdx.x == 0) block_sums[blockIdx.x] = cnt;
 }
 
-// The training step's Adam update fused with the whole delta extraction: one
-// thread per Gaussian (block ticket order) walks its 15 planes, updates them
-// and compares the new values with the baseline, so that the parameters are
-// read once; the block then finds its output offset by look-back and its
-// changed threads write their records (re-reading the planes they just
-// wrote).  Same arithmetic as k_adam and k_delta_onepass.  Six blocks an SM
-// (the learning rates in shared memory) keep enough loads in flight;
-// unrolling the plane loop, or 5 and 8 blocks, measured slower.
+// The training step's Adam update fused with the changed test of the delta
+// extraction: one thread per Gaussian walks its 15 planes, updates them and
+// compares the new values with the baseline, so that the parameters are read
+// once.  Same arithmetic as k_adam and k_delta_flags.  Six blocks an SM (40
+// registers, the learning rates in shared memory) keep enough loads in
+// flight; unrolling the plane loop, or 5 and 8 blocks, measured slower.
 __global__ void __launch_bounds__(kDeltaThreads, 6)
-k_adam_delta(float4* __restrict__ theta, const float4* __restrict__ grad, float4* __restrict__ m,
-             float4* __restrict__ v, float4* __restrict__ base, int64_t n, LrTable lr, float b1, float b2,
+k_adam_flags(float4* __restrict__ theta, const float4* __restrict__ grad, float4* __restrict__ m,
+             float4* __restrict__ v, const float4* __restrict__ base, int64_t n, LrTable lr, float b1, float b2,
              float eps, int host_step, const int32_t* __restrict__ d_step, const uint8_t* __restrict__ fwd,
-             float thr, uint32_t* __restrict__ d_idx, uint8_t* __restrict__ d_records, uint32_t* d_count,
-             unsigned long long* lookback, uint32_t* ticket, int64_t nblk, DevStatus* status, long long spin) {
+             float thr, uint8_t* __restrict__ flags, uint32_t* __restrict__ block_sums) {
     __shared__ float s_lr[60];
-    __shared__ uint32_t s_blk;
     if (threadIdx.x < 60) s_lr[threadIdx.x] = lr.lr[threadIdx.x];
-    if (threadIdx.x == 0) s_blk = atomicAdd(ticket, 1u);
     __syncthreads();
     const int step = d_step ? *d_step : host_step;
     const float bc1 = 1.f - powf(b1, (float)step);
     const float sbc2 = sqrtf(1.f - powf(b2, (float)step));
-    const int64_t b = s_blk;
-    const int64_t g = b * kDeltaThreads + threadIdx.x;
-    bool changed = false;
+    const int64_t g = (int64_t)blockIdx.x * kDeltaThreads + threadIdx.x;
+    uint32_t changed = 0;
     if (g < n) {
         const bool upd = !fwd || fwd[g];  // preculled: no update
 #pragma unroll 1
         for (int p = 0; p < 15; ++p) {
             const int64_t i = p * n + g;
             float4 th = theta[i];
-            const float4 bb = base[i];
+            const float4 b = base[i];
             if (upd) {
                 const float4 gr = grad[i];
                 float4 mm = m[i], vv = v[i];
@@ -211,12 +200,13 @@ k_adam_delta(float4* __restrict__ theta, const float4* __restrict__ grad, float4
                 v[i] = vv;
                 theta[i] = th;
             }
-            const float d = fmaxf(fmaxf(fabsf(th.x - bb.x), fabsf(th.y - bb.y)), fmaxf(fabsf(th.z - bb.z), fabsf(th.w - bb.w)));
-            changed |= d > thr;
+            const float d = fmaxf(fmaxf(fabsf(th.x - b.x), fabsf(th.y - b.y)), fmaxf(fabsf(th.z - b.z), fabsf(th.w - b.w)));
+            changed |= (d > thr) ? 1u : 0u;
         }
+        flags[g] = (uint8_t)changed;
     }
-    const uint32_t off = delta_slot(changed, b, nblk, lookback, d_count, status, spin);
-    if (changed) emit_record(theta, base, n, g, off, d_idx, d_records);
+    const uint32_t cnt = __syncthreads_count(changed);
+    if (threadIdx.x == 0) block_sums[blockIdx.x] = cnt;
 }
 
 __global__ void __launch_bounds__(kDeltaThreads)
@@ -279,30 +269,40 @@ __device__ __forceinline__ void set_lane(float4& a, int l, float v) {
     if (l == 0) a.x = v; else if (l == 1) a.y = v; else if (l == 2) a.z = v; else a.w = v;
 }
 
-// Tensor delta of one group in one pass (as k_delta_onepass): block ticket
-// b tests its Gaussians' group floats, finds its offset by look-back and
-// writes each changed Gaussian's index, its group record (float32 or float16
-// RNE, densely packed) and the group's baseline floats.
 __global__ void __launch_bounds__(kDeltaThreads)
-k_tdelta_onepass(const float4* __restrict__ theta, float4* __restrict__ base, int64_t n, Group gr, float thr,
-                 uint32_t* __restrict__ d_idx, uint8_t* __restrict__ d_vals, uint32_t* d_count,
-                 unsigned long long* lookback, uint32_t* ticket, int64_t nblk, DevStatus* status, long long spin) {
+k_tdelta_flags(const float4* __restrict__ theta, const float4* __restrict__ base, int64_t n, Group gr, float thr,
+               uint8_t* __restrict__ flags, uint32_t* __restrict__ block_sums) {
+    const int64_t g = (int64_t)blockIdx.x * kDeltaThreads + threadIdx.x;
+    uint32_t changed = 0;
+    if (g < n) {
+        for (int p = gr.lo >> 2; p <= (gr.hi - 1) >> 2; ++p) {
+            const float4 a = theta[p * n + g], b = base[p * n + g];
+#pragma unroll
+            for (int l = 0; l < 4; ++l) {
+                const int f = 4 * p + l;
+                if (f >= gr.lo && f < gr.hi && fabsf(lane_of(a, l) - lane_of(b, l)) > thr) changed = 1u;
+            }
+        }
+        flags[g] = (uint8_t)changed;
+    }
+    const uint32_t cnt = __syncthreads_count(changed);
+    if (threadIdx.x == 0) block_sums[blockIdx.x] = cnt;
+}
+
+// A group's records in index order from k_tdelta_flags's flags (as
+// k_delta_emit_lb): each changed Gaussian's index, its group record (float32
+// or float16 RNE, densely packed) and the group's baseline floats.
+__global__ void __launch_bounds__(kDeltaThreads)
+k_tdelta_emit_lb(const float4* __restrict__ theta, float4* __restrict__ base, int64_t n, Group gr,
+                 const uint8_t* __restrict__ flags, uint32_t* __restrict__ d_idx, uint8_t* __restrict__ d_vals,
+                 uint32_t* d_count, unsigned long long* lookback, uint32_t* ticket, int64_t nblk, DevStatus* status,
+                 long long spin) {
     __shared__ uint32_t s_blk;
     if (threadIdx.x == 0) s_blk = atomicAdd(ticket, 1u);
     __syncthreads();
     const int64_t b = s_blk;
     const int64_t g = b * kDeltaThreads + threadIdx.x;
-    bool changed = false;
-    if (g < n) {
-        for (int p = gr.lo >> 2; p <= (gr.hi - 1) >> 2; ++p) {
-            const float4 a = theta[p * n + g], c = base[p * n + g];
-#pragma unroll
-            for (int l = 0; l < 4; ++l) {
-                const int f = 4 * p + l;
-                if (f >= gr.lo && f < gr.hi && fabsf(lane_of(a, l) - lane_of(c, l)) > thr) changed = true;
-            }
-        }
-    }
+    const bool changed = g < n && flags[g];
     const uint32_t off = delta_slot(changed, b, nblk, lookback, d_count, status, spin);
     if (!changed) return;
     d_idx[off] = (uint32_t)g;
@@ -472,55 +472,77 @@ void launch_delta(const float* theta, float* baseline, int64_t n, float thr, uin
     k_delta_emit<<<(unsigned)nblk, kDeltaThreads, 0, st>>>(th, b, n, flags, sums, d_idx, d_records);
 }
 
-size_t delta_onepass_scratch_bytes(int64_t n) {
-    Carver c(nullptr);
-    c.take<unsigned long long>((n + kDeltaThreads - 1) / kDeltaThreads + 1);
-    c.take<uint32_t>(1);
-    return c.off;
+// Scratch of the look-back emit: flags, block sums (written by the flag
+// kernels, read only by the three-kernel form), then the look-back slots and
+// the ticket counter, which the launch clears.
+struct LbScratch {
+    uint8_t* flags;
+    uint32_t* sums;
+    unsigned long long* lookback;
+    uint32_t* ticket;
+    char* clear_from;
+    size_t clear_bytes;
+    size_t bytes;
+};
+
+LbScratch carve_lb(char* scratch, int64_t n) {
+    Carver c(scratch);
+    LbScratch l;
+    const int64_t nblk = (n + kDeltaThreads - 1) / kDeltaThreads;
+    l.flags = c.take<uint8_t>(n > 0 ? n : 1);
+    l.sums = c.take<uint32_t>(nblk + 1);
+    l.lookback = c.take<unsigned long long>(nblk + 1);
+    const size_t from = c.off - sizeof(unsigned long long) * (size_t)(nblk + 1);
+    l.ticket = c.take<uint32_t>(1);
+    l.clear_from = scratch ? scratch + from : nullptr;
+    l.clear_bytes = c.off - from;
+    l.bytes = c.off;
+    return l;
 }
 
-void launch_delta_onepass(const float* theta, float* baseline, int64_t n, float thr, uint32_t* d_idx,
-                          uint8_t* d_records, uint32_t* d_count, char* scratch, DevStatus* status, long long spin,
-                          cudaStream_t st) {
+size_t delta_lb_scratch_bytes(int64_t n) { return carve_lb(nullptr, n).bytes; }
+
+void launch_delta_lb(const float* theta, float* baseline, int64_t n, float thr, uint32_t* d_idx, uint8_t* d_records,
+                     uint32_t* d_count, char* scratch, DevStatus* status, long long spin, cudaStream_t st) {
     if (n <= 0) {
         cudaMemsetAsync(d_count, 0, sizeof(uint32_t), st);
         return;
     }
     const int64_t nblk = (n + kDeltaThreads - 1) / kDeltaThreads;
-    Carver c(scratch);
-    unsigned long long* lb = c.take<unsigned long long>(nblk + 1);
-    uint32_t* ticket = c.take<uint32_t>(1);
-    cudaMemsetAsync(scratch, 0, c.off, st);
-    k_delta_onepass<<<(unsigned)nblk, kDeltaThreads, 0, st>>>(reinterpret_cast<const float4*>(theta),
-                                                             reinterpret_cast<float4*>(baseline), n, thr, d_idx,
-                                                             d_records, d_count, lb, ticket, nblk, status, spin);
+    const LbScratch l = carve_lb(scratch, n);
+    cudaMemsetAsync(l.clear_from, 0, l.clear_bytes, st);
+    const float4* th = reinterpret_cast<const float4*>(theta);
+    float4* b = reinterpret_cast<float4*>(baseline);
+    k_delta_flags<<<(unsigned)nblk, kDeltaThreads, 0, st>>>(th, b, n, thr, l.flags, l.sums);
+    k_delta_emit_lb<<<(unsigned)nblk, kDeltaThreads, 0, st>>>(th, b, n, l.flags, d_idx, d_records, d_count,
+                                                             l.lookback, l.ticket, nblk, status, spin);
 }
 
 void launch_adam_delta(float* theta, const float* grad, float* m, float* v, int64_t n, const gs_adam_cfg& cfg,
                        const uint8_t* fwd, float* baseline, float thr, uint32_t* d_idx, uint8_t* d_records,
                        uint32_t* d_count, char* scratch, DevStatus* status, long long spin, cudaStream_t st,
                        void (*mark)(void* const*, int, cudaStream_t), void* const* events, int event) {
+    const int64_t nblk = (n + kDeltaThreads - 1) / kDeltaThreads;
+    const LbScratch l = carve_lb(scratch, n);
     if (n > 0) {
-        const int64_t nblk = (n + kDeltaThreads - 1) / kDeltaThreads;
-        Carver c(scratch);
-        unsigned long long* lb = c.take<unsigned long long>(nblk + 1);
-        uint32_t* ticket = c.take<uint32_t>(1);
-        cudaMemsetAsync(scratch, 0, c.off, st);
+        cudaMemsetAsync(l.clear_from, 0, l.clear_bytes, st);
         LrTable lr;
         for (int i = 0; i < 60; ++i) lr.lr[i] = cfg.lr[i];
-        k_adam_delta<<<(unsigned)nblk, kDeltaThreads, 0, st>>>(
+        k_adam_flags<<<(unsigned)nblk, kDeltaThreads, 0, st>>>(
             reinterpret_cast<float4*>(theta), reinterpret_cast<const float4*>(grad), reinterpret_cast<float4*>(m),
-            reinterpret_cast<float4*>(v), reinterpret_cast<float4*>(baseline), n, lr, cfg.beta1, cfg.beta2,
-            cfg.eps, cfg.step, cfg.d_step, fwd, thr, d_idx, d_records, d_count, lb, ticket, nblk, status, spin);
-    } else {
-        cudaMemsetAsync(d_count, 0, sizeof(uint32_t), st);
+            reinterpret_cast<float4*>(v), reinterpret_cast<const float4*>(baseline), n, lr, cfg.beta1, cfg.beta2,
+            cfg.eps, cfg.step, cfg.d_step, fwd, thr, l.flags, l.sums);
     }
     if (cfg.d_step && cfg.increment) k_inc_step<<<1, 1, 0, st>>>(const_cast<int32_t*>(cfg.d_step));
-    // Adam and the delta are one kernel: both phase marks follow it
-    if (mark) {
-        mark(events, event, st);
-        mark(events, event + 1, st);
+    if (mark) mark(events, event, st);
+    if (n <= 0) {
+        cudaMemsetAsync(d_count, 0, sizeof(uint32_t), st);
+    } else {
+        k_delta_emit_lb<<<(unsigned)nblk, kDeltaThreads, 0, st>>>(
+            reinterpret_cast<const float4*>(theta), reinterpret_cast<float4*>(baseline), n, l.flags, d_idx, d_records,
+            d_count, l.lookback, l.ticket, nblk, status, spin);
     }
+    if (mark) mark(events, event + 1, st);
 }
 
 bool attr_group(int attr, int* lo, int* hi, int* f32) {
@@ -545,13 +567,13 @@ void launch_tensor_delta(const float* theta, float* baseline, int64_t n, int att
         return;
     }
     const int64_t nblk = (n + kDeltaThreads - 1) / kDeltaThreads;
-    Carver c(scratch);
-    unsigned long long* lb = c.take<unsigned long long>(nblk + 1);
-    uint32_t* ticket = c.take<uint32_t>(1);
-    cudaMemsetAsync(scratch, 0, c.off, st);
-    k_tdelta_onepass<<<(unsigned)nblk, kDeltaThreads, 0, st>>>(reinterpret_cast<const float4*>(theta),
-                                                              reinterpret_cast<float4*>(baseline), n, gr, thr, d_idx,
-                                                              d_vals, d_count, lb, ticket, nblk, status, spin);
+    const LbScratch l = carve_lb(scratch, n);
+    cudaMemsetAsync(l.clear_from, 0, l.clear_bytes, st);
+    const float4* th = reinterpret_cast<const float4*>(theta);
+    float4* b = reinterpret_cast<float4*>(baseline);
+    k_tdelta_flags<<<(unsigned)nblk, kDeltaThreads, 0, st>>>(th, b, n, gr, thr, l.flags, l.sums);
+    k_tdelta_emit_lb<<<(unsigned)nblk, kDeltaThreads, 0, st>>>(th, b, n, gr, l.flags, d_idx, d_vals, d_count,
+                                                              l.lookback, l.ticket, nblk, status, spin);
 }
 
 void launch_apply_tensor_delta(float* params, int64_t n, int attr, const uint32_t* d_idx, const uint8_t* d_vals,

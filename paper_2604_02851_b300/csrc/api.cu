@@ -106,7 +106,7 @@ FusedPlan plan_fused(void* base, int V, int64_t n, int64_t keys_cap, int64_t tot
         p.dimage = c.take<float>(3 * total_pixels);
         p.loss = c.take<char>(loss_scratch_bytes(V, H, W));
         p.grad2d = c.take<float>((size_t)V * n * kGradStride);
-        p.delta = c.take<char>(std::max(delta_scratch_bytes(n), delta_onepass_scratch_bytes(n)));
+        p.delta = c.take<char>(std::max(delta_scratch_bytes(n), delta_lb_scratch_bytes(n)));
         p.fwd = c.take<uint8_t>(n > 0 ? n : 1);
     }
     p.bytes = c.off;
@@ -418,10 +418,10 @@ gs_status_t gs_extract_delta(gs_ctx* ctx, const float* theta, float* baseline, i
         n >= (1LL << 32) || !(thr >= 0.f))
         return GS_ERR_ARG;
     Carver c(ctx->ws);
-    char* ds = c.take<char>(delta_onepass_scratch_bytes(n));
+    char* ds = c.take<char>(delta_lb_scratch_bytes(n));
     if (check_ws(ctx, c.off)) return GS_ERR_CAPACITY;
     DeviceGuard g(ctx->device);
-    launch_delta_onepass(theta, baseline, n, thr, d_idx, d_records, d_count, ds, ctx->d_status, ctx->wait_cycles,
+    launch_delta_lb(theta, baseline, n, thr, d_idx, d_records, d_count, ds, ctx->d_status, ctx->wait_cycles,
                          S(stream));
     return launch_check();
 }
@@ -439,7 +439,7 @@ gs_status_t gs_extract_tensor_delta(gs_ctx* ctx, const float* theta, float* base
         n >= (1LL << 32) || !(thr >= 0.f) || !attr_group(attr, &lo, &hi, &f32))
         return GS_ERR_ARG;
     Carver c(ctx->ws);
-    char* ds = c.take<char>(delta_onepass_scratch_bytes(n));
+    char* ds = c.take<char>(delta_lb_scratch_bytes(n));
     if (check_ws(ctx, c.off)) return GS_ERR_CAPACITY;
     DeviceGuard g(ctx->device);
     launch_tensor_delta(theta, baseline, n, attr, thr, d_idx, static_cast<uint8_t*>(d_vals), d_count, ds,
@@ -523,8 +523,10 @@ gs_status_t gs_train_step_events(gs_ctx* ctx, const gs_camera* d_cams, const gs_
         !io->d_loss || !io->d_delta_idx || !io->d_delta_records || !io->d_delta_count || !io->d_step ||
         bad_dyn(cfg->dyn) || bad_precull(cfg->precull) || bad_lighting(cfg->lighting, cfg->dyn) ||
         cfg->n_frozen < 0 || (cfg->n_frozen > 0 && !io->frozen) ||
-        (int64_t)cfg->n_views * (cfg->n + cfg->n_frozen) >= (1LL << 32))
+        (int64_t)cfg->n_views * (cfg->n + cfg->n_frozen) >= (1LL << 32) || cfg->phases < 0 ||
+        cfg->phases > GS_TRAIN_ALL)
         return GS_ERR_ARG;
+    const int phases = cfg->phases ? cfg->phases : GS_TRAIN_ALL;
     const int V = cfg->n_views;
     const int64_t na = cfg->n;                  // active pool
     const int64_t n = cfg->n + cfg->n_frozen;   // every rendered Gaussian
@@ -542,6 +544,22 @@ gs_status_t gs_train_step_events(gs_ctx* ctx, const gs_camera* d_cams, const gs_
     mark(ev, 0, st);
     launch_view_table(d_cams, V, B, p.vt, tt, ctx->d_status, st);
     const Dyn dyn = scene_dyn(ctx, cfg->dyn, cfg->precull, p.fwd, cfg->lighting, st);
+    if (!(phases & GS_TRAIN_GRADIENT)) {
+        // update only: the gradient of the caller's io->grads; the phase marks
+        // of the skipped part are recorded together.  Preculling still marks
+        // the Gaussians it keeps (Adam leaves the others).
+        if (cfg->precull)
+            launch_project(io->params, na, cfg->sh_degree, dyn, d_cams, p.vt, V, B, p.proj, s.dkv[0], st, 0, n,
+                           s.rects);
+        for (int e = 1; e <= 8; ++e) mark(ev, e, st);
+        gs_adam_cfg ac = cfg->adam;
+        ac.d_step = io->d_step;
+        ac.increment = 1;
+        launch_adam_delta(io->params, io->grads, io->adam_m, io->adam_v, na, ac, cfg->precull ? p.fwd : nullptr,
+                          io->baseline, cfg->delta_thr, io->d_delta_idx, io->d_delta_records, io->d_delta_count,
+                          p.delta, ctx->d_status, ctx->wait_cycles, st, ev ? mark : nullptr, ev, 9);
+        return launch_check();
+    }
     launch_project(io->params, na, cfg->sh_degree, dyn, d_cams, p.vt, V, B, p.proj, s.dkv[0], st, 0, n, s.rects);
     if (cfg->n_frozen > 0)
         launch_project(io->frozen, cfg->n_frozen, cfg->sh_degree, dyn, d_cams, p.vt, V, B, p.proj, s.dkv[0], st,
@@ -565,6 +583,11 @@ gs_status_t gs_train_step_events(gs_ctx* ctx, const gs_camera* d_cams, const gs_
     mark(ev, 7, st);
     launch_project_bwd(io->params, na, cfg->sh_degree, dyn, d_cams, V, p.proj, p.grad2d, io->grads, 0, st, n);
     mark(ev, 8, st);
+    if (!(phases & GS_TRAIN_UPDATE)) {
+        mark(ev, 9, st);
+        mark(ev, 10, st);
+        return launch_check();
+    }
     gs_adam_cfg ac = cfg->adam;
     ac.d_step = io->d_step;
     ac.increment = 1;

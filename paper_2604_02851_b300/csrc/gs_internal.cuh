@@ -349,16 +349,16 @@ void launch_cell_visibility(const gs_camera* d_cams, const gs_camera* host_cams,
 size_t delta_scratch_bytes(int64_t n);
 void launch_delta(const float* theta, float* baseline, int64_t n, float thr, uint32_t* d_idx,
                   uint8_t* d_records, uint32_t* d_count, char* scratch, cudaStream_t st);
-// Delta extraction in one pass (decoupled look-back over block tickets; the
-// scratch is cleared by the launch): gs_extract_delta.
-size_t delta_onepass_scratch_bytes(int64_t n);
-void launch_delta_onepass(const float* theta, float* baseline, int64_t n, float thr, uint32_t* d_idx,
-                          uint8_t* d_records, uint32_t* d_count, char* scratch, DevStatus* status, long long spin,
-                          cudaStream_t st);
-// The training step's Adam update and delta extraction in one kernel
-// (k_adam_delta, scratch as the one-pass delta), then the step counter
-// increment and the phase marks `event` (after Adam) and `event` + 1 (after
-// the delta), both after the kernel.
+// Delta extraction as a flag pass and one emit kernel whose blocks find
+// their output offsets by decoupled look-back (the launch clears that part of
+// the scratch): gs_extract_delta.
+size_t delta_lb_scratch_bytes(int64_t n);
+void launch_delta_lb(const float* theta, float* baseline, int64_t n, float thr, uint32_t* d_idx, uint8_t* d_records,
+                     uint32_t* d_count, char* scratch, DevStatus* status, long long spin, cudaStream_t st);
+// The training step's Adam update fused with the delta's changed test
+// (k_adam_flags), the step counter increment, the phase mark `event`, the
+// look-back emit of the records, the mark `event` + 1 (scratch as
+// launch_delta_lb).
 void launch_adam_delta(float* theta, const float* grad, float* m, float* v, int64_t n, const gs_adam_cfg& cfg,
                        const uint8_t* fwd, float* baseline, float thr, uint32_t* d_idx, uint8_t* d_records,
                        uint32_t* d_count, char* scratch, DevStatus* status, long long spin, cudaStream_t st,
@@ -366,7 +366,7 @@ void launch_adam_delta(float* theta, const float* grad, float* m, float* v, int6
 
 // Tensor deltas of one attribute group (GS_ATTR_*) and client-side replay.
 bool attr_group(int attr, int* lo, int* hi, int* f32);
-// (one pass, scratch as launch_delta_onepass)
+// (flag pass and look-back emit, scratch as launch_delta_lb)
 void launch_tensor_delta(const float* theta, float* baseline, int64_t n, int attr, float thr, uint32_t* d_idx,
                          uint8_t* d_vals, uint32_t* d_count, char* scratch, DevStatus* status, long long spin,
                          cudaStream_t st);

@@ -26,7 +26,8 @@ from . import (Context, RECORD_BYTES, GRAD2D_STRIDE, PROJ_STRIDE, _lib, _ptr, _s
 class OnlineTrainer:
     def __init__(self, params, sh_degree: int, cams: dict, keys_cap: int, lr=1e-3, w_l1=0.8, w_ssim=0.2,
                  delta_thr=1e-3, bg=(0.0, 0.0, 0.0), tile=16, sort_bits=8, ctx: Context | None = None,
-                 dyn=None, share: "OnlineTrainer | None" = None, frozen=None, precull=None, lighting=None):
+                 dyn=None, share: "OnlineTrainer | None" = None, frozen=None, precull=None, lighting=None,
+                 phases: int = 0):
         """share: another trainer of the same model whose gradient, Adam
         moments, delta baseline and step counter this one uses (a second
         graph slot with its own targets, image and delta outputs).
@@ -36,7 +37,9 @@ class OnlineTrainer:
         precull: a Precull grid (Sec. 3.3): Gaussians of culled cells are not
         rendered and keep their parameters and Adam state this step.
         lighting: a Lighting (Sec. 3.4.1): colours are the SH-lighting
-        product, attenuated by its per-Gaussian light visibility."""
+        product, attenuated by its per-Gaussian light visibility.
+        phases: the parts of the step that step() runs (_lib.TRAIN_GRADIENT,
+        TRAIN_UPDATE, TRAIN_ALL; 0 = all); step_update() runs the update alone."""
         import torch
         self.torch = torch
         self.params = params
@@ -79,7 +82,10 @@ class OnlineTrainer:
         self.precull = precull
         self.lighting = lighting
         self.cfg = train_cfg(n, sh_degree, V, self.W, self.H, self.keys_cap, w_l1, w_ssim, self.bg, delta_thr, lr,
-                             dyn=dyn, n_frozen=self.n_frozen, precull=precull, lighting=lighting)
+                             dyn=dyn, n_frozen=self.n_frozen, precull=precull, lighting=lighting, phases=phases)
+        self.cfg_update = train_cfg(n, sh_degree, V, self.W, self.H, self.keys_cap, w_l1, w_ssim, self.bg, delta_thr,
+                                    lr, dyn=dyn, n_frozen=self.n_frozen, precull=precull, lighting=lighting,
+                                    phases=_lib.TRAIN_UPDATE)
         self._captured = False
         self._events = None
         self._plain = None
@@ -114,6 +120,12 @@ class OnlineTrainer:
         """The same batched step without the graph (one launch sequence)."""
         check("gs_train_step", _lib.lib().gs_train_step(self.ctx.ptr, _ptr(self.d_cams), C.byref(self.io),
                                                         C.byref(self.cfg), _stream(stream)))
+
+    def step_update(self, stream=None):
+        """The update part alone (Adam on self.grads, delta extraction, step
+        counter), without a graph: a few launches."""
+        check("gs_train_step", _lib.lib().gs_train_step(self.ctx.ptr, _ptr(self.d_cams), C.byref(self.io),
+                                                        C.byref(self.cfg_update), _stream(stream)))
 
     # ------------------------------------------------------------ plain step
     def _plain_buffers(self):

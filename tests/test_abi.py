@@ -37,8 +37,8 @@ def test_struct_layouts_match_header():
     # gs_adam_cfg: 60 lr + 3 floats + step + pointer + 2 ints
     assert _lib.gs_adam_cfg.d_step.offset == 256
     assert ctypes.sizeof(_lib.gs_train_io) == 104 and _lib.gs_train_io.frozen.offset == 96
-    assert ctypes.sizeof(_lib.gs_train_cfg) == 360 and _lib.gs_train_cfg.n_frozen.offset == 336
-    assert _lib.gs_train_cfg.lighting.offset == 352
+    assert ctypes.sizeof(_lib.gs_train_cfg) == 368 and _lib.gs_train_cfg.n_frozen.offset == 336
+    assert _lib.gs_train_cfg.lighting.offset == 352 and _lib.gs_train_cfg.phases.offset == 360
     assert ctypes.sizeof(_lib.gs_tune_entry) == 28
 
 
