@@ -108,8 +108,8 @@ def phase_model(n, V, K, total_tiles, npix, sum_nc, n_changed, binning, passes, 
         # Adam fused with the delta's changed test: theta, grad, m, v, baseline
         # read, theta, m, v written, one flag byte out
         "adam": ("hbm", 60 * nt * 4 * 8 + nt),
-        # the records: flags read, per changed Gaussian theta re-read, index,
-        # record and baseline written
+        # the records: block sums scanned, flags read, per changed Gaussian
+        # theta re-read, index, record and baseline written
         "delta": ("hbm", nt + n_changed * (240 + 4 + 128 + 240)),
     }
 
@@ -146,8 +146,7 @@ def measured_traffic(workload, kernel):
 
 # phases that are one kernel (plus negligible set-up launches), by kernel name
 SINGLE_KERNEL_PHASES = {"project": "k_project", "emit": "k_emit", "render_fwd": "k_render_fwd",
-                        "raster_bwd": "k_raster_bwd", "project_bwd": "k_project_bwd", "adam": "k_adam_flags",
-                        "delta": "k_delta_emit_lb"}
+                        "raster_bwd": "k_raster_bwd", "project_bwd": "k_project_bwd", "adam": "k_adam_flags"}
 
 
 def gpu_launches_per_step(binning, passes):
@@ -158,10 +157,10 @@ def gpu_launches_per_step(binning, passes):
     owners, bitmaps;
     direct: emission, ranges init, look-back clear, scan, passes, ranges
     fix), compositing, loss (2), adjoints (2), Adam with the delta's changed
-    test and the step counter (2), the delta records (1)."""
+    test and the step counter (2), delta scan and records (2)."""
     depth = 8
     sort = (9 + passes) if binning == "two_level" else (5 + passes)
-    return 1 + 1 + depth + sort + 1 + 2 + 1 + 1 + 2 + 1
+    return 1 + 1 + depth + sort + 1 + 2 + 1 + 1 + 2 + 2
 
 
 def replica_seeds(rank: int):
@@ -853,6 +852,7 @@ def run_ours(args, rank, world, local_rank):
                           "targets": "re-rendered each step by gs_render_batch outside the step's events",
                           "parallelism": "replicas" if world > 1 else "single"},
                "roofline": roofline, "cpu_baseline": cpu, "clocks": clk, "e2e": e2e,
+               "serving_p99_ms": serving_p99(serving),
                "plain_step": plain, "serving": serving,
                "gpu_launches": (gpu_launches_per_step(args.binning, tile_passes)
                                 + (1 + 3 + (2 if frozen is not None else 0) if args.relight else 0)
@@ -864,12 +864,21 @@ def run_ours(args, rank, world, local_rank):
     return out
 
 
+def serving_p99(serving):
+    """The p99 latency (ms) of the config-4 run at 50 % of saturation (the
+    metric's second half), or of the load nearest to it."""
+    if not serving or not serving.get("loads"):
+        return None
+    return min(serving["loads"], key=lambda r: abs(r["load"] - 0.5))["p99_ms"]
+
+
 def run_serving(args, local_rank, rank):
     """Config 4: forward-only renders of a static 2M-Gaussian SH-3 model for
     64 clients with Poisson arrivals, resolutions mixed 1280x720 / 1920x1080 /
     1440x1600 per eye, eyes within 0.3 of the ring of radius 3; continuous
     batching on 3 slots.  Saturation is measured first with every request
-    queued at once; the open-loop run then offers args.serve_load of it."""
+    queued at once; open-loop runs of args.serve_requests requests then offer
+    each load in args.serve_loads (fractions of saturation)."""
     import torch
     import paper_2604_02851_b300 as gs
     from paper_2604_02851_b300.serve import RenderServer, Request, measure_keys_per_pixel, percentiles
@@ -891,24 +900,26 @@ def run_serving(args, local_rank, rank):
         return out
 
     srv.run(requests(12, 1e6, gi.SEED_SERVING + 50), realtime=False)  # warm-up
-    done, el = srv.run(requests(args.serve_requests // 3 + 1, 1e6, gi.SEED_SERVING + 51), realtime=False)
+    done, el = srv.run(requests(max(args.serve_requests // 3, 64), 1e6, gi.SEED_SERVING + 51), realtime=False)
     saturation = len(done) / el
-    rate = args.serve_load * saturation
-    srv.batches = 0
-    srv.batch_sizes = []
-    srv.launch_while_busy = 0
-    srv.max_busy = 0
-    retries0 = srv.retries
-    done, el = srv.run(requests(args.serve_requests, rate, gi.SEED_SERVING + 52), realtime=True)
-    srv.check()
-    p50, p99, lat = percentiles(done)
-    res = {"model": "2M Gaussians, SH3", "clients": 64, "requests": len(done), "offered_rate_hz": rate,
-           "saturation_renders_per_s": saturation, "load": args.serve_load, "renders_per_s": len(done) / el,
-           "p50_ms": p50, "p99_ms": p99, "batches": srv.batches,
-           "mean_batch": float(np.mean(srv.batch_sizes)) if srv.batch_sizes else 0.0,
-           "max_slots_busy": srv.max_busy, "batches_started_while_busy": srv.launch_while_busy,
-           "capacity_retries": srv.retries - retries0,
-           "latency": "arrival to image in pinned host memory"}
+    loads = []
+    for i, load in enumerate(args.serve_loads):
+        rate = load * saturation
+        srv.batches = 0
+        srv.batch_sizes = []
+        srv.launch_while_busy = 0
+        srv.max_busy = 0
+        retries0 = srv.retries
+        done, el = srv.run(requests(args.serve_requests, rate, gi.SEED_SERVING + 52 + i), realtime=True)
+        srv.check()
+        p50, p99, lat = percentiles(done)
+        loads.append({"load": load, "requests": len(done), "offered_rate_hz": rate, "renders_per_s": len(done) / el,
+                      "p50_ms": p50, "p99_ms": p99, "batches": srv.batches,
+                      "mean_batch": float(np.mean(srv.batch_sizes)) if srv.batch_sizes else 0.0,
+                      "max_slots_busy": srv.max_busy, "batches_started_while_busy": srv.launch_while_busy,
+                      "capacity_retries": srv.retries - retries0})
+    res = {"model": "2M Gaussians, SH3", "clients": 64, "saturation_renders_per_s": saturation, "slots": 3,
+           "loads": loads, "latency": "arrival to image in pinned host memory"}
     del srv, params
     torch.cuda.empty_cache()
     return res
@@ -949,7 +960,7 @@ def measure_delta_standalone(gs, torch, tr, next_targets, hbm_peak, reps=10):
     ach = work / (ms / 1e3) / 1e9
     return {"ms": ms, "changed": m, "changed_by_fused_step": fused_m, "bound": "hbm", "achieved": ach,
             "unit": "GB/s", "peak": hbm_peak, "frac": ach / hbm_peak, "algorithmic_bytes": work,
-            "kernels": "k_delta_flags + k_delta_emit_lb", "reps": reps}
+            "kernels": "k_delta_flags + k_scan_sums + k_delta_emit", "reps": reps}
 
 
 TENSOR_GROUPS = (("mean", 0, 3, 4), ("opacity", 3, 4, 2), ("scale", 4, 7, 2), ("rotation", 8, 12, 2),
@@ -1045,8 +1056,9 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=30)
     ap.add_argument("--cpu-samples", type=int, default=12)
     ap.add_argument("--plain-steps", type=int, default=10)
-    ap.add_argument("--serve-requests", type=int, default=240)
-    ap.add_argument("--serve-load", type=float, default=0.5)
+    ap.add_argument("--serve-requests", type=int, default=10_000, help="requests per offered load (0: no serving)")
+    ap.add_argument("--serve-loads", type=lambda x: [float(v) for v in x.split(",")], default=[0.25, 0.5, 0.9],
+                    help="offered loads as fractions of the measured saturation, comma separated")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precull", action="store_true",
                     help="preculling grid (Sec. 3.3): Gaussians outside the views' cells are not processed")

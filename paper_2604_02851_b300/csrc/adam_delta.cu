@@ -9,13 +9,8 @@
 // with residuals against the previously transmitted state and fresh baselines
 // after a snapshot.  A Gaussian is sent when any of its 60 floats moved by
 // more than thr from its last transmitted value; the sent set is compacted in
-// index order and packed as 128-byte records: uint32 index, float32 mean, 56
-// float16 (RNE) attributes.  A flag pass (fused with Adam in the training
-// step) marks the changed Gaussians; gs_extract_delta and the training step
-// then emit in one kernel whose blocks find their output offsets by
-// decoupled look-back; the allocation-free entry point keeps a three-kernel
-// form (flags and block sums, a one-block scan, an ordered emit) whose
-// scratch needs no clearing.
+// index order (block sums, one-block scan, ordered emit) and packed as
+// 128-byte records: uint32 index, float32 mean, 56 float16 (RNE) attributes.
 #include <cuda_fp16.h>
 #include <math.h>
 
@@ -25,8 +20,6 @@ namespace gs {
 namespace {
 
 struct LrTable { float lr[60]; };
-
-constexpr int kDeltaThreads = 256;  // Gaussians per delta block
 
 // One bias-corrected Adam update of a float4 of parameters (learning rates
 // l[0..3]); bc1 = 1 - b1^t, sbc2 = sqrt(1 - b2^t).
@@ -67,87 +60,9 @@ k_adam(float4* __restrict__ theta, const float4* __restrict__ grad, float4* __re
 
 __global__ void k_inc_step(int32_t* d_step) { *d_step += 1; }
 
-// One 128-byte record of Gaussian g at output slot `off`, read plane by plane
-// from theta (so that few registers are live), and its baseline planes set to
-// theta: word 0 index, words 1-3 mean (float32), then float16 RNE pairs of
-// log-scale xyz, quaternion wxyz, opacity logit (words 4-7) and the 48 SH
-// coefficients in flat order (two words per plane 3..14).
-__device__ __forceinline__ uint32_t half2_bits(float a, float b) {
-    return (uint32_t)__half_as_ushort(__float2half_rn(a)) | ((uint32_t)__half_as_ushort(__float2half_rn(b)) << 16);
-}
+// ---------------------------------------------------------------- delta
+constexpr int kDeltaThreads = 256;
 
-__device__ __forceinline__ void emit_record(const float4* __restrict__ theta, float4* __restrict__ base, int64_t n,
-                                            int64_t g, uint32_t off, uint32_t* __restrict__ d_idx,
-                                            uint8_t* __restrict__ d_records) {
-    d_idx[off] = (uint32_t)g;
-    const float4 p0 = theta[g], p1 = theta[n + g], p2 = theta[2 * n + g];
-    base[g] = p0;
-    base[n + g] = p1;
-    base[2 * n + g] = p2;
-    uint4* rec = reinterpret_cast<uint4*>(d_records + (size_t)off * 128);
-    rec[0] = make_uint4((uint32_t)g, __float_as_uint(p0.x), __float_as_uint(p0.y), __float_as_uint(p0.z));
-    rec[1] = make_uint4(half2_bits(p1.x, p1.y), half2_bits(p1.z, p2.x), half2_bits(p2.y, p2.z),
-                        half2_bits(p2.w, p0.w));
-    uint2* sh = reinterpret_cast<uint2*>(rec + 2);
-#pragma unroll 4
-    for (int p = 3; p < 15; ++p) {
-        const float4 a = theta[p * n + g];
-        base[p * n + g] = a;
-        sh[p - 3] = make_uint2(half2_bits(a.x, a.y), half2_bits(a.z, a.w));
-    }
-}
-
-// Block part of the one-pass compaction: the block's changed count, its
-// output offset by look-back (block ticket b of nblk), and each changed
-// thread's slot.  The last block writes the total to *d_count.
-__device__ __forceinline__ uint32_t delta_slot(bool changed, int64_t b, int64_t nblk, unsigned long long* lookback,
-                                               uint32_t* d_count, DevStatus* status, long long spin) {
-    __shared__ uint32_t s_w[kDeltaThreads / 32];
-    __shared__ unsigned long long s_excl;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const uint32_t bal = __ballot_sync(0xFFFFFFFFu, changed);
-    if (lane == 0) s_w[warp] = __popc(bal);
-    __syncthreads();
-    uint32_t woff = 0, tot = 0;
-#pragma unroll
-    for (int w = 0; w < kDeltaThreads / 32; ++w) {
-        if (w < warp) woff += s_w[w];
-        tot += s_w[w];
-    }
-    if (threadIdx.x == 0) {
-        st_volatile(lookback + b, (b == 0 ? kFlagInc : kFlagAgg) | (unsigned long long)tot);
-        unsigned long long excl = 0;
-        look_back(lookback, b, 1, tot, &excl, status, spin);
-        s_excl = excl;
-        if (b == nblk - 1) *d_count = (uint32_t)(excl + tot);
-    }
-    __syncthreads();
-    return (uint32_t)s_excl + woff + __popc(bal & ((1u << lane) - 1u));
-}
-
-// The changed Gaussians' records in index order, from the flags of
-// k_delta_flags or k_adam_flags: block ticket b takes the flags of Gaussians
-// b*256 .. b*256 + 255, finds its output offset by decoupled look-back over
-// the blocks before it (short blocks: a predecessor is never long in
-// coming) and its changed threads write their records.  One kernel instead
-// of a one-block scan of the block sums followed by the emit.  lookback
-// [nblk] and the ticket counter start at zero.
-__global__ void __launch_bounds__(kDeltaThreads)
-k_delta_emit_lb(const float4* __restrict__ theta, float4* __restrict__ base, int64_t n,
-                const uint8_t* __restrict__ flags, uint32_t* __restrict__ d_idx, uint8_t* __restrict__ d_records,
-                uint32_t* d_count, unsigned long long* lookback, uint32_t* ticket, int64_t nblk, DevStatus* status,
-                long long spin) {
-    __shared__ uint32_t s_blk;
-    if (threadIdx.x == 0) s_blk = atomicAdd(ticket, 1u);
-    __syncthreads();
-    const int64_t b = s_blk;
-    const int64_t g = b * kDeltaThreads + threadIdx.x;
-    const bool changed = g < n && flags[g];
-    const uint32_t off = delta_slot(changed, b, nblk, lookback, d_count, status, spin);
-    if (changed) emit_record(theta, base, n, g, off, d_idx, d_records);
-}
-
-// ---------------------------------------------------------------- delta flags
 __global__ void __launch_bounds__(kDeltaThreads)
 k_delta_flags(const float4* __restrict__ theta, const float4* __restrict__ base, int64_t n, float thr,
               uint8_t* __restrict__ flags, uint32_t* __restrict__ block_sums) {
@@ -289,28 +204,27 @@ k_tdelta_flags(const float4* __restrict__ theta, const float4* __restrict__ base
     if (threadIdx.x == 0) block_sums[blockIdx.x] = cnt;
 }
 
-// A group's records in index order from k_tdelta_flags's flags (as
-// k_delta_emit_lb): each changed Gaussian's index, its group record (float32
-// or float16 RNE, densely packed) and the group's baseline floats.
 __global__ void __launch_bounds__(kDeltaThreads)
-k_tdelta_emit_lb(const float4* __restrict__ theta, float4* __restrict__ base, int64_t n, Group gr,
-                 const uint8_t* __restrict__ flags, uint32_t* __restrict__ d_idx, uint8_t* __restrict__ d_vals,
-                 uint32_t* d_count, unsigned long long* lookback, uint32_t* ticket, int64_t nblk, DevStatus* status,
-                 long long spin) {
-    __shared__ uint32_t s_blk;
-    if (threadIdx.x == 0) s_blk = atomicAdd(ticket, 1u);
+k_tdelta_emit(const float4* __restrict__ theta, float4* __restrict__ base, int64_t n, Group gr,
+              const uint8_t* __restrict__ flags, const uint32_t* __restrict__ block_off,
+              uint32_t* __restrict__ d_idx, uint8_t* __restrict__ d_vals) {
+    const int64_t g = (int64_t)blockIdx.x * kDeltaThreads + threadIdx.x;
+    const bool ch = g < n && flags[g];
+    const uint32_t ballot = __ballot_sync(0xFFFFFFFFu, ch);
+    __shared__ uint32_t s_w[kDeltaThreads / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) s_w[warp] = __popc(ballot);
     __syncthreads();
-    const int64_t b = s_blk;
-    const int64_t g = b * kDeltaThreads + threadIdx.x;
-    const bool changed = g < n && flags[g];
-    const uint32_t off = delta_slot(changed, b, nblk, lookback, d_count, status, spin);
-    if (!changed) return;
+    uint32_t off = block_off[blockIdx.x];
+    for (int w = 0; w < warp; ++w) off += s_w[w];
+    off += __popc(ballot & ((1u << lane) - 1u));
+    if (!ch) return;
     d_idx[off] = (uint32_t)g;
     const int rb = (gr.hi - gr.lo) * (gr.f32 ? 4 : 2);
     uint8_t* rec = d_vals + (size_t)off * rb;
     for (int p = gr.lo >> 2; p <= (gr.hi - 1) >> 2; ++p) {
         const float4 a = theta[p * n + g];
-        float4 c = base[p * n + g];
+        float4 b = base[p * n + g];
 #pragma unroll
         for (int l = 0; l < 4; ++l) {
             const int f = 4 * p + l;
@@ -318,9 +232,9 @@ k_tdelta_emit_lb(const float4* __restrict__ theta, float4* __restrict__ base, in
             const float v = lane_of(a, l);
             if (gr.f32) reinterpret_cast<float*>(rec)[f - gr.lo] = v;
             else reinterpret_cast<__half*>(rec)[f - gr.lo] = __float2half_rn(v);
-            set_lane(c, l, v);
+            set_lane(b, l, v);
         }
-        base[p * n + g] = c;
+        base[p * n + g] = b;
     }
 }
 
@@ -472,77 +386,32 @@ void launch_delta(const float* theta, float* baseline, int64_t n, float thr, uin
     k_delta_emit<<<(unsigned)nblk, kDeltaThreads, 0, st>>>(th, b, n, flags, sums, d_idx, d_records);
 }
 
-// Scratch of the look-back emit: flags, block sums (written by the flag
-// kernels, read only by the three-kernel form), then the look-back slots and
-// the ticket counter, which the launch clears.
-struct LbScratch {
-    uint8_t* flags;
-    uint32_t* sums;
-    unsigned long long* lookback;
-    uint32_t* ticket;
-    char* clear_from;
-    size_t clear_bytes;
-    size_t bytes;
-};
-
-LbScratch carve_lb(char* scratch, int64_t n) {
-    Carver c(scratch);
-    LbScratch l;
-    const int64_t nblk = (n + kDeltaThreads - 1) / kDeltaThreads;
-    l.flags = c.take<uint8_t>(n > 0 ? n : 1);
-    l.sums = c.take<uint32_t>(nblk + 1);
-    l.lookback = c.take<unsigned long long>(nblk + 1);
-    const size_t from = c.off - sizeof(unsigned long long) * (size_t)(nblk + 1);
-    l.ticket = c.take<uint32_t>(1);
-    l.clear_from = scratch ? scratch + from : nullptr;
-    l.clear_bytes = c.off - from;
-    l.bytes = c.off;
-    return l;
-}
-
-size_t delta_lb_scratch_bytes(int64_t n) { return carve_lb(nullptr, n).bytes; }
-
-void launch_delta_lb(const float* theta, float* baseline, int64_t n, float thr, uint32_t* d_idx, uint8_t* d_records,
-                     uint32_t* d_count, char* scratch, DevStatus* status, long long spin, cudaStream_t st) {
-    if (n <= 0) {
-        cudaMemsetAsync(d_count, 0, sizeof(uint32_t), st);
-        return;
-    }
-    const int64_t nblk = (n + kDeltaThreads - 1) / kDeltaThreads;
-    const LbScratch l = carve_lb(scratch, n);
-    cudaMemsetAsync(l.clear_from, 0, l.clear_bytes, st);
-    const float4* th = reinterpret_cast<const float4*>(theta);
-    float4* b = reinterpret_cast<float4*>(baseline);
-    k_delta_flags<<<(unsigned)nblk, kDeltaThreads, 0, st>>>(th, b, n, thr, l.flags, l.sums);
-    k_delta_emit_lb<<<(unsigned)nblk, kDeltaThreads, 0, st>>>(th, b, n, l.flags, d_idx, d_records, d_count,
-                                                             l.lookback, l.ticket, nblk, status, spin);
-}
-
 void launch_adam_delta(float* theta, const float* grad, float* m, float* v, int64_t n, const gs_adam_cfg& cfg,
                        const uint8_t* fwd, float* baseline, float thr, uint32_t* d_idx, uint8_t* d_records,
-                       uint32_t* d_count, char* scratch, DevStatus* status, long long spin, cudaStream_t st,
-                       void (*mark)(void* const*, int, cudaStream_t), void* const* events, int event) {
+                       uint32_t* d_count, char* scratch, cudaStream_t st, void (*mark)(void* const*, int, cudaStream_t),
+                       void* const* events, int event) {
+    Carver c(scratch);
+    uint8_t* flags = c.take<uint8_t>(n > 0 ? n : 1);
     const int64_t nblk = (n + kDeltaThreads - 1) / kDeltaThreads;
-    const LbScratch l = carve_lb(scratch, n);
+    uint32_t* sums = c.take<uint32_t>(nblk + 1);
     if (n > 0) {
-        cudaMemsetAsync(l.clear_from, 0, l.clear_bytes, st);
         LrTable lr;
         for (int i = 0; i < 60; ++i) lr.lr[i] = cfg.lr[i];
         k_adam_flags<<<(unsigned)nblk, kDeltaThreads, 0, st>>>(
             reinterpret_cast<float4*>(theta), reinterpret_cast<const float4*>(grad), reinterpret_cast<float4*>(m),
             reinterpret_cast<float4*>(v), reinterpret_cast<const float4*>(baseline), n, lr, cfg.beta1, cfg.beta2,
-            cfg.eps, cfg.step, cfg.d_step, fwd, thr, l.flags, l.sums);
+            cfg.eps, cfg.step, cfg.d_step, fwd, thr, flags, sums);
     }
     if (cfg.d_step && cfg.increment) k_inc_step<<<1, 1, 0, st>>>(const_cast<int32_t*>(cfg.d_step));
     if (mark) mark(events, event, st);
     if (n <= 0) {
         cudaMemsetAsync(d_count, 0, sizeof(uint32_t), st);
-    } else {
-        k_delta_emit_lb<<<(unsigned)nblk, kDeltaThreads, 0, st>>>(
-            reinterpret_cast<const float4*>(theta), reinterpret_cast<float4*>(baseline), n, l.flags, d_idx, d_records,
-            d_count, l.lookback, l.ticket, nblk, status, spin);
+        return;
     }
-    if (mark) mark(events, event + 1, st);
+    k_scan_sums<<<1, 1024, 0, st>>>(sums, nblk, d_count, -1, nullptr);
+    k_delta_emit<<<(unsigned)nblk, kDeltaThreads, 0, st>>>(reinterpret_cast<const float4*>(theta),
+                                                          reinterpret_cast<float4*>(baseline), n, flags, sums, d_idx,
+                                                          d_records);
 }
 
 bool attr_group(int attr, int* lo, int* hi, int* f32) {
@@ -558,22 +427,22 @@ bool attr_group(int attr, int* lo, int* hi, int* f32) {
 }
 
 void launch_tensor_delta(const float* theta, float* baseline, int64_t n, int attr, float thr, uint32_t* d_idx,
-                         uint8_t* d_vals, uint32_t* d_count, char* scratch, DevStatus* status, long long spin,
-                         cudaStream_t st) {
+                         uint8_t* d_vals, uint32_t* d_count, char* scratch, cudaStream_t st) {
     Group gr;
     attr_group(attr, &gr.lo, &gr.hi, &gr.f32);
+    Carver c(scratch);
+    uint8_t* flags = c.take<uint8_t>(n > 0 ? n : 1);
+    const int64_t nblk = (n + kDeltaThreads - 1) / kDeltaThreads;
+    uint32_t* sums = c.take<uint32_t>(nblk + 1);
     if (n <= 0) {
         cudaMemsetAsync(d_count, 0, sizeof(uint32_t), st);
         return;
     }
-    const int64_t nblk = (n + kDeltaThreads - 1) / kDeltaThreads;
-    const LbScratch l = carve_lb(scratch, n);
-    cudaMemsetAsync(l.clear_from, 0, l.clear_bytes, st);
     const float4* th = reinterpret_cast<const float4*>(theta);
     float4* b = reinterpret_cast<float4*>(baseline);
-    k_tdelta_flags<<<(unsigned)nblk, kDeltaThreads, 0, st>>>(th, b, n, gr, thr, l.flags, l.sums);
-    k_tdelta_emit_lb<<<(unsigned)nblk, kDeltaThreads, 0, st>>>(th, b, n, gr, l.flags, d_idx, d_vals, d_count,
-                                                              l.lookback, l.ticket, nblk, status, spin);
+    k_tdelta_flags<<<(unsigned)nblk, kDeltaThreads, 0, st>>>(th, b, n, gr, thr, flags, sums);
+    k_scan_sums<<<1, 1024, 0, st>>>(sums, nblk, d_count, -1, nullptr);
+    k_tdelta_emit<<<(unsigned)nblk, kDeltaThreads, 0, st>>>(th, b, n, gr, flags, sums, d_idx, d_vals);
 }
 
 void launch_apply_tensor_delta(float* params, int64_t n, int attr, const uint32_t* d_idx, const uint8_t* d_vals,

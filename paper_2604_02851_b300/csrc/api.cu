@@ -106,7 +106,7 @@ FusedPlan plan_fused(void* base, int V, int64_t n, int64_t keys_cap, int64_t tot
         p.dimage = c.take<float>(3 * total_pixels);
         p.loss = c.take<char>(loss_scratch_bytes(V, H, W));
         p.grad2d = c.take<float>((size_t)V * n * kGradStride);
-        p.delta = c.take<char>(std::max(delta_scratch_bytes(n), delta_lb_scratch_bytes(n)));
+        p.delta = c.take<char>(delta_scratch_bytes(n));
         p.fwd = c.take<uint8_t>(n > 0 ? n : 1);
     }
     p.bytes = c.off;
@@ -418,11 +418,10 @@ gs_status_t gs_extract_delta(gs_ctx* ctx, const float* theta, float* baseline, i
         n >= (1LL << 32) || !(thr >= 0.f))
         return GS_ERR_ARG;
     Carver c(ctx->ws);
-    char* ds = c.take<char>(delta_lb_scratch_bytes(n));
+    char* ds = c.take<char>(delta_scratch_bytes(n));
     if (check_ws(ctx, c.off)) return GS_ERR_CAPACITY;
     DeviceGuard g(ctx->device);
-    launch_delta_lb(theta, baseline, n, thr, d_idx, d_records, d_count, ds, ctx->d_status, ctx->wait_cycles,
-                         S(stream));
+    launch_delta(theta, baseline, n, thr, d_idx, d_records, d_count, ds, S(stream));
     return launch_check();
 }
 
@@ -439,11 +438,11 @@ gs_status_t gs_extract_tensor_delta(gs_ctx* ctx, const float* theta, float* base
         n >= (1LL << 32) || !(thr >= 0.f) || !attr_group(attr, &lo, &hi, &f32))
         return GS_ERR_ARG;
     Carver c(ctx->ws);
-    char* ds = c.take<char>(delta_lb_scratch_bytes(n));
+    char* ds = c.take<char>(delta_scratch_bytes(n));
     if (check_ws(ctx, c.off)) return GS_ERR_CAPACITY;
     DeviceGuard g(ctx->device);
     launch_tensor_delta(theta, baseline, n, attr, thr, d_idx, static_cast<uint8_t*>(d_vals), d_count, ds,
-                        ctx->d_status, ctx->wait_cycles, S(stream));
+                        S(stream));
     return launch_check();
 }
 
@@ -557,7 +556,7 @@ gs_status_t gs_train_step_events(gs_ctx* ctx, const gs_camera* d_cams, const gs_
         ac.increment = 1;
         launch_adam_delta(io->params, io->grads, io->adam_m, io->adam_v, na, ac, cfg->precull ? p.fwd : nullptr,
                           io->baseline, cfg->delta_thr, io->d_delta_idx, io->d_delta_records, io->d_delta_count,
-                          p.delta, ctx->d_status, ctx->wait_cycles, st, ev ? mark : nullptr, ev, 9);
+                          p.delta, st, ev ? mark : nullptr, ev, 9);
         return launch_check();
     }
     launch_project(io->params, na, cfg->sh_degree, dyn, d_cams, p.vt, V, B, p.proj, s.dkv[0], st, 0, n, s.rects);
@@ -591,10 +590,11 @@ gs_status_t gs_train_step_events(gs_ctx* ctx, const gs_camera* d_cams, const gs_
     gs_adam_cfg ac = cfg->adam;
     ac.d_step = io->d_step;
     ac.increment = 1;
-    // Adam and the delta extraction in one kernel (phases 9 and 10 end after it)
+    // Adam with the delta's changed test (phase 9 ends after it), then the
+    // delta's scan and records
     launch_adam_delta(io->params, io->grads, io->adam_m, io->adam_v, na, ac, cfg->precull ? p.fwd : nullptr,
                       io->baseline, cfg->delta_thr, io->d_delta_idx, io->d_delta_records, io->d_delta_count,
-                      p.delta, ctx->d_status, ctx->wait_cycles, st, ev ? mark : nullptr, ev, 9);
+                      p.delta, st, ev ? mark : nullptr, ev, 9);
     mark(ev, 10, st);
     return launch_check();
 }

@@ -343,33 +343,21 @@ size_t precull_scratch_bytes(const gs_camera* host_cams, int V);
 void launch_cell_visibility(const gs_camera* d_cams, const gs_camera* host_cams, int V, const float* depth,
                             const gs_precull& grid, uint8_t* vis, char* scratch, cudaStream_t st);
 
-// Delta extraction in three kernels (flags and block sums, one-block scan,
-// ordered emit) over scratch that needs no clearing: the allocation-free
-// entry point.
 size_t delta_scratch_bytes(int64_t n);
 void launch_delta(const float* theta, float* baseline, int64_t n, float thr, uint32_t* d_idx,
                   uint8_t* d_records, uint32_t* d_count, char* scratch, cudaStream_t st);
-// Delta extraction as a flag pass and one emit kernel whose blocks find
-// their output offsets by decoupled look-back (the launch clears that part of
-// the scratch): gs_extract_delta.
-size_t delta_lb_scratch_bytes(int64_t n);
-void launch_delta_lb(const float* theta, float* baseline, int64_t n, float thr, uint32_t* d_idx, uint8_t* d_records,
-                     uint32_t* d_count, char* scratch, DevStatus* status, long long spin, cudaStream_t st);
-// The training step's Adam update fused with the delta's changed test
-// (k_adam_flags), the step counter increment, the phase mark `event`, the
-// look-back emit of the records, the mark `event` + 1 (scratch as
-// launch_delta_lb).
+// The training step's Adam update and delta extraction: Adam fused with the
+// changed test (k_adam_flags), the step counter increment, then (after the
+// optional phase mark) the scan and the record emission.
 void launch_adam_delta(float* theta, const float* grad, float* m, float* v, int64_t n, const gs_adam_cfg& cfg,
                        const uint8_t* fwd, float* baseline, float thr, uint32_t* d_idx, uint8_t* d_records,
-                       uint32_t* d_count, char* scratch, DevStatus* status, long long spin, cudaStream_t st,
-                       void (*mark)(void* const*, int, cudaStream_t), void* const* events, int event);
+                       uint32_t* d_count, char* scratch, cudaStream_t st, void (*mark)(void* const*, int, cudaStream_t),
+                       void* const* events, int event);
 
 // Tensor deltas of one attribute group (GS_ATTR_*) and client-side replay.
 bool attr_group(int attr, int* lo, int* hi, int* f32);
-// (flag pass and look-back emit, scratch as launch_delta_lb)
 void launch_tensor_delta(const float* theta, float* baseline, int64_t n, int attr, float thr, uint32_t* d_idx,
-                         uint8_t* d_vals, uint32_t* d_count, char* scratch, DevStatus* status, long long spin,
-                         cudaStream_t st);
+                         uint8_t* d_vals, uint32_t* d_count, char* scratch, cudaStream_t st);
 void launch_apply_tensor_delta(float* params, int64_t n, int attr, const uint32_t* d_idx, const uint8_t* d_vals,
                                const uint32_t* d_count, DevStatus* status, int sm_count, cudaStream_t st);
 void launch_apply_delta(float* params, int64_t n, const uint8_t* d_records, const uint32_t* d_count,

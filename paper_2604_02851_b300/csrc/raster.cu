@@ -74,9 +74,9 @@ constexpr float kCullMargin = 0.01f;
 
 // A fragment whose opacity is at most kNoClampOpacity never reaches the 0.99
 // alpha clamp: alpha = o e^P with P <= 0 up to float32 rounding (a few
-// 1e-7), so alpha <= o (1 + 1e-6) < 0.99.  For such fragments both kernels
-// take alpha = o e^P without the min, and the adjoint dL/dP = dL/dalpha alpha
-// without the clamp test: the same values, fewer instructions.
+// 1e-7), so alpha <= o (1 + 1e-6) < 0.99.  For such fragments the adjoint
+// takes alpha = o e^P without the min and dL/dP = dL/dalpha alpha without the
+// clamp test: the same values, fewer instructions.
 constexpr float kNoClampOpacity = 0.9899f;
 
 __device__ __forceinline__ float box_max_exponent(float4 q, float dxl, float dxh, float dyl, float dyh) {
@@ -272,16 +272,16 @@ k_render_fwd(const float4* __restrict__ proj, const ViewInfo* __restrict__ vt, i
             s_a[d] = ra[h]; s_q[d] = rq[h]; s_c[d] = rc[h]; s_pos[d] = ipos[h];
         }
         __syncthreads();
-        // one fragment over this thread's pixel pairs; CL: the fragment's
-        // opacity can reach the alpha clamp
-        auto composite = [&](auto clamp_tag, const float4 a, const float4 q, uint32_t pos1, int j) {
-            constexpr bool CL = decltype(clamp_tag)::value;
+        for (int j = 0; j < cnt && nlive; ++j) {
+            const float4 a = s_a[j];
+            const float4 q = s_q[j];
             const float dy = a.y - fy;
             const float qb = q.y * dy;
             const float qc = q.z * dy * dy;
             const float dx0 = a.x - fx0;
             const float2 qx2 = make_float2(q.x, q.x), qb2 = make_float2(qb, qb), qc2 = make_float2(qc, qc);
             const float2 o2 = make_float2(a.z, a.z);
+            const uint32_t pos1 = s_pos[j] + 1;
 #pragma unroll
             for (int p = 0; p < NP; ++p) {
                 const int k0 = 2 * p, k1 = 2 * p + 1;
@@ -292,7 +292,7 @@ k_render_fwd(const float4* __restrict__ proj, const ViewInfo* __restrict__ vt, i
                 bool v0 = P2.x >= a.w, v1 = P2.y >= a.w;
                 if (!(v0 || v1)) continue;
                 const float2 raw = __fmul2_rn(o2, make_float2(v0 ? ex2(P2.x) : 0.f, v1 ? ex2(P2.y) : 0.f));
-                float2 al = CL ? make_float2(fminf(kAlphaMax, raw.x), fminf(kAlphaMax, raw.y)) : raw;
+                float2 al = make_float2(fminf(kAlphaMax, raw.x), fminf(kAlphaMax, raw.y));
                 float2 Tn = __fmul2_rn(T[p], __ffma2_rn(al, make_float2(-1.f, -1.f), make_float2(1.f, 1.f)));
                 // T >= 1e-4 holds for every pixel still compositing, and a pixel
                 // this fragment misses keeps its T: only a covered pixel can
@@ -310,14 +310,6 @@ k_render_fwd(const float4* __restrict__ proj, const ViewInfo* __restrict__ vt, i
                 if (v0) last[k0] = pos1;
                 if (v1) last[k1] = pos1;
             }
-        };
-        for (int j = 0; j < cnt && nlive; ++j) {
-            const float4 a = s_a[j];
-            const float4 q = s_q[j];
-            const uint32_t pos1 = s_pos[j] + 1;
-            // uniform over the block: every thread reads the same fragment
-            if (a.z > kNoClampOpacity) composite(std::true_type{}, a, q, pos1, j);
-            else composite(std::false_type{}, a, q, pos1, j);
         }
     };
     if (!COARSE) {
@@ -464,17 +456,11 @@ k_raster_bwd(const float4* __restrict__ proj, const ViewInfo* __restrict__ vt, i
     // a fragment, R, enters the gradient only as dL/dC . R (dL/dC is fixed per
     // pixel), so the walk keeps that scalar X instead of R:
     //   dL/dalpha_j = T_j (dL/dC . c_j - X_j),  X_{j-1} = X_j + alpha_j (dL/dC . c_j - X_j).
-    // A pixel joins the walk at its last contributor: until then pen (added
-    // to its exponent, as in compositing) is -inf, which fails the cut-off
-    // test; nextact is the largest last-contributor position among this
-    // thread's pixels that have not joined yet, so the per-pixel positions
-    // (kept in shared memory) are read only when one joins.
-    const float kNegInf = __int_as_float(0xff800000);
-    float2 T[NP], X[NP], pen[NP];
+    float2 T[NP], X[NP];
     // dL/dC per pixel pair: read-only in the walk, kept in this thread's
     // column of shared memory instead of 3 NP register pairs
     __shared__ float2 s_dC[3][NP][NT];
-    __shared__ uint32_t s_last[PX][NT];
+    uint32_t last[PX];
     uint32_t mylast = 0;
     const int64_t HW = (int64_t)vi.width * vi.height;
     const float* dimg = dimage + 3 * vi.pix_off;
@@ -485,18 +471,16 @@ k_raster_bwd(const float4* __restrict__ proj, const ViewInfo* __restrict__ vt, i
         for (int e = 0; e < 2; ++e) {
             const int k = 2 * p + e;
             const int px = px0 + k;
-            uint32_t lk = 0;
+            last[k] = 0;
             if (px < vi.width && py < vi.height) {
                 const int64_t pix = (int64_t)py * vi.width + px;
                 t[e] = T_final[vi.pix_off + pix];
-                lk = n_contrib[vi.pix_off + pix];
+                last[k] = n_contrib[vi.pix_off + pix];
                 r[e] = dimg[pix]; g[e] = dimg[HW + pix]; b[e] = dimg[2 * HW + pix];
-                mylast = max(mylast, lk);
+                mylast = max(mylast, last[k]);
             }
-            s_last[k][threadIdx.x] = lk;
         }
         T[p] = make_float2(t[0], t[1]);
-        pen[p] = make_float2(kNegInf, kNegInf);
         s_dC[0][p][threadIdx.x] = make_float2(r[0], r[1]);
         s_dC[1][p][threadIdx.x] = make_float2(g[0], g[1]);
         s_dC[2][p][threadIdx.x] = make_float2(b[0], b[1]);
@@ -507,7 +491,6 @@ k_raster_bwd(const float4* __restrict__ proj, const ViewInfo* __restrict__ vt, i
     if (mylast) atomicMax(&s_max, mylast);
     __syncthreads();
     const uint32_t maxl = s_max;
-    uint32_t nextact = mylast;
 
     // One round: list items [0, nslot) of a window (item(i, pos, g): list
     // position and Gaussian), staged in list order and walked back to front.
@@ -552,8 +535,8 @@ k_raster_bwd(const float4* __restrict__ proj, const ViewInfo* __restrict__ vt, i
         // one fragment over this thread's pixel pairs, accumulating the
         // pixels' dL/dP sums and colour gradients; CL: the fragment's opacity
         // can reach the alpha clamp
-        auto walk = [&](auto clamp_tag, const float4 a, const float4 q, const float4 c, float dy, float2& s0,
-                        float2& s1, float2& s2, float2& g6, float2& g7, float2& g8) -> bool {
+        auto walk = [&](auto clamp_tag, const uint32_t pos, const float4 a, const float4 q, const float4 c, float dy,
+                        float2& s0, float2& s1, float2& s2, float2& g6, float2& g7, float2& g8) -> bool {
             constexpr bool CL = decltype(clamp_tag)::value;
             const float qb = q.y * dy;
             const float qc = q.z * dy * dy;
@@ -566,11 +549,9 @@ k_raster_bwd(const float4* __restrict__ proj, const ViewInfo* __restrict__ vt, i
             for (int p = 0; p < NP; ++p) {
                 const int k0 = 2 * p, k1 = 2 * p + 1;
                 const float2 dx = make_float2(dx0 - (float)k0, dx0 - (float)k1);
-                // the exponent exactly as compositing computed it (pen is 0 for
-                // a pixel in the walk), so both take the same decisions
-                const float2 P2 = __fadd2_rn(__ffma2_rn(__ffma2_rn(qx2, dx, qb2), dx, qc2), pen[p]);
-                const bool v0 = P2.x >= a.w;
-                const bool v1 = P2.y >= a.w;
+                const float2 P2 = __ffma2_rn(__ffma2_rn(qx2, dx, qb2), dx, qc2);
+                const bool v0 = pos < last[k0] && P2.x >= a.w;
+                const bool v1 = pos < last[k1] && P2.y >= a.w;
                 if (!(v0 || v1)) continue;
                 contrib = true;
                 const float2 raw = __fmul2_rn(o2, make_float2(v0 ? ex2(P2.x) : 0.f, v1 ? ex2(P2.y) : 0.f));
@@ -586,7 +567,7 @@ k_raster_bwd(const float4* __restrict__ proj, const ViewInfo* __restrict__ vt, i
                 g7 = __ffma2_rn(w, dCg, g7);
                 g8 = __ffma2_rn(w, dCb, g8);
                 // e = dL/dC . (c - R)
-                const float2 e = __ffma2_rn(dCb, cb, __ffma2_rn(dCg, cg, __ffma2_rn(dCr, cr, __fmul2_rn(X[p], m1))));
+                const float2 e = __ffma2_rn(dCb, cb, __ffma2_rn(dCg, cg, __ffma2_rn(dCr, cr, make_float2(-X[p].x, -X[p].y))));
                 const float2 dal = __fmul2_rn(Tj, e);
                 X[p] = __ffma2_rn(al, e, X[p]);
                 // dL/dP = dL/dalpha * alpha where alpha is not clamped
@@ -603,20 +584,6 @@ k_raster_bwd(const float4* __restrict__ proj, const ViewInfo* __restrict__ vt, i
         for (int j = cnt - 1; j >= 0; --j) {
             const uint32_t pos = s_pos[j];
             if (!__any_sync(0xFFFFFFFFu, pos < mylast)) continue;
-            if (pos < nextact) {
-                // pixels whose last contributor is at or behind pos join
-                nextact = 0;
-#pragma unroll
-                for (int k = 0; k < PX; ++k) {
-                    const uint32_t lk = s_last[k][threadIdx.x];
-                    if (pos < lk) {
-                        if (k & 1) pen[k >> 1].y = 0.f;
-                        else pen[k >> 1].x = 0.f;
-                    } else {
-                        nextact = max(nextact, lk);
-                    }
-                }
-            }
             const float4 a = s_a[j];
             const float4 q = s_q[j];
             const float4 c = s_c[j];
@@ -624,8 +591,9 @@ k_raster_bwd(const float4* __restrict__ proj, const ViewInfo* __restrict__ vt, i
             const float2 zero = make_float2(0.f, 0.f);
             float2 s0 = zero, s1 = zero, s2 = zero, g6 = zero, g7 = zero, g8 = zero;
             // uniform over the warp: every lane reads the same fragment
-            const bool contrib = a.z > kNoClampOpacity ? walk(std::true_type{}, a, q, c, dy, s0, s1, s2, g6, g7, g8)
-                                                       : walk(std::false_type{}, a, q, c, dy, s0, s1, s2, g6, g7, g8);
+            const bool contrib = a.z > kNoClampOpacity
+                                     ? walk(std::true_type{}, pos, a, q, c, dy, s0, s1, s2, g6, g7, g8)
+                                     : walk(std::false_type{}, pos, a, q, c, dy, s0, s1, s2, g6, g7, g8);
             // frozen Gaussians (index >= n_active) take part in the
             // recursion but need no gradient
             if (s_g[j] < n_active && __any_sync(0xFFFFFFFFu, contrib)) {
