@@ -125,23 +125,51 @@ def delta_bytes(n, n_changed):
 # kernel in one ncu capture), valid while the kernel's source file is
 # unchanged (first 12 hex digits of its SHA-1).
 MEASURED_TRAFFIC = {
-    ("c3_1M_8x720p", "k_raster_bwd"): (252.9e6, "csrc/raster.cu", "a344e179321a"),
+    ("c3_1M_8x720p", "k_raster_bwd"): (254.7e6, "csrc/raster.cu", "9f93864afe47"),
+}
+
+# Warp instructions per (pixel, fragment) evaluation of a raster kernel
+# (smsp__inst_executed.sum of one launch over its sum of n_contrib, one ncu
+# capture of the 200k-Gaussian, 8 x 720p case), valid while the kernel's
+# source file is unchanged: with this run's sum of n_contrib it gives the
+# kernel's instructions per launch for the issue-slot roofline.
+MEASURED_INSTRUCTIONS = {
+    "k_raster_bwd": (956326193 / 889808123, "csrc/raster.cu", "9f93864afe47"),
 }
 
 
-def measured_traffic(workload, kernel):
+def _source_unchanged(src, sha):
     import hashlib
+    path = os.path.join(ROOT, "paper_2604_02851_b300", src)
+    try:
+        with open(path, "rb") as f:
+            return hashlib.sha1(f.read()).hexdigest()[:12] == sha
+    except OSError:
+        return False
+
+
+def measured_traffic(workload, kernel):
     ent = MEASURED_TRAFFIC.get((workload, kernel))
     if ent is None:
         return None
     nbytes, src, sha = ent
-    path = os.path.join(ROOT, "paper_2604_02851_b300", src)
-    try:
-        with open(path, "rb") as f:
-            cur = hashlib.sha1(f.read()).hexdigest()[:12]
-    except OSError:
+    return nbytes if _source_unchanged(src, sha) else None
+
+
+def issue_roofline(kernel, sum_nc, ms, sm_count, sm_mhz):
+    """Issue-slot roofline of a raster kernel: its warp instructions per
+    launch (the measured per-fragment budget x this run's fragments) over its
+    time, against SMs x 4 schedulers x 1 instruction a cycle."""
+    ent = MEASURED_INSTRUCTIONS.get(kernel)
+    if ent is None or not _source_unchanged(ent[1], ent[2]):
         return None
-    return nbytes if cur == sha else None
+    inst = ent[0] * sum_nc
+    ach = inst / (ms / 1e3) / 1e9
+    peak = sm_count * 4 * sm_mhz / 1e3
+    return {"achieved": ach, "peak": peak, "unit": "G warp instructions/s", "frac": ach / peak,
+            "warp_instructions": inst,
+            "source": "warp instructions per (pixel, fragment) from one ncu capture (smsp__inst_executed.sum / "
+                      "sum of n_contrib, 200k Gaussians, 8 x 720p) x this run's sum of n_contrib"}
 
 
 # phases that are one kernel (plus negligible set-up launches), by kernel name
@@ -765,7 +793,9 @@ def run_ours(args, rank, world, local_rank):
                 "peak": dk["peak"],
                 "unit": dk["unit"], "frac": dk["frac"],
                 "traffic": measured_traffic(args.workload, SINGLE_KERNEL_PHASES[dom]),
-                "peak_source": peak_src if dk["bound"] == "hbm" else fp32_src}
+                "peak_source": peak_src if dk["bound"] == "hbm" else fp32_src,
+                "issue": issue_roofline(SINGLE_KERNEL_PHASES[dom], sum_nc, phase_avg[dom], sm_count, sm_mhz)
+                if dk["bound"] == "alu" else None}
 
     # ---- tensor deltas per attribute group since the start of the timed steps
     tensor_deltas = measure_tensor_deltas(gs, torch, params, snapshot, _peaks()[0]) if args.tensor_deltas else None
