@@ -1083,7 +1083,7 @@ def main():
                     help="threads per pixel row of the compositing adjoint (default: --raster-threads)")
     ap.add_argument("--autotune", action=argparse.BooleanOptionalAction, default=True,
                     help="choose binning / sort / raster settings with gs_autotune before timing")
-    ap.add_argument("--e2e-steps", type=int, default=30)
+    ap.add_argument("--e2e-steps", type=int, default=100)
     ap.add_argument("--cpu-samples", type=int, default=12)
     ap.add_argument("--plain-steps", type=int, default=10)
     ap.add_argument("--serve-requests", type=int, default=10_000, help="requests per offered load (0: no serving)")

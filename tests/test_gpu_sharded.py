@@ -105,3 +105,43 @@ def test_phases_out_of_range_are_rejected():
     torch.cuda.synchronize()
     tr.raise_status()
     tr.ctx.close()
+
+
+def test_update_part_with_preculling_matches_the_full_step():
+    """The update part alone, given the full step's gradient, reproduces the
+    full step's update bit for bit with a preculling grid: it finds the kept
+    Gaussians itself (Adam leaves the culled ones and their moments alone)."""
+    import torch
+    import paper_2604_02851_b300 as gs
+    from paper_2604_02851_b300.train import OnlineTrainer, estimate_keys
+    n, sh = 20_000, 1
+    cams = gi.ring_cameras(3, 160, 112)
+    planes = gi.make_scene(n, sh, 93)
+    origin, size, dims = (-1.0, -1.0, -1.0), 0.25, (8, 8, 8)
+    pc = gs.Precull(origin, size, dims)
+    vis = (np.random.default_rng(6).random(dims[::-1]) < 0.6).astype(np.uint8)
+    pc.visible.copy_(torch.from_numpy(vis))
+    ctx = gs.Context(0, 0)
+    p0 = torch.from_numpy(planes).cuda()
+    keys = estimate_keys(ctx, p0, sh, cams, slack=1.5)
+    full = OnlineTrainer(p0.clone(), sh, cams, keys, ctx=ctx, precull=pc)
+    tparams = torch.from_numpy(gi.make_scene(n, sh, 94)).cuda()
+    gs.gs_render_batch(full.ctx, tparams, sh, full.d_cams, 3, full.total_tiles, keys, full.npix, image=full.targets)
+    full.step()
+    torch.cuda.synchronize()
+    full.raise_status()
+    upd = OnlineTrainer(p0.clone(), sh, cams, keys, ctx=gs.Context(0, 0), precull=pc)
+    upd.grads.copy_(full.grads)
+    upd.step_update()
+    torch.cuda.synchronize()
+    upd.raise_status()
+    assert torch.equal(upd.params, full.params)
+    assert torch.equal(upd.m, full.m) and torch.equal(upd.v, full.v)
+    assert torch.equal(upd.baseline, full.baseline)
+    M = full.delta_count()
+    assert upd.delta_count() == M and torch.equal(upd.d_records[:M], full.d_records[:M])
+    # some Gaussians are culled, and those keep their parameters
+    changed = (upd.params != p0).any(dim=2).any(dim=0).cpu().numpy()
+    assert 0.2 < changed.mean() < 0.95
+    upd.ctx.close()
+    ctx.close()
