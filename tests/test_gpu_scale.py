@@ -128,7 +128,7 @@ def oracle_records(case, cams, views_idx):
     return out
 
 
-def band_lists(case, cams, rects, depth32, tiles):
+def band_lists(cams, rects, depth32, tiles):
     """Band-only list arrays for the oracle: the given tiles' sorted lists
     (bin_tiles), every other tile empty; plus the per-tile runs."""
     vals, start = O.bin_tiles(cams, rects, depth32, tiles, B)
@@ -184,7 +184,7 @@ def test_stagewise_binning_compositing_and_adjoints(case, tuned):
     depth32 = np.ascontiguousarray(proj32[..., 2])
     o_ranges, K = O.bin_ranges(cams, rects, B)
     tiles = case.band_tiles()
-    b_vals, b_start, b_ranges = band_lists(case, cams, rects, depth32, tiles)
+    b_vals, b_start, b_ranges = band_lists(cams, rects, depth32, tiles)
 
     # ---- GPU binning and sort of all 8 views (the tuned binning)
     d_cams = gs.cameras_to_device(cams)
@@ -289,7 +289,7 @@ def test_end_to_end_bands(case, tuned):
     TX, TY = case.TX, case.TY
     tiles3 = np.asarray([i * TX * TY + b * TX + x for i in range(V3) for b in case.bands for x in range(TX)],
                         dtype=np.int64)
-    o_vals, _, o_ranges = band_lists(case, cams, og[..., 12:16].astype(np.int32), og[..., 2].astype(np.float32),
+    o_vals, _, o_ranges = band_lists(cams, og[..., 12:16].astype(np.int32), og[..., 2].astype(np.float32),
                                      tiles3)
     # GPU: projection, binning and compositing of the same three views
     d_cams = gs.cameras_to_device(cams)
@@ -464,3 +464,82 @@ def test_train_step_equals_separate_calls(case, tuned):
     tr.ctx.close()
     del tr, th, m, v, base0, params
     torch.cuda.empty_cache()
+
+
+# ---------------------------------------------------------------- config 4: serving renders
+def test_serving_render_bands_at_config_4():
+    """Config 4 (2M Gaussians, SH3, the three request resolutions in one
+    batch): gs_render_batch (chunk-bitmap lists) equals the expanded-list
+    compositing of the same projection bit for bit, and three 16-row bands of
+    every request match the FP64 oracle's render within 1e-4, at the pixels
+    whose walks keep the same fragments in the same order on both sides."""
+    import torch
+    import paper_2604_02851_b300 as gs
+    n = 2_000_000
+    planes = gi.make_scene(n, SH, gi.SEED_SERVING)
+    rows = gi.planes_to_rows(planes).astype(np.float64)
+    reqs = gi.serving_requests(40, rate_hz=100.0, seed=gi.SEED_SERVING + 60)
+    pick = []
+    for r in reqs:  # one request of each resolution class
+        if all((r["width"], r["height"]) != (p["width"], p["height"]) for p in pick):
+            pick.append(r)
+    assert len(pick) == 3
+    cams = cams32(gi.cameras_from_eyes([p["eye"] for p in pick], [p["width"] for p in pick],
+                                       [p["height"] for p in pick]))
+    V = 3
+    params = torch.from_numpy(planes).cuda()
+    ctx = gs.Context(0, 0)
+    from paper_2604_02851_b300.train import estimate_keys
+    keys_cap = estimate_keys(ctx, params, SH, cams, slack=1.05)
+    ctx.reserve(ctx.workspace_size(cams, n, keys_cap))
+    d_cams = gs.cameras_to_device(cams)
+    tt = ctx.total_tiles(cams)
+    npix = gs.total_pixels(cams)
+    img_b = gs.gs_render_batch(ctx, params, SH, d_cams, V, tt, keys_cap, npix)
+    proj = gs.gs_project(ctx, params, SH, d_cams, V)
+    _, vals, ranges, nk = gs.gs_bin_sort(ctx, proj, d_cams, V, n, tt, keys_cap, want_keys=False)
+    img, _, _ = gs.gs_render_fwd(ctx, proj, d_cams, V, n, tt, vals, ranges, npix)
+    torch.cuda.synchronize()
+    assert ctx.status() == (0, 0)
+    assert torch.equal(img_b, img)
+    # bands: rows 4, the middle and the last of every request (ragged where H % 16 != 0)
+    TXs = [(int(w) + B - 1) // B for w in cams["width"]]
+    TYs = [(int(h) + B - 1) // B for h in cams["height"]]
+    toff = np.concatenate([[0], np.cumsum([a * b for a, b in zip(TXs, TYs)])])
+    tiles, pm = [], []
+    for v in range(V):
+        m = np.zeros((int(cams["height"][v]), int(cams["width"][v])), dtype=bool)
+        for b in (4, TYs[v] // 2, TYs[v] - 1):
+            tiles.extend(toff[v] + b * TXs[v] + np.arange(TXs[v]))
+            m[b * B:(b + 1) * B] = True
+        pm.append(m.ravel())
+    tiles = np.asarray(tiles, dtype=np.int64)
+    pm = np.concatenate(pm)
+    og = np.zeros((V, n, 16))
+    for v in range(V):
+        og[v] = O.project(rows, SH, gi.subset_cameras(cams, [v]), B)[0]
+    o_vals, _, o_ranges = band_lists(cams, og[..., 12:16].astype(np.int32), og[..., 2].astype(np.float32),
+                                     tiles)
+    gp = gpu_proj_to_oracle(proj.cpu().numpy())
+    g_full = ranges.cpu().numpy().view(np.uint32)
+    g_vals = np.concatenate([vals[int(g_full[t, 0]):int(g_full[t, 1])].cpu().numpy() for t in tiles]).view(np.uint32)
+    g_start = np.concatenate([[0], np.cumsum(g_full[tiles, 1].astype(np.int64) - g_full[tiles, 0])])
+    g_ranges = np.zeros_like(o_ranges)
+    g_ranges[tiles, 0] = g_start[:-1]
+    g_ranges[tiles, 1] = g_start[1:]
+    U = np.union1d(np.unique(o_vals), np.unique(g_vals))
+    og_c, gp_c = og[:, U], gp[:, U]
+    del og, gp
+    o_cv, g_cv = compact(U, o_vals), compact(U, g_vals)
+    same = same_sequences(cams, og_c, o_cv, o_ranges, gp_c, g_cv, g_ranges, B)
+    use = pm & same
+    print("config 4: band pixels", int(pm.sum()), "with another kept sequence", int((pm & ~same).sum()))
+    assert (pm & ~same).sum() <= 0.02 * pm.sum()
+    o_img, _, _ = O.render(cams, og_c, o_cv, o_ranges, tile=B)
+    use3 = np.concatenate([np.repeat(u.reshape(1, -1), 3, axis=0).ravel()
+                           for u in np.split(use, np.cumsum([int(w) * int(h) for w, h in
+                                                             zip(cams["width"], cams["height"])])[:-1])])
+    e = rel_l2(img.cpu().numpy()[use3], o_img[use3])
+    print("config 4: band image rel-L2", e)
+    assert e <= TOL
+    ctx.close()
