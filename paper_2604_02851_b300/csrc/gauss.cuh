@@ -90,8 +90,21 @@ struct Cam {
     int W, H;
 };
 
+// The 80-byte camera record as five 16-byte loads when it is 16-byte aligned
+// (any cudaMalloc'd array of them is), else field by field; the branch is
+// uniform over the warp.
 __device__ __forceinline__ Cam load_cam(const gs_camera* __restrict__ c) {
     Cam k;
+    if ((reinterpret_cast<uintptr_t>(c) & 15u) == 0) {
+        const float4* p = reinterpret_cast<const float4*>(c);
+        const float4 a = __ldg(p), b = __ldg(p + 1), d = __ldg(p + 2), e = __ldg(p + 3), f = __ldg(p + 4);
+        k.R[0] = a.x; k.R[1] = a.y; k.R[2] = a.z; k.R[3] = a.w;
+        k.R[4] = b.x; k.R[5] = b.y; k.R[6] = b.z; k.R[7] = b.w;
+        k.R[8] = d.x; k.t[0] = d.y; k.t[1] = d.z; k.t[2] = d.w;
+        k.fx = e.x; k.fy = e.y; k.cx = e.z; k.cy = e.w;
+        k.W = __float_as_int(f.x); k.H = __float_as_int(f.y); k.near = f.z;
+        return k;
+    }
 #pragma unroll
     for (int i = 0; i < 9; ++i) k.R[i] = __ldg(&c->R[i]);
 #pragma unroll

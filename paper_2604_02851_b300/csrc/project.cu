@@ -25,6 +25,7 @@ struct ViewGeom {
     float a, b, c, det;
     float3 dir;
     float len;
+    float iz;            // 1 / t_z
 };
 
 __device__ __forceinline__ bool view_geom(const Gauss& G, const Cam& C, ViewGeom& V) {
@@ -35,12 +36,13 @@ __device__ __forceinline__ bool view_geom(const Gauss& G, const Cam& C, ViewGeom
     if (!(V.tz > C.near)) return false;
     V.limx = kGuard * ((float)C.W / (2.f * C.fx));
     V.limy = kGuard * ((float)C.H / (2.f * C.fy));
-    const float rx = V.tx / V.tz, ry = V.ty / V.tz;
+    const float iz = 1.f / V.tz, iz2 = iz * iz;
+    V.iz = iz;
+    const float rx = V.tx * iz, ry = V.ty * iz;
     V.clx = rx < -V.limx ? -1 : (rx > V.limx ? 1 : 0);
     V.cly = ry < -V.limy ? -1 : (ry > V.limy ? 1 : 0);
     V.xt = fminf(fmaxf(rx, -V.limx), V.limx) * V.tz;
     V.yt = fminf(fmaxf(ry, -V.limy), V.limy) * V.tz;
-    const float iz = 1.f / V.tz, iz2 = iz * iz;
     V.J00 = C.fx * iz;
     V.J02 = -C.fx * V.xt * iz2;
     V.J11 = C.fy * iz;
@@ -68,19 +70,22 @@ __device__ __forceinline__ bool view_geom(const Gauss& G, const Cam& C, ViewGeom
     const float cz = -(W[2] * C.t[0] + W[5] * C.t[1] + W[8] * C.t[2]);
     const float dx = G.mu.x - cx, dy = G.mu.y - cy, dz = G.mu.z - cz;
     V.len = sqrtf(dx * dx + dy * dy + dz * dz);
-    V.dir = make_float3(dx / V.len, dy / V.len, dz / V.len);
+    const float il = 1.f / V.len;
+    V.dir = make_float3(dx * il, dy * il, dz * il);
     return true;
 }
 
 // Tile rectangle of the square of half-side r around (u, v).  The clamp is
 // applied in float before the conversion so that huge coordinates stay safe.
+// The tile size is a power of two (8 or 16), so multiplying by its reciprocal
+// is the exact quotient.
 __device__ __forceinline__ void tile_rect(float u, float v, float r, int TX, int TY, int tile,
                                           int& x0, int& y0, int& x1, int& y1) {
-    const float ft = (float)tile;
-    x0 = (int)fminf(fmaxf(floorf((u - r) / ft), 0.f), (float)TX);
-    y0 = (int)fminf(fmaxf(floorf((v - r) / ft), 0.f), (float)TY);
-    x1 = (int)fminf(fmaxf(floorf((u + r + ft - 1.f) / ft), 0.f), (float)TX);
-    y1 = (int)fminf(fmaxf(floorf((v + r + ft - 1.f) / ft), 0.f), (float)TY);
+    const float ft = (float)tile, ift = 1.f / ft;
+    x0 = (int)fminf(fmaxf(floorf((u - r) * ift), 0.f), (float)TX);
+    y0 = (int)fminf(fmaxf(floorf((v - r) * ift), 0.f), (float)TY);
+    x1 = (int)fminf(fmaxf(floorf((u + r + ft - 1.f) * ift), 0.f), (float)TX);
+    y1 = (int)fminf(fmaxf(floorf((v + r + ft - 1.f) * ift), 0.f), (float)TY);
 }
 
 // ------------------------------------------------------------ relighting
@@ -279,8 +284,8 @@ k_project(const float4* __restrict__ P, int64_t n, int64_t g_off, int64_t n_out,
             const float mid = 0.5f * (Vg.a + Vg.c);
             const float lam = mid + sqrtf(fmaxf(0.1f, mid * mid - Vg.det));
             r = ceilf(3.f * sqrtf(lam));
-            u = C.fx * Vg.tx / Vg.tz + C.cx;
-            vv = C.fy * Vg.ty / Vg.tz + C.cy;
+            u = C.fx * (Vg.tx * Vg.iz) + C.cx;
+            vv = C.fy * (Vg.ty * Vg.iz) + C.cy;
             const ViewInfo vi = vt[v];
             tile_rect(u, vv, r, vi.tx, vi.ty, tile, x0, y0, x1, y1);
             // cut the square down to the tiles of pixel centres inside the
@@ -289,11 +294,11 @@ k_project(const float4* __restrict__ P, int64_t n, int64_t g_off, int64_t n_out,
             // takes the splat nowhere else, so the image is the square's
             if (tau >= 0.f) {
                 const float rx = sqrtf(tau * Vg.a) * 1.001f + 0.01f, ry = sqrtf(tau * Vg.c) * 1.001f + 0.01f;
-                const float ft = (float)tile;
-                const int ex0 = (int)fminf(fmaxf(floorf(ceilf(u - rx - 0.5f) / ft), 0.f), (float)vi.tx);
-                const int ex1 = (int)fminf(fmaxf(floorf((u + rx - 0.5f) / ft) + 1.f, 0.f), (float)vi.tx);
-                const int ey0 = (int)fminf(fmaxf(floorf(ceilf(vv - ry - 0.5f) / ft), 0.f), (float)vi.ty);
-                const int ey1 = (int)fminf(fmaxf(floorf((vv + ry - 0.5f) / ft) + 1.f, 0.f), (float)vi.ty);
+                const float ift = 1.f / (float)tile;  // exact: the tile size is a power of two
+                const int ex0 = (int)fminf(fmaxf(floorf(ceilf(u - rx - 0.5f) * ift), 0.f), (float)vi.tx);
+                const int ex1 = (int)fminf(fmaxf(floorf((u + rx - 0.5f) * ift) + 1.f, 0.f), (float)vi.tx);
+                const int ey0 = (int)fminf(fmaxf(floorf(ceilf(vv - ry - 0.5f) * ift), 0.f), (float)vi.ty);
+                const int ey1 = (int)fminf(fmaxf(floorf((vv + ry - 0.5f) * ift) + 1.f, 0.f), (float)vi.ty);
                 x0 = max(x0, ex0); x1 = min(x1, ex1); y0 = max(y0, ey0); y1 = min(y1, ey1);
             } else {
                 x1 = x0;  // a splat fainter than 1/255 takes no pixel
@@ -477,7 +482,7 @@ k_project_bwd(const float4* __restrict__ P, int64_t n, int64_t n_out, Dyn dyn, c
         const float dJ02 = dM0[0] * W[6] + dM0[1] * W[7] + dM0[2] * W[8];
         const float dJ11 = dM1[0] * W[3] + dM1[1] * W[4] + dM1[2] * W[5];
         const float dJ12 = dM1[0] * W[6] + dM1[1] * W[7] + dM1[2] * W[8];
-        const float tz = Vg.tz, iz = 1.f / tz, iz2 = iz * iz, iz3 = iz2 * iz;
+        const float iz = Vg.iz, iz2 = iz * iz, iz3 = iz2 * iz;
         float dtx = 0.f, dty = 0.f, dtz = 0.f;
         dtz += -dJ00 * C.fx * iz2 - dJ11 * C.fy * iz2;
         dtz += dJ02 * 2.f * C.fx * Vg.xt * iz3 + dJ12 * 2.f * C.fy * Vg.yt * iz3;
