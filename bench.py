@@ -97,9 +97,10 @@ def phase_model(n, V, K, total_tiles, npix, sum_nc, n_changed, binning, passes, 
         emit = vn * (8 + 4) + K * 8
         sort = K * (16 * (passes - 1) + 12) + total_tiles * 16
     return {
-        # parameters read; per (view, Gaussian) the 64-byte record, the 8-byte
-        # depth-sort item and the 4-byte tile rectangle written
-        "project": ("hbm", n * 240 + vn * (64 + 8 + 4)),
+        # parameters read; per (view, Gaussian) the 48-byte record of the
+        # fused step, the 8-byte depth-sort item and the 4-byte tile rectangle
+        # written
+        "project": ("hbm", n * 240 + vn * (48 + 8 + 4)),
         "depth_sort": ("hbm", vn * (4 * 16 + 4)),
         "emit": ("hbm", emit),
         "tile_sort": ("hbm", sort),

@@ -486,14 +486,14 @@ gs_status_t gs_render_batch(gs_ctx* ctx, const gs_scene* scene, const gs_camera*
     launch_view_table(d_cams, n_requests, ctx->tile, p.vt, total_tiles, ctx->d_status, st);
     const Dyn dyn = scene_dyn(ctx, scene->dyn, scene->precull, nullptr, scene->lighting, st);
     launch_project(scene->params, scene->n, scene->sh_degree, dyn, d_cams, p.vt, n_requests, ctx->tile, p.proj,
-                   s.dkv[0], st, 0, -1, s.rects);
+                   s.dkv[0], st, 0, -1, s.rects, kRecF4Compact);
     // two-level binning leaves the per-tile lists in chunk-bitmap form
     CoarseLists cl;
     launch_bin_sort(p.proj, p.vt, n_requests, scene->n, keys_cap, total_tiles, ctx->binning, ctx->sort_bits, ctx->sort_items, s, true, nullptr,
                     p.vals, p.ranges, p.n_keys, ctx->d_status, ctx->sm_count, st, nullptr, nullptr, 0,
                     scene->precull != nullptr, &cl, spin_only(ctx));
     launch_render_fwd(p.proj, p.vt, n_requests, scene->n, ctx->tile, ctx->raster_tpr, p.vals, p.ranges, b, image, nullptr,
-                      nullptr, total_tiles, st, &cl);
+                      nullptr, total_tiles, st, &cl, kRecF4Compact);
     return launch_check();
 }
 
@@ -549,7 +549,7 @@ gs_status_t gs_train_step_events(gs_ctx* ctx, const gs_camera* d_cams, const gs_
         // the Gaussians it keeps (Adam leaves the others).
         if (cfg->precull)
             launch_project(io->params, na, cfg->sh_degree, dyn, d_cams, p.vt, V, B, p.proj, s.dkv[0], st, 0, n,
-                           s.rects);
+                           s.rects, kRecF4Compact);
         for (int e = 1; e <= 8; ++e) mark(ev, e, st);
         gs_adam_cfg ac = cfg->adam;
         ac.d_step = io->d_step;
@@ -559,10 +559,11 @@ gs_status_t gs_train_step_events(gs_ctx* ctx, const gs_camera* d_cams, const gs_
                           p.delta, st, ev ? mark : nullptr, ev, 9);
         return launch_check();
     }
-    launch_project(io->params, na, cfg->sh_degree, dyn, d_cams, p.vt, V, B, p.proj, s.dkv[0], st, 0, n, s.rects);
+    launch_project(io->params, na, cfg->sh_degree, dyn, d_cams, p.vt, V, B, p.proj, s.dkv[0], st, 0, n, s.rects,
+                   kRecF4Compact);
     if (cfg->n_frozen > 0)
         launch_project(io->frozen, cfg->n_frozen, cfg->sh_degree, dyn, d_cams, p.vt, V, B, p.proj, s.dkv[0], st,
-                       na, n, s.rects);
+                       na, n, s.rects, kRecF4Compact);
     mark(ev, 1, st);
     // two-level binning leaves the per-tile lists in chunk-bitmap form, which
     // both raster kernels walk
@@ -572,15 +573,16 @@ gs_status_t gs_train_step_events(gs_ctx* ctx, const gs_camera* d_cams, const gs_
                     cfg->precull != nullptr, &cl, spin_only(ctx));
     mark(ev, 4, st);
     launch_render_fwd(p.proj, p.vt, V, n, B, ctx->raster_tpr, p.vals, p.ranges, b, io->image, p.T_final, p.n_contrib, tt,
-                      st, &cl);
+                      st, &cl, kRecF4Compact);
     mark(ev, 5, st);
     launch_loss(io->image, io->targets, V, cfg->height, cfg->width, cfg->w_l1, cfg->w_ssim, io->d_loss, p.dimage,
                 p.loss, st);
     mark(ev, 6, st);
     launch_raster_bwd(p.proj, p.vt, V, n, B, ctx->raster_bwd_tpr, p.vals, p.ranges, b, p.T_final, p.n_contrib, p.dimage, p.grad2d, tt,
-                      st, na, &cl);
+                      st, na, &cl, kRecF4Compact);
     mark(ev, 7, st);
-    launch_project_bwd(io->params, na, cfg->sh_degree, dyn, d_cams, V, p.proj, p.grad2d, io->grads, 0, st, n);
+    launch_project_bwd(io->params, na, cfg->sh_degree, dyn, d_cams, V, p.proj, p.grad2d, io->grads, 0, st, n,
+                       kRecF4Compact);
     mark(ev, 8, st);
     if (!(phases & GS_TRAIN_UPDATE)) {
         mark(ev, 9, st);
@@ -630,17 +632,18 @@ gs_status_t gs_autotune(gs_ctx* ctx, const gs_scene* scene, const gs_camera* d_c
     // its adjoint, and after the adjoint
     auto run = [&](cudaEvent_t* ev) {
         launch_view_table(d_cams, V, B, p.vt, tt, ctx->d_status, st);
-        launch_project(scene->params, n, scene->sh_degree, dyn, d_cams, p.vt, V, B, p.proj, s.dkv[0], st, 0, -1, s.rects);
+        launch_project(scene->params, n, scene->sh_degree, dyn, d_cams, p.vt, V, B, p.proj, s.dkv[0], st, 0, -1, s.rects,
+                       kRecF4Compact);
         CoarseLists cl;
         launch_bin_sort(p.proj, p.vt, V, n, keys_cap, tt, ctx->binning, ctx->sort_bits, ctx->sort_items, s, true,
                         nullptr, p.vals, p.ranges, p.n_keys, ctx->d_status, ctx->sm_count, st, nullptr, nullptr, 0,
                         scene->precull != nullptr, &cl, spin_only(ctx));
         if (ev) cudaEventRecord(ev[0], st);
         launch_render_fwd(p.proj, p.vt, V, n, B, ctx->raster_tpr, p.vals, p.ranges, bg, image, p.T_final,
-                          p.n_contrib, tt, st, &cl);
+                          p.n_contrib, tt, st, &cl, kRecF4Compact);
         if (ev) cudaEventRecord(ev[1], st);
         launch_raster_bwd(p.proj, p.vt, V, n, B, ctx->raster_bwd_tpr, p.vals, p.ranges, bg, p.T_final, p.n_contrib,
-                          p.dimage, p.grad2d, tt, st, -1, &cl);
+                          p.dimage, p.grad2d, tt, st, -1, &cl, kRecF4Compact);
         if (ev) cudaEventRecord(ev[2], st);
     };
     constexpr int kMaxReps = 16;

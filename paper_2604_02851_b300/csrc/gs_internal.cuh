@@ -9,6 +9,11 @@
 namespace gs {
 
 constexpr int kProjStride = 16;  // floats per (view, Gaussian) projection record
+// float4s per record: the public 64-byte form, and the 48-byte form the fused
+// calls keep in their workspace (the first three float4s; the tile rectangle,
+// which only the depth-key pass of gs_bin_sort reads from a record, goes to
+// the separate rectangle item there)
+constexpr int kRecF4 = 4, kRecF4Compact = 3;
 constexpr int kGradStride = 12;  // floats per (view, Gaussian) 2D-gradient record
 constexpr int kParamPlanes = 15;
 constexpr int kMaxViews = 4096;
@@ -200,7 +205,7 @@ inline Dyn make_dyn(const gs_dynamics* d, const gs_precull* pc = nullptr, uint8_
 // array; dynamics arrays are indexed by g_off + g.
 void launch_project(const float* params, int64_t n, int sh_degree, const Dyn& dyn, const gs_camera* d_cams,
                     const ViewInfo* vt, int V, int tile, float* proj, uint64_t* depth_kv, cudaStream_t st,
-                    int64_t g_off = 0, int64_t n_out = -1, uint2* rects = nullptr);
+                    int64_t g_off = 0, int64_t n_out = -1, uint2* rects = nullptr, int rec4 = kRecF4);
 
 // L2 eviction-priority policies for cache-hinted loads and stores.
 __device__ __forceinline__ uint64_t l2_policy_evict_last() {
@@ -234,7 +239,7 @@ __device__ __forceinline__ uint2 ld_hint(const uint2* p, uint64_t pol) {
 // Adjoint of the first n records of each view (record stride n_out).
 void launch_project_bwd(const float* params, int64_t n, int sh_degree, const Dyn& dyn, const gs_camera* d_cams,
                         int V, const float* proj, const float* grad2d, float* dparams,
-                        int accumulate, cudaStream_t st, int64_t n_out = -1);
+                        int accumulate, cudaStream_t st, int64_t n_out = -1, int rec4 = kRecF4);
 
 // Fills tab ([max(1, n_groups)][kLitTab]) from the device lighting buffer
 // (gs_lighting.light) and the group poses of `dyn`.
@@ -321,13 +326,13 @@ void launch_bin_sort(const float* proj, const ViewInfo* vt, int V, int64_t n, in
 void launch_render_fwd(const float* proj, const ViewInfo* vt, int V, int64_t n, int tile, int tpr,
                        const uint32_t* vals, const uint32_t* ranges, float3 bg, float* image,
                        float* T_final, uint32_t* n_contrib, int64_t total_tiles,
-                       cudaStream_t st, const CoarseLists* coarse = nullptr);
+                       cudaStream_t st, const CoarseLists* coarse = nullptr, int rec4 = kRecF4);
 
 void launch_raster_bwd(const float* proj, const ViewInfo* vt, int V, int64_t n, int tile, int tpr,
                        const uint32_t* vals, const uint32_t* ranges, float3 bg,
                        const float* T_final, const uint32_t* n_contrib, const float* dimage,
                        float* grad2d, int64_t total_tiles, cudaStream_t st, int64_t n_active = -1,
-                       const CoarseLists* coarse = nullptr);
+                       const CoarseLists* coarse = nullptr, int rec4 = kRecF4);
 
 size_t loss_scratch_bytes(int V, int H, int W);
 void launch_loss(const float* image, const float* target, int V, int H, int W, float w_l1,

@@ -211,7 +211,7 @@ template <int D, bool LIT>
 __global__ void __launch_bounds__(256, LIT ? 3 : 4)
 k_project(const float4* __restrict__ P, int64_t n, int64_t g_off, int64_t n_out, Dyn dyn,
           const gs_camera* __restrict__ cams, const ViewInfo* __restrict__ vt, int V, int tile,
-          float4* __restrict__ proj, uint64_t* __restrict__ dkv, uint2* __restrict__ rects) {
+          float4* __restrict__ proj, uint64_t* __restrict__ dkv, uint2* __restrict__ rects, int rec4) {
     const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     extern __shared__ float s_lt[];
     bool staged = false;
@@ -275,7 +275,7 @@ k_project(const float4* __restrict__ P, int64_t n, int64_t g_off, int64_t n_out,
     for (int v = 0; v < V; ++v) {
         const Cam C = load_cam(cams + v);
         const int64_t rec = (int64_t)v * n_out + g_off + g;
-        float4* out = proj + rec * 4;
+        float4* out = proj + rec * rec4;
         ViewGeom Vg;
         bool ok = kept && view_geom(G, C, Vg);
         float u = 0.f, vv = 0.f, r = 0.f;
@@ -307,7 +307,8 @@ k_project(const float4* __restrict__ P, int64_t n, int64_t g_off, int64_t n_out,
         }
         if (!ok) {
             const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-            out[0] = z; out[1] = z; out[2] = z; out[3] = z;
+            out[0] = z; out[1] = z; out[2] = z;
+            if (rec4 == kRecF4) out[3] = z;
             if (dkv) dkv[rec] = (0xFFFFFFFFull << 32) | (uint32_t)rec;
             if (rects) {
                 if (rect32) st_hint(reinterpret_cast<uint32_t*>(rects) + rec, 1u, l2_policy_evict_last());
@@ -344,8 +345,9 @@ k_project(const float4* __restrict__ P, int64_t n, int64_t g_off, int64_t n_out,
         out[1] = make_float4(Vg.c * idet, -Vg.b * idet, Vg.a * idet, r);
         out[2] = make_float4(rgb[0], rgb[1], rgb[2], __uint_as_float(mask));
         const uint32_t lo = (uint32_t)x0 | ((uint32_t)y0 << 16), hi = (uint32_t)x1 | ((uint32_t)y1 << 16);
-        out[3] = make_float4(__uint_as_float(lo), __uint_as_float(hi),
-                             __uint_as_float((uint32_t)((x1 - x0) * (y1 - y0))), 0.f);
+        if (rec4 == kRecF4)
+            out[3] = make_float4(__uint_as_float(lo), __uint_as_float(hi),
+                                 __uint_as_float((uint32_t)((x1 - x0) * (y1 - y0))), 0.f);
         if (dkv) dkv[rec] = ((uint64_t)__float_as_uint(Vg.tz) << 32) | (uint32_t)rec;
         // the emission gathers the rectangle in depth order: kept in L2
         if (rects) {
@@ -363,7 +365,7 @@ __global__ void __launch_bounds__(128, LIT ? 3 : 4)
 k_project_bwd(const float4* __restrict__ P, int64_t n, int64_t n_out, Dyn dyn, const gs_camera* __restrict__ cams,
               int V,
               const float4* __restrict__ proj, const float4* __restrict__ g2d,
-              float4* __restrict__ dP, int accumulate) {
+              float4* __restrict__ dP, int accumulate, int rec4) {
     const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= n) return;
     constexpr int NB = (D + 1) * (D + 1);
@@ -397,8 +399,10 @@ k_project_bwd(const float4* __restrict__ P, int64_t n, int64_t n_out, Dyn dyn, c
         if (ga.x == 0.f && ga.y == 0.f && ga.z == 0.f && ga.w == 0.f && gb.x == 0.f && gb.y == 0.f &&
             gb.z == 0.f && gb.w == 0.f && gc.x == 0.f)
             continue;
-        if (__float_as_uint(proj[rec * 4 + 3].z) == 0u) continue;  // culled in this view
-        const uint32_t mask = __float_as_uint(proj[rec * 4 + 2].w);
+        // culled in this view (a 48-byte record comes from a fused call, whose
+        // 2D gradient is zero for culled records: they are in no tile list)
+        if (rec4 == kRecF4 && __float_as_uint(proj[rec * 4 + 3].z) == 0u) continue;
+        const uint32_t mask = __float_as_uint(proj[rec * rec4 + 2].w);
         const Cam C = load_cam(cams + v);
         ViewGeom Vg;
         if (!view_geom(G, C, Vg)) continue;
@@ -634,7 +638,7 @@ void launch_view_table(const gs_camera* d_cams, int V, int tile, ViewInfo* vt, l
 
 void launch_project(const float* params, int64_t n, int sh_degree, const Dyn& dyn, const gs_camera* d_cams,
                     const ViewInfo* vt, int V, int tile, float* proj, uint64_t* depth_kv, cudaStream_t st,
-                    int64_t g_off, int64_t n_out, uint2* rects) {
+                    int64_t g_off, int64_t n_out, uint2* rects, int rec4) {
     if (n <= 0) return;
     if (n_out < 0) n_out = n;
     const int threads = 256;
@@ -644,9 +648,9 @@ void launch_project(const float* params, int64_t n, int sh_degree, const Dyn& dy
     const bool lit = dyn.lit_tab != nullptr;
     const size_t smem = lit && lit_groups(dyn) <= kStageGroups ? sizeof(float) * lit_groups(dyn) * kStageStride : 0;
 #define GS_PROJ(DD)                                                                                              \
-    (lit ? k_project<DD, true><<<blocks, threads, smem, st>>>(P, n, g_off, n_out, dyn, d_cams, vt, V, tile, out, depth_kv, rects) \
+    (lit ? k_project<DD, true><<<blocks, threads, smem, st>>>(P, n, g_off, n_out, dyn, d_cams, vt, V, tile, out, depth_kv, rects, rec4) \
          : k_project<DD, false><<<blocks, threads, sizeof(float4) * threads * ((3 * (DD + 1) * (DD + 1) + 3) / 4), st>>>( \
-               P, n, g_off, n_out, dyn, d_cams, vt, V, tile, out, depth_kv, rects))
+               P, n, g_off, n_out, dyn, d_cams, vt, V, tile, out, depth_kv, rects, rec4))
     switch (sh_degree) {
         case 0: GS_PROJ(0); break;
         case 1: GS_PROJ(1); break;
@@ -658,7 +662,7 @@ void launch_project(const float* params, int64_t n, int sh_degree, const Dyn& dy
 
 void launch_project_bwd(const float* params, int64_t n, int sh_degree, const Dyn& dyn, const gs_camera* d_cams,
                         int V, const float* proj, const float* grad2d, float* dparams, int accumulate,
-                        cudaStream_t st, int64_t n_out) {
+                        cudaStream_t st, int64_t n_out, int rec4) {
     if (n <= 0) return;
     if (n_out < 0) n_out = n;
     const int threads = 128;
@@ -669,8 +673,10 @@ void launch_project_bwd(const float* params, int64_t n, int sh_degree, const Dyn
     float4* dP = reinterpret_cast<float4*>(dparams);
     const bool lit = dyn.lit_tab != nullptr;
 #define GS_PROJ_BWD(DD)                                                                                          \
-    (lit ? k_project_bwd<DD, true><<<blocks, threads, 0, st>>>(P, n, n_out, dyn, d_cams, V, pr, g2, dP, accumulate) \
-         : k_project_bwd<DD, false><<<blocks, threads, 0, st>>>(P, n, n_out, dyn, d_cams, V, pr, g2, dP, accumulate))
+    (lit ? k_project_bwd<DD, true><<<blocks, threads, 0, st>>>(P, n, n_out, dyn, d_cams, V, pr, g2, dP, accumulate, \
+                                                               rec4)                                            \
+         : k_project_bwd<DD, false><<<blocks, threads, 0, st>>>(P, n, n_out, dyn, d_cams, V, pr, g2, dP, accumulate, \
+                                                                rec4))
     switch (sh_degree) {
         case 0: GS_PROJ_BWD(0); break;
         case 1: GS_PROJ_BWD(1); break;

@@ -175,7 +175,7 @@ template <int B, int TPR, bool COARSE>
 __global__ void __launch_bounds__(B * TPR, fwd_min_blocks<B, TPR>())
 k_render_fwd(const float4* __restrict__ proj, const ViewInfo* __restrict__ vt, int V, int64_t n,
              const uint32_t* __restrict__ vals, const uint2* __restrict__ ranges, CoarseLists cl, float3 bg,
-             float* __restrict__ image, float* __restrict__ T_final, uint32_t* __restrict__ n_contrib) {
+             float* __restrict__ image, float* __restrict__ T_final, uint32_t* __restrict__ n_contrib, int rec4) {
     constexpr int NT = B * TPR;        // threads per block
     constexpr int PX = B / TPR;        // pixels per thread
     constexpr int NP = PX / 2;         // pixel pairs per thread
@@ -239,7 +239,7 @@ k_render_fwd(const float4* __restrict__ proj, const ViewInfo* __restrict__ vt, i
             if (slot < nslot) {
                 uint32_t g;
                 item(slot, ipos[h], g);
-                const int64_t r = (rbase + g) * 4;
+                const int64_t r = (rbase + g) * rec4;
                 const float4 a = proj[r], b = proj[r + 1];
                 rc[h] = proj[r + 2];
                 ra[h] = make_float4(a.x, a.y, a.w, cutoff_log2(a.w));
@@ -421,7 +421,7 @@ __global__ void __launch_bounds__(B * TPR, bwd_min_blocks<B, TPR>())
 k_raster_bwd(const float4* __restrict__ proj, const ViewInfo* __restrict__ vt, int V, int64_t n,
              const uint32_t* __restrict__ vals, const uint2* __restrict__ ranges, CoarseLists cl, float3 bg,
              const float* __restrict__ T_final, const uint32_t* __restrict__ n_contrib,
-             const float* __restrict__ dimage, float* __restrict__ grad2d, int64_t n_active) {
+             const float* __restrict__ dimage, float* __restrict__ grad2d, int64_t n_active, int rec4) {
     constexpr int NT = B * TPR;
     constexpr int PX = B / TPR;
     constexpr int NP = PX / 2;
@@ -502,7 +502,7 @@ k_raster_bwd(const float4* __restrict__ proj, const ViewInfo* __restrict__ vt, i
         float4 a, b, c, aq, qq;
         if ((int)threadIdx.x < nslot) {
             item((int)threadIdx.x, ipos, g);
-            const int64_t r = (rbase + g) * 4;
+            const int64_t r = (rbase + g) * rec4;
             a = proj[r]; b = proj[r + 1]; c = proj[r + 2];
             aq = make_float4(a.x, a.y, a.w, cutoff_log2(a.w));
             qq = log2_conic(b);
@@ -680,7 +680,7 @@ k_raster_bwd(const float4* __restrict__ proj, const ViewInfo* __restrict__ vt, i
 void launch_render_fwd(const float* proj, const ViewInfo* vt, int V, int64_t n, int tile, int tpr,
                        const uint32_t* vals, const uint32_t* ranges, float3 bg, float* image,
                        float* T_final, uint32_t* n_contrib, int64_t total_tiles, cudaStream_t st,
-                       const CoarseLists* coarse) {
+                       const CoarseLists* coarse, int rec4) {
     if (total_tiles <= 0) return;
     const float4* p = reinterpret_cast<const float4*>(proj);
     const uint2* r = reinterpret_cast<const uint2*>(ranges);
@@ -688,9 +688,9 @@ void launch_render_fwd(const float* proj, const ViewInfo* vt, int V, int64_t n, 
     const CoarseLists cl = coarse ? *coarse : CoarseLists{};
 #define GS_FWD(BB, TT, NTH)                                                                                        \
     (cl.citems ? k_render_fwd<BB, TT, true><<<nb, NTH, 0, st>>>(p, vt, V, n, vals, r, cl, bg, image, T_final,      \
-                                                                n_contrib)                                         \
+                                                                n_contrib, rec4)                                   \
                : k_render_fwd<BB, TT, false><<<nb, NTH, 0, st>>>(p, vt, V, n, vals, r, cl, bg, image, T_final,     \
-                                                                 n_contrib))
+                                                                 n_contrib, rec4))
     if (tile == 8)
         GS_FWD(8, 4, 32);
     else if (tpr == 2)
@@ -703,7 +703,8 @@ void launch_render_fwd(const float* proj, const ViewInfo* vt, int V, int64_t n, 
 void launch_raster_bwd(const float* proj, const ViewInfo* vt, int V, int64_t n, int tile, int tpr,
                        const uint32_t* vals, const uint32_t* ranges, float3 bg, const float* T_final,
                        const uint32_t* n_contrib, const float* dimage, float* grad2d,
-                       int64_t total_tiles, cudaStream_t st, int64_t n_active, const CoarseLists* coarse) {
+                       int64_t total_tiles, cudaStream_t st, int64_t n_active, const CoarseLists* coarse,
+                       int rec4) {
     if (n_active < 0) n_active = n;
     cudaMemsetAsync(grad2d, 0, sizeof(float) * kGradStride * (size_t)V * (size_t)n, st);
     if (total_tiles <= 0) return;
@@ -713,9 +714,9 @@ void launch_raster_bwd(const float* proj, const ViewInfo* vt, int V, int64_t n, 
     const CoarseLists cl = coarse ? *coarse : CoarseLists{};
 #define GS_BWD(BB, TT, NTH)                                                                                        \
     (cl.citems ? k_raster_bwd<BB, TT, true><<<nb, NTH, 0, st>>>(p, vt, V, n, vals, r, cl, bg, T_final, n_contrib,  \
-                                                                dimage, grad2d, n_active)                          \
+                                                                dimage, grad2d, n_active, rec4)                    \
                : k_raster_bwd<BB, TT, false><<<nb, NTH, 0, st>>>(p, vt, V, n, vals, r, cl, bg, T_final, n_contrib, \
-                                                                 dimage, grad2d, n_active))
+                                                                 dimage, grad2d, n_active, rec4))
     if (tile == 8)
         GS_BWD(8, 4, 32);
     else if (tpr == 2)
