@@ -766,6 +766,11 @@ def run_ours(args, rank, world, local_rank):
     chunks = Kc // 256 + n_super
     del proj, vals, ranges, T, nc
     tile_passes = math.ceil(math.ceil(math.log2(max(tr.total_tiles, 2))) / args.sort_bits)
+    if args.binning == "two_level":
+        # the fused step sorts the super-tile key; a key of sort_bits + 1 to
+        # 9 bits takes one wide pass
+        sbits = math.ceil(math.log2(max(n_super, 2)))
+        tile_passes = 1 if args.sort_bits < sbits <= 9 else math.ceil(sbits / args.sort_bits)
     del wc_params
     model = phase_model(n, V, K, tr.total_tiles, tr.npix, sum_nc, changed, args.binning, tile_passes, Kc, chunks,
                         n_train=params.shape[1])

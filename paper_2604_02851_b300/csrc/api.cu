@@ -531,6 +531,7 @@ gs_status_t gs_train_step_events(gs_ctx* ctx, const gs_camera* d_cams, const gs_
     const int64_t n = cfg->n + cfg->n_frozen;   // every rendered Gaussian
     const int B = ctx->tile;
     const int64_t tt = (int64_t)V * ((cfg->width + B - 1) / B) * ((cfg->height + B - 1) / B);
+    const int64_t ns = super_tiles_of(V, cfg->width, cfg->height, B);
     const int64_t px = (int64_t)V * cfg->width * cfg->height;
     const FusedPlan p0 = plan_fused(nullptr, V, n, cfg->keys_cap, tt, px, cfg->height, cfg->width, true);
     if (check_ws(ctx, p0.bytes)) return GS_ERR_CAPACITY;
@@ -541,7 +542,7 @@ gs_status_t gs_train_step_events(gs_ctx* ctx, const gs_camera* d_cams, const gs_
     carve_sort_scratch(p.sort, V, n, cfg->keys_cap, tt, &s);
     const float3 b = make_float3(cfg->bg[0], cfg->bg[1], cfg->bg[2]);
     mark(ev, 0, st);
-    launch_view_table(d_cams, V, B, p.vt, tt, ctx->d_status, st);
+    launch_view_table(d_cams, V, B, p.vt, tt, ctx->d_status, st, ns);
     const Dyn dyn = scene_dyn(ctx, cfg->dyn, cfg->precull, p.fwd, cfg->lighting, st);
     if (!(phases & GS_TRAIN_GRADIENT)) {
         // update only: the gradient of the caller's io->grads; the phase marks
@@ -570,7 +571,7 @@ gs_status_t gs_train_step_events(gs_ctx* ctx, const gs_camera* d_cams, const gs_
     CoarseLists cl;
     launch_bin_sort(p.proj, p.vt, V, n, cfg->keys_cap, tt, ctx->binning, ctx->sort_bits, ctx->sort_items, s, true, nullptr,
                     p.vals, p.ranges, p.n_keys, ctx->d_status, ctx->sm_count, st, ev ? mark : nullptr, ev, 2,
-                    cfg->precull != nullptr, &cl, spin_only(ctx));
+                    cfg->precull != nullptr, &cl, spin_only(ctx), ns);
     mark(ev, 4, st);
     launch_render_fwd(p.proj, p.vt, V, n, B, ctx->raster_tpr, p.vals, p.ranges, b, io->image, p.T_final, p.n_contrib, tt,
                       st, &cl, kRecF4Compact);
@@ -614,8 +615,11 @@ gs_status_t gs_autotune(gs_ctx* ctx, const gs_scene* scene, const gs_camera* d_c
     const int64_t n = scene->n;
     const int B = ctx->tile;
     const int64_t tt = tiles_of(host_cams, V, B);
-    int64_t px = 0;
-    for (int v = 0; v < V; ++v) px += (int64_t)host_cams[v].width * host_cams[v].height;
+    int64_t px = 0, ns = 0;
+    for (int v = 0; v < V; ++v) {
+        px += (int64_t)host_cams[v].width * host_cams[v].height;
+        ns += super_tiles_of(1, host_cams[v].width, host_cams[v].height, B);
+    }
     const FusedPlan p0 = plan_fused(nullptr, V, n, keys_cap, tt, px, host_cams[0].height, host_cams[0].width, true);
     if (check_ws(ctx, p0.bytes)) return GS_ERR_CAPACITY;
     const FusedPlan p = plan_fused(ctx->ws, V, n, keys_cap, tt, px, host_cams[0].height, host_cams[0].width, true);
@@ -631,13 +635,13 @@ gs_status_t gs_autotune(gs_ctx* ctx, const gs_scene* scene, const gs_camera* d_c
     // ev (may be null): recorded before compositing, between compositing and
     // its adjoint, and after the adjoint
     auto run = [&](cudaEvent_t* ev) {
-        launch_view_table(d_cams, V, B, p.vt, tt, ctx->d_status, st);
+        launch_view_table(d_cams, V, B, p.vt, tt, ctx->d_status, st, ns);
         launch_project(scene->params, n, scene->sh_degree, dyn, d_cams, p.vt, V, B, p.proj, s.dkv[0], st, 0, -1, s.rects,
                        kRecF4Compact);
         CoarseLists cl;
         launch_bin_sort(p.proj, p.vt, V, n, keys_cap, tt, ctx->binning, ctx->sort_bits, ctx->sort_items, s, true,
                         nullptr, p.vals, p.ranges, p.n_keys, ctx->d_status, ctx->sm_count, st, nullptr, nullptr, 0,
-                        scene->precull != nullptr, &cl, spin_only(ctx));
+                        scene->precull != nullptr, &cl, spin_only(ctx), ns);
         if (ev) cudaEventRecord(ev[0], st);
         launch_render_fwd(p.proj, p.vt, V, n, B, ctx->raster_tpr, p.vals, p.ranges, bg, image, p.T_final,
                           p.n_contrib, tt, st, &cl, kRecF4Compact);

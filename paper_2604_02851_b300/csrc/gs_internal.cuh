@@ -145,8 +145,16 @@ __device__ __forceinline__ bool look_back(unsigned long long* lb, int64_t slot, 
 // ------------------------------------------------------------ launchers
 // Every launcher enqueues on `st`; none synchronises or allocates.
 
+// expect_tiles / expect_super (>= 0): the tile and super-tile totals the
+// caller planned for; a different total is reported as GS_ERR_ARG.
 void launch_view_table(const gs_camera* d_cams, int V, int tile, ViewInfo* vt,
-                       long long expect_tiles, DevStatus* status, cudaStream_t st);
+                       long long expect_tiles, DevStatus* status, cudaStream_t st, long long expect_super = -1);
+
+// Super-tiles of views of one size (kSuper x kSuper tiles each).
+inline int64_t super_tiles_of(int V, int width, int height, int tile) {
+    const int64_t tx = (width + tile - 1) / tile, ty = (height + tile - 1) / tile;
+    return (int64_t)V * ((tx + kSuper - 1) / kSuper) * ((ty + kSuper - 1) / kSuper);
+}
 
 // Per-scene extras as the projection kernels take them (by value):
 // dynamics (group == nullptr: static) and preculling (cell_vis == nullptr:
@@ -309,6 +317,9 @@ struct CoarseLists {
 // coarse: when non-null and the two-level path is taken, the per-tile lists
 // are left in chunk-bitmap form (*coarse filled; sorted_keys, sorted_vals and
 // ranges untouched); otherwise coarse->citems stays null.
+// n_super (> 0): the exact super-tile total, which the view table checks; it
+// sizes the super-tile key (one 9-bit pass instead of two 8-bit ones for up
+// to 512 super-tiles).  0: unknown, bounded by the tile count.
 void launch_bin_sort(const float* proj, const ViewInfo* vt, int V, int64_t n, int64_t keys_cap,
                      int64_t total_tiles, int binning, int sort_bits, int sort_items, const SortScratch& s,
                      bool depth_ready,
@@ -316,7 +327,7 @@ void launch_bin_sort(const float* proj, const ViewInfo* vt, int V, int64_t n, in
                      uint32_t* d_num_keys, DevStatus* status, int sm_count, cudaStream_t st,
                      void (*mark)(void* const*, int, cudaStream_t) = nullptr, void* const* events = nullptr,
                      int first_event = 0, bool compact = false, CoarseLists* coarse = nullptr,
-                     WaitCfg wait = WaitCfg{});
+                     WaitCfg wait = WaitCfg{}, int64_t n_super = 0);
 
 // tpr: threads per pixel row of a 16 x 16 tile (2 or 4); 8 x 8 tiles use 4.
 // Adjoint: Gaussians with index >= n_active (a frozen pool appended after the

@@ -596,7 +596,7 @@ k_project_bwd(const float4* __restrict__ P, int64_t n, int64_t n_out, Dyn dyn, c
 }
 
 __global__ void k_view_table(const gs_camera* __restrict__ cams, int V, int tile, ViewInfo* vt,
-                             long long expect_tiles, DevStatus* status) {
+                             long long expect_tiles, long long expect_super, DevStatus* status) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     int64_t toff = 0, poff = 0, soff = 0;
     for (int v = 0; v < V; ++v) {
@@ -627,13 +627,14 @@ __global__ void k_view_table(const gs_camera* __restrict__ cams, int V, int tile
         if (vt[v].tx > 256 || vt[v].ty > 256) tot.rect32 = 0;
     vt[V] = tot;
     if (expect_tiles >= 0 && toff != expect_tiles) record_status(status, GS_ERR_ARG, toff);
+    if (expect_super >= 0 && soff != expect_super) record_status(status, GS_ERR_ARG, soff);
 }
 
 }  // namespace
 
 void launch_view_table(const gs_camera* d_cams, int V, int tile, ViewInfo* vt, long long expect_tiles,
-                       DevStatus* status, cudaStream_t st) {
-    k_view_table<<<1, 32, 0, st>>>(d_cams, V, tile, vt, expect_tiles, status);
+                       DevStatus* status, cudaStream_t st, long long expect_super) {
+    k_view_table<<<1, 32, 0, st>>>(d_cams, V, tile, vt, expect_tiles, expect_super, status);
 }
 
 void launch_project(const float* params, int64_t n, int sh_degree, const Dyn& dyn, const gs_camera* d_cams,

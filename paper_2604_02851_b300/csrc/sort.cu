@@ -39,6 +39,12 @@ constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 constexpr int kMinTileKeys = kThreads * 8;       // smallest onesweep tile (look-back sizing)
 constexpr int kMaxPasses = 4;
+// Digits of the widest pass: the super-tile sort takes a key of up to 9 bits
+// (at most 512 super-tiles) in one pass.  Histograms and digit offsets keep
+// kMaxR words per pass.
+constexpr int kWideBits = 9;
+constexpr int kWideItems = 12;  // keys per thread of a 9-bit pass (static shared memory below 48 KB)
+constexpr int kMaxR = 1 << kWideBits;
 __device__ __forceinline__ uint32_t lanemask_lt() {
     uint32_t m;
     asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
@@ -72,19 +78,27 @@ k_hist(const uint64_t* __restrict__ items, const uint32_t* d_count, int64_t cap,
         const int p = i / R, d = i % R;
         uint32_t s = 0;
         for (int ww = 0; ww < kWarps; ++ww) s += sh[ww][p][d];
-        if (s) atomicAdd(&hist[p * 256 + d], s);
+        if (s) atomicAdd(&hist[p * kMaxR + d], s);
     }
 }
 
-// Exclusive scan of each pass's histogram in place (one block).
+// Exclusive scan of each pass's histogram in place (one block of 256
+// threads, each owning PER consecutive digits).
 template <int BITS>
 __global__ void k_hist_scan(uint32_t* hist, int passes) {
     constexpr int R = 1 << BITS;
+    constexpr int PER = (R + 255) / 256;
     __shared__ uint32_t s_w[8];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int p = 0; p < passes; ++p) {  // 256 threads, one digit each: exclusive block scan
-        const uint32_t x = threadIdx.x < R ? hist[p * 256 + threadIdx.x] : 0u;
-        uint32_t incl = x;
+    for (int p = 0; p < passes; ++p) {
+        uint32_t x[PER], sum = 0;
+#pragma unroll
+        for (int i = 0; i < PER; ++i) {
+            const int d = threadIdx.x * PER + i;
+            x[i] = d < R ? hist[p * kMaxR + d] : 0u;
+            sum += x[i];
+        }
+        uint32_t incl = sum;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
@@ -92,9 +106,14 @@ __global__ void k_hist_scan(uint32_t* hist, int passes) {
         }
         if (lane == 31) s_w[warp] = incl;
         __syncthreads();
-        uint32_t off = 0;
-        for (int w = 0; w < warp; ++w) off += s_w[w];
-        if (threadIdx.x < R) hist[p * 256 + threadIdx.x] = off + incl - x;
+        uint32_t run = incl - sum;
+        for (int w = 0; w < warp; ++w) run += s_w[w];
+#pragma unroll
+        for (int i = 0; i < PER; ++i) {
+            const int d = threadIdx.x * PER + i;
+            if (d < R) hist[p * kMaxR + d] = run;
+            run += x[i];
+        }
         __syncthreads();
     }
 }
@@ -171,16 +190,22 @@ k_onesweep(const uint64_t* __restrict__ in, uint64_t* __restrict__ out, uint32_t
         }
         __syncthreads();
 
-        // ---- per digit: prefix over warps, tile count, publish
-        uint32_t tile_cnt = 0;
-        if (threadIdx.x < R) {
-            const int d = threadIdx.x;
-            uint32_t acc = 0;
-            for (int w = 0; w < kWarps; ++w) { const uint32_t c = s_whist[w][d]; s_whist[w][d] = acc; acc += c; }
-            tile_cnt = acc;
-            if (!withheld)
-                st_volatile(lookback + tile * R + d, (tile == 0 ? kFlagInc : kFlagAgg) | (unsigned long long)tile_cnt);
-            s_local[d] = tile_cnt;
+        // ---- per digit (thread t owns digits t, t + 256, ...): prefix over
+        //      warps, tile count, publish
+        constexpr int DPT = (R + kThreads - 1) / kThreads;
+        uint32_t tile_cnt[DPT];
+#pragma unroll
+        for (int k = 0; k < DPT; ++k) {
+            const int d = (int)threadIdx.x + k * kThreads;
+            tile_cnt[k] = 0;
+            if (d < R) {
+                uint32_t acc = 0;
+                for (int w = 0; w < kWarps; ++w) { const uint32_t c = s_whist[w][d]; s_whist[w][d] = acc; acc += c; }
+                tile_cnt[k] = acc;
+                if (!withheld)
+                    st_volatile(lookback + tile * R + d, (tile == 0 ? kFlagInc : kFlagAgg) | (unsigned long long)acc);
+                s_local[d] = acc;
+            }
         }
         __syncthreads();
         // tile-local digit starts: exclusive scan of the tile counts (warp 0)
@@ -207,13 +232,19 @@ k_onesweep(const uint64_t* __restrict__ in, uint64_t* __restrict__ out, uint32_t
                 run += loc[i];
             }
         }
-        // ---- look back over preceding tiles, one thread per digit
-        if (threadIdx.x < R) {
-            unsigned long long excl = 0;
-            if (withheld) s_abort = 1;
-            else if (!look_back(lookback + threadIdx.x, tile, R, tile_cnt, &excl, status, spin)) s_abort = 1;
-            s_gbase[threadIdx.x] = digit_off[threadIdx.x] + (uint32_t)excl;
+        // ---- look back over preceding tiles, per digit (after a wait that
+        //      ran out the thread's further digits are not waited for)
+        bool gave_up = withheld;
+#pragma unroll
+        for (int k = 0; k < DPT; ++k) {
+            const int d = (int)threadIdx.x + k * kThreads;
+            if (d < R) {
+                unsigned long long excl = 0;
+                if (!gave_up && !look_back(lookback + d, tile, R, tile_cnt[k], &excl, status, spin)) gave_up = true;
+                s_gbase[d] = digit_off[d] + (uint32_t)excl;
+            }
         }
+        if (gave_up) s_abort = 1;
         __syncthreads();
         // ---- stage in shared memory in digit order
 #pragma unroll
@@ -551,7 +582,7 @@ k_emit(const uint64_t* __restrict__ dsorted, int64_t total, int64_t n, const uin
     __syncthreads();
     for (int i = threadIdx.x; i < passes * R; i += kEmitThreads) {
         const uint32_t c = (&s_hist[0][0])[i];
-        if (c) atomicAdd(&hist[(i / R) * 256 + (i % R)], c);
+        if (c) atomicAdd(&hist[(i / R) * kMaxR + (i % R)], c);
     }
 }
 
@@ -956,7 +987,7 @@ void onesweep_passes(uint64_t* const buf[2], uint64_t* last_out, uint32_t* kout,
         const uint64_t* src = buf[p % 2];
         uint64_t* dst = last ? last_out : buf[(p + 1) % 2];
         k_onesweep<BITS, ITEMS><<<sm_count * 3, kThreads, 0, st>>>(
-            src, dst, last ? kout : nullptr, last ? vout : nullptr, d_count, cap, p * BITS, kmask, s.hist + p * 256,
+            src, dst, last ? kout : nullptr, last ? vout : nullptr, d_count, cap, p * BITS, kmask, s.hist + p * kMaxR,
             s.lookback + (int64_t)p * s.max_sort_tiles * R, s.counters + p, last ? ranges : nullptr, status,
             wait.spin, last ? wait.withhold : -1);
     }
@@ -972,7 +1003,7 @@ void emit_and_sort(const uint64_t* dsorted, int64_t items, const uint32_t* d_ite
                    void (*mark)(void* const*, int, cudaStream_t), void* const* events, int ev, WaitCfg wait) {
     const int passes = (key_bits + BITS - 1) / BITS;
     const int64_t nblk = (items + kEmitBlock - 1) / kEmitBlock;
-    cudaMemsetAsync(s.hist, 0, sizeof(uint32_t) * kMaxPasses * 256, st);
+    cudaMemsetAsync(s.hist, 0, sizeof(uint32_t) * kMaxPasses * kMaxR, st);
     cudaMemsetAsync(s.counters, 0, sizeof(uint32_t) * 8, st);
     cudaMemsetAsync(s.emit_lookback, 0, sizeof(unsigned long long) * (size_t)nblk, st);
     k_emit<BITS><<<(unsigned)nblk, kEmitThreads, 0, st>>>(dsorted, items, n, s.rects, vt, keys_cap, s.tkv[0],
@@ -998,16 +1029,17 @@ void emit_two_level(const uint64_t* dsorted, int64_t items, const uint32_t* d_it
                     uint32_t* sorted_vals, uint32_t* ranges, int64_t total_tiles, uint32_t* d_num_keys,
                     DevStatus* status, int sm_count, cudaStream_t st,
                     void (*mark)(void* const*, int, cudaStream_t), void* const* events, int ev,
-                    CoarseLists* coarse, WaitCfg wait) {
+                    CoarseLists* coarse, WaitCfg wait, int64_t n_super_exact) {
     wait.withhold = -1;  // later kernels read this sort's output
-    // the host knows the tile count only: super-tiles never outnumber tiles,
-    // so it bounds their count (the kernels read the exact one from vt[V])
+    // super-tiles never outnumber tiles: the tile count bounds the arrays
+    // indexed by super-tile (the kernels read the exact count from vt[V]); the
+    // key width comes from the exact count when the caller knows it
     const int64_t n_super = total_tiles;
     int bits = 1;
-    while ((1LL << bits) < n_super) ++bits;
+    while ((1LL << bits) < (n_super_exact > 0 ? n_super_exact : n_super)) ++bits;
     const int passes = (bits + BITS - 1) / BITS;
     const int64_t nblk = (items + kEmitBlock - 1) / kEmitBlock;
-    cudaMemsetAsync(s.hist, 0, sizeof(uint32_t) * kMaxPasses * 256, st);
+    cudaMemsetAsync(s.hist, 0, sizeof(uint32_t) * kMaxPasses * kMaxR, st);
     cudaMemsetAsync(s.counters, 0, sizeof(uint32_t) * 8, st);
     cudaMemsetAsync(s.emit_lookback, 0, sizeof(unsigned long long) * (size_t)nblk, st);
     cudaMemsetAsync(s.d_fine_total, 0, sizeof(unsigned long long), st);
@@ -1094,7 +1126,7 @@ void carve_sort_scratch(char* base, int V, int64_t n, int64_t keys_cap, int64_t 
     c.take<char>(bm_room);
     s->tkv[1] = c.take<uint64_t>(keys_cap);
     c.take<char>(bm_room);
-    s->hist = c.take<uint32_t>(kMaxPasses * 256);
+    s->hist = c.take<uint32_t>(kMaxPasses * kMaxR);
     s->counters = c.take<uint32_t>(8);
     s->max_sort_tiles = (std::max(items, keys_cap) + kMinTileKeys - 1) / kMinTileKeys + 1;
     s->lookback = c.take<unsigned long long>((size_t)kMaxPasses * s->max_sort_tiles * 256);
@@ -1119,7 +1151,7 @@ void launch_bin_sort(const float* proj, const ViewInfo* vt, int V, int64_t n, in
                      uint32_t* sorted_keys, uint32_t* sorted_vals, uint32_t* ranges,
                      uint32_t* d_num_keys, DevStatus* status, int sm_count, cudaStream_t st,
                      void (*mark)(void* const*, int, cudaStream_t), void* const* events, int first_event,
-                     bool compact, CoarseLists* coarse, WaitCfg wait) {
+                     bool compact, CoarseLists* coarse, WaitCfg wait, int64_t n_super) {
     if (coarse) *coarse = CoarseLists{};
     WaitCfg dwait = wait;
     dwait.withhold = -1;  // the depth sort's output feeds the emission
@@ -1137,7 +1169,7 @@ void launch_bin_sort(const float* proj, const ViewInfo* vt, int V, int64_t n, in
     // with compaction the kept items move to dkv[1] and the sort ends there
     const uint64_t* dsorted = s.dkv[0];
     const uint32_t* d_items = nullptr;
-    cudaMemsetAsync(s.hist, 0, sizeof(uint32_t) * kMaxPasses * 256, st);
+    cudaMemsetAsync(s.hist, 0, sizeof(uint32_t) * kMaxPasses * kMaxR, st);
     cudaMemsetAsync(s.counters, 0, sizeof(uint32_t) * 8, st);
     if (compact) {
         const int64_t nb = (items + kKeepBlock - 1) / kKeepBlock;
@@ -1163,6 +1195,15 @@ void launch_bin_sort(const float* proj, const ViewInfo* vt, int V, int64_t n, in
     //    into tiles (two-level), into the caller's arrays with ranges
     int bits = 1;
     while ((1LL << bits) < total_tiles) ++bits;
+    int sbits = 1;
+    while ((1LL << sbits) < (n_super > 0 ? n_super : total_tiles)) ++sbits;
+    if (binning != kBinDirect && bits <= kMaxCoarseKeyBits && sbits > sort_bits && sbits <= kWideBits) {
+        // a super-tile key of 9 bits: one wide pass instead of two
+        emit_two_level<kWideBits, kWideItems>(dsorted, items, d_items, n, pr, vt, V, keys_cap, s, sorted_keys,
+                                              sorted_vals, ranges, total_tiles, d_num_keys, status, sm_count, st,
+                                              mark, events, first_event + 1, coarse, wait, n_super);
+        return;
+    }
 #define GS_EMIT_SORT(B, I)                                                                                      \
     do {                                                                                                        \
         if (binning == kBinDirect || bits > kMaxCoarseKeyBits)                                                  \
@@ -1174,7 +1215,7 @@ void launch_bin_sort(const float* proj, const ViewInfo* vt, int V, int64_t n, in
             emit_two_level<B, I>(dsorted, items, d_items, n, pr, vt, V, keys_cap, s, sorted_keys, sorted_vals,  \
                                  ranges,                                                                        \
                                  total_tiles, d_num_keys, status, sm_count, st, mark, events, first_event + 1,  \
-                                 coarse, wait);                                                                 \
+                                 coarse, wait, n_super);                                                        \
     } while (0)
     const int it = sort_items == 8 ? 8 : (sort_items == 16 ? 16 : 12);
     switch (sort_bits * 100 + it) {

@@ -10,8 +10,9 @@ image and loss are bit-identical; the gradients differ only in the order of
 the float atomics, and so do the parameters (and the next step's image) by
 rounding.  Cases: one super-tile holding many chunks, ragged image edges, big
 splats spanning many super-tiles, both raster layouts, 8-pixel tiles, an
-opaque scene whose pixels stop early, and a tiny scene over many views (more
-chunks than keys_cap / 256).
+opaque scene whose pixels stop early, a tiny scene over many views (more
+chunks than keys_cap / 256), and 320 or 512 super-tiles, whose 9-bit key the
+fused step sorts in one wide pass (the direct binning sorts tile keys).
 """
 import numpy as np
 import pytest
@@ -32,6 +33,10 @@ CASES = {
     # a handful of Gaussians over many views: more chunks (one per non-empty
     # super-tile) than keys_cap / 256, the bitmaps still fit
     "tiny_many_views": (12, 0, 16, 256, 160, 1.0, 2.0, 16, 4, 2),
+    # 320 and 512 super-tiles (8-pixel tiles, 8 x 8 of them a super-tile):
+    # the fused step sorts the 9-bit super-tile key in one wide pass
+    "wide_key_320": (6_000, 0, 16, 320, 256, 0.3, 0.0, 8, 4, 4),
+    "wide_key_512": (6_000, 0, 16, 512, 256, 0.3, 0.0, 8, 4, 4),
 }
 
 
@@ -76,6 +81,10 @@ def test_train_step_chunk_lists_match_expanded_lists(name):
         # the super-tile's list spans many 256-item chunks
         K = int(np.count_nonzero(O.project(planes, sh, cams32(cams))[..., 14] > 0))
         assert K > 20 * 256
+    if name.startswith("wide_key"):
+        st = tile * 8
+        n_super = V * ((W + st - 1) // st) * ((H + st - 1) // st)
+        assert 256 < n_super <= 512 and n_super == int(name.split("_")[-1])
     if name == "tiny_many_views":
         # every non-empty super-tile takes a chunk: more than keys_cap / 256
         rect = O.project(planes, sh, cams32(cams))[..., 12:16].astype(np.int64)
