@@ -87,6 +87,7 @@ struct FusedPlan {
     float* grad2d;
     char* delta;
     uint8_t* fwd;
+    uint32_t* order;  // super-tiles in raster order
     size_t bytes;
 };
 
@@ -108,6 +109,7 @@ FusedPlan plan_fused(void* base, int V, int64_t n, int64_t keys_cap, int64_t tot
         p.grad2d = c.take<float>((size_t)V * n * kGradStride);
         p.delta = c.take<char>(delta_scratch_bytes(n));
         p.fwd = c.take<uint8_t>(n > 0 ? n : 1);
+        p.order = c.take<uint32_t>(total_tiles > 0 ? total_tiles : 1);  // super-tiles never outnumber tiles
     }
     p.bytes = c.off;
     return p;
@@ -571,7 +573,7 @@ gs_status_t gs_train_step_events(gs_ctx* ctx, const gs_camera* d_cams, const gs_
     CoarseLists cl;
     launch_bin_sort(p.proj, p.vt, V, n, cfg->keys_cap, tt, ctx->binning, ctx->sort_bits, ctx->sort_items, s, true, nullptr,
                     p.vals, p.ranges, p.n_keys, ctx->d_status, ctx->sm_count, st, ev ? mark : nullptr, ev, 2,
-                    cfg->precull != nullptr, &cl, spin_only(ctx), ns);
+                    cfg->precull != nullptr, &cl, spin_only(ctx), ns, p.order);
     mark(ev, 4, st);
     launch_render_fwd(p.proj, p.vt, V, n, B, ctx->raster_tpr, p.vals, p.ranges, b, io->image, p.T_final, p.n_contrib, tt,
                       st, &cl, kRecF4Compact);
@@ -641,7 +643,7 @@ gs_status_t gs_autotune(gs_ctx* ctx, const gs_scene* scene, const gs_camera* d_c
         CoarseLists cl;
         launch_bin_sort(p.proj, p.vt, V, n, keys_cap, tt, ctx->binning, ctx->sort_bits, ctx->sort_items, s, true,
                         nullptr, p.vals, p.ranges, p.n_keys, ctx->d_status, ctx->sm_count, st, nullptr, nullptr, 0,
-                        scene->precull != nullptr, &cl, spin_only(ctx), ns);
+                        scene->precull != nullptr, &cl, spin_only(ctx), ns, p.order);
         if (ev) cudaEventRecord(ev[0], st);
         launch_render_fwd(p.proj, p.vt, V, n, B, ctx->raster_tpr, p.vals, p.ranges, bg, image, p.T_final,
                           p.n_contrib, tt, st, &cl, kRecF4Compact);

@@ -312,6 +312,11 @@ struct CoarseLists {
     const uint32_t* chunk_first = nullptr;
     const uint32_t* d_n_chunks = nullptr;
     const uint32_t* bitmap = nullptr;
+    // super-tiles in the order the raster kernels take them (null: tile
+    // order); then their grid is n_super x 64 blocks, one per tile slot of a
+    // super-tile (slots outside the view exit)
+    const uint32_t* sorder = nullptr;
+    int64_t n_super = 0;
 };
 
 // coarse: when non-null and the two-level path is taken, the per-tile lists
@@ -320,6 +325,10 @@ struct CoarseLists {
 // n_super (> 0): the exact super-tile total, which the view table checks; it
 // sizes the super-tile key (one 9-bit pass instead of two 8-bit ones for up
 // to 512 super-tiles).  0: unknown, bounded by the tile count.
+// order (with n_super > 0 and chunk-bitmap lists; room for n_super words):
+// receives the super-tiles by decreasing list length (ties by index), the
+// order in which the raster kernels then take them, so that the longest
+// lists start first instead of ending the launch (coarse->sorder).
 void launch_bin_sort(const float* proj, const ViewInfo* vt, int V, int64_t n, int64_t keys_cap,
                      int64_t total_tiles, int binning, int sort_bits, int sort_items, const SortScratch& s,
                      bool depth_ready,
@@ -327,7 +336,7 @@ void launch_bin_sort(const float* proj, const ViewInfo* vt, int V, int64_t n, in
                      uint32_t* d_num_keys, DevStatus* status, int sm_count, cudaStream_t st,
                      void (*mark)(void* const*, int, cudaStream_t) = nullptr, void* const* events = nullptr,
                      int first_event = 0, bool compact = false, CoarseLists* coarse = nullptr,
-                     WaitCfg wait = WaitCfg{}, int64_t n_super = 0);
+                     WaitCfg wait = WaitCfg{}, int64_t n_super = 0, uint32_t* order = nullptr);
 
 // tpr: threads per pixel row of a 16 x 16 tile (2 or 4); 8 x 8 tiles use 4.
 // Adjoint: Gaussians with index >= n_active (a frozen pool appended after the

@@ -40,6 +40,35 @@ __device__ __forceinline__ int find_view(const ViewInfo* __restrict__ vt, int V,
     return lo;
 }
 
+// The tile a block composites.  With a super-tile order (chunk-bitmap lists)
+// block b takes slot b % 64 of the (b / 64)-th super-tile of the order, and
+// returns false for slots outside the view; else block b takes tile b.
+__device__ __forceinline__ bool block_tile(const ViewInfo* __restrict__ vt, int V, const CoarseLists& cl,
+                                           int64_t& gt, int& v) {
+    if (cl.sorder) {
+        const int64_t sidx = cl.sorder[blockIdx.x >> (2 * kSuperShift)];
+        if (sidx >= vt[V].stile_off) return false;
+        int lo = 0, hi = V;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (vt[mid].stile_off <= sidx) lo = mid; else hi = mid;
+        }
+        v = lo;
+        const ViewInfo& vi = vt[v];
+        const int ls = (int)(sidx - vi.stile_off);
+        const int k = (int)(blockIdx.x & (kSuper * kSuper - 1));
+        const int tx = (ls % vi.stx) * kSuper + (k & (kSuper - 1));
+        const int ty = (ls / vi.stx) * kSuper + (k >> kSuperShift);
+        if (tx >= vi.tx || ty >= vi.ty) return false;
+        gt = vi.tile_off + (int64_t)ty * vi.tx + tx;
+        return true;
+    }
+    gt = blockIdx.x;
+    if (gt >= vt[V].tile_off) return false;
+    v = find_view(vt, V, gt);
+    return true;
+}
+
 // Thread layout: a B x B tile is covered by B rows of TPR threads; each
 // thread owns a strip of PX = B / TPR adjacent pixels of one row, so the
 // shared-memory reads of a fragment and the warp reductions of its gradient
@@ -190,9 +219,9 @@ k_render_fwd(const float4* __restrict__ proj, const ViewInfo* __restrict__ vt, i
     __shared__ float4 s_c[BATCH];      // r, g, b
     __shared__ uint32_t s_pos[BATCH];  // position in the tile's list
     __shared__ int s_wcnt[2 * NW];
-    const int64_t gt = blockIdx.x;
-    if (gt >= vt[V].tile_off) return;
-    const int v = find_view(vt, V, gt);
+    int64_t gt;
+    int v;
+    if (!block_tile(vt, V, cl, gt, v)) return;
     const ViewInfo vi = vt[v];
     const int lt = (int)(gt - vi.tile_off);
     const int row = (int)threadIdx.x / TPR;
@@ -438,9 +467,9 @@ k_raster_bwd(const float4* __restrict__ proj, const ViewInfo* __restrict__ vt, i
     __shared__ int s_wcnt[NT / 32];
     __shared__ uint32_t s_cand[COARSE ? kChunkItems : 1];
     __shared__ int s_ctot[NT / 32];
-    const int64_t gt = blockIdx.x;
-    if (gt >= vt[V].tile_off) return;
-    const int v = find_view(vt, V, gt);
+    int64_t gt;
+    int v;
+    if (!block_tile(vt, V, cl, gt, v)) return;
     const ViewInfo vi = vt[v];
     const int lt = (int)(gt - vi.tile_off);
     const int row = (int)threadIdx.x / TPR;
@@ -684,8 +713,8 @@ void launch_render_fwd(const float* proj, const ViewInfo* vt, int V, int64_t n, 
     if (total_tiles <= 0) return;
     const float4* p = reinterpret_cast<const float4*>(proj);
     const uint2* r = reinterpret_cast<const uint2*>(ranges);
-    const unsigned nb = (unsigned)total_tiles;
     const CoarseLists cl = coarse ? *coarse : CoarseLists{};
+    const unsigned nb = (unsigned)(cl.sorder ? cl.n_super << (2 * kSuperShift) : total_tiles);
 #define GS_FWD(BB, TT, NTH)                                                                                        \
     (cl.citems ? k_render_fwd<BB, TT, true><<<nb, NTH, 0, st>>>(p, vt, V, n, vals, r, cl, bg, image, T_final,      \
                                                                 n_contrib, rec4)                                   \
@@ -710,8 +739,8 @@ void launch_raster_bwd(const float* proj, const ViewInfo* vt, int V, int64_t n, 
     if (total_tiles <= 0) return;
     const float4* p = reinterpret_cast<const float4*>(proj);
     const uint2* r = reinterpret_cast<const uint2*>(ranges);
-    const unsigned nb = (unsigned)total_tiles;
     const CoarseLists cl = coarse ? *coarse : CoarseLists{};
+    const unsigned nb = (unsigned)(cl.sorder ? cl.n_super << (2 * kSuperShift) : total_tiles);
 #define GS_BWD(BB, TT, NTH)                                                                                        \
     (cl.citems ? k_raster_bwd<BB, TT, true><<<nb, NTH, 0, st>>>(p, vt, V, n, vals, r, cl, bg, T_final, n_contrib,  \
                                                                 dimage, grad2d, n_active, rec4)                    \

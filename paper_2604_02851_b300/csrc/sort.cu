@@ -616,12 +616,36 @@ __device__ __forceinline__ int find_super_view(const ViewInfo* __restrict__ vt, 
     return lo;
 }
 
+constexpr int kOrderMax = 2048;  // super-tiles the raster order ranks (above: identity order)
+
 // Chunk table (one block): chunk_first[s] = first chunk of super-tile s,
-// *d_n_chunks = total (clamped); k_chunk_owner then fills chunk_s.
+// *d_n_chunks = total (clamped); k_chunk_owner then fills chunk_s.  With
+// `order` (n_order words): the raster order, super-tiles by decreasing list
+// length, ties by index (each one's rank by counting); the identity order
+// when the view table's count is not n_order or exceeds kOrderMax.
 __global__ void __launch_bounds__(1024)
 k_fine_chunks(const uint2* __restrict__ cranges, const ViewInfo* __restrict__ vt, int V, int64_t ns_bound,
-              uint32_t* __restrict__ chunk_first, uint32_t* d_n_chunks, int64_t max_chunks, DevStatus* status) {
+              uint32_t* __restrict__ chunk_first, uint32_t* d_n_chunks, int64_t max_chunks, DevStatus* status,
+              uint32_t* __restrict__ order, int n_order) {
     __shared__ uint32_t s_part[1024];
+    __shared__ unsigned long long s_key[kOrderMax];
+    if (order) {
+        if (n_order > kOrderMax || vt[V].stile_off != (int64_t)n_order) {
+            for (int i = threadIdx.x; i < n_order; i += blockDim.x) order[i] = (uint32_t)i;
+        } else {
+            for (int i = threadIdx.x; i < n_order; i += blockDim.x) {
+                const uint2 r = cranges[i];
+                s_key[i] = ((unsigned long long)(~(r.y - r.x)) << 32) | (uint32_t)i;
+            }
+            __syncthreads();
+            for (int i = threadIdx.x; i < n_order; i += blockDim.x) {
+                const unsigned long long k = s_key[i];
+                int rank = 0;
+                for (int j = 0; j < n_order; ++j) rank += s_key[j] < k;
+                order[rank] = (uint32_t)i;
+            }
+        }
+    }
     const int64_t ns = vt[V].stile_off < ns_bound ? vt[V].stile_off : ns_bound;
     const int64_t per = (ns + blockDim.x - 1) / blockDim.x;
     const int64_t a = (int64_t)threadIdx.x * per;
@@ -1029,7 +1053,7 @@ void emit_two_level(const uint64_t* dsorted, int64_t items, const uint32_t* d_it
                     uint32_t* sorted_vals, uint32_t* ranges, int64_t total_tiles, uint32_t* d_num_keys,
                     DevStatus* status, int sm_count, cudaStream_t st,
                     void (*mark)(void* const*, int, cudaStream_t), void* const* events, int ev,
-                    CoarseLists* coarse, WaitCfg wait, int64_t n_super_exact) {
+                    CoarseLists* coarse, WaitCfg wait, int64_t n_super_exact, uint32_t* order) {
     wait.withhold = -1;  // later kernels read this sort's output
     // super-tiles never outnumber tiles: the tile count bounds the arrays
     // indexed by super-tile (the kernels read the exact count from vt[V]); the
@@ -1066,8 +1090,10 @@ void emit_two_level(const uint64_t* dsorted, int64_t items, const uint32_t* d_it
         // chunk-bitmap lists: the bitmaps go to the ping-pong buffer the last
         // pass read and the room after it (2 KB for each of max_chunks)
         uint32_t* bitmap = reinterpret_cast<uint32_t*>(buf[1 - passes % 2]);
+        const bool ordered = order && n_super_exact > 0;
         k_fine_chunks<<<1, 1024, 0, st>>>(s.cranges, vt, V, n_super, s.chunk_first, s.d_n_chunks,
-                                          s.max_chunks, status);
+                                          s.max_chunks, status, ordered ? order : nullptr,
+                                          ordered ? (int)n_super_exact : 0);
         k_chunk_owner<<<(unsigned)((n_super + 7) / 8), 256, 0, st>>>(s.chunk_first, vt, V, n_super, s.chunk_s,
                                                                    s.max_chunks);
         k_fine_mask<<<fgrid, kFineThreads, 0, st>>>(citems, s.cranges, s.chunk_first, s.chunk_s, s.d_n_chunks, vt,
@@ -1078,11 +1104,15 @@ void emit_two_level(const uint64_t* dsorted, int64_t items, const uint32_t* d_it
         coarse->chunk_first = s.chunk_first;
         coarse->d_n_chunks = s.d_n_chunks;
         coarse->bitmap = bitmap;
+        if (ordered) {
+            coarse->sorder = order;
+            coarse->n_super = n_super_exact;
+        }
         return;
     }
     // fine expansion
     k_fine_chunks<<<1, 1024, 0, st>>>(s.cranges, vt, V, n_super, s.chunk_first, s.d_n_chunks,
-                                      s.max_chunks, status);
+                                      s.max_chunks, status, nullptr, 0);
     k_chunk_owner<<<(unsigned)((n_super + 7) / 8), 256, 0, st>>>(s.chunk_first, vt, V, n_super, s.chunk_s,
                                                                s.max_chunks);
     k_fine_count<<<fgrid, kFineThreads, 0, st>>>(citems, s.cranges, s.chunk_first, s.chunk_s, s.d_n_chunks, vt, V,
@@ -1151,7 +1181,7 @@ void launch_bin_sort(const float* proj, const ViewInfo* vt, int V, int64_t n, in
                      uint32_t* sorted_keys, uint32_t* sorted_vals, uint32_t* ranges,
                      uint32_t* d_num_keys, DevStatus* status, int sm_count, cudaStream_t st,
                      void (*mark)(void* const*, int, cudaStream_t), void* const* events, int first_event,
-                     bool compact, CoarseLists* coarse, WaitCfg wait, int64_t n_super) {
+                     bool compact, CoarseLists* coarse, WaitCfg wait, int64_t n_super, uint32_t* order) {
     if (coarse) *coarse = CoarseLists{};
     WaitCfg dwait = wait;
     dwait.withhold = -1;  // the depth sort's output feeds the emission
@@ -1201,7 +1231,7 @@ void launch_bin_sort(const float* proj, const ViewInfo* vt, int V, int64_t n, in
         // a super-tile key of 9 bits: one wide pass instead of two
         emit_two_level<kWideBits, kWideItems>(dsorted, items, d_items, n, pr, vt, V, keys_cap, s, sorted_keys,
                                               sorted_vals, ranges, total_tiles, d_num_keys, status, sm_count, st,
-                                              mark, events, first_event + 1, coarse, wait, n_super);
+                                              mark, events, first_event + 1, coarse, wait, n_super, order);
         return;
     }
 #define GS_EMIT_SORT(B, I)                                                                                      \
@@ -1215,7 +1245,7 @@ void launch_bin_sort(const float* proj, const ViewInfo* vt, int V, int64_t n, in
             emit_two_level<B, I>(dsorted, items, d_items, n, pr, vt, V, keys_cap, s, sorted_keys, sorted_vals,  \
                                  ranges,                                                                        \
                                  total_tiles, d_num_keys, status, sm_count, st, mark, events, first_event + 1,  \
-                                 coarse, wait, n_super);                                                        \
+                                 coarse, wait, n_super, order);                                                 \
     } while (0)
     const int it = sort_items == 8 ? 8 : (sort_items == 16 ? 16 : 12);
     switch (sort_bits * 100 + it) {
