@@ -68,10 +68,22 @@ k_hist(const uint64_t* __restrict__ items, const uint32_t* d_count, int64_t cap,
     __syncthreads();
     const int64_t count = clamp_count(d_count, cap);
     const int w = threadIdx.x / 32;
-    for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < count;
-         i += (int64_t)gridDim.x * kThreads) {
-        const uint32_t k = (uint32_t)(items[i] >> 32);
-        for (int p = 0; p < passes; ++p) atomicAdd(&sh[w][p][(k >> (p * BITS)) & (R - 1)], 1u);
+    // eight loads of a thread in flight per round: the pass is bound by
+    // memory-level parallelism, not by the shared-memory atomics
+    constexpr int U = 8;
+    const int64_t stride = (int64_t)gridDim.x * kThreads * U;
+    for (int64_t i0 = (int64_t)blockIdx.x * kThreads * U + threadIdx.x; i0 < count; i0 += stride) {
+        uint32_t k[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t i = i0 + u * kThreads;
+            k[u] = i < count ? (uint32_t)(items[i] >> 32) : 0u;
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (i0 + u * kThreads >= count) break;
+            for (int p = 0; p < passes; ++p) atomicAdd(&sh[w][p][(k[u] >> (p * BITS)) & (R - 1)], 1u);
+        }
     }
     __syncthreads();
     for (int i = threadIdx.x; i < passes * R; i += kThreads) {
