@@ -278,7 +278,7 @@ struct SortScratch {
     // two-level binning (super-tile lists, then per-tile lists)
     uint2* cranges;            // [total_tiles] bound on super-tiles: coarse [start, end)
     uint32_t* chunk_first;     // [total_tiles + 1] first chunk of each super-tile
-    uint32_t* chunk_s;         // [max_chunks] super-tile of each chunk
+    uint4* chunk_meta;         // [max_chunks] per chunk: first and end coarse entry, super-tile, view
     uint32_t* chunk_off;       // [max_chunks][64] per-tile counts, then offsets
     uint32_t* tile_count;      // [total_tiles]
     uint32_t* d_count_coarse;  // coarse entries stored

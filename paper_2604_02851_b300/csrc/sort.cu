@@ -631,7 +631,7 @@ __device__ __forceinline__ int find_super_view(const ViewInfo* __restrict__ vt, 
 constexpr int kOrderMax = 2048;  // super-tiles the raster order ranks (above: identity order)
 
 // Chunk table (one block): chunk_first[s] = first chunk of super-tile s,
-// *d_n_chunks = total (clamped); k_chunk_owner then fills chunk_s.  With
+// *d_n_chunks = total (clamped); k_chunk_owner then fills chunk_meta.  With
 // `order` (n_order words): the raster order, super-tiles by decreasing list
 // length, ties by index (each one's rank by counting); the identity order
 // when the view table's count is not n_order or exceeds kOrderMax.
@@ -692,17 +692,25 @@ k_fine_chunks(const uint2* __restrict__ cranges, const ViewInfo* __restrict__ vt
     }
 }
 
-// chunk_s[c] := super-tile of chunk c, one warp per super-tile (coalesced
-// runs; chunks past the table are dropped, as k_fine_chunks reports).
+// chunk_meta[c] := (first coarse entry, end entry, super-tile, view) of
+// chunk c, one warp per super-tile (coalesced runs; chunks past the table
+// are dropped, as k_fine_chunks reports), so that the passes over chunks
+// find a chunk's geometry with one load.
 __global__ void __launch_bounds__(256)
-k_chunk_owner(const uint32_t* __restrict__ chunk_first, const ViewInfo* __restrict__ vt, int V, int64_t ns_bound,
-              uint32_t* __restrict__ chunk_s, int64_t max_chunks) {
+k_chunk_owner(const uint32_t* __restrict__ chunk_first, const uint2* __restrict__ cranges,
+              const ViewInfo* __restrict__ vt, int V, int64_t ns_bound, uint4* __restrict__ chunk_meta,
+              int64_t max_chunks) {
     const int64_t ns = vt[V].stile_off < ns_bound ? vt[V].stile_off : ns_bound;
     const int64_t s = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (s >= ns) return;
     const int64_t c0 = chunk_first[s];
     const int64_t c1 = min((int64_t)chunk_first[s + 1], max_chunks);
-    for (int64_t c = c0 + (threadIdx.x & 31); c < c1; c += 32) chunk_s[c] = (uint32_t)s;
+    const uint2 cr = cranges[s];
+    const uint32_t v = (uint32_t)find_super_view(vt, V, s);
+    for (int64_t c = c0 + (threadIdx.x & 31); c < c1; c += 32) {
+        const uint32_t a = cr.x + (uint32_t)(c - c0) * (uint32_t)kFineChunk;
+        chunk_meta[c] = make_uint4(a, min(cr.y, a + (uint32_t)kFineChunk), (uint32_t)s, v);
+    }
 }
 
 // 32 x 32 bit-matrix transpose across a warp: on return bit j of lane k's
@@ -728,16 +736,14 @@ struct FineChunk {
     uint64_t valid;         // tiles of the super-tile inside the view
 };
 
-__device__ __forceinline__ FineChunk fine_chunk(uint32_t c, const uint2* __restrict__ cranges,
-                                                const uint32_t* __restrict__ chunk_first,
-                                                const uint32_t* __restrict__ chunk_s, const ViewInfo* __restrict__ vt,
-                                                int V, int64_t total_tiles, int lane) {
+__device__ __forceinline__ FineChunk fine_chunk(uint32_t c, const uint4* __restrict__ chunk_meta,
+                                                const ViewInfo* __restrict__ vt, int64_t total_tiles, int lane) {
     FineChunk f;
-    const uint32_t s = chunk_s[c];
-    const uint2 cr = cranges[s];
-    f.a = cr.x + (c - chunk_first[s]) * (uint32_t)kFineChunk;
-    f.e = min(cr.y, f.a + (uint32_t)kFineChunk);
-    f.v = find_super_view(vt, V, s);
+    const uint4 m = chunk_meta[c];
+    f.a = m.x;
+    f.e = m.y;
+    const uint32_t s = m.z;
+    f.v = (int)m.w;
     const ViewInfo vi = vt[f.v];
     const int ls = (int)(s - vi.stile_off);
     f.ox = (ls % vi.stx) << kSuperShift;
@@ -782,14 +788,14 @@ __device__ __forceinline__ void fine_group(const FineChunk& f, uint32_t grp, con
 // tile k of its super-tile.
 __global__ void __launch_bounds__(kFineThreads)
 k_fine_count(const uint64_t* __restrict__ citems, const uint2* __restrict__ cranges,
-             const uint32_t* __restrict__ chunk_first, const uint32_t* __restrict__ chunk_s,
+             const uint32_t* __restrict__ chunk_first, const uint4* __restrict__ chunk_meta,
              const uint32_t* __restrict__ d_n_chunks, const ViewInfo* __restrict__ vt, int V,
              int64_t total_tiles, uint32_t* __restrict__ chunk_off) {
     const int lane = threadIdx.x & 31;
     const uint32_t nchunks = *d_n_chunks;
     const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
     for (uint32_t c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < nchunks; c += nw) {
-        const FineChunk f = fine_chunk(c, cranges, chunk_first, chunk_s, vt, V, total_tiles, lane);
+        const FineChunk f = fine_chunk(c, chunk_meta, vt, total_tiles, lane);
         uint32_t n0 = 0, n1 = 0;
         for (uint32_t grp = 0; f.a + grp * 32u < f.e; ++grp) {
             uint32_t gval, c0, c1;
@@ -806,14 +812,14 @@ k_fine_count(const uint64_t* __restrict__ citems, const uint2* __restrict__ cran
 // chunk's groups, stored as bitmap[c][k][group] (two 32-byte rows a lane).
 __global__ void __launch_bounds__(kFineThreads)
 k_fine_mask(const uint64_t* __restrict__ citems, const uint2* __restrict__ cranges,
-            const uint32_t* __restrict__ chunk_first, const uint32_t* __restrict__ chunk_s,
+            const uint32_t* __restrict__ chunk_first, const uint4* __restrict__ chunk_meta,
             const uint32_t* __restrict__ d_n_chunks, const ViewInfo* __restrict__ vt, int V,
             int64_t total_tiles, uint32_t* __restrict__ bitmap) {
     const int lane = threadIdx.x & 31;
     const uint32_t nchunks = *d_n_chunks;
     const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
     for (uint32_t c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < nchunks; c += nw) {
-        const FineChunk f = fine_chunk(c, cranges, chunk_first, chunk_s, vt, V, total_tiles, lane);
+        const FineChunk f = fine_chunk(c, chunk_meta, vt, total_tiles, lane);
         // the chunk's 8 items of this lane requested together, then decoded
         uint32_t rect[8];
 #pragma unroll
@@ -851,7 +857,7 @@ static_assert(kFineWarps == kFineGroups, "one warp per group of the chunk");
 template <bool KOUT>
 __global__ void __launch_bounds__(kFineThreads)
 k_fine_write(const uint64_t* __restrict__ citems, const uint2* __restrict__ cranges,
-             const uint32_t* __restrict__ chunk_first, const uint32_t* __restrict__ chunk_s,
+             const uint32_t* __restrict__ chunk_first, const uint4* __restrict__ chunk_meta,
              const uint32_t* __restrict__ d_n_chunks, const ViewInfo* __restrict__ vt, int V,
              int64_t total_tiles, const uint32_t* __restrict__ chunk_off,
              const uint2* __restrict__ ranges, int64_t cap, uint32_t* __restrict__ vout,
@@ -865,7 +871,7 @@ k_fine_write(const uint64_t* __restrict__ citems, const uint2* __restrict__ cran
     const uint32_t nchunks = *d_n_chunks;
     const uint32_t cap32 = cap < 0xFFFFFFFFll ? (uint32_t)cap : 0xFFFFFFFFu;  // keys_cap < 2^32
     for (uint32_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
-        const FineChunk f = fine_chunk(c, cranges, chunk_first, chunk_s, vt, V, total_tiles, lane);
+        const FineChunk f = fine_chunk(c, chunk_meta, vt, total_tiles, lane);
         if (warp == 0) {
             s_base[lane] = f.in0 ? ranges[f.t0].x + chunk_off[(size_t)c * 64 + lane] : 0u;
             s_base[lane + 32] = f.in1 ? ranges[f.t1].x + chunk_off[(size_t)c * 64 + 32 + lane] : 0u;
@@ -1106,9 +1112,9 @@ void emit_two_level(const uint64_t* dsorted, int64_t items, const uint32_t* d_it
         k_fine_chunks<<<1, 1024, 0, st>>>(s.cranges, vt, V, n_super, s.chunk_first, s.d_n_chunks,
                                           s.max_chunks, status, ordered ? order : nullptr,
                                           ordered ? (int)n_super_exact : 0);
-        k_chunk_owner<<<(unsigned)((n_super + 7) / 8), 256, 0, st>>>(s.chunk_first, vt, V, n_super, s.chunk_s,
-                                                                   s.max_chunks);
-        k_fine_mask<<<fgrid, kFineThreads, 0, st>>>(citems, s.cranges, s.chunk_first, s.chunk_s, s.d_n_chunks, vt,
+        k_chunk_owner<<<(unsigned)((n_super + 7) / 8), 256, 0, st>>>(s.chunk_first, s.cranges, vt, V, n_super,
+                                                                   s.chunk_meta, s.max_chunks);
+        k_fine_mask<<<fgrid, kFineThreads, 0, st>>>(citems, s.cranges, s.chunk_first, s.chunk_meta, s.d_n_chunks, vt,
                                                     V, total_tiles, bitmap);
         coarse->citems = citems;
         coarse->cvals = sorted_vals;
@@ -1125,9 +1131,9 @@ void emit_two_level(const uint64_t* dsorted, int64_t items, const uint32_t* d_it
     // fine expansion
     k_fine_chunks<<<1, 1024, 0, st>>>(s.cranges, vt, V, n_super, s.chunk_first, s.d_n_chunks,
                                       s.max_chunks, status, nullptr, 0);
-    k_chunk_owner<<<(unsigned)((n_super + 7) / 8), 256, 0, st>>>(s.chunk_first, vt, V, n_super, s.chunk_s,
-                                                               s.max_chunks);
-    k_fine_count<<<fgrid, kFineThreads, 0, st>>>(citems, s.cranges, s.chunk_first, s.chunk_s, s.d_n_chunks, vt, V,
+    k_chunk_owner<<<(unsigned)((n_super + 7) / 8), 256, 0, st>>>(s.chunk_first, s.cranges, vt, V, n_super,
+                                                               s.chunk_meta, s.max_chunks);
+    k_fine_count<<<fgrid, kFineThreads, 0, st>>>(citems, s.cranges, s.chunk_first, s.chunk_meta, s.d_n_chunks, vt, V,
                                                  total_tiles, s.chunk_off);
     k_fine_prefix<<<(unsigned)((n_super * 64 + 255) / 256), 256, 0, st>>>(s.chunk_first, s.d_n_chunks, vt, V,
                                                                          total_tiles, s.chunk_off, s.tile_count);
@@ -1136,11 +1142,11 @@ void emit_two_level(const uint64_t* dsorted, int64_t items, const uint32_t* d_it
     // resident (the staging buffers limit residency below 8 blocks an SM)
     if (sorted_keys)
         k_fine_write<true><<<fine_write_grid<true>(sm_count), kFineThreads, 0, st>>>(
-            citems, s.cranges, s.chunk_first, s.chunk_s, s.d_n_chunks, vt, V, total_tiles, s.chunk_off,
+            citems, s.cranges, s.chunk_first, s.chunk_meta, s.d_n_chunks, vt, V, total_tiles, s.chunk_off,
             reinterpret_cast<const uint2*>(ranges), keys_cap, sorted_vals, sorted_keys);
     else
         k_fine_write<false><<<fine_write_grid<false>(sm_count), kFineThreads, 0, st>>>(
-            citems, s.cranges, s.chunk_first, s.chunk_s, s.d_n_chunks, vt, V, total_tiles, s.chunk_off,
+            citems, s.cranges, s.chunk_first, s.chunk_meta, s.d_n_chunks, vt, V, total_tiles, s.chunk_off,
             reinterpret_cast<const uint2*>(ranges), keys_cap, sorted_vals, nullptr);
 }
 
@@ -1178,7 +1184,7 @@ void carve_sort_scratch(char* base, int V, int64_t n, int64_t keys_cap, int64_t 
     s->max_chunks = keys_cap / kFineChunk + ns + 1;
     s->cranges = c.take<uint2>(ns);
     s->chunk_first = c.take<uint32_t>(ns + 1);
-    s->chunk_s = c.take<uint32_t>(s->max_chunks);
+    s->chunk_meta = c.take<uint4>(s->max_chunks);
     s->chunk_off = c.take<uint32_t>((size_t)s->max_chunks * 64);
     s->tile_count = c.take<uint32_t>(ns);
     s->d_count_coarse = c.take<uint32_t>(1);
