@@ -421,10 +421,13 @@ __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t x, int lane) {
 
 // Item index within a block: warp w, round r, lane l -> w*128 + r*32 + l, so
 // the 32 items of one (warp, round) are consecutive and their outputs form
-// one contiguous range.
-// Compiled for 8 blocks an SM (32 registers, some spills): the kernel waits
-// on its gathers and barriers, and more resident blocks hide that better
-// than fewer at 64 registers (0.264 -> 0.231 ms; 5 and 6 blocks in between).
+// one contiguous range.  Each item's state (Gaussian, view, tile rectangle
+// and the reciprocal of its key rectangle's width) waits in shared memory
+// between the count and the expansion, where every output reads its owner's
+// state from there; in registers the four rounds' state spilled to memory at
+// the 32 registers that 8 blocks an SM allow.
+// Compiled for 8 blocks an SM: the kernel waits on its gathers and barriers,
+// and more resident blocks hide that better than fewer at 64 registers.
 template <int BITS>
 __global__ void __launch_bounds__(kEmitThreads, 8)
 k_emit(const uint64_t* __restrict__ dsorted, int64_t total, int64_t n, const uint2* __restrict__ rects,
@@ -433,14 +436,17 @@ k_emit(const uint64_t* __restrict__ dsorted, int64_t total, int64_t n, const uin
        int passes, uint32_t* __restrict__ hist, int sshift, unsigned long long* fine_total, uint32_t key_bound,
        const uint32_t* d_total, DevStatus* status, int V, long long spin) {
     constexpr int R = 1 << BITS;
-    __shared__ uint32_t s_hist[kMaxPasses][R];
+    constexpr int HP = BITS > 8 ? 1 : kMaxPasses;  // a wide digit is a single pass
+    __shared__ uint32_t s_hist[HP][R];
+    __shared__ uint4 s_item[kEmitBlock];   // Gaussian, view, tile rectangle lo, hi
+    __shared__ float s_rw[kEmitBlock];     // 1 / width of the key rectangle
     __shared__ int s_mark[kEmitWarps][32];
     __shared__ uint32_t s_wtot[kEmitWarps];
     __shared__ uint32_t s_blk;
     __shared__ unsigned long long s_excl;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const bool rect32 = vt[V].rect32 != 0;
-    for (int i = threadIdx.x; i < kMaxPasses * R; i += kEmitThreads) (&s_hist[0][0])[i] = 0;
+    for (int i = threadIdx.x; i < HP * R; i += kEmitThreads) (&s_hist[0][0])[i] = 0;
     if (threadIdx.x == 0) s_blk = atomicAdd(block_counter, 1u);
     __syncthreads();
     const int64_t b = s_blk;
@@ -449,15 +455,31 @@ k_emit(const uint64_t* __restrict__ dsorted, int64_t total, int64_t n, const uin
     // still covers `total`; blocks past them publish empty counts)
     if (d_total && (int64_t)*d_total < total) total = (int64_t)*d_total;
 
-    uint32_t cnt[kEmitRounds], lo[kEmitRounds], hi[kEmitRounds], gi[kEmitRounds], kb[kEmitRounds],
-        tx[kEmitRounds], incl[kEmitRounds], rtot[kEmitRounds], flo[kEmitRounds], fhi[kEmitRounds];
+    // the key rectangle of an item (the super-tile rectangle covering its
+    // tile rectangle with two-level binning) and its entry count
+    auto key_rect = [&](uint32_t flo, uint32_t fhi, uint32_t& lo, uint32_t& hi) -> uint32_t {
+        const uint32_t rw = (fhi & 0xFFFFu) - (flo & 0xFFFFu), rh = (fhi >> 16) - (flo >> 16);
+        lo = flo;
+        hi = fhi;
+        if (!sshift || rw * rh == 0) return rw * rh;
+        const uint32_t sx0 = (flo & 0xFFFFu) >> sshift, sy0 = (flo >> 16) >> sshift;
+        const uint32_t sx1 = (((fhi & 0xFFFFu) - 1u) >> sshift) + 1u;
+        const uint32_t sy1 = (((fhi >> 16) - 1u) >> sshift) + 1u;
+        lo = sx0 | (sy0 << 16);
+        hi = sx1 | (sy1 << 16);
+        return (sx1 - sx0) * (sy1 - sy0);
+    };
+
+    uint32_t incl[kEmitRounds];
     uint32_t wtot = 0;
     unsigned long long fine = 0;
 #pragma unroll
     for (int r = 0; r < kEmitRounds; ++r) {
-        const int64_t idx = b * kEmitBlock + warp * (32 * kEmitRounds) + r * 32 + lane;
-        cnt[r] = lo[r] = hi[r] = gi[r] = kb[r] = flo[r] = fhi[r] = 0;
-        tx[r] = 1;
+        const int slot = warp * (32 * kEmitRounds) + r * 32 + lane;
+        const int64_t idx = b * kEmitBlock + slot;
+        uint4 it = make_uint4(0u, 0u, 0u, 0u);
+        uint32_t cnt = 0;
+        float rw = 0.f;
         if (idx < total) {
             const uint32_t rr = (uint32_t)dsorted[idx];
             // the record's tile rectangle, left in L2 by the projection (its
@@ -465,33 +487,18 @@ k_emit(const uint64_t* __restrict__ dsorted, int64_t total, int64_t n, const uin
             const uint2 rc = rect32 ? rect32_unpack(ld_hint(reinterpret_cast<const uint32_t*>(rects) + rr,
                                                             l2_policy_evict_first()))
                                     : ld_hint(rects + rr, l2_policy_evict_first());
-            const uint32_t rw = (rc.y & 0xFFFFu) - (rc.x & 0xFFFFu), rh = (rc.y >> 16) - (rc.x >> 16);
-            const uint4 p3 = make_uint4(rc.x, rc.y, rw * rh, 0u);
             const uint32_t v = (uint32_t)(rr / (uint64_t)n);
-            cnt[r] = p3.z;
-            lo[r] = p3.x;
-            hi[r] = p3.y;
-            gi[r] = rr - v * (uint32_t)n;
-            kb[r] = (uint32_t)vt[v].tile_off;
-            tx[r] = (uint32_t)vt[v].tx;
-            fine += p3.z;
-            flo[r] = p3.x;
-            fhi[r] = p3.y;
-            if (sshift && p3.z) {
-                // super-tile rectangle covering the tile rectangle
-                const uint32_t sx0 = (p3.x & 0xFFFFu) >> sshift, sy0 = (p3.x >> 16) >> sshift;
-                const uint32_t sx1 = (((p3.y & 0xFFFFu) - 1u) >> sshift) + 1u;
-                const uint32_t sy1 = (((p3.y >> 16) - 1u) >> sshift) + 1u;
-                lo[r] = sx0 | (sy0 << 16);
-                hi[r] = sx1 | (sy1 << 16);
-                cnt[r] = (sx1 - sx0) * (sy1 - sy0);
-                kb[r] = (uint32_t)vt[v].stile_off;
-                tx[r] = (uint32_t)vt[v].stx;
-            }
+            fine += ((rc.y & 0xFFFFu) - (rc.x & 0xFFFFu)) * ((rc.y >> 16) - (rc.x >> 16));
+            uint32_t lo, hi;
+            cnt = key_rect(rc.x, rc.y, lo, hi);
+            const uint32_t w0 = (hi & 0xFFFFu) - (lo & 0xFFFFu);
+            rw = w0 ? 1.0f / (float)w0 : 0.f;
+            it = make_uint4(rr - v * (uint32_t)n, v, rc.x, rc.y);
         }
-        incl[r] = warp_incl_scan(cnt[r], lane);
-        rtot[r] = __shfl_sync(0xFFFFFFFFu, incl[r], 31);
-        wtot += rtot[r];
+        s_item[slot] = it;
+        s_rw[slot] = rw;
+        incl[r] = warp_incl_scan(cnt, lane);
+        wtot += __shfl_sync(0xFFFFFFFFu, incl[r], 31);
     }
     if (lane == 0) s_wtot[warp] = wtot;
     if (fine_total) {
@@ -523,14 +530,17 @@ k_emit(const uint64_t* __restrict__ dsorted, int64_t total, int64_t n, const uin
     uint64_t base = s_excl + wexcl;
 #pragma unroll
     for (int r = 0; r < kEmitRounds; ++r) {
-        const uint32_t off = incl[r] - cnt[r];
-        const uint32_t w0 = (hi[r] & 0xFFFFu) - (lo[r] & 0xFFFFu);
-        const float rw = w0 ? 1.0f / (float)w0 : 0.f;
+        const int row = warp * (32 * kEmitRounds) + r * 32;  // this (warp, round)'s items
+        const uint32_t rtot = __shfl_sync(0xFFFFFFFFu, incl[r], 31);
+        uint32_t mlo, mhi;
+        const uint4 mine = s_item[row + lane];
+        const uint32_t cnt = key_rect(mine.z, mine.w, mlo, mhi);
+        const uint32_t off = incl[r] - cnt;
         int carry = -1;
-        for (uint32_t c = 0; c < rtot[r]; c += 32) {
+        for (uint32_t c = 0; c < rtot; c += 32) {
             s_mark[warp][lane] = -1;
             __syncwarp();
-            if (cnt[r] > 0 && off >= c && off < c + 32) s_mark[warp][off - c] = lane;
+            if (cnt > 0 && off >= c && off < c + 32) s_mark[warp][off - c] = lane;
             __syncwarp();
             int m = s_mark[warp][lane];
 #pragma unroll
@@ -542,20 +552,20 @@ k_emit(const uint64_t* __restrict__ dsorted, int64_t total, int64_t n, const uin
             carry = __shfl_sync(0xFFFFFFFFu, m, 31);
             const int owner = m < 0 ? 0 : m;
             const uint32_t o_off = __shfl_sync(0xFFFFFFFFu, off, owner);
-            const uint32_t o_lo = __shfl_sync(0xFFFFFFFFu, lo[r], owner);
-            const uint32_t o_w = __shfl_sync(0xFFFFFFFFu, w0, owner);
-            const float o_rw = __shfl_sync(0xFFFFFFFFu, rw, owner);
-            const uint32_t o_kb = __shfl_sync(0xFFFFFFFFu, kb[r], owner);
-            const uint32_t o_tx = __shfl_sync(0xFFFFFFFFu, tx[r], owner);
-            const uint32_t o_g = __shfl_sync(0xFFFFFFFFu, gi[r], owner);
-            const uint32_t o_flo = __shfl_sync(0xFFFFFFFFu, flo[r], owner);
-            const uint32_t o_fhi = __shfl_sync(0xFFFFFFFFu, fhi[r], owner);
             const uint32_t o = c + lane;
             // only entries that fit the capacity are stored and counted, so the
             // sort's digit offsets always describe exactly the stored prefix
-            const bool stored = o < rtot[r] && base + o < (uint64_t)cap;
+            const bool stored = o < rtot && base + o < (uint64_t)cap;
             uint32_t key = 0;
             if (stored) {
+                const uint4 ow = s_item[row + owner];
+                const float o_rw = s_rw[row + owner];
+                uint32_t o_lo, o_hi;
+                key_rect(ow.z, ow.w, o_lo, o_hi);
+                const ViewInfo& vi = vt[ow.y];
+                const uint32_t o_kb = (uint32_t)(sshift ? vi.stile_off : vi.tile_off);
+                const uint32_t o_tx = (uint32_t)(sshift ? vi.stx : vi.tx);
+                const uint32_t o_w = (o_hi & 0xFFFFu) - (o_lo & 0xFFFFu);
                 const uint32_t j = o - o_off;
                 // j / w exactly: j < 2^16 and w < 2^16, so (j + 0.5) / w stays
                 // more than 0.5 / w away from an integer
@@ -572,27 +582,27 @@ k_emit(const uint64_t* __restrict__ dsorted, int64_t total, int64_t n, const uin
                     const int ox = (int)(((o_lo & 0xFFFFu) + txx) << sshift);
                     const int oy = (int)(((o_lo >> 16) + ty) << sshift);
                     const int S = 1 << sshift;
-                    const int x0 = max((int)(o_flo & 0xFFFFu) - ox, 0), x1 = min((int)(o_fhi & 0xFFFFu) - ox, S);
-                    const int y0 = max((int)(o_flo >> 16) - oy, 0), y1 = min((int)(o_fhi >> 16) - oy, S);
+                    const int x0 = max((int)(ow.z & 0xFFFFu) - ox, 0), x1 = min((int)(ow.w & 0xFFFFu) - ox, S);
+                    const int y0 = max((int)(ow.z >> 16) - oy, 0), y1 = min((int)(ow.w >> 16) - oy, S);
                     extra = (uint64_t)((uint32_t)x0 | ((uint32_t)(x1 - 1) << 3) | ((uint32_t)y0 << 6) |
                                        ((uint32_t)(y1 - 1) << 9)) << kRectShift;
                 }
-                kv[base + o] = extra | ((uint64_t)key << 32) | o_g;
+                kv[base + o] = extra | ((uint64_t)key << 32) | ow.x;
             }
             const uint32_t act = __ballot_sync(0xFFFFFFFFu, stored);
             if (stored) {
                 atomicAdd(&s_hist[0][key & (R - 1)], 1u);
-                for (int p = 1; p < passes; ++p) {
+                for (int p = 1; p < passes && p < HP; ++p) {
                     const uint32_t d = (key >> (p * BITS)) & (R - 1);
                     const uint32_t peers = __match_any_sync(act, d);
                     if (lane == __ffs(peers) - 1) atomicAdd(&s_hist[p][d], __popc(peers));
                 }
             }
         }
-        base += rtot[r];
+        base += rtot;
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < passes * R; i += kEmitThreads) {
+    for (int i = threadIdx.x; i < passes * R && i < HP * R; i += kEmitThreads) {
         const uint32_t c = (&s_hist[0][0])[i];
         if (c) atomicAdd(&hist[(i / R) * kMaxR + (i % R)], c);
     }
