@@ -311,15 +311,33 @@ k_render_fwd(const float4* __restrict__ proj, const ViewInfo* __restrict__ vt, i
             const float2 qx2 = make_float2(q.x, q.x), qb2 = make_float2(qb, qb), qc2 = make_float2(qc, qc);
             const float2 o2 = make_float2(a.z, a.z);
             const uint32_t pos1 = s_pos[j] + 1;
+            // pairs in groups of two: one branch per group, so that the two
+            // pairs' chains interleave (a pair without a valid pixel is an
+            // exact no-op: alpha 0 leaves T, the colour and last unchanged)
+            constexpr int GP = NP < 2 ? NP : 2;
 #pragma unroll
-            for (int p = 0; p < NP; ++p) {
+            for (int p0 = 0; p0 < NP; p0 += GP) {
+                float2 P2g[GP];
+                bool v0g[GP], v1g[GP];
+                bool any = false;
+#pragma unroll
+                for (int u = 0; u < GP; ++u) {
+                    const int p = p0 + u;
+                    const float2 dx = make_float2(dx0 - (float)(2 * p), dx0 - (float)(2 * p + 1));
+                    // the conic is positive definite, so P2 <= 0 up to rounding;
+                    // the fragment counts where alpha >= 1/255
+                    P2g[u] = __fadd2_rn(__ffma2_rn(__ffma2_rn(qx2, dx, qb2), dx, qc2), pen[p]);
+                    v0g[u] = P2g[u].x >= a.w;
+                    v1g[u] = P2g[u].y >= a.w;
+                    any = any || v0g[u] || v1g[u];
+                }
+                if (!any) continue;
+#pragma unroll
+                for (int u = 0; u < GP; ++u) {
+                const int p = p0 + u;
                 const int k0 = 2 * p, k1 = 2 * p + 1;
-                const float2 dx = make_float2(dx0 - (float)k0, dx0 - (float)k1);
-                // the conic is positive definite, so P2 <= 0 up to rounding;
-                // the fragment counts where alpha >= 1/255
-                const float2 P2 = __fadd2_rn(__ffma2_rn(__ffma2_rn(qx2, dx, qb2), dx, qc2), pen[p]);
-                bool v0 = P2.x >= a.w, v1 = P2.y >= a.w;
-                if (!(v0 || v1)) continue;
+                const float2 P2 = P2g[u];
+                bool v0 = v0g[u], v1 = v1g[u];
                 const float2 raw = __fmul2_rn(o2, make_float2(v0 ? ex2(P2.x) : 0.f, v1 ? ex2(P2.y) : 0.f));
                 float2 al = make_float2(fminf(kAlphaMax, raw.x), fminf(kAlphaMax, raw.y));
                 float2 Tn = __fmul2_rn(T[p], __ffma2_rn(al, make_float2(-1.f, -1.f), make_float2(1.f, 1.f)));
@@ -338,6 +356,7 @@ k_render_fwd(const float4* __restrict__ proj, const ViewInfo* __restrict__ vt, i
                 T[p] = Tn;
                 if (v0) last[k0] = pos1;
                 if (v1) last[k1] = pos1;
+                }
             }
         }
     };
@@ -574,39 +593,57 @@ k_raster_bwd(const float4* __restrict__ proj, const ViewInfo* __restrict__ vt, i
             const float2 o2 = make_float2(a.z, a.z), m1 = make_float2(-1.f, -1.f), one = make_float2(1.f, 1.f);
             const float2 cr = make_float2(c.x, c.x), cg = make_float2(c.y, c.y), cb = make_float2(c.z, c.z);
             bool contrib = false;
+            // pairs in groups of two: one branch per group, so that the two
+            // pairs' chains interleave (a pair without a valid pixel is an
+            // exact no-op: alpha 0 leaves T, X and every sum unchanged)
+            constexpr int GP = 2;
 #pragma unroll
-            for (int p = 0; p < NP; ++p) {
-                const int k0 = 2 * p, k1 = 2 * p + 1;
-                const float2 dx = make_float2(dx0 - (float)k0, dx0 - (float)k1);
-                const float2 P2 = __ffma2_rn(__ffma2_rn(qx2, dx, qb2), dx, qc2);
-                const bool v0 = pos < last[k0] && P2.x >= a.w;
-                const bool v1 = pos < last[k1] && P2.y >= a.w;
-                if (!(v0 || v1)) continue;
+            for (int p0 = 0; p0 < NP; p0 += GP) {
+                float2 dxg[GP], P2g[GP];
+                bool v0g[GP], v1g[GP];
+                bool any = false;
+#pragma unroll
+                for (int u = 0; u < GP; ++u) {
+                    const int p = p0 + u;
+                    const int k0 = 2 * p, k1 = 2 * p + 1;
+                    dxg[u] = make_float2(dx0 - (float)k0, dx0 - (float)k1);
+                    P2g[u] = __ffma2_rn(__ffma2_rn(qx2, dxg[u], qb2), dxg[u], qc2);
+                    v0g[u] = pos < last[k0] && P2g[u].x >= a.w;
+                    v1g[u] = pos < last[k1] && P2g[u].y >= a.w;
+                    any = any || v0g[u] || v1g[u];
+                }
+                if (!any) continue;
                 contrib = true;
-                const float2 raw = __fmul2_rn(o2, make_float2(v0 ? ex2(P2.x) : 0.f, v1 ? ex2(P2.y) : 0.f));
-                const float2 al = CL ? make_float2(fminf(kAlphaMax, raw.x), fminf(kAlphaMax, raw.y)) : raw;
-                const float2 om = __ffma2_rn(al, m1, one);  // 1 - alpha
-                const float2 Tj = make_float2(v0 ? T[p].x * rcp_approx(om.x) : T[p].x,
-                                              v1 ? T[p].y * rcp_approx(om.y) : T[p].y);
-                T[p] = Tj;
-                const float2 w = __fmul2_rn(al, Tj);
-                const float2 dCr = s_dC[0][p][threadIdx.x], dCg = s_dC[1][p][threadIdx.x],
-                             dCb = s_dC[2][p][threadIdx.x];
-                g6 = __ffma2_rn(w, dCr, g6);
-                g7 = __ffma2_rn(w, dCg, g7);
-                g8 = __ffma2_rn(w, dCb, g8);
-                // e = dL/dC . (c - R)
-                const float2 e = __ffma2_rn(dCb, cb, __ffma2_rn(dCg, cg, __ffma2_rn(dCr, cr, make_float2(-X[p].x, -X[p].y))));
-                const float2 dal = __fmul2_rn(Tj, e);
-                X[p] = __ffma2_rn(al, e, X[p]);
-                // dL/dP = dL/dalpha * alpha where alpha is not clamped
-                const float2 dP = CL ? __fmul2_rn(dal, make_float2(raw.x <= kAlphaMax ? raw.x : 0.f,
-                                                                  raw.y <= kAlphaMax ? raw.y : 0.f))
-                                     : __fmul2_rn(dal, raw);
-                const float2 t = __fmul2_rn(dP, dx);
-                s0 = __fadd2_rn(s0, dP);
-                s1 = __fadd2_rn(s1, t);
-                s2 = __ffma2_rn(t, dx, s2);
+#pragma unroll
+                for (int u = 0; u < GP; ++u) {
+                    const int p = p0 + u;
+                    const bool v0 = v0g[u], v1 = v1g[u];
+                    const float2 dx = dxg[u], P2 = P2g[u];
+                    const float2 raw = __fmul2_rn(o2, make_float2(v0 ? ex2(P2.x) : 0.f, v1 ? ex2(P2.y) : 0.f));
+                    const float2 al = CL ? make_float2(fminf(kAlphaMax, raw.x), fminf(kAlphaMax, raw.y)) : raw;
+                    const float2 om = __ffma2_rn(al, m1, one);  // 1 - alpha
+                    const float2 Tj = make_float2(v0 ? T[p].x * rcp_approx(om.x) : T[p].x,
+                                                  v1 ? T[p].y * rcp_approx(om.y) : T[p].y);
+                    T[p] = Tj;
+                    const float2 w = __fmul2_rn(al, Tj);
+                    const float2 dCr = s_dC[0][p][threadIdx.x], dCg = s_dC[1][p][threadIdx.x],
+                                 dCb = s_dC[2][p][threadIdx.x];
+                    g6 = __ffma2_rn(w, dCr, g6);
+                    g7 = __ffma2_rn(w, dCg, g7);
+                    g8 = __ffma2_rn(w, dCb, g8);
+                    // e = dL/dC . (c - R)
+                    const float2 e = __ffma2_rn(dCb, cb, __ffma2_rn(dCg, cg, __ffma2_rn(dCr, cr, make_float2(-X[p].x, -X[p].y))));
+                    const float2 dal = __fmul2_rn(Tj, e);
+                    X[p] = __ffma2_rn(al, e, X[p]);
+                    // dL/dP = dL/dalpha * alpha where alpha is not clamped
+                    const float2 dP = CL ? __fmul2_rn(dal, make_float2(raw.x <= kAlphaMax ? raw.x : 0.f,
+                                                                      raw.y <= kAlphaMax ? raw.y : 0.f))
+                                         : __fmul2_rn(dal, raw);
+                    const float2 t = __fmul2_rn(dP, dx);
+                    s0 = __fadd2_rn(s0, dP);
+                    s1 = __fadd2_rn(s1, t);
+                    s2 = __ffma2_rn(t, dx, s2);
+                }
             }
             return contrib;
         };
