@@ -700,6 +700,9 @@ def run_ours(args, rank, world, local_rank):
     tctx.raise_status()
 
     snapshot = params.clone()  # the model before the timed steps (tensor-delta measurement)
+    # the end-to-end run starts from the same model as the timed steps (the
+    # cost of a step grows as the synthetic model trains)
+    e2e_params = params.clone() if args.e2e_steps > 0 else None
     # ---- timed region: K steps, device time of each step by CUDA events
     ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
@@ -852,8 +855,8 @@ def run_ours(args, rank, world, local_rank):
             return gs.Context(local_rank, 0, tile=args.tile, sort_bits=args.sort_bits, sort_items=args.sort_items,
                               binning=args.binning, raster_threads=args.raster_threads,
                      raster_bwd_threads=args.raster_bwd_threads)
-        e2e = run_e2e(args, host_targets, params, sh, cams, keys_cap, make_ctx, dyn, world, lighting)
-        del host_targets
+        e2e = run_e2e(args, host_targets, e2e_params, sh, cams, keys_cap, make_ctx, dyn, world, lighting)
+        del host_targets, e2e_params
     serving = None
     if args.serve_requests > 0:
         torch.cuda.empty_cache()
@@ -1069,7 +1072,8 @@ def run_e2e(args, host_targets, params, sh, cams, keys_cap, make_ctx, dyn, world
     ms = e0.elapsed_time(e1)
     out = {"value": world * args.e2e_steps / (ms / 1e3), "unit": "steps/s",
            "h2d_bytes_per_step": st.h2d_bytes // args.e2e_steps, "d2h_bytes_per_step": st.d2h_bytes // args.e2e_steps,
-           "steps": args.e2e_steps, "pipeline": "two graph slots; uploads and read-backs overlap compute"}
+           "steps": args.e2e_steps, "pipeline": "two graph slots; uploads and read-backs overlap compute",
+           "model": "the state before the device-timed steps, fresh Adam moments"}
     for t in st.slots:
         t.ctx.close()
     return out
@@ -1091,7 +1095,8 @@ def main():
                     help="threads per pixel row of the compositing adjoint (default: --raster-threads)")
     ap.add_argument("--autotune", action=argparse.BooleanOptionalAction, default=True,
                     help="choose binning / sort / raster settings with gs_autotune before timing")
-    ap.add_argument("--e2e-steps", type=int, default=100)
+    ap.add_argument("--e2e-steps", type=int, default=-1,
+                    help="steps of the end-to-end measurement (-1: as many as --steps)")
     ap.add_argument("--cpu-samples", type=int, default=12)
     ap.add_argument("--plain-steps", type=int, default=10)
     ap.add_argument("--serve-requests", type=int, default=10_000, help="requests per offered load (0: no serving)")
@@ -1113,6 +1118,8 @@ def main():
                     help="time per-attribute tensor-delta extraction and replay after the timed steps")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    if args.e2e_steps < 0:
+        args.e2e_steps = args.steps
     if args.raster_bwd_threads is None:
         args.raster_bwd_threads = args.raster_threads
 
