@@ -700,9 +700,13 @@ def run_ours(args, rank, world, local_rank):
     tctx.raise_status()
 
     snapshot = params.clone()  # the model before the timed steps (tensor-delta measurement)
-    # the end-to-end run starts from the same model as the timed steps (the
-    # cost of a step grows as the synthetic model trains)
-    e2e_params = params.clone() if args.e2e_steps > 0 else None
+    # the end-to-end run starts from the same model and optimiser state as the
+    # timed steps (the cost of a step depends on how far the synthetic model
+    # has trained, and fresh Adam moments move every parameter at once)
+    e2e_state = None
+    if args.e2e_steps > 0:
+        e2e_state = {"params": params.clone(), "m": tr.m.clone(), "v": tr.v.clone(),
+                     "baseline": tr.baseline.clone(), "step": tr.d_step.clone()}
     # ---- timed region: K steps, device time of each step by CUDA events
     ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
@@ -855,8 +859,8 @@ def run_ours(args, rank, world, local_rank):
             return gs.Context(local_rank, 0, tile=args.tile, sort_bits=args.sort_bits, sort_items=args.sort_items,
                               binning=args.binning, raster_threads=args.raster_threads,
                      raster_bwd_threads=args.raster_bwd_threads)
-        e2e = run_e2e(args, host_targets, e2e_params, sh, cams, keys_cap, make_ctx, dyn, world, lighting)
-        del host_targets, e2e_params
+        e2e = run_e2e(args, host_targets, e2e_state, sh, cams, keys_cap, make_ctx, dyn, world, lighting)
+        del host_targets, e2e_state
     serving = None
     if args.serve_requests > 0:
         torch.cuda.empty_cache()
@@ -1048,7 +1052,7 @@ def measure_tensor_deltas(gs, torch, params, snapshot, hbm_peak, reps=5):
     return out
 
 
-def run_e2e(args, host_targets, params, sh, cams, keys_cap, make_ctx, dyn, world, lighting=None):
+def run_e2e(args, host_targets, state, sh, cams, keys_cap, make_ctx, dyn, world, lighting=None):
     """The same metric through the public API with host buffers: every step
     uploads its targets from pinned host memory and returns its loss, delta
     count and delta records to pinned host memory.  The copies overlap the
@@ -1056,7 +1060,14 @@ def run_e2e(args, host_targets, params, sh, cams, keys_cap, make_ctx, dyn, world
     runs from the first upload to the last record read-back."""
     import torch
     from paper_2604_02851_b300.train import StreamingTrainer
-    st = StreamingTrainer(params, sh, cams, keys_cap, make_ctx, dyn=dyn, lighting=lighting)
+    st = StreamingTrainer(state["params"], sh, cams, keys_cap, make_ctx, dyn=dyn, lighting=lighting)
+    # continue from the device-timed run's starting point: moments, baseline
+    # and step counter (the slots share them)
+    s0 = st.slots[0]
+    s0.m.copy_(state["m"])
+    s0.v.copy_(state["v"])
+    s0.baseline.copy_(state["baseline"])
+    s0.d_step.copy_(state["step"])
     st.capture()
     st.run(lambda k: host_targets[k % 2], 3)  # warm-up
     torch.cuda.synchronize()
@@ -1073,7 +1084,7 @@ def run_e2e(args, host_targets, params, sh, cams, keys_cap, make_ctx, dyn, world
     out = {"value": world * args.e2e_steps / (ms / 1e3), "unit": "steps/s",
            "h2d_bytes_per_step": st.h2d_bytes // args.e2e_steps, "d2h_bytes_per_step": st.d2h_bytes // args.e2e_steps,
            "steps": args.e2e_steps, "pipeline": "two graph slots; uploads and read-backs overlap compute",
-           "model": "the state before the device-timed steps, fresh Adam moments"}
+           "model": "the model and optimiser state before the device-timed steps"}
     for t in st.slots:
         t.ctx.close()
     return out

@@ -231,16 +231,31 @@ class StreamingTrainer:
         pinned host tensor (planar [V][3][H][W] floats).  on_delta(k, loss,
         count, records) receives each step's outputs in host memory (the
         records view is valid during the call).  Returns the loss of the last
-        step."""
+        step.
+
+        Step k + 1's upload is queued right after step k is launched and
+        starts when step k - 1 (the last user of that slot's targets) ends,
+        so it overlaps all of step k; the read-backs of step k - 1 are
+        queued on the (in-order) read-back stream before those of step k."""
         torch = self.torch
         Ev = torch.cuda.Event
         slot_free = [Ev(), Ev()]       # the slot's records have been copied out
         uploaded = [Ev(), Ev()]
-        done = [Ev(), Ev()]
+        done = [Ev(), Ev()]            # the slot's step (and its reads of the targets) ended
         counted = [Ev(), Ev()]
-        for e in slot_free:
+        for e in slot_free + done:
             e.record(self.compute)
         last_loss = None
+
+        def upload(k):
+            s = k % 2
+            t = self.slots[s]
+            src = host_targets(k)
+            with torch.cuda.stream(self.h2d):
+                self.h2d.wait_event(done[s])
+                t.targets.copy_(src, non_blocking=True)
+                uploaded[s].record(self.h2d)
+            self.h2d_bytes += t.targets.numel() * 4
 
         def drain(k):
             nonlocal last_loss
@@ -257,19 +272,17 @@ class StreamingTrainer:
             if on_delta is not None:
                 on_delta(k, last_loss, m, self.host_rec[s][:m])
 
+        if steps:
+            upload(0)
         for k in range(steps):
             s = k % 2
             t = self.slots[s]
-            src = host_targets(k)
-            with torch.cuda.stream(self.h2d):
-                self.h2d.wait_event(slot_free[s])
-                t.targets.copy_(src, non_blocking=True)
-                uploaded[s].record(self.h2d)
-            self.h2d_bytes += t.targets.numel() * 4
             self.compute.wait_event(uploaded[s])
             self.compute.wait_event(slot_free[s])
             t.step(self.compute)
             done[s].record(self.compute)
+            if k + 1 < steps:
+                upload(k + 1)
             # step k - 1's records go out before step k's read-backs are queued
             # on the (in-order) read-back stream, so they do not wait for step k
             if k >= 1:
