@@ -235,11 +235,13 @@ k_render_fwd(const float4* __restrict__ proj, const ViewInfo* __restrict__ vt, i
     __shared__ uint32_t s_cand[COARSE ? kChunkItems : 1];
     __shared__ int s_ctot[NW];
 
-    // pixel pairs (2p, 2p + 1) in packed float2 registers.  pen is added to
-    // a pixel's exponent: 0 while it composites, -inf once it has stopped (or
-    // lies outside the image), which fails the alpha cut-off test.
-    const float kNegInf = __int_as_float(0xff800000);
-    float2 T[NP], Cr[NP], Cg[NP], Cb[NP], pen[NP];
+    // pixel pairs (2p, 2p + 1) in packed float2 registers.  nk holds the
+    // negated offset of each pixel from the strip's first one (dx = dx0 + nk,
+    // exactly dx0 - k) while it composites and +inf once it has stopped (or
+    // lies outside the image): then dx = +inf and the exponent (concave, its
+    // dx^2 coefficient negative) is -inf, which fails the alpha cut-off test.
+    const float kPosInf = __int_as_float(0x7f800000);
+    float2 T[NP], Cr[NP], Cg[NP], Cb[NP], nk[NP];
     uint32_t last[PX];
     int nlive = 0;  // pixels of this thread still compositing
 #pragma unroll
@@ -248,7 +250,7 @@ k_render_fwd(const float4* __restrict__ proj, const ViewInfo* __restrict__ vt, i
         Cr[p] = Cg[p] = Cb[p] = make_float2(0.f, 0.f);
         const bool in0 = px0 + 2 * p < vi.width && py < vi.height;
         const bool in1 = px0 + 2 * p + 1 < vi.width && py < vi.height;
-        pen[p] = make_float2(in0 ? 0.f : kNegInf, in1 ? 0.f : kNegInf);
+        nk[p] = make_float2(in0 ? -(float)(2 * p) : kPosInf, in1 ? -(float)(2 * p + 1) : kPosInf);
         nlive += (int)in0 + (int)in1;
     }
 #pragma unroll
@@ -309,7 +311,7 @@ k_render_fwd(const float4* __restrict__ proj, const ViewInfo* __restrict__ vt, i
             const float qc = q.z * dy * dy;
             const float dx0 = a.x - fx0;
             const float2 qx2 = make_float2(q.x, q.x), qb2 = make_float2(qb, qb), qc2 = make_float2(qc, qc);
-            const float2 o2 = make_float2(a.z, a.z);
+            const float2 o2 = make_float2(a.z, a.z), dx02 = make_float2(dx0, dx0);
             const uint32_t pos1 = s_pos[j] + 1;
             // pairs in groups of two: one branch per group, so that the two
             // pairs' chains interleave (a pair without a valid pixel is an
@@ -323,10 +325,10 @@ k_render_fwd(const float4* __restrict__ proj, const ViewInfo* __restrict__ vt, i
 #pragma unroll
                 for (int u = 0; u < GP; ++u) {
                     const int p = p0 + u;
-                    const float2 dx = make_float2(dx0 - (float)(2 * p), dx0 - (float)(2 * p + 1));
+                    const float2 dx = __fadd2_rn(dx02, nk[p]);
                     // the conic is positive definite, so P2 <= 0 up to rounding;
                     // the fragment counts where alpha >= 1/255
-                    P2g[u] = __fadd2_rn(__ffma2_rn(__ffma2_rn(qx2, dx, qb2), dx, qc2), pen[p]);
+                    P2g[u] = __ffma2_rn(__ffma2_rn(qx2, dx, qb2), dx, qc2);
                     v0g[u] = P2g[u].x >= a.w;
                     v1g[u] = P2g[u].y >= a.w;
                     any = any || v0g[u] || v1g[u];
@@ -345,8 +347,8 @@ k_render_fwd(const float4* __restrict__ proj, const ViewInfo* __restrict__ vt, i
                 // this fragment misses keeps its T: only a covered pixel can
                 // fall below.  It stops before this fragment.
                 if (Tn.x < kTMin || Tn.y < kTMin) {
-                    if (Tn.x < kTMin) { al.x = 0.f; Tn.x = T[p].x; pen[p].x = kNegInf; v0 = false; --nlive; }
-                    if (Tn.y < kTMin) { al.y = 0.f; Tn.y = T[p].y; pen[p].y = kNegInf; v1 = false; --nlive; }
+                    if (Tn.x < kTMin) { al.x = 0.f; Tn.x = T[p].x; nk[p].x = kPosInf; v0 = false; --nlive; }
+                    if (Tn.y < kTMin) { al.y = 0.f; Tn.y = T[p].y; nk[p].y = kPosInf; v1 = false; --nlive; }
                 }
                 const float4 c = s_c[j];
                 const float2 w = __fmul2_rn(al, T[p]);
