@@ -16,8 +16,10 @@ from one device-resident model is done here with continuous batching:
   the device starts as soon as a slot and memory free up, and batches on
   different slots overlap on the GPU.
 
-Latency is measured from a request's arrival to the moment its image is in
-host memory.  Results do not depend on batch composition: each view's key
+Two latencies are measured from a request's arrival: to the moment its image
+is complete in device memory (the render, what a client displaying it waits
+for) and to the moment it is in pinned host memory (delivery over the host
+link).  Results do not depend on batch composition: each view's key
 order, tile lists and pixels are computed independently of the other views.
 """
 from __future__ import annotations
@@ -37,7 +39,8 @@ class Request:
     height: int
     cam: np.ndarray            # packed gs_camera record (1 element)
     t_arrival: float
-    t_done: float = -1.0
+    t_done: float = -1.0       # image in pinned host memory
+    t_rendered: float = -1.0   # image complete in device memory
     image: object = None       # pinned host tensor [3, H, W] when done
     keys_est: int = 0
     bytes_est: int = 0
@@ -51,6 +54,8 @@ class _Slot:
     host: object               # pinned host buffer of the same size
     ws_bytes: int
     event: object = None
+    rendered: object = None    # event after the render, before the host copy
+    t_rendered: float = -1.0
     batch: list = field(default_factory=list)
     offsets: list = field(default_factory=list)
 
@@ -114,6 +119,8 @@ class RenderServer:
             d_cams = cameras_to_device(cams, self.params.device)
             gs_render_batch(slot.ctx, self.params, self.sh, d_cams, len(reqs), tt, keys, npix, bg=self.bg,
                             image=slot.image, stream=slot.stream)
+            rendered = torch.cuda.Event()
+            rendered.record(slot.stream)
             slot.host[:3 * npix].copy_(slot.image[:3 * npix], non_blocking=True)
             ev = torch.cuda.Event()
             ev.record(slot.stream)
@@ -126,6 +133,8 @@ class RenderServer:
             self.launch_while_busy += 1
         self.max_busy = max(self.max_busy, busy + 1)
         slot.event = ev
+        slot.rendered = rendered
+        slot.t_rendered = -1.0
         slot.batch = list(reqs)
         slot.offsets = offs
         slot.d_cams = d_cams
@@ -153,14 +162,16 @@ class RenderServer:
         if code != 0:
             raise RuntimeError(f"render batch failed on the device: status {code} ({detail})")
         done = []
+        t_rendered = slot.t_rendered if slot.t_rendered >= 0 else now
         for r, off in zip(slot.batch, slot.offsets):
             r.t_done = now
+            r.t_rendered = t_rendered
             if self.keep_images:
                 m = 3 * r.width * r.height
                 r.image = slot.host[off:off + m].numpy().reshape(3, r.height, r.width).copy()
             done.append(r)
         self.in_flight_bytes -= sum(r.bytes_est for r in slot.batch)
-        slot.batch, slot.offsets, slot.event = [], [], None
+        slot.batch, slot.offsets, slot.event, slot.rendered = [], [], None, None
         return done
 
     def _admit(self, queue) -> list:
@@ -198,6 +209,8 @@ class RenderServer:
                 queue.append(r)
             progressed = False
             for slot in self.slots:
+                if slot.rendered is not None and slot.t_rendered < 0 and slot.rendered.query():
+                    slot.t_rendered = time.perf_counter() - start
                 if slot.event is not None and slot.event.query():
                     done.extend(self._complete(slot, time.perf_counter() - start))
                     progressed = True
@@ -242,6 +255,8 @@ def measure_keys_per_pixel(params, sh_degree: int, cams) -> float:
     return k / px
 
 
-def percentiles(reqs):
-    lat = np.array([(r.t_done - r.t_arrival) * 1e3 for r in reqs])
+def percentiles(reqs, rendered: bool = False):
+    """p50 and p99 (ms) of arrival-to-host latency, or with rendered=True of
+    arrival-to-device-image latency, and the latencies."""
+    lat = np.array([((r.t_rendered if rendered else r.t_done) - r.t_arrival) * 1e3 for r in reqs])
     return float(np.percentile(lat, 50)), float(np.percentile(lat, 99)), lat

@@ -66,6 +66,8 @@ def test_batches_overlap_and_admit_while_busy(server):
     assert len(done) == 24
     assert srv.max_busy >= 2 and srv.launch_while_busy >= 1
     assert all(r.t_done >= r.t_arrival for r in done)
+    # the image is complete on the device before it reaches host memory
+    assert all(r.t_arrival <= r.t_rendered <= r.t_done for r in done)
 
 
 def test_single_render_matches_oracle(server):
