@@ -358,10 +358,11 @@ k_project(const float4* __restrict__ P, int64_t n, int64_t g_off, int64_t n_out,
 }
 
 // ------------------------------------------------------------------ adjoint
-// View-dependent colour: 4 blocks an SM (128 registers; the SH coefficients
-// and their gradient accumulators in shared memory, 48 KB a block); relit: 3.
+// 4 blocks an SM.  View-dependent colour: 128 registers, the SH coefficients
+// and their gradient accumulators in shared memory (48 KB a block); relit:
+// 123 registers, no spills (measured faster than 3 blocks at 130).
 template <int D, bool LIT>
-__global__ void __launch_bounds__(128, LIT ? 3 : 4)
+__global__ void __launch_bounds__(128, 4)
 k_project_bwd(const float4* __restrict__ P, int64_t n, int64_t n_out, Dyn dyn, const gs_camera* __restrict__ cams,
               int V,
               const float4* __restrict__ proj, const float4* __restrict__ g2d,
