@@ -204,11 +204,12 @@ __device__ __forceinline__ float lit_vis(const Dyn& d, int64_t g) {
     return d.vis ? (float)d.vis[g] * (1.f / 255.f) : 1.f;
 }
 
-// View-dependent colour: four blocks an SM (64 registers; the coefficients
-// wait in shared memory); relit colour: three (85 registers).  Both measured
-// faster than two blocks with the coefficients in 116 registers.
+// Four blocks an SM (64 registers).  View-dependent colour: the coefficients
+// wait in shared memory; relit colour: a few spills, measured faster than
+// three blocks at 78 registers.  Both measured faster than two blocks with the
+// coefficients in 116 registers.
 template <int D, bool LIT>
-__global__ void __launch_bounds__(256, LIT ? 3 : 4)
+__global__ void __launch_bounds__(256, 4)
 k_project(const float4* __restrict__ P, int64_t n, int64_t g_off, int64_t n_out, Dyn dyn,
           const gs_camera* __restrict__ cams, const ViewInfo* __restrict__ vt, int V, int tile,
           float4* __restrict__ proj, uint64_t* __restrict__ dkv, uint2* __restrict__ rects, int rec4) {
