@@ -11,8 +11,10 @@ the float atomics, and so do the parameters (and the next step's image) by
 rounding.  Cases: one super-tile holding many chunks, ragged image edges, big
 splats spanning many super-tiles, both raster layouts, 8-pixel tiles, an
 opaque scene whose pixels stop early, a tiny scene over many views (more
-chunks than keys_cap / 256), and 320 or 512 super-tiles, whose 9-bit key the
-fused step sorts in one wide pass (the direct binning sorts tile keys).
+chunks than keys_cap / 256), 320 or 512 super-tiles, whose 9-bit key the
+fused step sorts in one wide pass (the direct binning sorts tile keys), and
+2304 super-tiles, more than the longest-list-first order ranks (the raster
+kernels then take them in index order).
 """
 import numpy as np
 import pytest
@@ -37,6 +39,8 @@ CASES = {
     # the fused step sorts the 9-bit super-tile key in one wide pass
     "wide_key_320": (6_000, 0, 16, 320, 256, 0.3, 0.0, 8, 4, 4),
     "wide_key_512": (6_000, 0, 16, 512, 256, 0.3, 0.0, 8, 4, 4),
+    # 2304 super-tiles, more than the raster order ranks: the identity order
+    "many_supertiles": (3_000, 0, 16, 1536, 1536, 1.0, 0.0, 16, 4, 2),
 }
 
 
@@ -72,8 +76,12 @@ def test_train_step_chunk_lists_match_expanded_lists(name):
             np.testing.assert_array_equal(a.image.cpu().numpy(), b.image.cpu().numpy())
             assert a.loss() == b.loss()
         else:
-            assert rel_l2(a.image.cpu().numpy(), b.image.cpu().numpy()) <= 1e-6
-            assert abs(a.loss() - b.loss()) <= 1e-6 * b.loss()
+            # the second image differs by the rounding of the first update
+            # (float atomics order); splats that each cover thousands of
+            # pixels carry it into more of the image
+            tol = 1e-5 if name == "many_supertiles" else 1e-6
+            assert rel_l2(a.image.cpu().numpy(), b.image.cpu().numpy()) <= tol
+            assert abs(a.loss() - b.loss()) <= tol * b.loss()
         assert rel_l2(a.grads.cpu().numpy(), b.grads.cpu().numpy()) <= 1e-5
         upd = np.linalg.norm(b.params.cpu().numpy() - planes)
         assert np.linalg.norm(a.params.cpu().numpy() - b.params.cpu().numpy()) <= 1e-3 * upd
@@ -85,6 +93,9 @@ def test_train_step_chunk_lists_match_expanded_lists(name):
         st = tile * 8
         n_super = V * ((W + st - 1) // st) * ((H + st - 1) // st)
         assert 256 < n_super <= 512 and n_super == int(name.split("_")[-1])
+    if name == "many_supertiles":
+        n_super = V * ((W + 127) // 128) * ((H + 127) // 128)
+        assert n_super > 2048
     if name == "tiny_many_views":
         # every non-empty super-tile takes a chunk: more than keys_cap / 256
         rect = O.project(planes, sh, cams32(cams))[..., 12:16].astype(np.int64)
