@@ -498,6 +498,17 @@ gs_status_t gs_render_batch(gs_ctx* ctx, const gs_scene* scene, const gs_camera*
                             const float* bg,
                             float* image, void* stream);
 
+/* gs_render_batch with a host copy of the cameras (host_cams: R records,
+ * read during the call, as d_cams holds them): the tile total comes from
+ * their sizes, and with the exact super-tile total the super-tile sort takes
+ * no more digit passes than that count needs and compositing takes the
+ * longest tile lists first.  Same image, bit for bit.  A device view table
+ * whose totals differ from host_cams' is reported as GS_ERR_ARG (device
+ * status).  GS_ERR_ARG for null host_cams or a view of zero size. */
+gs_status_t gs_render_batch_sized(gs_ctx* ctx, const gs_scene* scene, const gs_camera* d_cams,
+                                  const gs_camera* host_cams, int32_t n_requests, int64_t keys_cap,
+                                  const float* bg, float* image, void* stream);
+
 /* ------------------------------------------------------------ fused step */
 
 typedef struct gs_train_io {

@@ -525,11 +525,22 @@ def gs_apply_delta(ctx, params, d_records, d_count, stream=None):
 
 
 def gs_render_batch(ctx, params, sh_degree, d_cams, n_requests, total_tiles, keys_cap, npix, bg=None,
-                    image=None, stream=None, dyn=None, precull=None, lighting=None):
+                    image=None, stream=None, dyn=None, precull=None, lighting=None, host_cams=None):
+    """host_cams (the cameras of d_cams, packed or as a dict): render through
+    gs_render_batch_sized, which plans the tiles and super-tiles from them
+    (total_tiles is then not used)."""
     torch = _torch()
     if image is None:
         image = torch.empty(3 * npix, dtype=torch.float32, device=params.device)
     sc = _scene(params, sh_degree, dyn, precull, lighting)
+    if host_cams is not None:
+        packed, host = _host_cams(host_cams)
+        if len(packed) != n_requests:
+            raise ValueError("host_cams must hold the n_requests cameras of d_cams")
+        check("gs_render_batch_sized", _lib.lib().gs_render_batch_sized(ctx.ptr, C.byref(sc), _ptr(d_cams), host,
+                                                                        n_requests, keys_cap, _bg(bg), _ptr(image),
+                                                                        _stream(stream)))
+        return image
     check("gs_render_batch", _lib.lib().gs_render_batch(ctx.ptr, C.byref(sc), _ptr(d_cams), n_requests,
                                                         total_tiles, keys_cap, _bg(bg), _ptr(image),
                                                         _stream(stream)))

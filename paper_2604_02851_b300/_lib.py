@@ -22,7 +22,7 @@ EXPORTS = (
     "gs_ctx_set_raster_bwd_threads", "gs_ctx_get_tuning", "gs_ctx_set_wait_limit", "gs_ctx_set_wait_test",
     "gs_get_status", "gs_workspace_size", "gs_total_tiles", "gs_project", "gs_bin_sort",
     "gs_render_fwd", "gs_loss", "gs_raster_bwd", "gs_project_bwd", "gs_render_bwd",
-    "gs_adam_step", "gs_extract_delta", "gs_render_batch", "gs_train_step",
+    "gs_adam_step", "gs_extract_delta", "gs_render_batch", "gs_render_batch_sized", "gs_train_step",
     "gs_train_graph_capture", "gs_graph_launch", "gs_train_step_events",
     "gs_train_graph_capture_events", "gs_extract_delta_noalloc", "gs_autotune", "gs_tensor_record_bytes",
     "gs_extract_tensor_delta", "gs_apply_tensor_delta", "gs_apply_delta", "gs_cell_visibility",
@@ -129,6 +129,7 @@ _SIGS = {
     "gs_extract_delta": [_P, _P, _P, _I64, _F, _P, _P, _P, _P],
     "gs_extract_delta_noalloc": [_P, _P, _I64, _F, _P, _P, _P, _P],
     "gs_render_batch": [_P, C.POINTER(gs_scene), _P, _I32, _I64, _I64, _P, _P, _P],
+    "gs_render_batch_sized": [_P, C.POINTER(gs_scene), _P, C.POINTER(gs_camera), _I32, _I64, _P, _P, _P],
     "gs_train_step": [_P, _P, C.POINTER(gs_train_io), C.POINTER(gs_train_cfg), _P],
     "gs_train_graph_capture": [_P, _P, C.POINTER(gs_train_io), C.POINTER(gs_train_cfg), _P],
     "gs_graph_launch": [_P, _P],

@@ -109,8 +109,8 @@ FusedPlan plan_fused(void* base, int V, int64_t n, int64_t keys_cap, int64_t tot
         p.grad2d = c.take<float>((size_t)V * n * kGradStride);
         p.delta = c.take<char>(delta_scratch_bytes(n));
         p.fwd = c.take<uint8_t>(n > 0 ? n : 1);
-        p.order = c.take<uint32_t>(total_tiles > 0 ? total_tiles : 1);  // super-tiles never outnumber tiles
     }
+    p.order = c.take<uint32_t>(total_tiles > 0 ? total_tiles : 1);  // super-tiles never outnumber tiles
     p.bytes = c.off;
     return p;
 }
@@ -469,9 +469,12 @@ gs_status_t gs_apply_delta(gs_ctx* ctx, float* params, int64_t n, const uint8_t*
     return launch_check();
 }
 
-gs_status_t gs_render_batch(gs_ctx* ctx, const gs_scene* scene, const gs_camera* d_cams, int32_t n_requests,
-                            int64_t total_tiles, int64_t keys_cap, const float* bg, float* image,
-                            void* stream) {
+// n_super (> 0): the exact super-tile total of the views (checked by the view
+// table): the super-tile sort takes no more digits than it needs and the
+// compositing takes the longest tile lists first.
+static gs_status_t render_batch(gs_ctx* ctx, const gs_scene* scene, const gs_camera* d_cams, int32_t n_requests,
+                                int64_t total_tiles, int64_t n_super, int64_t keys_cap, const float* bg,
+                                float* image, void* stream) {
     if (!ctx || !scene || !d_cams || !image || bad_views(n_requests) || scene->n < 0 || total_tiles < 1 ||
         keys_cap < 0 || keys_cap >= (1LL << 32) || scene->sh_degree < 0 || scene->sh_degree > 3 ||
         (scene->n > 0 && !scene->params) || (int64_t)n_requests * scene->n >= (1LL << 32) || bad_dyn(scene->dyn) ||
@@ -485,7 +488,8 @@ gs_status_t gs_render_batch(gs_ctx* ctx, const gs_scene* scene, const gs_camera*
     SortScratch s;
     carve_sort_scratch(p.sort, n_requests, scene->n, keys_cap, total_tiles, &s);
     const float3 b = bg ? make_float3(bg[0], bg[1], bg[2]) : make_float3(0.f, 0.f, 0.f);
-    launch_view_table(d_cams, n_requests, ctx->tile, p.vt, total_tiles, ctx->d_status, st);
+    launch_view_table(d_cams, n_requests, ctx->tile, p.vt, total_tiles, ctx->d_status, st,
+                      n_super > 0 ? n_super : -1);
     const Dyn dyn = scene_dyn(ctx, scene->dyn, scene->precull, nullptr, scene->lighting, st);
     launch_project(scene->params, scene->n, scene->sh_degree, dyn, d_cams, p.vt, n_requests, ctx->tile, p.proj,
                    s.dkv[0], st, 0, -1, s.rects, kRecF4Compact);
@@ -493,10 +497,30 @@ gs_status_t gs_render_batch(gs_ctx* ctx, const gs_scene* scene, const gs_camera*
     CoarseLists cl;
     launch_bin_sort(p.proj, p.vt, n_requests, scene->n, keys_cap, total_tiles, ctx->binning, ctx->sort_bits, ctx->sort_items, s, true, nullptr,
                     p.vals, p.ranges, p.n_keys, ctx->d_status, ctx->sm_count, st, nullptr, nullptr, 0,
-                    scene->precull != nullptr, &cl, spin_only(ctx));
+                    scene->precull != nullptr, &cl, spin_only(ctx), n_super > 0 ? n_super : 0,
+                    n_super > 0 ? p.order : nullptr);
     launch_render_fwd(p.proj, p.vt, n_requests, scene->n, ctx->tile, ctx->raster_tpr, p.vals, p.ranges, b, image, nullptr,
                       nullptr, total_tiles, st, &cl, kRecF4Compact);
     return launch_check();
+}
+
+gs_status_t gs_render_batch(gs_ctx* ctx, const gs_scene* scene, const gs_camera* d_cams, int32_t n_requests,
+                            int64_t total_tiles, int64_t keys_cap, const float* bg, float* image,
+                            void* stream) {
+    return render_batch(ctx, scene, d_cams, n_requests, total_tiles, 0, keys_cap, bg, image, stream);
+}
+
+gs_status_t gs_render_batch_sized(gs_ctx* ctx, const gs_scene* scene, const gs_camera* d_cams,
+                                  const gs_camera* host_cams, int32_t n_requests, int64_t keys_cap,
+                                  const float* bg, float* image, void* stream) {
+    if (!ctx || !host_cams || bad_views(n_requests)) return GS_ERR_ARG;
+    int64_t ns = 0;
+    for (int v = 0; v < n_requests; ++v) {
+        if (host_cams[v].width < 1 || host_cams[v].height < 1) return GS_ERR_ARG;
+        ns += super_tiles_of(1, host_cams[v].width, host_cams[v].height, ctx->tile);
+    }
+    return render_batch(ctx, scene, d_cams, n_requests, tiles_of(host_cams, n_requests, ctx->tile), ns, keys_cap,
+                        bg, image, stream);
 }
 
 static void mark(void* const* events, int i, cudaStream_t st) {

@@ -118,7 +118,7 @@ class RenderServer:
         with torch.cuda.stream(slot.stream):
             d_cams = cameras_to_device(cams, self.params.device)
             gs_render_batch(slot.ctx, self.params, self.sh, d_cams, len(reqs), tt, keys, npix, bg=self.bg,
-                            image=slot.image, stream=slot.stream)
+                            image=slot.image, stream=slot.stream, host_cams=cams)
             rendered = torch.cuda.Event()
             rendered.record(slot.stream)
             slot.host[:3 * npix].copy_(slot.image[:3 * npix], non_blocking=True)

@@ -107,27 +107,35 @@ def test_train_step_chunk_lists_match_expanded_lists(name):
     b.ctx.close()
 
 
-@pytest.mark.parametrize("name", ["one_supertile_chunks", "ragged_edges", "opaque_early_stop", "tile8"])
+@pytest.mark.parametrize("name", ["one_supertile_chunks", "ragged_edges", "opaque_early_stop", "tile8",
+                                  "wide_key_320", "many_supertiles"])
 def test_render_batch_chunk_lists_match_expanded_lists(name):
+    """gs_render_batch with chunk-bitmap and expanded lists, and
+    gs_render_batch_sized (exact super-tile count: a 9-bit key in one pass for
+    wide_key_320, longest lists first up to 2048 super-tiles): the same image,
+    bit for bit."""
     import torch
     import paper_2604_02851_b300 as gs
+    from paper_2604_02851_b300.train import estimate_keys
     n, sh, V, W, H, sshift, lshift, tile, tpr, _ = CASES[name]
     planes = scene(n, sh, 23, sshift)
     planes[0, :, 3] += lshift
     cams = gi.ring_cameras(V, W, H)
     params = torch.from_numpy(np.ascontiguousarray(planes)).cuda()
     imgs = []
-    for mode in ("two_level", "direct"):
+    for mode, sized in (("two_level", False), ("direct", False), ("two_level", True)):
         ctx = gs.Context(0, 0, tile=tile, binning=mode, raster_threads=tpr)
-        cap = 1 << 22
+        cap = max(1 << 22, estimate_keys(ctx, params, sh, cams, slack=1.5))
         ctx.reserve(ctx.workspace_size(cams, n, cap))
         d_cams = gs.cameras_to_device(cams)
-        img = gs.gs_render_batch(ctx, params, sh, d_cams, V, ctx.total_tiles(cams), cap, gs.total_pixels(cams))
+        img = gs.gs_render_batch(ctx, params, sh, d_cams, V, ctx.total_tiles(cams), cap, gs.total_pixels(cams),
+                                 host_cams=cams if sized else None)
         torch.cuda.synchronize()
         assert ctx.status()[0] == 0
         imgs.append(img.cpu().numpy())
         ctx.close()
     np.testing.assert_array_equal(imgs[0], imgs[1])
+    np.testing.assert_array_equal(imgs[2], imgs[1])
 
 
 @pytest.mark.parametrize("case", ["all_culled", "one_gaussian"])
