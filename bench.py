@@ -80,13 +80,14 @@ def fp32_peak_tflops(sm_count: int, sm_mhz: float) -> float:
     return sm_count * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
 
 
-def phase_model(n, V, K, total_tiles, npix, sum_nc, n_changed, binning, passes, Kc, chunks, n_train=None):
+def phase_model(n, V, K, total_tiles, npix, sum_nc, n_changed, binning, passes, Kc, chunks, n_train=None,
+                depth_passes=4):
     """Algorithmic bytes (HBM) or FLOPs per launch of each phase.
 
     K fine (tile, Gaussian) entries; two-level binning moves Kc coarse
     (super-tile, Gaussian) entries through `passes` radix passes and writes
     the chunk bitmaps (2 KB per chunk); direct binning moves the K entries
-    through `passes` passes."""
+    through `passes` passes; the depth sort runs `depth_passes` passes."""
     vn = V * n
     nt = n if n_train is None else n_train  # Gaussians that are trained (the active pool)
     if binning == "two_level":
@@ -101,7 +102,9 @@ def phase_model(n, V, K, total_tiles, npix, sum_nc, n_changed, binning, passes, 
         # fused step, the 8-byte depth-sort item and the 4-byte tile rectangle
         # written
         "project": ("hbm", n * 240 + vn * (48 + 8 + 4)),
-        "depth_sort": ("hbm", vn * (4 * 16 + 4)),
+        # the key histogram reads 4 bytes, each pass reads and writes an
+        # 8-byte item
+        "depth_sort": ("hbm", vn * (depth_passes * 16 + 4)),
         "emit": ("hbm", emit),
         "tile_sort": ("hbm", sort),
         "render_fwd": ("alu", sum_nc * RASTER_FWD_FLOP_PER_FRAGMENT),
@@ -209,6 +212,18 @@ def replica_throughput(my_ms: float, steps: int, world: int, device):
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
     total_ms = float(t.item())
     return total_ms, world * steps / (total_ms / 1e3)
+
+
+def depth_passes(torch, proj, V, n):
+    """Radix passes the depth sort runs on a projection: three when the
+    visible Gaussians' keys (the float bits of their depths) span fewer than
+    2^24 - 1 values, since it then orders key - smallest key, else four."""
+    b = proj.view(torch.int32).view(V * n, 16)
+    vis = b[:, 14] > 0
+    if not bool(vis.any().item()):
+        return 4
+    k = b[:, 2][vis].to(torch.int64) & 0xFFFFFFFF
+    return 3 if int((k.max() - k.min()).item()) < 0xFFFFFF else 4
 
 
 def coarse_work(torch, proj, V, n):
@@ -767,6 +782,7 @@ def run_ours(args, rank, world, local_rank):
     K = int(nk.item())
     sum_nc = int(nc.to(torch.int64).sum().item())
     Kc = coarse_work(torch, proj, V, n)
+    dpasses = depth_passes(torch, proj, V, n)
     st_px = args.tile * 8
     n_super = sum(((int(w) + st_px - 1) // st_px) * ((int(h) + st_px - 1) // st_px)
                   for w, h in zip(packed["width"], packed["height"]))
@@ -780,7 +796,7 @@ def run_ours(args, rank, world, local_rank):
         tile_passes = 1 if args.sort_bits < sbits <= 9 else math.ceil(sbits / args.sort_bits)
     del wc_params
     model = phase_model(n, V, K, tr.total_tiles, tr.npix, sum_nc, changed, args.binning, tile_passes, Kc, chunks,
-                        n_train=params.shape[1])
+                        n_train=params.shape[1], depth_passes=dpasses)
     hbm_peak, peak_src = _peaks()
     # FP32 peak from the queried SM count at the median SM clock sampled in the timed region
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
@@ -879,7 +895,7 @@ def run_ours(args, rank, world, local_rank):
                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                "config": {"workload": args.workload, "gaussians": n, "sh_degree": sh, "views": V,
                           "resolution": [W, H], "keys_per_step": K, "coarse_keys_per_step": Kc,
-                          "keys_cap": keys_cap, "tile": args.tile,
+                          "keys_cap": keys_cap, "tile": args.tile, "depth_sort_passes": dpasses,
                           "dynamics": "16 rigid objects, new SE(3) pose per frame (spin <= 2 deg/frame, "
                                       "sinusoidal translation 0.1), light at 45 deg zenith turning 1 deg/frame; "
                                       + ("SH-lighting product with per-Gaussian light visibility"

@@ -489,10 +489,10 @@ static gs_status_t render_batch(gs_ctx* ctx, const gs_scene* scene, const gs_cam
     carve_sort_scratch(p.sort, n_requests, scene->n, keys_cap, total_tiles, &s);
     const float3 b = bg ? make_float3(bg[0], bg[1], bg[2]) : make_float3(0.f, 0.f, 0.f);
     launch_view_table(d_cams, n_requests, ctx->tile, p.vt, total_tiles, ctx->d_status, st,
-                      n_super > 0 ? n_super : -1);
+                      n_super > 0 ? n_super : -1, s.drange);
     const Dyn dyn = scene_dyn(ctx, scene->dyn, scene->precull, nullptr, scene->lighting, st);
     launch_project(scene->params, scene->n, scene->sh_degree, dyn, d_cams, p.vt, n_requests, ctx->tile, p.proj,
-                   s.dkv[0], st, 0, -1, s.rects, kRecF4Compact);
+                   s.dkv[0], st, 0, -1, s.rects, kRecF4Compact, s.drange);
     // two-level binning leaves the per-tile lists in chunk-bitmap form
     CoarseLists cl;
     launch_bin_sort(p.proj, p.vt, n_requests, scene->n, keys_cap, total_tiles, ctx->binning, ctx->sort_bits, ctx->sort_items, s, true, nullptr,
@@ -568,7 +568,7 @@ gs_status_t gs_train_step_events(gs_ctx* ctx, const gs_camera* d_cams, const gs_
     carve_sort_scratch(p.sort, V, n, cfg->keys_cap, tt, &s);
     const float3 b = make_float3(cfg->bg[0], cfg->bg[1], cfg->bg[2]);
     mark(ev, 0, st);
-    launch_view_table(d_cams, V, B, p.vt, tt, ctx->d_status, st, ns);
+    launch_view_table(d_cams, V, B, p.vt, tt, ctx->d_status, st, ns, s.drange);
     const Dyn dyn = scene_dyn(ctx, cfg->dyn, cfg->precull, p.fwd, cfg->lighting, st);
     if (!(phases & GS_TRAIN_GRADIENT)) {
         // update only: the gradient of the caller's io->grads; the phase marks
@@ -576,7 +576,7 @@ gs_status_t gs_train_step_events(gs_ctx* ctx, const gs_camera* d_cams, const gs_
         // the Gaussians it keeps (Adam leaves the others).
         if (cfg->precull)
             launch_project(io->params, na, cfg->sh_degree, dyn, d_cams, p.vt, V, B, p.proj, s.dkv[0], st, 0, n,
-                           s.rects, kRecF4Compact);
+                           s.rects, kRecF4Compact, s.drange);
         for (int e = 1; e <= 8; ++e) mark(ev, e, st);
         gs_adam_cfg ac = cfg->adam;
         ac.d_step = io->d_step;
@@ -587,10 +587,10 @@ gs_status_t gs_train_step_events(gs_ctx* ctx, const gs_camera* d_cams, const gs_
         return launch_check();
     }
     launch_project(io->params, na, cfg->sh_degree, dyn, d_cams, p.vt, V, B, p.proj, s.dkv[0], st, 0, n, s.rects,
-                   kRecF4Compact);
+                   kRecF4Compact, s.drange);
     if (cfg->n_frozen > 0)
         launch_project(io->frozen, cfg->n_frozen, cfg->sh_degree, dyn, d_cams, p.vt, V, B, p.proj, s.dkv[0], st,
-                       na, n, s.rects, kRecF4Compact);
+                       na, n, s.rects, kRecF4Compact, s.drange);
     mark(ev, 1, st);
     // two-level binning leaves the per-tile lists in chunk-bitmap form, which
     // both raster kernels walk
@@ -661,9 +661,9 @@ gs_status_t gs_autotune(gs_ctx* ctx, const gs_scene* scene, const gs_camera* d_c
     // ev (may be null): recorded before compositing, between compositing and
     // its adjoint, and after the adjoint
     auto run = [&](cudaEvent_t* ev) {
-        launch_view_table(d_cams, V, B, p.vt, tt, ctx->d_status, st, ns);
+        launch_view_table(d_cams, V, B, p.vt, tt, ctx->d_status, st, ns, s.drange);
         launch_project(scene->params, n, scene->sh_degree, dyn, d_cams, p.vt, V, B, p.proj, s.dkv[0], st, 0, -1, s.rects,
-                       kRecF4Compact);
+                       kRecF4Compact, s.drange);
         CoarseLists cl;
         launch_bin_sort(p.proj, p.vt, V, n, keys_cap, tt, ctx->binning, ctx->sort_bits, ctx->sort_items, s, true,
                         nullptr, p.vals, p.ranges, p.n_keys, ctx->d_status, ctx->sm_count, st, nullptr, nullptr, 0,

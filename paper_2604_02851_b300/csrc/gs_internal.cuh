@@ -147,8 +147,48 @@ __device__ __forceinline__ bool look_back(unsigned long long* lb, int64_t slot, 
 
 // expect_tiles / expect_super (>= 0): the tile and super-tile totals the
 // caller planned for; a different total is reported as GS_ERR_ARG.
+// drange (may be null): the depth-key range the projection then accumulates,
+// reset here ({all ones, 0}).
 void launch_view_table(const gs_camera* d_cams, int V, int tile, ViewInfo* vt,
-                       long long expect_tiles, DevStatus* status, cudaStream_t st, long long expect_super = -1);
+                       long long expect_tiles, DevStatus* status, cudaStream_t st, long long expect_super = -1,
+                       uint32_t* drange = nullptr);
+
+// ------------------------------------------------------------ depth-key range
+// drange[0] / drange[1]: the smallest / largest depth-sort key (float32 bits
+// of the depth) of the visible (view, Gaussian) items, accumulated by the
+// kernels that write the items.  When the keys span fewer than 2^24 - 1
+// values ("narrow"), the depth sort orders key - smallest instead (culled
+// items: 2^24 - 1): the same order, with a top byte of zero, so the fourth
+// 8-bit pass would not move anything and is skipped.
+struct DepthXform {
+    uint32_t mn;
+    bool narrow;
+};
+__device__ __forceinline__ DepthXform depth_xform(const uint32_t* drange) {
+    DepthXform x;
+    x.mn = 0;
+    x.narrow = false;
+    if (drange) {
+        const uint32_t mn = drange[0], mx = drange[1];
+        x.mn = mn;
+        x.narrow = mn <= mx && mx - mn < 0xFFFFFFu;
+    }
+    return x;
+}
+__device__ __forceinline__ uint32_t xform_key(uint32_t k, DepthXform x) {
+    return !x.narrow ? k : (k == 0xFFFFFFFFu ? 0xFFFFFFu : k - x.mn);
+}
+// Adds a thread's range [lo, hi] (lo > hi: none) of visible keys: reduced over
+// the warp's live threads, then an atomic only where it widens the range.
+__device__ __forceinline__ void depth_range_add(uint32_t* drange, uint32_t lo, uint32_t hi) {
+    const unsigned am = __activemask();
+    lo = __reduce_min_sync(am, lo);
+    hi = __reduce_max_sync(am, hi);
+    if ((int)(threadIdx.x & 31) == __ffs(am) - 1 && lo <= hi) {
+        if (lo < *reinterpret_cast<volatile uint32_t*>(drange)) atomicMin(drange, lo);
+        if (hi > *reinterpret_cast<volatile uint32_t*>(drange + 1)) atomicMax(drange + 1, hi);
+    }
+}
 
 // Super-tiles of views of one size (kSuper x kSuper tiles each).
 inline int64_t super_tiles_of(int V, int width, int height, int tile) {
@@ -213,7 +253,8 @@ inline Dyn make_dyn(const gs_dynamics* d, const gs_precull* pc = nullptr, uint8_
 // array; dynamics arrays are indexed by g_off + g.
 void launch_project(const float* params, int64_t n, int sh_degree, const Dyn& dyn, const gs_camera* d_cams,
                     const ViewInfo* vt, int V, int tile, float* proj, uint64_t* depth_kv, cudaStream_t st,
-                    int64_t g_off = 0, int64_t n_out = -1, uint2* rects = nullptr, int rec4 = kRecF4);
+                    int64_t g_off = 0, int64_t n_out = -1, uint2* rects = nullptr, int rec4 = kRecF4,
+                    uint32_t* drange = nullptr);
 
 // L2 eviction-priority policies for cache-hinted loads and stores.
 __device__ __forceinline__ uint64_t l2_policy_evict_last() {
@@ -271,6 +312,7 @@ struct SortScratch {
     unsigned long long* lookback;  // [4][max_tiles][256]
     int64_t max_sort_tiles;    // per pass
     uint32_t* d_count_depth;   // depth-sort items (V*n, or those kept by the compaction)
+    uint32_t* drange;          // [2] range of the visible depth keys (depth_xform)
     uint2* rects;              // [V*n] tile rectangle of each record: (x0 | y0 << 16, x1 | y1 << 16),
                                // or as uint32 [V*n] in the 4-byte form when vt[V].rect32; kept in
                                // L2 (evict-last) from the projection to the emission

@@ -212,7 +212,8 @@ template <int D, bool LIT>
 __global__ void __launch_bounds__(256, 4)
 k_project(const float4* __restrict__ P, int64_t n, int64_t g_off, int64_t n_out, Dyn dyn,
           const gs_camera* __restrict__ cams, const ViewInfo* __restrict__ vt, int V, int tile,
-          float4* __restrict__ proj, uint64_t* __restrict__ dkv, uint2* __restrict__ rects, int rec4) {
+          float4* __restrict__ proj, uint64_t* __restrict__ dkv, uint2* __restrict__ rects, int rec4,
+          uint32_t* __restrict__ drange) {
     const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     extern __shared__ float s_lt[];
     bool staged = false;
@@ -273,6 +274,7 @@ k_project(const float4* __restrict__ P, int64_t n, int64_t g_off, int64_t n_out,
         const float* lt = staged ? s_lt + lit_group(dyn, g_off + g) * kStageStride : lit_row(dyn, g_off + g);
         relit_rgb<NB>(sh, lt, lit_vis(dyn, g_off + g), lrgb, lmask);
     }
+    uint32_t klo = 0xFFFFFFFFu, khi = 0u;  // range of this thread's visible depth keys
     for (int v = 0; v < V; ++v) {
         const Cam C = load_cam(cams + v);
         const int64_t rec = (int64_t)v * n_out + g_off + g;
@@ -350,12 +352,15 @@ k_project(const float4* __restrict__ P, int64_t n, int64_t g_off, int64_t n_out,
             out[3] = make_float4(__uint_as_float(lo), __uint_as_float(hi),
                                  __uint_as_float((uint32_t)((x1 - x0) * (y1 - y0))), 0.f);
         if (dkv) dkv[rec] = ((uint64_t)__float_as_uint(Vg.tz) << 32) | (uint32_t)rec;
+        klo = min(klo, __float_as_uint(Vg.tz));
+        khi = max(khi, __float_as_uint(Vg.tz));
         // the emission gathers the rectangle in depth order: kept in L2
         if (rects) {
             if (rect32) st_hint(reinterpret_cast<uint32_t*>(rects) + rec, rect32_pack(lo, hi), l2_policy_evict_last());
             else st_hint(rects + rec, make_uint2(lo, hi), l2_policy_evict_last());
         }
     }
+    if (drange) depth_range_add(drange, klo, khi);
 }
 
 // ------------------------------------------------------------------ adjoint
@@ -598,8 +603,13 @@ k_project_bwd(const float4* __restrict__ P, int64_t n, int64_t n_out, Dyn dyn, c
 }
 
 __global__ void k_view_table(const gs_camera* __restrict__ cams, int V, int tile, ViewInfo* vt,
-                             long long expect_tiles, long long expect_super, DevStatus* status) {
+                             long long expect_tiles, long long expect_super, DevStatus* status,
+                             uint32_t* drange) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    if (drange) {
+        drange[0] = 0xFFFFFFFFu;
+        drange[1] = 0u;
+    }
     int64_t toff = 0, poff = 0, soff = 0;
     for (int v = 0; v < V; ++v) {
         ViewInfo vi;
@@ -635,13 +645,13 @@ __global__ void k_view_table(const gs_camera* __restrict__ cams, int V, int tile
 }  // namespace
 
 void launch_view_table(const gs_camera* d_cams, int V, int tile, ViewInfo* vt, long long expect_tiles,
-                       DevStatus* status, cudaStream_t st, long long expect_super) {
-    k_view_table<<<1, 32, 0, st>>>(d_cams, V, tile, vt, expect_tiles, expect_super, status);
+                       DevStatus* status, cudaStream_t st, long long expect_super, uint32_t* drange) {
+    k_view_table<<<1, 32, 0, st>>>(d_cams, V, tile, vt, expect_tiles, expect_super, status, drange);
 }
 
 void launch_project(const float* params, int64_t n, int sh_degree, const Dyn& dyn, const gs_camera* d_cams,
                     const ViewInfo* vt, int V, int tile, float* proj, uint64_t* depth_kv, cudaStream_t st,
-                    int64_t g_off, int64_t n_out, uint2* rects, int rec4) {
+                    int64_t g_off, int64_t n_out, uint2* rects, int rec4, uint32_t* drange) {
     if (n <= 0) return;
     if (n_out < 0) n_out = n;
     const int threads = 256;
@@ -651,9 +661,9 @@ void launch_project(const float* params, int64_t n, int sh_degree, const Dyn& dy
     const bool lit = dyn.lit_tab != nullptr;
     const size_t smem = lit && lit_groups(dyn) <= kStageGroups ? sizeof(float) * lit_groups(dyn) * kStageStride : 0;
 #define GS_PROJ(DD)                                                                                              \
-    (lit ? k_project<DD, true><<<blocks, threads, smem, st>>>(P, n, g_off, n_out, dyn, d_cams, vt, V, tile, out, depth_kv, rects, rec4) \
+    (lit ? k_project<DD, true><<<blocks, threads, smem, st>>>(P, n, g_off, n_out, dyn, d_cams, vt, V, tile, out, depth_kv, rects, rec4, drange) \
          : k_project<DD, false><<<blocks, threads, sizeof(float4) * threads * ((3 * (DD + 1) * (DD + 1) + 3) / 4), st>>>( \
-               P, n, g_off, n_out, dyn, d_cams, vt, V, tile, out, depth_kv, rects, rec4))
+               P, n, g_off, n_out, dyn, d_cams, vt, V, tile, out, depth_kv, rects, rec4, drange))
     switch (sh_degree) {
         case 0: GS_PROJ(0); break;
         case 1: GS_PROJ(1); break;

@@ -61,13 +61,14 @@ __device__ __forceinline__ int64_t clamp_count(const uint32_t* d_count, int64_t 
 template <int BITS>
 __global__ void __launch_bounds__(kThreads)
 k_hist(const uint64_t* __restrict__ items, const uint32_t* d_count, int64_t cap, int passes,
-       uint32_t* __restrict__ hist) {
+       uint32_t* __restrict__ hist, const uint32_t* __restrict__ drange) {
     constexpr int R = 1 << BITS;
     __shared__ uint32_t sh[kWarps][kMaxPasses][R];
     for (int i = threadIdx.x; i < kWarps * kMaxPasses * R; i += kThreads) (&sh[0][0][0])[i] = 0;
     __syncthreads();
     const int64_t count = clamp_count(d_count, cap);
     const int w = threadIdx.x / 32;
+    const DepthXform xf = depth_xform(drange);  // the keys the depth passes order
     // eight loads of a thread in flight per round: the pass is bound by
     // memory-level parallelism, not by the shared-memory atomics
     constexpr int U = 8;
@@ -77,7 +78,7 @@ k_hist(const uint64_t* __restrict__ items, const uint32_t* d_count, int64_t cap,
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const int64_t i = i0 + u * kThreads;
-            k[u] = i < count ? (uint32_t)(items[i] >> 32) : 0u;
+            k[u] = i < count ? xform_key((uint32_t)(items[i] >> 32), xf) : 0u;
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
@@ -134,15 +135,20 @@ __global__ void k_hist_scan(uint32_t* hist, int passes) {
 // ITEMS packed (key << 32 | value) items per thread, 256 threads: a tile of
 // 256*ITEMS.  Outputs: out (packed, for the next pass) and/or, on the last
 // pass of the tile-key sort, vout (values), kout (keys, may be null) and the
-// per-key [start, end) ranges.
+// per-key [start, end) ranges.  Depth sort (drange): dmode 1, the first pass,
+// replaces each key by the key it orders (xform_key), which the later passes
+// then read; dmode 2, the last pass, does nothing when the keys are narrow
+// (their top digit is zero: the pass would not move an item).
 template <int BITS, int ITEMS>
 __global__ void __launch_bounds__(kThreads, 3)
 k_onesweep(const uint64_t* __restrict__ in, uint64_t* __restrict__ out, uint32_t* __restrict__ kout,
            uint32_t* __restrict__ vout, const uint32_t* d_count, int64_t cap, int shift, uint32_t kmask,
            const uint32_t* __restrict__ digit_off, unsigned long long* __restrict__ lookback,
            uint32_t* tile_counter, uint32_t* __restrict__ ranges, DevStatus* status, long long spin,
-           int64_t withhold) {
+           int64_t withhold, const uint32_t* __restrict__ drange, int dmode) {
     constexpr int R = 1 << BITS;
+    const DepthXform xf = depth_xform(dmode ? drange : nullptr);
+    if (dmode == 2 && xf.narrow) return;  // uniform over the grid
     constexpr uint32_t MASK = R - 1;
     constexpr int TILE = kThreads * ITEMS;
     __shared__ uint64_t s_items[TILE];
@@ -180,6 +186,13 @@ k_onesweep(const uint64_t* __restrict__ in, uint64_t* __restrict__ out, uint32_t
         } else {
 #pragma unroll
             for (int j = 0; j < ITEMS; ++j) item[j] = (j * 32 < wrem) ? src[j * 32] : ~0ULL;
+        }
+        if (dmode == 1 && xf.narrow) {
+            // (missing tail items become the culled key 2^24 - 1: still the
+            // last run of every digit, at staged positions >= valid)
+#pragma unroll
+            for (int j = 0; j < ITEMS; ++j)
+                item[j] = ((uint64_t)xform_key((uint32_t)(item[j] >> 32), xf) << 32) | (uint32_t)item[j];
         }
         // ---- stable rank within the warp, item order j*32 + lane: the lanes
         //      holding the same digit are found with one ballot per digit bit;
@@ -294,6 +307,10 @@ k_onesweep(const uint64_t* __restrict__ in, uint64_t* __restrict__ out, uint32_t
 
 // ------------------------------------------------------------ utilities
 __global__ void k_set_u32(uint32_t* p, uint32_t v) { *p = v; }
+__global__ void k_range_reset(uint32_t* drange) {
+    drange[0] = 0xFFFFFFFFu;
+    drange[1] = 0u;
+}
 
 // Zero `radix` u64 words per look-back tile for each of `passes` arrays, for
 // the tiles that the device count implies.
@@ -329,13 +346,15 @@ __global__ void k_clear_u32(uint32_t* p, int64_t n) {
 
 // Depth-sort input from projection records: key = float32 depth bits of a
 // visible (view, Gaussian), all-ones when culled; value = record index.
+// The range of the visible keys goes to drange (reset before).
 __global__ void k_depth_keys(const uint4* __restrict__ proj, int64_t items, const ViewInfo* __restrict__ vt, int V,
-                             uint64_t* __restrict__ kv, uint2* __restrict__ rects) {
+                             uint64_t* __restrict__ kv, uint2* __restrict__ rects, uint32_t* __restrict__ drange) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= items) return;
     const uint4 r3 = proj[i * 4 + 3];
     const uint32_t key = r3.z ? proj[i * 4].z : 0xFFFFFFFFu;
     kv[i] = ((uint64_t)key << 32) | (uint32_t)i;
+    depth_range_add(drange, r3.z ? key : 0xFFFFFFFFu, r3.z ? key : 0u);
     if (vt[V].rect32)
         st_hint(reinterpret_cast<uint32_t*>(rects) + i, r3.z ? rect32_pack(r3.x, r3.y) : 1u, l2_policy_evict_last());
     else
@@ -430,7 +449,8 @@ __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t x, int lane) {
 // and more resident blocks hide that better than fewer at 64 registers.
 template <int BITS>
 __global__ void __launch_bounds__(kEmitThreads, 8)
-k_emit(const uint64_t* __restrict__ dsorted, int64_t total, int64_t n, const uint2* __restrict__ rects,
+k_emit(const uint64_t* __restrict__ dsorted, const uint64_t* __restrict__ dsorted_narrow,
+       const uint32_t* __restrict__ drange, int64_t total, int64_t n, const uint2* __restrict__ rects,
        const ViewInfo* __restrict__ vt, int64_t cap, uint64_t* __restrict__ kv,
        unsigned long long* __restrict__ lookback, uint32_t* block_counter, uint32_t* d_num_keys,
        int passes, uint32_t* __restrict__ hist, int sshift, unsigned long long* fine_total, uint32_t key_bound,
@@ -446,6 +466,9 @@ k_emit(const uint64_t* __restrict__ dsorted, int64_t total, int64_t n, const uin
     __shared__ unsigned long long s_excl;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const bool rect32 = vt[V].rect32 != 0;
+    // narrow depth keys: the depth sort skipped its last pass and ended in
+    // the other buffer
+    if (depth_xform(drange).narrow) dsorted = dsorted_narrow;
     for (int i = threadIdx.x; i < HP * R; i += kEmitThreads) (&s_hist[0][0])[i] = 0;
     if (threadIdx.x == 0) s_blk = atomicAdd(block_counter, 1u);
     __syncthreads();
@@ -1029,7 +1052,7 @@ template <int BITS, int ITEMS>
 void onesweep_passes(uint64_t* const buf[2], uint64_t* last_out, uint32_t* kout, uint32_t* vout,
                      const uint32_t* d_count, int64_t cap, int passes, const SortScratch& s, uint32_t* ranges,
                      DevStatus* status, int sm_count, cudaStream_t st, WaitCfg wait,
-                     uint32_t kmask = 0xFFFFFFFFu) {
+                     uint32_t kmask = 0xFFFFFFFFu, const uint32_t* drange = nullptr) {
     constexpr int R = 1 << BITS;
     k_clear_lookback<<<sm_count * 4, 256, 0, st>>>(s.lookback, d_count, cap, R, passes, s.max_sort_tiles,
                                                    kThreads * ITEMS);
@@ -1041,13 +1064,14 @@ void onesweep_passes(uint64_t* const buf[2], uint64_t* last_out, uint32_t* kout,
         k_onesweep<BITS, ITEMS><<<sm_count * 3, kThreads, 0, st>>>(
             src, dst, last ? kout : nullptr, last ? vout : nullptr, d_count, cap, p * BITS, kmask, s.hist + p * kMaxR,
             s.lookback + (int64_t)p * s.max_sort_tiles * R, s.counters + p, last ? ranges : nullptr, status,
-            wait.spin, last ? wait.withhold : -1);
+            wait.spin, last ? wait.withhold : -1, drange,
+            !drange ? 0 : (p == 0 ? 1 : (last && p == 3 ? 2 : 0)));
     }
 }
 
 // Emission + tile-key sort + ranges, for one digit width.
 template <int BITS, int ITEMS>
-void emit_and_sort(const uint64_t* dsorted, int64_t items, const uint32_t* d_items, int64_t n, const uint4* pr,
+void emit_and_sort(const uint64_t* dsorted, const uint64_t* dsorted_narrow, int64_t items, const uint32_t* d_items, int64_t n, const uint4* pr,
                    const ViewInfo* vt, int V,
                    int64_t keys_cap, int key_bits, const SortScratch& s, uint32_t* sorted_keys,
                    uint32_t* sorted_vals, uint32_t* ranges, int64_t total_tiles, uint32_t* d_num_keys,
@@ -1058,7 +1082,7 @@ void emit_and_sort(const uint64_t* dsorted, int64_t items, const uint32_t* d_ite
     cudaMemsetAsync(s.hist, 0, sizeof(uint32_t) * kMaxPasses * kMaxR, st);
     cudaMemsetAsync(s.counters, 0, sizeof(uint32_t) * 8, st);
     cudaMemsetAsync(s.emit_lookback, 0, sizeof(unsigned long long) * (size_t)nblk, st);
-    k_emit<BITS><<<(unsigned)nblk, kEmitThreads, 0, st>>>(dsorted, items, n, s.rects, vt, keys_cap, s.tkv[0],
+    k_emit<BITS><<<(unsigned)nblk, kEmitThreads, 0, st>>>(dsorted, dsorted_narrow, s.drange, items, n, s.rects, vt, keys_cap, s.tkv[0],
                                                           s.emit_lookback, s.counters + 7, d_num_keys, passes,
                                                           s.hist, 0, nullptr, (uint32_t)total_tiles, d_items,
                                                           status, V, wait.spin);
@@ -1075,7 +1099,7 @@ void emit_and_sort(const uint64_t* dsorted, int64_t items, const uint32_t* d_ite
 // Two-level binning: coarse emission and super-tile sort, then the fine
 // expansion into the caller's arrays and ranges.
 template <int BITS, int ITEMS>
-void emit_two_level(const uint64_t* dsorted, int64_t items, const uint32_t* d_items, int64_t n, const uint4* pr,
+void emit_two_level(const uint64_t* dsorted, const uint64_t* dsorted_narrow, int64_t items, const uint32_t* d_items, int64_t n, const uint4* pr,
                     const ViewInfo* vt, int V,
                     int64_t keys_cap, const SortScratch& s, uint32_t* sorted_keys,
                     uint32_t* sorted_vals, uint32_t* ranges, int64_t total_tiles, uint32_t* d_num_keys,
@@ -1095,7 +1119,7 @@ void emit_two_level(const uint64_t* dsorted, int64_t items, const uint32_t* d_it
     cudaMemsetAsync(s.counters, 0, sizeof(uint32_t) * 8, st);
     cudaMemsetAsync(s.emit_lookback, 0, sizeof(unsigned long long) * (size_t)nblk, st);
     cudaMemsetAsync(s.d_fine_total, 0, sizeof(unsigned long long), st);
-    k_emit<BITS><<<(unsigned)nblk, kEmitThreads, 0, st>>>(dsorted, items, n, s.rects, vt, keys_cap, s.tkv[0],
+    k_emit<BITS><<<(unsigned)nblk, kEmitThreads, 0, st>>>(dsorted, dsorted_narrow, s.drange, items, n, s.rects, vt, keys_cap, s.tkv[0],
                                                           s.emit_lookback, s.counters + 7, s.d_count_coarse,
                                                           passes, s.hist, kSuperShift, s.d_fine_total,
                                                           (uint32_t)n_super, d_items, status, V, wait.spin);
@@ -1189,6 +1213,7 @@ void carve_sort_scratch(char* base, int V, int64_t n, int64_t keys_cap, int64_t 
     s->max_sort_tiles = (std::max(items, keys_cap) + kMinTileKeys - 1) / kMinTileKeys + 1;
     s->lookback = c.take<unsigned long long>((size_t)kMaxPasses * s->max_sort_tiles * 256);
     s->d_count_depth = c.take<uint32_t>(1);
+    s->drange = c.take<uint32_t>(2);
     s->rects = c.take<uint2>(items);
     s->keep_sums = c.take<uint32_t>((items + kKeepBlock - 1) / kKeepBlock + 1);
     s->max_chunks = keys_cap / kFineChunk + ns + 1;
@@ -1222,10 +1247,16 @@ void launch_bin_sort(const float* proj, const ViewInfo* vt, int V, int64_t n, in
     }
     // 1. depth sort of all (view, Gaussian) pairs: 32-bit keys, 4 passes of
     //    8-bit digits ending back in dkv[0]
-    if (!depth_ready)
-        k_depth_keys<<<(unsigned)((items + 255) / 256), 256, 0, st>>>(pr, items, vt, V, s.dkv[0], s.rects);
-    // with compaction the kept items move to dkv[1] and the sort ends there
+    if (!depth_ready) {
+        k_range_reset<<<1, 1, 0, st>>>(s.drange);
+        k_depth_keys<<<(unsigned)((items + 255) / 256), 256, 0, st>>>(pr, items, vt, V, s.dkv[0], s.rects,
+                                                                     s.drange);
+    }
+    // with compaction the kept items move to dkv[1] and the sort ends there;
+    // with narrow keys (s.drange) the last pass is skipped and the sort ends
+    // in the other buffer (dsorted_narrow)
     const uint64_t* dsorted = s.dkv[0];
+    const uint64_t* dsorted_narrow = s.dkv[1];
     const uint32_t* d_items = nullptr;
     cudaMemsetAsync(s.hist, 0, sizeof(uint32_t) * kMaxPasses * kMaxR, st);
     cudaMemsetAsync(s.counters, 0, sizeof(uint32_t) * 8, st);
@@ -1234,18 +1265,19 @@ void launch_bin_sort(const float* proj, const ViewInfo* vt, int V, int64_t n, in
         k_keep_count<<<(unsigned)nb, 256, 0, st>>>(s.dkv[0], items, s.keep_sums);
         launch_scan_sums(s.keep_sums, nb, s.d_count_depth, -1, nullptr, st);
         k_keep_emit<<<(unsigned)nb, 256, 0, st>>>(s.dkv[0], items, s.keep_sums, s.dkv[1]);
-        k_hist<8><<<sm_count * 4, kThreads, 0, st>>>(s.dkv[1], s.d_count_depth, items, 4, s.hist);
+        k_hist<8><<<sm_count * 4, kThreads, 0, st>>>(s.dkv[1], s.d_count_depth, items, 4, s.hist, s.drange);
         uint64_t* const dbuf[2] = {s.dkv[1], s.dkv[0]};
         onesweep_passes<8, 16>(dbuf, s.dkv[1], nullptr, nullptr, s.d_count_depth, items, 4, s, nullptr, status,
-                               sm_count, st, dwait);
+                               sm_count, st, dwait, 0xFFFFFFFFu, s.drange);
         dsorted = s.dkv[1];
+        dsorted_narrow = s.dkv[0];
         d_items = s.d_count_depth;
     } else {
         k_set_u32<<<1, 1, 0, st>>>(s.d_count_depth, (uint32_t)items);
-        k_hist<8><<<sm_count * 4, kThreads, 0, st>>>(s.dkv[0], s.d_count_depth, items, 4, s.hist);
+        k_hist<8><<<sm_count * 4, kThreads, 0, st>>>(s.dkv[0], s.d_count_depth, items, 4, s.hist, s.drange);
         uint64_t* const dbuf[2] = {s.dkv[0], s.dkv[1]};
         onesweep_passes<8, 16>(dbuf, s.dkv[0], nullptr, nullptr, s.d_count_depth, items, 4, s, nullptr, status,
-                               sm_count, st, dwait);
+                               sm_count, st, dwait, 0xFFFFFFFFu, s.drange);
     }
     if (mark) mark(events, first_event, st);
     // 2. emission in depth order with the key histograms, 3. stable sort by
@@ -1257,7 +1289,7 @@ void launch_bin_sort(const float* proj, const ViewInfo* vt, int V, int64_t n, in
     while ((1LL << sbits) < (n_super > 0 ? n_super : total_tiles)) ++sbits;
     if (binning != kBinDirect && bits <= kMaxCoarseKeyBits && sbits > sort_bits && sbits <= kWideBits) {
         // a super-tile key of 9 bits: one wide pass instead of two
-        emit_two_level<kWideBits, kWideItems>(dsorted, items, d_items, n, pr, vt, V, keys_cap, s, sorted_keys,
+        emit_two_level<kWideBits, kWideItems>(dsorted, dsorted_narrow, items, d_items, n, pr, vt, V, keys_cap, s, sorted_keys,
                                               sorted_vals, ranges, total_tiles, d_num_keys, status, sm_count, st,
                                               mark, events, first_event + 1, coarse, wait, n_super, order);
         return;
@@ -1265,12 +1297,12 @@ void launch_bin_sort(const float* proj, const ViewInfo* vt, int V, int64_t n, in
 #define GS_EMIT_SORT(B, I)                                                                                      \
     do {                                                                                                        \
         if (binning == kBinDirect || bits > kMaxCoarseKeyBits)                                                  \
-            emit_and_sort<B, I>(dsorted, items, d_items, n, pr, vt, V, keys_cap, bits, s, sorted_keys, sorted_vals, \
+            emit_and_sort<B, I>(dsorted, dsorted_narrow, items, d_items, n, pr, vt, V, keys_cap, bits, s, sorted_keys, sorted_vals, \
                                 ranges,                                                                         \
                                 total_tiles, d_num_keys, status, sm_count, st, mark, events, first_event + 1,   \
                                 wait);                                                                          \
         else                                                                                                    \
-            emit_two_level<B, I>(dsorted, items, d_items, n, pr, vt, V, keys_cap, s, sorted_keys, sorted_vals,  \
+            emit_two_level<B, I>(dsorted, dsorted_narrow, items, d_items, n, pr, vt, V, keys_cap, s, sorted_keys, sorted_vals,  \
                                  ranges,                                                                        \
                                  total_tiles, d_num_keys, status, sm_count, st, mark, events, first_event + 1,  \
                                  coarse, wait, n_super, order);                                                 \
