@@ -118,3 +118,42 @@ def test_fused_paths_either_key_form_match_oracle_image(name, mode):
     assert rctx.status()[0] == 0
     assert rel_l2(img.cpu().numpy().reshape(ref.shape), ref) <= 1e-4
     rctx.close()
+
+
+@pytest.mark.parametrize("span", [NARROW - 1, NARROW])
+def test_depth_sort_at_the_narrow_limit(span):
+    """One visible Gaussian's depth moved so that the visible keys span
+    exactly 2^24 - 2 values (the largest narrow span: the culled key
+    2^24 - 1 still sorts after every visible one) or 2^24 - 1 (the smallest
+    wide span): gs_bin_sort gives the oracle's lists either way."""
+    import torch
+    import paper_2604_02851_b300 as gs
+    planes = SCENES["narrow"]()
+    cams = gi.ring_cameras(V, W, H)
+    og32 = oracle_proj_to_gpu(O.project(planes, 0, cams32(cams)))
+    rect = gpu_proj_to_oracle(og32)[..., 12:16].astype(np.int32)
+    vis = (rect[..., 2] > rect[..., 0]) & (rect[..., 3] > rect[..., 1])
+    bits = og32[..., 2].copy().view(np.uint32)
+    lo = int(bits[vis].min())
+    far = np.flatnonzero(vis.reshape(-1))[-1]  # some visible record other than the nearest
+    depth = og32[..., 2].copy().reshape(-1)
+    depth.view(np.uint32)[far] = lo + span
+    og32[..., 2] = depth.reshape(og32.shape[:-1])
+    b2 = og32[..., 2].copy().view(np.uint32)[vis]
+    assert int(b2.max()) - int(b2.min()) == span
+    keys, vals, ranges = O.bin_sort(cams32(cams), rect, og32[..., 2].copy())
+    n = planes.shape[1]
+    for mode in ("two_level", "direct"):
+        ctx = gs.Context(0, 0, binning=mode)
+        cap = max(1 << 20, 2 * len(vals))
+        ctx.reserve(ctx.workspace_size(cams, n, cap))
+        d_cams = gs.cameras_to_device(cams)
+        proj = torch.from_numpy(np.ascontiguousarray(og32)).cuda()
+        k, v, r, nk = gs.gs_bin_sort(ctx, proj, d_cams, V, n, ctx.total_tiles(cams), cap)
+        torch.cuda.synchronize()
+        assert ctx.status()[0] == 0
+        K = int(nk.item())
+        assert K == len(vals) > 0
+        np.testing.assert_array_equal(v.cpu().numpy()[:K].view(np.uint32), vals)
+        np.testing.assert_array_equal(r.cpu().numpy().view(np.uint32), ranges)
+        ctx.close()
