@@ -1246,7 +1246,8 @@ void launch_bin_sort(const float* proj, const ViewInfo* vt, int V, int64_t n, in
         return;
     }
     // 1. depth sort of all (view, Gaussian) pairs: 32-bit keys, 4 passes of
-    //    8-bit digits ending back in dkv[0]
+    //    8-bit digits ending back in dkv[0] (with narrow keys the fourth
+    //    launch returns at once and the sort ends in dkv[1])
     if (!depth_ready) {
         k_range_reset<<<1, 1, 0, st>>>(s.drange);
         k_depth_keys<<<(unsigned)((items + 255) / 256), 256, 0, st>>>(pr, items, vt, V, s.dkv[0], s.rects,
