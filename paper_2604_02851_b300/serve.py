@@ -220,12 +220,18 @@ class RenderServer:
                         self._launch(slot, batch)
                         progressed = True
             if not progressed:
+                # a timed sleep overshoots by the kernel's timer slack (about
+                # 50 us), which would delay noticing a finished batch or an
+                # arrival: sleep only while the next arrival is more than 2 ms
+                # away and nothing runs, otherwise yield and poll again
                 if pending and not queue and all(s.event is None for s in self.slots):
                     wait = pending[0].t_arrival - (time.perf_counter() - start)
-                    if wait > 0:
-                        time.sleep(min(wait, 1e-3))
+                    if wait > 2e-3:
+                        time.sleep(min(wait - 1.5e-3, 1e-3))
+                    else:
+                        time.sleep(0)
                 else:
-                    time.sleep(2e-5)
+                    time.sleep(0)
         return done, time.perf_counter() - start
 
     def render_now(self, reqs) -> list:
