@@ -24,6 +24,7 @@ order, tile lists and pixels are computed independently of the other views.
 """
 from __future__ import annotations
 
+import gc
 import time
 from dataclasses import dataclass, field
 
@@ -196,14 +197,29 @@ class RenderServer:
         completed requests and the elapsed seconds."""
         for r in requests:
             self.estimate(r)
+        # the loop allocates events and small tensors per batch; a cyclic
+        # garbage collection pass in the middle of a burst would stall every
+        # queued request, so collection waits until the run ends (reference
+        # counting still frees everything the loop drops)
+        gc_was_on = gc.isenabled()
+        gc.disable()
+        try:
+            return self._serve(requests, realtime, t0)
+        finally:
+            if gc_was_on:
+                gc.enable()
+
+    def _serve(self, requests, realtime: bool, t0: float | None):
         pending = list(requests)
+        nxt = 0  # pending[nxt:] have not arrived yet
         queue, done = [], []
         start = time.perf_counter() if t0 is None else t0
         self._start = start
         while len(done) < len(requests):
             now = time.perf_counter() - start
-            while pending and (not realtime or pending[0].t_arrival <= now):
-                r = pending.pop(0)
+            while nxt < len(pending) and (not realtime or pending[nxt].t_arrival <= now):
+                r = pending[nxt]
+                nxt += 1
                 if not realtime:
                     r.t_arrival = 0.0
                 queue.append(r)
@@ -224,8 +240,8 @@ class RenderServer:
                 # 50 us), which would delay noticing a finished batch or an
                 # arrival: sleep only while the next arrival is more than 2 ms
                 # away and nothing runs, otherwise yield and poll again
-                if pending and not queue and all(s.event is None for s in self.slots):
-                    wait = pending[0].t_arrival - (time.perf_counter() - start)
+                if nxt < len(pending) and not queue and all(s.event is None for s in self.slots):
+                    wait = pending[nxt].t_arrival - (time.perf_counter() - start)
                     if wait > 2e-3:
                         time.sleep(min(wait - 1.5e-3, 1e-3))
                     else:
