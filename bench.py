@@ -41,7 +41,7 @@ WORKLOADS = {
     "c1_10k_128": (10_000, 0, 1, 128, 128),
     "prof_200k_8x720p": (200_000, 3, 8, 1280, 720),
     "c5_3M_8x1080p_dynamic": (3_000_000, 3, 8, 1920, 1080),
-    # config 3 plus 3M Gaussians above the scene, outside every view (a large
+    # the 1M-Gaussian 8 x 720p scene plus 3M Gaussians above it, outside every view (a large
     # world of which the cameras see a part; Sec. 3.3 preculling)
     "c3_far3M_8x720p": (4_000_000, 3, 8, 1280, 720),
 }
@@ -928,7 +928,7 @@ def run_ours(args, rank, world, local_rank):
 
 def serving_p99(serving, key="render_p99_ms"):
     """The p99 render latency (ms: arrival to the image complete in device
-    memory) of the config-4 run at 50 % of saturation (the metric's second
+    memory) of the 2M-Gaussian serving run at 50 % of saturation (the metric's second
     half), or of the load nearest to it; key="p99_ms": arrival to the image
     in host memory."""
     if not serving or not serving.get("loads"):
@@ -937,7 +937,7 @@ def serving_p99(serving, key="render_p99_ms"):
 
 
 def run_serving(args, local_rank, rank):
-    """Config 4: forward-only renders of a static 2M-Gaussian SH-3 model for
+    """Serving: forward-only renders of a static 2M-Gaussian SH-3 model for
     64 clients with Poisson arrivals, resolutions mixed 1280x720 / 1920x1080 /
     1440x1600 per eye, eyes within 0.3 of the ring of radius 3; continuous
     batching on 3 slots.  Saturation is measured first with every request

@@ -1,6 +1,6 @@
 """The differentiable render behind torch.autograd.Function (GaussianRasterize)
 and the loss behind L1DSSIMLoss: gradients through torch's autograd against
-the FP64 oracle (config 2: 100k Gaussians, SH degree 3, 4 views of 512x512)
+the FP64 oracle (100k Gaussians, SH degree 3, 4 views of 512x512)
 and against central differences of the float32 forward on a small scene."""
 import numpy as np
 import pytest

@@ -1,12 +1,12 @@
 """Parity at the benchmarked sizes, through the autotuned path bench.py times.
 
-* Config 3: 1M Gaussians, SH3, 8 views of 1280x720.
-* Config 5: 3M Gaussians in 16 rigid objects with the Lambertian DC factor,
-  8 views of 1920x1080 (ragged last tile row).
+* 1M Gaussians, SH3, 8 views of 1280x720 (the headline step).
+* 3M Gaussians in 16 rigid objects with the Lambertian DC factor, 8 views
+  of 1920x1080 (ragged last tile row).
 
 The FP64 oracle cannot redo whole steps of this size in a test's time.  It
-checks three sampled 16-row bands in each of three views (config 5 includes
-the ragged last band), plus everything that is cheap at full size.
+checks three sampled 16-row bands in each of three views (at 1080 rows they
+include the ragged last band), plus everything that is cheap at full size.
 
 Stage-wise (each GPU stage runs on the oracle's own float32 upstream results):
   * binning and sort of all 8 views: the entry count and the [start, end)
@@ -18,7 +18,7 @@ Stage-wise (each GPU stage runs on the oracle's own float32 upstream results):
   * raster adjoint, with an image gradient that is zero outside the bands:
     every Gaussian's 2D gradient within 1e-4;
   * projection adjoint of the oracle's 2D gradient within 1e-4;
-  * the loss at full size (config 5: two views) on seeded images; Adam and
+  * the loss at full size (at 3M x 1080p: two views) on seeded images; Adam and
     the delta extraction at the full parameter count on seeded inputs.
 
 End to end (the float32 GPU chain from the parameters against the FP64
@@ -348,7 +348,7 @@ def test_loss_adam_delta_full_size(case, tuned):
     import paper_2604_02851_b300 as gs
     ctx = tuned[0]
     rng = np.random.default_rng(33)
-    # loss on seeded images at full size (config 5: two of its views)
+    # loss on seeded images at full size (at 3M x 1080p: two of its views)
     V = case.V if case.n <= 1_000_000 else 2
     m = V * 3 * case.H * case.W
     x = rng.uniform(0.0, 1.0, m).astype(np.float32)
@@ -466,9 +466,9 @@ def test_train_step_equals_separate_calls(case, tuned):
     torch.cuda.empty_cache()
 
 
-# ---------------------------------------------------------------- config 4: serving renders
-def test_serving_render_bands_at_config_4():
-    """Config 4 (2M Gaussians, SH3, the three request resolutions in one
+# ---------------------------------------------------------------- serving renders
+def test_serving_render_bands_2M_mixed_resolutions():
+    """Serving renders (2M Gaussians, SH3, the three request resolutions in one
     batch): gs_render_batch (chunk-bitmap lists) equals the expanded-list
     compositing of the same projection bit for bit, and three 16-row bands of
     every request match the FP64 oracle's render within 1e-4, at the pixels
@@ -533,13 +533,13 @@ def test_serving_render_bands_at_config_4():
     o_cv, g_cv = compact(U, o_vals), compact(U, g_vals)
     same = same_sequences(cams, og_c, o_cv, o_ranges, gp_c, g_cv, g_ranges, B)
     use = pm & same
-    print("config 4: band pixels", int(pm.sum()), "with another kept sequence", int((pm & ~same).sum()))
+    print("serving: band pixels", int(pm.sum()), "with another kept sequence", int((pm & ~same).sum()))
     assert (pm & ~same).sum() <= 0.02 * pm.sum()
     o_img, _, _ = O.render(cams, og_c, o_cv, o_ranges, tile=B)
     use3 = np.concatenate([np.repeat(u.reshape(1, -1), 3, axis=0).ravel()
                            for u in np.split(use, np.cumsum([int(w) * int(h) for w, h in
                                                              zip(cams["width"], cams["height"])])[:-1])])
     e = rel_l2(img.cpu().numpy()[use3], o_img[use3])
-    print("config 4: band image rel-L2", e)
+    print("serving: band image rel-L2", e)
     assert e <= TOL
     ctx.close()
